@@ -1,0 +1,312 @@
+"""FP64 CPU oracle of the ERMC Q_rad estimator -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the CUDA library and its
+binding) never does.  The C source ``mcrt_oracle.c`` follows Section 2 and
+Algorithm 1 of Silvestri & Pecnik (arXiv:1810.00188); this module compiles it
+with gcc and marshals numpy arrays through ctypes.  Q_i, sigma_i and the parity
+scale S_i are formed here from the oracle's per-cell FP64 sums (Eq. 8: the
+estimate is the mean of the per-ray samples).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mcrt_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libmcrt_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE FP64, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mcrt_oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double),
+                ("T", C.POINTER(C.c_double)), ("xh2o", C.POINTER(C.c_double)),
+                ("eps_wall", C.c_double * 2), ("T_wall", C.c_double * 2),
+                ("reflect", C.c_int), ("n_bands", C.c_int), ("n_g", C.c_int),
+                ("w_g", C.POINTER(C.c_double)), ("T0", C.c_double), ("dT", C.c_double),
+                ("nT", C.c_int), ("kappa", C.POINTER(C.c_double)),
+                ("B", C.POINTER(C.c_double)), ("x_ref", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("rays_per_cell", C.c_int), ("ray_offset", C.c_uint64), ("seed", C.c_uint64),
+                ("snapshot", C.c_uint32), ("tol", C.c_double), ("max_steps", C.c_int),
+                ("origin", C.c_int), ("use_box", C.c_int), ("box", C.c_int * 6),
+                ("nthreads", C.c_int), ("cell_cn", C.POINTER(C.c_uint64)),
+                ("cell_cg", C.POINTER(C.c_uint64)), ("cell_hemi", C.POINTER(C.c_uint32))]
+
+
+class CellSums(C.Structure):
+    _fields_ = [("sum_y", C.POINTER(C.c_double)), ("sum_y2", C.POINTER(C.c_double)),
+                ("sum_abs", C.POINTER(C.c_double)), ("sum_wall", C.POINTER(C.c_double)),
+                ("sum_wall2", C.POINTER(C.c_double)), ("steps", C.POINTER(C.c_uint64)),
+                ("capped", C.POINTER(C.c_uint64))]
+
+
+class RayIn(C.Structure):
+    _fields_ = [("n", C.c_int), ("g", C.c_int), ("cell", C.c_int * 3), ("frac", C.c_double * 3),
+                ("dir", C.c_double * 3), ("tol", C.c_double), ("max_steps", C.c_int),
+                ("seed", C.c_uint64), ("ray", C.c_uint32), ("snapshot", C.c_uint32)]
+
+
+class RayOut(C.Structure):
+    _fields_ = [("X", C.c_double), ("abs_terms", C.c_double), ("X_wall", C.c_double),
+                ("tau_end", C.c_double), ("steps", C.c_int64), ("capped", C.c_int),
+                ("walls", C.c_int), ("path", C.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, up = C.POINTER(C.c_double), C.POINTER(C.c_uint64)
+            L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+            L.orc_philox_batch.argtypes = [C.POINTER(C.c_uint32), C.c_int64,
+                                           C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            L.orc_uniform.argtypes = [C.c_uint32]
+            L.orc_uniform.restype = C.c_double
+            L.orc_interp.argtypes = [dp, C.c_double, C.c_double, C.c_int, C.c_double]
+            L.orc_interp.restype = C.c_double
+            L.orc_quantize.argtypes = [dp, C.c_int, up]
+            L.orc_plain_proposal.argtypes = [C.POINTER(Problem), up, up, dp]
+            L.orc_trace_ray.argtypes = [C.POINTER(Problem), C.POINTER(RayIn), C.POINTER(RayOut)]
+            L.orc_solve.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.POINTER(CellSums)]
+            L.orc_exchange.argtypes = [C.POINTER(Problem), C.POINTER(Params), dp, dp, dp, dp]
+            L.orc_quadrature.argtypes = [C.POINTER(Problem), dp, dp, C.c_int, C.c_int, dp, dp,
+                                         C.c_int, C.c_int, C.c_double, C.c_int,
+                                         C.POINTER(C.c_int), C.c_int, C.c_int, dp]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Keep:
+    """Holds the numpy arrays a ctypes Problem points into."""
+
+
+def make_problem(grid, kd, T, x=None):
+    keep = _Keep()
+    keep.T = _f64(T).reshape(-1)
+    keep.x = None if x is None else _f64(x).reshape(-1)
+    keep.w = _f64(kd.w_g)
+    keep.k = _f64(kd.kappa).reshape(-1)
+    keep.B = _f64(kd.B).reshape(-1)
+    assert keep.T.size == grid.ncells
+    P = Problem()
+    P.nx, P.ny, P.nz = grid.nx, grid.ny, grid.nz
+    P.lx, P.ly, P.lz = grid.lx, grid.ly, grid.lz
+    P.T = _dp(keep.T)
+    P.xh2o = _dp(keep.x) if keep.x is not None else C.POINTER(C.c_double)()
+    P.eps_wall[0], P.eps_wall[1] = grid.eps_wall
+    P.T_wall[0], P.T_wall[1] = grid.T_wall
+    P.reflect = grid.reflect
+    P.n_bands, P.n_g = kd.n_bands, kd.n_g
+    P.w_g = _dp(keep.w)
+    P.T0, P.dT, P.nT = kd.T0, kd.dT, kd.nT
+    P.kappa = _dp(keep.k)
+    P.B = _dp(keep.B)
+    P.x_ref = kd.x_ref
+    P._keep = keep
+    return P
+
+
+def philox(ctr, key):
+    """Philox4x32-10 of counters ctr [n,4] (uint32) under key [2] -> [n,4] uint32."""
+    ctr = np.ascontiguousarray(np.atleast_2d(ctr), dtype=np.uint32)
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty_like(ctr)
+    u32 = C.POINTER(C.c_uint32)
+    lib().orc_philox_batch(ctr.ctypes.data_as(u32), ctr.shape[0], key.ctypes.data_as(u32),
+                           out.ctypes.data_as(u32))
+    return out
+
+
+def uniform(w):
+    return ((np.asarray(w, dtype=np.uint32) >> 9).astype(np.float64) + 0.5) * 2.0**-23
+
+
+def interp(v, T0, dT, T):
+    v = _f64(v)
+    return lib().orc_interp(_dp(v), T0, dT, v.size, float(T))
+
+
+def quantize(w):
+    w = _f64(w)
+    cum = np.zeros(w.size, dtype=np.uint64)
+    rc = lib().orc_quantize(_dp(w), w.size, cum.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc != 0:
+        raise ValueError("no positive weight")
+    return cum
+
+
+def plain_proposal(grid, kd, T, x=None):
+    """Cumulative band counts [nb], g counts [nb, ng] and T_max of the plain proposal."""
+    P = make_problem(grid, kd, T, x)
+    cn = np.zeros(kd.n_bands, dtype=np.uint64)
+    cg = np.zeros(kd.n_bands * kd.n_g, dtype=np.uint64)
+    tm = C.c_double()
+    up = C.POINTER(C.c_uint64)
+    rc = lib().orc_plain_proposal(C.byref(P), cn.ctypes.data_as(up), cg.ctypes.data_as(up),
+                                  C.byref(tm))
+    if rc != 0:
+        raise ValueError(f"orc_plain_proposal failed: {rc}")
+    return cn, cg.reshape(kd.n_bands, kd.n_g), tm.value
+
+
+def trace_ray(grid, kd, T, x, n, g, cell, frac, direction, tol=1e-4, max_steps=1 << 30,
+              seed=0, ray=0, snapshot=0):
+    P = make_problem(grid, kd, T, x)
+    R = RayIn()
+    R.n, R.g = n, g
+    for a in range(3):
+        R.cell[a] = int(cell[a])
+        R.frac[a] = float(frac[a])
+        R.dir[a] = float(direction[a])
+    R.tol, R.max_steps, R.seed, R.ray, R.snapshot = tol, max_steps, seed, ray, snapshot
+    O = RayOut()
+    if lib().orc_trace_ray(C.byref(P), C.byref(R), C.byref(O)) != 0:
+        raise ValueError("bad ray")
+    return {f: getattr(O, f) for f, _ in RayOut._fields_}
+
+
+def default_threads():
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+
+
+def _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthreads):
+    S = Params()
+    S.rays_per_cell, S.ray_offset, S.seed, S.snapshot = rays, ray_offset, seed, snapshot
+    S.tol, S.max_steps, S.origin = tol, max_steps, origin
+    S.use_box = 0 if box is None else 1
+    if box is not None:
+        for i in range(6):
+            S.box[i] = int(box[i])
+    S.nthreads = default_threads() if nthreads is None else nthreads
+    return S
+
+
+def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4,
+          max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None):
+    """Per-cell ERMC estimate over the box (whole grid when box is None).
+
+    Returns a dict of arrays shaped [bnz, bny, bnx]: q (Q_i, W/m^3), sigma
+    (standard error of q), scale (S_i = mean of w sum|terms|), q_wall and
+    sigma_wall (the wall-exchange part), steps and capped counts, and the raw
+    sums.  ``proposal`` = (cell_cn [nc, nb], cell_cg [nc, nb, ng], cell_hemi
+    [nc]) overrides the plain T_max proposal per emitting cell.
+    """
+    P = make_problem(grid, kd, T, x)
+    S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthreads)
+    b = box if box is not None else (0, grid.nx, 0, grid.ny, 0, grid.nz)
+    shape = (max(b[5] - b[4], 0), max(b[3] - b[2], 0), max(b[1] - b[0], 0))
+    nc = int(np.prod(shape))
+    keep = []
+    if proposal is not None:
+        cn, cg, hemi = proposal
+        cn = np.ascontiguousarray(cn, dtype=np.uint64).reshape(nc, kd.n_bands)
+        cg = np.ascontiguousarray(cg, dtype=np.uint64).reshape(nc, kd.n_bands * kd.n_g)
+        hemi = np.ascontiguousarray(hemi, dtype=np.uint32).reshape(nc)
+        keep += [cn, cg, hemi]
+        S.cell_cn = cn.ctypes.data_as(C.POINTER(C.c_uint64))
+        S.cell_cg = cg.ctypes.data_as(C.POINTER(C.c_uint64))
+        S.cell_hemi = hemi.ctypes.data_as(C.POINTER(C.c_uint32))
+    out = {k: np.zeros(nc) for k in ("sum_y", "sum_y2", "sum_abs", "sum_wall", "sum_wall2")}
+    out["steps"] = np.zeros(nc, dtype=np.uint64)
+    out["capped"] = np.zeros(nc, dtype=np.uint64)
+    Cs = CellSums()
+    for k in ("sum_y", "sum_y2", "sum_abs", "sum_wall", "sum_wall2"):
+        setattr(Cs, k, _dp(out[k]))
+    Cs.steps = out["steps"].ctypes.data_as(C.POINTER(C.c_uint64))
+    Cs.capped = out["capped"].ctypes.data_as(C.POINTER(C.c_uint64))
+    rc = lib().orc_solve(C.byref(P), C.byref(S), C.byref(Cs))
+    if rc != 0:
+        raise ValueError(f"orc_solve failed: {rc}")
+    N = float(rays)
+    res = {k: v.reshape(shape) for k, v in out.items()}
+    res["q"] = res["sum_y"] / N
+    res["scale"] = res["sum_abs"] / N
+    res["q_wall"] = res["sum_wall"] / N
+    if rays > 1:
+        res["sigma"] = np.sqrt(np.maximum(res["sum_y2"] / N - res["q"] ** 2, 0.0) / (N - 1.0))
+        res["sigma_wall"] = np.sqrt(np.maximum(res["sum_wall2"] / N - res["q_wall"] ** 2, 0.0)
+                                    / (N - 1.0))
+    else:
+        res["sigma"] = np.zeros(shape)
+        res["sigma_wall"] = np.zeros(shape)
+    return res
+
+
+def exchange(grid, kd, T, x=None, rays=128, seed=0, tol=1e-9, max_steps=1 << 30, origin=0):
+    """Per-pair exchange estimates G[i, j] = E[w kappa_i tau alpha_j] and their
+    standard errors, plus the wall exchange Gw[i, 2]."""
+    P = make_problem(grid, kd, T, x)
+    S = _params(rays, seed, 0, 0, tol, max_steps, origin, None, 1)
+    nc = grid.ncells
+    G, G2 = np.zeros((nc, nc)), np.zeros((nc, nc))
+    Gw, Gw2 = np.zeros((nc, 2)), np.zeros((nc, 2))
+    rc = lib().orc_exchange(C.byref(P), C.byref(S), _dp(G), _dp(G2), _dp(Gw), _dp(Gw2))
+    if rc != 0:
+        raise ValueError(f"orc_exchange failed: {rc}")
+    N = float(rays)
+    mean, meanw = G / N, Gw / N
+    se = np.sqrt(np.maximum(G2 / N - mean**2, 0.0) / (N - 1.0))
+    sew = np.sqrt(np.maximum(Gw2 / N - meanw**2, 0.0) / (N - 1.0))
+    return mean, se, meanw, sew
+
+
+def quadrature(grid, kd, T, x=None, cells=None, nmu_panels=32, nmu_per_panel=4, nphi=128,
+               nv=3, origin=0, tol=1e-12, max_steps=1 << 30, nthreads=None, origins=None):
+    """Deterministic quadrature of Q_i (same estimand, no random draws): composite
+    Gauss-Legendre in mu, midpoint in phi, and over the cell a Gauss-Legendre
+    tensor rule with nv points per axis, the mean over an explicit list of
+    origin fractions ``origins`` [m, 3] (origin 0), or the cell centre (origin 1)."""
+    P = make_problem(grid, kd, T, x)
+    xg, wg = np.polynomial.legendre.leggauss(nmu_per_panel)
+    edges = np.linspace(-1.0, 1.0, nmu_panels + 1)
+    mu = np.concatenate([0.5 * (b - a) * xg + 0.5 * (a + b) for a, b in zip(edges[:-1], edges[1:])])
+    mw = np.concatenate([0.5 * (b - a) * wg for a, b in zip(edges[:-1], edges[1:])])
+    if origins is not None:
+        vn = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1)
+        vw = np.full(vn.size // 3, 3.0 / vn.size)
+        nv = -(vn.size // 3)
+    else:
+        xv, wv = np.polynomial.legendre.leggauss(nv)
+        vn, vw = 0.5 * (xv + 1.0), 0.5 * wv
+    if cells is None:
+        cells = np.arange(grid.ncells)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    q = np.zeros(cells.size)
+    rc = lib().orc_quadrature(C.byref(P), _dp(_f64(mu)), _dp(_f64(mw)), mu.size, nphi,
+                              _dp(_f64(vn)), _dp(_f64(vw)), int(nv), origin, tol, max_steps,
+                              cells.ctypes.data_as(C.POINTER(C.c_int)), cells.size,
+                              default_threads() if nthreads is None else nthreads, _dp(q))
+    if rc != 0:
+        raise ValueError(f"orc_quadrature failed: {rc}")
+    return q

@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the ERMC Q_rad solve on GB300.
+
+Workload (one "step" = one full solve): the non-grey turbulent channel on a
+64^3 grid (4 pi x 2 x 2 pi m), 40 narrow bands x 8 g-points of synthetic
+correlated-k tables, black walls at 500 / 1000 K, 1000 rays per cell, FP32
+traversal with FP64 tallies.  Each step traces a fresh block of ray indices
+(ray_offset advances), so no result is reused.  Under torchrun every rank solves
+its own snapshot (field seed = rank): weak scaling with no data-path collective.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-cell steps/s"
+UNIT = "steps/s"
+MUFU_EX2_PER_CLK_PER_SM = 16  # MUFU.EX2 results per clock per SM
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="grid is n^3")
+    ap.add_argument("--rays", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"nongrey_channel_{a.n}x{a.n}x{a.n}_40x8kdist_{a.rays}rays",
+            "grid": [a.n, a.n, a.n], "box_m": [4 * math.pi, 2.0, 2 * math.pi],
+            "rays_per_cell": a.rays, "bands": 40, "g_points": 8, "tol": 1e-4,
+            "walls": "black, 500 K / 1000 K", "x_h2o": 0.1,
+            "T_field": "linear 500->1000 K + 5% k^-5/3 Gaussian random field",
+            "precision": "fp32 traversal, fp64 compensated tallies",
+            "l2": "flushed between timed steps (256 MiB write)", "seed": 0}
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(a, target_s=12.0):
+    """The FP64 oracle on the host cores on z-slabs of the same workload."""
+    import oracle
+    from paper_1810_00188_gb300 import inputs
+    grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=0)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    r = oracle.solve(grid, kd, T, x, rays=a.rays, seed=0, tol=1e-4, max_steps=1 << 20,
+                     box=(0, a.n, 0, a.n, 0, 1), nthreads=threads)
+    t1 = time.perf_counter() - t0
+    planes = max(1, min(a.n, int(round(target_s / max(t1, 1e-3)))))
+    t0 = time.perf_counter()
+    r = oracle.solve(grid, kd, T, x, rays=a.rays, seed=0, tol=1e-4, max_steps=1 << 20,
+                     box=(0, a.n, 0, a.n, 1, 1 + min(planes, a.n - 1)), nthreads=threads)
+    dt = time.perf_counter() - t0
+    steps = float(r["steps"].sum())
+    return {"value": steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{min(planes, a.n - 1)} z-planes ({a.n}x{a.n} cells each) x {a.rays} rays, "
+                      f"{steps:.3g} steps in {dt:.1f} s"}
+
+
+def run_reference(a):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1810_00188_gb300 import inputs
+    grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=0)
+    threads = oracle.default_threads()
+
+    def one(k):
+        z = k % a.n
+        t0 = time.perf_counter()
+        r = oracle.solve(grid, kd, T, x, rays=a.rays, seed=0, tol=1e-4, max_steps=1 << 20,
+                         box=(0, a.n, 0, a.n, z, z + 1), nthreads=threads, ray_offset=0)
+        return float(r["steps"].sum()), time.perf_counter() - t0
+
+    for k in range(a.warmup):
+        one(k)
+    tot_s, tot_t = 0.0, 0.0
+    for k in range(a.steps):
+        s, t = one(a.warmup + k)
+        tot_s += s
+        tot_t += t
+    v = tot_s / tot_t
+    cfg = workload_config(a)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"one z-plane ({a.n}x{a.n} cells) x {a.rays} rays per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_00188_gb300 import inputs, mcrt
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allreduce(v, op):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=rank)
+    S = mcrt.Solver(grid, kd, device=local)
+    Td = torch.tensor(T, device="cuda")
+    xd = torch.tensor(x, device="cuda")
+    S.set_fields(Td, xd)
+    q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+    s = torch.empty_like(q)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def params(k, prec=mcrt.MCRT_FP32, rays=a.rays):
+        return S.params(rays=rays, seed=0, snapshot=rank, ray_offset=k * rays, tol=1e-4,
+                        max_steps=1 << 20, precision=prec)
+
+    for k in range(a.warmup):
+        S.solve_into(params(k), q, s, stream=sp)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    steps_total, kern_ms, launches = 0, [], 0
+    for k in range(a.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        S.solve_into(params(a.warmup + k), q, s, stream=sp)
+        ev[k][1].record(stream)
+        st = S.stats()  # waits for this solve
+        steps_total += st["steps"]
+        kern_ms.append(st["kernel_ms"])
+        launches += st["launches"]
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_local = sum(step_ms) / 1e3
+    t_max = allreduce(t_local, dist.ReduceOp.MAX if world > 1 else None)
+    steps_all = allreduce(float(steps_total), dist.ReduceOp.SUM if world > 1 else None)
+    value = steps_all / t_max
+    rays_all = float(world * a.steps) * grid.ncells * a.rays
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * sm_max * 1e6  # exp/s = steps/s ceiling
+    kernel_s = statistics.mean(kern_ms) / 1e3
+    steps_per_launch = steps_total / a.steps
+    achieved = steps_per_launch / kernel_s
+    hbm = float(peaks.get("hbm_gbs", 6789.3))
+
+    result = None
+    if rank == 0:
+        result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                  "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps,
+                  "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                  "dtype": "f32", "data": "synthetic", "config": workload_config(a),
+                  "rays_per_s": rays_all / t_max,
+                  "steps_per_ray": steps_total / (a.steps * grid.ncells * a.rays),
+                  "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ex2_peak / 1e9,
+                               "unit": "Gsteps/s", "frac": achieved / ex2_peak, "traffic": None,
+                               "peak_basis": f"MUFU ex2: {N_SM} SM x {MUFU_EX2_PER_CLK_PER_SM}/clk x "
+                                             f"{sm_max:.0f} MHz (1 exp per step)",
+                               "gather_GBs": achieved * 8 / 1e9,
+                               "gather_frac_of_hbm": achieved * 8 / 1e9 / hbm},
+                  "gpu_launches": launches, "clocks": clk}
+    # --- extras on rank 0: e2e through host buffers, FP64, solves/s at 1% sigma
+    if rank == 0:
+        Tp = torch.tensor(T).pin_memory()
+        xp = torch.tensor(x).pin_memory()
+        qh = torch.empty(grid.shape, dtype=torch.float64).pin_memory()
+        sh = torch.empty_like(qh).pin_memory()
+        ke = max(1, min(a.steps, 5))
+        torch.cuda.synchronize()
+        e_steps, t0 = 0, time.perf_counter()
+        for k in range(ke):
+            S.set_fields(Tp.numpy(), xp.numpy())
+            S.solve_into(params(a.warmup + k), qh.numpy(), sh.numpy())
+            e_steps += S.stats()["steps"]
+        te = time.perf_counter() - t0
+        result["e2e"] = {"value": e_steps / te, "unit": UNIT,
+                         "h2d_bytes_per_step": int(Tp.numel() * 8 + xp.numel() * 8),
+                         "d2h_bytes_per_step": int(qh.numel() * 8 + sh.numel() * 8)}
+        if not a.no_extras:
+            S.set_fields(Td, xd)
+            # FP64 traversal throughput on a tenth of the rays
+            r64 = max(32, a.rays // 10)
+            S.solve_into(params(0, mcrt.MCRT_FP64, r64), q, s, stream=sp)
+            st = S.stats()
+            result["fp64_steps_per_s"] = st["steps"] / (st["kernel_ms"] / 1e3)
+            # Q_rad solves/s at 1% cell sigma: N* from the 1000-ray sigma, then verified
+            S.solve_into(params(0), q, s, stream=sp)
+            qn, sn = q.cpu().numpy(), s.cpu().numpy()
+            ref = np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
+            p95 = float(np.percentile(sn / ref, 95))
+            nstar = int(math.ceil(a.rays * (p95 / 0.01) ** 2))
+            sol = {"rays_needed": nstar, "p95_rel_sigma_at_base": p95}
+            if nstar <= 64 * a.rays:
+                S.solve_into(params(0, rays=nstar), q, s, stream=sp)
+                st = S.stats()
+                qn, sn = q.cpu().numpy(), s.cpu().numpy()
+                ref = np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
+                sol["verified_p95_rel_sigma"] = float(np.percentile(sn / ref, 95))
+                sol["solve_s"] = st["kernel_ms"] / 1e3
+                sol["value"] = 1e3 / st["kernel_ms"]
+            else:
+                sol["value"] = value / (steps_per_launch / a.rays * nstar)
+            result["qrad_solves_per_s_at_1pct_sigma"] = sol
+            result["learned_vs_plain"] = None
+        if not a.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(a)
+        print(json.dumps(result), flush=True)
+    barrier()
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

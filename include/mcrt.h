@@ -1,0 +1,178 @@
+/*
+ * mcrt.h -- C ABI of the GB300 reciprocal Monte Carlo radiative-transfer library.
+ *
+ * The library computes the radiative source Q_rad [W/m^3] of every cell of a 3D
+ * Cartesian channel grid with the emission-based reciprocal Monte Carlo (ERMC)
+ * method of Silvestri & Pecnik (arXiv:1810.00188): Section 2 (Eqs. 1-14), the
+ * narrow-band correlated-k sampling of Section 2.1 (Eqs. 15-17), and the
+ * initialise / march / residual-dump steps of Algorithm 1.  The paper's problem
+ * statement (Section 2.2, Algorithm 2) gives the inputs: the grid, the
+ * temperature field, the absorption-coefficient and blackbody tables, the number
+ * of rays per cell and the transmissivity cut-off; the output is Q_rad per cell.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an mcrt_status code and never throws or aborts.
+ *  - Arrays are plain pointers.  `mem` says whether a pointer is host memory
+ *    (MCRT_MEM_HOST) or device memory of the context's GPU (MCRT_MEM_DEVICE).
+ *  - Field arrays are [nz][ny][nx] with x fastest: cell (i,j,k) is element
+ *    i + nx*(j + ny*k).  y is the wall-normal direction; x and z are periodic.
+ *  - set_* calls COPY their inputs into library-owned device memory; the caller
+ *    keeps ownership of its pointers and may reuse them when the call returns.
+ *  - Output buffers are caller-owned and hold one value per emitting cell of the
+ *    solve's box, x fastest within the box.
+ *  - `cuda_stream` is a cudaStream_t (NULL: the legacy default stream).  Device
+ *    work is ordered on that stream.  With MCRT_MEM_DEVICE outputs the solve is
+ *    asynchronous (like the paper's kickoff kernel, Algorithm 2); with
+ *    MCRT_MEM_HOST outputs it returns after the results are on the host.
+ *  - A context belongs to one thread at a time.  There is no CPU fallback: a
+ *    missing or unusable GPU yields MCRT_E_CUDA.
+ */
+#ifndef MCRT_H
+#define MCRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcrt_ctx mcrt_ctx; /* opaque, library-owned */
+
+typedef enum {
+  MCRT_OK = 0,
+  MCRT_E_ARG = 1,         /* NULL pointer, bad size, value out of its domain    */
+  MCRT_E_STATE = 2,       /* solve before set_kdist / set_fields                */
+  MCRT_E_CUDA = 3,        /* CUDA runtime error (no device, launch failure, ...) */
+  MCRT_E_OOM = 4,         /* device allocation failed                           */
+  MCRT_E_RANGE = 5,       /* non-finite or non-positive T, negative or NaN x     */
+  MCRT_E_TIMEOUT = 6,     /* a bounded device-side wait gave up                 */
+  MCRT_E_UNSUPPORTED = 7  /* valid request this build does not implement         */
+} mcrt_status;
+
+enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };
+/* MCRT_FP32: traversal, table lookups and exp in binary32, ray weights and all
+ * per-cell tallies in binary64 (compensated).  MCRT_FP64: everything binary64. */
+enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
+/* Ray origin: uniform in the cell volume (f_V = 1/V_i, Eq. 4) or the cell centre
+ * (Algorithm 1, "ray.pos <- cell.center"). */
+enum { MCRT_ORIGIN_UNIFORM = 0, MCRT_ORIGIN_CENTER = 1 };
+/* Spectral/directional proposal: Zhang's T_max Planck-kappa pdf (Eq. 13,
+ * discretised as Eq. 16) with isotropic directions, or per-cell pdfs supplied by
+ * mcrt_set_cell_proposal. */
+enum { MCRT_PROPOSAL_PLANCK_TMAX = 0, MCRT_PROPOSAL_CELL = 1 };
+enum { MCRT_REFLECT_DIFFUSE = 0, MCRT_REFLECT_SPECULAR = 1 };
+
+/* Grid and walls (Section 2.2: finite volumes with index (i,j,k); Eq. 3: the
+ * wall emissivity eps_w enters the transmissivity).  Uniform cells of size
+ * lx/nx x ly/ny x lz/nz.  Wall 0 is y = 0, wall 1 is y = ly.  eps_wall = 1 is a
+ * black wall (the ray ends there); 0 <= eps < 1 reflects the rest. */
+typedef struct {
+  int nx, ny, nz;          /* >= 1 each; nx*ny*nz < 2^31                          */
+  double lx, ly, lz;       /* box lengths [m], > 0                                */
+  double eps_wall[2];      /* in [0, 1]                                           */
+  double T_wall[2];        /* [K], >= 0                                           */
+  int reflect;             /* MCRT_REFLECT_*                                      */
+  int device;              /* CUDA device ordinal                                 */
+} mcrt_grid_desc;
+
+/* Narrow-band correlated-k tables (Section 2.1, Eq. 16; Section 2.2: tabulated
+ * blackbody intensity and absorption coefficient, linear interpolation in T).
+ * T nodes are T0 + t*dT, t = 0..nT-1; temperatures outside are clamped to the
+ * end nodes.  kappa(T, x) = kappa_table(T) * x / x_ref. */
+typedef struct {
+  int n_bands, n_g;        /* n_bands in [1, 1024], n_g in [1, 64]               */
+  const double *w_g;       /* [n_g] quadrature weights, >= 0                      */
+  double T0, dT;           /* dT > 0                                              */
+  int nT;                  /* >= 2                                                */
+  const double *kappa;     /* [n_bands][n_g][nT] [1/m] at x_ref, finite, >= 0     */
+  const double *B;         /* [n_bands][nT] band intensity [W m^-2 sr^-1], >= 0   */
+  double x_ref;            /* > 0                                                 */
+} mcrt_kdist_desc;
+
+typedef struct {
+  int rays_per_cell;       /* N_r of Eq. 8, >= 1                                  */
+  int max_steps;           /* cap on medium segments per ray (>= 1); a capped ray
+                              dumps its residual like the tol cut-off            */
+  double tol;              /* transmissivity cut-off of Algorithm 1, in (0, 1)    */
+  uint64_t seed;           /* Philox key                                          */
+  uint64_t ray_offset;     /* rays use indices ray_offset .. ray_offset+N-1       */
+  uint32_t snapshot;       /* fourth Philox counter word                          */
+  int precision;           /* MCRT_FP32 or MCRT_FP64                              */
+  int origin;              /* MCRT_ORIGIN_*                                       */
+  int proposal;            /* MCRT_PROPOSAL_*                                     */
+  int use_box;             /* 0: all cells emit; 1: only the box below            */
+  int box[6];              /* i0,i1,j0,j1,k0,k1, half-open, may be empty          */
+  uint64_t *steps_out;     /* optional per-cell medium-segment counts (same `mem`
+                              as the outputs), or NULL                           */
+} mcrt_solve_params;
+
+typedef struct {
+  uint64_t steps;          /* medium segments marched by the last solve           */
+  uint64_t rays;           /* rays traced                                         */
+  uint64_t capped;         /* rays stopped by max_steps                           */
+  uint64_t wall_hits;      /* wall events                                         */
+  double T_max;            /* temperature of the plain proposal (Eq. 13)          */
+  float kernel_ms;         /* device time of the last solve's trace launch        */
+  int launches;            /* kernels the last solve launched                     */
+} mcrt_solve_stats;
+
+/* Creates a context on grid->device.  *out receives the handle (NULL on error).
+ * Errors: MCRT_E_ARG (bad geometry / walls), MCRT_E_CUDA (no such device). */
+int mcrt_create(const mcrt_grid_desc *grid, mcrt_ctx **out);
+
+/* Copies the k-distribution tables (Section 2.1-2.2) to the device and builds
+ * the FP32 and FP64 interpolation nodes.  Synchronous.  Errors: MCRT_E_ARG. */
+int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd);
+
+/* Copies the temperature field T [K] and the H2O mole fraction x (NULL: x_ref
+ * everywhere) into the context -- the paper's host-to-device copy of T
+ * (Algorithm 2).  dtype_is_fp64 selects double (1) or float (0) inputs.
+ * Validates the field and finds its maximum temperature (one device reduction
+ * and a 32-byte read-back on cuda_stream: the call returns after it).
+ * Errors: MCRT_E_ARG, MCRT_E_STATE (x_h2o = NULL before mcrt_set_kdist, which
+ * supplies x_ref), MCRT_E_RANGE (NaN/inf or T <= 0, x < 0 or non-finite: the
+ * field is rejected and the previous one is forgotten). */
+int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x_h2o, int dtype_is_fp64, int mem,
+                    void *cuda_stream);
+
+/* Supplies per-emitting-cell proposals for MCRT_PROPOSAL_CELL solves (one per
+ * cell of the whole grid): cumulative counts of 2^32 over the bands
+ * cn[ncells][n_bands] and over g within each band cg[ncells][n_bands][n_g] (each
+ * row non-decreasing, last entry 2^32, a band/g with non-zero kappa must have a
+ * non-zero count for the estimate to stay unbiased), and the upward-hemisphere
+ * (d_y > 0) count hemi[ncells] of 2^23 in [1, 2^23 - 1].  The ray weight uses
+ * these exact probabilities (Eq. 14 with the pdfs of Eqs. 4, 9, 16 replaced).
+ * Copies; synchronous.  Errors: MCRT_E_ARG, MCRT_E_STATE (no kdist). */
+int mcrt_set_cell_proposal(mcrt_ctx *ctx, const uint64_t *cn, const uint64_t *cg,
+                           const uint32_t *hemi, int mem, void *cuda_stream);
+
+/* Estimates Q_rad for every emitting cell of the box: rays_per_cell rays per
+ * cell, each drawn with Philox4x32-10 at counter (cell, ray, block, snapshot)
+ * and key seed, marched cell by cell until tau <= tol, a black wall, or
+ * max_steps, tallying kappa_i (I_b,i - I_b,j) tau alpha_j (Eqs. 2, 3, 14) and the
+ * residual dump of Algorithm 1.  q_out[c] = the mean of the per-ray samples
+ * (Eq. 8) in W/m^3 (> 0: the cell cools); sigma_out[c] (nullable) = its
+ * standard error.  Output pointers are caller-owned, box-sized, `mem` memory.
+ * Errors: MCRT_E_ARG, MCRT_E_STATE (no fields or kdist, or no cell proposal for
+ * MCRT_PROPOSAL_CELL), MCRT_E_CUDA, MCRT_E_OOM. */
+int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, double *sigma_out,
+                    int mem, void *cuda_stream);
+
+/* Waits for the last solve and reports its counters.  Errors: MCRT_E_STATE (no
+ * solve yet), MCRT_E_CUDA. */
+int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
+
+/* Releases all device memory of the context; NULL is accepted.  Waits for the
+ * context's outstanding work. */
+int mcrt_destroy(mcrt_ctx *ctx);
+
+/* Static description of a status code. */
+const char *mcrt_status_string(int status);
+
+/* Message of the last error raised on this context (empty if none). */
+const char *mcrt_last_error(const mcrt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCRT_H */

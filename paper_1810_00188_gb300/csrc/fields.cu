@@ -1,0 +1,70 @@
+// Field staging: packs the temperature T and H2O mole fraction x of every cell
+// into the interleaved {T, x} layouts the trace kernel gathers (one 8- or
+// 16-byte load per traversed cell), and reduces the maximum / minimum valid
+// temperature and the number of rejected cells in the same pass.  The maximum
+// feeds T_max of the spectral proposal (Eq. 13).
+#include <math.h>
+
+#include "mcrt_internal.h"
+
+namespace mcrt {
+namespace {
+
+__global__ void __launch_bounds__(256) pack_fields_kernel(const void *T, const void *x, int fp64_in,
+                                                          double x_ref, long long n, double2 *f64,
+                                                          float2 *f32,
+                                                          unsigned long long *stats) {
+  unsigned long long tmax = 0ull, tmin = ~0ull, bad = 0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double t, xv;
+    if (fp64_in) {
+      t = ((const double *)T)[i];
+      xv = x ? ((const double *)x)[i] : x_ref;
+    } else {
+      t = (double)((const float *)T)[i];
+      xv = x ? (double)((const float *)x)[i] : x_ref;
+    }
+    const bool ok = isfinite(t) && t > 0.0 && isfinite(xv) && xv >= 0.0;
+    if (ok) {
+      // positive doubles order like their bit patterns
+      const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+      tmax = b > tmax ? b : tmax;
+      tmin = b < tmin ? b : tmin;
+    } else {
+      ++bad;
+    }
+    f64[i] = make_double2(t, xv);
+    f32[i] = make_float2((float)t, (float)xv);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, tmax, off);
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, tmin, off);
+    tmax = a > tmax ? a : tmax;
+    tmin = b < tmin ? b : tmin;
+    bad += __shfl_xor_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(stats + 0, tmax);
+    atomicMin(stats + 1, tmin);
+    if (bad) atomicAdd(stats + 2, bad);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
+                               long long n, double2 *f64, float2 *f32,
+                               unsigned long long *stats, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(stats + 1, 0xff, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;  // grid-stride: 16 blocks per SM
+  pack_fields_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, x, fp64_in, x_ref, n, f64, f32, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace mcrt

@@ -1,0 +1,581 @@
+// C ABI of the reciprocal Monte Carlo Q_rad library (declared in include/mcrt.h).
+//
+// Host side only: argument validation, library-owned device buffers, the
+// FP64 construction of the quantised spectral proposal (Eq. 13 discretised as
+// Eq. 16), and the launches.  Every step of the solve runs in the CUDA kernels
+// of trace.cu and fields.cu; nothing here computes Q on the CPU.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mcrt.h"
+#include "mcrt_internal.h"
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mcrt_ctx {
+  mcrt_grid_desc grid{};
+  // k-distribution (host copy, FP64)
+  bool have_kdist = false;
+  int nb = 0, ng = 0, nT = 0;
+  double T0 = 0, dT = 1, x_ref = 1;
+  std::vector<double> w_g, kappa, B;
+  // fields
+  bool have_fields = false;
+  double T_max_field = 0, T_min_field = 0;
+  // cell proposal
+  bool have_cell_prop = false;
+  // plain proposal cache (valid for prop_T_max)
+  bool prop_valid = false;
+  double prop_T_max = -1;
+  // device buffers
+  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, cn, cg,
+      cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool solved = false;
+  int last_launches = 0;
+  double last_T_max = 0;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int fail(mcrt_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(mcrt_ctx *c, cudaError_t e, const char *where) {
+  cudaGetLastError();  // clear a sticky non-fatal error
+  const int code = e == cudaErrorMemoryAllocation ? MCRT_E_OOM : MCRT_E_CUDA;
+  return fail(c, code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+cudaError_t ensure(DevBuf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool finite_nonneg(const double *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i]) || v[i] < 0.0) return false;
+  return true;
+}
+
+// Linear interpolation on the uniform T nodes with clamping (Section 2.2).
+double interp_host(const double *v, double T0, double dT, int nT, double T) {
+  const double f = (T - T0) / dT;
+  double t = std::floor(f);
+  double frac;
+  if (t < 0.0) {
+    t = 0.0;
+    frac = 0.0;
+  } else if (t >= (double)(nT - 1)) {
+    t = (double)(nT - 2);
+    frac = 1.0;
+  } else {
+    frac = f - t;
+  }
+  const int it = (int)t;
+  return v[it] + frac * (v[it + 1] - v[it]);
+}
+
+// Integer counts of 2^32 proportional to the weights: every positive weight
+// gets at least one count (so every contributing (n, g) stays drawable and the
+// estimate stays unbiased), the rounding remainder goes to the first largest
+// weight.  Writes cumulative counts; false when no weight is positive.
+bool quantize_counts(const double *w, int K, unsigned long long *cum) {
+  double W = 0.0;
+  for (int k = 0; k < K; ++k) W += w[k];
+  if (!(W > 0.0)) return false;
+  int kmax = 0;
+  for (int k = 1; k < K; ++k)
+    if (w[k] > w[kmax]) kmax = k;
+  std::vector<long long> m(K);
+  long long total = 0;
+  for (int k = 0; k < K; ++k) {
+    if (w[k] > 0.0) {
+      const long long mk = (long long)std::floor((w[k] / W) * 4294967296.0);
+      m[k] = mk < 1 ? 1 : mk;
+    } else {
+      m[k] = 0;
+    }
+    total += m[k];
+  }
+  m[kmax] += 4294967296LL - total;
+  unsigned long long acc = 0;
+  for (int k = 0; k < K; ++k) {
+    acc += (unsigned long long)m[k];
+    cum[k] = acc;
+  }
+  return true;
+}
+
+// Zhang's T_max proposal (Eq. 13) in the narrow-band form of Eq. 16:
+// f_n ~ B_n(T_max) sum_g w_g k_{n,g}(T_max) and f_g(n) ~ w_g k_{n,g}(T_max).
+int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
+  const int nb = ctx->nb, ng = ctx->ng, nT = ctx->nT;
+  std::vector<unsigned long long> cn(nb), cg((size_t)nb * ng);
+  std::vector<double> wn(nb), wgv(ng);
+  for (int n = 0; n < nb; ++n) {
+    double sum = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      wgv[g] = ctx->w_g[g] *
+               interp_host(ctx->kappa.data() + ((size_t)n * ng + g) * nT, ctx->T0, ctx->dT, nT, Tm);
+      sum += wgv[g];
+    }
+    wn[n] = interp_host(ctx->B.data() + (size_t)n * nT, ctx->T0, ctx->dT, nT, Tm) * sum;
+    if (!quantize_counts(wgv.data(), ng, cg.data() + (size_t)n * ng)) {
+      for (int g = 0; g < ng; ++g) wgv[g] = 1.0;  // never drawn; keep rows valid
+      quantize_counts(wgv.data(), ng, cg.data() + (size_t)n * ng);
+    }
+  }
+  if (!quantize_counts(wn.data(), nb, cn.data()))
+    return fail(ctx, MCRT_E_ARG, "no band emits at T_max (all kappa*B are zero)");
+  CK(cudaMemcpyAsync(ctx->cn.p, cn.data(), sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s),
+     "upload band counts");
+  CK(cudaMemcpyAsync(ctx->cg.p, cg.data(), sizeof(unsigned long long) * nb * ng,
+                     cudaMemcpyHostToDevice, s),
+     "upload g counts");
+  // pageable sources: the copies are staged before cudaMemcpyAsync returns
+  ctx->prop_valid = true;
+  ctx->prop_T_max = Tm;
+  return MCRT_OK;
+}
+
+double proposal_T_max(const mcrt_ctx *ctx) {
+  double Tm = ctx->T_max_field;
+  for (int w = 0; w < 2; ++w)
+    if (ctx->grid.eps_wall[w] > 0.0 && ctx->grid.T_wall[w] > Tm) Tm = ctx->grid.T_wall[w];
+  return Tm;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mcrt_status_string(int status) {
+  switch (status) {
+    case MCRT_OK: return "ok";
+    case MCRT_E_ARG: return "invalid argument";
+    case MCRT_E_STATE: return "call out of order";
+    case MCRT_E_CUDA: return "CUDA error";
+    case MCRT_E_OOM: return "device out of memory";
+    case MCRT_E_RANGE: return "field value out of range";
+    case MCRT_E_TIMEOUT: return "device wait timed out";
+    case MCRT_E_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char *mcrt_last_error(const mcrt_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
+  if (!out) return MCRT_E_ARG;
+  *out = nullptr;
+  if (!g) return MCRT_E_ARG;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return MCRT_E_ARG;
+  if ((long long)g->nx * g->ny * g->nz >= (1LL << 31)) return MCRT_E_ARG;
+  if (!(g->lx > 0) || !(g->ly > 0) || !(g->lz > 0) || !std::isfinite(g->lx) ||
+      !std::isfinite(g->ly) || !std::isfinite(g->lz))
+    return MCRT_E_ARG;
+  for (int w = 0; w < 2; ++w) {
+    if (!(g->eps_wall[w] >= 0.0 && g->eps_wall[w] <= 1.0)) return MCRT_E_ARG;
+    if (!(g->T_wall[w] >= 0.0) || !std::isfinite(g->T_wall[w])) return MCRT_E_ARG;
+  }
+  if (g->reflect != MCRT_REFLECT_DIFFUSE && g->reflect != MCRT_REFLECT_SPECULAR) return MCRT_E_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || g->device < 0 || g->device >= ndev) {
+    cudaGetLastError();
+    return MCRT_E_CUDA;
+  }
+  mcrt_ctx *ctx = new (std::nothrow) mcrt_ctx();
+  if (!ctx) return MCRT_E_OOM;
+  ctx->grid = *g;
+  DeviceGuard dg(g->device);
+  if (!dg.ok || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+      ensure(ctx->counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      ensure(ctx->fstats, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    mcrt_destroy(ctx);
+    return MCRT_E_CUDA;
+  }
+  *out = ctx;
+  return MCRT_OK;
+}
+
+int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!kd || !kd->w_g || !kd->kappa || !kd->B) return fail(ctx, MCRT_E_ARG, "null table");
+  if (kd->n_bands < 1 || kd->n_bands > 1024 || kd->n_g < 1 || kd->n_g > 64 || kd->nT < 2 ||
+      kd->nT > (1 << 20))
+    return fail(ctx, MCRT_E_ARG, "table sizes out of range");
+  if (!(kd->dT > 0) || !std::isfinite(kd->dT) || !std::isfinite(kd->T0) || !(kd->x_ref > 0) ||
+      !std::isfinite(kd->x_ref))
+    return fail(ctx, MCRT_E_ARG, "bad T axis or x_ref");
+  const int nb = kd->n_bands, ng = kd->n_g, nT = kd->nT;
+  const size_t nk = (size_t)nb * ng * nT, nbT = (size_t)nb * nT;
+  if (!finite_nonneg(kd->w_g, ng) || !finite_nonneg(kd->kappa, nk) || !finite_nonneg(kd->B, nbT))
+    return fail(ctx, MCRT_E_ARG, "negative or non-finite table entry");
+  DeviceGuard dg(ctx->grid.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  ctx->have_kdist = false;
+  ctx->prop_valid = false;
+  ctx->have_cell_prop = false;
+  ctx->nb = nb;
+  ctx->ng = ng;
+  ctx->nT = nT;
+  ctx->T0 = kd->T0;
+  ctx->dT = kd->dT;
+  ctx->x_ref = kd->x_ref;
+  ctx->w_g.assign(kd->w_g, kd->w_g + ng);
+  ctx->kappa.assign(kd->kappa, kd->kappa + nk);
+  ctx->B.assign(kd->B, kd->B + nbT);
+  // interpolation nodes {v_t, v_{t+1} - v_t}; the last node repeats with zero slope
+  std::vector<double2> k64(nk), b64(nbT);
+  std::vector<float2> k32(nk), b32(nbT);
+  for (size_t r = 0; r < (size_t)nb * ng; ++r)
+    for (int t = 0; t < nT; ++t) {
+      const double v = kd->kappa[r * nT + t];
+      const double dv = t + 1 < nT ? kd->kappa[r * nT + t + 1] - v : 0.0;
+      k64[r * nT + t] = make_double2(v, dv);
+      k32[r * nT + t] = make_float2((float)v, (float)dv);
+    }
+  for (size_t r = 0; r < (size_t)nb; ++r)
+    for (int t = 0; t < nT; ++t) {
+      const double v = kd->B[r * nT + t];
+      const double dv = t + 1 < nT ? kd->B[r * nT + t + 1] - v : 0.0;
+      b64[r * nT + t] = make_double2(v, dv);
+      b32[r * nT + t] = make_float2((float)v, (float)dv);
+    }
+  std::vector<double> bw64(2 * (size_t)nb);
+  std::vector<float> bw32(2 * (size_t)nb);
+  for (int w = 0; w < 2; ++w)
+    for (int n = 0; n < nb; ++n) {
+      bw64[w * nb + n] =
+          interp_host(kd->B + (size_t)n * nT, kd->T0, kd->dT, nT, ctx->grid.T_wall[w]);
+      bw32[w * nb + n] = (float)bw64[w * nb + n];
+    }
+  CK(ensure(ctx->ktab64, nk * sizeof(double2)), "alloc kappa table");
+  CK(ensure(ctx->ktab32, nk * sizeof(float2)), "alloc kappa table");
+  CK(ensure(ctx->btab64, nbT * sizeof(double2)), "alloc B table");
+  CK(ensure(ctx->btab32, nbT * sizeof(float2)), "alloc B table");
+  CK(ensure(ctx->bwall64, 2 * nb * sizeof(double)), "alloc wall B");
+  CK(ensure(ctx->bwall32, 2 * nb * sizeof(float)), "alloc wall B");
+  CK(ensure(ctx->wg, ng * sizeof(double)), "alloc w_g");
+  CK(ensure(ctx->cn, nb * sizeof(unsigned long long)), "alloc band counts");
+  CK(ensure(ctx->cg, (size_t)nb * ng * sizeof(unsigned long long)), "alloc g counts");
+  CK(cudaMemcpy(ctx->ktab64.p, k64.data(), nk * sizeof(double2), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->btab32.p, b32.data(), nbT * sizeof(float2), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 2 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 2 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->wg.p, kd->w_g, ng * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  ctx->have_kdist = true;
+  return MCRT_OK;
+}
+
+int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int mem, void *stream) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!T) return fail(ctx, MCRT_E_ARG, "null T");
+  if (mem != MCRT_MEM_HOST && mem != MCRT_MEM_DEVICE) return fail(ctx, MCRT_E_ARG, "bad mem");
+  if (fp64 != 0 && fp64 != 1) return fail(ctx, MCRT_E_ARG, "bad dtype flag");
+  DeviceGuard dg(ctx->grid.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  ctx->have_fields = false;
+  ctx->prop_valid = false;
+  CK(ensure(ctx->field64, (size_t)n * sizeof(double2)), "alloc field");
+  CK(ensure(ctx->field32, (size_t)n * sizeof(float2)), "alloc field");
+  const void *dT = T, *dx = x;
+  DevBuf stage;
+  if (mem == MCRT_MEM_HOST) {
+    CK(ensure(stage, (size_t)n * esz * (x ? 2 : 1)), "alloc staging");
+    CK(cudaMemcpyAsync(stage.p, T, (size_t)n * esz, cudaMemcpyHostToDevice, s), "copy T");
+    dT = stage.p;
+    if (x) {
+      CK(cudaMemcpyAsync((char *)stage.p + (size_t)n * esz, x, (size_t)n * esz,
+                         cudaMemcpyHostToDevice, s),
+         "copy x");
+      dx = (char *)stage.p + (size_t)n * esz;
+    }
+  }
+  if (!x && !ctx->have_kdist) return fail(ctx, MCRT_E_STATE, "x = NULL needs set_kdist first (x_ref)");
+  const double x_ref = ctx->have_kdist ? ctx->x_ref : 1.0;
+  cudaError_t e = mcrt::launch_pack_fields(dT, dx, fp64, x_ref, n, (double2 *)ctx->field64.p,
+                                           (float2 *)ctx->field32.p,
+                                           (unsigned long long *)ctx->fstats.p, s);
+  unsigned long long st[3] = {0, 0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st, ctx->fstats.p, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (stage.p) cudaFree(stage.p);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pack fields");
+  if (st[2] != 0)
+    return fail(ctx, MCRT_E_RANGE,
+                std::to_string(st[2]) + " cells with non-finite or non-positive T or bad x");
+  double tmax, tmin;
+  std::memcpy(&tmax, &st[0], sizeof(double));
+  std::memcpy(&tmin, &st[1], sizeof(double));
+  ctx->T_max_field = tmax;
+  ctx->T_min_field = tmin;
+  ctx->have_fields = true;
+  return MCRT_OK;
+}
+
+int mcrt_set_cell_proposal(mcrt_ctx *ctx, const uint64_t *cn, const uint64_t *cg,
+                           const uint32_t *hemi, int mem, void *stream) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!ctx->have_kdist) return fail(ctx, MCRT_E_STATE, "set_kdist first");
+  if (!cn || !cg || !hemi) return fail(ctx, MCRT_E_ARG, "null proposal array");
+  if (mem != MCRT_MEM_HOST && mem != MCRT_MEM_DEVICE) return fail(ctx, MCRT_E_ARG, "bad mem");
+  DeviceGuard dg(ctx->grid.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  const size_t nc = (size_t)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+  const size_t nb = ctx->nb, ng = ctx->ng;
+  if (mem == MCRT_MEM_HOST) {
+    for (size_t c = 0; c < nc; ++c) {
+      const uint64_t *a = cn + c * nb;
+      if (a[nb - 1] != (1ull << 32)) return fail(ctx, MCRT_E_ARG, "band counts must end at 2^32");
+      for (size_t k = 1; k < nb; ++k)
+        if (a[k] < a[k - 1]) return fail(ctx, MCRT_E_ARG, "band counts decrease");
+      for (size_t n = 0; n < nb; ++n) {
+        const uint64_t *b = cg + (c * nb + n) * ng;
+        if (b[ng - 1] != (1ull << 32)) return fail(ctx, MCRT_E_ARG, "g counts must end at 2^32");
+        for (size_t k = 1; k < ng; ++k)
+          if (b[k] < b[k - 1]) return fail(ctx, MCRT_E_ARG, "g counts decrease");
+      }
+      if (hemi[c] < 1u || hemi[c] >= (1u << 23))
+        return fail(ctx, MCRT_E_ARG, "hemisphere count outside [1, 2^23-1]");
+    }
+  }
+  ctx->have_cell_prop = false;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(ensure(ctx->cell_cn, nc * nb * sizeof(uint64_t)), "alloc cell proposal");
+  CK(ensure(ctx->cell_cg, nc * nb * ng * sizeof(uint64_t)), "alloc cell proposal");
+  CK(ensure(ctx->cell_hemi, nc * sizeof(uint32_t)), "alloc cell proposal");
+  const cudaMemcpyKind k = mem == MCRT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(ctx->cell_cn.p, cn, nc * nb * sizeof(uint64_t), k, s), "copy cn");
+  CK(cudaMemcpyAsync(ctx->cell_cg.p, cg, nc * nb * ng * sizeof(uint64_t), k, s), "copy cg");
+  CK(cudaMemcpyAsync(ctx->cell_hemi.p, hemi, nc * sizeof(uint32_t), k, s), "copy hemi");
+  CK(cudaStreamSynchronize(s), "sync");
+  ctx->have_cell_prop = true;
+  return MCRT_OK;
+}
+
+int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, double *sigma_out,
+                    int mem, void *stream) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!p || !q_out) return fail(ctx, MCRT_E_ARG, "null params or q_out");
+  if (mem != MCRT_MEM_HOST && mem != MCRT_MEM_DEVICE) return fail(ctx, MCRT_E_ARG, "bad mem");
+  if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
+  if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
+  if (!(p->tol > 0.0 && p->tol < 1.0)) return fail(ctx, MCRT_E_ARG, "tol outside (0, 1)");
+  if (p->precision != MCRT_FP32 && p->precision != MCRT_FP64)
+    return fail(ctx, MCRT_E_ARG, "bad precision");
+  if (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER)
+    return fail(ctx, MCRT_E_ARG, "bad origin");
+  if (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL)
+    return fail(ctx, MCRT_E_ARG, "bad proposal");
+  if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
+    return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
+  const mcrt_grid_desc &g = ctx->grid;
+  int b[6] = {0, g.nx, 0, g.ny, 0, g.nz};
+  if (p->use_box) {
+    std::memcpy(b, p->box, sizeof(b));
+    if (b[0] < 0 || b[1] > g.nx || b[0] > b[1] || b[2] < 0 || b[3] > g.ny || b[2] > b[3] ||
+        b[4] < 0 || b[5] > g.nz || b[4] > b[5])
+      return fail(ctx, MCRT_E_ARG, "box outside the grid");
+  }
+  if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
+  if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
+    return fail(ctx, MCRT_E_STATE, "no cell proposal");
+  DeviceGuard dg(g.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  const double Tm = proposal_T_max(ctx);
+  if (!ctx->prop_valid || ctx->prop_T_max != Tm) {
+    const int rc = build_plain_proposal(ctx, Tm, s);
+    if (rc != MCRT_OK) return rc;
+  }
+  const long long nbox = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
+
+  mcrt::TraceArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.dx = g.lx / g.nx;
+  a.dy = g.ly / g.ny;
+  a.dz = g.lz / g.nz;
+  a.nb = ctx->nb;
+  a.ng = ctx->ng;
+  a.nT = ctx->nT;
+  a.T0 = ctx->T0;
+  a.inv_dT = 1.0 / ctx->dT;
+  a.inv_xref = 1.0 / ctx->x_ref;
+  a.eps_wall[0] = g.eps_wall[0];
+  a.eps_wall[1] = g.eps_wall[1];
+  a.reflect = g.reflect;
+  a.field32 = (const float2 *)ctx->field32.p;
+  a.field64 = (const double2 *)ctx->field64.p;
+  a.ktab32 = (const float2 *)ctx->ktab32.p;
+  a.ktab64 = (const double2 *)ctx->ktab64.p;
+  a.btab32 = (const float2 *)ctx->btab32.p;
+  a.btab64 = (const double2 *)ctx->btab64.p;
+  a.bwall32 = (const float *)ctx->bwall32.p;
+  a.bwall64 = (const double *)ctx->bwall64.p;
+  a.w_g = (const double *)ctx->wg.p;
+  a.cn = (const unsigned long long *)ctx->cn.p;
+  a.cg = (const unsigned long long *)ctx->cg.p;
+  if (p->proposal == MCRT_PROPOSAL_CELL) {
+    a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
+    a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
+    a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
+  }
+  a.rays = p->rays_per_cell;
+  a.max_steps = p->max_steps;
+  a.origin = p->origin;
+  a.tol = p->tol;
+  a.key0 = (unsigned)(p->seed & 0xffffffffu);
+  a.key1 = (unsigned)(p->seed >> 32);
+  a.snapshot = p->snapshot;
+  a.ray_offset = p->ray_offset;
+  a.bi0 = b[0];
+  a.bj0 = b[2];
+  a.bk0 = b[4];
+  a.bnx = b[1] - b[0];
+  a.bny = b[3] - b[2];
+  a.bnz = b[5] - b[4];
+  a.ncells_box = nbox;
+  a.counters = (unsigned long long *)ctx->counters.p;
+
+  double *dq = q_out, *ds = sigma_out;
+  unsigned long long *dst = (unsigned long long *)p->steps_out;
+  if (mem == MCRT_MEM_HOST && nbox > 0) {
+    CK(ensure(ctx->q, nbox * sizeof(double)), "alloc q");
+    dq = (double *)ctx->q.p;
+    if (sigma_out) {
+      CK(ensure(ctx->sigma, nbox * sizeof(double)), "alloc sigma");
+      ds = (double *)ctx->sigma.p;
+    }
+    if (p->steps_out) {
+      CK(ensure(ctx->steps, nbox * sizeof(unsigned long long)), "alloc steps");
+      dst = (unsigned long long *)ctx->steps.p;
+    }
+  }
+  a.q = dq;
+  a.sigma = ds;
+  a.steps_cell = dst;
+
+  CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaEventRecord(ctx->ev0, s), "event");
+  CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
+  CK(cudaEventRecord(ctx->ev1, s), "event");
+  ctx->last_launches = nbox > 0 ? 1 : 0;
+  ctx->last_stream = s;
+  ctx->solved = true;
+  ctx->last_T_max = Tm;
+  if (mem == MCRT_MEM_HOST && nbox > 0) {
+    CK(cudaMemcpyAsync(q_out, dq, nbox * sizeof(double), cudaMemcpyDeviceToHost, s), "copy q");
+    if (sigma_out)
+      CK(cudaMemcpyAsync(sigma_out, ds, nbox * sizeof(double), cudaMemcpyDeviceToHost, s),
+         "copy sigma");
+    if (p->steps_out)
+      CK(cudaMemcpyAsync(p->steps_out, dst, nbox * sizeof(unsigned long long),
+                         cudaMemcpyDeviceToHost, s),
+         "copy steps");
+    CK(cudaStreamSynchronize(s), "sync");
+  }
+  return MCRT_OK;
+}
+
+int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!out) return fail(ctx, MCRT_E_ARG, "null out");
+  if (!ctx->solved) return fail(ctx, MCRT_E_STATE, "no solve yet");
+  DeviceGuard dg(ctx->grid.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  unsigned long long c[4];
+  CK(cudaMemcpyAsync(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream),
+     "read counters");
+  CK(cudaStreamSynchronize(ctx->last_stream), "sync");
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "elapsed");
+  out->steps = c[0];
+  out->capped = c[1];
+  out->wall_hits = c[2];
+  out->rays = c[3];
+  out->T_max = ctx->last_T_max;
+  out->kernel_ms = ms;
+  out->launches = ctx->last_launches;
+  return MCRT_OK;
+}
+
+int mcrt_destroy(mcrt_ctx *ctx) {
+  if (!ctx) return MCRT_OK;
+  {
+    DeviceGuard dg(ctx->grid.device);
+    cudaDeviceSynchronize();
+    DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
+                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->cn,
+                      &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
+                      &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
+    for (DevBuf *b : bufs) release(*b);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    cudaGetLastError();
+  }
+  delete ctx;
+  return MCRT_OK;
+}
+
+}  // extern "C"

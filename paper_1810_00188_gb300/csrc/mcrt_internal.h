@@ -1,0 +1,57 @@
+// Internal interface between the C-ABI host code (mcrt_api.cpp) and the CUDA
+// kernels (trace.cu, fields.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcrt {
+
+// Everything one trace launch reads.  Device pointers only.
+struct TraceArgs {
+  // grid (uniform cells; y wall-normal; x, z periodic)
+  int nx, ny, nz;
+  double dx, dy, dz;
+  // tables on uniform T nodes: T0 + t/inv_dT
+  int nb, ng, nT;
+  double T0, inv_dT, inv_xref;
+  double eps_wall[2];
+  int reflect;  // 0 diffuse, 1 specular
+  // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
+  const float2 *field32;    // {T, x} per cell
+  const double2 *field64;
+  const float2 *ktab32;     // [nb*ng][nT] {kappa_t, kappa_{t+1} - kappa_t} at x_ref
+  const double2 *ktab64;
+  const float2 *btab32;     // [nb][nT] {B_t, B_{t+1} - B_t}
+  const double2 *btab64;
+  const float *bwall32;     // [2][nb] wall band intensity
+  const double *bwall64;
+  const double *w_g;        // [ng]
+  const unsigned long long *cn;       // [nb] cumulative counts of 2^32 (plain proposal)
+  const unsigned long long *cg;       // [nb*ng]
+  const unsigned long long *cell_cn;  // per-cell proposal [ncells][nb] or null
+  const unsigned long long *cell_cg;  // [ncells][nb*ng]
+  const unsigned int *cell_hemi;      // [ncells] count of 2^23, or null (plain: 2^22)
+  // solve
+  int rays, max_steps, origin;
+  double tol;
+  unsigned int key0, key1, snapshot;
+  unsigned long long ray_offset;
+  int bi0, bj0, bk0, bnx, bny, bnz;
+  long long ncells_box;
+  // outputs (box-sized)
+  double *q, *sigma;
+  unsigned long long *steps_cell;
+  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays
+};
+
+cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
+
+// Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
+// layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),
+// [1] min T bits (u64), [2] count of rejected cells.
+cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
+                               long long n, double2 *f64, float2 *f32,
+                               unsigned long long *stats, cudaStream_t s);
+
+}  // namespace mcrt

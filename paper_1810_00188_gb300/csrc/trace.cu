@@ -1,0 +1,386 @@
+// ERMC ray-trace kernel: the per-cell ray loop that produces Q_rad.
+//
+// Silvestri & Pecnik (arXiv:1810.00188): Section 2 (Eqs. 2, 3, 12-14), Section
+// 2.1 (band / quadrature-point sampling, Eqs. 15-17), Algorithm 1 (initialise,
+// march, residual dump) and the domain parallelisation of Section 3 (all rays of
+// a cell owned by one worker, so the per-cell tally needs no atomics).
+//
+// GB300 mapping: one warp per emitting cell, its 32 lanes stride over the cell's
+// rays; per-lane binary64 compensated tallies, a warp-shuffle reduction, and a
+// single store of Q and sigma per cell.  Random numbers come from a counter-based
+// Philox4x32-10 keyed by (cell, ray, draw block, snapshot), so each ray's draws
+// are independent of the launch shape.  The k-distribution tables are read
+// through the read-only path as {value, next-minus-value} pairs so a lookup is one
+// 8- or 16-byte load and one fused multiply-add.
+#include <math.h>
+#include <stdint.h>
+
+#include "mcrt_internal.h"
+
+namespace mcrt {
+namespace {
+
+// ---- counter-based random numbers -----------------------------------------
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11): each round multiplies counter words 0
+// and 2 by the round constants, mixes the high halves into words 1 and 3 with
+// the key, and the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Uniform on (0, 1) from the top 23 bits of a word: (w>>9 + 1/2) 2^-23, exact
+// in binary32 and binary64.
+template <typename R>
+__device__ __forceinline__ R unif(unsigned w) {
+  return ((R)(w >> 9) + (R)0.5) * (R)1.1920928955078125e-07;
+}
+
+// ---- precision-specific pieces ---------------------------------------------
+template <typename R> struct Prec;
+template <> struct Prec<float> {
+  typedef float2 R2;
+  __device__ static const float2 *field(const TraceArgs &a) { return a.field32; }
+  __device__ static const float2 *ktab(const TraceArgs &a) { return a.ktab32; }
+  __device__ static const float2 *btab(const TraceArgs &a) { return a.btab32; }
+  __device__ static const float *bwall(const TraceArgs &a) { return a.bwall32; }
+  __device__ static void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+  // alpha = 1 - exp(-x) (Eq. 2) and the transmission factor exp(-x) (Eq. 3).
+  // Below x = 0.05 a 4-term series keeps alpha's relative error near 1 ulp
+  // instead of the cancellation in 1 - exp(-x).
+  __device__ static void absorb(float x, float &alpha, float &trans) {
+    const float e = __expf(-x);
+    const float sr = x * (1.f - x * (0.5f - x * (0.16666667f - x * 0.041666668f)));
+    const bool small = x < 0.05f;
+    alpha = small ? sr : 1.f - e;
+    trans = small ? 1.f - sr : e;
+  }
+};
+template <> struct Prec<double> {
+  typedef double2 R2;
+  __device__ static const double2 *field(const TraceArgs &a) { return a.field64; }
+  __device__ static const double2 *ktab(const TraceArgs &a) { return a.ktab64; }
+  __device__ static const double2 *btab(const TraceArgs &a) { return a.btab64; }
+  __device__ static const double *bwall(const TraceArgs &a) { return a.bwall64; }
+  __device__ static void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+  __device__ static void absorb(double x, double &alpha, double &trans) {
+    alpha = -expm1(-x);
+    trans = exp(-x);
+  }
+};
+
+// Linear-interpolation position on the uniform T nodes (Section 2.2); clamps
+// to the end nodes outside the table.
+template <typename R>
+__device__ __forceinline__ void tpos(R T, R T0, R inv_dT, int nT, int &it, R &fr) {
+  const R f = (T - T0) * inv_dT;
+  const R fl = fmin(fmax(floor(f), (R)0), (R)(nT - 2));
+  it = (int)fl;
+  fr = fmin(fmax(f - fl, (R)0), (R)1);
+}
+
+// First k with u < cum[k] (cum non-decreasing, cum[K-1] = 2^32): the inverse
+// CDF of a discrete pdf held as integer counts (Eq. 17 with R_n, R_g).
+__device__ __forceinline__ int pick(const unsigned long long *__restrict__ cum, int K, unsigned u) {
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((unsigned long long)u < __ldg(cum + mid))
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void neumaier(double &s, double &c, double v) {
+  const double t = s + v;
+  if (fabs(s) >= fabs(v))
+    c += (s - t) + v;
+  else
+    c += (v - t) + s;
+  s = t;
+}
+
+// Distance parameters of one axis of the parametric ray o + t d: the m-th face
+// crossing is at t = t0 + m * ts.
+template <typename R>
+__device__ __forceinline__ void axis_setup(R d, R fr, R delta, int &s, R &t0, R &ts) {
+  if (d > (R)0) {
+    s = 1;
+    ts = delta / d;
+    t0 = ((R)1 - fr) * ts;
+  } else if (d < (R)0) {
+    s = -1;
+    ts = delta / (-d);
+    t0 = fr * ts;
+  } else {
+    s = 0;
+    ts = (R)INFINITY;
+    t0 = (R)INFINITY;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
+  typedef typename Prec<R>::R2 R2;
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= a.ncells_box) return;  // whole warps only
+
+  const int ci = a.bi0 + (int)(w % a.bnx);
+  const int cj = a.bj0 + (int)((w / a.bnx) % a.bny);
+  const int ck = a.bk0 + (int)(w / ((long long)a.bnx * a.bny));
+  const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nb = a.nb, ng = a.ng, nT = a.nT;
+  const int nxyz = nxy * nz;
+  const unsigned cell = (unsigned)(ci + nx * cj + nxy * ck);
+
+  const R2 *__restrict__ field = Prec<R>::field(a);
+  const R2 *__restrict__ ktab = Prec<R>::ktab(a);
+  const R2 *__restrict__ btab = Prec<R>::btab(a);
+  const R *__restrict__ bwall = Prec<R>::bwall(a);
+  const R T0 = (R)a.T0, inv_dT = (R)a.inv_dT, inv_xref = (R)a.inv_xref, tol = (R)a.tol;
+  const R DX = (R)a.dx, DY = (R)a.dy, DZ = (R)a.dz;
+
+  // emitting cell state
+  const R2 fi = __ldg(field + cell);
+  int it_i;
+  R fr_i;
+  tpos<R>(fi.x, T0, inv_dT, nT, it_i, fr_i);
+  const R xr_i = fi.y * inv_xref;
+
+  const unsigned long long *__restrict__ cn = a.cell_cn ? a.cell_cn + (size_t)cell * nb : a.cn;
+  const unsigned long long *__restrict__ cg = a.cell_cg ? a.cell_cg + (size_t)cell * nb * ng : a.cg;
+  const unsigned hemi = a.cell_hemi ? __ldg(a.cell_hemi + cell) : 4194304u;
+
+  double sy = 0.0, cy = 0.0, sy2 = 0.0, cy2 = 0.0;
+  unsigned long long nsteps = 0, ncap = 0, nwall = 0;
+
+  for (int r = lane; r < a.rays; r += 32) {
+    const unsigned ray = (unsigned)(a.ray_offset + (unsigned long long)r);
+    const uint4 u = philox10(make_uint4(cell, ray, 0u, a.snapshot), a.key0, a.key1);
+
+    // direction: hemisphere of the y axis by the integer count `hemi` of 2^23,
+    // mu uniform inside it; azimuth phi = 2 pi R_phi (Eq. 9)
+    const unsigned m0 = u.x >> 9;
+    R mu;
+    double ph;
+    if (m0 < hemi) {
+      mu = (R)1 - ((R)m0 + (R)0.5) / (R)hemi;
+      ph = (double)hemi * 1.1920928955078125e-07;
+    } else {
+      mu = -(((R)(m0 - hemi) + (R)0.5) / (R)(8388608u - hemi));
+      ph = (double)(8388608u - hemi) * 1.1920928955078125e-07;
+    }
+    R sphi, cphi;
+    Prec<R>::sincospi_((R)2 * unif<R>(u.y), &sphi, &cphi);
+    const R st = sqrt(fmax((R)0, (R)1 - mu * mu));
+    R ddx = st * cphi, ddy = mu, ddz = st * sphi;
+
+    // band and quadrature point from two words (Eq. 17); weight w_g / (p q)
+    const int n = pick(cn, nb, u.z);
+    const unsigned long long *cgn = cg + (size_t)n * ng;
+    const int g = pick(cgn, ng, u.w);
+    const unsigned long long mn = __ldg(cn + n) - (n ? __ldg(cn + n - 1) : 0ull);
+    const unsigned long long mg = __ldg(cgn + g) - (g ? __ldg(cgn + g - 1) : 0ull);
+    const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
+    const double wgt = (__ldg(a.w_g + g) / p) * (6.283185307179586 / ph);
+
+    // origin: uniform in the cell (block 1 draws) or the centre
+    R fx = (R)0.5, fy = (R)0.5, fz = (R)0.5;
+    if (a.origin == 0) {
+      const uint4 v = philox10(make_uint4(cell, ray, 1u, a.snapshot), a.key0, a.key1);
+      fx = unif<R>(v.x);
+      fy = unif<R>(v.y);
+      fz = unif<R>(v.z);
+    }
+
+    const size_t krow = (size_t)(n * ng + g) * nT;
+    const size_t brow = (size_t)n * nT;
+    const R2 ki = __ldg(ktab + krow + it_i);
+    const R2 bi = __ldg(btab + brow + it_i);
+    const R kap_i = (ki.x + fr_i * ki.y) * xr_i;
+    const R B_i = bi.x + fr_i * bi.y;
+
+    // ---- march (Algorithm 1) ----
+    int ix = ci, iy = cj, iz = ck, lin = (int)cell;
+    int sx, sy_, sz;
+    R t0x, t0y, t0z, tsx, tsy, tsz;
+    axis_setup<R>(ddx, fx, DX, sx, t0x, tsx);
+    axis_setup<R>(ddy, fy, DY, sy_, t0y, tsy);
+    axis_setup<R>(ddz, fz, DZ, sz, t0z, tsz);
+    R cntx = 0, cnty = 0, cntz = 0;
+    R tnx = t0x, tny = t0y, tnz = t0z, tprev = 0;
+    R X = 0, tau = 1, B_last = B_i;
+    int steps = 0;
+    unsigned nrefl = 0;
+    for (;;) {
+      int ax;
+      R tn;
+      if (tnx <= tny && tnx <= tnz) {
+        ax = 0;
+        tn = tnx;
+      } else if (tny <= tnz) {
+        ax = 1;
+        tn = tny;
+      } else {
+        ax = 2;
+        tn = tnz;
+      }
+      const R ds = fmax(tn - tprev, (R)0);
+      const R2 f = __ldg(field + lin);
+      int it;
+      R fr;
+      tpos<R>(f.x, T0, inv_dT, nT, it, fr);
+      const R2 kk = __ldg(ktab + krow + it);
+      const R2 bb = __ldg(btab + brow + it);
+      const R kap = (kk.x + fr * kk.y) * (f.y * inv_xref);
+      const R Bj = bb.x + fr * bb.y;
+      R alpha, trans;
+      Prec<R>::absorb(kap * ds, alpha, trans);
+      X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
+      tau *= trans;                     // Eq. 3
+      B_last = Bj;
+      ++steps;
+      if (tau <= tol) break;
+      if (steps >= a.max_steps) {
+        ++ncap;
+        break;
+      }
+      tprev = tn;
+      if (ax == 0) {
+        cntx += (R)1;
+        tnx = fma(cntx, tsx, t0x);
+        ix += sx;
+        lin += sx;
+        if (ix >= nx) {
+          ix -= nx;
+          lin -= nx;
+        } else if (ix < 0) {
+          ix += nx;
+          lin += nx;
+        }
+      } else if (ax == 2) {
+        cntz += (R)1;
+        tnz = fma(cntz, tsz, t0z);
+        iz += sz;
+        lin += sz * nxy;
+        if (iz >= nz) {
+          iz -= nz;
+          lin -= nxyz;
+        } else if (iz < 0) {
+          iz += nz;
+          lin += nxyz;
+        }
+      } else {
+        cnty += (R)1;
+        tny = fma(cnty, tsy, t0y);
+        iy += sy_;
+        lin += sy_ * nx;
+        if (iy < 0 || iy >= ny) {
+          // wall event: the wall absorbs eps of the ray and emits at T_wall
+          const int wl = iy < 0 ? 0 : 1;
+          const R eps = (R)a.eps_wall[wl];
+          const R Bw = __ldg(bwall + wl * nb + n);
+          X += (B_i - Bw) * (tau * eps);
+          tau *= (R)1 - eps;
+          ++nwall;
+          if (eps >= (R)1 || tau <= tol) break;
+          // reflect from the crossing point at t = tprev
+          R nfx = fx, nfz = fz;
+          if (sx > 0)
+            nfx = (R)1 - (tnx - tprev) / tsx;
+          else if (sx < 0)
+            nfx = (tnx - tprev) / tsx;
+          if (sz > 0)
+            nfz = (R)1 - (tnz - tprev) / tsz;
+          else if (sz < 0)
+            nfz = (tnz - tprev) / tsz;
+          fx = fmin(fmax(nfx, (R)0), (R)1);
+          fz = fmin(fmax(nfz, (R)0), (R)1);
+          fy = wl == 0 ? (R)0 : (R)1;
+          iy = wl == 0 ? 0 : ny - 1;
+          lin = ix + nx * iy + nxy * iz;
+          if (a.reflect == 1) {
+            ddy = -ddy;
+          } else {
+            // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
+            const uint4 v =
+                philox10(make_uint4(cell, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
+            const R mr = sqrt(unif<R>(v.x));
+            R sp, cp;
+            Prec<R>::sincospi_((R)2 * unif<R>(v.y), &sp, &cp);
+            const R sr = sqrt(fmax((R)0, (R)1 - mr * mr));
+            ddx = sr * cp;
+            ddy = wl == 0 ? mr : -mr;
+            ddz = sr * sp;
+          }
+          ++nrefl;
+          axis_setup<R>(ddx, fx, DX, sx, t0x, tsx);
+          axis_setup<R>(ddy, fy, DY, sy_, t0y, tsy);
+          axis_setup<R>(ddz, fz, DZ, sz, t0z, tsz);
+          cntx = cnty = cntz = 0;
+          tnx = t0x;
+          tny = t0y;
+          tnz = t0z;
+          tprev = 0;
+        }
+      }
+    }
+    if (tau > (R)0) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+
+    const double Y = wgt * (double)(kap_i * X);
+    neumaier(sy, cy, Y);
+    neumaier(sy2, cy2, Y * Y);
+    nsteps += (unsigned long long)steps;
+  }
+
+  // warp reduction of the lanes' tallies
+  double S = sy + cy, S2 = sy2 + cy2;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    S += __shfl_xor_sync(0xffffffffu, S, off);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, off);
+    nsteps += __shfl_xor_sync(0xffffffffu, nsteps, off);
+    ncap += __shfl_xor_sync(0xffffffffu, ncap, off);
+    nwall += __shfl_xor_sync(0xffffffffu, nwall, off);
+  }
+  if (lane == 0) {
+    const double N = (double)a.rays;
+    const double Q = S / N;
+    a.q[w] = Q;  // Eq. 8: mean of the per-ray samples
+    if (a.sigma)
+      a.sigma[w] = a.rays > 1 ? sqrt(fmax(S2 / N - Q * Q, 0.0) / (N - 1.0)) : 0.0;
+    if (a.steps_cell) a.steps_cell[w] = nsteps;
+    atomicAdd(a.counters + 0, nsteps);
+    if (ncap) atomicAdd(a.counters + 1, ncap);
+    if (nwall) atomicAdd(a.counters + 2, nwall);
+    atomicAdd(a.counters + 3, (unsigned long long)a.rays);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s) {
+  if (a.ncells_box <= 0) return cudaSuccess;
+  const int threads = 256;
+  const long long blocks = (a.ncells_box * 32 + threads - 1) / threads;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (precision == 1)
+    trace_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(a);
+  else
+    trace_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mcrt

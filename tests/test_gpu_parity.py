@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA library against the FP64 oracle, draw for draw.
+
+Both sides consume the same Philox draws, so per-cell Q must agree to rounding:
+|Q_gpu - Q_oracle| <= rtol * S_i with S_i the oracle's mean absolute tally
+(sum of |terms| per ray, weighted): rtol = 1e-10 in FP64 mode and 1e-4 in FP32
+mode.  S_i scales the tolerance because Q_i is a difference of terms of both
+signs and can vanish where they cancel.  All calls go through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_00188_gb300 import inputs, mcrt
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {mcrt.MCRT_FP64: 1e-10, mcrt.MCRT_FP32: 1e-4}
+
+
+def run_pair(grid, kd, T, x, rays, precision, seed=0, tol=1e-4, max_steps=1 << 20, origin=0,
+             box=None, ray_offset=0, snapshot=0):
+    orc = oracle.solve(grid, kd, T, x, rays=rays, seed=seed, tol=tol, max_steps=max_steps,
+                       origin=origin, box=box, ray_offset=ray_offset, snapshot=snapshot)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    q, s, st = S.solve(box=box, with_steps=True, rays=rays, seed=seed, tol=tol,
+                       max_steps=max_steps, origin=origin, precision=precision,
+                       ray_offset=ray_offset, snapshot=snapshot)
+    stats = S.stats()
+    S.close()
+    return orc, q, s, st, stats
+
+
+def assert_parity(orc, q, s, st, precision):
+    rtol = RTOL[precision]
+    scale = orc["scale"]
+    err = np.abs(q - orc["q"])
+    bad = err > rtol * scale + 1e-300
+    assert not bad.any(), (f"{bad.sum()} cells beyond {rtol} S; worst "
+                           f"{np.max(err / np.maximum(scale, 1e-300)):.3e}")
+    # standard errors follow (they come from the same per-ray samples)
+    srel = 1e-8 if precision == mcrt.MCRT_FP64 else 2e-2
+    big = orc["sigma"] > 1e-3 * scale
+    assert np.allclose(s[big], orc["sigma"][big], rtol=srel)
+    if precision == mcrt.MCRT_FP64:
+        assert np.array_equal(st, orc["steps"])
+    else:
+        assert abs(st.sum() / orc["steps"].sum() - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("precision", [mcrt.MCRT_FP64, mcrt.MCRT_FP32])
+@pytest.mark.parametrize("kap", [0.1, 1.0, 10.0])
+def test_grey_slab_16x32x16_parity(precision, kap):
+    grid, kd, T, x = inputs.grey_slab_16x32x16(kap)
+    orc, q, s, st, stats = run_pair(grid, kd, T, x, 32, precision, seed=0, tol=1e-6)
+    assert_parity(orc, q, s, st, precision)
+    assert stats["rays"] == grid.ncells * 32
+    assert stats["steps"] == st.sum()
+
+
+@pytest.mark.parametrize("precision", [mcrt.MCRT_FP64, mcrt.MCRT_FP32])
+def test_nongrey_channel_parity(precision):
+    grid, kd, T, x = inputs.nongrey_channel(16, 16, 16, seed=3)
+    orc, q, s, st, _ = run_pair(grid, kd, T, x, 64, precision, seed=5)
+    assert_parity(orc, q, s, st, precision)
+
+
+@pytest.mark.parametrize("precision", [mcrt.MCRT_FP64, mcrt.MCRT_FP32])
+@pytest.mark.parametrize("reflect", [0, 1])
+def test_grey_walls_x_field_parity(precision, reflect):
+    grid, kd, T, x = inputs.nongrey_channel(12, 16, 10, seed=4, eps_wall=0.8, x_mode="field")
+    grid.reflect = reflect
+    orc, q, s, st, stats = run_pair(grid, kd, T, x, 48, precision, seed=6)
+    assert_parity(orc, q, s, st, precision)
+    assert stats["wall_hits"] > 0
+
+
+@pytest.mark.parametrize("precision", [mcrt.MCRT_FP64, mcrt.MCRT_FP32])
+def test_ragged_box_center_origin_offset(precision):
+    """Ragged grid, ragged ray count, a crop box, centre origin, ray offset and a
+    snapshot index."""
+    grid, kd, T, x = inputs.nongrey_channel(7, 9, 5, seed=7, x_mode="field")
+    box = (1, 6, 2, 9, 0, 3)
+    orc, q, s, st, _ = run_pair(grid, kd, T, x, 37, precision, seed=(1 << 40) + 9, origin=1,
+                                box=box, ray_offset=1000, snapshot=3)
+    assert q.shape == (3, 7, 5)
+    assert_parity(orc, q, s, st, precision)
+
+
+def test_single_ray_and_step_cap():
+    grid, kd, T, x = inputs.nongrey_channel(8, 8, 8, seed=8)
+    orc, q, s, st, stats = run_pair(grid, kd, T, x, 1, mcrt.MCRT_FP64, seed=1, max_steps=3)
+    assert np.all(s == 0.0)
+    assert_parity(orc, q, s, st, mcrt.MCRT_FP64)
+    assert stats["capped"] > 0 and np.all(st <= 3)
+
+
+def test_empty_box_and_state_errors():
+    grid, kd, T, x = inputs.nongrey_channel(8, 8, 8, seed=9)
+    S = mcrt.Solver(grid, kd)
+    q = np.zeros(1)
+    with pytest.raises(mcrt.McrtError) as e:
+        S.solve_into(S.params(rays=4), q)
+    assert e.value.status == mcrt.MCRT_E_STATE
+    S.set_fields(T, x)
+    q0, s0 = S.solve(box=(2, 2, 0, 8, 0, 8), rays=4)
+    assert q0.size == 0
+    with pytest.raises(mcrt.McrtError) as e:
+        S.solve(box=(0, 9, 0, 8, 0, 8), rays=4)
+    assert e.value.status == mcrt.MCRT_E_ARG
+    with pytest.raises(mcrt.McrtError) as e:
+        S.solve(rays=4, tol=1.5)
+    assert e.value.status == mcrt.MCRT_E_ARG
+    with pytest.raises(mcrt.McrtError) as e:
+        S.solve(rays=4, proposal=mcrt.MCRT_PROPOSAL_CELL)
+    assert e.value.status == mcrt.MCRT_E_STATE
+    Tbad = T.copy()
+    Tbad[1, 2, 3] = np.nan
+    with pytest.raises(mcrt.McrtError) as e:
+        S.set_fields(Tbad, x)
+    assert e.value.status == mcrt.MCRT_E_RANGE
+    with pytest.raises(mcrt.McrtError) as e:  # the rejected field is forgotten
+        S.solve(rays=4)
+    assert e.value.status == mcrt.MCRT_E_STATE
+    S.close()
+
+
+def test_device_and_host_memory_paths_agree_bitwise():
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(16, 12, 8, seed=10)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    qh, sh = S.solve(rays=64, seed=2)
+    Td = torch.tensor(T, device="cuda")
+    xd = torch.tensor(x, device="cuda")
+    S.set_fields(Td, xd)
+    qd = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    sd = torch.zeros_like(qd)
+    stream = torch.cuda.current_stream().cuda_stream
+    S.solve_into(S.params(rays=64, seed=2), qd, sd, stream=stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(qd.cpu().numpy(), qh) and np.array_equal(sd.cpu().numpy(), sh)
+    # float32 inputs give the same FP32-mode result as float64 inputs rounded
+    S.set_fields(T.astype(np.float32), x.astype(np.float32))
+    q32a, _ = S.solve(rays=16, seed=3)
+    S.set_fields(T.astype(np.float32).astype(np.float64), x.astype(np.float32).astype(np.float64))
+    q32b, _ = S.solve(rays=16, seed=3)
+    assert np.array_equal(q32a, q32b)
+    S.close()
+
+
+def test_shards_union_equals_full_solve_bitwise():
+    """Q_i depends only on cell i's rays (Section 3): disjoint boxes solved
+    separately give the full solve bit for bit, so slabs shard across GPUs."""
+    grid, kd, T, x = inputs.nongrey_channel(16, 16, 12, seed=11)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    full, fs = S.solve(rays=40, seed=4)
+    parts = [S.solve(box=(0, 16, 0, 16, k0, k1), rays=40, seed=4) for k0, k1 in ((0, 5), (5, 12))]
+    assert np.array_equal(np.concatenate([p[0] for p in parts], axis=0), full)
+    assert np.array_equal(np.concatenate([p[1] for p in parts], axis=0), fs)
+    S.close()
+
+
+def test_fp32_matches_E3_closed_form():
+    """FP32 mode on the 16x32x16 grey slab (kappa = 1, 128 rays) against the
+    exponential-integral cell averages, within the sampled error."""
+    from scipy.special import expn
+    grid, kd, T, x = inputs.grey_slab_16x32x16(1.0)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    q, s = S.solve(rays=128, seed=0, tol=1e-6, precision=mcrt.MCRT_FP32)
+    S.close()
+    L, dy = 2.0, 2.0 / 32
+    y0 = np.arange(32) * dy
+    y1 = y0 + dy
+    ref = 2 * inputs.SIGMA_SB * 1e12 / dy * (expn(3, y0) - expn(3, y1) + expn(3, L - y1) - expn(3, L - y0))
+    row = q.mean(axis=(0, 2))
+    se = np.sqrt((s**2).sum(axis=(0, 2))) / 256
+    z = (row - ref) / se
+    assert np.max(np.abs(z)) < 4 and np.sqrt(np.mean(z**2)) < 1.6
+
+
+def test_full_size_channel_64cubed_sampled_cells():
+    """The benchmark workload (64^3 channel, 40x8 k-distribution, 1000 rays,
+    FP32, whole-grid launch) against the oracle on sampled cells."""
+    grid, kd, T, x = inputs.nongrey_channel(64, 64, 64, seed=0)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    q, s = S.solve(rays=1000, seed=0, tol=1e-4, max_steps=1 << 20, precision=mcrt.MCRT_FP32)
+    S.close()
+    rng = np.random.default_rng(0)
+    cells = [tuple(rng.integers(0, 64, 3)) for _ in range(12)] + [(0, 0, 0), (63, 63, 63), (5, 0, 9), (7, 63, 2)]
+    for (i, j, k) in cells:
+        o = oracle.solve(grid, kd, T, x, rays=1000, seed=0, tol=1e-4, max_steps=1 << 20,
+                         box=(i, i + 1, j, j + 1, k, k + 1))
+        assert abs(q[k, j, i] - o["q"][0, 0, 0]) <= 1e-4 * o["scale"][0, 0, 0], (i, j, k)

@@ -116,6 +116,15 @@ typedef struct {
   int launches;            /* kernels the last solve launched                     */
 } mcrt_solve_stats;
 
+/* Launch shape of the FP32 trace kernel.  The paper sizes its launches so that
+ * "the GPU resources are fully utilized" (Section 3); here the choice is left to
+ * an autotuner.  Q, sigma and the step counts do not depend on these settings:
+ * every cell's samples are reduced in a fixed order. */
+typedef struct {
+  int min_blocks_per_sm;   /* 0: default (2); 1..4 CTAs of 256 threads per SM,
+                              trading registers per thread against occupancy */
+} mcrt_tuning;
+
 /* Creates a context on grid->device.  *out receives the handle (NULL on error).
  * Errors: MCRT_E_ARG (bad geometry / walls), MCRT_E_CUDA (no such device). */
 int mcrt_create(const mcrt_grid_desc *grid, mcrt_ctx **out);
@@ -157,6 +166,11 @@ int mcrt_set_cell_proposal(mcrt_ctx *ctx, const uint64_t *cn, const uint64_t *cg
  * MCRT_PROPOSAL_CELL), MCRT_E_CUDA, MCRT_E_OOM. */
 int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, double *sigma_out,
                     int mem, void *cuda_stream);
+
+/* Sets / reads the launch shape used by later FP32 solves.  Errors: MCRT_E_ARG
+ * (value out of range). */
+int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t);
+int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t);
 
 /* Waits for the last solve and reports its counters.  Errors: MCRT_E_STATE (no
  * solve yet), MCRT_E_CUDA. */

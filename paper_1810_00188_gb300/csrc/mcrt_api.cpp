@@ -41,12 +41,13 @@ struct mcrt_ctx {
   bool prop_valid = false;
   double prop_T_max = -1;
   // device buffers
-  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, cn, cg,
+  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wgt32, cn, cg,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;
   int last_launches = 0;
+  int min_blocks = 2;
   double last_T_max = 0;
   std::string err;
 };
@@ -175,6 +176,17 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   }
   if (!quantize_counts(wn.data(), nb, cn.data()))
     return fail(ctx, MCRT_E_ARG, "no band emits at T_max (all kappa*B are zero)");
+  // ray weights w_g / (p(n,g) q) with q = 1/(4 pi), in FP64, rounded once for the FP32 kernel
+  std::vector<float> w32((size_t)nb * ng);
+  for (int n = 0; n < nb; ++n)
+    for (int g = 0; g < ng; ++g) {
+      const unsigned long long mn = cn[n] - (n ? cn[n - 1] : 0ull);
+      const unsigned long long mg = cg[(size_t)n * ng + g] - (g ? cg[(size_t)n * ng + g - 1] : 0ull);
+      const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
+      w32[(size_t)n * ng + g] = mn && mg ? (float)((ctx->w_g[g] / p) * (6.283185307179586 / 0.5)) : 0.f;
+    }
+  CK(cudaMemcpyAsync(ctx->wgt32.p, w32.data(), sizeof(float) * nb * ng, cudaMemcpyHostToDevice, s),
+     "upload weights");
   CK(cudaMemcpyAsync(ctx->cn.p, cn.data(), sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s),
      "upload band counts");
   CK(cudaMemcpyAsync(ctx->cg.p, cg.data(), sizeof(unsigned long long) * nb * ng,
@@ -238,7 +250,7 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   DeviceGuard dg(g->device);
   if (!dg.ok || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
       cudaEventCreate(&ctx->ev1) != cudaSuccess ||
-      ensure(ctx->counters, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      ensure(ctx->counters, 6 * sizeof(unsigned long long)) != cudaSuccess ||
       ensure(ctx->fstats, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     mcrt_destroy(ctx);
@@ -309,6 +321,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(ensure(ctx->wg, ng * sizeof(double)), "alloc w_g");
   CK(ensure(ctx->cn, nb * sizeof(unsigned long long)), "alloc band counts");
   CK(ensure(ctx->cg, (size_t)nb * ng * sizeof(unsigned long long)), "alloc g counts");
+  CK(ensure(ctx->wgt32, (size_t)nb * ng * sizeof(float)), "alloc weights");
   CK(cudaMemcpy(ctx->ktab64.p, k64.data(), nk * sizeof(double2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
@@ -474,6 +487,8 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.bwall32 = (const float *)ctx->bwall32.p;
   a.bwall64 = (const double *)ctx->bwall64.p;
   a.w_g = (const double *)ctx->wg.p;
+  a.wgt32 = (const float *)ctx->wgt32.p;
+  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
   if (p->proposal == MCRT_PROPOSAL_CELL) {
@@ -516,9 +531,12 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.sigma = ds;
   a.steps_cell = dst;
 
-  CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(ctx->counters.p, 0, 6 * sizeof(unsigned long long), s), "clear counters");
   CK(cudaEventRecord(ctx->ev0, s), "event");
-  CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
+  if (p->precision == MCRT_FP32)
+    CK(mcrt::launch_trace_pool(a, ctx->min_blocks, s), "trace launch");
+  else
+    CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
   CK(cudaEventRecord(ctx->ev1, s), "event");
   ctx->last_launches = nbox > 0 ? 1 : 0;
   ctx->last_stream = s;
@@ -538,16 +556,32 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   return MCRT_OK;
 }
 
+int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!t) return fail(ctx, MCRT_E_ARG, "null tuning");
+  if (t->min_blocks_per_sm < 0 || t->min_blocks_per_sm > 4)
+    return fail(ctx, MCRT_E_ARG, "min_blocks_per_sm outside 0..4");
+  ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 2;
+  return MCRT_OK;
+}
+
+int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
+  if (!ctx || !t) return MCRT_E_ARG;
+  t->min_blocks_per_sm = ctx->min_blocks;
+  return MCRT_OK;
+}
+
 int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   if (!ctx) return MCRT_E_ARG;
   if (!out) return fail(ctx, MCRT_E_ARG, "null out");
   if (!ctx->solved) return fail(ctx, MCRT_E_STATE, "no solve yet");
   DeviceGuard dg(ctx->grid.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
-  unsigned long long c[4];
+  unsigned long long c[6];
   CK(cudaMemcpyAsync(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream),
      "read counters");
   CK(cudaStreamSynchronize(ctx->last_stream), "sync");
+  if (c[5] != 0) return fail(ctx, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "elapsed");
   out->steps = c[0];
@@ -566,7 +600,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
-                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->cn,
+                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wgt32, &ctx->cn,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
     for (DevBuf *b : bufs) release(*b);

@@ -27,11 +27,13 @@ struct TraceArgs {
   const float *bwall32;     // [2][nb] wall band intensity
   const double *bwall64;
   const double *w_g;        // [ng]
+  const float *wgt32;       // [nb*ng] plain-proposal ray weight w_g / (p q), host FP64 -> FP32
   const unsigned long long *cn;       // [nb] cumulative counts of 2^32 (plain proposal)
   const unsigned long long *cg;       // [nb*ng]
   const unsigned long long *cell_cn;  // per-cell proposal [ncells][nb] or null
   const unsigned long long *cell_cg;  // [ncells][nb*ng]
   const unsigned int *cell_hemi;      // [ncells] count of 2^23, or null (plain: 2^22)
+  int counts_in_smem;                 // plain counts staged in shared memory (<= 48 KB)
   // solve
   int rays, max_steps, origin;
   double tol;
@@ -42,10 +44,14 @@ struct TraceArgs {
   // outputs (box-sized)
   double *q, *sigma;
   unsigned long long *steps_cell;
-  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays
+  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] unused [5] error flags
 };
 
+// Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
+// FP32 kernel with converged initialisation and lane refill (trace_pool.cu).
+// min_blocks: occupancy target (1-4 CTAs of 256 threads per SM; registers vs spills).
+cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, cudaStream_t s);
 
 // Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
 // layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),

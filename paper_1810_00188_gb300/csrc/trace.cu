@@ -6,8 +6,13 @@
 // a cell owned by one worker, so the per-cell tally needs no atomics).
 //
 // GB300 mapping: one warp per emitting cell, its 32 lanes stride over the cell's
-// rays; per-lane binary64 compensated tallies, a warp-shuffle reduction, and a
-// single store of Q and sigma per cell.  Random numbers come from a counter-based
+// rays; a warp-shuffle reduction in binary64 and a single store of Q and sigma
+// per cell.  GB300 issues binary64 arithmetic at about 1/64 of the binary32
+// rate, so the FP32 kernel keeps per-ray work in binary32: ray weights come from
+// a host-built FP64 table rounded once, and each lane accumulates its rays in a
+// compensated binary32 pair (about 48 significant bits) that is widened to
+// binary64 for the cross-lane reduction.  The FP64 kernel does everything in
+// binary64 (parity mode).  Random numbers come from a counter-based
 // Philox4x32-10 keyed by (cell, ray, draw block, snapshot), so each ray's draws
 // are independent of the launch shape.  The k-distribution tables are read
 // through the read-only path as {value, next-minus-value} pairs so a lookup is one
@@ -55,6 +60,7 @@ template <> struct Prec<float> {
   __device__ static const float2 *btab(const TraceArgs &a) { return a.btab32; }
   __device__ static const float *bwall(const TraceArgs &a) { return a.bwall32; }
   __device__ static void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+  __device__ static float div(float a, float b) { return __fdividef(a, b); }
   // alpha = 1 - exp(-x) (Eq. 2) and the transmission factor exp(-x) (Eq. 3).
   // Below x = 0.05 a 4-term series keeps alpha's relative error near 1 ulp
   // instead of the cancellation in 1 - exp(-x).
@@ -73,6 +79,7 @@ template <> struct Prec<double> {
   __device__ static const double2 *btab(const TraceArgs &a) { return a.btab64; }
   __device__ static const double *bwall(const TraceArgs &a) { return a.bwall64; }
   __device__ static void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+  __device__ static double div(double a, double b) { return a / b; }
   __device__ static void absorb(double x, double &alpha, double &trans) {
     alpha = -expm1(-x);
     trans = exp(-x);
@@ -95,7 +102,7 @@ __device__ __forceinline__ int pick(const unsigned long long *__restrict__ cum, 
   int lo = 0, hi = K - 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if ((unsigned long long)u < __ldg(cum + mid))
+    if ((unsigned long long)u < cum[mid])
       hi = mid;
     else
       lo = mid + 1;
@@ -112,17 +119,72 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
   s = t;
 }
 
+// Per-lane tally of sum(Y) and sum(Y^2).  Binary64 kernel: Neumaier sums in
+// binary64.  Binary32 kernel: compensated binary32 pairs (TwoSum for the
+// running sum, an FMA-exact product for Y^2), widened to binary64 at the end.
+template <typename R> struct Tally;
+template <> struct Tally<double> {
+  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
+  __device__ void add(double y) {
+    neumaier(s, c, y);
+    neumaier(s2, c2, y * y);
+  }
+  __device__ double sum() const { return s + c; }
+  __device__ double sum2() const { return s2 + c2; }
+};
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+template <> struct Tally<float> {
+  float s = 0.f, c = 0.f, s2 = 0.f, c2 = 0.f;
+  __device__ void add(float y) {
+    two_sum_acc(s, c, y);
+    const float p = y * y;
+    const float e = fmaf(y, y, -p);  // exact: y*y = p + e
+    two_sum_acc(s2, c2, p);
+    c2 += e;
+  }
+  __device__ double sum() const { return (double)s + (double)c; }
+  __device__ double sum2() const { return (double)s2 + (double)c2; }
+};
+
+// Ray weight w_g / (p(n,g) q(Omega)) from the integer counts (Eq. 14 with the
+// pdfs of Eqs. 4, 9, 16).  The binary32 kernel reads the plain proposal's
+// weights from a host-built table and evaluates per-cell proposals in binary32.
+template <typename R>
+__device__ __forceinline__ R ray_weight(const TraceArgs &a, bool plain, int n, int g,
+                                        unsigned long long mn, unsigned long long mg, double ph);
+template <>
+__device__ __forceinline__ double ray_weight<double>(const TraceArgs &a, bool, int, int g,
+                                                     unsigned long long mn, unsigned long long mg,
+                                                     double ph) {
+  const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
+  return (__ldg(a.w_g + g) / p) * (6.283185307179586 / ph);
+}
+template <>
+__device__ __forceinline__ float ray_weight<float>(const TraceArgs &a, bool plain, int n, int g,
+                                                   unsigned long long mn, unsigned long long mg,
+                                                   double ph) {
+  if (plain) return __ldg(a.wgt32 + n * a.ng + g);
+  const float p = ((float)mn * 2.3283064365386963e-10f) * ((float)mg * 2.3283064365386963e-10f);
+  return __fdividef((float)__ldg(a.w_g + g), p) * __fdividef(6.2831855f, (float)ph);
+}
+
 // Distance parameters of one axis of the parametric ray o + t d: the m-th face
 // crossing is at t = t0 + m * ts.
 template <typename R>
 __device__ __forceinline__ void axis_setup(R d, R fr, R delta, int &s, R &t0, R &ts) {
   if (d > (R)0) {
     s = 1;
-    ts = delta / d;
+    ts = Prec<R>::div(delta, d);
     t0 = ((R)1 - fr) * ts;
   } else if (d < (R)0) {
     s = -1;
-    ts = delta / (-d);
+    ts = Prec<R>::div(delta, -d);
     t0 = fr * ts;
   } else {
     s = 0;
@@ -134,6 +196,14 @@ __device__ __forceinline__ void axis_setup(R d, R fr, R delta, int &s, R &t0, R 
 template <typename R>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   typedef typename Prec<R>::R2 R2;
+  extern __shared__ unsigned long long s_counts[];  // plain band counts, then g counts
+  const bool plain = a.cell_cn == nullptr;
+  if (plain && a.counts_in_smem) {
+    const int ncount = a.nb + a.nb * a.ng;
+    for (int i = threadIdx.x; i < ncount; i += blockDim.x)
+      s_counts[i] = i < a.nb ? a.cn[i] : a.cg[i - a.nb];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= a.ncells_box) return;  // whole warps only
@@ -159,11 +229,14 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   tpos<R>(fi.x, T0, inv_dT, nT, it_i, fr_i);
   const R xr_i = fi.y * inv_xref;
 
-  const unsigned long long *__restrict__ cn = a.cell_cn ? a.cell_cn + (size_t)cell * nb : a.cn;
-  const unsigned long long *__restrict__ cg = a.cell_cg ? a.cell_cg + (size_t)cell * nb * ng : a.cg;
+  const unsigned long long *__restrict__ cn =
+      plain ? (a.counts_in_smem ? s_counts : a.cn) : a.cell_cn + (size_t)cell * nb;
+  const unsigned long long *__restrict__ cg =
+      plain ? (a.counts_in_smem ? s_counts + nb : a.cg) : a.cell_cg + (size_t)cell * nb * ng;
   const unsigned hemi = a.cell_hemi ? __ldg(a.cell_hemi + cell) : 4194304u;
+  const R inv_hemi = (R)1 / (R)hemi, inv_lo = (R)1 / (R)(8388608u - hemi);
 
-  double sy = 0.0, cy = 0.0, sy2 = 0.0, cy2 = 0.0;
+  Tally<R> tally;
   unsigned long long nsteps = 0, ncap = 0, nwall = 0;
 
   for (int r = lane; r < a.rays; r += 32) {
@@ -176,10 +249,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     R mu;
     double ph;
     if (m0 < hemi) {
-      mu = (R)1 - ((R)m0 + (R)0.5) / (R)hemi;
+      mu = (R)1 - ((R)m0 + (R)0.5) * inv_hemi;
       ph = (double)hemi * 1.1920928955078125e-07;
     } else {
-      mu = -(((R)(m0 - hemi) + (R)0.5) / (R)(8388608u - hemi));
+      mu = -(((R)(m0 - hemi) + (R)0.5) * inv_lo);
       ph = (double)(8388608u - hemi) * 1.1920928955078125e-07;
     }
     R sphi, cphi;
@@ -191,10 +264,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     const int n = pick(cn, nb, u.z);
     const unsigned long long *cgn = cg + (size_t)n * ng;
     const int g = pick(cgn, ng, u.w);
-    const unsigned long long mn = __ldg(cn + n) - (n ? __ldg(cn + n - 1) : 0ull);
-    const unsigned long long mg = __ldg(cgn + g) - (g ? __ldg(cgn + g - 1) : 0ull);
-    const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
-    const double wgt = (__ldg(a.w_g + g) / p) * (6.283185307179586 / ph);
+    const unsigned long long mn = cn[n] - (n ? cn[n - 1] : 0ull);
+    const unsigned long long mg = cgn[g] - (g ? cgn[g - 1] : 0ull);
+    const R wgt = ray_weight<R>(a, plain, n, g, mn, mg, ph);
 
     // origin: uniform in the cell (block 1 draws) or the centre
     R fx = (R)0.5, fy = (R)0.5, fz = (R)0.5;
@@ -339,14 +411,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     }
     if (tau > (R)0) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
 
-    const double Y = wgt * (double)(kap_i * X);
-    neumaier(sy, cy, Y);
-    neumaier(sy2, cy2, Y * Y);
+    tally.add(wgt * (kap_i * X));
     nsteps += (unsigned long long)steps;
   }
 
   // warp reduction of the lanes' tallies
-  double S = sy + cy, S2 = sy2 + cy2;
+  double S = tally.sum(), S2 = tally.sum2();
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     S += __shfl_xor_sync(0xffffffffu, S, off);
@@ -376,10 +446,12 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s) {
   const int threads = 256;
   const long long blocks = (a.ncells_box * 32 + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const size_t smem =
+      a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) : 0;
   if (precision == 1)
-    trace_kernel<double><<<(unsigned)blocks, threads, 0, s>>>(a);
+    trace_kernel<double><<<(unsigned)blocks, threads, smem, s>>>(a);
   else
-    trace_kernel<float><<<(unsigned)blocks, threads, 0, s>>>(a);
+    trace_kernel<float><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

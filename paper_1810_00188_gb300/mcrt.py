@@ -55,6 +55,10 @@ class mcrt_solve_params(C.Structure):
                 ("use_box", C.c_int), ("box", C.c_int * 6), ("steps_out", C.c_void_p)]
 
 
+class mcrt_tuning(C.Structure):
+    _fields_ = [("min_blocks_per_sm", C.c_int)]
+
+
 class mcrt_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("rays", C.c_uint64), ("capped", C.c_uint64),
                 ("wall_hits", C.c_uint64), ("T_max", C.c_double), ("kernel_ms", C.c_float),
@@ -65,7 +69,7 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_proposal",
            "mcrt_solve_qrad", "mcrt_get_stats", "mcrt_destroy", "mcrt_status_string",
-           "mcrt_last_error")
+           "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning")
 
 
 def library_path() -> str:
@@ -91,6 +95,8 @@ def load(build_if_missing: bool = True):
         L.mcrt_set_cell_proposal.argtypes = [vp, vp, vp, vp, C.c_int, vp]
         L.mcrt_solve_qrad.argtypes = [vp, C.POINTER(mcrt_solve_params), vp, vp, C.c_int, vp]
         L.mcrt_get_stats.argtypes = [vp, C.POINTER(mcrt_solve_stats)]
+        L.mcrt_set_tuning.argtypes = [vp, C.POINTER(mcrt_tuning)]
+        L.mcrt_get_tuning.argtypes = [vp, C.POINTER(mcrt_tuning)]
         L.mcrt_destroy.argtypes = [vp]
         L.mcrt_status_string.argtypes = [C.c_int]
         L.mcrt_status_string.restype = C.c_char_p
@@ -137,6 +143,18 @@ def mcrt_get_stats(ctx) -> dict:
     st = mcrt_solve_stats()
     _check(load().mcrt_get_stats(ctx, C.byref(st)), ctx)
     return {f: getattr(st, f) for f, _ in mcrt_solve_stats._fields_}
+
+
+def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0):
+    t = mcrt_tuning()
+    t.min_blocks_per_sm = min_blocks_per_sm
+    _check(load().mcrt_set_tuning(ctx, C.byref(t)), ctx)
+
+
+def mcrt_get_tuning(ctx) -> dict:
+    t = mcrt_tuning()
+    _check(load().mcrt_get_tuning(ctx, C.byref(t)), ctx)
+    return {"min_blocks_per_sm": t.min_blocks_per_sm}
 
 
 def mcrt_destroy(ctx):
@@ -266,3 +284,9 @@ class Solver:
 
     def stats(self) -> dict:
         return mcrt_get_stats(self.ctx)
+
+    def set_tuning(self, min_blocks_per_sm: int = 0):
+        mcrt_set_tuning(self.ctx, min_blocks_per_sm)
+
+    def tuning(self) -> dict:
+        return mcrt_get_tuning(self.ctx)

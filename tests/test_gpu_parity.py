@@ -197,3 +197,30 @@ def test_full_size_channel_64cubed_sampled_cells():
         o = oracle.solve(grid, kd, T, x, rays=1000, seed=0, tol=1e-4, max_steps=1 << 20,
                          box=(i, i + 1, j, j + 1, k, k + 1))
         assert abs(q[k, j, i] - o["q"][0, 0, 0]) <= 1e-4 * o["scale"][0, 0, 0], (i, j, k)
+
+
+@pytest.mark.parametrize("rays", [255, 256, 257, 600])
+def test_fp32_multi_block_cells_parity(rays):
+    """Cells whose rays span several ray blocks of the FP32 kernel (and ragged
+    last blocks) against the oracle."""
+    grid, kd, T, x = inputs.nongrey_channel(6, 8, 5, seed=12, eps_wall=0.9)
+    orc, q, s, st, stats = run_pair(grid, kd, T, x, rays, mcrt.MCRT_FP32, seed=13)
+    assert_parity(orc, q, s, st, mcrt.MCRT_FP32)
+    assert stats["rays"] == grid.ncells * rays
+
+
+def test_fp32_results_independent_of_launch_shape():
+    """The FP32 kernel reduces every cell's samples in a fixed order, so the
+    occupancy target does not change a single bit."""
+    grid, kd, T, x = inputs.nongrey_channel(20, 16, 12, seed=14, eps_wall=0.8)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    q0, s0, st0 = S.solve(rays=300, seed=3, with_steps=True)
+    for mb in (1, 3, 4, 2):
+        S.set_tuning(mb)
+        assert S.tuning()["min_blocks_per_sm"] == mb
+        q, s, st = S.solve(rays=300, seed=3, with_steps=True)
+        assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
+    with pytest.raises(mcrt.McrtError):
+        S.set_tuning(9)
+    S.close()

@@ -111,6 +111,7 @@ typedef struct {
   uint64_t rays;           /* rays traced                                         */
   uint64_t capped;         /* rays stopped by max_steps                           */
   uint64_t wall_hits;      /* wall events                                         */
+  uint64_t max_ray_steps;  /* medium segments of the longest ray                  */
   double T_max;            /* temperature of the plain proposal (Eq. 13)          */
   float kernel_ms;         /* device time of the last solve's trace launch        */
   int launches;            /* kernels the last solve launched                     */

@@ -551,7 +551,12 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
       CK(cudaMemcpyAsync(p->steps_out, dst, nbox * sizeof(unsigned long long),
                          cudaMemcpyDeviceToHost, s),
          "copy steps");
+    unsigned long long flag = 0;
+    CK(cudaMemcpyAsync(&flag, (unsigned long long *)ctx->counters.p + 5, sizeof(flag),
+                       cudaMemcpyDeviceToHost, s),
+       "read error flag");
     CK(cudaStreamSynchronize(s), "sync");
+    if (flag != 0) return fail(ctx, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
   }
   return MCRT_OK;
 }
@@ -587,6 +592,7 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   out->steps = c[0];
   out->capped = c[1];
   out->wall_hits = c[2];
+  out->max_ray_steps = c[4];
   out->rays = c[3];
   out->T_max = ctx->last_T_max;
   out->kernel_ms = ms;

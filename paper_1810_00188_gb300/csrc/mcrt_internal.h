@@ -44,7 +44,7 @@ struct TraceArgs {
   // outputs (box-sized)
   double *q, *sigma;
   unsigned long long *steps_cell;
-  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] unused [5] error flags
+  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps) [5] error flags
 };
 
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).

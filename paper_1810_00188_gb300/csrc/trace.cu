@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   const R inv_hemi = (R)1 / (R)hemi, inv_lo = (R)1 / (R)(8388608u - hemi);
 
   Tally<R> tally;
-  unsigned long long nsteps = 0, ncap = 0, nwall = 0;
+  unsigned long long nsteps = 0, ncap = 0, nwall = 0, max_ray = 0;
 
   for (int r = lane; r < a.rays; r += 32) {
     const unsigned ray = (unsigned)(a.ray_offset + (unsigned long long)r);
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
 
     tally.add(wgt * (kap_i * X));
     nsteps += (unsigned long long)steps;
+    max_ray = max(max_ray, (unsigned long long)steps);
   }
 
   // warp reduction of the lanes' tallies
@@ -424,8 +425,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     nsteps += __shfl_xor_sync(0xffffffffu, nsteps, off);
     ncap += __shfl_xor_sync(0xffffffffu, ncap, off);
     nwall += __shfl_xor_sync(0xffffffffu, nwall, off);
+    max_ray = max(max_ray, __shfl_xor_sync(0xffffffffu, max_ray, off));
   }
   if (lane == 0) {
+    atomicMax(a.counters + 4, max_ray);
     const double N = (double)a.rays;
     const double Q = S / N;
     a.q[w] = Q;  // Eq. 8: mean of the per-ray samples

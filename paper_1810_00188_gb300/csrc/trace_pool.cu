@@ -33,6 +33,9 @@ namespace {
 constexpr int POOL = 64;   // prepared ray states per warp
 constexpr int NB = 256;    // rays per work item
 constexpr int WARPS = 8;   // warps per CTA
+constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks; each warp takes a
+                           // contiguous run, so an SM's rays stay near its cells and
+                           // the field gathers hit L1 (rays average a few cells)
 
 struct WarpSmem {
   float4 A[POOL];     // t0x, t0y, t0z, tsx
@@ -116,17 +119,30 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
 
 struct Item {  // warp-uniform description of one work item
   int lin, ix, iy, iz;  // emitting cell
-  long long bc;         // index in the box
+  int bc;               // index in the box (x fastest)
   int b, nr;            // ray block and its number of rays
 };
 
-__device__ __forceinline__ Item make_item(const TraceArgs &a, long long bc, int b) {
+// Position p of the brick-ordered enumeration -> box coordinates; false when the
+// position falls outside the box (ragged edge bricks).
+__device__ __forceinline__ bool brick_cell(const TraceArgs &a, long long p, int nbx, int nby,
+                                           int &bx, int &by, int &bz) {
+  const long long brick = p / (BRICK * BRICK * BRICK);
+  const int off = (int)(p - brick * (BRICK * BRICK * BRICK));
+  const int gx = (int)(brick % nbx), gy = (int)((brick / nbx) % nby), gz = (int)(brick / ((long long)nbx * nby));
+  bx = gx * BRICK + off % BRICK;
+  by = gy * BRICK + (off / BRICK) % BRICK;
+  bz = gz * BRICK + off / (BRICK * BRICK);
+  return bx < a.bnx && by < a.bny && bz < a.bnz;
+}
+
+__device__ __forceinline__ Item make_item(const TraceArgs &a, int bx, int by, int bz, int b) {
   Item it;
-  it.bc = bc;
+  it.bc = bx + a.bnx * (by + a.bny * bz);
   it.b = b;
-  it.ix = a.bi0 + (int)(bc % a.bnx);
-  it.iy = a.bj0 + (int)((bc / a.bnx) % a.bny);
-  it.iz = a.bk0 + (int)(bc / ((long long)a.bnx * a.bny));
+  it.ix = a.bi0 + bx;
+  it.iy = a.bj0 + by;
+  it.iz = a.bk0 + bz;
   it.lin = it.ix + a.nx * (it.iy + a.ny * it.iz);
   const int left = a.rays - b * NB;
   it.nr = left < NB ? left : NB;
@@ -153,8 +169,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
   const long long W = (long long)gridDim.x * WARPS;
   const long long wg = (long long)blockIdx.x * WARPS + warp;
   const int nblk = (a.rays + NB - 1) / NB;
-  const long long my_cells = wg < a.ncells_box ? (a.ncells_box - 1 - wg) / W + 1 : 0;
-  const long long n_items = my_cells * nblk;
+  const int nbx = (a.bnx + BRICK - 1) / BRICK, nby = (a.bny + BRICK - 1) / BRICK,
+            nbz = (a.bnz + BRICK - 1) / BRICK;
+  const long long P = (long long)nbx * nby * nbz * (BRICK * BRICK * BRICK);
+  const long long chunk = (P + W - 1) / W;
+  long long p_next = wg * chunk;
+  const long long p_end = min(P, p_next + chunk);
+  int cur_bx = 0, cur_by = 0, cur_bz = 0, cur_b = nblk;  // cell being initialised
+  bool exhausted = p_next >= p_end;
+  unsigned my_cells = 0;
 
   const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nxyz = nxy * nz, nb = a.nb,
             ng = a.ng, nT = a.nT;
@@ -167,10 +190,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
   const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
 
   // warp-uniform scheduling state
-  long long it_init = 0, it_done = 0;
+  int it_init = 0, it_done = 0;  // item sequence numbers
   int r_init = 0;
   unsigned head = 0, tail = 0;  // ring positions (mod POOL); count = tail - head
-  Item item0 = make_item(a, wg, 0), item1 = item0;  // the two slots' items
+  Item item0 = make_item(a, 0, 0, 0, 0), item1 = item0;  // the two slots' items
   int done0 = 0, done1 = 0;                          // finished rays per slot
   double cell_S = 0.0, cell_S2 = 0.0;  // running sums of the oldest item's cell
   unsigned long long cell_steps_lane = 0;
@@ -184,16 +207,33 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
   float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
   float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
   unsigned long long tot_steps = 0;
-  unsigned tot_cap = 0, tot_wall = 0;
+  unsigned tot_cap = 0, tot_wall = 0, max_ray = 0;
 
-  while (it_done < n_items) {
+  while (!(exhausted && r_init == 0 && it_done == it_init)) {
     bool progress = false;
     // ---- A. converged initialisation of up to 32 rays into the ring ----
-    if ((int)(tail - head) <= POOL - 32 && it_init < n_items && it_init < it_done + 2) {
+    const bool room = (int)(tail - head) <= POOL - 32 && it_init < it_done + 2;
+    if (room && r_init == 0 && !exhausted && cur_b >= nblk) {
+      // next emitting cell of this warp's brick-ordered run
+      bool found = false;
+      while (!found && p_next < p_end) {
+        found = brick_cell(a, p_next, nbx, nby, cur_bx, cur_by, cur_bz);
+        ++p_next;
+      }
+      if (found) {
+        cur_b = 0;
+        ++my_cells;
+      } else {
+        exhausted = true;
+      }
+      progress = true;
+    }
+    if (room && (r_init > 0 || cur_b < nblk)) {
       progress = true;
       const int s = (int)(it_init & 1);
       if (r_init == 0) {
-        const Item nI = make_item(a, wg + (it_init / nblk) * W, (int)(it_init % nblk));
+        const Item nI = make_item(a, cur_bx, cur_by, cur_bz, cur_b);
+        ++cur_b;
         if (s)
           item1 = nI;
         else
@@ -322,8 +362,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
 
     // ---- C. one march step per active lane (Algorithm 1 "March") ----
     bool finished = false;
+    if (__any_sync(0xffffffffu, active)) progress = true;  // warp-uniform
     if (active) {
-      progress = true;
       float tn;
       int ax;
       if (tnx <= tny && tnx <= tnz) {
@@ -449,6 +489,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
         else
           steps0 += (unsigned)steps;
         tot_steps += (unsigned long long)steps;
+        max_ray = max(max_ray, (unsigned)steps);
         active = false;
         finished = true;
       }
@@ -506,7 +547,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
       }
       ++it_done;
       __syncwarp();
-      if (it_done >= n_items) break;
     }
     if (!progress) {  // unreachable by construction; never spin
       if (lane == 0) atomicOr(a.counters + 5, 1ull);
@@ -520,8 +560,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
     tot_steps += __shfl_xor_sync(0xffffffffu, tot_steps, off);
     tot_cap += __shfl_xor_sync(0xffffffffu, tot_cap, off);
     tot_wall += __shfl_xor_sync(0xffffffffu, tot_wall, off);
+    max_ray = max(max_ray, __shfl_xor_sync(0xffffffffu, max_ray, off));
   }
-  if (lane == 0 && n_items > 0) {
+  if (lane == 0 && my_cells > 0) {
+    atomicMax(a.counters + 4, (unsigned long long)max_ray);
     atomicAdd(a.counters + 0, tot_steps);
     if (tot_cap) atomicAdd(a.counters + 1, (unsigned long long)tot_cap);
     if (tot_wall) atomicAdd(a.counters + 2, (unsigned long long)tot_wall);

@@ -61,7 +61,8 @@ class mcrt_tuning(C.Structure):
 
 class mcrt_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("rays", C.c_uint64), ("capped", C.c_uint64),
-                ("wall_hits", C.c_uint64), ("T_max", C.c_double), ("kernel_ms", C.c_float),
+                ("wall_hits", C.c_uint64), ("max_ray_steps", C.c_uint64), ("T_max", C.c_double),
+                ("kernel_ms", C.c_float),
                 ("launches", C.c_int)]
 
 

@@ -41,13 +41,14 @@ struct mcrt_ctx {
   bool prop_valid = false;
   double prop_T_max = -1;
   // device buffers
-  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wgt32, cn, cg,
+  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;
   int last_launches = 0;
   int min_blocks = 2;
+  int steps_per_round = 1;
   double last_T_max = 0;
   std::string err;
 };
@@ -329,6 +330,9 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 2 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 2 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->wg.p, kd->w_g, ng * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  std::vector<float> wg32(kd->w_g, kd->w_g + ng);
+  CK(ensure(ctx->wg32, ng * sizeof(float)), "alloc w_g");
+  CK(cudaMemcpy(ctx->wg32.p, wg32.data(), ng * sizeof(float), cudaMemcpyHostToDevice), "copy");
   ctx->have_kdist = true;
   return MCRT_OK;
 }
@@ -488,6 +492,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.bwall64 = (const double *)ctx->bwall64.p;
   a.w_g = (const double *)ctx->wg.p;
   a.wgt32 = (const float *)ctx->wgt32.p;
+  a.w_g32 = (const float *)ctx->wg32.p;
   a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
@@ -534,7 +539,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   CK(cudaMemsetAsync(ctx->counters.p, 0, 6 * sizeof(unsigned long long), s), "clear counters");
   CK(cudaEventRecord(ctx->ev0, s), "event");
   if (p->precision == MCRT_FP32)
-    CK(mcrt::launch_trace_pool(a, ctx->min_blocks, s), "trace launch");
+    CK(mcrt::launch_trace_pool(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
   else
     CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
   CK(cudaEventRecord(ctx->ev1, s), "event");
@@ -564,15 +569,20 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
 int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
   if (!ctx) return MCRT_E_ARG;
   if (!t) return fail(ctx, MCRT_E_ARG, "null tuning");
-  if (t->min_blocks_per_sm < 0 || t->min_blocks_per_sm > 4)
-    return fail(ctx, MCRT_E_ARG, "min_blocks_per_sm outside 0..4");
+  if (t->min_blocks_per_sm < 0 || t->min_blocks_per_sm > 3)
+    return fail(ctx, MCRT_E_ARG, "min_blocks_per_sm outside 0..3");
+  if (t->steps_per_round != 0 && t->steps_per_round != 1 && t->steps_per_round != 2 &&
+      t->steps_per_round != 4)
+    return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 2;
+  ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
   return MCRT_OK;
 }
 
 int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   if (!ctx || !t) return MCRT_E_ARG;
   t->min_blocks_per_sm = ctx->min_blocks;
+  t->steps_per_round = ctx->steps_per_round;
   return MCRT_OK;
 }
 
@@ -606,7 +616,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
-                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wgt32, &ctx->cn,
+                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
     for (DevBuf *b : bufs) release(*b);

@@ -28,6 +28,7 @@ struct TraceArgs {
   const double *bwall64;
   const double *w_g;        // [ng]
   const float *wgt32;       // [nb*ng] plain-proposal ray weight w_g / (p q), host FP64 -> FP32
+  const float *w_g32;       // [ng] quadrature weights in FP32
   const unsigned long long *cn;       // [nb] cumulative counts of 2^32 (plain proposal)
   const unsigned long long *cg;       // [nb*ng]
   const unsigned long long *cell_cn;  // per-cell proposal [ncells][nb] or null
@@ -50,8 +51,10 @@ struct TraceArgs {
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // FP32 kernel with converged initialisation and lane refill (trace_pool.cu).
-// min_blocks: occupancy target (1-4 CTAs of 256 threads per SM; registers vs spills).
-cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, cudaStream_t s);
+// min_blocks: occupancy target (1-3 CTAs of 256 threads per SM; registers vs
+// spills); steps_per_round: march steps between pool refills (1, 2, 4).
+cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, int steps_per_round,
+                              cudaStream_t s);
 
 // Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
 // layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),

@@ -61,15 +61,37 @@ __device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1) {
   return c;
 }
 
+// The hot path avoids integer<->float conversion instructions, which GB300
+// executes on its narrow FP64 pipe, with exact bit constructions:
+//  * uniform (w>>9 + 1/2) 2^-23: the 23 draw bits as the mantissa of a number
+//    in [1, 2), minus (1 - 2^-24); exact (Sterbenz);
+//  * u < 2^23 as a float: mantissa bits of 2^23 + u, minus 2^23; exact;
+//  * floor of f in [0, 2^22]: adding 1.5 * 2^23 with round-down puts floor(f)
+//    in the low mantissa bits (the sum's ulp is 1); exact.
 __device__ __forceinline__ float unif(unsigned w) {
-  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
 }
 
-__device__ __forceinline__ void tpos(float T, float T0, float inv_dT, int nT, int &it, float &fr) {
+__device__ __forceinline__ float u23_to_float(unsigned u) {
+  return __uint_as_float(0x4B000000u | u) - 8388608.f;
+}
+
+// A count in [0, 2^32] as a float (16-bit halves, each exact).
+__device__ __forceinline__ float u33_to_float(unsigned long long c) {
+  if (c >> 32) return 4294967296.f;
+  const unsigned v = (unsigned)c;
+  return u23_to_float(v >> 16) * 65536.f + u23_to_float(v & 0xffffu);
+}
+
+// Linear-interpolation position on the uniform T nodes, clamped to the end
+// nodes (same result as clamp(floor(f), 0, nT-2) and clamp(f - floor, 0, 1)).
+__device__ __forceinline__ void tpos(float T, float T0, float inv_dT, float tmax_node, int &it,
+                                     float &fr) {
   const float f = (T - T0) * inv_dT;
-  const float fl = fminf(fmaxf(floorf(f), 0.f), (float)(nT - 2));
-  it = (int)fl;
-  fr = fminf(fmaxf(f - fl, 0.f), 1.f);
+  const float fc = fminf(fmaxf(f, 0.f), tmax_node);
+  const float big = __fadd_rd(fc, 12582912.f);
+  it = __float_as_int(big) - 0x4B400000;
+  fr = fminf(fmaxf(f - (big - 12582912.f), 0.f), 1.f);
 }
 
 __device__ __forceinline__ int pick(const unsigned long long *__restrict__ cum, int K, unsigned u) {
@@ -149,7 +171,7 @@ __device__ __forceinline__ Item make_item(const TraceArgs &a, int bx, int by, in
   return it;
 }
 
-template <int MINB>
+template <int MINB, int KSTEPS>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem *wsm = reinterpret_cast<WarpSmem *>(smem_raw);
@@ -185,7 +207,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
   const float2 *__restrict__ ktab = a.ktab32;
   const float2 *__restrict__ btab = a.btab32;
   const float T0 = (float)a.T0, inv_dT = (float)a.inv_dT, inv_xref = (float)a.inv_xref,
-              tol = (float)a.tol;
+              tol = (float)a.tol, tmax_node = (float)(a.nT - 2);
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
   const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
 
@@ -247,7 +269,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
         const float2 fi = __ldg(field + cell);
         int it_i;
         float fr_i;
-        tpos(fi.x, T0, inv_dT, nT, it_i, fr_i);
+        tpos(fi.x, T0, inv_dT, tmax_node, it_i, fr_i);
         const unsigned long long *__restrict__ cn =
             plain ? (a.counts_in_smem ? s_counts : a.cn) : a.cell_cn + (size_t)cell * nb;
         const unsigned long long *__restrict__ cg =
@@ -257,11 +279,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
         const unsigned m0 = u.x >> 9;
         float mu, ph;
         if (m0 < hemi) {
-          mu = 1.f - ((float)m0 + 0.5f) * __frcp_rn((float)hemi);
-          ph = (float)hemi * 1.1920928955078125e-07f;
+          const float h = u23_to_float(hemi);
+          mu = 1.f - (u23_to_float(m0) + 0.5f) * __frcp_rn(h);
+          ph = h * 1.1920928955078125e-07f;
         } else {
-          mu = -(((float)(m0 - hemi) + 0.5f) * __frcp_rn((float)(8388608u - hemi)));
-          ph = (float)(8388608u - hemi) * 1.1920928955078125e-07f;
+          const float h = u23_to_float(8388608u - hemi);
+          mu = -((u23_to_float(m0 - hemi) + 0.5f) * __frcp_rn(h));
+          ph = h * 1.1920928955078125e-07f;
         }
         float sphi, cphi;
         sincospif(2.f * unif(u.y), &sphi, &cphi);
@@ -275,8 +299,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
         } else {
           const unsigned long long mn = cn[nn] - (nn ? cn[nn - 1] : 0ull);
           const unsigned long long mg = cgn[gg] - (gg ? cgn[gg - 1] : 0ull);
-          const float p = ((float)mn * 2.3283064365386963e-10f) * ((float)mg * 2.3283064365386963e-10f);
-          wgt = __fdividef((float)__ldg(a.w_g + gg), p) * __fdividef(6.2831855f, ph);
+          const float p = u33_to_float(mn) * 2.3283064365386963e-10f * (u33_to_float(mg) * 2.3283064365386963e-10f);
+          wgt = __fdividef(__ldg(a.w_g32 + gg), p) * __fdividef(6.2831855f, ph);
         }
         float fx = 0.5f, fy = 0.5f, fz = 0.5f;
         if (a.origin == 0) {
@@ -360,139 +384,141 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
       __syncwarp();
     }
 
-    // ---- C. one march step per active lane (Algorithm 1 "March") ----
+    // ---- C. up to KSTEPS march steps per active lane (Algorithm 1 "March") ----
     bool finished = false;
     if (__any_sync(0xffffffffu, active)) progress = true;  // warp-uniform
-    if (active) {
-      float tn;
-      int ax;
-      if (tnx <= tny && tnx <= tnz) {
-        ax = 0;
-        tn = tnx;
-      } else if (tny <= tnz) {
-        ax = 1;
-        tn = tny;
-      } else {
-        ax = 2;
-        tn = tnz;
-      }
-      const float ds = fmaxf(tn - tprev, 0.f);
-      const float2 f = __ldg(field + lin);
-      int it;
-      float fr;
-      tpos(f.x, T0, inv_dT, nT, it, fr);
-      const float2 kk = __ldg(ktab + krow + it);
-      const float2 bb = __ldg(btab + n * nT + it);
-      const float kap = (kk.x + fr * kk.y) * (f.y * inv_xref);
-      const float Bj = bb.x + fr * bb.y;
-      float alpha, trans;
-      absorb(kap * ds, alpha, trans);
-      X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
-      tau *= trans;                     // Eq. 3
-      B_last = Bj;
-      ++steps;
-      bool done = tau <= tol;
-      if (!done && steps >= a.max_steps) {
-        done = true;
-        ++tot_cap;
-      }
-      if (!done) {
-        tprev = tn;
-        if (ax == 0) {
-          cntx += 1.f;
-          tnx = fmaf(cntx, tsx, t0x);
-          ix += sx;
-          lin += sx;
-          if (ix >= nx) {
-            ix -= nx;
-            lin -= nx;
-          } else if (ix < 0) {
-            ix += nx;
-            lin += nx;
-          }
-        } else if (ax == 2) {
-          cntz += 1.f;
-          tnz = fmaf(cntz, tsz, t0z);
-          iz += sz;
-          lin += sz * nxy;
-          if (iz >= nz) {
-            iz -= nz;
-            lin -= nxyz;
-          } else if (iz < 0) {
-            iz += nz;
-            lin += nxyz;
-          }
+    for (int kstep = 0; kstep < KSTEPS; ++kstep) {
+      if (!active) break;
+        float tn;
+        int ax;
+        if (tnx <= tny && tnx <= tnz) {
+          ax = 0;
+          tn = tnx;
+        } else if (tny <= tnz) {
+          ax = 1;
+          tn = tny;
         } else {
-          cnty += 1.f;
-          tny = fmaf(cnty, tsy, t0y);
-          iy += sy;
-          lin += sy * nx;
-          if (iy < 0 || iy >= ny) {
-            // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
-            const int wl = iy < 0 ? 0 : 1;
-            const float eps = wl ? eps1 : eps0;
-            const float Bw = __ldg(a.bwall32 + wl * nb + n);
-            X += (B_i - Bw) * (tau * eps);
-            tau *= 1.f - eps;
-            ++tot_wall;
-            if (eps >= 1.f || tau <= tol) {
-              done = true;
-            } else {
-              float nfx = 0.5f, nfz = 0.5f;
-              if (sx > 0)
-                nfx = 1.f - (tnx - tprev) / tsx;
-              else if (sx < 0)
-                nfx = (tnx - tprev) / tsx;
-              if (sz > 0)
-                nfz = 1.f - (tnz - tprev) / tsz;
-              else if (sz < 0)
-                nfz = (tnz - tprev) / tsz;
-              nfx = fminf(fmaxf(nfx, 0.f), 1.f);
-              nfz = fminf(fmaxf(nfz, 0.f), 1.f);
-              const float nfy = wl == 0 ? 0.f : 1.f;
-              iy = wl == 0 ? 0 : ny - 1;
-              lin = ix + nx * iy + nxy * iz;
-              float ddx, ddy, ddz;
-              if (a.reflect == 1) {
-                // specular: |d| per axis unchanged, the y component flips
-                ddx = sx > 0 ? DX / tsx : (sx < 0 ? -DX / tsx : 0.f);
-                ddz = sz > 0 ? DZ / tsz : (sz < 0 ? -DZ / tsz : 0.f);
-                ddy = wl == 0 ? DY / tsy : -DY / tsy;
+          ax = 2;
+          tn = tnz;
+        }
+        const float ds = fmaxf(tn - tprev, 0.f);
+        const float2 f = __ldg(field + lin);
+        int it;
+        float fr;
+        tpos(f.x, T0, inv_dT, tmax_node, it, fr);
+        const float2 kk = __ldg(ktab + krow + it);
+        const float2 bb = __ldg(btab + n * nT + it);
+        const float kap = (kk.x + fr * kk.y) * (f.y * inv_xref);
+        const float Bj = bb.x + fr * bb.y;
+        float alpha, trans;
+        absorb(kap * ds, alpha, trans);
+        X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
+        tau *= trans;                     // Eq. 3
+        B_last = Bj;
+        ++steps;
+        bool done = tau <= tol;
+        if (!done && steps >= a.max_steps) {
+          done = true;
+          ++tot_cap;
+        }
+        if (!done) {
+          tprev = tn;
+          if (ax == 0) {
+            cntx += 1.f;
+            tnx = fmaf(cntx, tsx, t0x);
+            ix += sx;
+            lin += sx;
+            if (ix >= nx) {
+              ix -= nx;
+              lin -= nx;
+            } else if (ix < 0) {
+              ix += nx;
+              lin += nx;
+            }
+          } else if (ax == 2) {
+            cntz += 1.f;
+            tnz = fmaf(cntz, tsz, t0z);
+            iz += sz;
+            lin += sz * nxy;
+            if (iz >= nz) {
+              iz -= nz;
+              lin -= nxyz;
+            } else if (iz < 0) {
+              iz += nz;
+              lin += nxyz;
+            }
+          } else {
+            cnty += 1.f;
+            tny = fmaf(cnty, tsy, t0y);
+            iy += sy;
+            lin += sy * nx;
+            if (iy < 0 || iy >= ny) {
+              // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
+              const int wl = iy < 0 ? 0 : 1;
+              const float eps = wl ? eps1 : eps0;
+              const float Bw = __ldg(a.bwall32 + wl * nb + n);
+              X += (B_i - Bw) * (tau * eps);
+              tau *= 1.f - eps;
+              ++tot_wall;
+              if (eps >= 1.f || tau <= tol) {
+                done = true;
               } else {
-                const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
-                const float mr = sqrtf(unif(v.x));
-                float sp, cp;
-                sincospif(2.f * unif(v.y), &sp, &cp);
-                const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
-                ddx = sr * cp;
-                ddy = wl == 0 ? mr : -mr;
-                ddz = sr * sp;
+                float nfx = 0.5f, nfz = 0.5f;
+                if (sx > 0)
+                  nfx = 1.f - (tnx - tprev) / tsx;
+                else if (sx < 0)
+                  nfx = (tnx - tprev) / tsx;
+                if (sz > 0)
+                  nfz = 1.f - (tnz - tprev) / tsz;
+                else if (sz < 0)
+                  nfz = (tnz - tprev) / tsz;
+                nfx = fminf(fmaxf(nfx, 0.f), 1.f);
+                nfz = fminf(fmaxf(nfz, 0.f), 1.f);
+                const float nfy = wl == 0 ? 0.f : 1.f;
+                iy = wl == 0 ? 0 : ny - 1;
+                lin = ix + nx * iy + nxy * iz;
+                float ddx, ddy, ddz;
+                if (a.reflect == 1) {
+                  // specular: |d| per axis unchanged, the y component flips
+                  ddx = sx > 0 ? DX / tsx : (sx < 0 ? -DX / tsx : 0.f);
+                  ddz = sz > 0 ? DZ / tsz : (sz < 0 ? -DZ / tsz : 0.f);
+                  ddy = wl == 0 ? DY / tsy : -DY / tsy;
+                } else {
+                  const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
+                  const float mr = sqrtf(unif(v.x));
+                  float sp, cp;
+                  sincospif(2.f * unif(v.y), &sp, &cp);
+                  const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
+                  ddx = sr * cp;
+                  ddy = wl == 0 ? mr : -mr;
+                  ddz = sr * sp;
+                }
+                ++nrefl;
+                axis_setup(ddx, nfx, DX, sx, t0x, tsx);
+                axis_setup(ddy, nfy, DY, sy, t0y, tsy);
+                axis_setup(ddz, nfz, DZ, sz, t0z, tsz);
+                cntx = cnty = cntz = 0.f;
+                tnx = t0x;
+                tny = t0y;
+                tnz = t0z;
+                tprev = 0.f;
               }
-              ++nrefl;
-              axis_setup(ddx, nfx, DX, sx, t0x, tsx);
-              axis_setup(ddy, nfy, DY, sy, t0y, tsy);
-              axis_setup(ddz, nfz, DZ, sz, t0z, tsz);
-              cntx = cnty = cntz = 0.f;
-              tnx = t0x;
-              tny = t0y;
-              tnz = t0z;
-              tprev = 0.f;
             }
           }
         }
-      }
-      if (done) {
-        if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
-        S.ybuf[slot][rl] = scale * X;
-        if (slot)
-          steps1 += (unsigned)steps;
-        else
-          steps0 += (unsigned)steps;
-        tot_steps += (unsigned long long)steps;
-        max_ray = max(max_ray, (unsigned)steps);
-        active = false;
-        finished = true;
-      }
+        if (done) {
+          if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+          S.ybuf[slot][rl] = scale * X;
+          if (slot)
+            steps1 += (unsigned)steps;
+          else
+            steps0 += (unsigned)steps;
+          tot_steps += (unsigned long long)steps;
+          max_ray = max(max_ray, (unsigned)steps);
+          active = false;
+          finished = true;
+        }
+    
     }
     // ---- D. bookkeeping and in-order completion of work items ----
     const unsigned fin0 = __ballot_sync(0xffffffffu, finished && slot == 0);
@@ -571,7 +597,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_pool_kernel(const Trac
   }
 }
 
-template <int MINB>
+template <int MINB, int KSTEPS>
 cudaError_t launch_pool_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
   // per-device launch shape, computed once per device and shared-memory size
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
@@ -585,12 +611,12 @@ cudaError_t launch_pool_variant(const TraceArgs &a, cudaStream_t s, size_t smem)
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (configured_smem[dev] != (int)smem) {
-    e = cudaFuncSetAttribute(trace_pool_kernel<MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(trace_pool_kernel<MINB, KSTEPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], trace_pool_kernel<MINB>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], trace_pool_kernel<MINB, KSTEPS>,
                                                       WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
@@ -599,22 +625,29 @@ cudaError_t launch_pool_variant(const TraceArgs &a, cudaStream_t s, size_t smem)
   const long long need = (a.ncells_box + WARPS - 1) / WARPS;
   long long blocks = (long long)num_sms[dev] * blocks_per_sm[dev];
   if (blocks > need) blocks = need;
-  trace_pool_kernel<MINB><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  trace_pool_kernel<MINB, KSTEPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, cudaStream_t s) {
+cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, int steps_per_round,
+                              cudaStream_t s) {
   if (a.ncells_box <= 0) return cudaSuccess;
   const size_t smem = WARPS * sizeof(WarpSmem) +
                       (a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) : 0);
-  switch (min_blocks) {
-    case 1: return launch_pool_variant<1>(a, s, smem);
-    case 3: return launch_pool_variant<3>(a, s, smem);
-    case 4: return launch_pool_variant<4>(a, s, smem);
-    default: return launch_pool_variant<2>(a, s, smem);
+#define MCRT_POOL_K(MB)                                                   \
+  switch (steps_per_round) {                                              \
+    case 2: return launch_pool_variant<MB, 2>(a, s, smem);                \
+    case 4: return launch_pool_variant<MB, 4>(a, s, smem);                \
+    default: return launch_pool_variant<MB, 1>(a, s, smem);               \
   }
+  switch (min_blocks) {
+    case 1: MCRT_POOL_K(1)
+    case 3: MCRT_POOL_K(3)
+    default: MCRT_POOL_K(2)
+  }
+#undef MCRT_POOL_K
 }
 
 }  // namespace mcrt

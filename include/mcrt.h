@@ -122,10 +122,12 @@ typedef struct {
  * an autotuner.  Q, sigma and the step counts do not depend on these settings:
  * every cell's samples are reduced in a fixed order. */
 typedef struct {
-  int min_blocks_per_sm;   /* 0: default (2); 1..3 CTAs of 256 threads per SM,
+  int min_blocks_per_sm;   /* 0: default (3); 1..4 CTAs of 256 threads per SM,
                               trading registers per thread against occupancy */
-  int steps_per_round;     /* 0: default (1); 1, 2 or 4 march steps per lane
+  int steps_per_round;     /* 0: default (2); 1, 2 or 4 march steps per lane
                               between refills of idle lanes                      */
+  int scratch_mib;         /* 0: default (1024); cap of the per-ray sample
+                              scratch; larger solves run in several chunks      */
 } mcrt_tuning;
 
 /* Creates a context on grid->device.  *out receives the handle (NULL on error).

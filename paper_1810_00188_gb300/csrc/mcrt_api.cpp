@@ -42,13 +42,15 @@ struct mcrt_ctx {
   double prop_T_max = -1;
   // device buffers
   DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
+      guide, ybuf, step_acc,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;
   int last_launches = 0;
-  int min_blocks = 2;
-  int steps_per_round = 1;
+  int min_blocks = 3;
+  int steps_per_round = 2;
+  int scratch_mib = 1024;
   double last_T_max = 0;
   std::string err;
 };
@@ -188,6 +190,17 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
     }
   CK(cudaMemcpyAsync(ctx->wgt32.p, w32.data(), sizeof(float) * nb * ng, cudaMemcpyHostToDevice, s),
      "upload weights");
+  // guide table of the band counts: guide[m] = first band with cum > m 2^32 / G
+  const int G = mcrt::fp32_guide_size();
+  std::vector<unsigned short> guide(G);
+  for (int m = 0, k = 0; m < G; ++m) {
+    const unsigned long long lo = (unsigned long long)m << (32 - 6);
+    while (cn[k] <= lo) ++k;
+    guide[m] = (unsigned short)k;
+  }
+  CK(cudaMemcpyAsync(ctx->guide.p, guide.data(), sizeof(unsigned short) * G, cudaMemcpyHostToDevice,
+                     s),
+     "upload guide");
   CK(cudaMemcpyAsync(ctx->cn.p, cn.data(), sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s),
      "upload band counts");
   CK(cudaMemcpyAsync(ctx->cg.p, cg.data(), sizeof(unsigned long long) * nb * ng,
@@ -323,6 +336,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(ensure(ctx->cn, nb * sizeof(unsigned long long)), "alloc band counts");
   CK(ensure(ctx->cg, (size_t)nb * ng * sizeof(unsigned long long)), "alloc g counts");
   CK(ensure(ctx->wgt32, (size_t)nb * ng * sizeof(float)), "alloc weights");
+  CK(ensure(ctx->guide, (size_t)mcrt::fp32_guide_size() * sizeof(unsigned short)), "alloc guide");
   CK(cudaMemcpy(ctx->ktab64.p, k64.data(), nk * sizeof(double2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
@@ -494,6 +508,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.wgt32 = (const float *)ctx->wgt32.p;
   a.w_g32 = (const float *)ctx->wg32.p;
   a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
+  a.guide = (const unsigned short *)ctx->guide.p;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
   if (p->proposal == MCRT_PROPOSAL_CELL) {
@@ -537,13 +552,36 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.steps_cell = dst;
 
   CK(cudaMemsetAsync(ctx->counters.p, 0, 6 * sizeof(unsigned long long), s), "clear counters");
-  CK(cudaEventRecord(ctx->ev0, s), "event");
-  if (p->precision == MCRT_FP32)
-    CK(mcrt::launch_trace_pool(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
-  else
+  int launches = 0;
+  if (p->precision == MCRT_FP32 && nbox > 0) {
+    // brick-ordered positions in chunks whose per-ray samples fit the scratch
+    const long long P = mcrt::fp32_bricks_positions(a.bnx, a.bny, a.bnz);
+    const long long cap = (long long)ctx->scratch_mib << 20;
+    long long Pc = cap / ((long long)p->rays_per_cell * (long long)sizeof(float));
+    if (Pc < 1) Pc = 1;
+    if (Pc > P) Pc = P;
+    CK(ensure(ctx->ybuf, (size_t)Pc * p->rays_per_cell * sizeof(float)), "alloc sample scratch");
+    CK(ensure(ctx->step_acc, (size_t)Pc * sizeof(unsigned long long)), "alloc step scratch");
+    a.ybuf = (float *)ctx->ybuf.p;
+    a.step_acc = (unsigned long long *)ctx->step_acc.p;
+    CK(cudaEventRecord(ctx->ev0, s), "event");
+    for (long long p0 = 0; p0 < P; p0 += Pc) {
+      a.chunk_p0 = p0;
+      a.chunk_p1 = p0 + Pc < P ? p0 + Pc : P;
+      if (dst)
+        CK(cudaMemsetAsync(ctx->step_acc.p, 0, (size_t)(a.chunk_p1 - p0) * sizeof(unsigned long long), s),
+           "clear step scratch");
+      CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
+      launches += 2;
+    }
+    CK(cudaEventRecord(ctx->ev1, s), "event");
+  } else {
+    CK(cudaEventRecord(ctx->ev0, s), "event");
     CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
-  CK(cudaEventRecord(ctx->ev1, s), "event");
-  ctx->last_launches = nbox > 0 ? 1 : 0;
+    CK(cudaEventRecord(ctx->ev1, s), "event");
+    launches = nbox > 0 ? 1 : 0;
+  }
+  ctx->last_launches = launches;
   ctx->last_stream = s;
   ctx->solved = true;
   ctx->last_T_max = Tm;
@@ -569,13 +607,16 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
 int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
   if (!ctx) return MCRT_E_ARG;
   if (!t) return fail(ctx, MCRT_E_ARG, "null tuning");
-  if (t->min_blocks_per_sm < 0 || t->min_blocks_per_sm > 3)
-    return fail(ctx, MCRT_E_ARG, "min_blocks_per_sm outside 0..3");
+  if (t->min_blocks_per_sm < 0 || t->min_blocks_per_sm > 4)
+    return fail(ctx, MCRT_E_ARG, "min_blocks_per_sm outside 0..4");
+  if (t->scratch_mib < 0 || t->scratch_mib > (1 << 20))
+    return fail(ctx, MCRT_E_ARG, "scratch_mib outside 0..2^20");
   if (t->steps_per_round != 0 && t->steps_per_round != 1 && t->steps_per_round != 2 &&
       t->steps_per_round != 4)
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
-  ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 2;
-  ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
+  ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
+  ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 2;
+  ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
   return MCRT_OK;
 }
 
@@ -583,6 +624,7 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   if (!ctx || !t) return MCRT_E_ARG;
   t->min_blocks_per_sm = ctx->min_blocks;
   t->steps_per_round = ctx->steps_per_round;
+  t->scratch_mib = ctx->scratch_mib;
   return MCRT_OK;
 }
 
@@ -616,7 +658,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
-                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn,
+                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
     for (DevBuf *b : bufs) release(*b);

@@ -35,6 +35,12 @@ struct TraceArgs {
   const unsigned long long *cell_cg;  // [ncells][nb*ng]
   const unsigned int *cell_hemi;      // [ncells] count of 2^23, or null (plain: 2^22)
   int counts_in_smem;                 // plain counts staged in shared memory (<= 48 KB)
+  const unsigned short *guide;        // [64] guide table of the plain band counts
+  // FP32 kernel: brick-order positions [chunk_p0, chunk_p1) of this launch, the
+  // per-ray sample scratch [(p - chunk_p0) * rays + r] and per-position step sums
+  long long chunk_p0, chunk_p1;
+  float *ybuf;
+  unsigned long long *step_acc;
   // solve
   int rays, max_steps, origin;
   double tol;
@@ -51,10 +57,15 @@ struct TraceArgs {
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // FP32 kernel with converged initialisation and lane refill (trace_pool.cu).
-// min_blocks: occupancy target (1-3 CTAs of 256 threads per SM; registers vs
-// spills); steps_per_round: march steps between pool refills (1, 2, 4).
-cudaError_t launch_trace_pool(const TraceArgs &a, int min_blocks, int steps_per_round,
+// FP32 kernel with converged initialisation and lane refill, then the per-cell
+// reduction (trace_fp32.cu); two launches per chunk.  min_blocks: occupancy
+// target (1-4 CTAs of 256 threads per SM); steps_per_round: march steps between
+// refills of idle lanes (1, 2, 4).
+cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s);
+long long fp32_bricks_positions(int bnx, int bny, int bnz);
+int fp32_brick_volume();
+int fp32_guide_size();
 
 // Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
 // layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),

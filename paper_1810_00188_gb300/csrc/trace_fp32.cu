@@ -1,0 +1,671 @@
+// FP32 ERMC ray-trace kernel (converged initialisation, lane refill) and the
+// per-cell reduction of its samples.
+//
+// Same estimator as trace.cu (Silvestri & Pecnik, arXiv:1810.00188: Eqs. 2, 3,
+// 12-17 and Algorithm 1), scheduled for the SIMT machine.  The paper identifies
+// warp divergence from rays of very different lengths as the dominant loss of a
+// GPU ERMC (Section 4.2) and reorders rays by absorption coefficient; here the
+// divergence is removed structurally:
+//
+//  * each warp owns a contiguous run of emitting cells in 8x8x8-brick order
+//    (rays travel a few cells on average, so an SM's field gathers stay in L1)
+//    and all their rays;
+//  * ray initialisation (Philox draws, band/g sampling, direction, origin, the
+//    emitting cell's kappa and B, the DDA set-up) runs converged: 32 lanes
+//    initialise 32 rays at once into a per-warp ring of prepared states in
+//    shared memory;
+//  * the march advances every active lane by up to KSTEPS cells per round; a lane
+//    whose ray ends stores its sample Y and takes the next prepared state;
+//  * samples go to a scratch array indexed by (cell, ray); reduce_cells_kernel
+//    sums each cell's samples in a fixed order (compensated binary32 pairs per
+//    lane, binary64 across lanes), so Q and sigma do not depend on scheduling,
+//    launch shape or box.
+//
+// GB300 issues binary64 arithmetic and int<->float conversions on a narrow pipe,
+// so the per-ray and per-step code uses neither: ray weights come from a
+// host-built FP64 table rounded once, and conversions are exact bit
+// constructions (see unif, u23_to_float, tpos).
+//
+// A round that makes no progress cannot happen; if it did, the warp sets an
+// error flag (counters[5]) and returns instead of spinning.
+#include <math.h>
+#include <stdint.h>
+
+#include "mcrt_internal.h"
+
+namespace mcrt {
+namespace {
+
+constexpr int POOL = 64;   // prepared ray states per warp
+constexpr int WARPS = 8;   // warps per CTA
+constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks
+constexpr int GUIDE = 64;  // guide-table buckets of the band CDF
+
+struct WarpRing {
+  float4 A[POOL];  // t0x, t0y, t0z, tsx
+  float4 B[POOL];  // tsy, tsz, B_i, w * kappa_i
+  uint4 C[POOL];   // n | g << 16, Philox ray index, axis signs, emitting cell (linear)
+  int4 D[POOL];    // sample slot (cell position in the chunk), ix, iy, iz
+};
+
+__device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Exact bit constructions instead of conversion instructions:
+//  * uniform (w>>9 + 1/2) 2^-23: the 23 draw bits as the mantissa of a number in
+//    [1, 2), minus (1 - 2^-24); exact (Sterbenz);
+//  * u < 2^23 as a float: mantissa bits of 2^23 + u, minus 2^23; exact;
+//  * floor / nearest integer of f in [0, 2^22]: adding 1.5 * 2^23 with directed
+//    or nearest rounding puts the integer in the low mantissa bits (the sum's ulp
+//    is 1); exact.
+__device__ __forceinline__ float unif(unsigned w) {
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
+}
+
+__device__ __forceinline__ float u23_to_float(unsigned u) {
+  return __uint_as_float(0x4B000000u | u) - 8388608.f;
+}
+
+__device__ __forceinline__ float u33_to_float(unsigned long long c) {
+  if (c >> 32) return 4294967296.f;
+  const unsigned v = (unsigned)c;
+  return u23_to_float(v >> 16) * 65536.f + u23_to_float(v & 0xffffu);
+}
+
+// Linear-interpolation position on the uniform T nodes, clamped to the end nodes
+// (same result as clamp(floor(f), 0, nT-2) and clamp(f - floor, 0, 1)).
+__device__ __forceinline__ void tpos(float T, float T0, float inv_dT, float tmax_node, int &it,
+                                     float &fr) {
+  const float f = (T - T0) * inv_dT;
+  const float fc = fminf(fmaxf(f, 0.f), tmax_node);
+  const float big = __fadd_rd(fc, 12582912.f);
+  it = __float_as_int(big) - 0x4B400000;
+  fr = fminf(fmaxf(f - (big - 12582912.f), 0.f), 1.f);
+}
+
+// sin(pi x), cos(pi x) for x in [0, 2]: x = k/2 + r with k the nearest integer of
+// 2x and |r| <= 1/4 (both exact), then Taylor series of sin and cos at pi r
+// (truncation below 2e-9 relative) rotated by the quadrant k.
+__device__ __forceinline__ void sincospi_02(float x, float &s, float &c) {
+  const float kf = __fadd_rn(2.f * x, 12582912.f);
+  const int k = __float_as_int(kf) - 0x4B400000;
+  const float r = x - 0.5f * (kf - 12582912.f);
+  const float a = 3.14159265358979f * r, a2 = a * a;
+  const float sp = a * (1.f + a2 * (-1.f / 6.f + a2 * (1.f / 120.f + a2 * (-1.f / 5040.f + a2 * (1.f / 362880.f)))));
+  const float cp = 1.f + a2 * (-0.5f + a2 * (1.f / 24.f + a2 * (-1.f / 720.f + a2 * (1.f / 40320.f + a2 * (-1.f / 3628800.f)))));
+  const int q = k & 3;
+  const float ss = (q & 1) ? cp : sp, cc = (q & 1) ? sp : cp;
+  s = (q & 2) ? -ss : ss;
+  c = ((q + 1) & 2) ? -cc : cc;
+}
+
+// First k with u < cum[k] (the inverse CDF of Eq. 17), started from a guide
+// table: guide[m] = first k with cum[k] > m 2^26, so the scan is short.
+__device__ __forceinline__ int pick_guided(const unsigned long long *__restrict__ cum,
+                                           const unsigned short *__restrict__ guide, unsigned u) {
+  int k = guide[u >> 26];
+  while ((unsigned long long)u >= cum[k]) ++k;
+  return k;
+}
+
+__device__ __forceinline__ int pick(const unsigned long long *__restrict__ cum, int K, unsigned u) {
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((unsigned long long)u < cum[mid])
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void absorb(float x, float &alpha, float &trans) {
+  // alpha = 1 - exp(-x) (Eq. 2), trans = exp(-x) (Eq. 3); a 4-term series below
+  // x = 0.05 avoids the cancellation of 1 - exp(-x)
+  const float e = __expf(-x);
+  const float sr = x * (1.f - x * (0.5f - x * (0.16666667f - x * 0.041666668f)));
+  const bool small = x < 0.05f;
+  alpha = small ? sr : 1.f - e;
+  trans = small ? 1.f - sr : e;
+}
+
+// Parametric ray o + t d along one axis: the m-th face crossing is at t0 + m ts.
+__device__ __forceinline__ void axis_setup(float d, float fr, float delta, int &s, float &t0,
+                                           float &ts) {
+  if (d > 0.f) {
+    s = 1;
+    ts = __fdividef(delta, d);
+    t0 = (1.f - fr) * ts;
+  } else if (d < 0.f) {
+    s = -1;
+    ts = __fdividef(delta, -d);
+    t0 = fr * ts;
+  } else {
+    s = 0;
+    ts = INFINITY;
+    t0 = INFINITY;
+  }
+}
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+
+// Brick-order position p (relative to the box) -> box coordinates; false for
+// positions outside the box (ragged edge bricks).
+__device__ __forceinline__ bool brick_cell(const TraceArgs &a, long long p, int &bx, int &by,
+                                           int &bz) {
+  const int nbx = (a.bnx + BRICK - 1) / BRICK, nby = (a.bny + BRICK - 1) / BRICK;
+  const long long brick = p / (BRICK * BRICK * BRICK);
+  const int off = (int)(p - brick * (BRICK * BRICK * BRICK));
+  const int gx = (int)(brick % nbx), gy = (int)((brick / nbx) % nby), gz = (int)(brick / ((long long)nbx * nby));
+  bx = gx * BRICK + off % BRICK;
+  by = gy * BRICK + (off / BRICK) % BRICK;
+  bz = gz * BRICK + off / (BRICK * BRICK);
+  return bx < a.bnx && by < a.bny && bz < a.bnz;
+}
+
+template <int MINB, int KSTEPS>
+__global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpRing *rings = reinterpret_cast<WarpRing *>(smem_raw);
+  const bool plain = a.cell_cn == nullptr;
+  // plain-proposal counts and guide table: staged in shared memory when they fit
+  const unsigned long long *s_cn = a.cn, *s_cg = a.cg;
+  const unsigned short *s_guide = a.guide;
+  if (plain && a.counts_in_smem) {
+    unsigned long long *cn_sh = reinterpret_cast<unsigned long long *>(smem_raw + WARPS * sizeof(WarpRing));
+    unsigned short *g_sh = reinterpret_cast<unsigned short *>(cn_sh + a.nb + a.nb * a.ng);
+    const int ncount = a.nb + a.nb * a.ng;
+    for (int i = threadIdx.x; i < ncount; i += blockDim.x)
+      cn_sh[i] = i < a.nb ? a.cn[i] : a.cg[i - a.nb];
+    for (int i = threadIdx.x; i < GUIDE; i += blockDim.x) g_sh[i] = a.guide[i];
+    s_cn = cn_sh;
+    s_cg = cn_sh + a.nb;
+    s_guide = g_sh;
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  WarpRing &R = rings[threadIdx.x >> 5];
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const long long W = (long long)gridDim.x * WARPS;
+  const long long wg = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  const long long per = (P + W - 1) / W;
+  long long p_next = a.chunk_p0 + wg * per;
+  const long long p_end = min(a.chunk_p1, p_next + per);
+
+  const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nxyz = nxy * nz, nb = a.nb,
+            ng = a.ng, nT = a.nT, N = a.rays;
+  const float2 *__restrict__ field = a.field32;
+  const float2 *__restrict__ ktab = a.ktab32;
+  const float2 *__restrict__ btab = a.btab32;
+  const float T0 = (float)a.T0, inv_dT = (float)a.inv_dT, inv_xref = (float)a.inv_xref,
+              tol = (float)a.tol, tmax_node = (float)(a.nT - 2);
+  const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
+  const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
+  float *__restrict__ Ybuf = a.ybuf;
+
+  // warp-uniform: the emitting cell being initialised and its next ray
+  int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N;
+  bool exhausted = false;
+  unsigned head = 0, tail = 0;  // ring positions (mod POOL)
+
+  // per-lane ray registers
+  bool active = false;
+  int lin = 0, ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0, slot = 0, r = 0, krow = 0,
+      n = 0;
+  unsigned ray = 0, nrefl = 0, cellid = 0;
+  float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
+  float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
+  unsigned long long tot_steps = 0;
+  unsigned tot_cap = 0, tot_wall = 0, max_ray = 0, tot_rays = 0;
+  int acc_slot = -1;  // run of steps for the per-cell step counts
+  unsigned acc_steps = 0;
+
+  for (;;) {
+    bool progress = false;
+    // ---- A. converged initialisation of up to 32 rays of one cell ----
+    if ((int)(tail - head) <= POOL - 32 && !exhausted) {
+      progress = true;
+      if (c_r >= N) {  // next emitting cell of this warp's brick-ordered run
+        bool found = false;
+        long long p = p_next;
+        while (!found && p < p_end) {
+          found = brick_cell(a, p, c_bx, c_by, c_bz);
+          ++p;
+        }
+        p_next = p;
+        if (found) {
+          c_r = 0;
+          c_slot = (int)(p - 1 - a.chunk_p0);
+          c_lin = (a.bi0 + c_bx) + nx * ((a.bj0 + c_by) + ny * (a.bk0 + c_bz));
+        } else {
+          exhausted = true;
+        }
+      }
+      if (!exhausted) {
+        const int rr = c_r + lane;
+        if (rr < N) {
+          const unsigned cell = (unsigned)c_lin;
+          const unsigned rayid = (unsigned)(a.ray_offset + (unsigned long long)rr);
+          const float2 fi = __ldg(field + cell);
+          int it_i;
+          float fr_i;
+          tpos(fi.x, T0, inv_dT, tmax_node, it_i, fr_i);
+          const uint4 u = philox10(make_uint4(cell, rayid, 0u, a.snapshot), a.key0, a.key1);
+          unsigned hemi = 4194304u;
+          int nn, gg;
+          float wgt;
+          if (plain) {
+            nn = pick_guided(s_cn, s_guide, u.z);
+            gg = pick(s_cg + nn * ng, ng, u.w);
+          } else {
+            hemi = __ldg(a.cell_hemi + cell);
+            const unsigned long long *cn = a.cell_cn + (size_t)cell * nb;
+            const unsigned long long *cgn0 = a.cell_cg + (size_t)cell * nb * ng;
+            nn = pick(cn, nb, u.z);
+            gg = pick(cgn0 + (size_t)nn * ng, ng, u.w);
+          }
+          // direction: hemisphere of the y axis by the integer count `hemi` of
+          // 2^23, mu uniform inside it (plain: mu = 1 - 2 U); phi = 2 pi R_phi
+          const unsigned m0 = u.x >> 9;
+          float mu, ph;
+          if (m0 < hemi) {
+            const float h = u23_to_float(hemi);
+            mu = 1.f - (u23_to_float(m0) + 0.5f) * __frcp_rn(h);
+            ph = h * 1.1920928955078125e-07f;
+          } else {
+            const float h = u23_to_float(8388608u - hemi);
+            mu = -((u23_to_float(m0 - hemi) + 0.5f) * __frcp_rn(h));
+            ph = h * 1.1920928955078125e-07f;
+          }
+          if (plain) {
+            wgt = __ldg(a.wgt32 + nn * ng + gg);
+          } else {
+            const unsigned long long *cn = a.cell_cn + (size_t)cell * nb;
+            const unsigned long long *cgn = a.cell_cg + ((size_t)cell * nb + nn) * ng;
+            const unsigned long long mn = cn[nn] - (nn ? cn[nn - 1] : 0ull);
+            const unsigned long long mg = cgn[gg] - (gg ? cgn[gg - 1] : 0ull);
+            const float p = u33_to_float(mn) * 2.3283064365386963e-10f * (u33_to_float(mg) * 2.3283064365386963e-10f);
+            wgt = __fdividef(__ldg(a.w_g32 + gg), p) * __fdividef(6.2831855f, ph);
+          }
+          float sphi, cphi;
+          sincospi_02(2.f * unif(u.y), sphi, cphi);
+          const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
+          float fx = 0.5f, fy = 0.5f, fz = 0.5f;
+          if (a.origin == 0) {
+            const uint4 v = philox10(make_uint4(cell, rayid, 1u, a.snapshot), a.key0, a.key1);
+            fx = unif(v.x);
+            fy = unif(v.y);
+            fz = unif(v.z);
+          }
+          const float2 ki = __ldg(ktab + (size_t)(nn * ng + gg) * nT + it_i);
+          const float2 bi = __ldg(btab + (size_t)nn * nT + it_i);
+          const float kap_i = (ki.x + fr_i * ki.y) * (fi.y * inv_xref);
+          int ssx, ssy, ssz;
+          float a0x, a0y, a0z, asx, asy, asz;
+          axis_setup(st * cphi, fx, DX, ssx, a0x, asx);
+          axis_setup(mu, fy, DY, ssy, a0y, asy);
+          axis_setup(st * sphi, fz, DZ, ssz, a0z, asz);
+          const int pos = (tail + lane) & (POOL - 1);
+          R.A[pos] = make_float4(a0x, a0y, a0z, asx);
+          R.B[pos] = make_float4(asy, asz, bi.x + fr_i * bi.y, wgt * kap_i);
+          const unsigned flags = (unsigned)(ssx + 1) | ((unsigned)(ssy + 1) << 2) |
+                                 ((unsigned)(ssz + 1) << 4);
+          R.C[pos] = make_uint4((unsigned)nn | ((unsigned)gg << 16), rayid, flags, cell);
+          R.D[pos] = make_int4(c_slot, a.bi0 + c_bx, a.bj0 + c_by, a.bk0 + c_bz);
+        }
+        tail += (unsigned)min(32, N - c_r);
+        c_r += 32;
+      }
+      __syncwarp();
+    }
+
+    // ---- B. idle lanes take prepared rays ----
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    const int avail = (int)(tail - head);
+    if (idle && avail > 0) {
+      progress = true;
+      const int rank = __popc(idle & lt_mask);
+      if (!active && rank < avail) {
+        const int pos = (head + rank) & (POOL - 1);
+        const float4 A = R.A[pos];
+        const float4 Bv = R.B[pos];
+        const uint4 Cv = R.C[pos];
+        const int4 Dv = R.D[pos];
+        t0x = A.x;
+        t0y = A.y;
+        t0z = A.z;
+        tsx = A.w;
+        tsy = Bv.x;
+        tsz = Bv.y;
+        B_i = Bv.z;
+        scale = Bv.w;
+        n = (int)(Cv.x & 0xffffu);
+        krow = (n * ng + (int)(Cv.x >> 16)) * nT;
+        ray = Cv.y;
+        sx = (int)(Cv.z & 3u) - 1;
+        sy = (int)((Cv.z >> 2) & 3u) - 1;
+        sz = (int)((Cv.z >> 4) & 3u) - 1;
+        cellid = Cv.w;
+        lin = (int)Cv.w;
+        slot = Dv.x;
+        ix = Dv.y;
+        iy = Dv.z;
+        iz = Dv.w;
+        r = (int)(ray - (unsigned)a.ray_offset);
+        tnx = t0x;
+        tny = t0y;
+        tnz = t0z;
+        cntx = cnty = cntz = 0.f;
+        tprev = 0.f;
+        tau = 1.f;
+        X = 0.f;
+        B_last = B_i;
+        steps = 0;
+        nrefl = 0;
+        active = true;
+      }
+      head += (unsigned)min(__popc(idle), avail);
+      __syncwarp();
+    }
+
+    const unsigned busy = __ballot_sync(0xffffffffu, active);
+    if (!busy && exhausted && tail == head) break;
+    if (busy) progress = true;
+
+    // ---- C. up to KSTEPS march steps per active lane (Algorithm 1 "March") ----
+    for (int kstep = 0; kstep < KSTEPS; ++kstep) {
+      if (!active) break;
+      float tn;
+      int ax;
+      if (tnx <= tny && tnx <= tnz) {
+        ax = 0;
+        tn = tnx;
+      } else if (tny <= tnz) {
+        ax = 1;
+        tn = tny;
+      } else {
+        ax = 2;
+        tn = tnz;
+      }
+      const float ds = fmaxf(tn - tprev, 0.f);
+      const float2 f = __ldg(field + lin);
+      int it;
+      float fr;
+      tpos(f.x, T0, inv_dT, tmax_node, it, fr);
+      const float2 kk = __ldg(ktab + krow + it);
+      const float2 bb = __ldg(btab + n * nT + it);
+      const float kap = (kk.x + fr * kk.y) * (f.y * inv_xref);
+      const float Bj = bb.x + fr * bb.y;
+      float alpha, trans;
+      absorb(kap * ds, alpha, trans);
+      X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
+      tau *= trans;                     // Eq. 3
+      B_last = Bj;
+      ++steps;
+      bool done = tau <= tol;
+      if (!done && steps >= a.max_steps) {
+        done = true;
+        ++tot_cap;
+      }
+      if (!done) {
+        tprev = tn;
+        if (ax == 0) {
+          cntx += 1.f;
+          tnx = fmaf(cntx, tsx, t0x);
+          ix += sx;
+          lin += sx;
+          if (ix >= nx) {
+            ix -= nx;
+            lin -= nx;
+          } else if (ix < 0) {
+            ix += nx;
+            lin += nx;
+          }
+        } else if (ax == 2) {
+          cntz += 1.f;
+          tnz = fmaf(cntz, tsz, t0z);
+          iz += sz;
+          lin += sz * nxy;
+          if (iz >= nz) {
+            iz -= nz;
+            lin -= nxyz;
+          } else if (iz < 0) {
+            iz += nz;
+            lin += nxyz;
+          }
+        } else {
+          cnty += 1.f;
+          tny = fmaf(cnty, tsy, t0y);
+          iy += sy;
+          lin += sy * nx;
+          if (iy < 0 || iy >= ny) {
+            // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
+            const int wl = iy < 0 ? 0 : 1;
+            const float eps = wl ? eps1 : eps0;
+            const float Bw = __ldg(a.bwall32 + wl * nb + n);
+            X += (B_i - Bw) * (tau * eps);
+            tau *= 1.f - eps;
+            ++tot_wall;
+            if (eps >= 1.f || tau <= tol) {
+              done = true;
+            } else {
+              float nfx = 0.5f, nfz = 0.5f;
+              if (sx > 0)
+                nfx = 1.f - (tnx - tprev) / tsx;
+              else if (sx < 0)
+                nfx = (tnx - tprev) / tsx;
+              if (sz > 0)
+                nfz = 1.f - (tnz - tprev) / tsz;
+              else if (sz < 0)
+                nfz = (tnz - tprev) / tsz;
+              nfx = fminf(fmaxf(nfx, 0.f), 1.f);
+              nfz = fminf(fmaxf(nfz, 0.f), 1.f);
+              const float nfy = wl == 0 ? 0.f : 1.f;
+              iy = wl == 0 ? 0 : ny - 1;
+              lin = ix + nx * iy + nxy * iz;
+              float ddx, ddy, ddz;
+              if (a.reflect == 1) {
+                // specular: |d| per axis unchanged, the y component flips
+                ddx = sx > 0 ? DX / tsx : (sx < 0 ? -DX / tsx : 0.f);
+                ddz = sz > 0 ? DZ / tsz : (sz < 0 ? -DZ / tsz : 0.f);
+                ddy = wl == 0 ? DY / tsy : -DY / tsy;
+              } else {
+                // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
+                const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
+                const float mr = sqrtf(unif(v.x));
+                float sp, cp;
+                sincospi_02(2.f * unif(v.y), sp, cp);
+                const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
+                ddx = sr * cp;
+                ddy = wl == 0 ? mr : -mr;
+                ddz = sr * sp;
+              }
+              ++nrefl;
+              axis_setup(ddx, nfx, DX, sx, t0x, tsx);
+              axis_setup(ddy, nfy, DY, sy, t0y, tsy);
+              axis_setup(ddz, nfz, DZ, sz, t0z, tsz);
+              cntx = cnty = cntz = 0.f;
+              tnx = t0x;
+              tny = t0y;
+              tnz = t0z;
+              tprev = 0.f;
+            }
+          }
+        }
+      }
+      if (done) {
+        if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+        Ybuf[(size_t)slot * N + r] = scale * X;     // the ray's sample Y (Eq. 14)
+        if (a.steps_cell) {
+          if (slot != acc_slot) {
+            if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
+            acc_slot = slot;
+            acc_steps = 0;
+          }
+          acc_steps += (unsigned)steps;
+        }
+        tot_steps += (unsigned long long)steps;
+        max_ray = max(max_ray, (unsigned)steps);
+        ++tot_rays;
+        active = false;
+      }
+    }
+    if (!progress) {  // unreachable by construction; never spin
+      if (lane == 0) atomicOr(a.counters + 5, 1ull);
+      break;
+    }
+  }
+  if (a.steps_cell && acc_slot >= 0 && acc_steps)
+    atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
+
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    tot_steps += __shfl_xor_sync(0xffffffffu, tot_steps, off);
+    tot_cap += __shfl_xor_sync(0xffffffffu, tot_cap, off);
+    tot_wall += __shfl_xor_sync(0xffffffffu, tot_wall, off);
+    max_ray = max(max_ray, __shfl_xor_sync(0xffffffffu, max_ray, off));
+    tot_rays += __shfl_xor_sync(0xffffffffu, tot_rays, off);
+  }
+  if (lane == 0 && tot_rays) {
+    atomicAdd(a.counters + 0, tot_steps);
+    atomicAdd(a.counters + 3, (unsigned long long)tot_rays);
+    if (tot_cap) atomicAdd(a.counters + 1, (unsigned long long)tot_cap);
+    if (tot_wall) atomicAdd(a.counters + 2, (unsigned long long)tot_wall);
+    atomicMax(a.counters + 4, (unsigned long long)max_ray);
+  }
+}
+
+// One warp per chunk position: the cell's N samples are summed in a fixed order
+// (lane l takes samples l, l + 32, ... as a compensated binary32 pair; the lanes
+// are combined in binary64 by a fixed butterfly), giving Q = sum / N (Eq. 8) and
+// its standard error.
+__global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int N = a.rays;
+  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       p < a.chunk_p1 - a.chunk_p0; p += W) {
+    int bx, by, bz;
+    if (!brick_cell(a, a.chunk_p0 + p, bx, by, bz)) continue;  // warp-uniform
+    const float *y = a.ybuf + (size_t)p * N;
+    float hi = 0.f, lo = 0.f, hi2 = 0.f, lo2 = 0.f;
+    for (int k = lane; k < N; k += 32) {
+      const float v = y[k];
+      two_sum_acc(hi, lo, v);
+      const float pr = v * v;
+      two_sum_acc(hi2, lo2, pr);
+      lo2 += fmaf(v, v, -pr);
+    }
+    double S = (double)hi + (double)lo, S2 = (double)hi2 + (double)lo2;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      S += __shfl_xor_sync(0xffffffffu, S, off);
+      S2 += __shfl_xor_sync(0xffffffffu, S2, off);
+    }
+    if (lane == 0) {
+      const long long bc = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
+      const double Nd = (double)N;
+      const double Q = S / Nd;
+      a.q[bc] = Q;
+      if (a.sigma) a.sigma[bc] = N > 1 ? sqrt(fmax(S2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
+      if (a.steps_cell) a.steps_cell[bc] = a.step_acc[p];
+    }
+  }
+}
+
+template <int MINB, int KSTEPS>
+cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
+  // per-device launch shape, computed once per device and shared-memory size
+  static int configured_smem[64], blocks_per_sm[64], num_sms[64];
+  static bool init_done = false;
+  if (!init_done) {
+    for (int i = 0; i < 64; ++i) configured_smem[i] = -1;
+    init_done = true;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (configured_smem[dev] != (int)smem) {
+    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev],
+                                                      trace_fp32_kernel<MINB, KSTEPS>, WARPS * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
+    configured_smem[dev] = (int)smem;
+  }
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  const long long need = (P + WARPS - 1) / WARPS;
+  long long blocks = (long long)num_sms[dev] * blocks_per_sm[dev];
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  trace_fp32_kernel<MINB, KSTEPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+long long fp32_bricks_positions(int bnx, int bny, int bnz) {
+  const long long nbx = (bnx + BRICK - 1) / BRICK, nby = (bny + BRICK - 1) / BRICK,
+                  nbz = (bnz + BRICK - 1) / BRICK;
+  return nbx * nby * nbz * (BRICK * BRICK * BRICK);
+}
+
+int fp32_brick_volume() { return BRICK * BRICK * BRICK; }
+
+int fp32_guide_size() { return GUIDE; }
+
+cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
+                              cudaStream_t s) {
+  if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
+  const size_t smem = WARPS * sizeof(WarpRing) +
+                      (a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) +
+                                              sizeof(unsigned short) * GUIDE
+                                        : 0);
+  cudaError_t e;
+#define MCRT_FP32_K(MB)                                              \
+  switch (steps_per_round) {                                         \
+    case 2: e = launch_variant<MB, 2>(a, s, smem); break;            \
+    case 4: e = launch_variant<MB, 4>(a, s, smem); break;            \
+    default: e = launch_variant<MB, 1>(a, s, smem); break;           \
+  }
+  switch (min_blocks) {
+    case 1: MCRT_FP32_K(1) break;
+    case 3: MCRT_FP32_K(3) break;
+    case 4: MCRT_FP32_K(4) break;
+    default: MCRT_FP32_K(2) break;
+  }
+#undef MCRT_FP32_K
+  if (e != cudaSuccess) return e;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  long long blocks = (P * 32 + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mcrt

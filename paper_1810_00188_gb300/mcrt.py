@@ -56,7 +56,8 @@ class mcrt_solve_params(C.Structure):
 
 
 class mcrt_tuning(C.Structure):
-    _fields_ = [("min_blocks_per_sm", C.c_int), ("steps_per_round", C.c_int)]
+    _fields_ = [("min_blocks_per_sm", C.c_int), ("steps_per_round", C.c_int),
+                ("scratch_mib", C.c_int)]
 
 
 class mcrt_solve_stats(C.Structure):
@@ -146,17 +147,20 @@ def mcrt_get_stats(ctx) -> dict:
     return {f: getattr(st, f) for f, _ in mcrt_solve_stats._fields_}
 
 
-def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0, steps_per_round: int = 0):
+def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
+                    scratch_mib: int = 0):
     t = mcrt_tuning()
     t.min_blocks_per_sm = min_blocks_per_sm
     t.steps_per_round = steps_per_round
+    t.scratch_mib = scratch_mib
     _check(load().mcrt_set_tuning(ctx, C.byref(t)), ctx)
 
 
 def mcrt_get_tuning(ctx) -> dict:
     t = mcrt_tuning()
     _check(load().mcrt_get_tuning(ctx, C.byref(t)), ctx)
-    return {"min_blocks_per_sm": t.min_blocks_per_sm, "steps_per_round": t.steps_per_round}
+    return {"min_blocks_per_sm": t.min_blocks_per_sm, "steps_per_round": t.steps_per_round,
+            "scratch_mib": t.scratch_mib}
 
 
 def mcrt_destroy(ctx):
@@ -287,8 +291,9 @@ class Solver:
     def stats(self) -> dict:
         return mcrt_get_stats(self.ctx)
 
-    def set_tuning(self, min_blocks_per_sm: int = 0, steps_per_round: int = 0):
-        mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round)
+    def set_tuning(self, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
+                   scratch_mib: int = 0):
+        mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round, scratch_mib)
 
     def tuning(self) -> dict:
         return mcrt_get_tuning(self.ctx)

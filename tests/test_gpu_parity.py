@@ -216,9 +216,12 @@ def test_fp32_results_independent_of_launch_shape():
     S = mcrt.Solver(grid, kd)
     S.set_fields(T, x)
     q0, s0, st0 = S.solve(rays=300, seed=3, with_steps=True)
-    for mb, k in ((1, 1), (3, 2), (2, 4), (1, 4), (2, 1)):
-        S.set_tuning(mb, k)
-        assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k}
+    # occupancy target, steps per round and the scratch cap (1 MiB forces many
+    # chunks here) change nothing
+    for mb, k, mib in ((1, 1, 0), (3, 2, 0), (2, 4, 1), (4, 4, 0), (1, 4, 3), (2, 1, 0)):
+        S.set_tuning(mb, k, mib)
+        assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k,
+                              "scratch_mib": mib if mib else 1024}
         q, s, st = S.solve(rays=300, seed=3, with_steps=True)
         assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
     with pytest.raises(mcrt.McrtError):

@@ -30,6 +30,13 @@ METRIC = "ray-cell steps/s"
 UNIT = "steps/s"
 MUFU_EX2_PER_CLK_PER_SM = 16  # MUFU.EX2 results per clock per SM
 N_SM = 152
+LANES_PER_SM = 128            # FP32/INT lanes per SM (one op per lane per clock)
+# Algorithmic FP32/INT operations of the estimator, counted from the source:
+OPS_PER_STEP = 44             # axis choice, table position, two interpolations,
+                              # absorption, tally, DDA advance
+OPS_PER_RAY = 260             # 2 Philox4x32-10 blocks (2 x 80), sampling, direction,
+                              # origin, DDA set-up, sample store
+GATHER_BYTES_PER_STEP = 8     # FP32 {T, x} of the traversed cell
 
 
 def parse():
@@ -181,6 +188,7 @@ def main():
     import torch
     import torch.distributed as dist
 
+    from paper_1810_00188_gb300 import dist as pdist
     from paper_1810_00188_gb300 import inputs, mcrt
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -194,12 +202,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def allreduce(v, op):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=op)
-        return float(t.item())
 
     grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=rank)
     S = mcrt.Solver(grid, kd, device=local)
@@ -241,17 +243,21 @@ def main():
     clk = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     t_local = sum(step_ms) / 1e3
-    t_max = allreduce(t_local, dist.ReduceOp.MAX if world > 1 else None)
-    steps_all = allreduce(float(steps_total), dist.ReduceOp.SUM if world > 1 else None)
+    steps_all, t_max = pdist.aggregate(float(steps_total), t_local, device="cuda")
     value = steps_all / t_max
     rays_all = float(world * a.steps) * grid.ncells * a.rays
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * sm_max * 1e6  # exp/s = steps/s ceiling
-    kernel_s = statistics.mean(kern_ms) / 1e3
+    clk = sm_max * 1e6
+    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * clk  # exp/s = steps/s ceiling
+    alu_peak = N_SM * LANES_PER_SM * clk              # op/s
+    kernel_s = statistics.mean(kern_ms) / 1e3          # the solve's launches, library events
     steps_per_launch = steps_total / a.steps
-    achieved = steps_per_launch / kernel_s
+    rays_per_launch = grid.ncells * a.rays
+    steps_rate = steps_per_launch / kernel_s
+    ops = OPS_PER_STEP * steps_per_launch + OPS_PER_RAY * rays_per_launch
+    achieved = ops / kernel_s
     hbm = float(peaks.get("hbm_gbs", 6789.3))
 
     result = None
@@ -262,12 +268,15 @@ def main():
                   "dtype": "f32", "data": "synthetic", "config": workload_config(a),
                   "rays_per_s": rays_all / t_max,
                   "steps_per_ray": steps_total / (a.steps * grid.ncells * a.rays),
-                  "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": ex2_peak / 1e9,
-                               "unit": "Gsteps/s", "frac": achieved / ex2_peak, "traffic": None,
-                               "peak_basis": f"MUFU ex2: {N_SM} SM x {MUFU_EX2_PER_CLK_PER_SM}/clk x "
-                                             f"{sm_max:.0f} MHz (1 exp per step)",
-                               "gather_GBs": achieved * 8 / 1e9,
-                               "gather_frac_of_hbm": achieved * 8 / 1e9 / hbm},
+                  "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                               "unit": "Top/s", "frac": achieved / alu_peak, "traffic": None,
+                               "peak_basis": f"FP32/INT issue: {N_SM} SM x {LANES_PER_SM} lanes x "
+                                             f"{sm_max:.0f} MHz, 1 op/lane/clk (derived)",
+                               "ops_per_step": OPS_PER_STEP, "ops_per_ray": OPS_PER_RAY,
+                               "kernel_ms": kernel_s * 1e3,
+                               "gather_GBs": steps_rate * GATHER_BYTES_PER_STEP / 1e9,
+                               "gather_frac_of_hbm": steps_rate * GATHER_BYTES_PER_STEP / 1e9 / hbm,
+                               "exp_frac_of_mufu": steps_rate / ex2_peak},
                   "gpu_launches": launches, "clocks": clk}
     # --- extras on rank 0: e2e through host buffers, FP64, solves/s at 1% sigma
     if rank == 0:

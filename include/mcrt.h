@@ -181,6 +181,33 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t);
  * solve yet), MCRT_E_CUDA. */
 int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
 
+/* Allocation-free solve.  The paper has no counterpart: this is a service for
+ * callers that may not allocate device memory while they run -- hosts that
+ * reserve the GPU's memory up front and treat any later cudaMalloc as an error or
+ * an unpredictable stall (a DNS code that owns the device between its own time
+ * steps, a serving process with a fixed memory plan).  It computes the same
+ * estimate as mcrt_solve_qrad with MCRT_FP32 and device outputs, on a context
+ * whose k-distribution and fields are already set, but calls no cudaMalloc or
+ * cudaFree: its scratch (per-ray samples, per-cell step sums, counters) lives in a
+ * static device array of 64 MiB that every GPU that loads the library holds until
+ * the process exits.
+ *  - q_out, sigma_out (nullable) and p->steps_out (nullable) are device pointers,
+ *    box-sized as for mcrt_solve_qrad; the call is asynchronous on cuda_stream.
+ *  - The first call on a device looks up the array's device address on that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - Large boxes run in several launches, each holding as many cells' samples as
+ *    fit; rays_per_cell above what one cell's samples can hold in 64 MiB (about
+ *    16.7 million) is rejected with MCRT_E_ARG and a message giving the limit.
+ *  - Every call shares the array and leaves the last call's contents in it (the
+ *    counters and step sums are cleared at the start of each call); calls whose
+ *    work overlaps on the GPU -- on different streams of one device -- race and
+ *    corrupt each other's results.
+ *  - mcrt_get_stats does not report this call.
+ * Errors: as mcrt_solve_qrad, plus MCRT_E_ARG when precision is not MCRT_FP32. */
+int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out,
+                            double *sigma_out, void *cuda_stream);
+
 /* Releases all device memory of the context; NULL is accepted.  Waits for the
  * context's outstanding work. */
 int mcrt_destroy(mcrt_ctx *ctx);

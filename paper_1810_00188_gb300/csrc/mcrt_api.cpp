@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -671,3 +672,181 @@ int mcrt_destroy(mcrt_ctx *ctx) {
 }
 
 }  // extern "C"
+
+// ---- allocation-free solve (no counterpart in the paper) ----------------------
+
+namespace {
+
+// Plain-proposal counts, weights and guide table built from fixed host buffers
+// (no heap or device allocation) into the context's existing device buffers.
+// Same construction as build_plain_proposal.
+int noalloc_build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
+  static std::mutex mu;
+  static unsigned long long cn[1024], cg[1024 * 64];
+  static double wn[1024], wgv[64], wtmp[64];
+  static float w32[1024 * 64];
+  static unsigned short guide[64];
+  std::lock_guard<std::mutex> lock(mu);
+  const int nb = ctx->nb, ng = ctx->ng, nT = ctx->nT;
+  for (int n = 0; n < nb; ++n) {
+    double sum = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      wgv[g] = ctx->w_g[g] *
+               interp_host(ctx->kappa.data() + ((size_t)n * ng + g) * nT, ctx->T0, ctx->dT, nT, Tm);
+      sum += wgv[g];
+    }
+    wn[n] = interp_host(ctx->B.data() + (size_t)n * nT, ctx->T0, ctx->dT, nT, Tm) * sum;
+    if (!quantize_counts(wgv, ng, cg + (size_t)n * ng)) {
+      for (int g = 0; g < ng; ++g) wtmp[g] = 1.0;  // never drawn; keep rows valid
+      quantize_counts(wtmp, ng, cg + (size_t)n * ng);
+    }
+  }
+  if (!quantize_counts(wn, nb, cn))
+    return fail(ctx, MCRT_E_ARG, "no band emits at T_max (all kappa*B are zero)");
+  for (int n = 0; n < nb; ++n)
+    for (int g = 0; g < ng; ++g) {
+      const unsigned long long mn = cn[n] - (n ? cn[n - 1] : 0ull);
+      const unsigned long long mg = cg[(size_t)n * ng + g] - (g ? cg[(size_t)n * ng + g - 1] : 0ull);
+      const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
+      w32[(size_t)n * ng + g] = mn && mg ? (float)((ctx->w_g[g] / p) * (6.283185307179586 / 0.5)) : 0.f;
+    }
+  const int G = mcrt::fp32_guide_size();
+  for (int m = 0, k = 0; m < G; ++m) {
+    const unsigned long long lo = (unsigned long long)m << (32 - 6);
+    while (cn[k] <= lo) ++k;
+    guide[m] = (unsigned short)k;
+  }
+  // pageable sources: each copy is staged before cudaMemcpyAsync returns
+  CK(cudaMemcpyAsync(ctx->wgt32.p, w32, sizeof(float) * nb * ng, cudaMemcpyHostToDevice, s), "weights");
+  CK(cudaMemcpyAsync(ctx->guide.p, guide, sizeof(unsigned short) * G, cudaMemcpyHostToDevice, s), "guide");
+  CK(cudaMemcpyAsync(ctx->cn.p, cn, sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s), "counts");
+  CK(cudaMemcpyAsync(ctx->cg.p, cg, sizeof(unsigned long long) * nb * ng, cudaMemcpyHostToDevice, s),
+     "counts");
+  ctx->prop_valid = true;
+  ctx->prop_T_max = Tm;
+  return MCRT_OK;
+}
+
+}  // namespace
+
+extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out,
+                                       double *sigma_out, void *stream) {
+  if (!ctx) return MCRT_E_ARG;
+  if (!p || !q_out) return fail(ctx, MCRT_E_ARG, "null params or q_out");
+  if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_ARG, "the allocation-free solve is FP32 only");
+  if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
+  if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
+  if (!(p->tol > 0.0 && p->tol < 1.0)) return fail(ctx, MCRT_E_ARG, "tol outside (0, 1)");
+  if (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER)
+    return fail(ctx, MCRT_E_ARG, "bad origin");
+  if (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL)
+    return fail(ctx, MCRT_E_ARG, "bad proposal");
+  if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
+    return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
+  // scratch layout in the static array: counters | per-position step sums | samples
+  const size_t total = mcrt::noalloc_scratch_bytes();
+  const size_t head_bytes = 256;
+  const size_t per_pos = (size_t)p->rays_per_cell * sizeof(float) + sizeof(unsigned long long);
+  if (total < head_bytes + 256 + per_pos)
+    return fail(ctx, MCRT_E_ARG,
+                "rays_per_cell too large for the static scratch of the allocation-free solve (" +
+                    std::to_string(total >> 20) + " MiB: at most " +
+                    std::to_string((total - head_bytes - 256 - sizeof(unsigned long long)) / sizeof(float)) +
+                    " rays per cell)");
+  const mcrt_grid_desc &g = ctx->grid;
+  int b[6] = {0, g.nx, 0, g.ny, 0, g.nz};
+  if (p->use_box) {
+    std::memcpy(b, p->box, sizeof(b));
+    if (b[0] < 0 || b[1] > g.nx || b[0] > b[1] || b[2] < 0 || b[3] > g.ny || b[2] > b[3] ||
+        b[4] < 0 || b[5] > g.nz || b[4] > b[5])
+      return fail(ctx, MCRT_E_ARG, "box outside the grid");
+  }
+  if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
+  if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
+    return fail(ctx, MCRT_E_STATE, "no cell proposal");
+  DeviceGuard dg(g.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  void *base = nullptr;
+  CK(mcrt::noalloc_scratch(g.device, &base), "static scratch address");
+
+  const double Tm = proposal_T_max(ctx);
+  if (!ctx->prop_valid || ctx->prop_T_max != Tm) {
+    const int rc = noalloc_build_plain_proposal(ctx, Tm, s);
+    if (rc != MCRT_OK) return rc;
+  }
+  const long long nbox = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
+  if (nbox == 0) return MCRT_OK;
+
+  mcrt::TraceArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.dx = g.lx / g.nx;
+  a.dy = g.ly / g.ny;
+  a.dz = g.lz / g.nz;
+  a.nb = ctx->nb;
+  a.ng = ctx->ng;
+  a.nT = ctx->nT;
+  a.T0 = ctx->T0;
+  a.inv_dT = 1.0 / ctx->dT;
+  a.inv_xref = 1.0 / ctx->x_ref;
+  a.eps_wall[0] = g.eps_wall[0];
+  a.eps_wall[1] = g.eps_wall[1];
+  a.reflect = g.reflect;
+  a.field32 = (const float2 *)ctx->field32.p;
+  a.ktab32 = (const float2 *)ctx->ktab32.p;
+  a.btab32 = (const float2 *)ctx->btab32.p;
+  a.bwall32 = (const float *)ctx->bwall32.p;
+  a.w_g = (const double *)ctx->wg.p;
+  a.w_g32 = (const float *)ctx->wg32.p;
+  a.wgt32 = (const float *)ctx->wgt32.p;
+  a.cn = (const unsigned long long *)ctx->cn.p;
+  a.cg = (const unsigned long long *)ctx->cg.p;
+  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
+  a.guide = (const unsigned short *)ctx->guide.p;
+  if (p->proposal == MCRT_PROPOSAL_CELL) {
+    a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
+    a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
+    a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
+  }
+  a.rays = p->rays_per_cell;
+  a.max_steps = p->max_steps;
+  a.origin = p->origin;
+  a.tol = p->tol;
+  a.key0 = (unsigned)(p->seed & 0xffffffffu);
+  a.key1 = (unsigned)(p->seed >> 32);
+  a.snapshot = p->snapshot;
+  a.ray_offset = p->ray_offset;
+  a.bi0 = b[0];
+  a.bj0 = b[2];
+  a.bk0 = b[4];
+  a.bnx = b[1] - b[0];
+  a.bny = b[3] - b[2];
+  a.bnz = b[5] - b[4];
+  a.ncells_box = nbox;
+  a.q = q_out;
+  a.sigma = sigma_out;
+  a.steps_cell = (unsigned long long *)p->steps_out;
+
+  // carve the static array; positions per chunk as many as fit
+  const long long P = mcrt::fp32_bricks_positions(a.bnx, a.bny, a.bnz);
+  long long Pc = (long long)((total - head_bytes - 256) / per_pos);
+  if (Pc > P) Pc = P;
+  unsigned char *cbase = (unsigned char *)base;
+  a.counters = (unsigned long long *)cbase;
+  a.step_acc = (unsigned long long *)(cbase + head_bytes);
+  const size_t ybuf_off = (head_bytes + (size_t)Pc * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  a.ybuf = (float *)(cbase + ybuf_off);
+  CK(cudaMemsetAsync(a.counters, 0, 6 * sizeof(unsigned long long), s), "clear counters");
+  for (long long p0 = 0; p0 < P; p0 += Pc) {
+    a.chunk_p0 = p0;
+    a.chunk_p1 = p0 + Pc < P ? p0 + Pc : P;
+    if (a.steps_cell)
+      CK(cudaMemsetAsync(a.step_acc, 0, (size_t)(a.chunk_p1 - p0) * sizeof(unsigned long long), s),
+         "clear step sums");
+    CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
+  }
+  return MCRT_OK;
+}

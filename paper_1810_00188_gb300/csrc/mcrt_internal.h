@@ -67,6 +67,12 @@ long long fp32_bricks_positions(int bnx, int bny, int bnz);
 int fp32_brick_volume();
 int fp32_guide_size();
 
+// Static device scratch of the allocation-free solve (noalloc.cu): its size,
+// and its device address on `device` (the current device), looked up once per
+// device.
+size_t noalloc_scratch_bytes();
+cudaError_t noalloc_scratch(int device, void **out);
+
 // Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
 // layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),
 // [1] min T bits (u64), [2] count of rejected cells.

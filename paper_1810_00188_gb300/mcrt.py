@@ -71,7 +71,7 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_proposal",
            "mcrt_solve_qrad", "mcrt_get_stats", "mcrt_destroy", "mcrt_status_string",
-           "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning")
+           "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning", "mcrt_solve_qrad_noalloc")
 
 
 def library_path() -> str:
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         L.mcrt_set_fields.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
         L.mcrt_set_cell_proposal.argtypes = [vp, vp, vp, vp, C.c_int, vp]
         L.mcrt_solve_qrad.argtypes = [vp, C.POINTER(mcrt_solve_params), vp, vp, C.c_int, vp]
+        L.mcrt_solve_qrad_noalloc.argtypes = [vp, C.POINTER(mcrt_solve_params), vp, vp, vp]
         L.mcrt_get_stats.argtypes = [vp, C.POINTER(mcrt_solve_stats)]
         L.mcrt_set_tuning.argtypes = [vp, C.POINTER(mcrt_tuning)]
         L.mcrt_get_tuning.argtypes = [vp, C.POINTER(mcrt_tuning)]
@@ -139,6 +140,12 @@ def mcrt_set_cell_proposal(ctx, cn_ptr, cg_ptr, hemi_ptr, mem: int, stream: int 
 
 def mcrt_solve_qrad(ctx, params: mcrt_solve_params, q_ptr, sigma_ptr, mem: int, stream: int = 0):
     _check(load().mcrt_solve_qrad(ctx, C.byref(params), q_ptr, sigma_ptr, mem, stream), ctx)
+
+
+def mcrt_solve_qrad_noalloc(ctx, params: mcrt_solve_params, q_ptr, sigma_ptr, stream: int = 0):
+    """The allocation-free solve: FP32, device outputs, scratch in a static 64 MiB
+    device array (see include/mcrt.h)."""
+    _check(load().mcrt_solve_qrad_noalloc(ctx, C.byref(params), q_ptr, sigma_ptr, stream), ctx)
 
 
 def mcrt_get_stats(ctx) -> dict:

@@ -249,9 +249,9 @@ def main():
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    clk = sm_max * 1e6
-    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * clk  # exp/s = steps/s ceiling
-    alu_peak = N_SM * LANES_PER_SM * clk              # op/s
+    f_clk = sm_max * 1e6
+    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * f_clk  # exp/s = steps/s ceiling
+    alu_peak = N_SM * LANES_PER_SM * f_clk              # op/s
     kernel_s = statistics.mean(kern_ms) / 1e3          # the solve's launches, library events
     steps_per_launch = steps_total / a.steps
     rays_per_launch = grid.ncells * a.rays
@@ -277,6 +277,8 @@ def main():
                                "gather_GBs": steps_rate * GATHER_BYTES_PER_STEP / 1e9,
                                "gather_frac_of_hbm": steps_rate * GATHER_BYTES_PER_STEP / 1e9 / hbm,
                                "exp_frac_of_mufu": steps_rate / ex2_peak},
+                  "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                              "max": max(step_ms)},
                   "gpu_launches": launches, "clocks": clk}
     # --- extras on rank 0: e2e through host buffers, FP64, solves/s at 1% sigma
     if rank == 0:

@@ -52,7 +52,46 @@ __global__ void __launch_bounds__(256) pack_fields_kernel(const void *T, const v
   }
 }
 
+// Interpolation position of every cell for the FP32 trace kernel: the node index
+// t and the fraction of the way to node t+1 (Section 2.2's linear interpolation
+// in T), packed as (t << 23) | round(fraction * 2^23), next to x / x_ref.  A
+// temperature at or beyond the last node maps to (nT-1, 0), which reads the same
+// value as (nT-2, 1) because the last node's slope is stored as 0.  Computed once
+// per field / table change, so the march does no floor, clamp or multiply.
+__global__ void __launch_bounds__(256) pack_positions_kernel(const double2 *f64, long long n, double T0,
+                                                             double inv_dT, int nT, double inv_xref,
+                                                             uint2 *pos) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = f64[i];
+    double f = (v.x - T0) * inv_dT;
+    if (!(f > 0.0)) f = 0.0;
+    if (f > (double)(nT - 1)) f = (double)(nT - 1);
+    const double fl = floor(f);
+    unsigned t = (unsigned)fl;
+    unsigned q = (unsigned)rint((f - fl) * 8388608.0);
+    if (q >= 8388608u) {
+      q = 0u;
+      ++t;
+    }
+    if (t > (unsigned)(nT - 1)) {
+      t = (unsigned)(nT - 1);
+      q = 0u;
+    }
+    pos[i] = make_uint2((t << 23) | q, __float_as_uint((float)(v.y * inv_xref)));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_positions(const double2 *f64, long long n, double T0, double inv_dT, int nT,
+                                  double inv_xref, uint2 *pos, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  pack_positions_kernel<<<(unsigned)blocks, 256, 0, s>>>(f64, n, T0, inv_dT, nT, inv_xref, pos);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
                                long long n, double2 *f64, float2 *f32,

@@ -42,7 +42,7 @@ struct mcrt_ctx {
   bool prop_valid = false;
   double prop_T_max = -1;
   // device buffers
-  DevBuf field64, field32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
+  DevBuf field64, field32, fpos32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
       guide, ybuf, step_acc,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -213,6 +213,19 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   return MCRT_OK;
 }
 
+// Interpolation positions of the FP32 kernel; valid once both the field and the
+// tables are set (recomputed whenever either changes).
+int refresh_positions(mcrt_ctx *ctx, cudaStream_t s) {
+  if (!ctx->have_kdist || !ctx->have_fields || ctx->nT > 512) return MCRT_OK;
+  const long long n = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+  CK(ensure(ctx->fpos32, (size_t)n * sizeof(uint2)), "alloc positions");
+  CK(mcrt::launch_pack_positions((const double2 *)ctx->field64.p, n, ctx->T0, 1.0 / ctx->dT, ctx->nT,
+                                 1.0 / ctx->x_ref, (uint2 *)ctx->fpos32.p, s),
+     "pack positions");
+  CK(cudaStreamSynchronize(s), "sync");
+  return MCRT_OK;
+}
+
 double proposal_T_max(const mcrt_ctx *ctx) {
   double Tm = ctx->T_max_field;
   for (int w = 0; w < 2; ++w)
@@ -349,7 +362,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(ensure(ctx->wg32, ng * sizeof(float)), "alloc w_g");
   CK(cudaMemcpy(ctx->wg32.p, wg32.data(), ng * sizeof(float), cudaMemcpyHostToDevice), "copy");
   ctx->have_kdist = true;
-  return MCRT_OK;
+  return refresh_positions(ctx, nullptr);
 }
 
 int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int mem, void *stream) {
@@ -399,7 +412,7 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   ctx->T_max_field = tmax;
   ctx->T_min_field = tmin;
   ctx->have_fields = true;
-  return MCRT_OK;
+  return refresh_positions(ctx, s);
 }
 
 int mcrt_set_cell_proposal(mcrt_ctx *ctx, const uint64_t *cn, const uint64_t *cg,
@@ -469,6 +482,8 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
   if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
     return fail(ctx, MCRT_E_STATE, "no cell proposal");
+  if (p->precision == MCRT_FP32 && ctx->nT > 512)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
   DeviceGuard dg(g.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
@@ -498,6 +513,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.eps_wall[1] = g.eps_wall[1];
   a.reflect = g.reflect;
   a.field32 = (const float2 *)ctx->field32.p;
+  a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.field64 = (const double2 *)ctx->field64.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
   a.ktab64 = (const double2 *)ctx->ktab64.p;
@@ -658,7 +674,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
@@ -764,6 +780,8 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
   if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
     return fail(ctx, MCRT_E_STATE, "no cell proposal");
+  if (ctx->nT > 512)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
   DeviceGuard dg(g.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
@@ -796,6 +814,7 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.eps_wall[1] = g.eps_wall[1];
   a.reflect = g.reflect;
   a.field32 = (const float2 *)ctx->field32.p;
+  a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
   a.btab32 = (const float2 *)ctx->btab32.p;
   a.bwall32 = (const float *)ctx->bwall32.p;

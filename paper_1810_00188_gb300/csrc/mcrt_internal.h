@@ -19,6 +19,7 @@ struct TraceArgs {
   int reflect;  // 0 diffuse, 1 specular
   // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
   const float2 *field32;    // {T, x} per cell
+  const uint2 *fpos32;      // FP32 kernel: {(node << 23) | fraction * 2^23, bits of x / x_ref}
   const double2 *field64;
   const float2 *ktab32;     // [nb*ng][nT] {kappa_t, kappa_{t+1} - kappa_t} at x_ref
   const double2 *ktab64;
@@ -76,6 +77,10 @@ cudaError_t noalloc_scratch(int device, void **out);
 // Packs T (and x, or x_ref where x is null) into the FP64 and FP32 field
 // layouts and reduces {max T, min T, bad count}.  stats: [0] max T bits (u64),
 // [1] min T bits (u64), [2] count of rejected cells.
+// Packs each cell's interpolation position for the FP32 kernel (nT <= 512).
+cudaError_t launch_pack_positions(const double2 *f64, long long n, double T0, double inv_dT, int nT,
+                                  double inv_xref, uint2 *pos, cudaStream_t s);
+
 cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
                                long long n, double2 *f64, float2 *f32,
                                unsigned long long *stats, cudaStream_t s);

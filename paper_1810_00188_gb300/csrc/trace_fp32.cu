@@ -23,8 +23,9 @@
 //
 // GB300 issues binary64 arithmetic and int<->float conversions on a narrow pipe,
 // so the per-ray and per-step code uses neither: ray weights come from a
-// host-built FP64 table rounded once, and conversions are exact bit
-// constructions (see unif, u23_to_float, tpos).
+// host-built FP64 table rounded once, each cell's table position is precomputed
+// (tpos), and the remaining conversions are exact bit constructions (unif,
+// u23_to_float).
 //
 // A round that makes no progress cannot happen; if it did, the warp sets an
 // error flag (counters[5]) and returns instead of spinning.
@@ -83,15 +84,12 @@ __device__ __forceinline__ float u33_to_float(unsigned long long c) {
   return u23_to_float(v >> 16) * 65536.f + u23_to_float(v & 0xffffu);
 }
 
-// Linear-interpolation position on the uniform T nodes, clamped to the end nodes
-// (same result as clamp(floor(f), 0, nT-2) and clamp(f - floor, 0, 1)).
-__device__ __forceinline__ void tpos(float T, float T0, float inv_dT, float tmax_node, int &it,
-                                     float &fr) {
-  const float f = (T - T0) * inv_dT;
-  const float fc = fminf(fmaxf(f, 0.f), tmax_node);
-  const float big = __fadd_rd(fc, 12582912.f);
-  it = __float_as_int(big) - 0x4B400000;
-  fr = fminf(fmaxf(f - (big - 12582912.f), 0.f), 1.f);
+// A cell's precomputed interpolation position (Section 2.2's linear
+// interpolation in T; see pack_positions_kernel): node index in the top 9 bits,
+// the fraction towards the next node as 23 mantissa bits (exact).
+__device__ __forceinline__ void tpos(unsigned packed, unsigned &it, float &fr) {
+  it = packed >> 23;
+  fr = __uint_as_float(0x3F800000u | (packed & 0x7FFFFFu)) - 1.f;
 }
 
 // sin(pi x), cos(pi x) for x in [0, 2]: x = k/2 + r with k the nearest integer of
@@ -214,11 +212,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
 
   const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nxyz = nxy * nz, nb = a.nb,
             ng = a.ng, nT = a.nT, N = a.rays;
-  const float2 *__restrict__ field = a.field32;
+  const uint2 *__restrict__ field = a.fpos32;
   const float2 *__restrict__ ktab = a.ktab32;
   const float2 *__restrict__ btab = a.btab32;
-  const float T0 = (float)a.T0, inv_dT = (float)a.inv_dT, inv_xref = (float)a.inv_xref,
-              tol = (float)a.tol, tmax_node = (float)(a.nT - 2);
+  const float tol = (float)a.tol;
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
   const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
   float *__restrict__ Ybuf = a.ybuf;
@@ -230,8 +227,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
 
   // per-lane ray registers
   bool active = false;
-  int lin = 0, ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0, slot = 0, r = 0, krow = 0,
-      n = 0;
+  // table and field indices are unsigned: widening them to 64-bit addresses is
+  // free, while sign-extending an int costs a conversion on GB300's narrow pipe
+  unsigned lin = 0, krow = 0, n = 0, slot = 0, r = 0;
+  int ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0;
   unsigned ray = 0, nrefl = 0, cellid = 0;
   float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
   float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
@@ -266,10 +265,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         if (rr < N) {
           const unsigned cell = (unsigned)c_lin;
           const unsigned rayid = (unsigned)(a.ray_offset + (unsigned long long)rr);
-          const float2 fi = __ldg(field + cell);
-          int it_i;
+          const uint2 fi = __ldg(field + cell);
+          unsigned it_i;
           float fr_i;
-          tpos(fi.x, T0, inv_dT, tmax_node, it_i, fr_i);
+          tpos(fi.x, it_i, fr_i);
           const uint4 u = philox10(make_uint4(cell, rayid, 0u, a.snapshot), a.key0, a.key1);
           unsigned hemi = 4194304u;
           int nn, gg;
@@ -317,9 +316,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             fy = unif(v.y);
             fz = unif(v.z);
           }
-          const float2 ki = __ldg(ktab + (size_t)(nn * ng + gg) * nT + it_i);
-          const float2 bi = __ldg(btab + (size_t)nn * nT + it_i);
-          const float kap_i = (ki.x + fr_i * ki.y) * (fi.y * inv_xref);
+          const float2 ki = __ldg(ktab + ((unsigned)(nn * ng + gg) * (unsigned)nT + it_i));
+          const float2 bi = __ldg(btab + ((unsigned)nn * (unsigned)nT + it_i));
+          const float kap_i = (ki.x + fr_i * ki.y) * __uint_as_float(fi.y);
           int ssx, ssy, ssz;
           float a0x, a0y, a0z, asx, asy, asz;
           axis_setup(st * cphi, fx, DX, ssx, a0x, asx);
@@ -359,19 +358,19 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         tsz = Bv.y;
         B_i = Bv.z;
         scale = Bv.w;
-        n = (int)(Cv.x & 0xffffu);
-        krow = (n * ng + (int)(Cv.x >> 16)) * nT;
+        n = Cv.x & 0xffffu;
+        krow = (n * (unsigned)ng + (Cv.x >> 16)) * (unsigned)nT;
         ray = Cv.y;
         sx = (int)(Cv.z & 3u) - 1;
         sy = (int)((Cv.z >> 2) & 3u) - 1;
         sz = (int)((Cv.z >> 4) & 3u) - 1;
         cellid = Cv.w;
-        lin = (int)Cv.w;
-        slot = Dv.x;
+        lin = Cv.w;
+        slot = (unsigned)Dv.x;
         ix = Dv.y;
         iy = Dv.z;
         iz = Dv.w;
-        r = (int)(ray - (unsigned)a.ray_offset);
+        r = ray - (unsigned)a.ray_offset;
         tnx = t0x;
         tny = t0y;
         tnz = t0z;
@@ -408,13 +407,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         tn = tnz;
       }
       const float ds = fmaxf(tn - tprev, 0.f);
-      const float2 f = __ldg(field + lin);
-      int it;
+      const uint2 f = __ldg(field + lin);
+      unsigned it;
       float fr;
-      tpos(f.x, T0, inv_dT, tmax_node, it, fr);
-      const float2 kk = __ldg(ktab + krow + it);
-      const float2 bb = __ldg(btab + n * nT + it);
-      const float kap = (kk.x + fr * kk.y) * (f.y * inv_xref);
+      tpos(f.x, it, fr);
+      const float2 kk = __ldg(ktab + (krow + it));
+      const float2 bb = __ldg(btab + (n * (unsigned)nT + it));
+      const float kap = (kk.x + fr * kk.y) * __uint_as_float(f.y);
       const float Bj = bb.x + fr * bb.y;
       float alpha, trans;
       absorb(kap * ds, alpha, trans);
@@ -433,36 +432,36 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           cntx += 1.f;
           tnx = fmaf(cntx, tsx, t0x);
           ix += sx;
-          lin += sx;
+          lin += (unsigned)sx;
           if (ix >= nx) {
             ix -= nx;
-            lin -= nx;
+            lin -= (unsigned)nx;
           } else if (ix < 0) {
             ix += nx;
-            lin += nx;
+            lin += (unsigned)nx;
           }
         } else if (ax == 2) {
           cntz += 1.f;
           tnz = fmaf(cntz, tsz, t0z);
           iz += sz;
-          lin += sz * nxy;
+          lin += (unsigned)(sz * nxy);
           if (iz >= nz) {
             iz -= nz;
-            lin -= nxyz;
+            lin -= (unsigned)nxyz;
           } else if (iz < 0) {
             iz += nz;
-            lin += nxyz;
+            lin += (unsigned)nxyz;
           }
         } else {
           cnty += 1.f;
           tny = fmaf(cnty, tsy, t0y);
           iy += sy;
-          lin += sy * nx;
+          lin += (unsigned)(sy * nx);
           if (iy < 0 || iy >= ny) {
             // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
             const int wl = iy < 0 ? 0 : 1;
             const float eps = wl ? eps1 : eps0;
-            const float Bw = __ldg(a.bwall32 + wl * nb + n);
+            const float Bw = __ldg(a.bwall32 + ((unsigned)(wl * nb) + n));
             X += (B_i - Bw) * (tau * eps);
             tau *= 1.f - eps;
             ++tot_wall;
@@ -482,7 +481,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
               nfz = fminf(fmaxf(nfz, 0.f), 1.f);
               const float nfy = wl == 0 ? 0.f : 1.f;
               iy = wl == 0 ? 0 : ny - 1;
-              lin = ix + nx * iy + nxy * iz;
+              lin = (unsigned)(ix + nx * iy + nxy * iz);
               float ddx, ddy, ddz;
               if (a.reflect == 1) {
                 // specular: |d| per axis unchanged, the y component flips
@@ -515,11 +514,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       }
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
-        Ybuf[(size_t)slot * N + r] = scale * X;     // the ray's sample Y (Eq. 14)
+        Ybuf[(size_t)slot * (unsigned)N + r] = scale * X;  // the ray's sample Y (Eq. 14)
         if (a.steps_cell) {
-          if (slot != acc_slot) {
+          if ((int)slot != acc_slot) {
             if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
-            acc_slot = slot;
+            acc_slot = (int)slot;
             acc_steps = 0;
           }
           acc_steps += (unsigned)steps;
@@ -555,40 +554,73 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   }
 }
 
-// One warp per chunk position: the cell's N samples are summed in a fixed order
-// (lane l takes samples l, l + 32, ... as a compensated binary32 pair; the lanes
-// are combined in binary64 by a fixed butterfly), giving Q = sum / N (Eq. 8) and
-// its standard error.
+// Compensated binary32 pair (hi + lo) plus another pair, renormalised.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float bhi, float blo) {
+  const float s = hi + bhi;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bhi - bb) + (lo + blo);
+  hi = s + err;
+  lo = err - (hi - s);
+}
+
+// Per-cell reduction.  A warp takes 32 consecutive chunk positions; for each
+// cell the lanes sum its N samples in a fixed order (lane l takes samples l,
+// l + 32, ... as compensated binary32 pairs, then a fixed butterfly of pair
+// additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
+// (Eq. 8) and the standard error in binary64 for their own cell at once.  The
+// order never depends on scheduling, so Q and sigma are reproducible bit for bit.
 __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
-  const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const int N = a.rays;
-  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       p < a.chunk_p1 - a.chunk_p0; p += W) {
-    int bx, by, bz;
-    if (!brick_cell(a, a.chunk_p0 + p, bx, by, bz)) continue;  // warp-uniform
-    const float *y = a.ybuf + (size_t)p * N;
-    float hi = 0.f, lo = 0.f, hi2 = 0.f, lo2 = 0.f;
-    for (int k = lane; k < N; k += 32) {
-      const float v = y[k];
-      two_sum_acc(hi, lo, v);
-      const float pr = v * v;
-      two_sum_acc(hi2, lo2, pr);
-      lo2 += fmaf(v, v, -pr);
-    }
-    double S = (double)hi + (double)lo, S2 = (double)hi2 + (double)lo2;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < P;
+       base += nwarps * 32) {
+    float mh = 0.f, ml = 0.f, mh2 = 0.f, ml2 = 0.f;
+    bool mine = false;
+    int mbx = 0, mby = 0, mbz = 0;
+    const int ncell = (int)min(32LL, P - base);
+    for (int c = 0; c < ncell; ++c) {
+      int bx, by, bz;
+      if (!brick_cell(a, a.chunk_p0 + base + c, bx, by, bz)) continue;  // warp-uniform
+      const float *y = a.ybuf + (size_t)(base + c) * N;
+      float hi = 0.f, lo = 0.f, hi2 = 0.f, lo2 = 0.f;
+      for (int k = lane; k < N; k += 32) {
+        const float v = y[k];
+        two_sum_acc(hi, lo, v);
+        const float pr = v * v;
+        two_sum_acc(hi2, lo2, pr);
+        lo2 += fmaf(v, v, -pr);
+      }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      S += __shfl_xor_sync(0xffffffffu, S, off);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, off);
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
+        const float oh2 = __shfl_xor_sync(0xffffffffu, hi2, off), ol2 = __shfl_xor_sync(0xffffffffu, lo2, off);
+        // combine in a lane-independent order so every lane holds identical bits
+        if (lane & off) {
+          float th = oh, tl = ol, th2 = oh2, tl2 = ol2;
+          pair_add(th, tl, hi, lo);
+          pair_add(th2, tl2, hi2, lo2);
+          hi = th; lo = tl; hi2 = th2; lo2 = tl2;
+        } else {
+          pair_add(hi, lo, oh, ol);
+          pair_add(hi2, lo2, oh2, ol2);
+        }
+      }
+      if (lane == c) {
+        mh = hi; ml = lo; mh2 = hi2; ml2 = lo2;
+        mine = true;
+        mbx = bx; mby = by; mbz = bz;
+      }
     }
-    if (lane == 0) {
-      const long long bc = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
+    if (mine) {
+      const double S = (double)mh + (double)ml, S2 = (double)mh2 + (double)ml2;
+      const long long bc = mbx + (long long)a.bnx * (mby + (long long)a.bny * mbz);
       const double Nd = (double)N;
       const double Q = S / Nd;
       a.q[bc] = Q;
       if (a.sigma) a.sigma[bc] = N > 1 ? sqrt(fmax(S2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
-      if (a.steps_cell) a.steps_cell[bc] = a.step_acc[p];
+      if (a.steps_cell) a.steps_cell[bc] = a.step_acc[base + lane];
     }
   }
 }
@@ -662,8 +694,8 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_
 #undef MCRT_FP32_K
   if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
-  long long blocks = (P * 32 + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
+  if (blocks > 152 * 16) blocks = 152 * 16;
   reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -143,6 +143,64 @@ def cpu_baseline(a, target_s=12.0):
                       f"{steps:.3g} steps in {dt:.1f} s"}
 
 
+def batch_extra(sp, rays=256, n=32, seed=0):
+    """32 snapshots of uneven grid sizes (32^3, 48x64x48, 96^3, 128^3), 256 rays
+    per cell, solved in one graph launch; compared with the same snapshots
+    solved one after another."""
+    import torch
+
+    from paper_1810_00188_gb300 import autotune, inputs, mcrt
+    kd, snaps = inputs.snapshot_batch(n, seed)
+    solvers, outs, items = [], [], []
+    for k, (grid, T, x) in enumerate(snaps):
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+        q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(q)
+        solvers.append(S)
+        outs.append((q, sg))
+        items.append((S.ctx, q.data_ptr(), sg.data_ptr(), k))
+    params = mcrt.Solver.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32)
+
+    def make(cfg):
+        streams, weighted = cfg
+        w = autotune.batch_weights(solvers, outs, rays_probe=64, stream=sp) if weighted else None
+        return mcrt.mcrt_batch_create(items, params, weights=w, streams=streams)
+
+    def run(b):
+        mcrt.mcrt_batch_run(b, rays, sp)
+        return mcrt.mcrt_batch_get_stats(b)["kernel_ms"]
+
+    cfgs = ((1, False), (2, False), (4, False), (n, True))
+    best, table = autotune.tune_batch(make, run, shapes=cfgs, reps=1)
+    b = make(best)
+    try:
+        mcrt.mcrt_batch_run(b, 0, sp)
+        mcrt.mcrt_batch_get_stats(b)
+        times, st = [], None
+        for k in range(3):
+            mcrt.mcrt_batch_run(b, (k + 1) * rays, sp)
+            st = mcrt.mcrt_batch_get_stats(b)
+            times.append(st["kernel_ms"])
+    finally:
+        mcrt.mcrt_batch_destroy(b)
+    seq = 0.0
+    for S, (q, sg) in zip(solvers, outs):
+        S.solve_into(S.params(rays=rays, seed=seed, ray_offset=rays, precision=mcrt.MCRT_FP32), q, sg,
+                     stream=sp)
+        seq += S.stats()["kernel_ms"]
+    for S in solvers:
+        S.close()
+    t = statistics.median(times) / 1e3
+    cells = sum(g.ncells for g, _, _ in snaps)
+    return {"workload": f"{n} snapshots {{32^3, 48x64x48, 96^3, 128^3}}, {rays} rays/cell",
+            "cells": cells, "graph_ms": t * 1e3, "rays_per_s": cells * rays / t,
+            "steps_per_s": st["steps"] / t, "launches_in_graph": st["launches"],
+            "sequential_ms": seq, "speedup_vs_sequential": seq / (t * 1e3),
+            "tuned": {"streams": best[0], "weighted": best[1]},
+            "tuning_ms": {f"{k[0]}{'w' if k[1] else ''}": v for k, v in table.items()}}
+
+
 def run_reference(a):
     """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -323,6 +381,8 @@ def main():
                 sol["value"] = value / (steps_per_launch / a.rays * nstar)
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
             result["learned_vs_plain"] = None
+            if world == 1:
+                result["batched_snapshots"] = batch_extra(sp)
         if not a.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(a)
         print(json.dumps(result), flush=True)

@@ -208,6 +208,48 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
 int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out,
                             double *sigma_out, void *cuda_stream);
 
+/* Batched snapshots (no counterpart in the paper, which solves one field per
+ * call; its DNS coupling solves one snapshot per time step, Section 5).  A batch
+ * solves many contexts -- snapshots of possibly different grid sizes, each with
+ * its k-distribution and fields set -- in one CUDA-graph launch.  Inside the
+ * graph each item is one persistent FP32 trace kernel (and its per-cell
+ * reduction); `streams` concurrent branches run the items in decreasing order of
+ * `weights` (NULL: cell counts), round-robin.  Without weights every item's
+ * kernel is a full wave of persistent CTAs, so one kernel's tail overlaps the
+ * next one's start; with weights each item gets that share of one wave (meant
+ * for streams = n: all items at once).  The solve parameters (FP32 only, whole
+ * grids; p->box, p->snapshot, p->ray_offset and p->steps_out are ignored) and the
+ * launch shape of items[0].ctx are fixed at creation. */
+typedef struct mcrt_batch mcrt_batch;
+typedef struct {
+  mcrt_ctx *ctx;           /* distinct contexts on one device                    */
+  double *q_out;           /* device, the item's whole grid (x fastest)          */
+  double *sigma_out;       /* device or NULL                                     */
+  uint32_t snapshot;       /* fourth Philox counter word of the item             */
+} mcrt_batch_item;
+
+/* Builds the batch: proposals, scratch, and the captured graph.  items[0..n-1]
+ * are the snapshots; weights (host, n values > 0, or NULL) their relative cost;
+ * streams (>= 1, clamped to n) the number of concurrent graph branches.  Items of
+ * one branch run one after another and share that branch's sample scratch (the
+ * largest item's chunk, capped by items[0].ctx's scratch_mib).  Synchronous;
+ * allocates.  Errors: MCRT_E_ARG, MCRT_E_STATE, MCRT_E_UNSUPPORTED, MCRT_E_CUDA,
+ * MCRT_E_OOM (messages on items[0].ctx). */
+int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt_solve_params *p,
+                      const double *weights, int streams, mcrt_batch **out);
+/* Replays the graph on cuda_stream with rays ray_offset .. ray_offset + N - 1 of
+ * every cell (asynchronous).  The batch owns its scratch; the items' contexts
+ * may be used for other solves between runs.  mcrt_set_fields on an item's
+ * context (same grid) between runs is picked up by the next run; its proposal is
+ * the one current in the context (valid and unbiased for any field).
+ * mcrt_set_kdist on an item's context invalidates the batch. */
+int mcrt_batch_run(mcrt_batch *b, uint64_t ray_offset, void *cuda_stream);
+/* Waits for the last run; sums the items' counters; kernel_ms is the graph's
+ * device time. */
+int mcrt_batch_get_stats(mcrt_batch *b, mcrt_solve_stats *out);
+const char *mcrt_batch_last_error(const mcrt_batch *b);
+int mcrt_batch_destroy(mcrt_batch *b);
+
 /* Releases all device memory of the context; NULL is accepted.  Waits for the
  * context's outstanding work. */
 int mcrt_destroy(mcrt_ctx *ctx);

@@ -1,0 +1,66 @@
+"""Autotuner of the FP32 solve's launch shape and of batch partitions.
+
+The knobs are the library's `mcrt_tuning` (CTAs per SM, march steps per refill
+round, sample-scratch cap) and, for batches, the share of the GPU's persistent
+CTAs given to each snapshot.  Q, sigma and the step counts are bitwise
+independent of all of them (every cell's samples are reduced in a fixed order),
+so the tuner only measures time: the library's own CUDA events around each
+solve's launches.
+"""
+from __future__ import annotations
+
+import statistics
+
+from . import mcrt
+
+SHAPES = ((2, 1), (2, 2), (3, 1), (3, 2), (4, 2))
+
+
+def time_solve(S, params, q, s, stream=0, reps=3):
+    """Median device time [ms] of `reps` solves into device buffers q, s."""
+    times = []
+    for _ in range(reps):
+        S.solve_into(params, q, s, stream=stream)
+        times.append(S.stats()["kernel_ms"])
+    return statistics.median(times)
+
+
+def tune_solver(S, params, q, s, stream=0, shapes=SHAPES, reps=3):
+    """Tries each (CTAs per SM, steps per round), keeps the fastest on S.
+    Returns (best, {shape: ms})."""
+    table = {}
+    for mb, k in shapes:
+        S.set_tuning(mb, k)
+        time_solve(S, params, q, s, stream, reps=1)  # first launch configures the variant
+        table[(mb, k)] = time_solve(S, params, q, s, stream, reps)
+    best = min(table, key=table.get)
+    S.set_tuning(*best)
+    return best, table
+
+
+def batch_weights(solvers, outs, rays_probe=16, stream=0, seed=0):
+    """Relative cost of each snapshot from a short probe solve (few rays per
+    cell): the batch gives each snapshot a share of the persistent CTAs in
+    proportion to it."""
+    w = []
+    for S, (q, s) in zip(solvers, outs):
+        p = S.params(rays=rays_probe, seed=seed, precision=mcrt.MCRT_FP32)
+        S.solve_into(p, q, s, stream=stream)
+        st = S.stats()
+        w.append(max(st["kernel_ms"], 1e-3))
+    return w
+
+
+def tune_batch(make_batch, run, shapes=SHAPES, reps=2):
+    """make_batch(shape) -> batch handle built with that launch shape;
+    run(batch) -> device ms.  Returns (best shape, {shape: ms})."""
+    table = {}
+    for shape in shapes:
+        b = make_batch(shape)
+        try:
+            run(b)
+            table[shape] = statistics.median(run(b) for _ in range(reps))
+        finally:
+            mcrt.mcrt_batch_destroy(b)
+    best = min(table, key=table.get)
+    return best, table

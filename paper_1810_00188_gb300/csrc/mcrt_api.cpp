@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -867,5 +868,308 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
          "clear step sums");
     CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
   }
+  return MCRT_OK;
+}
+
+// ---- batched snapshots in one graph launch ------------------------------------
+
+struct mcrt_batch {
+  int device = 0;
+  std::vector<mcrt_ctx *> ctxs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long *d_offset = nullptr;
+  unsigned long long h_offset = 0;
+  std::vector<void *> owned;           // per-branch sample scratch and step sums, per-item counters
+  std::vector<unsigned long long *> counters;
+  int rays = 0;
+  int launches = 0;
+  bool ran = false;
+  cudaStream_t last_stream = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int batch_fail(mcrt_batch *b, int code, const std::string &msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+void batch_release(mcrt_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t st : b->streams)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->d_offset) cudaFree(b->d_offset);
+  for (void *q : b->owned)
+    if (q) cudaFree(q);
+  cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt_solve_params *p,
+                                 const double *weights, int streams, mcrt_batch **out) {
+  if (!out) return MCRT_E_ARG;
+  *out = nullptr;
+  if (!items || n < 1 || !p || streams < 1) return MCRT_E_ARG;
+  if (streams > n) streams = n;
+  if (p->precision != MCRT_FP32 || p->rays_per_cell < 1 || p->max_steps < 1 ||
+      !(p->tol > 0.0 && p->tol < 1.0) || (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER) ||
+      (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL))
+    return MCRT_E_ARG;
+  const int dev = items[0].ctx ? items[0].ctx->grid.device : -1;
+  for (int k = 0; k < n; ++k) {
+    mcrt_ctx *c = items[k].ctx;
+    if (!c || !items[k].q_out) return MCRT_E_ARG;
+    if (c->grid.device != dev) return fail(c, MCRT_E_ARG, "batch items on different devices");
+    if (!c->have_kdist || !c->have_fields) return fail(c, MCRT_E_STATE, "set kdist and fields first");
+    if (c->nT > 512) return fail(c, MCRT_E_UNSUPPORTED, "the FP32 kernel supports at most 512 T nodes");
+    if (p->proposal == MCRT_PROPOSAL_CELL && !c->have_cell_prop)
+      return fail(c, MCRT_E_STATE, "no cell proposal");
+    if (weights && !(weights[k] > 0.0) ) return fail(c, MCRT_E_ARG, "batch weights must be > 0");
+    for (int j = 0; j < k; ++j)
+      if (items[j].ctx == c) return fail(c, MCRT_E_ARG, "a context appears twice in the batch");
+  }
+  mcrt_batch *b = new (std::nothrow) mcrt_batch();
+  if (!b) return MCRT_E_OOM;
+  b->device = dev;
+  b->rays = p->rays_per_cell;
+  DeviceGuard dg(dev);
+  auto bail = [&](int code, cudaError_t e, const char *where) {
+    cudaGetLastError();
+    mcrt_ctx *c0 = items[0].ctx;
+    fail(c0, code, std::string(where) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : ""));
+    batch_release(b);
+    delete b;
+    return code;
+  };
+#define BK(call, where)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return bail(e_ == cudaErrorMemoryAllocation ? MCRT_E_OOM : MCRT_E_CUDA, e_, where); \
+  } while (0)
+  if (!dg.ok) return bail(MCRT_E_CUDA, cudaSuccess, "cudaSetDevice");
+  BK(cudaMalloc(&b->d_offset, sizeof(unsigned long long)), "alloc offset");
+  BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
+  BK(cudaEventCreate(&b->ev0), "event");
+  BK(cudaEventCreate(&b->ev1), "event");
+  // per-item preparation: proposal, scratch, launch arguments
+  std::vector<mcrt::TraceArgs> args(n);
+  std::vector<long long> P(n), Pc(n);
+  double wsum = 0.0;
+  std::vector<double> w(n);
+  for (int k = 0; k < n; ++k) {
+    mcrt_ctx *c = items[k].ctx;
+    b->ctxs.push_back(c);
+    const double Tm = proposal_T_max(c);
+    if (!c->prop_valid || c->prop_T_max != Tm) {
+      const int rc = build_plain_proposal(c, Tm, nullptr);
+      if (rc != MCRT_OK) return bail(rc, cudaSuccess, "proposal");
+    }
+    const mcrt_grid_desc &g = c->grid;
+    mcrt::TraceArgs &a = args[k];
+    std::memset(&a, 0, sizeof(a));
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.dx = g.lx / g.nx;
+    a.dy = g.ly / g.ny;
+    a.dz = g.lz / g.nz;
+    a.nb = c->nb;
+    a.ng = c->ng;
+    a.nT = c->nT;
+    a.T0 = c->T0;
+    a.inv_dT = 1.0 / c->dT;
+    a.inv_xref = 1.0 / c->x_ref;
+    a.eps_wall[0] = g.eps_wall[0];
+    a.eps_wall[1] = g.eps_wall[1];
+    a.reflect = g.reflect;
+    a.field32 = (const float2 *)c->field32.p;
+    a.fpos32 = (const uint2 *)c->fpos32.p;
+    a.ktab32 = (const float2 *)c->ktab32.p;
+    a.btab32 = (const float2 *)c->btab32.p;
+    a.bwall32 = (const float *)c->bwall32.p;
+    a.w_g = (const double *)c->wg.p;
+    a.w_g32 = (const float *)c->wg32.p;
+    a.wgt32 = (const float *)c->wgt32.p;
+    a.cn = (const unsigned long long *)c->cn.p;
+    a.cg = (const unsigned long long *)c->cg.p;
+    a.counts_in_smem = (size_t)(c->nb + c->nb * c->ng) * 8 <= 48 * 1024;
+    a.guide = (const unsigned short *)c->guide.p;
+    if (p->proposal == MCRT_PROPOSAL_CELL) {
+      a.cell_cn = (const unsigned long long *)c->cell_cn.p;
+      a.cell_cg = (const unsigned long long *)c->cell_cg.p;
+      a.cell_hemi = (const unsigned int *)c->cell_hemi.p;
+    }
+    a.rays = p->rays_per_cell;
+    a.max_steps = p->max_steps;
+    a.origin = p->origin;
+    a.tol = p->tol;
+    a.key0 = (unsigned)(p->seed & 0xffffffffu);
+    a.key1 = (unsigned)(p->seed >> 32);
+    a.snapshot = items[k].snapshot;
+    a.ray_offset_dev = b->d_offset;
+    a.bnx = g.nx;
+    a.bny = g.ny;
+    a.bnz = g.nz;
+    a.ncells_box = (long long)g.nx * g.ny * g.nz;
+    a.q = items[k].q_out;
+    a.sigma = items[k].sigma_out;
+    P[k] = mcrt::fp32_bricks_positions(a.bnx, a.bny, a.bnz);
+    long long pc = ((long long)c->scratch_mib << 20) / ((long long)p->rays_per_cell * (long long)sizeof(float));
+    if (pc < 1) pc = 1;
+    if (pc > P[k]) pc = P[k];
+    Pc[k] = pc;
+    void *ct = nullptr;
+    BK(cudaMalloc(&ct, 6 * sizeof(unsigned long long)), "alloc counters");
+    b->owned.push_back(ct);
+    a.counters = (unsigned long long *)ct;
+    b->counters.push_back((unsigned long long *)ct);
+    w[k] = weights ? weights[k] : (double)a.ncells_box;
+    wsum += w[k];
+  }
+  // persistent CTAs: with weights, one wave shared by the items in proportion to
+  // their work (all items run at once); without, each item's kernel is a full
+  // wave and `streams` branches run items in decreasing order of work, so one
+  // kernel's tail overlaps the next kernel's start
+  mcrt_ctx *c0 = items[0].ctx;
+  int bps = 0, nsm = 0;
+  BK(mcrt::prepare_trace_fp32(c0->min_blocks, c0->steps_per_round, args[0].nb, args[0].ng,
+                              args[0].counts_in_smem, &bps, &nsm),
+     "prepare launch");
+  const long long total = (long long)bps * nsm;
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  b->streams.assign(streams, nullptr);
+  b->joins.assign(streams, nullptr);
+  for (int k = 0; k < streams; ++k) {
+    BK(cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking), "stream");
+    BK(cudaEventCreateWithFlags(&b->joins[k], cudaEventDisableTiming), "event");
+  }
+  for (int k = 0; k < n; ++k) {
+    long long blocks = weights ? (long long)((double)total * w[k] / wsum + 0.5) : total;
+    args[k].grid_blocks = (int)(blocks < 1 ? 1 : blocks);
+  }
+  // items of one branch run one after another, so they share its scratch
+  for (int j = 0; j < streams; ++j) {
+    long long pmax = 0;
+    for (int r = j; r < n; r += streams) pmax = Pc[order[r]] > pmax ? Pc[order[r]] : pmax;
+    void *yb = nullptr, *sa = nullptr;
+    BK(cudaMalloc(&yb, (size_t)pmax * p->rays_per_cell * sizeof(float)), "alloc sample scratch");
+    b->owned.push_back(yb);
+    BK(cudaMalloc(&sa, (size_t)pmax * sizeof(unsigned long long)), "alloc step scratch");
+    b->owned.push_back(sa);
+    for (int r = j; r < n; r += streams) {
+      args[order[r]].ybuf = (float *)yb;
+      args[order[r]].step_acc = (unsigned long long *)sa;
+    }
+  }
+  BK(cudaDeviceSynchronize(), "sync");
+  // capture: fork -> branch j runs its items [clear counters, chunks of trace + reduce] -> join
+  cudaStream_t s0 = b->streams[0];
+  BK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t ce = cudaEventRecord(b->fork, s0);
+  for (int j = 1; j < streams && ce == cudaSuccess; ++j) ce = cudaStreamWaitEvent(b->streams[j], b->fork, 0);
+  int launches = 0;
+  for (int r = 0; r < n && ce == cudaSuccess; ++r) {
+    const int k = order[r];
+    cudaStream_t sk = b->streams[r % streams];
+    ce = cudaMemsetAsync(args[k].counters, 0, 6 * sizeof(unsigned long long), sk);
+    for (long long p0 = 0; p0 < P[k] && ce == cudaSuccess; p0 += Pc[k]) {
+      args[k].chunk_p0 = p0;
+      args[k].chunk_p1 = p0 + Pc[k] < P[k] ? p0 + Pc[k] : P[k];
+      ce = mcrt::launch_trace_fp32(args[k], c0->min_blocks, c0->steps_per_round, sk);
+      launches += 2;
+    }
+  }
+  for (int j = 1; j < streams && ce == cudaSuccess; ++j) {
+    ce = cudaEventRecord(b->joins[j], b->streams[j]);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s0, b->joins[j], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(s0, &graph);
+  b->graph = graph;
+  if (ce != cudaSuccess) return bail(MCRT_E_CUDA, ce, "capture");
+  if (ee != cudaSuccess) return bail(MCRT_E_CUDA, ee, "end capture");
+  BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph");
+  b->launches = launches;
+#undef BK
+  *out = b;
+  return MCRT_OK;
+}
+
+extern "C" int mcrt_batch_run(mcrt_batch *b, uint64_t ray_offset, void *stream) {
+  if (!b) return MCRT_E_ARG;
+  if ((unsigned long long)ray_offset + (unsigned long long)b->rays > (1ull << 32))
+    return batch_fail(b, MCRT_E_ARG, "ray indices beyond 2^32");
+  DeviceGuard dg(b->device);
+  if (!dg.ok) return batch_fail(b, MCRT_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  b->h_offset = ray_offset;  // pageable source: staged before cudaMemcpyAsync returns
+  cudaError_t e = cudaMemcpyAsync(b->d_offset, &b->h_offset, sizeof(b->h_offset),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev0, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev1, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return batch_fail(b, MCRT_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  b->ran = true;
+  b->last_stream = s;
+  return MCRT_OK;
+}
+
+extern "C" int mcrt_batch_get_stats(mcrt_batch *b, mcrt_solve_stats *out) {
+  if (!b || !out) return MCRT_E_ARG;
+  if (!b->ran) return batch_fail(b, MCRT_E_STATE, "no run yet");
+  DeviceGuard dg(b->device);
+  if (!dg.ok) return batch_fail(b, MCRT_E_CUDA, "cudaSetDevice");
+  std::memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaEventSynchronize(b->ev1);
+  for (unsigned long long *cp : b->counters) {
+    unsigned long long cnt[6];
+    if (e == cudaSuccess) e = cudaMemcpy(cnt, cp, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    if (cnt[5] != 0) return batch_fail(b, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
+    out->steps += cnt[0];
+    out->capped += cnt[1];
+    out->wall_hits += cnt[2];
+    out->rays += cnt[3];
+    if (cnt[4] > out->max_ray_steps) out->max_ray_steps = cnt[4];
+  }
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return batch_fail(b, MCRT_E_CUDA, std::string("batch stats: ") + cudaGetErrorString(e));
+  }
+  out->kernel_ms = ms;
+  out->launches = b->launches;
+  return MCRT_OK;
+}
+
+extern "C" const char *mcrt_batch_last_error(const mcrt_batch *b) { return b ? b->err.c_str() : ""; }
+
+extern "C" int mcrt_batch_destroy(mcrt_batch *b) {
+  if (!b) return MCRT_OK;
+  {
+    DeviceGuard dg(b->device);
+    if (b->ran && b->ev1) cudaEventSynchronize(b->ev1);
+    batch_release(b);
+  }
+  delete b;
   return MCRT_OK;
 }

@@ -42,6 +42,10 @@ struct TraceArgs {
   long long chunk_p0, chunk_p1;
   float *ybuf;
   unsigned long long *step_acc;
+  // batched runs: ray_offset read from device memory (set before each graph
+  // replay) when non-null; persistent grid size override (0: one full wave)
+  const unsigned long long *ray_offset_dev;
+  int grid_blocks;
   // solve
   int rays, max_steps, origin;
   double tol;
@@ -65,6 +69,10 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);
+// Sets the launch attributes of the chosen FP32 variant and returns its
+// resident CTAs per SM (call before stream capture).
+cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
+                               int *blocks_per_sm, int *num_sms);
 int fp32_brick_volume();
 int fp32_guide_size();
 

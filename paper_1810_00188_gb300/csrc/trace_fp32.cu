@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
   const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
   float *__restrict__ Ybuf = a.ybuf;
+  const unsigned long long ray_off = a.ray_offset_dev ? *a.ray_offset_dev : a.ray_offset;
 
   // warp-uniform: the emitting cell being initialised and its next ray
   int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         const int rr = c_r + lane;
         if (rr < N) {
           const unsigned cell = (unsigned)c_lin;
-          const unsigned rayid = (unsigned)(a.ray_offset + (unsigned long long)rr);
+          const unsigned rayid = (unsigned)(ray_off + (unsigned long long)rr);
           const uint2 fi = __ldg(field + cell);
           unsigned it_i;
           float fr_i;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         ix = Dv.y;
         iy = Dv.z;
         iz = Dv.w;
-        r = ray - (unsigned)a.ray_offset;
+        r = ray - (unsigned)ray_off;
         tnx = t0x;
         tny = t0y;
         tnz = t0z;
@@ -626,8 +627,7 @@ __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
 }
 
 template <int MINB, int KSTEPS>
-cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
-  // per-device launch shape, computed once per device and shared-memory size
+cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
   static bool init_done = false;
   if (!init_done) {
@@ -650,9 +650,20 @@ cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
     configured_smem[dev] = (int)smem;
   }
+  *bps = blocks_per_sm[dev];
+  *nsm = num_sms[dev];
+  return cudaSuccess;
+}
+
+template <int MINB, int KSTEPS>
+cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
+  // per-device launch shape, computed once per device and shared-memory size
+  int bps = 0, nsm = 0;
+  cudaError_t e = configure_variant<MINB, KSTEPS>(smem, &bps, &nsm);
+  if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const long long need = (P + WARPS - 1) / WARPS;
-  long long blocks = (long long)num_sms[dev] * blocks_per_sm[dev];
+  long long blocks = a.grid_blocks > 0 ? a.grid_blocks : (long long)nsm * bps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   trace_fp32_kernel<MINB, KSTEPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
@@ -671,13 +682,34 @@ int fp32_brick_volume() { return BRICK * BRICK * BRICK; }
 
 int fp32_guide_size() { return GUIDE; }
 
+static size_t fp32_smem_bytes(int nb, int ng, int counts_in_smem) {
+  return WARPS * sizeof(WarpRing) +
+         (counts_in_smem ? sizeof(unsigned long long) * (size_t)(nb + nb * ng) + sizeof(unsigned short) * GUIDE
+                         : 0);
+}
+
+cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
+                               int *blocks_per_sm, int *num_sms) {
+  const size_t smem = fp32_smem_bytes(nb, ng, counts_in_smem);
+#define MCRT_PREP_K(MB)                                                                  \
+  switch (steps_per_round) {                                                             \
+    case 2: return configure_variant<MB, 2>(smem, blocks_per_sm, num_sms);               \
+    case 4: return configure_variant<MB, 4>(smem, blocks_per_sm, num_sms);               \
+    default: return configure_variant<MB, 1>(smem, blocks_per_sm, num_sms);              \
+  }
+  switch (min_blocks) {
+    case 1: MCRT_PREP_K(1)
+    case 3: MCRT_PREP_K(3)
+    case 4: MCRT_PREP_K(4)
+    default: MCRT_PREP_K(2)
+  }
+#undef MCRT_PREP_K
+}
+
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s) {
   if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
-  const size_t smem = WARPS * sizeof(WarpRing) +
-                      (a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) +
-                                              sizeof(unsigned short) * GUIDE
-                                        : 0);
+  const size_t smem = fp32_smem_bytes(a.nb, a.ng, a.counts_in_smem);
   cudaError_t e;
 #define MCRT_FP32_K(MB)                                              \
   switch (steps_per_round) {                                         \

@@ -228,3 +228,23 @@ def nongrey_channel(nx: int = 64, ny: int = 64, nz: int = 64, seed: int = 0,
     kd = make_kdist(kdist_seed)
     T, x = channel_fields(grid, seed, x_mode=x_mode)
     return grid, kd, T, x
+
+
+SNAPSHOT_SHAPES = ((32, 32, 32), (48, 64, 48), (96, 96, 96), (128, 128, 128))
+
+
+def snapshot_batch(n: int = 32, seed: int = 0, shapes=SNAPSHOT_SHAPES, x_mode: str = "field"):
+    """Independent channel snapshots of uneven grid sizes: shape k drawn from
+    `shapes` with default_rng(seed), fields seeded with seed + 1 + k (x_H2O a
+    random field by default), black walls at 500 / 1000 K, one shared 40 x 8
+    k-distribution.  Returns (kdist, [(grid, T, x), ...])."""
+    rng = np.random.default_rng(seed)
+    picks = rng.integers(0, len(shapes), n)
+    kd = make_kdist(0)
+    snaps = []
+    for k, i in enumerate(picks):
+        nx, ny, nz = shapes[int(i)]
+        grid = Grid(nx, ny, nz, 4.0 * math.pi, 2.0, 2.0 * math.pi, T_wall=(500.0, 1000.0))
+        T, x = channel_fields(grid, seed + 1 + k, x_mode=x_mode)
+        snaps.append((grid, T, x))
+    return kd, snaps

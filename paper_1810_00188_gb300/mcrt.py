@@ -60,6 +60,11 @@ class mcrt_tuning(C.Structure):
                 ("scratch_mib", C.c_int)]
 
 
+class mcrt_batch_item(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("q_out", C.c_void_p), ("sigma_out", C.c_void_p),
+                ("snapshot", C.c_uint32)]
+
+
 class mcrt_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("rays", C.c_uint64), ("capped", C.c_uint64),
                 ("wall_hits", C.c_uint64), ("max_ray_steps", C.c_uint64), ("T_max", C.c_double),
@@ -71,7 +76,9 @@ _lib = None
 _lock = threading.Lock()
 EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_proposal",
            "mcrt_solve_qrad", "mcrt_get_stats", "mcrt_destroy", "mcrt_status_string",
-           "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning", "mcrt_solve_qrad_noalloc")
+           "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning", "mcrt_solve_qrad_noalloc",
+           "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_get_stats", "mcrt_batch_last_error",
+           "mcrt_batch_destroy")
 
 
 def library_path() -> str:
@@ -105,8 +112,16 @@ def load(build_if_missing: bool = True):
         L.mcrt_status_string.restype = C.c_char_p
         L.mcrt_last_error.argtypes = [vp]
         L.mcrt_last_error.restype = C.c_char_p
+        L.mcrt_batch_create.argtypes = [C.POINTER(mcrt_batch_item), C.c_int,
+                                        C.POINTER(mcrt_solve_params), C.POINTER(C.c_double),
+                                        C.c_int, C.POINTER(vp)]
+        L.mcrt_batch_run.argtypes = [vp, C.c_uint64, vp]
+        L.mcrt_batch_get_stats.argtypes = [vp, C.POINTER(mcrt_solve_stats)]
+        L.mcrt_batch_last_error.argtypes = [vp]
+        L.mcrt_batch_last_error.restype = C.c_char_p
+        L.mcrt_batch_destroy.argtypes = [vp]
         for f in EXPORTS:
-            if f not in ("mcrt_status_string", "mcrt_last_error"):
+            if f not in ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error"):
                 getattr(L, f).restype = C.c_int
         _lib = L
         return _lib
@@ -146,6 +161,43 @@ def mcrt_solve_qrad_noalloc(ctx, params: mcrt_solve_params, q_ptr, sigma_ptr, st
     """The allocation-free solve: FP32, device outputs, scratch in a static 64 MiB
     device array (see include/mcrt.h)."""
     _check(load().mcrt_solve_qrad_noalloc(ctx, C.byref(params), q_ptr, sigma_ptr, stream), ctx)
+
+
+def mcrt_batch_create(items, params: mcrt_solve_params, weights=None, streams: int = 2):
+    """items: list of (ctx, q_ptr, sigma_ptr or None, snapshot)."""
+    arr = (mcrt_batch_item * len(items))()
+    for k, (ctx, q, s, snap) in enumerate(items):
+        arr[k].ctx = ctx.value if hasattr(ctx, "value") else ctx
+        arr[k].q_out = q.value if hasattr(q, "value") else q
+        arr[k].sigma_out = None if s is None else (s.value if hasattr(s, "value") else s)
+        arr[k].snapshot = snap
+    w = None
+    if weights is not None:
+        w = (C.c_double * len(items))(*[float(v) for v in weights])
+    h = C.c_void_p()
+    rc = load().mcrt_batch_create(arr, len(items), C.byref(params), w, streams, C.byref(h))
+    if rc != MCRT_OK:
+        raise McrtError(rc, load().mcrt_last_error(arr[0].ctx).decode() if len(items) else "")
+    return h
+
+
+def mcrt_batch_run(batch, ray_offset: int = 0, stream: int = 0):
+    rc = load().mcrt_batch_run(batch, ray_offset, stream)
+    if rc != MCRT_OK:
+        raise McrtError(rc, load().mcrt_batch_last_error(batch).decode())
+
+
+def mcrt_batch_get_stats(batch) -> dict:
+    st = mcrt_solve_stats()
+    rc = load().mcrt_batch_get_stats(batch, C.byref(st))
+    if rc != MCRT_OK:
+        raise McrtError(rc, load().mcrt_batch_last_error(batch).decode())
+    return {f: getattr(st, f) for f, _ in mcrt_solve_stats._fields_}
+
+
+def mcrt_batch_destroy(batch):
+    if batch:
+        load().mcrt_batch_destroy(batch)
 
 
 def mcrt_get_stats(ctx) -> dict:

@@ -1,0 +1,99 @@
+"""Batched snapshots in one graph launch, and the autotuner.
+
+Each batch item must equal the regular FP32 solve of the same context with the
+same snapshot and ray offset, bit for bit (results do not depend on the launch
+shape), on two consecutive runs with different ray offsets.
+"""
+import numpy as np
+import pytest
+
+from paper_1810_00188_gb300 import autotune, inputs, mcrt
+
+pytestmark = pytest.mark.gpu
+
+
+def _snapshots():
+    kd = inputs.make_kdist(0)
+    shapes = [(12, 16, 10), (20, 24, 8), (7, 9, 5)]
+    snaps = []
+    for k, (nx, ny, nz) in enumerate(shapes):
+        grid = inputs.Grid(nx, ny, nz, 4.0, 2.0, 2.0, eps_wall=(0.8, 1.0), T_wall=(500.0, 1000.0))
+        T, x = inputs.channel_fields(grid, 40 + k, x_mode="field")
+        snaps.append((grid, T, x))
+    return kd, snaps
+
+
+def test_batch_matches_single_solves_bitwise_on_two_runs():
+    import torch
+    kd, snaps = _snapshots()
+    solvers, outs, items = [], [], []
+    for k, (grid, T, x) in enumerate(snaps):
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+        q = torch.full(grid.shape, float("nan"), dtype=torch.float64, device="cuda")
+        s = torch.full_like(q, float("nan"))
+        solvers.append(S)
+        outs.append((q, s))
+        items.append((S.ctx, q.data_ptr(), s.data_ptr(), 10 + k))
+    rays = 300
+    params = mcrt.Solver.params(rays=rays, seed=7, precision=mcrt.MCRT_FP32)
+    stream = torch.cuda.current_stream().cuda_stream
+    for weights, streams, offsets in (([1.0, 2.0, 0.5], 3, (0, 5000)), (None, 2, (700,)), (None, 1, (0,))):
+        b = mcrt.mcrt_batch_create(items, params, weights=weights, streams=streams)
+        try:
+            _check_runs(b, snaps, solvers, outs, rays, stream, offsets)
+        finally:
+            mcrt.mcrt_batch_destroy(b)
+    for S in solvers:
+        S.close()
+
+
+def _check_runs(b, snaps, solvers, outs, rays, stream, offsets):
+    if True:
+        for offset in offsets:
+            mcrt.mcrt_batch_run(b, offset, stream)
+            st = mcrt.mcrt_batch_get_stats(b)
+            assert st["rays"] == sum(g.ncells for g, _, _ in snaps) * rays
+            assert st["launches"] >= 2 * len(snaps)
+            for k, (S, (q, s)) in enumerate(zip(solvers, outs)):
+                qr, sr = S.solve(rays=rays, seed=7, snapshot=10 + k, ray_offset=offset,
+                                 precision=mcrt.MCRT_FP32)
+                assert np.array_equal(q.cpu().numpy(), qr), (offset, k)
+                assert np.array_equal(s.cpu().numpy(), sr), (offset, k)
+
+
+def test_batch_rejects_bad_items():
+    import torch
+    kd, snaps = _snapshots()
+    grid, T, x = snaps[0]
+    S = mcrt.Solver(grid, kd)
+    q = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    params = mcrt.Solver.params(rays=8, precision=mcrt.MCRT_FP32)
+    with pytest.raises(mcrt.McrtError) as e:  # no fields yet
+        mcrt.mcrt_batch_create([(S.ctx, q.data_ptr(), None, 0)], params)
+    assert e.value.status == mcrt.MCRT_E_STATE
+    S.set_fields(T, x)
+    with pytest.raises(mcrt.McrtError):  # same context twice
+        mcrt.mcrt_batch_create([(S.ctx, q.data_ptr(), None, 0), (S.ctx, q.data_ptr(), None, 1)], params)
+    with pytest.raises(mcrt.McrtError):  # FP64 is not batched
+        mcrt.mcrt_batch_create([(S.ctx, q.data_ptr(), None, 0)],
+                               mcrt.Solver.params(rays=8, precision=mcrt.MCRT_FP64))
+    S.close()
+
+
+def test_autotuner_picks_a_shape_without_changing_results():
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(24, 24, 24, seed=2)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    q = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    s = torch.zeros_like(q)
+    params = S.params(rays=200, seed=3, precision=mcrt.MCRT_FP32)
+    S.solve_into(params, q, s)
+    before = q.cpu().numpy().copy()
+    best, table = autotune.tune_solver(S, params, q, s, reps=2)
+    assert best in table and all(v > 0 for v in table.values())
+    assert S.tuning()["min_blocks_per_sm"] == best[0] and S.tuning()["steps_per_round"] == best[1]
+    S.solve_into(params, q, s)
+    assert np.array_equal(q.cpu().numpy(), before)
+    S.close()

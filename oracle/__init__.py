@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mcrt_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "learn_oracle.c")]
 _LIB = os.path.join(_HERE, "_build", "libmcrt_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -28,10 +29,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (IEEE FP64, no FMA contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mcrt_oracle.h"))):
+            [os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(os.path.join(_HERE, "mcrt_oracle.h"))]):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-pthread", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -52,7 +53,8 @@ class Params(C.Structure):
                 ("snapshot", C.c_uint32), ("tol", C.c_double), ("max_steps", C.c_int),
                 ("origin", C.c_int), ("use_box", C.c_int), ("box", C.c_int * 6),
                 ("nthreads", C.c_int), ("cell_cn", C.POINTER(C.c_uint64)),
-                ("cell_cg", C.POINTER(C.c_uint64)), ("cell_hemi", C.POINTER(C.c_uint32))]
+                ("cell_cg", C.POINTER(C.c_uint64)), ("cell_hemi", C.POINTER(C.c_uint32)),
+                ("tally", C.POINTER(C.c_double))]
 
 
 class CellSums(C.Structure):
@@ -95,6 +97,16 @@ def lib():
             L.orc_quadrature.argtypes = [C.POINTER(Problem), dp, dp, C.c_int, C.c_int, dp, dp,
                                          C.c_int, C.c_int, C.c_double, C.c_int,
                                          C.POINTER(C.c_int), C.c_int, C.c_int, dp]
+            i64 = C.c_int64
+            L.orc_features.argtypes = [C.POINTER(Problem), C.POINTER(C.c_int32), i64, C.c_double, dp]
+            L.orc_mlp_nparams.argtypes = [C.c_int]
+            L.orc_mlp_nparams.restype = i64
+            L.orc_mlp_forward.argtypes = [dp, C.c_int, dp, dp, dp, i64, dp, C.c_int, C.c_double, dp]
+            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, i64, C.c_double, dp, dp]
+            L.orc_adam.argtypes = [dp, dp, dp, dp, i64, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_int]
+            L.orc_learned_counts.argtypes = [dp, C.c_int, C.c_int, C.c_double, up, up,
+                                             C.POINTER(C.c_uint32)]
             _lib = L
     return _lib
 
@@ -213,14 +225,17 @@ def _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthre
 
 
 def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4,
-          max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None):
+          max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, tally=False):
     """Per-cell ERMC estimate over the box (whole grid when box is None).
 
     Returns a dict of arrays shaped [bnz, bny, bnx]: q (Q_i, W/m^3), sigma
     (standard error of q), scale (S_i = mean of w sum|terms|), q_wall and
     sigma_wall (the wall-exchange part), steps and capped counts, and the raw
     sums.  ``proposal`` = (cell_cn [nc, nb], cell_cg [nc, nb, ng], cell_hemi
-    [nc]) overrides the plain T_max proposal per emitting cell.
+    [nc]) overrides the plain T_max proposal per emitting cell.  With
+    ``tally`` the result also holds "tally" [bnz, bny, bnx, nb * ng, 2]: per
+    spectral point and hemisphere (0 upward), (1/N) sum of Y^2 p(n,g) p(h) over
+    the rays that drew them.
     """
     P = make_problem(grid, kd, T, x)
     S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthreads)
@@ -237,6 +252,9 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
         S.cell_cn = cn.ctypes.data_as(C.POINTER(C.c_uint64))
         S.cell_cg = cg.ctypes.data_as(C.POINTER(C.c_uint64))
         S.cell_hemi = hemi.ctypes.data_as(C.POINTER(C.c_uint32))
+    if tally:
+        tl = np.zeros((nc, kd.n_bands * kd.n_g, 2))
+        S.tally = _dp(tl)
     out = {k: np.zeros(nc) for k in ("sum_y", "sum_y2", "sum_abs", "sum_wall", "sum_wall2")}
     out["steps"] = np.zeros(nc, dtype=np.uint64)
     out["capped"] = np.zeros(nc, dtype=np.uint64)
@@ -250,6 +268,8 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
         raise ValueError(f"orc_solve failed: {rc}")
     N = float(rays)
     res = {k: v.reshape(shape) for k, v in out.items()}
+    if tally:
+        res["tally"] = tl.reshape(shape + (kd.n_bands * kd.n_g, 2))
     res["q"] = res["sum_y"] / N
     res["scale"] = res["sum_abs"] / N
     res["q_wall"] = res["sum_wall"] / N
@@ -310,3 +330,81 @@ def quadrature(grid, kd, T, x=None, cells=None, nmu_panels=32, nmu_per_panel=4, 
     if rc != 0:
         raise ValueError(f"orc_quadrature failed: {rc}")
     return q
+
+
+# ---- learned proposal (see learn_oracle.c) ----------------------------------
+
+NFEAT, HIDDEN = 12, 64
+
+
+def features(grid, kd, T, x=None, cells=None, T_max=None):
+    """The 12 local features [n, 12] of the listed cells (whole grid if None);
+    T_max defaults to the plain proposal's."""
+    P = make_problem(grid, kd, T, x)
+    if T_max is None:
+        T_max = plain_proposal(grid, kd, T, x)[2]
+    cells = np.arange(grid.ncells, dtype=np.int32) if cells is None else np.asarray(cells)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros((cells.size, NFEAT))
+    rc = lib().orc_features(C.byref(P), cells.ctypes.data_as(C.POINTER(C.c_int32)), cells.size,
+                            float(T_max), _dp(out))
+    if rc != 0:
+        raise ValueError("bad cell index")
+    return out
+
+
+def mlp_nparams(K):
+    return int(lib().orc_mlp_nparams(int(K)))
+
+
+def mlp_forward(theta, K, fmean, finv, feat, p0, mix=0.1):
+    """Mixed proposal probabilities [n, K + 2] (spectral points, then up, down).
+    p0 is [K] (shared) or [n, K]."""
+    theta, fmean, finv = _f64(theta), _f64(fmean), _f64(finv)
+    feat = _f64(feat).reshape(-1, NFEAT)
+    p0 = _f64(p0)
+    stride = 0 if p0.ndim == 1 else K
+    q = np.zeros((feat.shape[0], K + 2))
+    rc = lib().orc_mlp_forward(_dp(theta), K, _dp(fmean), _dp(finv), _dp(feat), feat.shape[0],
+                               _dp(p0), stride, float(mix), _dp(q))
+    if rc != 0:
+        raise ValueError("orc_mlp_forward failed")
+    return q
+
+
+def mlp_loss_grad(theta, K, fmean, finv, feat, m, p0, mix=0.1):
+    """(mean second-moment ratio loss, gradient [nparams]); m [n, K, 2], p0 [n, K]."""
+    theta, fmean, finv = _f64(theta), _f64(fmean), _f64(finv)
+    feat = _f64(feat).reshape(-1, NFEAT)
+    n = feat.shape[0]
+    m = _f64(m).reshape(n, K, 2)
+    p0 = _f64(p0).reshape(n, K)
+    grad = np.zeros(mlp_nparams(K))
+    loss = C.c_double()
+    rc = lib().orc_mlp_loss_grad(_dp(theta), K, _dp(fmean), _dp(finv), _dp(feat), _dp(m), _dp(p0),
+                                 n, float(mix), C.byref(loss), _dp(grad))
+    if rc != 0:
+        raise ValueError("orc_mlp_loss_grad failed")
+    return loss.value, grad
+
+
+def adam(theta, grad, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on FP64 copies; returns (theta, m1, m2)."""
+    theta, grad, m1, m2 = (np.array(a, dtype=np.float64) for a in (theta, grad, m1, m2))
+    lib().orc_adam(_dp(theta), _dp(grad), _dp(m1), _dp(m2), theta.size, lr, beta1, beta2, eps, int(t))
+    return theta, m1, m2
+
+
+def learned_counts(q, nb, ng, q_up):
+    """Integer proposal (cn [nb], cg [nb, ng], hemi) of one cell from its
+    probabilities q [nb * ng] and q_up."""
+    q = _f64(q).reshape(-1)
+    cn = np.zeros(nb, dtype=np.uint64)
+    cg = np.zeros(nb * ng, dtype=np.uint64)
+    hemi = C.c_uint32()
+    up = C.POINTER(C.c_uint64)
+    rc = lib().orc_learned_counts(_dp(q), nb, ng, float(q_up), cn.ctypes.data_as(up),
+                                  cg.ctypes.data_as(up), C.byref(hemi))
+    if rc != 0:
+        raise ValueError("orc_learned_counts failed")
+    return cn, cg.reshape(nb, ng), hemi.value

@@ -349,6 +349,9 @@ int orc_trace_ray(const orc_problem *P, const orc_ray_in *in, orc_ray_out *out) 
 
 typedef struct {
   int n, g;
+  int h;           /* 0: upward hemisphere (d_y > 0), 1: downward */
+  double p_ng;     /* p(n,g) the ray was drawn with */
+  double p_h;      /* probability of its hemisphere */
   double w;        /* w_g / (p(n,g) q(Omega)) */
   double frac[3];
   double dir[3];
@@ -367,10 +370,13 @@ static void init_ray(const orc_problem *P, const orc_params *S, const uint64_t *
   if (m0 < hemi) {
     mu = 1.0 - ((double)m0 + 0.5) / (double)hemi;
     ph = (double)hemi * 0x1p-23;
+    R->h = 0;
   } else {
     mu = -(((double)(m0 - hemi)) + 0.5) / (double)(8388608u - hemi);
     ph = (double)(8388608u - hemi) * 0x1p-23;
+    R->h = 1;
   }
+  R->p_h = ph;
   const double phi = 2.0 * M_PI * orc_uniform(u[1]);
   const double s = sqrt(fmax(0.0, 1.0 - mu * mu));
   R->dir[0] = s * cos(phi);
@@ -382,6 +388,7 @@ static void init_ray(const orc_problem *P, const orc_params *S, const uint64_t *
   R->g = pick(cg + (size_t)R->n * ng, ng, u[3]);
   const double p = ((double)count_of(cn, R->n) * 0x1p-32) *
                    ((double)count_of(cg + (size_t)R->n * ng, R->g) * 0x1p-32);
+  R->p_ng = p;
   R->w = (P->w_g[R->g] / p) * (2.0 * M_PI / ph);
   if (S->origin == 1) {
     R->frac[0] = R->frac[1] = R->frac[2] = 0.5;
@@ -435,6 +442,9 @@ static void solve_cell(solve_job *J, long b, xch_acc *xa) {
     trace_core(P, R.n, R.g, cell0, R.frac, R.dir, S->tol, S->max_steps, S->seed, cellid, ray,
                S->snapshot, &o, xa);
     const double Y = R.w * o.X;
+    if (S->tally)
+      S->tally[(size_t)b * nb * ng * 2 + ((size_t)R.n * ng + R.g) * 2 + R.h] +=
+          Y * Y * R.p_ng * R.p_h / (double)S->rays_per_cell;
     sy += Y;
     sy2 += Y * Y;
     sa += R.w * o.abs_terms;

@@ -47,6 +47,13 @@ typedef struct {
   const uint64_t *cell_cn;   /* [ncells_box][n_bands] cumulative counts of 2^32   */
   const uint64_t *cell_cg;   /* [ncells_box][n_bands][n_g]                        */
   const uint32_t *cell_hemi; /* [ncells_box] upward-hemisphere count of 2^23      */
+  /* Optional second-moment tallies per emitting cell, spectral point and
+   * hemisphere (NULL: none): tally[b][(n n_g + g) 2 + h] = (1/N) sum over the
+   * rays r of cell b that drew (n, g, h) of Y_r^2 p(n,g) p(h), where p are the
+   * probabilities the ray was drawn with and h = 0 is the upward (d_y > 0)
+   * hemisphere.  Summed over h and (n,g) with weights 1/(q(n,g) q(h)) it is the
+   * unbiased estimate of E[Y^2] under another proposal q. */
+  double *tally;
 } orc_params;
 
 typedef struct {             /* per emitting cell of the box, x fastest           */
@@ -91,6 +98,23 @@ int orc_trace_ray(const orc_problem *P, const orc_ray_in *in, orc_ray_out *out);
 int orc_solve(const orc_problem *P, const orc_params *S, orc_cell_sums *out);
 int orc_exchange(const orc_problem *P, const orc_params *S, double *G, double *G2,
                  double *Gw, double *Gw2);
+/* ---- learned proposal (no counterpart in the paper; replaces the pdf of
+ * Eqs. 13, 16 per emitting cell) -- see learn_oracle.c ---------------------- */
+enum { ORC_NFEAT = 12, ORC_HIDDEN = 64 };
+int orc_features(const orc_problem *P, const int32_t *cells, int64_t n, double T_max,
+                 double *out);
+int64_t orc_mlp_nparams(int K);
+int orc_mlp_forward(const double *theta, int K, const double *fmean, const double *finv,
+                    const double *feat, int64_t n, const double *p0, int p0_stride,
+                    double mix, double *q);
+int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const double *finv,
+                      const double *feat, const double *m, const double *p0, int64_t n,
+                      double mix, double *loss, double *grad);
+void orc_adam(double *theta, const double *grad, double *m1, double *m2, int64_t n, double lr,
+              double beta1, double beta2, double eps, int t);
+int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *cn,
+                       uint64_t *cg, uint32_t *hemi);
+
 int orc_quadrature(const orc_problem *P, const double *mu, const double *mu_w, int nmu,
                    int nphi, const double *vn, const double *vw, int nv, int origin,
                    double tol, int max_steps, const int *cells, int ncq, int nthreads,

@@ -1,0 +1,299 @@
+"""Pins of the oracle's learned-proposal parts (features, second-moment tallies,
+network forward/backward, Adam, integer counts) to closed forms, special cases
+and brute force -- nothing here compares the oracle with itself."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle
+from paper_1810_00188_gb300 import inputs
+
+K_SMALL = 6
+
+
+def _grid(nx=6, ny=8, nz=5, eps=(1.0, 1.0), Tw=(500.0, 1000.0)):
+    return inputs.Grid(nx, ny, nz, 3.0, 2.0, 2.5, eps_wall=eps, T_wall=Tw)
+
+
+# ---- features ----------------------------------------------------------------
+
+def test_features_linear_in_y():
+    """T = a + b y: centred and one-sided differences are exact, the x-z
+    gradient is zero, the 3^3 mean is T_j inside and shifted by b dy / 2 at the
+    walls (the neighbourhood is cut there)."""
+    g = _grid(eps=(0.7, 0.9))
+    kd = inputs.make_grey_kdist(0.8)
+    a, b = 600.0, 150.0
+    dy = g.ly / g.ny
+    yc = (np.arange(g.ny) + 0.5) * dy
+    T = np.broadcast_to((a + b * yc)[None, :, None], (g.nz, g.ny, g.nx)).copy()
+    x = np.full(T.shape, 0.1)
+    f = oracle.features(g, kd, T, x, T_max=1234.0)
+    f = f.reshape(g.nz, g.ny, g.nx, 12)
+    h = g.ly / 2
+    for j in range(g.ny):
+        Tj = a + b * yc[j]
+        row = f[2, j, 3]
+        assert row[0] == pytest.approx(Tj / 1000)
+        assert row[1] == pytest.approx(0.1)
+        assert row[2] == pytest.approx(yc[j] / h - 1)
+        assert row[3] == pytest.approx(0.5) and row[4] == pytest.approx(1.0)
+        assert row[5] == (0.7 if yc[j] < h else 0.9)
+        assert row[6] == pytest.approx(h * b / 1000, rel=1e-12)
+        assert abs(row[7]) < 1e-12
+        mean = Tj + (b * dy / 2 if j == 0 else (-b * dy / 2 if j == g.ny - 1 else 0.0))
+        assert row[8] == pytest.approx(mean / Tj, rel=1e-12)
+        # std of 3 rows (or 2 at a wall) of a linear profile, 9 cells each
+        vals = [a + b * yc[jj] for jj in (j - 1, j, j + 1) if 0 <= jj < g.ny]
+        assert row[9] == pytest.approx(np.std(vals) / Tj, rel=1e-10)
+        assert row[11] == pytest.approx(1234.0 / Tj)
+
+
+def test_features_periodic_gradient_and_grey_planck_mean():
+    """T = a + c cos(2 pi x / lx): the centred difference is
+    -c sin(2 pi x_i / lx) sin(2 pi dx / lx) / dx; with a grey table the Planck
+    mean absorption coefficient is kappa x / x_ref."""
+    g = _grid(nx=8)
+    kap = 1.7
+    kd = inputs.make_grey_kdist(kap)
+    a, c = 900.0, 40.0
+    dx = g.lx / g.nx
+    xc = (np.arange(g.nx) + 0.5) * dx
+    T = np.broadcast_to((a + c * np.cos(2 * np.pi * xc / g.lx))[None, None, :], (g.nz, g.ny, g.nx)).copy()
+    xh = np.full(T.shape, 0.05)
+    f = oracle.features(g, kd, T, xh).reshape(g.nz, g.ny, g.nx, 12)
+    h = g.ly / 2
+    d = -c * np.sin(2 * np.pi * xc / g.lx) * np.sin(2 * np.pi * dx / g.lx) / dx
+    np.testing.assert_allclose(f[1, 3, :, 7], h * np.abs(d) / 1000, rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(f[..., 10], kap * 0.05 / kd.x_ref * h, rtol=1e-12)
+    assert np.all(np.abs(f[..., 6]) < 1e-12)
+
+
+def test_features_uniform_field():
+    g = _grid()
+    kd = inputs.make_kdist(0)
+    T = np.full((g.nz, g.ny, g.nx), 1000.0)
+    f = oracle.features(g, kd, T, None)
+    np.testing.assert_allclose(f[:, 8], 1.0, rtol=1e-14)
+    np.testing.assert_allclose(f[:, 9], 0.0, atol=1e-14)
+    np.testing.assert_allclose(f[:, 1], kd.x_ref)
+    np.testing.assert_allclose(f[:, 11], 1000.0 / 1000.0)  # T_max is the medium maximum (1000)
+    with pytest.raises(ValueError):
+        oracle.features(g, kd, T, None, cells=[g.ncells])
+
+
+# ---- second-moment tallies -----------------------------------------------------
+
+def _probs(cn, cg, nb, ng):
+    pn = np.diff(np.concatenate([[0], cn.astype(np.float64)])) / 2.0**32
+    pg = np.diff(np.concatenate([np.zeros((nb, 1)), cg.astype(np.float64)], axis=1), axis=1) / 2.0**32
+    return (pn[:, None] * pg).reshape(-1)
+
+
+def test_tally_reweights_to_plain_second_moment():
+    """Dividing the tallies by the probabilities they were drawn with gives back
+    the plain per-cell mean of Y^2 exactly (up to rounding)."""
+    grid, kd, T, x = inputs.nongrey_channel(6, 8, 5, seed=3, x_mode="field")
+    r = oracle.solve(grid, kd, T, x, rays=200, seed=5, tally=True)
+    cn, cg, _ = oracle.plain_proposal(grid, kd, T, x)
+    p0 = _probs(cn, cg, kd.n_bands, kd.n_g)
+    tl = r["tally"]
+    back = (tl / (p0[:, None] * 0.5)).sum(axis=(-1, -2))
+    np.testing.assert_allclose(back, r["sum_y2"] / 200, rtol=1e-12)
+    # only spectral points / hemispheres that were drawn are non-zero
+    assert np.count_nonzero(tl) <= tl.shape[0] * tl.shape[1] * tl.shape[2] * 200
+
+
+def test_tally_predicts_second_moment_under_another_proposal():
+    """sum m / (q_k q_h) from plain tallies is an unbiased estimate of E[Y^2]
+    under proposal q: compare with a direct solve under q (many rays)."""
+    grid, kd, T, x = inputs.nongrey_channel(4, 6, 4, seed=1, x_mode="field")
+    nb, ng = kd.n_bands, kd.n_g
+    nc = grid.ncells
+    cn, cg, _ = oracle.plain_proposal(grid, kd, T, x)
+    p0 = _probs(cn, cg, nb, ng)
+    # a smooth alternative proposal: plain^0.5 mixed with uniform, biased upward
+    qk = 0.5 * np.sqrt(p0) / np.sqrt(p0).sum() + 0.5 / (nb * ng)
+    q_up = 0.7
+    pc = oracle.learned_counts(qk, nb, ng, q_up)
+    qk_exact = _probs(pc[0], pc[1], nb, ng)
+    qh = np.array([pc[2], 2**23 - pc[2]]) / 2.0**23
+    rays = 4000
+    plain = oracle.solve(grid, kd, T, x, rays=rays, seed=1, tally=True)
+    pred = (plain["tally"] / (qk_exact[:, None] * qh[None, :])).sum(axis=(-1, -2)).reshape(-1)
+    prop = (np.tile(pc[0], (nc, 1)), np.tile(pc[1].reshape(-1), (nc, 1)), np.full(nc, pc[2]))
+    direct = oracle.solve(grid, kd, T, x, rays=rays, seed=2, proposal=prop)
+    m2 = (direct["sum_y2"] / rays).reshape(-1)
+    # both are means of heavy-tailed positive samples: compare the grid totals
+    ratio = pred.sum() / m2.sum()
+    assert 0.85 < ratio < 1.15, ratio
+
+
+# ---- network -------------------------------------------------------------------
+
+def _theta_zero(K):
+    return np.zeros(oracle.mlp_nparams(K))
+
+
+def _split(theta, K):
+    H, F = 64, 12
+    o = 0
+    parts = {}
+    for name, size in (("W1", H * F), ("b1", H), ("W2", H * H), ("b2", H), ("W3", (K + 2) * H),
+                       ("b3", K + 2)):
+        parts[name] = theta[o:o + size]
+        o += size
+    assert o == theta.size
+    return parts
+
+
+def test_mlp_param_count():
+    assert oracle.mlp_nparams(320) == 64 * 12 + 64 + 64 * 64 + 64 + 322 * 64 + 322 == 25922
+
+
+def test_mlp_forward_constant_network_is_uniform_mix():
+    K = K_SMALL
+    th = _theta_zero(K)
+    p0 = np.array([0.5, 0.2, 0.1, 0.1, 0.05, 0.05])
+    feat = np.random.default_rng(0).normal(size=(3, 12))
+    q = oracle.mlp_forward(th, K, np.zeros(12), np.ones(12), feat, p0, mix=0.1)
+    np.testing.assert_allclose(q[:, :K], np.broadcast_to(0.9 / K + 0.1 * p0, (3, K)), rtol=1e-15)
+    np.testing.assert_allclose(q[:, K:], 0.5, rtol=1e-15)
+
+
+def test_mlp_forward_chain_through_gelu():
+    """One active path: x -> a1 = (x0 - mu) s -> gelu -> gelu -> z_k = c_k v."""
+    K = K_SMALL
+    th = _theta_zero(K)
+    P = _split(th, K)
+    P["W1"][0 * 12 + 0] = 1.0
+    P["W2"][0 * 64 + 0] = 1.0
+    c = np.array([0.3, -1.0, 2.0, 0.0, 0.5, -0.2, 1.5, -0.5])
+    P["W3"][np.arange(K + 2) * 64] = c
+    fmean = np.full(12, 0.25)
+    finv = np.full(12, 2.0)
+    feat = np.zeros((1, 12))
+    feat[0, 0] = 1.1
+    gelu = lambda v: 0.5 * v * (1 + erf(v / math.sqrt(2)))
+    v = gelu(gelu((1.1 - 0.25) * 2.0))
+    z = c * v
+    s = np.exp(z[:K] - z[:K].max())
+    s /= s.sum()
+    up = 1 / (1 + np.exp(z[K + 1] - z[K]))
+    q = oracle.mlp_forward(th, K, fmean, finv, feat, np.full(K, 1.0 / K), mix=0.0)
+    np.testing.assert_allclose(q[0, :K], s, rtol=1e-13)
+    assert q[0, K] == pytest.approx(up, rel=1e-13)
+    assert q[0, K + 1] == pytest.approx(1 - up, rel=1e-13)
+
+
+def _rand_problem(K, n, seed):
+    rng = np.random.default_rng(seed)
+    th = rng.normal(scale=0.3, size=oracle.mlp_nparams(K))
+    feat = rng.normal(size=(n, 12))
+    m = rng.exponential(size=(n, K, 2)) * (rng.random((n, K, 2)) < 0.6)
+    p0 = rng.dirichlet(np.ones(K), size=n)
+    return th, feat, m, p0
+
+
+def test_mlp_gradient_matches_finite_differences():
+    K, n = K_SMALL, 5
+    th, feat, m, p0 = _rand_problem(K, n, 1)
+    fmean, finv = np.zeros(12), np.ones(12)
+    L, gr = oracle.mlp_loss_grad(th, K, fmean, finv, feat, m, p0, mix=0.1)
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.choice(64 * 12, 6, replace=False),              # W1
+                          64 * 12 + rng.choice(64, 3, replace=False),           # b1
+                          64 * 13 + rng.choice(64 * 64, 6, replace=False),      # W2
+                          oracle.mlp_nparams(K) - (K + 2) - (K + 2) * 64 + rng.choice((K + 2) * 64, 6, replace=False),
+                          oracle.mlp_nparams(K) - (K + 2) + np.arange(K + 2)])  # b3
+    for i in idx:
+        e = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += e
+        tm[i] -= e
+        Lp, _ = oracle.mlp_loss_grad(tp, K, fmean, finv, feat, m, p0, mix=0.1)
+        Lm, _ = oracle.mlp_loss_grad(tm, K, fmean, finv, feat, m, p0, mix=0.1)
+        fd = (Lp - Lm) / (2 * e)
+        assert gr[i] == pytest.approx(fd, rel=2e-5, abs=1e-9), i
+
+
+def test_mlp_loss_optimum_is_sqrt_of_separable_moments():
+    """For m[k][h] = a_k b_h the second moment sum m / (q_k q_h) is smallest at
+    q_k ~ sqrt(a_k), q_h ~ sqrt(b_h) (Cauchy-Schwarz), where it equals
+    (sum sqrt a)^2 (sum sqrt b)^2 and the gradient vanishes (no mixture)."""
+    K = K_SMALL
+    a = np.array([4.0, 1.0, 0.25, 9.0, 0.01, 1.0])
+    bh = np.array([1.0, 4.0])
+    m = (a[:, None] * bh[None, :])[None]
+    p0 = np.full((1, K), 1.0 / K)
+    th = _theta_zero(K)
+    P = _split(th, K)
+    P["b3"][:K] = 0.5 * np.log(a)
+    P["b3"][K:] = 0.5 * np.log(bh)
+    L, gr = oracle.mlp_loss_grad(th, K, np.zeros(12), np.ones(12), np.zeros((1, 12)), m, p0, mix=0.0)
+    M2 = (m[0] / (p0[0][:, None] * 0.5)).sum()
+    assert L == pytest.approx(np.sqrt(a).sum() ** 2 * np.sqrt(bh).sum() ** 2 / M2, rel=1e-12)
+    assert np.abs(gr).max() < 1e-12
+    # any other logits give a larger loss
+    P["b3"][0] += 0.3
+    L2, _ = oracle.mlp_loss_grad(th, K, np.zeros(12), np.ones(12), np.zeros((1, 12)), m, p0, mix=0.0)
+    assert L2 > L
+
+
+def test_mlp_softmax_gradients_sum_to_zero():
+    """Shifting all spectral logits (or both hemisphere logits) by a constant
+    changes nothing: the b3 gradient sums to zero over each group."""
+    K = K_SMALL
+    th, feat, m, p0 = _rand_problem(K, 4, 7)
+    _, gr = oracle.mlp_loss_grad(th, K, np.zeros(12), np.ones(12), feat, m, p0, mix=0.1)
+    gb3 = gr[-(K + 2):]
+    scale = np.abs(gb3).max()
+    assert abs(gb3[:K].sum()) < 1e-12 * max(scale, 1)
+    assert abs(gb3[K:].sum()) < 1e-12 * max(scale, 1)
+
+
+# ---- Adam ------------------------------------------------------------------------
+
+def test_adam_first_steps_closed_form():
+    """With a constant gradient the bias-corrected moments are g and g^2, so
+    every step moves theta by lr g / (|g| + eps)."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    th, m1, m2 = np.ones(4), np.zeros(4), np.zeros(4)
+    for t in (1, 2, 3):
+        th_prev = th.copy()
+        th, m1, m2 = oracle.adam(th, g, m1, m2, t, lr=0.01, eps=1e-8)
+        np.testing.assert_allclose(th, th_prev - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+# ---- integer counts ----------------------------------------------------------------
+
+def test_learned_counts_are_exact_and_close():
+    rng = np.random.default_rng(4)
+    nb, ng = 40, 8
+    q = rng.dirichlet(np.ones(nb * ng) * 0.3)
+    q[5] = 0.0
+    cn, cg, hemi = oracle.learned_counts(q, nb, ng, 0.3)
+    assert cn[-1] == 2**32 and np.all(cg[:, -1] == 2**32)
+    pn = np.diff(np.concatenate([[0], cn.astype(np.int64)]))
+    wn = q.reshape(nb, ng).sum(1)
+    assert np.all(pn >= 1)
+    assert np.all(np.abs(pn - wn / wn.sum() * 2**32) <= nb + 1)
+    pg = np.diff(np.concatenate([np.zeros((nb, 1), np.int64), cg.astype(np.int64)], axis=1), axis=1)
+    assert pg[0, 5] == 0 and np.all(pg.reshape(-1)[q > 0] >= 1)
+    assert hemi == int(math.floor(0.3 * 2**23 + 0.5))
+    assert oracle.learned_counts(q, nb, ng, 0.0)[2] == 1
+    assert oracle.learned_counts(q, nb, ng, 1.0)[2] == 2**23 - 1
+
+
+def test_learned_counts_reproduce_dyadic_probabilities():
+    """Probabilities that are already multiples of 2^-32 (one band) come back
+    as the same counts."""
+    rng = np.random.default_rng(5)
+    c = rng.integers(1, 2**26, size=8).astype(np.int64)
+    c[-1] += 2**32 - c.sum()
+    q = c.astype(np.float64) / 2.0**32
+    cn, cg, _ = oracle.learned_counts(q, 1, 8, 0.5)
+    np.testing.assert_array_equal(cg[0], np.cumsum(c).astype(np.uint64))
+    assert cn[0] == 2**32

@@ -54,7 +54,7 @@ class Params(C.Structure):
                 ("origin", C.c_int), ("use_box", C.c_int), ("box", C.c_int * 6),
                 ("nthreads", C.c_int), ("cell_cn", C.POINTER(C.c_uint64)),
                 ("cell_cg", C.POINTER(C.c_uint64)), ("cell_hemi", C.POINTER(C.c_uint32)),
-                ("tally", C.POINTER(C.c_double))]
+                ("tally", C.POINTER(C.c_double)), ("tally_cost", C.POINTER(C.c_double))]
 
 
 class CellSums(C.Structure):
@@ -102,7 +102,8 @@ def lib():
             L.orc_mlp_nparams.argtypes = [C.c_int]
             L.orc_mlp_nparams.restype = i64
             L.orc_mlp_forward.argtypes = [dp, C.c_int, dp, dp, dp, i64, dp, C.c_int, C.c_double, dp]
-            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, i64, C.c_double, dp, dp]
+            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, C.c_double, dp, i64,
+                                            C.c_double, dp, dp]
             L.orc_adam.argtypes = [dp, dp, dp, dp, i64, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int]
             L.orc_learned_counts.argtypes = [dp, C.c_int, C.c_int, C.c_double, up, up,
@@ -235,7 +236,8 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
     [nc]) overrides the plain T_max proposal per emitting cell.  With
     ``tally`` the result also holds "tally" [bnz, bny, bnx, nb * ng, 2]: per
     spectral point and hemisphere (0 upward), (1/N) sum of Y^2 p(n,g) p(h) over
-    the rays that drew them.
+    the rays that drew them, and "tally_cost" (same shape): (1/N) sum of
+    steps / (p(n,g) p(h)).
     """
     P = make_problem(grid, kd, T, x)
     S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthreads)
@@ -254,7 +256,9 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
         S.cell_hemi = hemi.ctypes.data_as(C.POINTER(C.c_uint32))
     if tally:
         tl = np.zeros((nc, kd.n_bands * kd.n_g, 2))
+        tc = np.zeros((nc, kd.n_bands * kd.n_g, 2))
         S.tally = _dp(tl)
+        S.tally_cost = _dp(tc)
     out = {k: np.zeros(nc) for k in ("sum_y", "sum_y2", "sum_abs", "sum_wall", "sum_wall2")}
     out["steps"] = np.zeros(nc, dtype=np.uint64)
     out["capped"] = np.zeros(nc, dtype=np.uint64)
@@ -270,6 +274,7 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
     res = {k: v.reshape(shape) for k, v in out.items()}
     if tally:
         res["tally"] = tl.reshape(shape + (kd.n_bands * kd.n_g, 2))
+        res["tally_cost"] = tc.reshape(shape + (kd.n_bands * kd.n_g, 2))
     res["q"] = res["sum_y"] / N
     res["scale"] = res["sum_abs"] / N
     res["q_wall"] = res["sum_wall"] / N
@@ -372,17 +377,20 @@ def mlp_forward(theta, K, fmean, finv, feat, p0, mix=0.1):
     return q
 
 
-def mlp_loss_grad(theta, K, fmean, finv, feat, m, p0, mix=0.1):
-    """(mean second-moment ratio loss, gradient [nparams]); m [n, K, 2], p0 [n, K]."""
+def mlp_loss_grad(theta, K, fmean, finv, feat, m, p0, mix=0.1, cost=None, c0=0.0):
+    """(mean work-ratio loss, gradient [nparams]); m, cost [n, K, 2] (cost None:
+    second moment only), p0 [n, K]."""
     theta, fmean, finv = _f64(theta), _f64(fmean), _f64(finv)
     feat = _f64(feat).reshape(-1, NFEAT)
     n = feat.shape[0]
     m = _f64(m).reshape(n, K, 2)
     p0 = _f64(p0).reshape(n, K)
+    cst = None if cost is None else _f64(cost).reshape(n, K, 2)
     grad = np.zeros(mlp_nparams(K))
     loss = C.c_double()
-    rc = lib().orc_mlp_loss_grad(_dp(theta), K, _dp(fmean), _dp(finv), _dp(feat), _dp(m), _dp(p0),
-                                 n, float(mix), C.byref(loss), _dp(grad))
+    rc = lib().orc_mlp_loss_grad(_dp(theta), K, _dp(fmean), _dp(finv), _dp(feat), _dp(m),
+                                 _dp(cst) if cst is not None else C.POINTER(C.c_double)(),
+                                 float(c0), _dp(p0), n, float(mix), C.byref(loss), _dp(grad))
     if rc != 0:
         raise ValueError("orc_mlp_loss_grad failed")
     return loss.value, grad

@@ -13,13 +13,16 @@
  *
  * with z the output of a 12 -> 64 -> 64 -> (K + 2) multilayer perceptron (GELU
  * activations) of local features of the cell and p0 the plain pdf.  Trained to
- * minimise the per-ray second moment
+ * minimise, per emitting cell, the work to reach a given standard error --
+ * second moment per ray times cost per ray -- relative to the plain proposal:
  *
- *   L_c = sum_(k,h) m_c[k][h] / (q_k q_h) / sum_(k,h) m_c[k][h] / (p0_k / 2)
+ *   L_c = A(q) C(q) / (A(p0) C(p0)),   A(q) = sum_(k,h) m_c[k][h] / (q_k q_h),
+ *                                      C(q) = c0 + sum_(k,h) c_c[k][h] q_k q_h,
  *
- * where m_c are the second-moment tallies of a plain solve (the unbiased
- * estimate of E[Y^2] under proposal q is sum m / (q_k q_h)); the minimiser of
- * the numerator over all pdfs is q proportional to sqrt(m).
+ * where m_c and c_c are the second-moment and cost tallies of a plain solve
+ * (unbiased estimates of E[Y^2] and of the mean steps per ray under q) and c0
+ * the fixed cost of a ray in steps.  Without cost tallies C = 1; the minimiser
+ * of A alone over all pdfs is q proportional to sqrt(m).
  *
  * Everything here is written from those definitions: no blocking or reordering
  * beyond the plain loops.  It shares no code with the CUDA library.
@@ -206,13 +209,13 @@ int orc_mlp_forward(const double *theta, int K, const double *fmean, const doubl
 }
 
 /* Mean over the n samples of L_c and its gradient with respect to theta (the
- * chain rule written out layer by layer).  m [n][K][2], p0 [n][K].  A sample
- * whose plain second moment is zero contributes nothing; terms with p0_k = 0
- * are left out (that spectral point is never drawn by either proposal's
- * defensive part, and contributes nothing to m). */
+ * chain rule written out layer by layer).  m, cst [n][K][2] (cst NULL: no cost
+ * factor), p0 [n][K].  A sample whose plain second moment is zero contributes
+ * nothing; terms with p0_k = 0 are left out (that spectral point is never drawn
+ * by the plain proposal, so its tallies are zero). */
 int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const double *finv,
-                      const double *feat, const double *m, const double *p0, int64_t n,
-                      double mix, double *loss, double *grad) {
+                      const double *feat, const double *m, const double *cst, double c0,
+                      const double *p0, int64_t n, double mix, double *loss, double *grad) {
   const int64_t np = orc_mlp_nparams(K);
   memset(grad, 0, sizeof(double) * np);
   *loss = 0.0;
@@ -235,29 +238,40 @@ int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const dou
   for (int64_t c = 0; c < n; ++c) {
     forward_one(theta, K, fmean, finv, feat + c * F, &A);
     const double *mc = m + c * (int64_t)K * 2, *pc = p0 + c * (int64_t)K;
+    const double *cc = cst ? cst + c * (int64_t)K * 2 : NULL;
     for (int k = 0; k < K; ++k) q[k] = (1.0 - mix) * A.s[k] + mix * pc[k];
     q[K] = (1.0 - mix) * A.s[K] + mix * 0.5;
     q[K + 1] = (1.0 - mix) * A.s[K + 1] + mix * 0.5;
-    double M2 = 0.0, num = 0.0;
+    double A0 = 0.0, Aq = 0.0, C0 = c0, Cq = c0;
     for (int k = 0; k < K; ++k) {
       if (!(pc[k] > 0.0)) continue;
       for (int hh = 0; hh < 2; ++hh) {
-        M2 += mc[k * 2 + hh] / (pc[k] * 0.5);
-        num += mc[k * 2 + hh] / (q[k] * q[K + hh]);
+        A0 += mc[k * 2 + hh] / (pc[k] * 0.5);
+        Aq += mc[k * 2 + hh] / (q[k] * q[K + hh]);
+        if (cc) {
+          C0 += cc[k * 2 + hh] * (pc[k] * 0.5);
+          Cq += cc[k * 2 + hh] * (q[k] * q[K + hh]);
+        }
       }
     }
-    if (!(M2 > 0.0)) continue;
-    *loss += num / M2 / (double)n;
-    /* dL/dq, scaled by 1/(n M2) */
-    const double sc = 1.0 / ((double)n * M2);
+    if (!cc) C0 = Cq = 1.0;
+    if (!(A0 > 0.0) || !(C0 > 0.0)) continue;
+    const double norm = A0 * C0;
+    *loss += Aq * Cq / norm / (double)n;
+    /* dL/dq = (dA/dq C + A dC/dq) / (n A0 C0) */
+    const double sc = 1.0 / ((double)n * norm);
     gq[K] = gq[K + 1] = 0.0;
     for (int k = 0; k < K; ++k) {
       gq[k] = 0.0;
       if (!(pc[k] > 0.0)) continue;
       for (int hh = 0; hh < 2; ++hh) {
         const double v = mc[k * 2 + hh];
-        gq[k] -= sc * v / (q[k] * q[k] * q[K + hh]);
-        gq[K + hh] -= sc * v / (q[k] * q[K + hh] * q[K + hh]);
+        gq[k] -= sc * Cq * v / (q[k] * q[k] * q[K + hh]);
+        gq[K + hh] -= sc * Cq * v / (q[k] * q[K + hh] * q[K + hh]);
+        if (cc) {
+          gq[k] += sc * Aq * cc[k * 2 + hh] * q[K + hh];
+          gq[K + hh] += sc * Aq * cc[k * 2 + hh] * q[k];
+        }
       }
     }
     /* through the mixtures and the two softmaxes */

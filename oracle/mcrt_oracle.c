@@ -442,9 +442,10 @@ static void solve_cell(solve_job *J, long b, xch_acc *xa) {
     trace_core(P, R.n, R.g, cell0, R.frac, R.dir, S->tol, S->max_steps, S->seed, cellid, ray,
                S->snapshot, &o, xa);
     const double Y = R.w * o.X;
-    if (S->tally)
-      S->tally[(size_t)b * nb * ng * 2 + ((size_t)R.n * ng + R.g) * 2 + R.h] +=
-          Y * Y * R.p_ng * R.p_h / (double)S->rays_per_cell;
+    const size_t tix = (size_t)b * nb * ng * 2 + ((size_t)R.n * ng + R.g) * 2 + R.h;
+    if (S->tally) S->tally[tix] += Y * Y * R.p_ng * R.p_h / (double)S->rays_per_cell;
+    if (S->tally_cost)
+      S->tally_cost[tix] += (double)o.steps / (R.p_ng * R.p_h) / (double)S->rays_per_cell;
     sy += Y;
     sy2 += Y * Y;
     sa += R.w * o.abs_terms;

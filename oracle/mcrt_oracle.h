@@ -54,6 +54,10 @@ typedef struct {
    * hemisphere.  Summed over h and (n,g) with weights 1/(q(n,g) q(h)) it is the
    * unbiased estimate of E[Y^2] under another proposal q. */
   double *tally;
+  /* Optional cost tallies, same layout: (1/N) sum over those rays of
+   * steps_r / (p(n,g) p(h)); weighted by q(n,g) q(h) and summed it is the
+   * unbiased estimate of the mean medium segments per ray under q. */
+  double *tally_cost;
 } orc_params;
 
 typedef struct {             /* per emitting cell of the box, x fastest           */
@@ -108,8 +112,8 @@ int orc_mlp_forward(const double *theta, int K, const double *fmean, const doubl
                     const double *feat, int64_t n, const double *p0, int p0_stride,
                     double mix, double *q);
 int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const double *finv,
-                      const double *feat, const double *m, const double *p0, int64_t n,
-                      double mix, double *loss, double *grad);
+                      const double *feat, const double *m, const double *cst, double c0,
+                      const double *p0, int64_t n, double mix, double *loss, double *grad);
 void orc_adam(double *theta, const double *grad, double *m1, double *m2, int64_t n, double lr,
               double beta1, double beta2, double eps, int t);
 int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *cn,

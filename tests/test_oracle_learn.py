@@ -102,6 +102,9 @@ def test_tally_reweights_to_plain_second_moment():
     tl = r["tally"]
     back = (tl / (p0[:, None] * 0.5)).sum(axis=(-1, -2))
     np.testing.assert_allclose(back, r["sum_y2"] / 200, rtol=1e-12)
+    # the cost tallies weighted by the drawing probabilities give the mean steps
+    steps = (r["tally_cost"] * (p0[:, None] * 0.5)).sum(axis=(-1, -2))
+    np.testing.assert_allclose(steps, r["steps"].astype(np.float64) / 200, rtol=1e-12)
     # only spectral points / hemispheres that were drawn are non-zero
     assert np.count_nonzero(tl) <= tl.shape[0] * tl.shape[1] * tl.shape[2] * 200
 
@@ -111,24 +114,28 @@ def test_tally_predicts_second_moment_under_another_proposal():
     under proposal q: compare with a direct solve under q (many rays)."""
     grid, kd, T, x = inputs.nongrey_channel(4, 6, 4, seed=1, x_mode="field")
     nb, ng = kd.n_bands, kd.n_g
-    nc = grid.ncells
     cn, cg, _ = oracle.plain_proposal(grid, kd, T, x)
     p0 = _probs(cn, cg, nb, ng)
-    # a smooth alternative proposal: plain^0.5 mixed with uniform, biased upward
-    qk = 0.5 * np.sqrt(p0) / np.sqrt(p0).sum() + 0.5 / (nb * ng)
+    # an alternative proposal within a bounded ratio of the plain one (so that
+    # the reweighted estimates stay light-tailed), biased upward
+    qk = p0 * (1.0 + 0.6 * np.cos(np.arange(nb * ng)))
+    qk /= qk.sum()
     q_up = 0.7
     pc = oracle.learned_counts(qk, nb, ng, q_up)
     qk_exact = _probs(pc[0], pc[1], nb, ng)
     qh = np.array([pc[2], 2**23 - pc[2]]) / 2.0**23
-    rays = 4000
-    plain = oracle.solve(grid, kd, T, x, rays=rays, seed=1, tally=True)
-    pred = (plain["tally"] / (qk_exact[:, None] * qh[None, :])).sum(axis=(-1, -2)).reshape(-1)
-    prop = (np.tile(pc[0], (nc, 1)), np.tile(pc[1].reshape(-1), (nc, 1)), np.full(nc, pc[2]))
-    direct = oracle.solve(grid, kd, T, x, rays=rays, seed=2, proposal=prop)
-    m2 = (direct["sum_y2"] / rays).reshape(-1)
-    # both are means of heavy-tailed positive samples: compare the grid totals
-    ratio = pred.sum() / m2.sum()
-    assert 0.85 < ratio < 1.15, ratio
+    # Y^2 is heavy-tailed: many rays on a few cells, compared in total
+    rays, box, nbx = 100000, (0, 2, 2, 4, 0, 1), 4
+    plain = oracle.solve(grid, kd, T, x, rays=rays, seed=1, tally=True, box=box)
+    pred = (plain["tally"] / (qk_exact[:, None] * qh[None, :])).sum()
+    prop = (np.tile(pc[0], (nbx, 1)), np.tile(pc[1].reshape(-1), (nbx, 1)), np.full(nbx, pc[2]))
+    direct = oracle.solve(grid, kd, T, x, rays=rays, seed=2, proposal=prop, box=box)
+    ratio = pred / (direct["sum_y2"].sum() / rays)
+    assert 0.93 < ratio < 1.07, ratio
+    # the mean steps per ray under q, predicted from the plain cost tallies
+    cpred = (plain["tally_cost"] * (qk_exact[:, None] * qh[None, :])).sum()
+    cdir = direct["steps"].astype(np.float64).sum() / rays
+    assert abs(cpred / cdir - 1) < 0.02, (cpred, cdir)
 
 
 # ---- network -------------------------------------------------------------------
@@ -197,11 +204,18 @@ def _rand_problem(K, n, seed):
     return th, feat, m, p0
 
 
-def test_mlp_gradient_matches_finite_differences():
+def _rand_cost(K, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.exponential(scale=20.0, size=(n, K, 2)) * (rng.random((n, K, 2)) < 0.7)
+
+
+@pytest.mark.parametrize("with_cost", [False, True])
+def test_mlp_gradient_matches_finite_differences(with_cost):
     K, n = K_SMALL, 5
     th, feat, m, p0 = _rand_problem(K, n, 1)
     fmean, finv = np.zeros(12), np.ones(12)
-    L, gr = oracle.mlp_loss_grad(th, K, fmean, finv, feat, m, p0, mix=0.1)
+    kw = dict(mix=0.1, cost=_rand_cost(K, n, 3) if with_cost else None, c0=6.0)
+    L, gr = oracle.mlp_loss_grad(th, K, fmean, finv, feat, m, p0, **kw)
     rng = np.random.default_rng(2)
     idx = np.concatenate([rng.choice(64 * 12, 6, replace=False),              # W1
                           64 * 12 + rng.choice(64, 3, replace=False),           # b1
@@ -213,8 +227,8 @@ def test_mlp_gradient_matches_finite_differences():
         tp, tm = th.copy(), th.copy()
         tp[i] += e
         tm[i] -= e
-        Lp, _ = oracle.mlp_loss_grad(tp, K, fmean, finv, feat, m, p0, mix=0.1)
-        Lm, _ = oracle.mlp_loss_grad(tm, K, fmean, finv, feat, m, p0, mix=0.1)
+        Lp, _ = oracle.mlp_loss_grad(tp, K, fmean, finv, feat, m, p0, **kw)
+        Lm, _ = oracle.mlp_loss_grad(tm, K, fmean, finv, feat, m, p0, **kw)
         fd = (Lp - Lm) / (2 * e)
         assert gr[i] == pytest.approx(fd, rel=2e-5, abs=1e-9), i
 
@@ -240,6 +254,31 @@ def test_mlp_loss_optimum_is_sqrt_of_separable_moments():
     P["b3"][0] += 0.3
     L2, _ = oracle.mlp_loss_grad(th, K, np.zeros(12), np.ones(12), np.zeros((1, 12)), m, p0, mix=0.0)
     assert L2 > L
+
+
+def test_mlp_cost_optimum():
+    """With cost c[k][h] = g_k and c0 = 0 the spectral part of
+    A(q) C(q) = (sum a_k / q_k)(sum g_k q_k)(sum b_h / q_h) is smallest at
+    q_k ~ sqrt(a_k / g_k) (Cauchy-Schwarz) with value (sum sqrt(a_k g_k))^2:
+    the loss there is the closed form and the gradient vanishes."""
+    K = K_SMALL
+    a = np.array([4.0, 1.0, 0.25, 9.0, 0.01, 1.0])
+    gk = np.array([1.0, 30.0, 2.0, 5.0, 1.0, 0.5])
+    bh = np.array([1.0, 4.0])
+    m = (a[:, None] * bh[None, :])[None]
+    cost = np.broadcast_to(gk[:, None], (K, 2))[None].copy()
+    p0 = np.full((1, K), 1.0 / K)
+    th = _theta_zero(K)
+    P = _split(th, K)
+    P["b3"][:K] = 0.5 * np.log(a / gk)
+    P["b3"][K:] = 0.5 * np.log(bh)
+    kw = dict(mix=0.0, cost=cost, c0=0.0)
+    L, gr = oracle.mlp_loss_grad(th, K, np.zeros(12), np.ones(12), np.zeros((1, 12)), m, p0, **kw)
+    A0 = (m[0] / (p0[0][:, None] * 0.5)).sum()
+    C0 = (cost[0] * (p0[0][:, None] * 0.5)).sum()
+    best = np.sqrt(a * gk).sum() ** 2 * np.sqrt(bh).sum() ** 2
+    assert L == pytest.approx(best / (A0 * C0), rel=1e-12)
+    assert np.abs(gr).max() < 1e-12
 
 
 def test_mlp_softmax_gradients_sum_to_zero():

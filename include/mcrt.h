@@ -250,6 +250,117 @@ int mcrt_batch_get_stats(mcrt_batch *b, mcrt_solve_stats *out);
 const char *mcrt_batch_last_error(const mcrt_batch *b);
 int mcrt_batch_destroy(mcrt_batch *b);
 
+/* ---- learned proposal (no counterpart in the paper) ------------------------
+ * The paper draws (n, g) from Zhang's T_max pdf (Section 2.1, Eqs. 13 and 16)
+ * and directions isotropically (Eq. 9).  A learned proposal replaces both, per
+ * emitting cell, by
+ *   q(n,g) = (1 - mix) softmax(z)_(n,g) + mix p0(n,g),
+ *   q(h)   = (1 - mix) softmax(z_up, z_down)_h + mix / 2   (h: sign of d_y),
+ * where p0 is the plain pdf and z = MLP(features): 12 -> 64 -> 64 -> K + 2
+ * with GELU activations, FP16 weights and FP32 arithmetic, K = n_bands n_g.
+ * q is quantised to the integer counts of mcrt_set_cell_proposal and the ray
+ * weight divides by the quantised probabilities, so Eq. 14 stays unbiased for
+ * any weights; mix > 0 keeps every (n, g) that the plain pdf can draw drawable.
+ * The network is trained on the GPU from tallies of plain solves to minimise
+ * (E_q[Y^2] x E_q[steps per ray]) relative to the plain pdf, per cell:
+ *   L = A(q) C(q) / (A(p0) C(p0)),  A(q) = sum_(k,h) m[k][h] / (q_k q_h),
+ *   C(q) = c0 + sum_(k,h) c[k][h] q_k q_h,
+ * with m and c the tallies of mcrt_tally_moments and c0 the fixed cost of a
+ * ray in steps (cost == NULL: C = 1). */
+enum { MCRT_NFEAT = 12, MCRT_NHIDDEN = 64 };
+typedef struct mcrt_mlp mcrt_mlp;
+
+/* Parameters of a network with K spectral outputs: theta = [W1 (64 x 12,
+ * row-major output x input), b1 (64), W2 (64 x 64), b2 (64), W3 ((K+2) x 64),
+ * b3 (K+2)]; output K is the upward hemisphere, K + 1 the downward one. */
+int64_t mcrt_mlp_nparams(int K);
+/* Creates a network for K = 1 .. 350 spectral points on `device` with all
+ * parameters zero.  Errors: MCRT_E_ARG, MCRT_E_UNSUPPORTED (K > 350),
+ * MCRT_E_CUDA, MCRT_E_OOM. */
+int mcrt_mlp_create(int device, int K, mcrt_mlp **out);
+/* Sets the FP32 master parameters (host [nparams]; the network runs with their
+ * FP16 roundings) and the feature normalisation x = (f - mean) * inv_std (host
+ * [12] each), and resets the Adam state.  Synchronous. */
+int mcrt_mlp_set_params(mcrt_mlp *m, const float *theta, const float *feat_mean,
+                        const float *feat_inv_std);
+/* Copies the FP32 master parameters and, if theta_used != NULL, the FP16
+ * values the network runs with (as floats) to host arrays [nparams].
+ * Synchronous. */
+int mcrt_mlp_get_params(mcrt_mlp *m, float *theta, float *theta_used);
+/* Forward pass: feat (device [n][12]) -> q_out (device [n][K+2]): the mixed
+ * spectral probabilities, then q_up and q_down.  p0: device plain
+ * probabilities, [K] shared (p0_stride 0) or [n][K] (p0_stride K).
+ * Asynchronous on cuda_stream. */
+int mcrt_mlp_forward(mcrt_mlp *m, const float *feat, int64_t n, const float *p0, int p0_stride,
+                     float mix, float *q_out, void *cuda_stream);
+/* Mean loss over a batch and its gradient.  Samples idx[0..n-1] (device, NULL:
+ * 0..n-1) of a dataset of n_data samples: feat (device [n_data][12]), mom and
+ * cost (device [n_data][K][2]; cost nullable) and p0 ([n_data][K], p0_stride
+ * K, or [K], stride 0).  The gradient (FP32, [nparams]) goes to grad_out
+ * (device, nullable) and to the network's own buffer; the loss is read by
+ * mcrt_mlp_last_loss, which also reports (MCRT_E_ARG) an index outside
+ * [0, n_data) -- such a sample is skipped, never read.  The gradient is reduced
+ * in a fixed order: identical inputs give identical bits.  Asynchronous. */
+int mcrt_mlp_loss_grad(mcrt_mlp *m, const float *feat, const float *mom, const float *cost,
+                       float c0, const float *p0, int p0_stride, int64_t n_data,
+                       const int32_t *idx, int64_t n, float mix, float *grad_out,
+                       void *cuda_stream);
+/* One Adam step (Kingma & Ba 2015) of the master parameters with gradient grad
+ * (device [nparams]; NULL: the network's last gradient); refreshes the FP16
+ * copy.  Asynchronous. */
+int mcrt_mlp_adam_step(mcrt_mlp *m, const float *grad, float lr, float beta1, float beta2,
+                       float eps, void *cuda_stream);
+/* Waits for the last mcrt_mlp_loss_grad and returns its loss. */
+int mcrt_mlp_last_loss(mcrt_mlp *m, double *loss);
+const char *mcrt_mlp_last_error(const mcrt_mlp *m);
+int mcrt_mlp_destroy(mcrt_mlp *m);
+
+/* The 12 features of cells (device int32 [n], linear index x fastest; NULL:
+ * cells 0..n-1) into out (device float [n][12]): T_i/1000, x_i, y_c/h - 1
+ * (h = ly/2), T_wall/1000 (two), eps of the nearer wall, h dT/dy / 1000
+ * (centred, one-sided at the walls), h |grad_xz T| / 1000 (centred, periodic),
+ * mean and standard deviation of T over the 3x3x3 neighbourhood (periodic in
+ * x, z, cut at the walls) / T_i, the Planck-mean absorption coefficient at
+ * (T_i, x_i) times h, T_max / T_i (T_max of Eq. 13).  Synchronous.  Errors:
+ * MCRT_E_ARG (an index outside the grid; its row is NaN), MCRT_E_STATE,
+ * MCRT_E_UNSUPPORTED (more than 512 T nodes). */
+int mcrt_cell_features(mcrt_ctx *ctx, const int32_t *cells, int64_t n, float *out,
+                       void *cuda_stream);
+/* An FP32 solve of the whole grid (p->use_box must be 0) that also tallies,
+ * for the listed cells (device int32 [n]), per spectral point k = n n_g + g and
+ * hemisphere h (0: d_y > 0):
+ *   mom_out [n][K][2]:  (1/N) sum of Y^2 p_k p_h over the rays that drew (k, h),
+ *   cost_out [n][K][2]: (1/N) sum of steps / (p_k p_h) over the same rays,
+ * with p the probabilities the rays were drawn with (plain or cell proposal).
+ * sum m / (q_k q_h) and sum c q_k q_h are unbiased estimates of the second
+ * moment of Y and of the medium steps per ray under any other proposal q.
+ * q_out / sigma_out (device, nullable) receive the solve's Q and sigma.
+ * Synchronous.  Errors as mcrt_solve_qrad, MCRT_E_UNSUPPORTED for K > 1024. */
+int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t *cells, int64_t n,
+                       float *mom_out, float *cost_out, double *q_out, double *sigma_out,
+                       void *cuda_stream);
+/* The plain pdf p0(n, g) of the current fields (Eq. 16 at T_max, as quantised)
+ * to a host array [K].  Synchronous. */
+int mcrt_get_plain_probs(mcrt_ctx *ctx, float *p0);
+/* Quantises per-cell probabilities q (device [ncells][K+2]: spectral points,
+ * then q_up; the last entry is ignored) into the cell proposal used by
+ * MCRT_PROPOSAL_CELL solves: band counts from the sums over g, g counts within
+ * each band, each a count of 2^32 proportional to its weight with at least one
+ * count for every positive weight and the remainder on the first largest
+ * weight; hemisphere count round(q_up 2^23) in [1, 2^23 - 1].  Synchronous.
+ * Errors: MCRT_E_ARG (a row without positive weight), MCRT_E_STATE. */
+int mcrt_set_cell_proposal_probs(mcrt_ctx *ctx, const float *q, void *cuda_stream);
+/* Copies the current cell proposal to host arrays cn [ncells][nb],
+ * cg [ncells][nb][ng], hemi [ncells].  Synchronous. */
+int mcrt_get_cell_proposal(mcrt_ctx *ctx, uint64_t *cn, uint64_t *cg, uint32_t *hemi);
+/* Features of every cell -> network -> mixture with the plain pdf (0 < mix <= 1)
+ * -> cell proposal, all on the device; later solves use it with
+ * MCRT_PROPOSAL_CELL.  The result equals mcrt_set_cell_proposal_probs of
+ * mcrt_mlp_forward of mcrt_cell_features.  Synchronous.  Errors: MCRT_E_ARG
+ * (K of the network differs from n_bands n_g, mix outside (0, 1]),
+ * MCRT_E_STATE. */
+int mcrt_set_learned_proposal(mcrt_ctx *ctx, mcrt_mlp *m, float mix, void *cuda_stream);
+
 /* Releases all device memory of the context; NULL is accepted.  Waits for the
  * context's outstanding work. */
 int mcrt_destroy(mcrt_ctx *ctx);

@@ -1,0 +1,844 @@
+// Learned spectral/directional proposal: cell features, second-moment and cost
+// tallies of a solve, the network's forward pass (straight into a per-cell
+// integer proposal), and its training (fused forward + loss + backward, a
+// fixed-order gradient reduction, Adam).
+//
+// The paper draws (n, g) from Zhang's T_max pdf (Section 2.1, Eqs. 13, 16) and
+// the direction isotropically (Eq. 9).  Eq. 14 stays unbiased for any other pdf
+// if the ray weight divides by the probabilities actually used and every
+// contributing (n, g, hemisphere) keeps a non-zero probability; here the pdf of
+// each emitting cell is
+//     q(n,g) = (1 - mix) softmax(z)_(n,g) + mix p0(n,g),
+//     q(h)   = (1 - mix) softmax(z_up, z_down)_h + mix / 2,
+// z the output of a 12 -> 64 -> 64 -> (K + 2) perceptron with GELU activations
+// and FP16 weights (FP32 arithmetic), quantised to integer counts (the trace
+// kernel's weights use the quantised probabilities exactly).  The network is
+// trained to minimise, per cell, (second moment per ray) x (steps per ray)
+// relative to the plain pdf, from unbiased tallies of plain solves:
+//     m[k][h] = (1/N) sum_(rays in k,h) Y^2 p_k p_h   ->  E_q[Y^2] = sum m / (q_k q_h)
+//     c[k][h] = (1/N) sum_(rays in k,h) steps / (p_k p_h) -> E_q[steps] = sum c q_k q_h
+//     L = A(q) C(q) / (A(p0) C(p0)),  A = sum m / (q_k q_h),  C = c0 + sum c q_k q_h.
+//
+// The tiny contractions (12x64, 64x64, 64x(K+2) per cell) run as FP32 FMAs on
+// shared-memory tiles; the work is a few milliseconds next to the solves that
+// produce its data, so they do not go to the tensor cores.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "draws.cuh"
+#include "mcrt_internal.h"
+
+namespace mcrt {
+namespace {
+
+constexpr int NF = kNFeat, NH = kNHidden;
+constexpr int IT = 32;   // cells per inference tile
+constexpr int TT = 16;   // samples per training tile
+constexpr int NTHR = 256;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678f)); }
+
+__device__ __forceinline__ float gelu_prime(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678f)) + x * 0.39894228f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---- features ------------------------------------------------------------------
+// 0 T_i/1000, 1 x_i, 2 y_c/h - 1, 3-4 wall T/1000, 5 eps of the nearer wall,
+// 6 h dT/dy / 1000 (centred, one-sided at the walls), 7 h |grad_xz T| / 1000
+// (centred, periodic), 8-9 mean and standard deviation of T over the 3^3
+// neighbourhood (periodic in x, z; cut at the walls) / T_i, 10 the Planck-mean
+// absorption coefficient at (T_i, x_i) times h, 11 T_max / T_i.
+
+__global__ void __launch_bounds__(NTHR) features_kernel(const FeatArgs f) {
+  const long long ncell = (long long)f.nx * f.ny * f.nz;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < f.n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = f.cells ? (long long)f.cells[q] : q;
+    float *o = f.out + q * NF;
+    if (c < 0 || c >= ncell) {
+      atomicOr(f.err, 1ull);
+      for (int i = 0; i < NF; ++i) o[i] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    const int nx = f.nx, ny = f.ny, nz = f.nz;
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    auto T = [&](int ii, int jj, int kk) {
+      return f.field64[(size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * kk)].x;
+    };
+    const double2 v = f.field64[c];
+    const double Ti = v.x, yc = (j + 0.5) * f.dy;
+    o[0] = (float)(Ti / 1000.0);
+    o[1] = (float)v.y;
+    o[2] = (float)(yc / f.h - 1.0);
+    o[3] = (float)(f.T_wall[0] / 1000.0);
+    o[4] = (float)(f.T_wall[1] / 1000.0);
+    o[5] = (float)(yc < f.h ? f.eps_wall[0] : f.eps_wall[1]);
+    double dTdy = 0.0;
+    if (ny > 1) {
+      if (j == 0)
+        dTdy = (T(i, 1, k) - T(i, 0, k)) / f.dy;
+      else if (j == ny - 1)
+        dTdy = (T(i, ny - 1, k) - T(i, ny - 2, k)) / f.dy;
+      else
+        dTdy = (T(i, j + 1, k) - T(i, j - 1, k)) / (2.0 * f.dy);
+    }
+    o[6] = (float)(f.h * dTdy / 1000.0);
+    const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+    const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
+    const double dTdx = (T(ip, j, k) - T(im, j, k)) / (2.0 * f.dx);
+    const double dTdz = (T(i, j, kp) - T(i, j, km)) / (2.0 * f.dz);
+    o[7] = (float)(f.h * sqrt(dTdx * dTdx + dTdz * dTdz) / 1000.0);
+    double sum = 0.0;
+    int cnt = 0;
+    const int xs[3] = {im, i, ip}, zs[3] = {km, k, kp};
+    for (int c2 = 0; c2 < 3; ++c2)
+      for (int b2 = -1; b2 <= 1; ++b2) {
+        const int jj = j + b2;
+        if (jj < 0 || jj >= ny) continue;
+        for (int a2 = 0; a2 < 3; ++a2) {
+          sum += T(xs[a2], jj, zs[c2]);
+          ++cnt;
+        }
+      }
+    const double mean = sum / cnt;
+    double var = 0.0;
+    for (int c2 = 0; c2 < 3; ++c2)
+      for (int b2 = -1; b2 <= 1; ++b2) {
+        const int jj = j + b2;
+        if (jj < 0 || jj >= ny) continue;
+        for (int a2 = 0; a2 < 3; ++a2) {
+          const double d = T(xs[a2], jj, zs[c2]) - mean;
+          var += d * d;
+        }
+      }
+    o[8] = (float)(mean / Ti);
+    o[9] = (float)(sqrt(var / cnt) / Ti);
+    // Planck mean at T_i from the FP32 tables at the cell's interpolation position
+    const uint2 pk = f.fpos32[c];
+    const unsigned it = pk.x >> 23;
+    const float fr = __uint_as_float(0x3F800000u | (pk.x & 0x7FFFFFu)) - 1.f;
+    float num = 0.f, den = 0.f;
+    for (int n = 0; n < f.nb; ++n) {
+      const float2 b = f.btab32[(size_t)n * f.nT + it];
+      const float Bn = b.x + fr * b.y;
+      float s = 0.f;
+      for (int g = 0; g < f.ng; ++g) {
+        const float2 kk = f.ktab32[((size_t)n * f.ng + g) * f.nT + it];
+        s += f.w_g32[g] * (kk.x + fr * kk.y);
+      }
+      num += Bn * s;
+      den += Bn;
+    }
+    o[10] = den > 0.f ? (float)((double)(num / den) * (double)__uint_as_float(pk.y) * f.h) : 0.f;
+    o[11] = (float)(f.T_max / Ti);
+  }
+}
+
+// ---- second-moment and cost tallies ----------------------------------------------
+// One warp per listed cell whose samples are in this chunk: recomputes each
+// ray's (n, g, hemisphere) from its Philox draw exactly as the trace kernel did,
+// and adds Y^2 p_k p_h / N and steps / (p_k p_h) / N to its bin.  The 32 rays of
+// a round are added one after another by the lane that owns the bin, so the
+// sums have a fixed order.
+
+constexpr int TALLY_WARPS = 4;
+
+__global__ void __launch_bounds__(TALLY_WARPS * 32) tally_kernel(const TallyArgs t) {
+  extern __shared__ double tsm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int K2 = 2 * t.nb * t.ng;
+  double *sm = tsm + (size_t)w * 2 * K2, *sc = sm + K2;
+  const long long ncell = (long long)t.nx * t.ny * t.nz;
+  const int nbx = (t.nx + 7) / 8, nby = (t.ny + 7) / 8;
+  const unsigned N = (unsigned)t.N;
+  for (long long q = (long long)blockIdx.x * TALLY_WARPS + w; q < t.n;
+       q += (long long)gridDim.x * TALLY_WARPS) {
+    const long long c = t.cells[q];
+    if (c < 0 || c >= ncell) {
+      if (lane == 0) atomicOr(t.err, 1ull);
+      continue;
+    }
+    const int x = (int)(c % t.nx), y = (int)((c / t.nx) % t.ny), z = (int)(c / ((long long)t.nx * t.ny));
+    const long long p = ((long long)(x >> 3) + nbx * ((long long)(y >> 3) + (long long)nby * (z >> 3))) * 512 +
+                        (x & 7) + 8 * ((y & 7) + 8 * (z & 7));
+    if (p < t.chunk_p0 || p >= t.chunk_p1) continue;
+    const size_t slot = (size_t)(p - t.chunk_p0);
+    for (int e = lane; e < K2; e += 32) sm[e] = sc[e] = 0.0;
+    __syncwarp();
+    const unsigned long long *cn = t.cell_cn ? t.cell_cn + (size_t)c * t.nb : t.cn;
+    const unsigned long long *cg = t.cell_cg ? t.cell_cg + (size_t)c * t.nb * t.ng : t.cg;
+    const unsigned hemi = t.cell_hemi ? t.cell_hemi[c] : 4194304u;
+    for (unsigned r0 = 0; r0 < N; r0 += 32) {
+      const unsigned r = r0 + lane;
+      int bin = 0;
+      double vm = 0.0, vc = 0.0;
+      if (r < N) {
+        const unsigned rayid = (unsigned)(t.ray_off + r);
+        const uint4 u = philox10(make_uint4((unsigned)c, rayid, 0u, t.snapshot), t.key0, t.key1);
+        const unsigned m0 = u.x >> 9;
+        const int h = m0 < hemi ? 0 : 1;
+        const double ph = (double)(h ? 8388608u - hemi : hemi) * 0x1p-23;
+        const int nn = pick(cn, t.nb, u.z);
+        const unsigned long long *cgn = cg + (size_t)nn * t.ng;
+        const int gg = pick(cgn, t.ng, u.w);
+        const double pn = (double)(cn[nn] - (nn ? cn[nn - 1] : 0ull)) * 0x1p-32;
+        const double pg = (double)(cgn[gg] - (gg ? cgn[gg - 1] : 0ull)) * 0x1p-32;
+        const double png = pn * pg;
+        const double Y = (double)t.ybuf[slot * N + r];
+        const double st = (double)t.ray_steps[slot * N + r];
+        vm = Y * Y * png * ph / (double)N;
+        vc = st / (png * ph) / (double)N;
+        bin = (nn * t.ng + gg) * 2 + h;
+      }
+      const int cntr = N - r0 < 32u ? (int)(N - r0) : 32;
+      for (int jr = 0; jr < cntr; ++jr) {
+        const int bj = __shfl_sync(0xffffffffu, bin, jr);
+        const double mj = __shfl_sync(0xffffffffu, vm, jr);
+        const double cj = __shfl_sync(0xffffffffu, vc, jr);
+        if ((bj & 31) == lane) {
+          sm[bj] += mj;
+          sc[bj] += cj;
+        }
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < K2; e += 32) {
+      t.m_out[q * K2 + e] = (float)sm[e];
+      t.c_out[q * K2 + e] = (float)sc[e];
+    }
+    __syncwarp();
+  }
+}
+
+// ---- integer proposal of one cell ------------------------------------------------
+// Counts of 2^32 proportional to the weights, at least one for every positive
+// weight, the rounding remainder on the first largest weight; W is the sum of
+// the weights in order (the same rule, in FP64, as the host's plain proposal).
+
+template <class T>
+__device__ bool quantize_row(const T *w, int K, double W, unsigned long long *cum) {
+  if (!(W > 0.0)) return false;
+  int kmax = 0;
+  for (int k = 1; k < K; ++k)
+    if ((double)w[k] > (double)w[kmax]) kmax = k;
+  long long total = 0;
+  for (int k = 0; k < K; ++k) {
+    const double wk = (double)w[k];
+    if (wk > 0.0) {
+      const long long mk = (long long)floor((wk / W) * 4294967296.0);
+      total += mk < 1 ? 1 : mk;
+    }
+  }
+  unsigned long long acc = 0;
+  for (int k = 0; k < K; ++k) {
+    const double wk = (double)w[k];
+    long long mk = 0;
+    if (wk > 0.0) {
+      mk = (long long)floor((wk / W) * 4294967296.0);
+      mk = mk < 1 ? 1 : mk;
+    }
+    if (k == kmax) mk += 4294967296LL - total;
+    acc += (unsigned long long)mk;
+    cum[k] = acc;
+  }
+  return true;
+}
+
+// Warp-cooperative: q [nb * ng] spectral probabilities and q_up of one cell ->
+// cumulative band counts cn [nb], g counts within each band cg [nb][ng], and the
+// upward-hemisphere count of 2^23.  wn: nb doubles of scratch.
+__device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double *wn,
+                              unsigned long long *cn, unsigned long long *cg, unsigned *hemi,
+                              unsigned long long *err) {
+  const int lane = threadIdx.x & 31;
+  for (int n = lane; n < nb; n += 32) {
+    const float *qn = q + (size_t)n * ng;
+    double W = 0.0;
+    for (int g = 0; g < ng; ++g) W += (double)qn[g];
+    wn[n] = W;
+    if (!quantize_row(qn, ng, W, cg + (size_t)n * ng)) {
+      // a band that is never drawn gets uniform g counts (weights 1, so the
+      // remainder goes to g = 0)
+      double Wu = 0.0;
+      for (int g = 0; g < ng; ++g) Wu += 1.0;
+      const long long mk = (long long)floor((1.0 / Wu) * 4294967296.0);
+      unsigned long long acc = 0;
+      for (int g = 0; g < ng; ++g) {
+        acc += (unsigned long long)(g == 0 ? mk + (4294967296LL - mk * ng) : mk);
+        cg[(size_t)n * ng + g] = acc;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double W = 0.0;
+    for (int n = 0; n < nb; ++n) W += wn[n];
+    if (!quantize_row(wn, nb, W, cn)) atomicOr(err, 2ull);
+    double hq = floor((double)q_up * 8388608.0 + 0.5);
+    if (!(hq >= 1.0)) hq = 1.0;
+    if (hq > 8388607.0) hq = 8388607.0;
+    *hemi = (unsigned)hq;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(NTHR) quantize_cells_kernel(const float *q, long long n, int nb,
+                                                             int ng, unsigned long long *cell_cn,
+                                                             unsigned long long *cell_cg,
+                                                             unsigned *cell_hemi,
+                                                             unsigned long long *err) {
+  extern __shared__ double qsm[];
+  const int w = threadIdx.x >> 5;
+  const int K = nb * ng;
+  double *wn = qsm + (size_t)w * nb;
+  for (long long c = (long long)blockIdx.x * (NTHR / 32) + w; c < n;
+       c += (long long)gridDim.x * (NTHR / 32)) {
+    const float *qc = q + c * (K + 2);
+    quantize_cell(qc, qc[K], nb, ng, wn, cell_cn + c * nb, cell_cg + c * (long long)K,
+                  cell_hemi + c, err);
+  }
+}
+
+// ---- network: shared-memory weights ------------------------------------------------
+// W1T [12][64], W2T [64][64] (input-major, for the forward pass), W3T [64][LDO]
+// with LDO an odd number of 32-bit words so that both the forward pass (lanes
+// along outputs) and the backward pass (lanes along inputs) are free of bank
+// conflicts.
+
+__host__ __device__ inline int ldo_halves(int K) { return 2 * ((((K + 2) + 1) / 2) | 1); }
+
+struct MlpSmem {
+  __half *W1T, *W2T, *W2, *W3T;
+  float *b1, *b2, *b3;
+};
+
+__device__ void load_weights(const __half *th, int K, const MlpSmem &S, bool need_w2) {
+  const int ldo = ldo_halves(K);
+  const __half *W1 = th, *W2 = W1 + NH * NF + NH, *W3 = W2 + NH * NH + NH;
+  const __half *b1 = W1 + NH * NF, *b2 = W2 + NH * NH, *b3 = W3 + (size_t)(K + 2) * NH;
+  for (int e = threadIdx.x; e < NH * NF; e += blockDim.x) {
+    const int o = e / NF, i = e % NF;
+    S.W1T[i * NH + o] = W1[e];
+  }
+  for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) {
+    const int o = e / NH, i = e % NH;
+    S.W2T[i * NH + o] = W2[e];
+    if (need_w2) S.W2[e] = W2[e];
+  }
+  for (int e = threadIdx.x; e < (K + 2) * NH; e += blockDim.x) {
+    const int o = e / NH, i = e % NH;
+    S.W3T[i * ldo + o] = W3[e];
+  }
+  for (int e = threadIdx.x; e < NH; e += blockDim.x) {
+    S.b1[e] = __half2float(b1[e]);
+    S.b2[e] = __half2float(b2[e]);
+  }
+  for (int e = threadIdx.x; e < K + 2; e += blockDim.x) S.b3[e] = __half2float(b3[e]);
+}
+
+// Forward pass of `rows` cells whose normalised features are in X [T][12]:
+// A1, H1, A2, H2 [T][64] (A* may be null) and logits Z [T][K+2].
+template <int T>
+__device__ void forward_tile(const MlpSmem &S, int K, const float *X, float *A1, float *H1,
+                             float *A2, float *H2, float *Z) {
+  const int ldo = ldo_halves(K);
+  for (int e = threadIdx.x; e < T * NH; e += blockDim.x) {
+    const int c = e / NH, o = e % NH;
+    float a = S.b1[o];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) a += __half2float(S.W1T[i * NH + o]) * X[c * NF + i];
+    if (A1) A1[e] = a;
+    H1[e] = gelu(a);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < T * NH; e += blockDim.x) {
+    const int c = e / NH, o = e % NH;
+    float a = S.b2[o];
+#pragma unroll 8
+    for (int i = 0; i < NH; ++i) a += __half2float(S.W2T[i * NH + o]) * H1[c * NH + i];
+    if (A2) A2[e] = a;
+    H2[e] = gelu(a);
+  }
+  __syncthreads();
+  const int KO = K + 2;
+  for (int e = threadIdx.x; e < T * KO; e += blockDim.x) {
+    const int c = e / KO, o = e % KO;
+    float a = S.b3[o];
+#pragma unroll 8
+    for (int i = 0; i < NH; ++i) a += __half2float(S.W3T[i * ldo + o]) * H2[c * NH + i];
+    Z[e] = a;
+  }
+  __syncthreads();
+}
+
+size_t infer_smem_bytes(int K, int nb) {
+  const size_t halves = (size_t)NF * NH + NH * NH + (size_t)NH * ldo_halves(K);
+  const size_t floats = 2 * NH + (K + 2) + IT * NF + 2 * IT * NH + (size_t)IT * (K + 2) + K + 2 * NF;
+  return ((halves * 2 + 15) / 16) * 16 + floats * 4 + (size_t)(NTHR / 32) * nb * 8 + 64;
+}
+
+__global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
+  extern __shared__ __align__(16) unsigned char ism[];
+  const int K = a.K, KO = K + 2, ldo = ldo_halves(K);
+  MlpSmem S;
+  __half *hp = reinterpret_cast<__half *>(ism);
+  S.W1T = hp;
+  S.W2T = S.W1T + NF * NH;
+  S.W2 = nullptr;
+  S.W3T = S.W2T + NH * NH;
+  const size_t halves = (size_t)NF * NH + NH * NH + (size_t)NH * ldo;
+  float *fp = reinterpret_cast<float *>(ism + ((halves * 2 + 15) / 16) * 16);
+  S.b1 = fp;
+  S.b2 = S.b1 + NH;
+  S.b3 = S.b2 + NH;
+  float *X = S.b3 + KO;
+  float *H1 = X + IT * NF, *H2 = H1 + IT * NH, *Z = H2 + IT * NH;
+  float *p0s = Z + (size_t)IT * KO;
+  float *nrm = p0s + K;  // fmean [12], finv [12]
+  double *wn = reinterpret_cast<double *>((reinterpret_cast<size_t>(nrm + 2 * NF) + 7) & ~(size_t)7);
+  load_weights(a.theta16, K, S, false);
+  for (int e = threadIdx.x; e < NF; e += blockDim.x) {
+    nrm[e] = a.fmean[e];
+    nrm[NF + e] = a.finv[e];
+  }
+  if (a.p0_stride == 0)
+    for (int e = threadIdx.x; e < K; e += blockDim.x) p0s[e] = a.p0[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long ntiles = (a.n + IT - 1) / IT;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long t0 = tile * IT;
+    const int rows = (int)min((long long)IT, a.n - t0);
+    for (int e = threadIdx.x; e < IT * NF; e += blockDim.x) {
+      const int c = e / NF, i = e % NF;
+      X[e] = c < rows ? (a.feat[(t0 + c) * NF + i] - nrm[i]) * nrm[NF + i] : 0.f;
+    }
+    __syncthreads();
+    forward_tile<IT>(S, K, X, nullptr, H1, nullptr, H2, Z);
+    // softmax over the spectral logits and the hemisphere pair, then the mixture
+    for (int c = w; c < rows; c += NTHR / 32) {
+      float *z = Z + (size_t)c * KO;
+      const float *p0 = a.p0_stride ? a.p0 + (t0 + c) * (long long)a.p0_stride : p0s;
+      float mx = -INFINITY;
+      for (int k = lane; k < K; k += 32) mx = fmaxf(mx, z[k]);
+      mx = warp_max(mx);
+      float sum = 0.f;
+      for (int k = lane; k < K; k += 32) sum += expf(z[k] - mx);
+      sum = warp_sum(sum);
+      const float inv = 1.f / sum;
+      const float hm = fmaxf(z[K], z[K + 1]);
+      const float eu = expf(z[K] - hm), ed = expf(z[K + 1] - hm);
+      __syncwarp();
+      for (int k = lane; k < K; k += 32)
+        z[k] = (1.f - a.mix) * (expf(z[k] - mx) * inv) + a.mix * p0[k];
+      __syncwarp();
+      if (lane == 0) {
+        z[K] = (1.f - a.mix) * (eu / (eu + ed)) + a.mix * 0.5f;
+        z[K + 1] = (1.f - a.mix) * (ed / (eu + ed)) + a.mix * 0.5f;
+      }
+      __syncwarp();
+      if (a.q_out)
+        for (int k = lane; k < KO; k += 32) a.q_out[(t0 + c) * KO + k] = z[k];
+      if (a.cell_cn)
+        quantize_cell(z, z[K], a.nb, a.ng, wn + (size_t)w * a.nb, a.cell_cn + (t0 + c) * a.nb,
+                      a.cell_cg + (t0 + c) * (long long)K, a.cell_hemi + (t0 + c), a.err);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- training ------------------------------------------------------------------
+// Persistent CTAs; each takes tiles of TT samples of the batch, runs the forward
+// pass, the loss gradient with respect to the logits, and the backward pass,
+// accumulating its share of the gradient in shared memory (each entry owned by
+// one thread, samples added in order), then writes it to partial[blockIdx.x].
+// grad_reduce_kernel adds the CTAs' partials in order: the gradient does not
+// depend on timing.
+
+size_t train_smem_bytes(int K) {
+  const int KO = K + 2;
+  const size_t halves = (size_t)NF * NH + 2 * NH * NH + (size_t)NH * ldo_halves(K);
+  const size_t grads = (size_t)NF * NH + NH + NH * NH + NH + (size_t)NH * KO + KO;
+  const size_t floats = 2 * NH + KO + grads + TT * NF + 6 * TT * NH + (size_t)TT * KO + 2 * NF + 8;
+  return ((halves * 2 + 15) / 16) * 16 + floats * 4 + 16;
+}
+
+__global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a) {
+  extern __shared__ __align__(16) unsigned char tsm2[];
+  const int K = a.K, KO = K + 2, ldo = ldo_halves(K);
+  MlpSmem S;
+  __half *hp = reinterpret_cast<__half *>(tsm2);
+  S.W1T = hp;
+  S.W2T = S.W1T + NF * NH;
+  S.W2 = S.W2T + NH * NH;
+  S.W3T = S.W2 + NH * NH;
+  const size_t halves = (size_t)NF * NH + 2 * NH * NH + (size_t)NH * ldo;
+  float *fp = reinterpret_cast<float *>(tsm2 + ((halves * 2 + 15) / 16) * 16);
+  S.b1 = fp;
+  S.b2 = S.b1 + NH;
+  S.b3 = S.b2 + NH;
+  float *gW1T = S.b3 + KO, *gb1 = gW1T + NF * NH, *gW2T = gb1 + NH, *gb2 = gW2T + NH * NH,
+        *gW3T = gb2 + NH, *gb3 = gW3T + (size_t)NH * KO;
+  float *X = gb3 + KO, *A1 = X + TT * NF, *H1 = A1 + TT * NH, *A2 = H1 + TT * NH, *H2 = A2 + TT * NH,
+        *dA2 = H2 + TT * NH, *dA1 = dA2 + TT * NH, *Z = dA1 + TT * NH;
+  float *nrm = Z + (size_t)TT * KO;
+  __shared__ double s_loss;
+  __shared__ float s_lsamp[TT];
+  load_weights(a.theta16, K, S, true);
+  const long long ngrad = (long long)NF * NH + NH + NH * NH + NH + (long long)NH * KO + KO;
+  for (long long e = threadIdx.x; e < ngrad; e += blockDim.x) gW1T[e] = 0.f;
+  for (int e = threadIdx.x; e < NF; e += blockDim.x) {
+    nrm[e] = a.fmean[e];
+    nrm[NF + e] = a.finv[e];
+  }
+  if (threadIdx.x == 0) s_loss = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float invB = 1.f / (float)a.n;
+  const long long ntiles = (a.n + TT - 1) / TT;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long t0 = tile * TT;
+    const int rows = (int)min((long long)TT, a.n - t0);
+    for (int e = threadIdx.x; e < TT * NF; e += blockDim.x) {
+      const int c = e / NF, i = e % NF;
+      float v = 0.f;
+      if (c < rows) {
+        const long long smp = a.idx ? (long long)a.idx[t0 + c] : t0 + c;
+        if (smp >= 0 && smp < a.n_data) v = (a.feat[smp * NF + i] - nrm[i]) * nrm[NF + i];
+      }
+      X[e] = v;
+    }
+    __syncthreads();
+    forward_tile<TT>(S, K, X, A1, H1, A2, H2, Z);
+    // loss and its gradient with respect to the logits, one warp per sample
+    for (int c = w; c < TT; c += NTHR / 32) {
+      float *z = Z + (size_t)c * KO;
+      if (lane == 0) s_lsamp[c] = 0.f;
+      if (c >= rows) {
+        for (int k = lane; k < KO; k += 32) z[k] = 0.f;
+        continue;
+      }
+      const long long smp = a.idx ? (long long)a.idx[t0 + c] : t0 + c;
+      if (smp < 0 || smp >= a.n_data) {  // outside the dataset: no contribution
+        if (lane == 0) atomicOr(a.err, 1ull);
+        for (int k = lane; k < KO; k += 32) z[k] = 0.f;
+        continue;
+      }
+      const float *m = a.mom + smp * 2 * K;
+      const float *cs = a.cost ? a.cost + smp * 2 * K : nullptr;
+      const float *p0 = a.p0 + smp * (long long)a.p0_stride;
+      float mx = -INFINITY;
+      for (int k = lane; k < K; k += 32) mx = fmaxf(mx, z[k]);
+      mx = warp_max(mx);
+      float sum = 0.f;
+      for (int k = lane; k < K; k += 32) sum += expf(z[k] - mx);
+      sum = warp_sum(sum);
+      const float inv = 1.f / sum;
+      const float hm = fmaxf(z[K], z[K + 1]);
+      const float eu = expf(z[K] - hm), ed = expf(z[K + 1] - hm);
+      const float tu = eu / (eu + ed), td = ed / (eu + ed);
+      const float qu = (1.f - a.mix) * tu + a.mix * 0.5f, qd = (1.f - a.mix) * td + a.mix * 0.5f;
+      float A0 = 0.f, Aq = 0.f, C0 = 0.f, Cq = 0.f;
+      for (int k = lane; k < K; k += 32) {
+        const float pk = p0[k];
+        if (!(pk > 0.f)) continue;
+        const float qk = (1.f - a.mix) * (expf(z[k] - mx) * inv) + a.mix * pk;
+        const float mu = m[2 * k], md = m[2 * k + 1];
+        A0 += (mu + md) / (pk * 0.5f);
+        Aq += mu / (qk * qu) + md / (qk * qd);
+        if (cs) {
+          C0 += (cs[2 * k] + cs[2 * k + 1]) * (pk * 0.5f);
+          Cq += cs[2 * k] * (qk * qu) + cs[2 * k + 1] * (qk * qd);
+        }
+      }
+      A0 = warp_sum(A0);
+      Aq = warp_sum(Aq);
+      if (cs) {
+        C0 = warp_sum(C0) + a.c0;
+        Cq = warp_sum(Cq) + a.c0;
+      } else {
+        C0 = Cq = 1.f;
+      }
+      if (!(A0 > 0.f) || !(C0 > 0.f)) {
+        __syncwarp();
+        for (int k = lane; k < KO; k += 32) z[k] = 0.f;
+        continue;
+      }
+      const float norm = A0 * C0;
+      if (lane == 0) s_lsamp[c] = Aq * Cq / norm;
+      const float sc = invB / norm;
+      // dL/dq_k and the hemisphere gradients; then through the softmaxes
+      float dot = 0.f, gu = 0.f, gd = 0.f;
+      for (int k = lane; k < K; k += 32) {
+        const float pk = p0[k];
+        if (!(pk > 0.f)) continue;
+        const float sk = expf(z[k] - mx) * inv;
+        const float qk = (1.f - a.mix) * sk + a.mix * pk;
+        const float mu = m[2 * k], md = m[2 * k + 1];
+        float g = -sc * Cq * (mu / (qk * qk * qu) + md / (qk * qk * qd));
+        gu -= sc * Cq * mu / (qk * qu * qu);
+        gd -= sc * Cq * md / (qk * qd * qd);
+        if (cs) {
+          g += sc * Aq * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
+          gu += sc * Aq * cs[2 * k] * qk;
+          gd += sc * Aq * cs[2 * k + 1] * qk;
+        }
+        dot += sk * g;
+      }
+      dot = warp_sum(dot);
+      gu = warp_sum(gu);
+      gd = warp_sum(gd);
+      __syncwarp();
+      for (int k = lane; k < K; k += 32) {
+        const float pk = p0[k];
+        const float sk = expf(z[k] - mx) * inv;
+        float g = 0.f;
+        if (pk > 0.f) {
+          const float qk = (1.f - a.mix) * sk + a.mix * pk;
+          const float mu = m[2 * k], md = m[2 * k + 1];
+          g = -sc * Cq * (mu / (qk * qk * qu) + md / (qk * qk * qd));
+          if (cs) g += sc * Aq * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
+        }
+        z[k] = (1.f - a.mix) * sk * (g - dot);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const float dh = tu * gu + td * gd;
+        z[K] = (1.f - a.mix) * tu * (gu - dh);
+        z[K + 1] = (1.f - a.mix) * td * (gd - dh);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int c = 0; c < rows; ++c) s_loss += (double)s_lsamp[c] * (double)invB;
+    // layer 3: gW3T[i][o] += sum_c H2[c][i] dz[c][o]; gb3; dH2 -> dA2
+    for (int e = threadIdx.x; e < NH * KO; e += blockDim.x) {
+      const int i = e / KO, o = e % KO;
+      float acc = gW3T[e];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += H2[c * NH + i] * Z[c * KO + o];
+      gW3T[e] = acc;
+    }
+    for (int o = threadIdx.x; o < KO; o += blockDim.x) {
+      float acc = gb3[o];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += Z[c * KO + o];
+      gb3[o] = acc;
+    }
+    for (int e = threadIdx.x; e < TT * NH; e += blockDim.x) {
+      const int c = e / NH, i = e % NH;
+      float acc = 0.f;
+      const float *zc = Z + (size_t)c * KO;
+      const __half *wr = S.W3T + (size_t)i * ldo;
+      for (int o = 0; o < KO; ++o) acc += __half2float(wr[o]) * zc[o];
+      dA2[e] = acc * gelu_prime(A2[e]);
+    }
+    __syncthreads();
+    // layer 2
+    for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) {
+      const int i = e / NH, o = e % NH;
+      float acc = gW2T[e];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += H1[c * NH + i] * dA2[c * NH + o];
+      gW2T[e] = acc;
+    }
+    for (int o = threadIdx.x; o < NH; o += blockDim.x) {
+      float acc = gb2[o];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += dA2[c * NH + o];
+      gb2[o] = acc;
+    }
+    for (int e = threadIdx.x; e < TT * NH; e += blockDim.x) {
+      const int c = e / NH, i = e % NH;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int o = 0; o < NH; ++o) acc += __half2float(S.W2[o * NH + i]) * dA2[c * NH + o];
+      dA1[e] = acc * gelu_prime(A1[e]);
+    }
+    __syncthreads();
+    // layer 1
+    for (int e = threadIdx.x; e < NF * NH; e += blockDim.x) {
+      const int i = e / NH, o = e % NH;
+      float acc = gW1T[e];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += X[c * NF + i] * dA1[c * NH + o];
+      gW1T[e] = acc;
+    }
+    for (int o = threadIdx.x; o < NH; o += blockDim.x) {
+      float acc = gb1[o];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc += dA1[c * NH + o];
+      gb1[o] = acc;
+    }
+    __syncthreads();
+  }
+  // this CTA's share, in theta's layout
+  float *out = a.partial + (size_t)blockIdx.x * ngrad;
+  const long long oW1 = 0, ob1 = NH * NF, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 = ob2 + NH,
+                  ob3 = oW3 + (long long)KO * NH;
+  for (int e = threadIdx.x; e < NH * NF; e += blockDim.x) {
+    const int o = e / NF, i = e % NF;
+    out[oW1 + e] = gW1T[i * NH + o];
+  }
+  for (int e = threadIdx.x; e < NH; e += blockDim.x) {
+    out[ob1 + e] = gb1[e];
+    out[ob2 + e] = gb2[e];
+  }
+  for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) {
+    const int o = e / NH, i = e % NH;
+    out[oW2 + e] = gW2T[i * NH + o];
+  }
+  for (int e = threadIdx.x; e < KO * NH; e += blockDim.x) {
+    const int o = e / NH, i = e % NH;
+    out[oW3 + e] = gW3T[(size_t)i * KO + o];
+  }
+  for (int e = threadIdx.x; e < KO; e += blockDim.x) out[ob3 + e] = gb3[e];
+  __syncthreads();
+  if (threadIdx.x == 0) a.loss_partial[blockIdx.x] = s_loss;
+}
+
+__global__ void grad_reduce_kernel(const float *partial, const double *loss_partial, int grid,
+                                   long long np, float *grad, double *loss) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np;
+       j += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int b = 0; b < grid; ++b) acc += partial[(size_t)b * np + j];
+    grad[j] = acc;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double l = 0.0;
+    for (int b = 0; b < grid; ++b) l += loss_partial[b];
+    *loss = l;
+  }
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 master weights; the FP16
+// copy the network runs with is refreshed in the same pass.
+__global__ void adam_kernel(float *theta, __half *theta16, const float *grad, float *m1, float *m2,
+                            long long np, float lr, float beta1, float beta2, float eps, float c1,
+                            float c2) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np;
+       j += (long long)gridDim.x * blockDim.x) {
+    const float g = grad[j];
+    const float a = beta1 * m1[j] + (1.f - beta1) * g;
+    const float b = beta2 * m2[j] + (1.f - beta2) * g * g;
+    m1[j] = a;
+    m2[j] = b;
+    const float t = theta[j] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+    theta[j] = t;
+    theta16[j] = __float2half_rn(t);
+  }
+}
+
+__global__ void to_half_kernel(const float *theta, __half *theta16, long long np) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np;
+       j += (long long)gridDim.x * blockDim.x)
+    theta16[j] = __float2half_rn(theta[j]);
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  }
+  return n;
+}
+
+unsigned grid_for(long long items, int per_block, int per_sm = 8) {
+  long long b = (items + per_block - 1) / per_block;
+  const long long cap = (long long)num_sms() * per_sm;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+long long mlp_nparams(int K) {
+  return (long long)NH * NF + NH + (long long)NH * NH + NH + (long long)(K + 2) * NH + (K + 2);
+}
+
+int mlp_train_grid() { return num_sms(); }
+
+cudaError_t launch_features(const FeatArgs &f, cudaStream_t s) {
+  if (f.n <= 0) return cudaSuccess;
+  features_kernel<<<grid_for(f.n, NTHR), NTHR, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tally(const TallyArgs &t, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  const size_t smem = (size_t)TALLY_WARPS * 2 * 2 * t.nb * t.ng * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(tally_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  tally_kernel<<<grid_for(t.n, TALLY_WARPS, 4), TALLY_WARPS * 32, smem, s>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t smem = infer_smem_bytes(a.K, a.nb > 0 ? a.nb : 1);
+  cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  mlp_infer_kernel<<<grid_for(a.n, IT, 1), NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
+                                  unsigned long long *cell_cn, unsigned long long *cell_cg,
+                                  unsigned *cell_hemi, unsigned long long *err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(NTHR / 32) * nb * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(quantize_cells_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  quantize_cells_kernel<<<grid_for(n, NTHR / 32, 4), NTHR, smem, s>>>(q, n, nb, ng, cell_cn, cell_cg,
+                                                                       cell_hemi, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train(const MlpTrainArgs &a, cudaStream_t s) {
+  const size_t smem = train_smem_bytes(a.K);
+  cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  mlp_train_kernel<<<a.grid, NTHR, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(const float *partial, const double *loss_partial, int grid,
+                               long long np, float *grad, double *loss, cudaStream_t s) {
+  grad_reduce_kernel<<<grid_for(np, 256, 2), 256, 0, s>>>(partial, loss_partial, grid, np, grad, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *theta, __half *theta16, const float *grad, float *m1, float *m2,
+                        long long np, float lr, float beta1, float beta2, float eps, float c1,
+                        float c2, cudaStream_t s) {
+  adam_kernel<<<grid_for(np, 256, 2), 256, 0, s>>>(theta, theta16, grad, m1, m2, np, lr, beta1, beta2,
+                                                   eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_theta_to_half(const float *theta, __half *theta16, long long np, cudaStream_t s) {
+  to_half_kernel<<<grid_for(np, 256, 2), 256, 0, s>>>(theta, theta16, np);
+  return cudaGetLastError();
+}
+
+}  // namespace mcrt

@@ -16,94 +16,12 @@
 #include <vector>
 
 #include "../../include/mcrt.h"
+#include "ctx.h"
 #include "mcrt_internal.h"
 
-namespace {
-
-struct DevBuf {
-  void *p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-struct mcrt_ctx {
-  mcrt_grid_desc grid{};
-  // k-distribution (host copy, FP64)
-  bool have_kdist = false;
-  int nb = 0, ng = 0, nT = 0;
-  double T0 = 0, dT = 1, x_ref = 1;
-  std::vector<double> w_g, kappa, B;
-  // fields
-  bool have_fields = false;
-  double T_max_field = 0, T_min_field = 0;
-  // cell proposal
-  bool have_cell_prop = false;
-  // plain proposal cache (valid for prop_T_max)
-  bool prop_valid = false;
-  double prop_T_max = -1;
-  // device buffers
-  DevBuf field64, field32, fpos32, ktab64, ktab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
-      guide, ybuf, step_acc,
-      cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaStream_t last_stream = nullptr;
-  bool solved = false;
-  int last_launches = 0;
-  int min_blocks = 3;
-  int steps_per_round = 2;
-  int scratch_mib = 1024;
-  double last_T_max = 0;
-  std::string err;
-};
+using namespace mcrt_host;
 
 namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-int fail(mcrt_ctx *c, int code, const std::string &msg) {
-  if (c) c->err = msg;
-  return code;
-}
-
-int cuda_fail(mcrt_ctx *c, cudaError_t e, const char *where) {
-  cudaGetLastError();  // clear a sticky non-fatal error
-  const int code = e == cudaErrorMemoryAllocation ? MCRT_E_OOM : MCRT_E_CUDA;
-  return fail(c, code, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-#define CK(call, where)                                   \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
-  } while (0)
-
-cudaError_t ensure(DevBuf &b, size_t bytes) {
-  if (b.bytes >= bytes && b.p) return cudaSuccess;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-  if (bytes == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&b.p, bytes);
-  if (e == cudaSuccess) b.bytes = bytes;
-  return e;
-}
-
-void release(DevBuf &b) {
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-}
 
 bool finite_nonneg(const double *v, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -160,6 +78,10 @@ bool quantize_counts(const double *w, int K, unsigned long long *cum) {
   return true;
 }
 
+}  // namespace
+
+namespace mcrt_host {
+
 // Zhang's T_max proposal (Eq. 13) in the narrow-band form of Eq. 16:
 // f_n ~ B_n(T_max) sum_g w_g k_{n,g}(T_max) and f_g(n) ~ w_g k_{n,g}(T_max).
 int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
@@ -181,17 +103,24 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   }
   if (!quantize_counts(wn.data(), nb, cn.data()))
     return fail(ctx, MCRT_E_ARG, "no band emits at T_max (all kappa*B are zero)");
-  // ray weights w_g / (p(n,g) q) with q = 1/(4 pi), in FP64, rounded once for the FP32 kernel
+  // ray weights w_g / (p(n,g) q) with q = 1/(4 pi), in FP64, rounded once for the FP32 kernel;
+  // the probabilities p(n,g) themselves (FP32) for the learned proposal's mixture
   std::vector<float> w32((size_t)nb * ng);
+  ctx->p0_host.assign((size_t)nb * ng, 0.f);
   for (int n = 0; n < nb; ++n)
     for (int g = 0; g < ng; ++g) {
       const unsigned long long mn = cn[n] - (n ? cn[n - 1] : 0ull);
       const unsigned long long mg = cg[(size_t)n * ng + g] - (g ? cg[(size_t)n * ng + g - 1] : 0ull);
       const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
       w32[(size_t)n * ng + g] = mn && mg ? (float)((ctx->w_g[g] / p) * (6.283185307179586 / 0.5)) : 0.f;
+      ctx->p0_host[(size_t)n * ng + g] = (float)p;
     }
   CK(cudaMemcpyAsync(ctx->wgt32.p, w32.data(), sizeof(float) * nb * ng, cudaMemcpyHostToDevice, s),
      "upload weights");
+  CK(ensure(ctx->p0_32, sizeof(float) * nb * ng), "alloc plain probabilities");
+  CK(cudaMemcpyAsync(ctx->p0_32.p, ctx->p0_host.data(), sizeof(float) * nb * ng, cudaMemcpyHostToDevice, s),
+     "upload plain probabilities");
+  ctx->p0_T_max = Tm;
   // guide table of the band counts: guide[m] = first band with cum > m 2^32 / G
   const int G = mcrt::fp32_guide_size();
   std::vector<unsigned short> guide(G);
@@ -214,6 +143,10 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   return MCRT_OK;
 }
 
+}  // namespace mcrt_host
+
+namespace {
+
 // Interpolation positions of the FP32 kernel; valid once both the field and the
 // tables are set (recomputed whenever either changes).
 int refresh_positions(mcrt_ctx *ctx, cudaStream_t s) {
@@ -227,6 +160,10 @@ int refresh_positions(mcrt_ctx *ctx, cudaStream_t s) {
   return MCRT_OK;
 }
 
+}  // namespace
+
+namespace mcrt_host {
+
 double proposal_T_max(const mcrt_ctx *ctx) {
   double Tm = ctx->T_max_field;
   for (int w = 0; w < 2; ++w)
@@ -234,7 +171,106 @@ double proposal_T_max(const mcrt_ctx *ctx) {
   return Tm;
 }
 
-}  // namespace
+int ensure_plain_proposal(mcrt_ctx *ctx, cudaStream_t s) {
+  const double Tm = proposal_T_max(ctx);
+  if (!ctx->prop_valid || ctx->prop_T_max != Tm || ctx->p0_T_max != Tm)
+    return build_plain_proposal(ctx, Tm, s);
+  return MCRT_OK;
+}
+
+int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
+  if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
+  if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
+  if (!(p->tol > 0.0 && p->tol < 1.0)) return fail(ctx, MCRT_E_ARG, "tol outside (0, 1)");
+  if (p->precision != MCRT_FP32 && p->precision != MCRT_FP64)
+    return fail(ctx, MCRT_E_ARG, "bad precision");
+  if (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER)
+    return fail(ctx, MCRT_E_ARG, "bad origin");
+  if (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL)
+    return fail(ctx, MCRT_E_ARG, "bad proposal");
+  if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
+    return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
+  const mcrt_grid_desc &g = ctx->grid;
+  b[0] = 0;
+  b[1] = g.nx;
+  b[2] = 0;
+  b[3] = g.ny;
+  b[4] = 0;
+  b[5] = g.nz;
+  if (p->use_box) {
+    std::memcpy(b, p->box, sizeof(int) * 6);
+    if (b[0] < 0 || b[1] > g.nx || b[0] > b[1] || b[2] < 0 || b[3] > g.ny || b[2] > b[3] ||
+        b[4] < 0 || b[5] > g.nz || b[4] > b[5])
+      return fail(ctx, MCRT_E_ARG, "box outside the grid");
+  }
+  if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
+  if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
+    return fail(ctx, MCRT_E_STATE, "no cell proposal");
+  if (p->precision == MCRT_FP32 && ctx->nT > 512)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
+  return MCRT_OK;
+}
+
+void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int b[6],
+                     mcrt::TraceArgs *ap) {
+  const mcrt_grid_desc &g = ctx->grid;
+  mcrt::TraceArgs &a = *ap;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.dx = g.lx / g.nx;
+  a.dy = g.ly / g.ny;
+  a.dz = g.lz / g.nz;
+  a.nb = ctx->nb;
+  a.ng = ctx->ng;
+  a.nT = ctx->nT;
+  a.T0 = ctx->T0;
+  a.inv_dT = 1.0 / ctx->dT;
+  a.inv_xref = 1.0 / ctx->x_ref;
+  a.eps_wall[0] = g.eps_wall[0];
+  a.eps_wall[1] = g.eps_wall[1];
+  a.reflect = g.reflect;
+  a.field32 = (const float2 *)ctx->field32.p;
+  a.fpos32 = (const uint2 *)ctx->fpos32.p;
+  a.field64 = (const double2 *)ctx->field64.p;
+  a.ktab32 = (const float2 *)ctx->ktab32.p;
+  a.ktab64 = (const double2 *)ctx->ktab64.p;
+  a.btab32 = (const float2 *)ctx->btab32.p;
+  a.btab64 = (const double2 *)ctx->btab64.p;
+  a.bwall32 = (const float *)ctx->bwall32.p;
+  a.bwall64 = (const double *)ctx->bwall64.p;
+  a.w_g = (const double *)ctx->wg.p;
+  a.wgt32 = (const float *)ctx->wgt32.p;
+  a.w_g32 = (const float *)ctx->wg32.p;
+  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
+  a.guide = (const unsigned short *)ctx->guide.p;
+  a.cn = (const unsigned long long *)ctx->cn.p;
+  a.cg = (const unsigned long long *)ctx->cg.p;
+  if (p->proposal == MCRT_PROPOSAL_CELL) {
+    a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
+    a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
+    a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
+  }
+  a.rays = p->rays_per_cell;
+  a.max_steps = p->max_steps;
+  a.origin = p->origin;
+  a.tol = p->tol;
+  a.key0 = (unsigned)(p->seed & 0xffffffffu);
+  a.key1 = (unsigned)(p->seed >> 32);
+  a.snapshot = p->snapshot;
+  a.ray_offset = p->ray_offset;
+  a.bi0 = b[0];
+  a.bj0 = b[2];
+  a.bk0 = b[4];
+  a.bnx = b[1] - b[0];
+  a.bny = b[3] - b[2];
+  a.bnz = b[5] - b[4];
+  a.ncells_box = (long long)a.bnx * a.bny * a.bnz;
+  a.counters = (unsigned long long *)ctx->counters.p;
+}
+
+}  // namespace mcrt_host
 
 extern "C" {
 
@@ -461,95 +497,20 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   if (!ctx) return MCRT_E_ARG;
   if (!p || !q_out) return fail(ctx, MCRT_E_ARG, "null params or q_out");
   if (mem != MCRT_MEM_HOST && mem != MCRT_MEM_DEVICE) return fail(ctx, MCRT_E_ARG, "bad mem");
-  if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
-  if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
-  if (!(p->tol > 0.0 && p->tol < 1.0)) return fail(ctx, MCRT_E_ARG, "tol outside (0, 1)");
-  if (p->precision != MCRT_FP32 && p->precision != MCRT_FP64)
-    return fail(ctx, MCRT_E_ARG, "bad precision");
-  if (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER)
-    return fail(ctx, MCRT_E_ARG, "bad origin");
-  if (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL)
-    return fail(ctx, MCRT_E_ARG, "bad proposal");
-  if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
-    return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
-  const mcrt_grid_desc &g = ctx->grid;
-  int b[6] = {0, g.nx, 0, g.ny, 0, g.nz};
-  if (p->use_box) {
-    std::memcpy(b, p->box, sizeof(b));
-    if (b[0] < 0 || b[1] > g.nx || b[0] > b[1] || b[2] < 0 || b[3] > g.ny || b[2] > b[3] ||
-        b[4] < 0 || b[5] > g.nz || b[4] > b[5])
-      return fail(ctx, MCRT_E_ARG, "box outside the grid");
-  }
-  if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
-  if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
-    return fail(ctx, MCRT_E_STATE, "no cell proposal");
-  if (p->precision == MCRT_FP32 && ctx->nT > 512)
-    return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
-  DeviceGuard dg(g.device);
+  int b[6];
+  const int rc0 = check_solve_params(ctx, p, b);
+  if (rc0 != MCRT_OK) return rc0;
+  DeviceGuard dg(ctx->grid.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
 
-  const double Tm = proposal_T_max(ctx);
-  if (!ctx->prop_valid || ctx->prop_T_max != Tm) {
-    const int rc = build_plain_proposal(ctx, Tm, s);
-    if (rc != MCRT_OK) return rc;
-  }
+  const int rcp = ensure_plain_proposal(ctx, s);
+  if (rcp != MCRT_OK) return rcp;
+  const double Tm = ctx->prop_T_max;
   const long long nbox = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
 
   mcrt::TraceArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.nz = g.nz;
-  a.dx = g.lx / g.nx;
-  a.dy = g.ly / g.ny;
-  a.dz = g.lz / g.nz;
-  a.nb = ctx->nb;
-  a.ng = ctx->ng;
-  a.nT = ctx->nT;
-  a.T0 = ctx->T0;
-  a.inv_dT = 1.0 / ctx->dT;
-  a.inv_xref = 1.0 / ctx->x_ref;
-  a.eps_wall[0] = g.eps_wall[0];
-  a.eps_wall[1] = g.eps_wall[1];
-  a.reflect = g.reflect;
-  a.field32 = (const float2 *)ctx->field32.p;
-  a.fpos32 = (const uint2 *)ctx->fpos32.p;
-  a.field64 = (const double2 *)ctx->field64.p;
-  a.ktab32 = (const float2 *)ctx->ktab32.p;
-  a.ktab64 = (const double2 *)ctx->ktab64.p;
-  a.btab32 = (const float2 *)ctx->btab32.p;
-  a.btab64 = (const double2 *)ctx->btab64.p;
-  a.bwall32 = (const float *)ctx->bwall32.p;
-  a.bwall64 = (const double *)ctx->bwall64.p;
-  a.w_g = (const double *)ctx->wg.p;
-  a.wgt32 = (const float *)ctx->wgt32.p;
-  a.w_g32 = (const float *)ctx->wg32.p;
-  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
-  a.guide = (const unsigned short *)ctx->guide.p;
-  a.cn = (const unsigned long long *)ctx->cn.p;
-  a.cg = (const unsigned long long *)ctx->cg.p;
-  if (p->proposal == MCRT_PROPOSAL_CELL) {
-    a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
-    a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
-    a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
-  }
-  a.rays = p->rays_per_cell;
-  a.max_steps = p->max_steps;
-  a.origin = p->origin;
-  a.tol = p->tol;
-  a.key0 = (unsigned)(p->seed & 0xffffffffu);
-  a.key1 = (unsigned)(p->seed >> 32);
-  a.snapshot = p->snapshot;
-  a.ray_offset = p->ray_offset;
-  a.bi0 = b[0];
-  a.bj0 = b[2];
-  a.bk0 = b[4];
-  a.bnx = b[1] - b[0];
-  a.bny = b[3] - b[2];
-  a.bnz = b[5] - b[4];
-  a.ncells_box = nbox;
-  a.counters = (unsigned long long *)ctx->counters.p;
+  fill_trace_args(ctx, p, b, &a);
 
   double *dq = q_out, *ds = sigma_out;
   unsigned long long *dst = (unsigned long long *)p->steps_out;
@@ -678,7 +639,8 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
-                      &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps};
+                      &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
+                      &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

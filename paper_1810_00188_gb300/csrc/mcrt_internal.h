@@ -2,6 +2,7 @@
 // kernels (trace.cu, fields.cu).  Not installed; not part of the ABI.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,6 +43,9 @@ struct TraceArgs {
   long long chunk_p0, chunk_p1;
   float *ybuf;
   unsigned long long *step_acc;
+  // per-ray step counts, same indexing as ybuf (null: not stored); read by the
+  // second-moment tally of the learned proposal
+  unsigned *ray_steps;
   // batched runs: ray_offset read from device memory (set before each graph
   // replay) when non-null; persistent grid size override (0: one full wave)
   const unsigned long long *ray_offset_dev;
@@ -88,6 +92,99 @@ cudaError_t noalloc_scratch(int device, void **out);
 // Packs each cell's interpolation position for the FP32 kernel (nT <= 512).
 cudaError_t launch_pack_positions(const double2 *f64, long long n, double T0, double inv_dT, int nT,
                                   double inv_xref, uint2 *pos, cudaStream_t s);
+
+// ---- learned proposal (learn.cu) ----
+constexpr int kNFeat = 12, kNHidden = 64;
+constexpr int kMaxTrainOut = 352;   // n_out (spectral points + 2) limit of the training kernel
+constexpr int kMaxTallyK = 1024;    // spectral points limit of the tally kernel
+
+struct FeatArgs {
+  int nx, ny, nz;
+  double dx, dy, dz, h;
+  double T_wall[2], eps_wall[2], T_max;
+  const double2 *field64;
+  const uint2 *fpos32;
+  const float2 *ktab32, *btab32;
+  const float *w_g32;
+  int nb, ng, nT;
+  const int *cells;  // null: cells 0..n-1
+  long long n;
+  float *out;        // [n][12]
+  unsigned long long *err;
+};
+cudaError_t launch_features(const FeatArgs &f, cudaStream_t s);
+
+struct TallyArgs {
+  const int *cells;
+  long long n;
+  int nx, ny, nz;
+  long long chunk_p0, chunk_p1;
+  const float *ybuf;
+  const unsigned *ray_steps;
+  int N;
+  unsigned key0, key1, snapshot;
+  unsigned long long ray_off;
+  const unsigned long long *cn, *cg;            // plain proposal
+  const unsigned long long *cell_cn, *cell_cg;  // or per-cell proposal
+  const unsigned *cell_hemi;
+  int nb, ng;
+  float *m_out, *c_out;  // [n][nb*ng][2]
+  unsigned long long *err;
+};
+cudaError_t launch_tally(const TallyArgs &t, cudaStream_t s);
+
+// theta layout: W1 [64][12], b1 [64], W2 [64][64], b2 [64], W3 [K+2][64], b3 [K+2]
+long long mlp_nparams(int K);
+
+struct MlpInferArgs {
+  const __half *theta16;
+  const float *fmean, *finv;  // [12]
+  int K;
+  const float *feat;          // [n][12]
+  long long n;
+  const float *p0;            // [K] (p0_stride 0) or [n][K]
+  int p0_stride;
+  float mix;
+  float *q_out;               // [n][K+2] or null
+  // or quantised straight into a per-cell proposal (cells 0..n-1)
+  unsigned long long *cell_cn, *cell_cg;
+  unsigned *cell_hemi;
+  int nb, ng;
+  unsigned long long *err;
+};
+cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t s);
+
+// Quantises per-cell probabilities q [n][K+2] (spectral points, then q_up) into
+// cumulative counts (same rule as the host's plain proposal).
+cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
+                                  unsigned long long *cell_cn, unsigned long long *cell_cg,
+                                  unsigned *cell_hemi, unsigned long long *err, cudaStream_t s);
+
+struct MlpTrainArgs {
+  const __half *theta16;
+  const float *fmean, *finv;
+  int K;
+  const float *feat, *mom, *cost;  // [N][12], [N][K][2], [N][K][2] or null
+  float c0;
+  const float *p0;                 // [N][K] or [K]
+  int p0_stride;
+  const int *idx;                  // batch -> sample, or null (sample = batch index)
+  long long n_data;                // samples in the dataset (idx must stay below)
+  long long n;                     // batch size
+  float mix;
+  float *partial;                  // [grid][nparams]
+  double *loss_partial;            // [grid]
+  int grid;
+  unsigned long long *err;         // set when an index is outside the dataset
+};
+cudaError_t launch_mlp_train(const MlpTrainArgs &a, cudaStream_t s);
+cudaError_t launch_grad_reduce(const float *partial, const double *loss_partial, int grid,
+                               long long np, float *grad, double *loss, cudaStream_t s);
+cudaError_t launch_adam(float *theta, __half *theta16, const float *grad, float *m1, float *m2,
+                        long long np, float lr, float beta1, float beta2, float eps, float c1,
+                        float c2, cudaStream_t s);
+cudaError_t launch_theta_to_half(const float *theta, __half *theta16, long long np, cudaStream_t s);
+int mlp_train_grid();
 
 cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
                                long long n, double2 *f64, float2 *f32,

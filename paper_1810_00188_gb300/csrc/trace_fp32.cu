@@ -32,6 +32,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "draws.cuh"
 #include "mcrt_internal.h"
 
 namespace mcrt {
@@ -48,20 +49,6 @@ struct WarpRing {
   uint4 C[POOL];   // n | g << 16, Philox ray index, axis signs, emitting cell (linear)
   int4 D[POOL];    // sample slot (cell position in the chunk), ix, iy, iz
 };
-
-__device__ __forceinline__ uint4 philox10(uint4 c, unsigned k0, unsigned k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
 
 // Exact bit constructions instead of conversion instructions:
 //  * uniform (w>>9 + 1/2) 2^-23: the 23 draw bits as the mantissa of a number in
@@ -115,18 +102,6 @@ __device__ __forceinline__ int pick_guided(const unsigned long long *__restrict_
   int k = guide[u >> 26];
   while ((unsigned long long)u >= cum[k]) ++k;
   return k;
-}
-
-__device__ __forceinline__ int pick(const unsigned long long *__restrict__ cum, int K, unsigned u) {
-  int lo = 0, hi = K - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if ((unsigned long long)u < cum[mid])
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  return lo;
 }
 
 __device__ __forceinline__ void absorb(float x, float &alpha, float &trans) {
@@ -516,6 +491,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
         Ybuf[(size_t)slot * (unsigned)N + r] = scale * X;  // the ray's sample Y (Eq. 14)
+        if (a.ray_steps) a.ray_steps[(size_t)slot * (unsigned)N + r] = (unsigned)steps;
         if (a.steps_cell) {
           if ((int)slot != acc_slot) {
             if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);

@@ -1,0 +1,182 @@
+"""Training driver of the learned proposal.
+
+Host orchestration only: the tallies, features, forward/backward passes, the
+gradient reduction and Adam all run in the library's kernels through the C ABI;
+this module picks the fields, the cells and the batches (seeded), and keeps the
+device tensors the kernels read.
+
+Training data (one sample per tallied cell): the 12 features, the second-moment
+tallies m [K][2] and cost tallies c [K][2] of a plain FP32 solve, and the plain
+pdf p0 [K] of the sample's field.  The loss per sample is
+A(q) C(q) / (A(p0) C(p0)) with A(q) = sum m / (q_k q_h) (the second moment of the
+estimate per ray under q) and C(q) = c0 + sum c q_k q_h (the ray's cost in
+steps, c0 its fixed part); its mean over a batch is what one Adam step lowers.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import inputs, mcrt
+
+
+@dataclasses.dataclass
+class Dataset:
+    feat: object        # torch [N, 12] float32, cuda
+    mom: object         # torch [N, K, 2]
+    cost: object        # torch [N, K, 2]
+    p0: object          # torch [N, K]
+    K: int
+    fields: int
+
+    @property
+    def n(self) -> int:
+        return int(self.feat.shape[0])
+
+
+def tally_field(S, rays, seed, snapshot, cells, stream=0):
+    """Features, tallies and p0 rows of `cells` (torch int32 cuda) of the
+    context's current fields."""
+    import torch
+    feat = S.features(cells, stream=stream)
+    p = S.params(rays=rays, seed=seed, snapshot=snapshot, precision=mcrt.MCRT_FP32)
+    mom, cost = S.tally(p, cells, stream=stream)
+    p0 = torch.tensor(S.plain_probs(), device=feat.device)
+    return feat, mom, cost, p0.expand(cells.shape[0], -1)
+
+
+def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per_field=4096,
+                  kdist_seed=0, x_mode="field", sample_seed=0, stream=0):
+    """Tallies of `cells_per_field` random cells of each seeded channel field."""
+    import torch
+    nx, ny, nz = grid_shape
+    feats, moms, costs, p0s = [], [], [], []
+    rng = np.random.default_rng(sample_seed)
+    S = None
+    kd = None
+    for s in seeds:
+        grid, kd_s, T, x = inputs.nongrey_channel(nx, ny, nz, seed=int(s), kdist_seed=kdist_seed,
+                                                  x_mode=x_mode)
+        if S is None:
+            kd = kd_s
+            S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=stream)
+        n = min(cells_per_field, grid.ncells)
+        cells = torch.tensor(np.sort(rng.choice(grid.ncells, n, replace=False)).astype(np.int32),
+                             device="cuda")
+        f, m, c, p = tally_field(S, rays, seed=1000 + int(s), snapshot=int(s), cells=cells,
+                                 stream=stream)
+        feats.append(f)
+        moms.append(m)
+        costs.append(c)
+        p0s.append(p.contiguous())
+    S.close()
+    K = kd.n_bands * kd.n_g
+    return Dataset(torch.cat(feats), torch.cat(moms), torch.cat(costs), torch.cat(p0s), K,
+                   len(feats))
+
+
+def feature_norm(ds: Dataset):
+    """Mean and 1/std of each feature over the dataset (constant features get 1)."""
+    f = ds.feat.double().cpu().numpy()
+    mean = f.mean(axis=0)
+    std = f.std(axis=0)
+    inv = np.where(std > 1e-6 * np.maximum(np.abs(mean), 1.0), 1.0 / np.maximum(std, 1e-30), 1.0)
+    return mean.astype(np.float32), inv.astype(np.float32)
+
+
+def init_theta(K, p0_mean, seed=0, scale=1.0):
+    """He-style random weights; the spectral biases start at log p0 (so the
+    untrained network proposes the mean plain pdf), the hemisphere ones at 0."""
+    H, F = mcrt.MCRT_NHIDDEN, mcrt.MCRT_NFEAT
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(scale=scale * math.sqrt(2.0 / F), size=(H, F))
+    W2 = rng.normal(scale=scale * math.sqrt(2.0 / H), size=(H, H))
+    W3 = rng.normal(scale=0.1 * scale * math.sqrt(1.0 / H), size=(K + 2, H))
+    b3 = np.zeros(K + 2)
+    b3[:K] = np.log(np.maximum(np.asarray(p0_mean, dtype=np.float64), 1e-12))
+    b3[:K] -= b3[:K].max()
+    theta = np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(), b3])
+    assert theta.size == mcrt.mcrt_mlp_nparams(K)
+    return theta.astype(np.float32)
+
+
+def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=8.0, mix=0.1, seed=0,
+          log_every=0, stream=0, use_cost=True):
+    """Adam on the mean work-ratio loss over random batches.  Returns the losses
+    at the logged steps (and the last one)."""
+    import torch
+    if batch is None:
+        batch = 16 * torch.cuda.get_device_properties(0).multi_processor_count * 2
+    rng = np.random.default_rng(seed)
+    losses = []
+    perm = None
+    pos = ds.n
+    for it in range(steps):
+        if pos + batch > ds.n:
+            perm = torch.tensor(rng.permutation(ds.n).astype(np.int32), device=ds.feat.device)
+            pos = 0
+        idx = perm[pos:pos + min(batch, ds.n)]
+        pos += batch
+        mlp.loss_grad(ds.feat, ds.mom, ds.p0, cost=ds.cost if use_cost else None, c0=c0, idx=idx,
+                      mix=mix, stream=stream)
+        mlp.adam(lr=lr, stream=stream)
+        if (log_every and it % log_every == 0) or it == steps - 1:
+            losses.append((it, mlp.last_loss()))
+    return losses
+
+
+def mean_loss(mlp, ds: Dataset, c0=8.0, mix=0.1, stream=0, use_cost=True):
+    """Loss over the whole dataset (no update)."""
+    mlp.loss_grad(ds.feat, ds.mom, ds.p0, cost=ds.cost if use_cost else None, c0=c0, mix=mix,
+                  stream=stream)
+    return mlp.last_loss()
+
+
+def rel_sigma_p95(q, s):
+    """95th percentile over cells of sigma / max(|Q|, 0.05 mean |Q|) (the
+    per-cell 1% criterion)."""
+    q = np.asarray(q).reshape(-1)
+    s = np.asarray(s).reshape(-1)
+    ref = np.maximum(np.abs(q), 0.05 * np.mean(np.abs(q)))
+    return float(np.percentile(s / ref, 95))
+
+
+def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0):
+    """Plain and learned FP32 solves of the context's fields at `rays` per cell:
+    kernel time, p95 relative sigma, and the projected GPU time to reach 1%
+    (time x (p95 / 0.01)^2, the estimator's 1/N law)."""
+    import torch
+    shape = S.box_shape(None)
+    dev = f"cuda:{S.device}"
+    q = torch.empty(shape, dtype=torch.float64, device=dev)
+    s = torch.empty_like(q)
+    out = {}
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    S.set_learned_proposal(mlp, mix=mix, stream=stream)
+    t1.record()
+    torch.cuda.synchronize()
+    out["proposal_ms"] = t0.elapsed_time(t1)
+    for name, prop in (("plain", mcrt.MCRT_PROPOSAL_PLANCK_TMAX), ("learned", mcrt.MCRT_PROPOSAL_CELL)):
+        times, p95 = [], []
+        steps = 0
+        for r in range(reps):
+            p = S.params(rays=rays, seed=seed, ray_offset=r * rays, precision=mcrt.MCRT_FP32,
+                         proposal=prop)
+            S.solve_into(p, q, s, stream=stream)
+            st = S.stats()
+            times.append(st["kernel_ms"])
+            steps += st["steps"]
+            p95.append(rel_sigma_p95(q.cpu().numpy(), s.cpu().numpy()))
+        t = float(np.median(times))
+        pr = float(np.median(p95))
+        out[name] = {"kernel_ms": t, "p95_rel_sigma": pr,
+                     "steps_per_ray": steps / (reps * rays * S.grid.ncells),
+                     "ms_to_1pct": t * (pr / 0.01) ** 2}
+    out["speedup_to_1pct"] = out["plain"]["ms_to_1pct"] / out["learned"]["ms_to_1pct"]
+    return out

@@ -78,7 +78,14 @@ EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_pr
            "mcrt_solve_qrad", "mcrt_get_stats", "mcrt_destroy", "mcrt_status_string",
            "mcrt_last_error", "mcrt_set_tuning", "mcrt_get_tuning", "mcrt_solve_qrad_noalloc",
            "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_get_stats", "mcrt_batch_last_error",
-           "mcrt_batch_destroy")
+           "mcrt_batch_destroy", "mcrt_mlp_nparams", "mcrt_mlp_create", "mcrt_mlp_set_params",
+           "mcrt_mlp_get_params", "mcrt_mlp_forward", "mcrt_mlp_loss_grad", "mcrt_mlp_adam_step",
+           "mcrt_mlp_last_loss", "mcrt_mlp_last_error", "mcrt_mlp_destroy", "mcrt_cell_features",
+           "mcrt_tally_moments", "mcrt_get_plain_probs", "mcrt_set_cell_proposal_probs",
+           "mcrt_get_cell_proposal", "mcrt_set_learned_proposal")
+_NOT_INT = ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error", "mcrt_mlp_last_error",
+            "mcrt_mlp_nparams")
+MCRT_NFEAT, MCRT_NHIDDEN = 12, 64
 
 
 def library_path() -> str:
@@ -120,8 +127,27 @@ def load(build_if_missing: bool = True):
         L.mcrt_batch_last_error.argtypes = [vp]
         L.mcrt_batch_last_error.restype = C.c_char_p
         L.mcrt_batch_destroy.argtypes = [vp]
+        i64, f32 = C.c_int64, C.c_float
+        L.mcrt_mlp_nparams.argtypes = [C.c_int]
+        L.mcrt_mlp_nparams.restype = i64
+        L.mcrt_mlp_create.argtypes = [C.c_int, C.c_int, C.POINTER(vp)]
+        L.mcrt_mlp_set_params.argtypes = [vp, vp, vp, vp]
+        L.mcrt_mlp_get_params.argtypes = [vp, vp, vp]
+        L.mcrt_mlp_forward.argtypes = [vp, vp, i64, vp, C.c_int, f32, vp, vp]
+        L.mcrt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, f32, vp, C.c_int, i64, vp, i64, f32, vp, vp]
+        L.mcrt_mlp_adam_step.argtypes = [vp, vp, f32, f32, f32, f32, vp]
+        L.mcrt_mlp_last_loss.argtypes = [vp, C.POINTER(C.c_double)]
+        L.mcrt_mlp_last_error.argtypes = [vp]
+        L.mcrt_mlp_last_error.restype = C.c_char_p
+        L.mcrt_mlp_destroy.argtypes = [vp]
+        L.mcrt_cell_features.argtypes = [vp, vp, i64, vp, vp]
+        L.mcrt_tally_moments.argtypes = [vp, C.POINTER(mcrt_solve_params), vp, i64, vp, vp, vp, vp, vp]
+        L.mcrt_get_plain_probs.argtypes = [vp, vp]
+        L.mcrt_set_cell_proposal_probs.argtypes = [vp, vp, vp]
+        L.mcrt_get_cell_proposal.argtypes = [vp, vp, vp, vp]
+        L.mcrt_set_learned_proposal.argtypes = [vp, vp, f32, vp]
         for f in EXPORTS:
-            if f not in ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error"):
+            if f not in _NOT_INT:
                 getattr(L, f).restype = C.c_int
         _lib = L
         return _lib
@@ -232,6 +258,146 @@ def mcrt_status_string(status: int) -> str:
 
 
 # --- convenience wrapper ----------------------------------------------------------
+
+# --- learned proposal ------------------------------------------------------------
+
+def _mcheck(rc, m):
+    if rc != MCRT_OK:
+        raise McrtError(rc, load().mcrt_mlp_last_error(m).decode() if m else "")
+
+
+def mcrt_mlp_nparams(K: int) -> int:
+    return int(load().mcrt_mlp_nparams(K))
+
+
+def mcrt_mlp_create(device: int, K: int):
+    h = C.c_void_p()
+    _check(load().mcrt_mlp_create(device, K, C.byref(h)))
+    return h
+
+
+def mcrt_mlp_set_params(m, theta, feat_mean, feat_inv_std):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    fm = np.ascontiguousarray(feat_mean, dtype=np.float32)
+    fi = np.ascontiguousarray(feat_inv_std, dtype=np.float32)
+    _mcheck(load().mcrt_mlp_set_params(m, _ptr(theta), _ptr(fm), _ptr(fi)), m)
+
+
+def mcrt_mlp_get_params(m, K: int, used: bool = False):
+    n = mcrt_mlp_nparams(K)
+    th = np.zeros(n, dtype=np.float32)
+    tu = np.zeros(n, dtype=np.float32) if used else None
+    _mcheck(load().mcrt_mlp_get_params(m, _ptr(th), _ptr(tu)), m)
+    return (th, tu) if used else th
+
+
+def mcrt_mlp_forward(m, feat_ptr, n: int, p0_ptr, p0_stride: int, mix: float, q_ptr, stream=0):
+    _mcheck(load().mcrt_mlp_forward(m, feat_ptr, n, p0_ptr, p0_stride, mix, q_ptr, stream), m)
+
+
+def mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0: float, p0_ptr, p0_stride: int,
+                       n_data: int, idx_ptr, n: int, mix: float, grad_ptr=None, stream=0):
+    _mcheck(load().mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0, p0_ptr, p0_stride, n_data,
+                                      idx_ptr, n, mix, grad_ptr, stream), m)
+
+
+def mcrt_mlp_adam_step(m, grad_ptr=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _mcheck(load().mcrt_mlp_adam_step(m, grad_ptr, lr, beta1, beta2, eps, stream), m)
+
+
+def mcrt_mlp_last_loss(m) -> float:
+    v = C.c_double()
+    _mcheck(load().mcrt_mlp_last_loss(m, C.byref(v)), m)
+    return v.value
+
+
+def mcrt_mlp_destroy(m):
+    load().mcrt_mlp_destroy(m)
+
+
+def mcrt_cell_features(ctx, cells_ptr, n: int, out_ptr, stream=0):
+    _check(load().mcrt_cell_features(ctx, cells_ptr, n, out_ptr, stream), ctx)
+
+
+def mcrt_tally_moments(ctx, params, cells_ptr, n: int, mom_ptr, cost_ptr, q_ptr=None,
+                       sigma_ptr=None, stream=0):
+    _check(load().mcrt_tally_moments(ctx, C.byref(params), cells_ptr, n, mom_ptr, cost_ptr, q_ptr,
+                                     sigma_ptr, stream), ctx)
+
+
+def mcrt_get_plain_probs(ctx, K: int):
+    p0 = np.zeros(K, dtype=np.float32)
+    _check(load().mcrt_get_plain_probs(ctx, _ptr(p0)), ctx)
+    return p0
+
+
+def mcrt_set_cell_proposal_probs(ctx, q_ptr, stream=0):
+    _check(load().mcrt_set_cell_proposal_probs(ctx, q_ptr, stream), ctx)
+
+
+def mcrt_get_cell_proposal(ctx, ncells: int, nb: int, ng: int):
+    cn = np.zeros((ncells, nb), dtype=np.uint64)
+    cg = np.zeros((ncells, nb, ng), dtype=np.uint64)
+    hemi = np.zeros(ncells, dtype=np.uint32)
+    _check(load().mcrt_get_cell_proposal(ctx, _ptr(cn), _ptr(cg), _ptr(hemi)), ctx)
+    return cn, cg, hemi
+
+
+def mcrt_set_learned_proposal(ctx, m, mix: float = 0.1, stream=0):
+    _check(load().mcrt_set_learned_proposal(ctx, m, mix, stream), ctx)
+
+
+class Mlp:
+    """The proposal network (device-resident FP32 master weights, FP16 copy,
+    Adam state).  Arrays passed to the methods are torch CUDA tensors."""
+
+    def __init__(self, K: int, device: int = 0):
+        self.K = K
+        self.device = device
+        self.handle = mcrt_mlp_create(device, K)
+        self.nparams = mcrt_mlp_nparams(K)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mcrt_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta, feat_mean=None, feat_inv_std=None):
+        fm = np.zeros(MCRT_NFEAT) if feat_mean is None else feat_mean
+        fi = np.ones(MCRT_NFEAT) if feat_inv_std is None else feat_inv_std
+        mcrt_mlp_set_params(self.handle, theta, fm, fi)
+
+    def params(self, used: bool = False):
+        return mcrt_mlp_get_params(self.handle, self.K, used)
+
+    def forward(self, feat, p0, mix=0.1, out=None, stream=0):
+        import torch
+        n = feat.shape[0]
+        if out is None:
+            out = torch.empty((n, self.K + 2), dtype=torch.float32, device=feat.device)
+        stride = 0 if p0.dim() == 1 else self.K
+        mcrt_mlp_forward(self.handle, _ptr(feat), n, _ptr(p0), stride, mix, _ptr(out), stream)
+        return out
+
+    def loss_grad(self, feat, mom, p0, cost=None, c0=0.0, idx=None, n=None, mix=0.1, grad=None,
+                  stream=0):
+        n = (idx.shape[0] if idx is not None else feat.shape[0]) if n is None else n
+        stride = 0 if p0.dim() == 1 else self.K
+        mcrt_mlp_loss_grad(self.handle, _ptr(feat), _ptr(mom), _ptr(cost), c0, _ptr(p0), stride,
+                           feat.shape[0], _ptr(idx), n, mix, _ptr(grad), stream)
+
+    def adam(self, grad=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+        mcrt_mlp_adam_step(self.handle, _ptr(grad), lr, beta1, beta2, eps, stream)
+
+    def last_loss(self) -> float:
+        return mcrt_mlp_last_loss(self.handle)
+
 
 def _ptr(a):
     """Device pointer of a torch tensor or host pointer of a numpy array."""
@@ -356,3 +522,40 @@ class Solver:
 
     def tuning(self) -> dict:
         return mcrt_get_tuning(self.ctx)
+
+    # learned proposal
+    def features(self, cells=None, out=None, stream: int = 0):
+        """Features [n, 12] (torch CUDA float32) of cells (torch int32, or None: all)."""
+        import torch
+        n = self.grid.ncells if cells is None else cells.shape[0]
+        if out is None:
+            out = torch.empty((n, MCRT_NFEAT), dtype=torch.float32, device=f"cuda:{self.device}")
+        mcrt_cell_features(self.ctx, _ptr(cells), n, _ptr(out), stream)
+        return out
+
+    def tally(self, params, cells, mom=None, cost=None, q=None, sigma=None, stream: int = 0):
+        """Second-moment and cost tallies [n, K, 2] of the listed cells from one
+        FP32 solve (whole grid)."""
+        import torch
+        K = self.kd.n_bands * self.kd.n_g
+        n = cells.shape[0]
+        dev = f"cuda:{self.device}"
+        if mom is None:
+            mom = torch.empty((n, K, 2), dtype=torch.float32, device=dev)
+        if cost is None:
+            cost = torch.empty((n, K, 2), dtype=torch.float32, device=dev)
+        mcrt_tally_moments(self.ctx, params, _ptr(cells), n, _ptr(mom), _ptr(cost), _ptr(q),
+                           _ptr(sigma), stream)
+        return mom, cost
+
+    def plain_probs(self):
+        return mcrt_get_plain_probs(self.ctx, self.kd.n_bands * self.kd.n_g)
+
+    def set_cell_proposal_probs(self, q, stream: int = 0):
+        mcrt_set_cell_proposal_probs(self.ctx, _ptr(q), stream)
+
+    def cell_proposal(self):
+        return mcrt_get_cell_proposal(self.ctx, self.grid.ncells, self.kd.n_bands, self.kd.n_g)
+
+    def set_learned_proposal(self, mlp, mix=0.1, stream: int = 0):
+        mcrt_set_learned_proposal(self.ctx, mlp.handle, mix, stream)

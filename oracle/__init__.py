@@ -102,8 +102,8 @@ def lib():
             L.orc_mlp_nparams.argtypes = [C.c_int]
             L.orc_mlp_nparams.restype = i64
             L.orc_mlp_forward.argtypes = [dp, C.c_int, dp, dp, dp, i64, dp, C.c_int, C.c_double, dp]
-            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, C.c_double, dp, i64,
-                                            C.c_double, dp, dp]
+            L.orc_mlp_loss_grad.argtypes = [dp, C.c_int, dp, dp, dp, dp, dp, C.c_double, dp, dp,
+                                            C.c_int, i64, C.c_double, dp, dp]
             L.orc_adam.argtypes = [dp, dp, dp, dp, i64, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_int]
             L.orc_learned_counts.argtypes = [dp, C.c_int, C.c_int, C.c_double, up, up,
@@ -377,20 +377,25 @@ def mlp_forward(theta, K, fmean, finv, feat, p0, mix=0.1):
     return q
 
 
-def mlp_loss_grad(theta, K, fmean, finv, feat, m, p0, mix=0.1, cost=None, c0=0.0):
-    """(mean work-ratio loss, gradient [nparams]); m, cost [n, K, 2] (cost None:
-    second moment only), p0 [n, K]."""
+def mlp_loss_grad(theta, K, fmean, finv, feat, m, p0, mix=0.1, cost=None, c0=0.0, wgt=None,
+                  mode=0):
+    """(loss, gradient [nparams]); m, cost [n, K, 2] (cost None: second moment
+    only), p0 [n, K].  mode 0: mean over samples of the per-cell work ratio;
+    mode 1: the batch time ratio with sample weights wgt [n] (None: 1)."""
     theta, fmean, finv = _f64(theta), _f64(fmean), _f64(finv)
     feat = _f64(feat).reshape(-1, NFEAT)
     n = feat.shape[0]
     m = _f64(m).reshape(n, K, 2)
     p0 = _f64(p0).reshape(n, K)
     cst = None if cost is None else _f64(cost).reshape(n, K, 2)
+    w = None if wgt is None else _f64(wgt).reshape(n)
     grad = np.zeros(mlp_nparams(K))
     loss = C.c_double()
+    null = C.POINTER(C.c_double)()
     rc = lib().orc_mlp_loss_grad(_dp(theta), K, _dp(fmean), _dp(finv), _dp(feat), _dp(m),
-                                 _dp(cst) if cst is not None else C.POINTER(C.c_double)(),
-                                 float(c0), _dp(p0), n, float(mix), C.byref(loss), _dp(grad))
+                                 _dp(cst) if cst is not None else null, float(c0), _dp(p0),
+                                 _dp(w) if w is not None else null, int(mode), n, float(mix),
+                                 C.byref(loss), _dp(grad))
     if rc != 0:
         raise ValueError("orc_mlp_loss_grad failed")
     return loss.value, grad

@@ -24,6 +24,14 @@
  * the fixed cost of a ray in steps.  Without cost tallies C = 1; the minimiser
  * of A alone over all pdfs is q proportional to sqrt(m).
  *
+ * The batch form (mode 1) estimates the ratio of the GPU time a whole field
+ * needs for a given relative error: with per-sample weights w_c = 1/ref_c^2
+ * (ref_c the cell's error scale),
+ *
+ *   L = (sum_c w_c A_c(q) / sum_c w_c A_c(p0)) (sum_c C_c(q) / sum_c C_c(p0)):
+ *
+ * the mean relative second moment per ray times the mean cost per ray.
+ *
  * Everything here is written from those definitions: no blocking or reordering
  * beyond the plain loops.  It shares no code with the CUDA library.
  */
@@ -213,16 +221,92 @@ int orc_mlp_forward(const double *theta, int K, const double *fmean, const doubl
  * factor), p0 [n][K].  A sample whose plain second moment is zero contributes
  * nothing; terms with p0_k = 0 are left out (that spectral point is never drawn
  * by the plain proposal, so its tallies are zero). */
+/* Per-sample A(q), A(p0), C(q), C(p0) of sample c and dL/dq via the multipliers
+ * gA = dL/dA_c(q), gC = dL/dC_c(q) (chain rule through the mixtures and the two
+ * softmaxes, then layer by layer); adds the parameter gradient to grad. */
+static void sample_terms(const mlp_act *A, int K, const double *mc, const double *cc, double c0,
+                         const double *pc, double mix, double *q, double *Aq, double *A0, double *Cq,
+                         double *C0) {
+  for (int k = 0; k < K; ++k) q[k] = (1.0 - mix) * A->s[k] + mix * pc[k];
+  q[K] = (1.0 - mix) * A->s[K] + mix * 0.5;
+  q[K + 1] = (1.0 - mix) * A->s[K + 1] + mix * 0.5;
+  *A0 = 0.0;
+  *Aq = 0.0;
+  *C0 = c0;
+  *Cq = c0;
+  for (int k = 0; k < K; ++k) {
+    if (!(pc[k] > 0.0)) continue;
+    for (int hh = 0; hh < 2; ++hh) {
+      *A0 += mc[k * 2 + hh] / (pc[k] * 0.5);
+      *Aq += mc[k * 2 + hh] / (q[k] * q[K + hh]);
+      if (cc) {
+        *C0 += cc[k * 2 + hh] * (pc[k] * 0.5);
+        *Cq += cc[k * 2 + hh] * (q[k] * q[K + hh]);
+      }
+    }
+  }
+  if (!cc) *C0 = *Cq = 1.0;
+}
+
+static void sample_backward(const double *theta, int K, const mlp_act *A, const double *mc,
+                            const double *cc, const double *pc, double mix, const double *q,
+                            double gA, double gC, double *dz, double *gq, double *grad) {
+  const double *W2 = theta + H * F + H, *W3 = W2 + H * H + H;
+  double *gW1 = grad, *gb1 = gW1 + H * F, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H,
+         *gb3 = gW3 + (size_t)(K + 2) * H;
+  gq[K] = gq[K + 1] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    gq[k] = 0.0;
+    if (!(pc[k] > 0.0)) continue;
+    for (int hh = 0; hh < 2; ++hh) {
+      const double v = mc[k * 2 + hh];
+      gq[k] -= gA * v / (q[k] * q[k] * q[K + hh]);
+      gq[K + hh] -= gA * v / (q[k] * q[K + hh] * q[K + hh]);
+      if (cc) {
+        gq[k] += gC * cc[k * 2 + hh] * q[K + hh];
+        gq[K + hh] += gC * cc[k * 2 + hh] * q[k];
+      }
+    }
+  }
+  double dot = 0.0;
+  for (int k = 0; k < K; ++k) dot += A->s[k] * gq[k];
+  for (int k = 0; k < K; ++k) dz[k] = (1.0 - mix) * A->s[k] * (gq[k] - dot);
+  const double doth = A->s[K] * gq[K] + A->s[K + 1] * gq[K + 1];
+  dz[K] = (1.0 - mix) * A->s[K] * (gq[K] - doth);
+  dz[K + 1] = (1.0 - mix) * A->s[K + 1] * (gq[K + 1] - doth);
+  double dh2[H], da2[H], dh1[H], da1[H];
+  for (int i = 0; i < H; ++i) dh2[i] = 0.0;
+  for (int o = 0; o < K + 2; ++o) {
+    gb3[o] += dz[o];
+    for (int i = 0; i < H; ++i) {
+      gW3[(size_t)o * H + i] += dz[o] * A->h2[i];
+      dh2[i] += W3[(size_t)o * H + i] * dz[o];
+    }
+  }
+  for (int i = 0; i < H; ++i) da2[i] = dh2[i] * gelu_prime(A->a2[i]);
+  for (int i = 0; i < H; ++i) dh1[i] = 0.0;
+  for (int o = 0; o < H; ++o) {
+    gb2[o] += da2[o];
+    for (int i = 0; i < H; ++i) {
+      gW2[o * H + i] += da2[o] * A->h1[i];
+      dh1[i] += W2[o * H + i] * da2[o];
+    }
+  }
+  for (int i = 0; i < H; ++i) da1[i] = dh1[i] * gelu_prime(A->a1[i]);
+  for (int o = 0; o < H; ++o) {
+    gb1[o] += da1[o];
+    for (int i = 0; i < F; ++i) gW1[o * F + i] += da1[o] * A->xin[i];
+  }
+}
+
 int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const double *finv,
                       const double *feat, const double *m, const double *cst, double c0,
-                      const double *p0, int64_t n, double mix, double *loss, double *grad) {
+                      const double *p0, const double *wgt, int mode, int64_t n, double mix,
+                      double *loss, double *grad) {
   const int64_t np = orc_mlp_nparams(K);
   memset(grad, 0, sizeof(double) * np);
   *loss = 0.0;
   if (n <= 0) return 0;
-  const double *W2 = theta + H * F + H, *W3 = W2 + H * H + H;
-  double *gW1 = grad, *gb1 = gW1 + H * F, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gW3 = gb2 + H,
-         *gb3 = gW3 + (size_t)(K + 2) * H;
   mlp_act A;
   if (K < 1 || act_alloc(&A, K) != 0) return -1;
   double *dz = (double *)malloc(sizeof(double) * (K + 2));
@@ -235,79 +319,44 @@ int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const dou
     free(q);
     return -1;
   }
+  /* batch sums for mode 1 */
+  double SAq = 0.0, SA0 = 0.0, SCq = 0.0, SC0 = 0.0;
+  if (mode == 1) {
+    for (int64_t c = 0; c < n; ++c) {
+      forward_one(theta, K, fmean, finv, feat + c * F, &A);
+      double Aq, A0, Cq, C0;
+      sample_terms(&A, K, m + c * (int64_t)K * 2, cst ? cst + c * (int64_t)K * 2 : NULL, c0,
+                   p0 + c * (int64_t)K, mix, q, &Aq, &A0, &Cq, &C0);
+      const double w = wgt ? wgt[c] : 1.0;
+      SAq += w * Aq;
+      SA0 += w * A0;
+      SCq += Cq;
+      SC0 += C0;
+    }
+    if (!(SA0 > 0.0) || !(SC0 > 0.0)) goto done;
+    *loss = (SAq / SA0) * (SCq / SC0);
+  }
   for (int64_t c = 0; c < n; ++c) {
     forward_one(theta, K, fmean, finv, feat + c * F, &A);
     const double *mc = m + c * (int64_t)K * 2, *pc = p0 + c * (int64_t)K;
     const double *cc = cst ? cst + c * (int64_t)K * 2 : NULL;
-    for (int k = 0; k < K; ++k) q[k] = (1.0 - mix) * A.s[k] + mix * pc[k];
-    q[K] = (1.0 - mix) * A.s[K] + mix * 0.5;
-    q[K + 1] = (1.0 - mix) * A.s[K + 1] + mix * 0.5;
-    double A0 = 0.0, Aq = 0.0, C0 = c0, Cq = c0;
-    for (int k = 0; k < K; ++k) {
-      if (!(pc[k] > 0.0)) continue;
-      for (int hh = 0; hh < 2; ++hh) {
-        A0 += mc[k * 2 + hh] / (pc[k] * 0.5);
-        Aq += mc[k * 2 + hh] / (q[k] * q[K + hh]);
-        if (cc) {
-          C0 += cc[k * 2 + hh] * (pc[k] * 0.5);
-          Cq += cc[k * 2 + hh] * (q[k] * q[K + hh]);
-        }
-      }
+    double Aq, A0, Cq, C0, gA, gC;
+    sample_terms(&A, K, mc, cc, c0, pc, mix, q, &Aq, &A0, &Cq, &C0);
+    if (mode == 1) {
+      const double w = wgt ? wgt[c] : 1.0;
+      gA = w * SCq / (SA0 * SC0);
+      gC = SAq / (SA0 * SC0);
+      if (!cc) gC = 0.0;
+    } else {
+      if (!(A0 > 0.0) || !(C0 > 0.0)) continue;
+      const double norm = A0 * C0;
+      *loss += Aq * Cq / norm / (double)n;
+      gA = Cq / ((double)n * norm);
+      gC = cc ? Aq / ((double)n * norm) : 0.0;
     }
-    if (!cc) C0 = Cq = 1.0;
-    if (!(A0 > 0.0) || !(C0 > 0.0)) continue;
-    const double norm = A0 * C0;
-    *loss += Aq * Cq / norm / (double)n;
-    /* dL/dq = (dA/dq C + A dC/dq) / (n A0 C0) */
-    const double sc = 1.0 / ((double)n * norm);
-    gq[K] = gq[K + 1] = 0.0;
-    for (int k = 0; k < K; ++k) {
-      gq[k] = 0.0;
-      if (!(pc[k] > 0.0)) continue;
-      for (int hh = 0; hh < 2; ++hh) {
-        const double v = mc[k * 2 + hh];
-        gq[k] -= sc * Cq * v / (q[k] * q[k] * q[K + hh]);
-        gq[K + hh] -= sc * Cq * v / (q[k] * q[K + hh] * q[K + hh]);
-        if (cc) {
-          gq[k] += sc * Aq * cc[k * 2 + hh] * q[K + hh];
-          gq[K + hh] += sc * Aq * cc[k * 2 + hh] * q[k];
-        }
-      }
-    }
-    /* through the mixtures and the two softmaxes */
-    double dot = 0.0;
-    for (int k = 0; k < K; ++k) dot += A.s[k] * gq[k];
-    for (int k = 0; k < K; ++k) dz[k] = (1.0 - mix) * A.s[k] * (gq[k] - dot);
-    const double doth = A.s[K] * gq[K] + A.s[K + 1] * gq[K + 1];
-    dz[K] = (1.0 - mix) * A.s[K] * (gq[K] - doth);
-    dz[K + 1] = (1.0 - mix) * A.s[K + 1] * (gq[K + 1] - doth);
-    /* layer 3 */
-    double dh2[H], da2[H], dh1[H], da1[H];
-    for (int i = 0; i < H; ++i) dh2[i] = 0.0;
-    for (int o = 0; o < K + 2; ++o) {
-      gb3[o] += dz[o];
-      for (int i = 0; i < H; ++i) {
-        gW3[(size_t)o * H + i] += dz[o] * A.h2[i];
-        dh2[i] += W3[(size_t)o * H + i] * dz[o];
-      }
-    }
-    /* layer 2 */
-    for (int i = 0; i < H; ++i) da2[i] = dh2[i] * gelu_prime(A.a2[i]);
-    for (int i = 0; i < H; ++i) dh1[i] = 0.0;
-    for (int o = 0; o < H; ++o) {
-      gb2[o] += da2[o];
-      for (int i = 0; i < H; ++i) {
-        gW2[o * H + i] += da2[o] * A.h1[i];
-        dh1[i] += W2[o * H + i] * da2[o];
-      }
-    }
-    /* layer 1 */
-    for (int i = 0; i < H; ++i) da1[i] = dh1[i] * gelu_prime(A.a1[i]);
-    for (int o = 0; o < H; ++o) {
-      gb1[o] += da1[o];
-      for (int i = 0; i < F; ++i) gW1[o * F + i] += da1[o] * A.xin[i];
-    }
+    sample_backward(theta, K, &A, mc, cc, pc, mix, q, gA, gC, dz, gq, grad);
   }
+done:
   act_free(&A);
   free(dz);
   free(gq);

@@ -113,7 +113,8 @@ int orc_mlp_forward(const double *theta, int K, const double *fmean, const doubl
                     double mix, double *q);
 int orc_mlp_loss_grad(const double *theta, int K, const double *fmean, const double *finv,
                       const double *feat, const double *m, const double *cst, double c0,
-                      const double *p0, int64_t n, double mix, double *loss, double *grad);
+                      const double *p0, const double *wgt, int mode, int64_t n, double mix,
+                      double *loss, double *grad);
 void orc_adam(double *theta, const double *grad, double *m1, double *m2, int64_t n, double lr,
               double beta1, double beta2, double eps, int t);
 int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *cn,

@@ -361,3 +361,34 @@ def test_skewed_cell_proposal_is_unbiased_against_quadrature():
     z = (res["q"].reshape(-1) - q_quad) / res["sigma"].reshape(-1)
     assert np.max(np.abs(z)) < 4.5, np.round(z, 2)
     assert np.sqrt(np.mean(z**2)) < 1.4
+
+
+def test_batch_time_ratio_mode():
+    """Mode 1: one sample gives the per-cell ratio (mode 0); the loss and its
+    gradient do not depend on the scale of the weights; and the gradient
+    matches central finite differences."""
+    K, n = K_SMALL, 6
+    th, feat, m, p0 = _rand_problem(K, n, 9)
+    cost = _rand_cost(K, n, 10)
+    w = np.random.default_rng(11).uniform(0.1, 3.0, n)
+    z12, o12 = np.zeros(12), np.ones(12)
+    L0, g0 = oracle.mlp_loss_grad(th, K, z12, o12, feat[:1], m[:1], p0[:1], cost=cost[:1], c0=2.0)
+    L1, g1 = oracle.mlp_loss_grad(th, K, z12, o12, feat[:1], m[:1], p0[:1], cost=cost[:1], c0=2.0,
+                                  wgt=w[:1], mode=1)
+    assert L1 == pytest.approx(L0, rel=1e-12)
+    np.testing.assert_allclose(g1, g0, rtol=1e-10, atol=1e-14)
+    kw = dict(cost=cost, c0=2.0, mode=1)
+    La, ga = oracle.mlp_loss_grad(th, K, z12, o12, feat, m, p0, wgt=w, **kw)
+    Lb, gb = oracle.mlp_loss_grad(th, K, z12, o12, feat, m, p0, wgt=7.5 * w, **kw)
+    assert Lb == pytest.approx(La, rel=1e-12)
+    np.testing.assert_allclose(gb, ga, rtol=1e-10, atol=1e-14)
+    rng = np.random.default_rng(12)
+    for i in np.concatenate([rng.choice(64 * 12, 4, replace=False),
+                             oracle.mlp_nparams(K) - (K + 2) + np.arange(K + 2)]):
+        e = 1e-6
+        tp, tm = th.copy(), th.copy()
+        tp[i] += e
+        tm[i] -= e
+        Lp, _ = oracle.mlp_loss_grad(tp, K, z12, o12, feat, m, p0, wgt=w, **kw)
+        Lm, _ = oracle.mlp_loss_grad(tm, K, z12, o12, feat, m, p0, wgt=w, **kw)
+        assert ga[i] == pytest.approx((Lp - Lm) / (2 * e), rel=2e-5, abs=1e-9), i

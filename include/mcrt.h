@@ -293,18 +293,25 @@ int mcrt_mlp_get_params(mcrt_mlp *m, float *theta, float *theta_used);
  * Asynchronous on cuda_stream. */
 int mcrt_mlp_forward(mcrt_mlp *m, const float *feat, int64_t n, const float *p0, int p0_stride,
                      float mix, float *q_out, void *cuda_stream);
-/* Mean loss over a batch and its gradient.  Samples idx[0..n-1] (device, NULL:
+/* Loss modes: MCRT_LOSS_CELL, the mean over the batch of the per-cell ratio
+ * A_c(q) C_c(q) / (A_c(p0) C_c(p0)); MCRT_LOSS_BATCH, the batch estimate of the
+ * ratio of GPU time to a given relative error,
+ *   (sum_c w_c A_c(q) / sum_c w_c A_c(p0)) (sum_c C_c(q) / sum_c C_c(p0)),
+ * with sample weights w_c (1 / error scale^2 of the cell). */
+enum { MCRT_LOSS_CELL = 0, MCRT_LOSS_BATCH = 1 };
+/* Loss over a batch and its gradient.  Samples idx[0..n-1] (device, NULL:
  * 0..n-1) of a dataset of n_data samples: feat (device [n_data][12]), mom and
- * cost (device [n_data][K][2]; cost nullable) and p0 ([n_data][K], p0_stride
- * K, or [K], stride 0).  The gradient (FP32, [nparams]) goes to grad_out
- * (device, nullable) and to the network's own buffer; the loss is read by
+ * cost (device [n_data][K][2]; cost nullable: C = 1), p0 ([n_data][K],
+ * p0_stride K, or [K], stride 0) and wgt (device [n_data], nullable: 1; used by
+ * MCRT_LOSS_BATCH).  The gradient (FP32, [nparams]) goes to grad_out (device,
+ * nullable) and to the network's own buffer; the loss is read by
  * mcrt_mlp_last_loss, which also reports (MCRT_E_ARG) an index outside
  * [0, n_data) -- such a sample is skipped, never read.  The gradient is reduced
  * in a fixed order: identical inputs give identical bits.  Asynchronous. */
 int mcrt_mlp_loss_grad(mcrt_mlp *m, const float *feat, const float *mom, const float *cost,
-                       float c0, const float *p0, int p0_stride, int64_t n_data,
-                       const int32_t *idx, int64_t n, float mix, float *grad_out,
-                       void *cuda_stream);
+                       float c0, const float *p0, int p0_stride, const float *wgt, int mode,
+                       int64_t n_data, const int32_t *idx, int64_t n, float mix,
+                       float *grad_out, void *cuda_stream);
 /* One Adam step (Kingma & Ba 2015) of the master parameters with gradient grad
  * (device [nparams]; NULL: the network's last gradient); refreshes the FP16
  * copy.  Asynchronous. */

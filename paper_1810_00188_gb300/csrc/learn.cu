@@ -496,6 +496,9 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
   float *nrm = Z + (size_t)TT * KO;
   __shared__ double s_loss;
   __shared__ float s_lsamp[TT];
+  __shared__ double s_stat[TT][4];
+  __shared__ double s_tot[4];
+  __shared__ double s_bs[4];
   load_weights(a.theta16, K, S, true);
   const long long ngrad = (long long)NF * NH + NH + NH * NH + NH + (long long)NH * KO + KO;
   for (long long e = threadIdx.x; e < ngrad; e += blockDim.x) gW1T[e] = 0.f;
@@ -503,7 +506,14 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
     nrm[e] = a.fmean[e];
     nrm[NF + e] = a.finv[e];
   }
-  if (threadIdx.x == 0) s_loss = 0.0;
+  if (threadIdx.x == 0) {
+    s_loss = 0.0;
+    for (int j = 0; j < 4; ++j) {
+      s_tot[j] = 0.0;
+      s_bs[j] = a.bsum ? a.bsum[j] : 0.0;
+    }
+  }
+  const bool stats_only = a.mode == 1 && a.pass == 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float invB = 1.f / (float)a.n;
@@ -525,7 +535,10 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
     // loss and its gradient with respect to the logits, one warp per sample
     for (int c = w; c < TT; c += NTHR / 32) {
       float *z = Z + (size_t)c * KO;
-      if (lane == 0) s_lsamp[c] = 0.f;
+      if (lane == 0) {
+        s_lsamp[c] = 0.f;
+        for (int j = 0; j < 4; ++j) s_stat[c][j] = 0.0;
+      }
       if (c >= rows) {
         for (int k = lane; k < KO; k += 32) z[k] = 0.f;
         continue;
@@ -571,14 +584,31 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
       } else {
         C0 = Cq = 1.f;
       }
-      if (!(A0 > 0.f) || !(C0 > 0.f)) {
-        __syncwarp();
-        for (int k = lane; k < KO; k += 32) z[k] = 0.f;
-        continue;
+      // multipliers dL/dA(q), dL/dC(q) of this sample
+      float gA, gC;
+      if (a.mode == 1) {
+        const float wc = a.wgt ? a.wgt[smp] : 1.f;
+        if (lane == 0) {
+          s_stat[c][0] = (double)wc * Aq;
+          s_stat[c][1] = (double)wc * A0;
+          s_stat[c][2] = Cq;
+          s_stat[c][3] = C0;
+        }
+        if (stats_only) continue;
+        const float den = (float)(s_bs[1] * s_bs[3]);
+        gA = wc * (float)s_bs[2] / den;
+        gC = cs ? (float)s_bs[0] / den : 0.f;
+      } else {
+        if (!(A0 > 0.f) || !(C0 > 0.f)) {
+          __syncwarp();
+          for (int k = lane; k < KO; k += 32) z[k] = 0.f;
+          continue;
+        }
+        const float norm = A0 * C0;
+        if (lane == 0) s_lsamp[c] = Aq * Cq / norm;
+        gA = invB * Cq / norm;
+        gC = cs ? invB * Aq / norm : 0.f;
       }
-      const float norm = A0 * C0;
-      if (lane == 0) s_lsamp[c] = Aq * Cq / norm;
-      const float sc = invB / norm;
       // dL/dq_k and the hemisphere gradients; then through the softmaxes
       float dot = 0.f, gu = 0.f, gd = 0.f;
       for (int k = lane; k < K; k += 32) {
@@ -587,13 +617,13 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
         const float sk = expf(z[k] - mx) * inv;
         const float qk = (1.f - a.mix) * sk + a.mix * pk;
         const float mu = m[2 * k], md = m[2 * k + 1];
-        float g = -sc * Cq * (mu / (qk * qk * qu) + md / (qk * qk * qd));
-        gu -= sc * Cq * mu / (qk * qu * qu);
-        gd -= sc * Cq * md / (qk * qd * qd);
+        float g = -gA * (mu / (qk * qk * qu) + md / (qk * qk * qd));
+        gu -= gA * mu / (qk * qu * qu);
+        gd -= gA * md / (qk * qd * qd);
         if (cs) {
-          g += sc * Aq * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
-          gu += sc * Aq * cs[2 * k] * qk;
-          gd += sc * Aq * cs[2 * k + 1] * qk;
+          g += gC * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
+          gu += gC * cs[2 * k] * qk;
+          gd += gC * cs[2 * k + 1] * qk;
         }
         dot += sk * g;
       }
@@ -608,8 +638,8 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
         if (pk > 0.f) {
           const float qk = (1.f - a.mix) * sk + a.mix * pk;
           const float mu = m[2 * k], md = m[2 * k + 1];
-          g = -sc * Cq * (mu / (qk * qk * qu) + md / (qk * qk * qd));
-          if (cs) g += sc * Aq * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
+          g = -gA * (mu / (qk * qk * qu) + md / (qk * qk * qd));
+          if (cs) g += gC * (cs[2 * k] * qu + cs[2 * k + 1] * qd);
         }
         z[k] = (1.f - a.mix) * sk * (g - dot);
       }
@@ -622,8 +652,15 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
       __syncwarp();
     }
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
       for (int c = 0; c < rows; ++c) s_loss += (double)s_lsamp[c] * (double)invB;
+      for (int c = 0; c < rows; ++c)
+        for (int j = 0; j < 4; ++j) s_tot[j] += s_stat[c][j];
+    }
+    if (stats_only) {
+      __syncthreads();
+      continue;
+    }
     // layer 3: gW3T[i][o] += sum_c H2[c][i] dz[c][o]; gb3; dH2 -> dA2
     for (int e = threadIdx.x; e < NH * KO; e += blockDim.x) {
       const int i = e / KO, o = e % KO;
@@ -685,6 +722,11 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
     }
     __syncthreads();
   }
+  if (stats_only) {
+    __syncthreads();
+    if (threadIdx.x < 4) a.stat_partial[(size_t)blockIdx.x * 4 + threadIdx.x] = s_tot[threadIdx.x];
+    return;
+  }
   // this CTA's share, in theta's layout
   float *out = a.partial + (size_t)blockIdx.x * ngrad;
   const long long oW1 = 0, ob1 = NH * NF, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 = ob2 + NH,
@@ -711,7 +753,7 @@ __global__ void __launch_bounds__(NTHR, 1) mlp_train_kernel(const MlpTrainArgs a
 }
 
 __global__ void grad_reduce_kernel(const float *partial, const double *loss_partial, int grid,
-                                   long long np, float *grad, double *loss) {
+                                   long long np, const double *bsum, float *grad, double *loss) {
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < np;
        j += (long long)gridDim.x * blockDim.x) {
     float acc = 0.f;
@@ -720,8 +762,20 @@ __global__ void grad_reduce_kernel(const float *partial, const double *loss_part
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double l = 0.0;
-    for (int b = 0; b < grid; ++b) l += loss_partial[b];
+    if (bsum) {
+      l = (bsum[0] / bsum[1]) * (bsum[2] / bsum[3]);
+    } else {
+      for (int b = 0; b < grid; ++b) l += loss_partial[b];
+    }
     *loss = l;
+  }
+}
+
+__global__ void stat_reduce_kernel(const double *stat_partial, int grid, double *bsum) {
+  if (threadIdx.x < 4) {
+    double acc = 0.0;
+    for (int b = 0; b < grid; ++b) acc += stat_partial[(size_t)b * 4 + threadIdx.x];
+    bsum[threadIdx.x] = acc;
   }
 }
 
@@ -823,8 +877,15 @@ cudaError_t launch_mlp_train(const MlpTrainArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_grad_reduce(const float *partial, const double *loss_partial, int grid,
-                               long long np, float *grad, double *loss, cudaStream_t s) {
-  grad_reduce_kernel<<<grid_for(np, 256, 2), 256, 0, s>>>(partial, loss_partial, grid, np, grad, loss);
+                               long long np, const double *bsum, float *grad, double *loss,
+                               cudaStream_t s) {
+  grad_reduce_kernel<<<grid_for(np, 256, 2), 256, 0, s>>>(partial, loss_partial, grid, np, bsum, grad,
+                                                          loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stat_reduce(const double *stat_partial, int grid, double *bsum, cudaStream_t s) {
+  stat_reduce_kernel<<<1, 32, 0, s>>>(stat_partial, grid, bsum);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ struct mcrt_mlp {
   int device = 0, K = 0;
   long long np = 0;
   int grid = 0;
-  DevBuf theta, theta16, m1, m2, grad, partial, loss_partial, loss, nrm, errf;
+  DevBuf theta, theta16, m1, m2, grad, partial, loss_partial, loss, nrm, errf, stat_partial, bsum;
   int t = 0;
   bool have_loss = false;
   cudaStream_t last_stream = nullptr;
@@ -49,7 +49,7 @@ int mcuda_fail(mcrt_mlp *m, cudaError_t e, const char *where) {
 
 void mlp_release(mcrt_mlp *m) {
   DevBuf *bufs[] = {&m->theta, &m->theta16, &m->m1, &m->m2, &m->grad, &m->partial,
-                    &m->loss_partial, &m->loss, &m->nrm, &m->errf};
+                    &m->loss_partial, &m->loss, &m->nrm, &m->errf, &m->stat_partial, &m->bsum};
   for (DevBuf *b : bufs) release(*b);
 }
 
@@ -153,6 +153,8 @@ int mcrt_mlp_create(int device, int K, mcrt_mlp **out) {
   if (e == cudaSuccess) e = ensure(m->loss, sizeof(double));
   if (e == cudaSuccess) e = ensure(m->nrm, 2 * MCRT_NFEAT * sizeof(float));
   if (e == cudaSuccess) e = ensure(m->errf, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = ensure(m->stat_partial, (size_t)m->grid * 4 * sizeof(double));
+  if (e == cudaSuccess) e = ensure(m->bsum, 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(m->errf.p, 0, sizeof(unsigned long long));
   for (DevBuf *b : f32)
     if (e == cudaSuccess) e = cudaMemset(b->p, 0, np * sizeof(float));
@@ -242,9 +244,11 @@ int mcrt_mlp_forward(mcrt_mlp *m, const float *feat, int64_t n, const float *p0,
 }
 
 int mcrt_mlp_loss_grad(mcrt_mlp *m, const float *feat, const float *mom, const float *cost,
-                       float c0, const float *p0, int p0_stride, int64_t n_data, const int32_t *idx,
-                       int64_t n, float mix, float *grad_out, void *stream) {
+                       float c0, const float *p0, int p0_stride, const float *wgt, int mode,
+                       int64_t n_data, const int32_t *idx, int64_t n, float mix, float *grad_out,
+                       void *stream) {
   if (!m) return MCRT_E_ARG;
+  if (mode != MCRT_LOSS_CELL && mode != MCRT_LOSS_BATCH) return mfail(m, MCRT_E_ARG, "bad loss mode");
   if (n < 1 || !feat || !mom || !p0) return mfail(m, MCRT_E_ARG, "bad arguments");
   if (n_data < 1 || (!idx && n > n_data)) return mfail(m, MCRT_E_ARG, "batch beyond the dataset");
   if (p0_stride != 0 && p0_stride != m->K) return mfail(m, MCRT_E_ARG, "p0_stride must be 0 or K");
@@ -265,6 +269,9 @@ int mcrt_mlp_loss_grad(mcrt_mlp *m, const float *feat, const float *mom, const f
   a.c0 = c0;
   a.p0 = p0;
   a.p0_stride = p0_stride;
+  a.wgt = wgt;
+  a.mode = mode;
+  a.stat_partial = (double *)m->stat_partial.p;
   a.idx = idx;
   a.n_data = n_data;
   a.n = n;
@@ -273,9 +280,20 @@ int mcrt_mlp_loss_grad(mcrt_mlp *m, const float *feat, const float *mom, const f
   a.partial = (float *)m->partial.p;
   a.loss_partial = (double *)m->loss_partial.p;
   a.grid = m->grid;
+  const double *bsum = nullptr;
+  if (mode == MCRT_LOSS_BATCH) {
+    // pass 0: the batch sums the per-sample multipliers depend on
+    a.pass = 0;
+    MK(mcrt::launch_mlp_train(a, s), "train step (batch sums)");
+    MK(mcrt::launch_stat_reduce((const double *)m->stat_partial.p, m->grid, (double *)m->bsum.p, s),
+       "batch sums");
+    bsum = (const double *)m->bsum.p;
+    a.bsum = bsum;
+  }
+  a.pass = 1;
   MK(mcrt::launch_mlp_train(a, s), "train step");
   MK(mcrt::launch_grad_reduce((const float *)m->partial.p, (const double *)m->loss_partial.p, m->grid,
-                              m->np, (float *)m->grad.p, (double *)m->loss.p, s),
+                              m->np, bsum, (float *)m->grad.p, (double *)m->loss.p, s),
      "gradient reduction");
   if (grad_out)
     MK(cudaMemcpyAsync(grad_out, m->grad.p, (size_t)m->np * sizeof(float), cudaMemcpyDeviceToDevice, s),

@@ -168,6 +168,11 @@ struct MlpTrainArgs {
   float c0;
   const float *p0;                 // [N][K] or [K]
   int p0_stride;
+  const float *wgt;                // [N] sample weights (mode 1), or null (1)
+  int mode;                        // 0: mean per-cell work ratio; 1: batch time ratio
+  int pass;                        // mode 1: 0 = batch sums only, 1 = gradient
+  const double *bsum;              // mode 1 pass 1: {sum w A(q), sum w A(p0), sum C(q), sum C(p0)}
+  double *stat_partial;            // mode 1 pass 0: [grid][4]
   const int *idx;                  // batch -> sample, or null (sample = batch index)
   long long n_data;                // samples in the dataset (idx must stay below)
   long long n;                     // batch size
@@ -178,8 +183,12 @@ struct MlpTrainArgs {
   unsigned long long *err;         // set when an index is outside the dataset
 };
 cudaError_t launch_mlp_train(const MlpTrainArgs &a, cudaStream_t s);
+// Adds the CTAs' gradient partials in order; the loss is the sum of the loss
+// partials, or (bsum non-null) the batch time ratio of the four batch sums.
 cudaError_t launch_grad_reduce(const float *partial, const double *loss_partial, int grid,
-                               long long np, float *grad, double *loss, cudaStream_t s);
+                               long long np, const double *bsum, float *grad, double *loss,
+                               cudaStream_t s);
+cudaError_t launch_stat_reduce(const double *stat_partial, int grid, double *bsum, cudaStream_t s);
 cudaError_t launch_adam(float *theta, __half *theta16, const float *grad, float *m1, float *m2,
                         long long np, float lr, float beta1, float beta2, float eps, float c1,
                         float c2, cudaStream_t s);

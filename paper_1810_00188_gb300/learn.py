@@ -6,11 +6,13 @@ this module picks the fields, the cells and the batches (seeded), and keeps the
 device tensors the kernels read.
 
 Training data (one sample per tallied cell): the 12 features, the second-moment
-tallies m [K][2] and cost tallies c [K][2] of a plain FP32 solve, and the plain
-pdf p0 [K] of the sample's field.  The loss per sample is
-A(q) C(q) / (A(p0) C(p0)) with A(q) = sum m / (q_k q_h) (the second moment of the
-estimate per ray under q) and C(q) = c0 + sum c q_k q_h (the ray's cost in
-steps, c0 its fixed part); its mean over a batch is what one Adam step lowers.
+tallies m [K][2] and cost tallies c [K][2] of a plain FP32 solve, the plain pdf
+p0 [K] of the sample's field, and the weight w = 1 / ref^2 with
+ref = max(|Q|, 0.05 mean |Q|) the cell's error scale (the per-cell 1% criterion).
+With A(q) = sum m / (q_k q_h) (the second moment of the estimate per ray under q)
+and C(q) = c0 + sum c q_k q_h (the ray's cost in steps, c0 its fixed part), the
+default loss is the batch estimate of the GPU-time ratio to a given relative
+error, (sum w A(q) / sum w A(p0)) (sum C(q) / sum C(p0)).
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ class Dataset:
     mom: object         # torch [N, K, 2]
     cost: object        # torch [N, K, 2]
     p0: object          # torch [N, K]
+    wgt: object         # torch [N]: 1 / ref^2
     K: int
     fields: int
 
@@ -37,14 +40,18 @@ class Dataset:
 
 
 def tally_field(S, rays, seed, snapshot, cells, stream=0):
-    """Features, tallies and p0 rows of `cells` (torch int32 cuda) of the
-    context's current fields."""
+    """Features, tallies, p0 rows and weights 1/ref^2 of `cells` (torch int32
+    cuda) of the context's current fields."""
     import torch
     feat = S.features(cells, stream=stream)
     p = S.params(rays=rays, seed=seed, snapshot=snapshot, precision=mcrt.MCRT_FP32)
-    mom, cost = S.tally(p, cells, stream=stream)
+    q = torch.empty(S.box_shape(None), dtype=torch.float64, device=feat.device)
+    mom, cost = S.tally(p, cells, q=q, stream=stream)
     p0 = torch.tensor(S.plain_probs(), device=feat.device)
-    return feat, mom, cost, p0.expand(cells.shape[0], -1)
+    qa = q.reshape(-1).abs()
+    ref = torch.clamp(qa[cells.long()], min=0.05 * float(qa.mean()))
+    wgt = (1.0 / ref**2).float()
+    return feat, mom, cost, p0.expand(cells.shape[0], -1), wgt
 
 
 def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per_field=4096,
@@ -52,7 +59,7 @@ def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per
     """Tallies of `cells_per_field` random cells of each seeded channel field."""
     import torch
     nx, ny, nz = grid_shape
-    feats, moms, costs, p0s = [], [], [], []
+    feats, moms, costs, p0s, wgts = [], [], [], [], []
     rng = np.random.default_rng(sample_seed)
     S = None
     kd = None
@@ -66,16 +73,18 @@ def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per
         n = min(cells_per_field, grid.ncells)
         cells = torch.tensor(np.sort(rng.choice(grid.ncells, n, replace=False)).astype(np.int32),
                              device="cuda")
-        f, m, c, p = tally_field(S, rays, seed=1000 + int(s), snapshot=int(s), cells=cells,
-                                 stream=stream)
+        f, m, c, p, w = tally_field(S, rays, seed=1000 + int(s), snapshot=int(s), cells=cells,
+                                    stream=stream)
         feats.append(f)
         moms.append(m)
         costs.append(c)
         p0s.append(p.contiguous())
+        wgts.append(w)
     S.close()
     K = kd.n_bands * kd.n_g
-    return Dataset(torch.cat(feats), torch.cat(moms), torch.cat(costs), torch.cat(p0s), K,
-                   len(feats))
+    w = torch.cat(wgts)
+    return Dataset(torch.cat(feats), torch.cat(moms), torch.cat(costs), torch.cat(p0s),
+                   (w / w.mean()).contiguous(), K, len(feats))
 
 
 def feature_norm(ds: Dataset):
@@ -103,10 +112,10 @@ def init_theta(K, p0_mean, seed=0, scale=1.0):
     return theta.astype(np.float32)
 
 
-def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=8.0, mix=0.1, seed=0,
-          log_every=0, stream=0, use_cost=True):
-    """Adam on the mean work-ratio loss over random batches.  Returns the losses
-    at the logged steps (and the last one)."""
+def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=2.0, mix=0.1, seed=0,
+          log_every=0, stream=0, use_cost=True, mode=mcrt.MCRT_LOSS_BATCH):
+    """Adam on the loss over random batches.  Returns the losses at the logged
+    steps (and the last one)."""
     import torch
     if batch is None:
         batch = 16 * torch.cuda.get_device_properties(0).multi_processor_count * 2
@@ -121,17 +130,18 @@ def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=8.0, mix=0.1, se
         idx = perm[pos:pos + min(batch, ds.n)]
         pos += batch
         mlp.loss_grad(ds.feat, ds.mom, ds.p0, cost=ds.cost if use_cost else None, c0=c0, idx=idx,
-                      mix=mix, stream=stream)
+                      mix=mix, wgt=ds.wgt, mode=mode, stream=stream)
         mlp.adam(lr=lr, stream=stream)
         if (log_every and it % log_every == 0) or it == steps - 1:
             losses.append((it, mlp.last_loss()))
     return losses
 
 
-def mean_loss(mlp, ds: Dataset, c0=8.0, mix=0.1, stream=0, use_cost=True):
+def mean_loss(mlp, ds: Dataset, c0=2.0, mix=0.1, stream=0, use_cost=True,
+              mode=mcrt.MCRT_LOSS_BATCH):
     """Loss over the whole dataset (no update)."""
     mlp.loss_grad(ds.feat, ds.mom, ds.p0, cost=ds.cost if use_cost else None, c0=c0, mix=mix,
-                  stream=stream)
+                  wgt=ds.wgt, mode=mode, stream=stream)
     return mlp.last_loss()
 
 
@@ -179,4 +189,6 @@ def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0):
                      "steps_per_ray": steps / (reps * rays * S.grid.ncells),
                      "ms_to_1pct": t * (pr / 0.01) ** 2}
     out["speedup_to_1pct"] = out["plain"]["ms_to_1pct"] / out["learned"]["ms_to_1pct"]
+    out["speedup_to_1pct_incl_proposal"] = out["plain"]["ms_to_1pct"] / (
+        out["learned"]["ms_to_1pct"] + out["proposal_ms"])
     return out

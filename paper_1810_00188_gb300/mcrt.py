@@ -86,6 +86,7 @@ EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_pr
 _NOT_INT = ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error", "mcrt_mlp_last_error",
             "mcrt_mlp_nparams")
 MCRT_NFEAT, MCRT_NHIDDEN = 12, 64
+MCRT_LOSS_CELL, MCRT_LOSS_BATCH = 0, 1
 
 
 def library_path() -> str:
@@ -134,7 +135,8 @@ def load(build_if_missing: bool = True):
         L.mcrt_mlp_set_params.argtypes = [vp, vp, vp, vp]
         L.mcrt_mlp_get_params.argtypes = [vp, vp, vp]
         L.mcrt_mlp_forward.argtypes = [vp, vp, i64, vp, C.c_int, f32, vp, vp]
-        L.mcrt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, f32, vp, C.c_int, i64, vp, i64, f32, vp, vp]
+        L.mcrt_mlp_loss_grad.argtypes = [vp, vp, vp, vp, f32, vp, C.c_int, vp, C.c_int, i64, vp, i64,
+                                         f32, vp, vp]
         L.mcrt_mlp_adam_step.argtypes = [vp, vp, f32, f32, f32, f32, vp]
         L.mcrt_mlp_last_loss.argtypes = [vp, C.POINTER(C.c_double)]
         L.mcrt_mlp_last_error.argtypes = [vp]
@@ -295,10 +297,10 @@ def mcrt_mlp_forward(m, feat_ptr, n: int, p0_ptr, p0_stride: int, mix: float, q_
     _mcheck(load().mcrt_mlp_forward(m, feat_ptr, n, p0_ptr, p0_stride, mix, q_ptr, stream), m)
 
 
-def mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0: float, p0_ptr, p0_stride: int,
-                       n_data: int, idx_ptr, n: int, mix: float, grad_ptr=None, stream=0):
-    _mcheck(load().mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0, p0_ptr, p0_stride, n_data,
-                                      idx_ptr, n, mix, grad_ptr, stream), m)
+def mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0: float, p0_ptr, p0_stride: int, wgt_ptr,
+                       mode: int, n_data: int, idx_ptr, n: int, mix: float, grad_ptr=None, stream=0):
+    _mcheck(load().mcrt_mlp_loss_grad(m, feat_ptr, mom_ptr, cost_ptr, c0, p0_ptr, p0_stride, wgt_ptr,
+                                      mode, n_data, idx_ptr, n, mix, grad_ptr, stream), m)
 
 
 def mcrt_mlp_adam_step(m, grad_ptr=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
@@ -386,11 +388,11 @@ class Mlp:
         return out
 
     def loss_grad(self, feat, mom, p0, cost=None, c0=0.0, idx=None, n=None, mix=0.1, grad=None,
-                  stream=0):
+                  wgt=None, mode=0, stream=0):
         n = (idx.shape[0] if idx is not None else feat.shape[0]) if n is None else n
         stride = 0 if p0.dim() == 1 else self.K
         mcrt_mlp_loss_grad(self.handle, _ptr(feat), _ptr(mom), _ptr(cost), c0, _ptr(p0), stride,
-                           feat.shape[0], _ptr(idx), n, mix, _ptr(grad), stream)
+                           _ptr(wgt), mode, feat.shape[0], _ptr(idx), n, mix, _ptr(grad), stream)
 
     def adam(self, grad=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
         mcrt_mlp_adam_step(self.handle, _ptr(grad), lr, beta1, beta2, eps, stream)

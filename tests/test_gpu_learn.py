@@ -153,31 +153,33 @@ def test_mlp_forward_matches_oracle():
     net.close()
 
 
-@pytest.mark.parametrize("with_cost", [False, True])
-def test_mlp_gradient_matches_oracle(with_cost):
+@pytest.mark.parametrize("with_cost,mode", [(False, 0), (True, 0), (False, 1), (True, 1)])
+def test_mlp_gradient_matches_oracle(with_cost, mode):
     torch = _torch()
     K, N = 320, 300
     theta, feat, fmean, finv, mom, cost, p0 = _net_problem(K, N, 2)
+    wgt = np.random.default_rng(7).uniform(0.05, 4.0, N).astype(np.float32)
     net = mcrt.Mlp(K)
     net.set_params(theta, fmean, finv)
     idx = np.random.default_rng(3).permutation(N)[:203].astype(np.int32)
     d = {k: torch.tensor(v, device="cuda") for k, v in
-         dict(feat=feat, mom=mom, cost=cost, p0=p0, idx=idx).items()}
+         dict(feat=feat, mom=mom, cost=cost, p0=p0, idx=idx, wgt=wgt).items()}
     grad = torch.empty(net.nparams, dtype=torch.float32, device="cuda")
     c0 = 8.0
-    net.loss_grad(d["feat"], d["mom"], d["p0"], cost=d["cost"] if with_cost else None, c0=c0,
-                  idx=d["idx"], mix=0.1, grad=grad)
+    kw = dict(cost=d["cost"] if with_cost else None, c0=c0, idx=d["idx"], mix=0.1, wgt=d["wgt"],
+              mode=mode)
+    net.loss_grad(d["feat"], d["mom"], d["p0"], grad=grad, **kw)
     loss = net.last_loss()
     g = grad.cpu().numpy().astype(np.float64)
     Lr, gr = oracle.mlp_loss_grad(theta, K, fmean, finv, feat[idx], mom[idx], p0[idx], mix=0.1,
-                                  cost=cost[idx] if with_cost else None, c0=c0)
+                                  cost=cost[idx] if with_cost else None, c0=c0, wgt=wgt[idx],
+                                  mode=mode)
     assert loss == pytest.approx(Lr, rel=1e-5)
     assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr)
     assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr))
     # fixed-order reduction: the same batch gives the same bits
     grad2 = torch.empty_like(grad)
-    net.loss_grad(d["feat"], d["mom"], d["p0"], cost=d["cost"] if with_cost else None, c0=c0,
-                  idx=d["idx"], mix=0.1, grad=grad2)
+    net.loss_grad(d["feat"], d["mom"], d["p0"], grad=grad2, **kw)
     assert torch.equal(grad, grad2)
     # an index outside the dataset is skipped and reported
     bad = d["idx"].clone()

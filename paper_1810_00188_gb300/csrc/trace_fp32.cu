@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   long long p_next = a.chunk_p0 + wg * per;
   const long long p_end = min(a.chunk_p1, p_next + per);
 
-  const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nxyz = nxy * nz, nb = a.nb,
+  const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nb = a.nb,
             ng = a.ng, nT = a.nT, N = a.rays;
   const uint2 *__restrict__ field = a.fpos32;
   const float2 *__restrict__ ktab = a.ktab32;
@@ -404,35 +404,25 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       }
       if (!done) {
         tprev = tn;
-        if (ax == 0) {
-          cntx += 1.f;
-          tnx = fmaf(cntx, tsx, t0x);
-          ix += sx;
-          lin += (unsigned)sx;
-          if (ix >= nx) {
-            ix -= nx;
-            lin -= (unsigned)nx;
-          } else if (ix < 0) {
-            ix += nx;
-            lin += (unsigned)nx;
-          }
-        } else if (ax == 2) {
-          cntz += 1.f;
-          tnz = fmaf(cntz, tsz, t0z);
-          iz += sz;
-          lin += (unsigned)(sz * nxy);
-          if (iz >= nz) {
-            iz -= nz;
-            lin -= (unsigned)nxyz;
-          } else if (iz < 0) {
-            iz += nz;
-            lin += (unsigned)nxyz;
-          }
-        } else {
-          cnty += 1.f;
-          tny = fmaf(cnty, tsy, t0y);
-          iy += sy;
-          lin += (unsigned)(sy * nx);
+        {
+          // branch-free advance of the crossed axis (lanes cross different axes)
+          const bool mx = ax == 0, my = ax == 1, mz = ax == 2;
+          cntx += mx ? 1.f : 0.f;
+          cnty += my ? 1.f : 0.f;
+          cntz += mz ? 1.f : 0.f;
+          tnx = mx ? fmaf(cntx, tsx, t0x) : tnx;
+          tny = my ? fmaf(cnty, tsy, t0y) : tny;
+          tnz = mz ? fmaf(cntz, tsz, t0z) : tnz;
+          ix += mx ? sx : 0;
+          iy += my ? sy : 0;
+          iz += mz ? sz : 0;
+          lin += mx ? (unsigned)sx : (my ? (unsigned)(sy * nx) : (unsigned)(sz * nxy));
+          const int wx = ix >= nx ? -nx : (ix < 0 ? nx : 0);
+          ix += wx;
+          lin += (unsigned)wx;
+          const int wz = iz >= nz ? -nz : (iz < 0 ? nz : 0);
+          iz += wz;
+          lin += (unsigned)(wz * nxy);
           if (iy < 0 || iy >= ny) {
             // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
             const int wl = iy < 0 ? 0 : 1;

@@ -55,17 +55,31 @@ def tally_field(S, rays, seed, snapshot, cells, stream=0):
 
 
 def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per_field=4096,
-                  kdist_seed=0, x_mode="field", sample_seed=0, stream=0):
-    """Tallies of `cells_per_field` random cells of each seeded channel field."""
+                  kdist_seed=0, x_mode="field", sample_seed=0, stream=0, dense=True):
+    """Tallies of `cells_per_field` random cells of each seeded channel field
+    (cost tallies replaced by the dataset-wide mean steps per point unless
+    dense=False)."""
+    import concurrent.futures as cf
+
     import torch
     nx, ny, nz = grid_shape
     feats, moms, costs, p0s, wgts = [], [], [], [], []
     rng = np.random.default_rng(sample_seed)
     S = None
     kd = None
-    for s in seeds:
-        grid, kd_s, T, x = inputs.nongrey_channel(nx, ny, nz, seed=int(s), kdist_seed=kdist_seed,
-                                                  x_mode=x_mode)
+    seeds = [int(s) for s in seeds]
+
+    def make(s):
+        return inputs.nongrey_channel(nx, ny, nz, seed=s, kdist_seed=kdist_seed, x_mode=x_mode)
+
+    # the host builds the next fields while the GPU tallies the current one
+    pool = cf.ThreadPoolExecutor(max_workers=8)
+    futs = [pool.submit(make, s) for s in seeds[:8]]
+    for i, s in enumerate(seeds):
+        grid, kd_s, T, x = futs[i].result()
+        futs[i] = None
+        if i + 8 < len(seeds):
+            futs.append(pool.submit(make, seeds[i + 8]))
         if S is None:
             kd = kd_s
             S = mcrt.Solver(grid, kd)
@@ -73,18 +87,42 @@ def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per
         n = min(cells_per_field, grid.ncells)
         cells = torch.tensor(np.sort(rng.choice(grid.ncells, n, replace=False)).astype(np.int32),
                              device="cuda")
-        f, m, c, p, w = tally_field(S, rays, seed=1000 + int(s), snapshot=int(s), cells=cells,
-                                    stream=stream)
+        f, m, c, p, w = tally_field(S, rays, seed=1000 + s, snapshot=s, cells=cells, stream=stream)
         feats.append(f)
         moms.append(m)
         costs.append(c)
         p0s.append(p.contiguous())
         wgts.append(w)
+    pool.shutdown()
     S.close()
     K = kd.n_bands * kd.n_g
     w = torch.cat(wgts)
-    return Dataset(torch.cat(feats), torch.cat(moms), torch.cat(costs), torch.cat(p0s),
-                   (w / w.mean()).contiguous(), K, len(feats))
+    ds = Dataset(torch.cat(feats), torch.cat(moms), torch.cat(costs), torch.cat(p0s),
+                 (w / w.mean()).contiguous(), K, len(feats))
+    if dense:
+        dense_cost(ds)
+    return ds
+
+
+def dense_cost(ds: Dataset):
+    """Replaces the per-cell cost tallies by the mean steps per ray of each
+    spectral point over the whole dataset (the same for every cell and both
+    hemispheres).  A cell's tallies are zero at the points its rays never drew;
+    trained on them, a network learns that those points are free and moves its
+    probability there -- typically optically thin bands, whose rays are the
+    longest.  The dataset-wide mean is an unbiased ratio estimate of the steps of
+    a ray at each point: sum_c sum_h p_k p_h c[c,k,h] / sum_c p_k."""
+    import torch
+    w = ds.p0.double() * 0.5                                         # [N, K]
+    steps = (ds.cost.double() * w[:, :, None]).sum(dim=(0, 2))       # sum_c sum_h p_k p_h c
+    norm = ds.p0.double().sum(dim=0)
+    drawn = steps > 0  # every drawn ray takes at least one step
+    sbar = torch.where(drawn, steps / torch.clamp(norm, min=1e-300), torch.zeros_like(norm))
+    # a point never drawn in the whole dataset is an optically thin one (the plain
+    # pdf weights points by kappa): it gets the largest mean seen
+    sbar = torch.where(drawn, sbar, sbar.max())
+    ds.cost = sbar.float()[None, :, None].expand(ds.n, -1, 2).contiguous()
+    return sbar
 
 
 def feature_norm(ds: Dataset):
@@ -112,7 +150,7 @@ def init_theta(K, p0_mean, seed=0, scale=1.0):
     return theta.astype(np.float32)
 
 
-def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=2.0, mix=0.1, seed=0,
+def train(mlp, ds: Dataset, steps=1500, batch=None, lr=2e-3, c0=1.0, mix=0.1, seed=0,
           log_every=0, stream=0, use_cost=True, mode=mcrt.MCRT_LOSS_BATCH):
     """Adam on the loss over random batches.  Returns the losses at the logged
     steps (and the last one)."""
@@ -137,7 +175,7 @@ def train(mlp, ds: Dataset, steps=2000, batch=None, lr=2e-3, c0=2.0, mix=0.1, se
     return losses
 
 
-def mean_loss(mlp, ds: Dataset, c0=2.0, mix=0.1, stream=0, use_cost=True,
+def mean_loss(mlp, ds: Dataset, c0=1.0, mix=0.1, stream=0, use_cost=True,
               mode=mcrt.MCRT_LOSS_BATCH):
     """Loss over the whole dataset (no update)."""
     mlp.loss_grad(ds.feat, ds.mom, ds.p0, cost=ds.cost if use_cost else None, c0=c0, mix=mix,

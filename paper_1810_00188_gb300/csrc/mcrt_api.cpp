@@ -243,7 +243,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.w_g = (const double *)ctx->wg.p;
   a.wgt32 = (const float *)ctx->wgt32.p;
   a.w_g32 = (const float *)ctx->wg32.p;
-  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
+  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024 ? 1 : 0;
   a.guide = (const unsigned short *)ctx->guide.p;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
@@ -251,6 +251,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
     a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
     a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
     a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
+    if (mcrt::fp32_cell_stage_fits(ctx->nb, ctx->ng)) a.counts_in_smem |= 2;
   }
   a.rays = p->rays_per_cell;
   a.max_steps = p->max_steps;
@@ -786,12 +787,13 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.wgt32 = (const float *)ctx->wgt32.p;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
-  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024;
+  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024 ? 1 : 0;
   a.guide = (const unsigned short *)ctx->guide.p;
   if (p->proposal == MCRT_PROPOSAL_CELL) {
     a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
     a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
     a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
+    if (mcrt::fp32_cell_stage_fits(ctx->nb, ctx->ng)) a.counts_in_smem |= 2;
   }
   a.rays = p->rays_per_cell;
   a.max_steps = p->max_steps;
@@ -967,12 +969,13 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.wgt32 = (const float *)c->wgt32.p;
     a.cn = (const unsigned long long *)c->cn.p;
     a.cg = (const unsigned long long *)c->cg.p;
-    a.counts_in_smem = (size_t)(c->nb + c->nb * c->ng) * 8 <= 48 * 1024;
+    a.counts_in_smem = (size_t)(c->nb + c->nb * c->ng) * 8 <= 48 * 1024 ? 1 : 0;
     a.guide = (const unsigned short *)c->guide.p;
     if (p->proposal == MCRT_PROPOSAL_CELL) {
       a.cell_cn = (const unsigned long long *)c->cell_cn.p;
       a.cell_cg = (const unsigned long long *)c->cell_cg.p;
       a.cell_hemi = (const unsigned int *)c->cell_hemi.p;
+      if (mcrt::fp32_cell_stage_fits(c->nb, c->ng)) a.counts_in_smem |= 2;
     }
     a.rays = p->rays_per_cell;
     a.max_steps = p->max_steps;

@@ -36,7 +36,8 @@ struct TraceArgs {
   const unsigned long long *cell_cn;  // per-cell proposal [ncells][nb] or null
   const unsigned long long *cell_cg;  // [ncells][nb*ng]
   const unsigned int *cell_hemi;      // [ncells] count of 2^23, or null (plain: 2^22)
-  int counts_in_smem;                 // plain counts staged in shared memory (<= 48 KB)
+  int counts_in_smem;                 // bit 0: plain counts staged in shared memory (<= 48 KB);
+                                      // bit 1: per-cell counts staged per warp (<= 48 KB)
   const unsigned short *guide;        // [64] guide table of the plain band counts
   // FP32 kernel: brick-order positions [chunk_p0, chunk_p1) of this launch, the
   // per-ray sample scratch [(p - chunk_p0) * rays + r] and per-position step sums
@@ -78,6 +79,7 @@ long long fp32_bricks_positions(int bnx, int bny, int bnz);
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
                                int *blocks_per_sm, int *num_sms);
 int fp32_brick_volume();
+int fp32_cell_stage_fits(int nb, int ng);
 int fp32_guide_size();
 
 // Static device scratch of the allocation-free solve (noalloc.cu): its size,

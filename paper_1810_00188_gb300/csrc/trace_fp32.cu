@@ -160,9 +160,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   WarpRing *rings = reinterpret_cast<WarpRing *>(smem_raw);
   const bool plain = a.cell_cn == nullptr;
   // plain-proposal counts and guide table: staged in shared memory when they fit
+  // (counts_in_smem bit 0); a per-cell proposal is staged per warp, one emitting
+  // cell at a time (bit 1), in the same space
   const unsigned long long *s_cn = a.cn, *s_cg = a.cg;
   const unsigned short *s_guide = a.guide;
-  if (plain && a.counts_in_smem) {
+  const bool cell_stage = !plain && (a.counts_in_smem & 2);
+  unsigned long long *w_cn = reinterpret_cast<unsigned long long *>(smem_raw + WARPS * sizeof(WarpRing)) +
+                             (size_t)(threadIdx.x >> 5) * (a.nb + a.nb * a.ng);
+  unsigned long long *w_cg = w_cn + a.nb;
+  if (plain && (a.counts_in_smem & 1)) {
     unsigned long long *cn_sh = reinterpret_cast<unsigned long long *>(smem_raw + WARPS * sizeof(WarpRing));
     unsigned short *g_sh = reinterpret_cast<unsigned short *>(cn_sh + a.nb + a.nb * a.ng);
     const int ncount = a.nb + a.nb * a.ng;
@@ -196,8 +202,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   float *__restrict__ Ybuf = a.ybuf;
   const unsigned long long ray_off = a.ray_offset_dev ? *a.ray_offset_dev : a.ray_offset;
 
-  // warp-uniform: the emitting cell being initialised and its next ray
+  // warp-uniform: the emitting cell being initialised, its next ray, and (per-cell
+  // proposal) its hemisphere count
   int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N;
+  unsigned c_hemi = 4194304u;
   bool exhausted = false;
   unsigned head = 0, tail = 0;  // ring positions (mod POOL)
 
@@ -232,6 +240,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           c_r = 0;
           c_slot = (int)(p - 1 - a.chunk_p0);
           c_lin = (a.bi0 + c_bx) + nx * ((a.bj0 + c_by) + ny * (a.bk0 + c_bz));
+          if (!plain) {
+            c_hemi = __ldg(a.cell_hemi + c_lin);
+            if (cell_stage) {  // all of this cell's rays are initialised before the next cell's
+              const unsigned long long *gcn = a.cell_cn + (size_t)c_lin * nb;
+              const unsigned long long *gcg = a.cell_cg + (size_t)c_lin * nb * ng;
+              for (int i = lane; i < nb; i += 32) w_cn[i] = __ldg(gcn + i);
+              for (int i = lane; i < nb * ng; i += 32) w_cg[i] = __ldg(gcg + i);
+              __syncwarp();
+            }
+          }
         } else {
           exhausted = true;
         }
@@ -252,8 +270,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           if (plain) {
             nn = pick_guided(s_cn, s_guide, u.z);
             gg = pick(s_cg + nn * ng, ng, u.w);
+          } else if (cell_stage) {
+            hemi = c_hemi;
+            nn = pick(w_cn, nb, u.z);
+            gg = pick(w_cg + nn * ng, ng, u.w);
           } else {
-            hemi = __ldg(a.cell_hemi + cell);
+            hemi = c_hemi;
             const unsigned long long *cn = a.cell_cn + (size_t)cell * nb;
             const unsigned long long *cgn0 = a.cell_cg + (size_t)cell * nb * ng;
             nn = pick(cn, nb, u.z);
@@ -275,8 +297,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           if (plain) {
             wgt = __ldg(a.wgt32 + nn * ng + gg);
           } else {
-            const unsigned long long *cn = a.cell_cn + (size_t)cell * nb;
-            const unsigned long long *cgn = a.cell_cg + ((size_t)cell * nb + nn) * ng;
+            const unsigned long long *cn = cell_stage ? w_cn : a.cell_cn + (size_t)cell * nb;
+            const unsigned long long *cgn =
+                cell_stage ? w_cg + nn * ng : a.cell_cg + ((size_t)cell * nb + nn) * ng;
             const unsigned long long mn = cn[nn] - (nn ? cn[nn - 1] : 0ull);
             const unsigned long long mg = cgn[gg] - (gg ? cgn[gg - 1] : 0ull);
             const float p = u33_to_float(mn) * 2.3283064365386963e-10f * (u33_to_float(mg) * 2.3283064365386963e-10f);
@@ -648,10 +671,17 @@ int fp32_brick_volume() { return BRICK * BRICK * BRICK; }
 
 int fp32_guide_size() { return GUIDE; }
 
+// Ring states, then (bit 0) the plain counts and guide table or (bit 1) one
+// cell's counts per warp.
 static size_t fp32_smem_bytes(int nb, int ng, int counts_in_smem) {
-  return WARPS * sizeof(WarpRing) +
-         (counts_in_smem ? sizeof(unsigned long long) * (size_t)(nb + nb * ng) + sizeof(unsigned short) * GUIDE
-                         : 0);
+  const size_t rows = sizeof(unsigned long long) * (size_t)(nb + nb * ng);
+  const size_t plain = (counts_in_smem & 1) ? rows + sizeof(unsigned short) * GUIDE : 0;
+  const size_t cell = (counts_in_smem & 2) ? WARPS * rows : 0;
+  return WARPS * sizeof(WarpRing) + (plain > cell ? plain : cell);
+}
+
+int fp32_cell_stage_fits(int nb, int ng) {
+  return (size_t)WARPS * sizeof(unsigned long long) * (size_t)(nb + nb * ng) <= 48 * 1024;
 }
 
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,

@@ -42,7 +42,7 @@ struct mcrt_ctx {
       guide, ybuf, step_acc,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   // learned proposal: plain probabilities, feature scratch, per-ray steps, error flag
-  DevBuf p0_32, feat, ray_steps, lerr;
+  DevBuf p0_32, feat, ray_steps, lerr, kptab;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;

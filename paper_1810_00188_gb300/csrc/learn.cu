@@ -125,22 +125,14 @@ __global__ void __launch_bounds__(NTHR) features_kernel(const FeatArgs f) {
       }
     o[8] = (float)(mean / Ti);
     o[9] = (float)(sqrt(var / cnt) / Ti);
-    // Planck mean at T_i from the FP32 tables at the cell's interpolation position
+    // Planck mean at T_i: sum_n B_n sum_g w_g kappa_(n,g) / sum_n B_n with B and
+    // kappa linear in the fraction between nodes, i.e. a quadratic over a linear
+    // polynomial per node (coefficients summed on the host in FP64)
     const uint2 pk = f.fpos32[c];
     const unsigned it = pk.x >> 23;
     const float fr = __uint_as_float(0x3F800000u | (pk.x & 0x7FFFFFu)) - 1.f;
-    float num = 0.f, den = 0.f;
-    for (int n = 0; n < f.nb; ++n) {
-      const float2 b = f.btab32[(size_t)n * f.nT + it];
-      const float Bn = b.x + fr * b.y;
-      float s = 0.f;
-      for (int g = 0; g < f.ng; ++g) {
-        const float2 kk = f.ktab32[((size_t)n * f.ng + g) * f.nT + it];
-        s += f.w_g32[g] * (kk.x + fr * kk.y);
-      }
-      num += Bn * s;
-      den += Bn;
-    }
+    const float4 k0 = f.kptab[2 * it], k1 = f.kptab[2 * it + 1];
+    const float num = k0.x + fr * (k0.y + fr * k0.z), den = k0.w + fr * k1.x;
     o[10] = den > 0.f ? (float)((double)(num / den) * (double)__uint_as_float(pk.y) * f.h) : 0.f;
     o[11] = (float)(f.T_max / Ti);
   }
@@ -231,26 +223,25 @@ template <class T>
 __device__ bool quantize_row(const T *w, int K, double W, unsigned long long *cum) {
   if (!(W > 0.0)) return false;
   int kmax = 0;
-  for (int k = 1; k < K; ++k)
-    if ((double)w[k] > (double)w[kmax]) kmax = k;
+  double wmax = (double)w[0];
   long long total = 0;
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < K; ++k) {  // counts (kept in cum), their total, the first largest weight
     const double wk = (double)w[k];
-    if (wk > 0.0) {
-      const long long mk = (long long)floor((wk / W) * 4294967296.0);
-      total += mk < 1 ? 1 : mk;
+    if (wk > wmax) {
+      wmax = wk;
+      kmax = k;
     }
-  }
-  unsigned long long acc = 0;
-  for (int k = 0; k < K; ++k) {
-    const double wk = (double)w[k];
     long long mk = 0;
     if (wk > 0.0) {
       mk = (long long)floor((wk / W) * 4294967296.0);
       mk = mk < 1 ? 1 : mk;
     }
-    if (k == kmax) mk += 4294967296LL - total;
-    acc += (unsigned long long)mk;
+    cum[k] = (unsigned long long)mk;
+    total += mk;
+  }
+  unsigned long long acc = 0;
+  for (int k = 0; k < K; ++k) {
+    acc += cum[k] + (k == kmax ? (unsigned long long)(4294967296LL - total) : 0ull);
     cum[k] = acc;
   }
   return true;
@@ -258,7 +249,10 @@ __device__ bool quantize_row(const T *w, int K, double W, unsigned long long *cu
 
 // Warp-cooperative: q [nb * ng] spectral probabilities and q_up of one cell ->
 // cumulative band counts cn [nb], g counts within each band cg [nb][ng], and the
-// upward-hemisphere count of 2^23.  wn: nb doubles of scratch.
+// upward-hemisphere count of 2^23.  wn: nb doubles of scratch.  The band weights
+// are summed in band order on one lane (the same FP64 sum as the host's); the
+// counts, their exact integer total and the first largest weight are formed
+// across lanes.
 __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double *wn,
                               unsigned long long *cn, unsigned long long *cg, unsigned *hemi,
                               unsigned long long *err) {
@@ -282,10 +276,50 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
     }
   }
   __syncwarp();
-  if (lane == 0) {
-    double W = 0.0;
+  double W = 0.0;
+  if (lane == 0)
     for (int n = 0; n < nb; ++n) W += wn[n];
-    if (!quantize_row(wn, nb, W, cn)) atomicOr(err, 2ull);
+  W = __shfl_sync(0xffffffffu, W, 0);
+  if (!(W > 0.0)) {
+    if (lane == 0) atomicOr(err, 2ull);
+  } else {
+    long long tot = 0;
+    double bw = -1.0;
+    int bk = nb;
+    for (int n = lane; n < nb; n += 32) {
+      const double w = wn[n];
+      if (w > bw) {
+        bw = w;
+        bk = n;
+      }
+      long long mk = 0;
+      if (w > 0.0) {
+        mk = (long long)floor((w / W) * 4294967296.0);
+        mk = mk < 1 ? 1 : mk;
+      }
+      cn[n] = (unsigned long long)mk;
+      tot += mk;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      if (ow > bw || (ow == bw && ok < bk)) {
+        bw = ow;
+        bk = ok;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      unsigned long long acc = 0;
+      for (int n = 0; n < nb; ++n) {
+        acc += cn[n] + (n == bk ? (unsigned long long)(4294967296LL - tot) : 0ull);
+        cn[n] = acc;
+      }
+    }
+  }
+  if (lane == 0) {
     double hq = floor((double)q_up * 8388608.0 + 0.5);
     if (!(hq >= 1.0)) hq = 1.0;
     if (hq > 8388607.0) hq = 8388607.0;

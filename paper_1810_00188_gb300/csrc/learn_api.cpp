@@ -96,11 +96,7 @@ mcrt::FeatArgs feat_args(const mcrt_ctx *ctx, const int32_t *cells, long long n,
   f.T_max = proposal_T_max(ctx);
   f.field64 = (const double2 *)ctx->field64.p;
   f.fpos32 = (const uint2 *)ctx->fpos32.p;
-  f.ktab32 = (const float2 *)ctx->ktab32.p;
-  f.btab32 = (const float2 *)ctx->btab32.p;
-  f.w_g32 = (const float *)ctx->wg32.p;
-  f.nb = ctx->nb;
-  f.ng = ctx->ng;
+  f.kptab = (const float4 *)ctx->kptab.p;
   f.nT = ctx->nT;
   f.cells = cells;
   f.n = n;

@@ -396,6 +396,29 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 2 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 2 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->wg.p, kd->w_g, ng * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  // Planck-mean coefficients per node (features of the learned proposal)
+  std::vector<float4> kp(2 * (size_t)nT);
+  for (int t = 0; t < nT; ++t) {
+    double N0 = 0, N1 = 0, N2 = 0, D0 = 0, D1 = 0;
+    for (int n = 0; n < nb; ++n) {
+      const double2 b = b64[(size_t)n * nT + t];
+      double S = 0, dS = 0;
+      for (int g = 0; g < ng; ++g) {
+        const double2 k = k64[((size_t)n * ng + g) * nT + t];
+        S += kd->w_g[g] * k.x;
+        dS += kd->w_g[g] * k.y;
+      }
+      N0 += b.x * S;
+      N1 += b.x * dS + b.y * S;
+      N2 += b.y * dS;
+      D0 += b.x;
+      D1 += b.y;
+    }
+    kp[2 * t] = make_float4((float)N0, (float)N1, (float)N2, (float)D0);
+    kp[2 * t + 1] = make_float4((float)D1, 0.f, 0.f, 0.f);
+  }
+  CK(ensure(ctx->kptab, kp.size() * sizeof(float4)), "alloc Planck-mean table");
+  CK(cudaMemcpy(ctx->kptab.p, kp.data(), kp.size() * sizeof(float4), cudaMemcpyHostToDevice), "copy");
   std::vector<float> wg32(kd->w_g, kd->w_g + ng);
   CK(ensure(ctx->wg32, ng * sizeof(float)), "alloc w_g");
   CK(cudaMemcpy(ctx->wg32.p, wg32.data(), ng * sizeof(float), cudaMemcpyHostToDevice), "copy");
@@ -641,7 +664,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
-                      &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr};
+                      &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr, &ctx->kptab};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -106,9 +106,11 @@ struct FeatArgs {
   double T_wall[2], eps_wall[2], T_max;
   const double2 *field64;
   const uint2 *fpos32;
-  const float2 *ktab32, *btab32;
-  const float *w_g32;
-  int nb, ng, nT;
+  // Planck-mean absorption per T node as a rational function of the fraction fr
+  // towards the next node: [2 t] = {N0, N1, N2, D0}, [2 t + 1] = {D1, 0, 0, 0},
+  // kappa_P = (N0 + N1 fr + N2 fr^2) / (D0 + D1 fr) at x_ref
+  const float4 *kptab;
+  int nT;
   const int *cells;  // null: cells 0..n-1
   long long n;
   float *out;        // [n][12]

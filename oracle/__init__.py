@@ -54,7 +54,8 @@ class Params(C.Structure):
                 ("origin", C.c_int), ("use_box", C.c_int), ("box", C.c_int * 6),
                 ("nthreads", C.c_int), ("cell_cn", C.POINTER(C.c_uint64)),
                 ("cell_cg", C.POINTER(C.c_uint64)), ("cell_hemi", C.POINTER(C.c_uint32)),
-                ("tally", C.POINTER(C.c_double)), ("tally_cost", C.POINTER(C.c_double))]
+                ("tally", C.POINTER(C.c_double)), ("tally_cost", C.POINTER(C.c_double)),
+                ("mg_levels", C.c_int), ("mg_steps", C.c_int)]
 
 
 class CellSums(C.Structure):
@@ -92,6 +93,9 @@ def lib():
             L.orc_quantize.argtypes = [dp, C.c_int, up]
             L.orc_plain_proposal.argtypes = [C.POINTER(Problem), up, up, dp]
             L.orc_trace_ray.argtypes = [C.POINTER(Problem), C.POINTER(RayIn), C.POINTER(RayOut)]
+            L.orc_trace_ray_mg.argtypes = [C.POINTER(Problem), C.POINTER(RayIn), C.c_int, C.c_int,
+                                           C.POINTER(RayOut)]
+            L.orc_mg_max_levels.argtypes = [C.c_int, C.c_int, C.c_int]
             L.orc_solve.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.POINTER(CellSums)]
             L.orc_exchange.argtypes = [C.POINTER(Problem), C.POINTER(Params), dp, dp, dp, dp]
             L.orc_quadrature.argtypes = [C.POINTER(Problem), dp, dp, C.c_int, C.c_int, dp, dp,
@@ -194,7 +198,9 @@ def plain_proposal(grid, kd, T, x=None):
 
 
 def trace_ray(grid, kd, T, x, n, g, cell, frac, direction, tol=1e-4, max_steps=1 << 30,
-              seed=0, ray=0, snapshot=0):
+              seed=0, ray=0, snapshot=0, mg_levels=1, mg_steps=5):
+    """One ray's march (Algorithm 1); with mg_levels > 1 on overlaid coarsened
+    grids (Section 4.3)."""
     P = make_problem(grid, kd, T, x)
     R = RayIn()
     R.n, R.g = n, g
@@ -204,9 +210,18 @@ def trace_ray(grid, kd, T, x, n, g, cell, frac, direction, tol=1e-4, max_steps=1
         R.dir[a] = float(direction[a])
     R.tol, R.max_steps, R.seed, R.ray, R.snapshot = tol, max_steps, seed, ray, snapshot
     O = RayOut()
-    if lib().orc_trace_ray(C.byref(P), C.byref(R), C.byref(O)) != 0:
-        raise ValueError("bad ray")
+    if mg_levels > 1:
+        rc = lib().orc_trace_ray_mg(C.byref(P), C.byref(R), mg_levels, mg_steps, C.byref(O))
+    else:
+        rc = lib().orc_trace_ray(C.byref(P), C.byref(R), C.byref(O))
+    if rc != 0:
+        raise ValueError(f"bad ray ({rc})")
     return {f: getattr(O, f) for f, _ in RayOut._fields_}
+
+
+def mg_max_levels(nx, ny, nz):
+    """Number of overlaid grids the multigrid march can use on an nx x ny x nz grid."""
+    return int(lib().orc_mg_max_levels(nx, ny, nz))
 
 
 def default_threads():
@@ -226,14 +241,17 @@ def _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthre
 
 
 def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4,
-          max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, tally=False):
+          max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, tally=False,
+          mg_levels=1, mg_steps=5):
     """Per-cell ERMC estimate over the box (whole grid when box is None).
 
     Returns a dict of arrays shaped [bnz, bny, bnx]: q (Q_i, W/m^3), sigma
     (standard error of q), scale (S_i = mean of w sum|terms|), q_wall and
     sigma_wall (the wall-exchange part), steps and capped counts, and the raw
     sums.  ``proposal`` = (cell_cn [nc, nb], cell_cg [nc, nb, ng], cell_hemi
-    [nc]) overrides the plain T_max proposal per emitting cell.  With
+    [nc]) overrides the plain T_max proposal per emitting cell.  mg_levels > 1
+    marches rays on that many overlaid grids, mg_steps segments per grid
+    (Section 4.3).  With
     ``tally`` the result also holds "tally" [bnz, bny, bnx, nb * ng, 2]: per
     spectral point and hemisphere (0 upward), (1/N) sum of Y^2 p(n,g) p(h) over
     the rays that drew them, and "tally_cost" (same shape): (1/N) sum of
@@ -241,6 +259,7 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
     """
     P = make_problem(grid, kd, T, x)
     S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, box, nthreads)
+    S.mg_levels, S.mg_steps = mg_levels, mg_steps
     b = box if box is not None else (0, grid.nx, 0, grid.ny, 0, grid.nz)
     shape = (max(b[5] - b[4], 0), max(b[3] - b[2], 0), max(b[1] - b[0], 0))
     nc = int(np.prod(shape))

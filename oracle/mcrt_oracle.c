@@ -189,6 +189,89 @@ static int pick(const uint64_t *cum, int K, uint32_t u) {
 
 static uint64_t count_of(const uint64_t *cum, int k) { return k == 0 ? cum[0] : cum[k] - cum[k - 1]; }
 
+/* ---- multigrid (Section 4.3) ------------------------------------------------ */
+/* Overlaid grids, each coarsened by 2 from the previous one: grid 0 is the
+ * problem's own, grid l + 1 holds in each of its cells the mean T and x of the
+ * 2x2x2 cells of grid l it covers (the coarse temperatures come from the fine
+ * solution).  A grid is added while every dimension of the previous one is even
+ * and halves to at least 3 cells, the paper's smallest 3^3 mesh. */
+enum { ORC_MG_MAX = 16 };
+
+typedef struct {
+  int L; /* grids in use */
+  int k; /* segments marched on a grid before falling onto the next */
+  int N[ORC_MG_MAX][3];
+  double delta[ORC_MG_MAX][3];
+  const double *T[ORC_MG_MAX], *x[ORC_MG_MAX]; /* x NULL: x_ref everywhere */
+  double *own[ORC_MG_MAX];                     /* coarse T and x storage */
+} mg_grids;
+
+int orc_mg_max_levels(int nx, int ny, int nz) {
+  int n[3] = {nx, ny, nz}, L = 1;
+  while (L < ORC_MG_MAX) {
+    int ok = 1;
+    for (int a = 0; a < 3; ++a)
+      if (n[a] % 2 != 0 || n[a] / 2 < 3) ok = 0;
+    if (!ok) break;
+    for (int a = 0; a < 3; ++a) n[a] /= 2;
+    ++L;
+  }
+  return L;
+}
+
+static void mg_free(mg_grids *M) {
+  for (int l = 0; l < ORC_MG_MAX; ++l) free(M->own[l]);
+  memset(M, 0, sizeof(*M));
+}
+
+/* mean of the 8 children of coarse cell (I, J, K), z outermost, x innermost */
+static double mean8(const double *v, const int n[3], int I, int J, int K) {
+  double s = 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a)
+        s += v[(size_t)(2 * I + a) + (size_t)n[0] * ((size_t)(2 * J + b) + (size_t)n[1] * (2 * K + c))];
+  return s * 0.125;
+}
+
+static int mg_build(const orc_problem *P, int L, int k, mg_grids *M) {
+  memset(M, 0, sizeof(*M));
+  if (L < 1 || L > orc_mg_max_levels(P->nx, P->ny, P->nz) || k < 1) return -3;
+  M->L = L;
+  M->k = k;
+  M->N[0][0] = P->nx;
+  M->N[0][1] = P->ny;
+  M->N[0][2] = P->nz;
+  M->delta[0][0] = P->lx / P->nx;
+  M->delta[0][1] = P->ly / P->ny;
+  M->delta[0][2] = P->lz / P->nz;
+  M->T[0] = P->T;
+  M->x[0] = P->xh2o;
+  for (int l = 1; l < L; ++l) {
+    for (int a = 0; a < 3; ++a) M->N[l][a] = M->N[l - 1][a] / 2;
+    M->delta[l][0] = P->lx / M->N[l][0];
+    M->delta[l][1] = P->ly / M->N[l][1];
+    M->delta[l][2] = P->lz / M->N[l][2];
+    const size_t nc = (size_t)M->N[l][0] * M->N[l][1] * M->N[l][2];
+    M->own[l] = (double *)malloc(sizeof(double) * nc * 2);
+    if (!M->own[l]) {
+      mg_free(M);
+      return -4;
+    }
+    double *T = M->own[l], *x = P->xh2o ? M->own[l] + nc : NULL;
+    for (int K = 0; K < M->N[l][2]; ++K)
+      for (int J = 0; J < M->N[l][1]; ++J)
+        for (int I = 0; I < M->N[l][0]; ++I) {
+          const size_t c = (size_t)I + (size_t)M->N[l][0] * ((size_t)J + (size_t)M->N[l][1] * K);
+          T[c] = mean8(M->T[l - 1], M->N[l - 1], I, J, K);
+          if (x) x[c] = mean8(M->x[l - 1], M->N[l - 1], I, J, K);
+        }
+    M->T[l] = T;
+    M->x[l] = x;
+  }
+  return 0;
+}
+
 /* ---- one ray: Algorithm 1 "March", Eqs. 2, 3, 14 ---------------------------- */
 
 typedef struct {
@@ -199,12 +282,14 @@ typedef struct {
   double wall[2];
 } xch_acc;
 
-static void trace_core(const orc_problem *P, int n, int g, const int cell0[3],
+static void trace_core(const orc_problem *P, const mg_grids *M, int n, int g, const int cell0[3],
                        const double frac0[3], const double dir0[3], double tol,
                        int max_steps, uint64_t seed, uint32_t cellid, uint32_t ray,
                        uint32_t snap, orc_ray_out *o, xch_acc *xa) {
-  const int N[3] = {P->nx, P->ny, P->nz};
-  const double delta[3] = {P->lx / P->nx, P->ly / P->ny, P->lz / P->nz};
+  int N[3] = {P->nx, P->ny, P->nz};
+  double delta[3] = {P->lx / P->nx, P->ly / P->ny, P->lz / P->nz};
+  const double *Tl = P->T, *xl = P->xh2o; /* fields of the current grid */
+  int lev = 0, lsteps = 0;                /* current grid, segments marched on it */
   int c[3] = {cell0[0], cell0[1], cell0[2]};
   double fr[3] = {frac0[0], frac0[1], frac0[2]};
   double d[3] = {dir0[0], dir0[1], dir0[2]};
@@ -244,14 +329,38 @@ restart:
   tprev = 0.0;
 
   for (;;) {
+    if (M && lev + 1 < M->L && lsteps >= M->k) {
+      /* multigrid (Section 4.3): after k segments on this grid the ray falls onto
+       * the next coarser one at its current point; its position inside the
+       * coarse cell follows from the position inside the current cell */
+      for (int b = 0; b < 3; ++b) {
+        if (sgn[b] > 0)
+          fr[b] = 1.0 - (tnext[b] - tprev) / tstep[b];
+        else if (sgn[b] < 0)
+          fr[b] = (tnext[b] - tprev) / tstep[b];
+        if (fr[b] < 0.0) fr[b] = 0.0;
+        if (fr[b] > 1.0) fr[b] = 1.0;
+        fr[b] = ((double)(c[b] & 1) + fr[b]) * 0.5;
+        c[b] >>= 1;
+      }
+      ++lev;
+      lsteps = 0;
+      for (int b = 0; b < 3; ++b) {
+        N[b] = M->N[lev][b];
+        delta[b] = M->delta[lev][b];
+      }
+      Tl = M->T[lev];
+      xl = M->x[lev];
+      goto restart;
+    }
     int a = 0; /* face crossed first; lowest axis on ties */
     if (tnext[1] < tnext[a]) a = 1;
     if (tnext[2] < tnext[a]) a = 2;
     double ds = tnext[a] - tprev;
     if (ds < 0.0) ds = 0.0;
     const size_t j = (size_t)c[0] + (size_t)N[0] * ((size_t)c[1] + (size_t)N[1] * c[2]);
-    const double kap_j = kappa_at(P, n, g, P->T[j], x_of(P, j));
-    const double B_j = B_at(P, n, P->T[j]);
+    const double kap_j = kappa_at(P, n, g, Tl[j], xl ? xl[j] : P->x_ref);
+    const double B_j = B_at(P, n, Tl[j]);
     const double alpha = -expm1(-kap_j * ds); /* Eq. 2: 1 - exp(-kappa_j l_j) */
     const double term = kap_i * (B_i - B_j) * tau * alpha; /* Eq. 14 per segment */
     if (xa && xa->row) {
@@ -267,6 +376,7 @@ restart:
     B_last = B_j;
     path += ds;
     ++steps;
+    ++lsteps;
     if (tau <= tol) break;
     if (steps >= max_steps) {
       capped = 1;
@@ -340,8 +450,22 @@ int orc_trace_ray(const orc_problem *P, const orc_ray_in *in, orc_ray_out *out) 
   if (in->n < 0 || in->n >= P->n_bands || in->g < 0 || in->g >= P->n_g) return -1;
   const uint32_t cellid =
       (uint32_t)(in->cell[0] + P->nx * (in->cell[1] + P->ny * in->cell[2]));
-  trace_core(P, in->n, in->g, in->cell, in->frac, in->dir, in->tol, in->max_steps, in->seed,
+  trace_core(P, NULL, in->n, in->g, in->cell, in->frac, in->dir, in->tol, in->max_steps, in->seed,
              cellid, in->ray, in->snapshot, out, NULL);
+  return 0;
+}
+
+int orc_trace_ray_mg(const orc_problem *P, const orc_ray_in *in, int mg_levels, int mg_steps,
+                     orc_ray_out *out) {
+  if (in->n < 0 || in->n >= P->n_bands || in->g < 0 || in->g >= P->n_g) return -1;
+  mg_grids M;
+  const int rc = mg_build(P, mg_levels < 1 ? 1 : mg_levels, mg_steps, &M);
+  if (rc != 0) return rc;
+  const uint32_t cellid =
+      (uint32_t)(in->cell[0] + P->nx * (in->cell[1] + P->ny * in->cell[2]));
+  trace_core(P, &M, in->n, in->g, in->cell, in->frac, in->dir, in->tol, in->max_steps, in->seed,
+             cellid, in->ray, in->snapshot, out, NULL);
+  mg_free(&M);
   return 0;
 }
 
@@ -414,6 +538,7 @@ typedef struct {
   /* exchange mode */
   double *G, *G2, *Gw, *Gw2;
   pthread_mutex_t lock;
+  const mg_grids *M; /* multigrid, or NULL */
 } solve_job;
 
 static void solve_cell(solve_job *J, long b, xch_acc *xa) {
@@ -439,8 +564,8 @@ static void solve_cell(solve_job *J, long b, xch_acc *xa) {
       xa->ntouched = 0;
       xa->wall[0] = xa->wall[1] = 0.0;
     }
-    trace_core(P, R.n, R.g, cell0, R.frac, R.dir, S->tol, S->max_steps, S->seed, cellid, ray,
-               S->snapshot, &o, xa);
+    trace_core(P, J->M, R.n, R.g, cell0, R.frac, R.dir, S->tol, S->max_steps, S->seed, cellid,
+               ray, S->snapshot, &o, xa);
     const double Y = R.w * o.X;
     const size_t tix = (size_t)b * nb * ng * 2 + ((size_t)R.n * ng + R.g) * 2 + R.h;
     if (S->tally) S->tally[tix] += Y * Y * R.p_ng * R.p_h / (double)S->rays_per_cell;
@@ -546,11 +671,16 @@ int orc_solve(const orc_problem *P, const orc_params *S, orc_cell_sums *out) {
   uint64_t *cn = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands);
   uint64_t *cg = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands * P->n_g);
   solve_job J;
-  int rc = setup_job(P, S, &J, cn, cg);
+  mg_grids M;
+  int use_mg = S->mg_levels > 1;
+  int rc = use_mg ? mg_build(P, S->mg_levels, S->mg_steps, &M) : 0;
+  if (rc == 0) rc = setup_job(P, S, &J, cn, cg);
   if (rc == 0) {
     J.out = out;
+    J.M = use_mg ? &M : NULL;
     run_jobs(&J, S->nthreads);
   }
+  if (use_mg) mg_free(&M);
   free(cn);
   free(cg);
   return rc;
@@ -635,7 +765,7 @@ static void *quad_worker(void *arg) {
                 wv = Q->vw[v];
               }
               orc_ray_out o;
-              trace_core(P, n, g, cell0, fr, dir, Q->tol, Q->max_steps, 0, (uint32_t)c, 0, 0, &o,
+              trace_core(P, NULL, n, g, cell0, fr, dir, Q->tol, Q->max_steps, 0, (uint32_t)c, 0, 0, &o,
                          NULL);
               acc += wa * wv * o.X;
             }

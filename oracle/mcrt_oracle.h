@@ -58,6 +58,13 @@ typedef struct {
    * steps_r / (p(n,g) p(h)); weighted by q(n,g) q(h) and summed it is the
    * unbiased estimate of the mean medium segments per ray under q. */
   double *tally_cost;
+  /* Multigrid (Section 4.3): number of overlaid grids (0 or 1: the problem's
+   * grid only) and the segments a ray marches on each grid before it falls onto
+   * the next coarser one.  Grid l + 1 halves every dimension of grid l and holds
+   * the mean T and x of its 2x2x2 children; it exists while every dimension of
+   * grid l is even and halves to at least 3 (orc_mg_max_levels). */
+  int mg_levels;
+  int mg_steps;
 } orc_params;
 
 typedef struct {             /* per emitting cell of the box, x fastest           */
@@ -99,6 +106,11 @@ double orc_interp(const double *v, double T0, double dT, int nT, double T);
 int orc_quantize(const double *w, int K, uint64_t *cum);
 int orc_plain_proposal(const orc_problem *P, uint64_t *cn, uint64_t *cg, double *T_max);
 int orc_trace_ray(const orc_problem *P, const orc_ray_in *in, orc_ray_out *out);
+int orc_mg_max_levels(int nx, int ny, int nz);
+/* One ray as orc_trace_ray, marched on mg_levels overlaid grids with mg_steps
+ * segments per grid (Section 4.3). */
+int orc_trace_ray_mg(const orc_problem *P, const orc_ray_in *in, int mg_levels, int mg_steps,
+                     orc_ray_out *out);
 int orc_solve(const orc_problem *P, const orc_params *S, orc_cell_sums *out);
 int orc_exchange(const orc_problem *P, const orc_params *S, double *G, double *G2,
                  double *Gw, double *Gw2);

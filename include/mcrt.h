@@ -104,6 +104,17 @@ typedef struct {
   int box[6];              /* i0,i1,j0,j1,k0,k1, half-open, may be empty          */
   uint64_t *steps_out;     /* optional per-cell medium-segment counts (same `mem`
                               as the outputs), or NULL                           */
+  /* Multigrid (Section 4.3, "Multigrid"): rays march on overlaid grids that
+   * coarsen by 2, mg_steps segments on each grid before falling onto the next
+   * coarser one at their current point, and run to termination on the
+   * coarsest.  Grid l + 1 halves every dimension of grid l and holds the mean T
+   * and x of the 2x2x2 cells it covers; it exists while every dimension of
+   * grid l is even and halves to at least 3 cells (mcrt_multigrid_levels).
+   * An approximation of the single-grid estimate (the coarse cells average T
+   * before the table lookups), not an unbiased estimator of it. */
+  int mg_levels;           /* grids used, 0 or 1: the grid itself (exact march)   */
+  int mg_steps;            /* segments per grid but the coarsest, >= 1 when
+                              mg_levels > 1 (the paper uses 5)                   */
 } mcrt_solve_params;
 
 typedef struct {
@@ -129,6 +140,12 @@ typedef struct {
   int scratch_mib;         /* 0: default (1024); cap of the per-ray sample
                               scratch; larger solves run in several chunks      */
 } mcrt_tuning;
+
+/* Number of overlaid grids the multigrid march can use on an nx x ny x nz grid
+ * (1 when no dimension pair allows a coarser grid): the paper's counts, e.g.
+ * 3 for 16^3, 5 for 64^3, 6 for 128^3, 7 for 192^3 (Sections 4.3 and 5).
+ * Returns 0 for a non-positive dimension. */
+int mcrt_multigrid_levels(int nx, int ny, int nz);
 
 /* Creates a context on grid->device.  *out receives the handle (NULL on error).
  * Errors: MCRT_E_ARG (bad geometry / walls), MCRT_E_CUDA (no such device). */

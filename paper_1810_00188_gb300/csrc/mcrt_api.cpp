@@ -151,7 +151,9 @@ namespace {
 // tables are set (recomputed whenever either changes).
 int refresh_positions(mcrt_ctx *ctx, cudaStream_t s) {
   if (!ctx->have_kdist || !ctx->have_fields || ctx->nT > 512) return MCRT_OK;
-  const long long n = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+  // every grid of the multigrid march, the problem's own first
+  const mcrt_grid_desc &g = ctx->grid;
+  const long long n = mcrt::multigrid_cells(g.nx, g.ny, g.nz, mcrt::multigrid_levels(g.nx, g.ny, g.nz));
   CK(ensure(ctx->fpos32, (size_t)n * sizeof(uint2)), "alloc positions");
   CK(mcrt::launch_pack_positions((const double2 *)ctx->field64.p, n, ctx->T0, 1.0 / ctx->dT, ctx->nT,
                                  1.0 / ctx->x_ref, (uint2 *)ctx->fpos32.p, s),
@@ -208,6 +210,9 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
     return fail(ctx, MCRT_E_STATE, "no cell proposal");
   if (p->precision == MCRT_FP32 && ctx->nT > 512)
     return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
+  if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(g.nx, g.ny, g.nz))
+    return fail(ctx, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)]");
+  if (p->mg_levels > 1 && p->mg_steps < 1) return fail(ctx, MCRT_E_ARG, "mg_steps < 1");
   return MCRT_OK;
 }
 
@@ -255,6 +260,8 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   }
   a.rays = p->rays_per_cell;
   a.max_steps = p->max_steps;
+  a.mg_levels = p->mg_levels > 1 ? p->mg_levels : 1;
+  a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
   a.origin = p->origin;
   a.tol = p->tol;
   a.key0 = (unsigned)(p->seed & 0xffffffffu);
@@ -290,6 +297,8 @@ const char *mcrt_status_string(int status) {
 }
 
 const char *mcrt_last_error(const mcrt_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int mcrt_multigrid_levels(int nx, int ny, int nz) { return mcrt::multigrid_levels(nx, ny, nz); }
 
 int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   if (!out) return MCRT_E_ARG;
@@ -438,7 +447,11 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   ctx->have_fields = false;
   ctx->prop_valid = false;
-  CK(ensure(ctx->field64, (size_t)n * sizeof(double2)), "alloc field");
+  // field64 also holds the coarser grids of the multigrid march after the
+  // problem's own (Section 4.3)
+  const int mg_levels = mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+  const long long n_all = mcrt::multigrid_cells(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, mg_levels);
+  CK(ensure(ctx->field64, (size_t)n_all * sizeof(double2)), "alloc field");
   CK(ensure(ctx->field32, (size_t)n * sizeof(float2)), "alloc field");
   const void *dT = T, *dx = x;
   DevBuf stage;
@@ -458,6 +471,16 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   cudaError_t e = mcrt::launch_pack_fields(dT, dx, fp64, x_ref, n, (double2 *)ctx->field64.p,
                                            (float2 *)ctx->field32.p,
                                            (unsigned long long *)ctx->fstats.p, s);
+  {
+    double2 *lev = (double2 *)ctx->field64.p;
+    int d[3] = {ctx->grid.nx, ctx->grid.ny, ctx->grid.nz};
+    for (int l = 1; l < mg_levels && e == cudaSuccess; ++l) {
+      double2 *next = lev + (size_t)d[0] * d[1] * d[2];
+      e = mcrt::launch_coarsen(lev, d[0], d[1], d[2], next, s);
+      for (int a = 0; a < 3; ++a) d[a] /= 2;
+      lev = next;
+    }
+  }
   unsigned long long st[3] = {0, 0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st, ctx->fstats.p, sizeof(st), cudaMemcpyDeviceToHost, s);
@@ -746,6 +769,9 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
     return fail(ctx, MCRT_E_ARG, "bad proposal");
   if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
     return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
+  if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz))
+    return fail(ctx, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)]");
+  if (p->mg_levels > 1 && p->mg_steps < 1) return fail(ctx, MCRT_E_ARG, "mg_steps < 1");
   // scratch layout in the static array: counters | per-position step sums | samples
   const size_t total = mcrt::noalloc_scratch_bytes();
   const size_t head_bytes = 256;
@@ -820,6 +846,8 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   }
   a.rays = p->rays_per_cell;
   a.max_steps = p->max_steps;
+  a.mg_levels = p->mg_levels > 1 ? p->mg_levels : 1;
+  a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
   a.origin = p->origin;
   a.tol = p->tol;
   a.key0 = (unsigned)(p->seed & 0xffffffffu);
@@ -925,6 +953,9 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     if (p->proposal == MCRT_PROPOSAL_CELL && !c->have_cell_prop)
       return fail(c, MCRT_E_STATE, "no cell proposal");
     if (weights && !(weights[k] > 0.0) ) return fail(c, MCRT_E_ARG, "batch weights must be > 0");
+    if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(c->grid.nx, c->grid.ny, c->grid.nz) ||
+        (p->mg_levels > 1 && p->mg_steps < 1))
+      return fail(c, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)] or mg_steps < 1");
     for (int j = 0; j < k; ++j)
       if (items[j].ctx == c) return fail(c, MCRT_E_ARG, "a context appears twice in the batch");
   }
@@ -1002,6 +1033,8 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     }
     a.rays = p->rays_per_cell;
     a.max_steps = p->max_steps;
+    a.mg_levels = p->mg_levels > 1 ? p->mg_levels : 1;
+    a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
     a.origin = p->origin;
     a.tol = p->tol;
     a.key0 = (unsigned)(p->seed & 0xffffffffu);
@@ -1034,7 +1067,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   mcrt_ctx *c0 = items[0].ctx;
   int bps = 0, nsm = 0;
   BK(mcrt::prepare_trace_fp32(c0->min_blocks, c0->steps_per_round, args[0].nb, args[0].ng,
-                              args[0].counts_in_smem, &bps, &nsm),
+                              args[0].counts_in_smem, args[0].mg_levels > 1, &bps, &nsm),
      "prepare launch");
   const long long total = (long long)bps * nsm;
   std::vector<int> order(n);

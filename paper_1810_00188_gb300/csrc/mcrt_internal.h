@@ -51,6 +51,9 @@ struct TraceArgs {
   // replay) when non-null; persistent grid size override (0: one full wave)
   const unsigned long long *ray_offset_dev;
   int grid_blocks;
+  // multigrid (Section 4.3): grids used (1: exact march) and segments per grid;
+  // the fields of grid l (l >= 1) follow those of grid l - 1 in field64 / fpos32
+  int mg_levels, mg_steps;
   // solve
   int rays, max_steps, origin;
   double tol;
@@ -63,6 +66,13 @@ struct TraceArgs {
   unsigned long long *steps_cell;
   unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps) [5] error flags
 };
+
+// Multigrid grid count of an nx x ny x nz grid and the cells of all its grids.
+int multigrid_levels(int nx, int ny, int nz);
+long long multigrid_cells(int nx, int ny, int nz, int levels);
+// Fields of grid l + 1 (2x2x2 means of T and x) from grid l of n0 x n1 x n2 cells.
+cudaError_t launch_coarsen(const double2 *fine, int n0, int n1, int n2, double2 *coarse,
+                           cudaStream_t s);
 
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
@@ -77,7 +87,7 @@ long long fp32_bricks_positions(int bnx, int bny, int bnz);
 // Sets the launch attributes of the chosen FP32 variant and returns its
 // resident CTAs per SM (call before stream capture).
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
-                               int *blocks_per_sm, int *num_sms);
+                               int multigrid, int *blocks_per_sm, int *num_sms);
 int fp32_brick_volume();
 int fp32_cell_stage_fits(int nb, int ng);
 int fp32_guide_size();

@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   const int cj = a.bj0 + (int)((w / a.bnx) % a.bny);
   const int ck = a.bk0 + (int)(w / ((long long)a.bnx * a.bny));
   const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nb = a.nb, ng = a.ng, nT = a.nT;
-  const int nxyz = nxy * nz;
   const unsigned cell = (unsigned)(ci + nx * cj + nxy * ck);
 
   const R2 *__restrict__ field = Prec<R>::field(a);
@@ -296,6 +295,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     R X = 0, tau = 1, B_last = B_i;
     int steps = 0;
     unsigned nrefl = 0;
+    // multigrid (Section 4.3): current grid, its dimensions and the offset of its
+    // fields, segments marched on it, and the face counter step: grid l keeps
+    // every inc-th face of the grid the axis parameters were set up on
+    int lev = 0, lsteps = 0, nxl = nx, nyl = ny, nzl = nz;
+    long long loff = 0;
+    R inc = 1;
     for (;;) {
       int ax;
       R tn;
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
         tn = tnz;
       }
       const R ds = fmax(tn - tprev, (R)0);
-      const R2 f = __ldg(field + lin);
+      const R2 f = __ldg(field + loff + lin);
       int it;
       R fr;
       tpos<R>(f.x, T0, inv_dT, nT, it, fr);
@@ -324,42 +329,44 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
       tau *= trans;                     // Eq. 3
       B_last = Bj;
       ++steps;
+      ++lsteps;
       if (tau <= tol) break;
       if (steps >= a.max_steps) {
         ++ncap;
         break;
       }
       tprev = tn;
+      const int nxyl = nxl * nyl;
       if (ax == 0) {
-        cntx += (R)1;
+        cntx += inc;
         tnx = fma(cntx, tsx, t0x);
         ix += sx;
         lin += sx;
-        if (ix >= nx) {
-          ix -= nx;
-          lin -= nx;
+        if (ix >= nxl) {
+          ix -= nxl;
+          lin -= nxl;
         } else if (ix < 0) {
-          ix += nx;
-          lin += nx;
+          ix += nxl;
+          lin += nxl;
         }
       } else if (ax == 2) {
-        cntz += (R)1;
+        cntz += inc;
         tnz = fma(cntz, tsz, t0z);
         iz += sz;
-        lin += sz * nxy;
-        if (iz >= nz) {
-          iz -= nz;
-          lin -= nxyz;
+        lin += sz * nxyl;
+        if (iz >= nzl) {
+          iz -= nzl;
+          lin -= nxyl * nzl;
         } else if (iz < 0) {
-          iz += nz;
-          lin += nxyz;
+          iz += nzl;
+          lin += nxyl * nzl;
         }
       } else {
-        cnty += (R)1;
+        cnty += inc;
         tny = fma(cnty, tsy, t0y);
         iy += sy_;
-        lin += sy_ * nx;
-        if (iy < 0 || iy >= ny) {
+        lin += sy_ * nxl;
+        if (iy < 0 || iy >= nyl) {
           // wall event: the wall absorbs eps of the ray and emits at T_wall
           const int wl = iy < 0 ? 0 : 1;
           const R eps = (R)a.eps_wall[wl];
@@ -368,21 +375,22 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
           tau *= (R)1 - eps;
           ++nwall;
           if (eps >= (R)1 || tau <= tol) break;
-          // reflect from the crossing point at t = tprev
+          // reflect from the crossing point at t = tprev (fractions of the
+          // current grid's cell, whose extent along an axis is inc face steps)
           R nfx = fx, nfz = fz;
           if (sx > 0)
-            nfx = (R)1 - (tnx - tprev) / tsx;
+            nfx = (R)1 - (tnx - tprev) / (tsx * inc);
           else if (sx < 0)
-            nfx = (tnx - tprev) / tsx;
+            nfx = (tnx - tprev) / (tsx * inc);
           if (sz > 0)
-            nfz = (R)1 - (tnz - tprev) / tsz;
+            nfz = (R)1 - (tnz - tprev) / (tsz * inc);
           else if (sz < 0)
-            nfz = (tnz - tprev) / tsz;
+            nfz = (tnz - tprev) / (tsz * inc);
           fx = fmin(fmax(nfx, (R)0), (R)1);
           fz = fmin(fmax(nfz, (R)0), (R)1);
           fy = wl == 0 ? (R)0 : (R)1;
-          iy = wl == 0 ? 0 : ny - 1;
-          lin = ix + nx * iy + nxy * iz;
+          iy = wl == 0 ? 0 : nyl - 1;
+          lin = ix + nxl * iy + nxyl * iz;
           if (a.reflect == 1) {
             ddy = -ddy;
           } else {
@@ -398,15 +406,45 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
             ddz = sr * sp;
           }
           ++nrefl;
-          axis_setup<R>(ddx, fx, DX, sx, t0x, tsx);
-          axis_setup<R>(ddy, fy, DY, sy_, t0y, tsy);
-          axis_setup<R>(ddz, fz, DZ, sz, t0z, tsz);
+          const R gl = (R)(1 << lev);  // cell size of the current grid / finest
+          axis_setup<R>(ddx, fx, DX * gl, sx, t0x, tsx);
+          axis_setup<R>(ddy, fy, DY * gl, sy_, t0y, tsy);
+          axis_setup<R>(ddz, fz, DZ * gl, sz, t0z, tsz);
           cntx = cnty = cntz = 0;
           tnx = t0x;
           tny = t0y;
           tnz = t0z;
           tprev = 0;
+          inc = 1;
         }
+      }
+      if (lev + 1 < a.mg_levels && lsteps >= a.mg_steps) {
+        // multigrid (Section 4.3): fall onto the next coarser grid here.  Its
+        // faces are the even-numbered faces of this grid, so an axis whose next
+        // face is odd-numbered skips it; the cell is the one containing this one.
+        if (sx != 0 && ((sx > 0 ? ix + 1 : ix) & 1)) {
+          cntx += inc;
+          tnx = fma(cntx, tsx, t0x);
+        }
+        if (sy_ != 0 && ((sy_ > 0 ? iy + 1 : iy) & 1)) {
+          cnty += inc;
+          tny = fma(cnty, tsy, t0y);
+        }
+        if (sz != 0 && ((sz > 0 ? iz + 1 : iz) & 1)) {
+          cntz += inc;
+          tnz = fma(cntz, tsz, t0z);
+        }
+        loff += (long long)nxl * nyl * nzl;
+        nxl >>= 1;
+        nyl >>= 1;
+        nzl >>= 1;
+        ix >>= 1;
+        iy >>= 1;
+        iz >>= 1;
+        lin = ix + nxl * (iy + nyl * iz);
+        inc *= (R)2;
+        ++lev;
+        lsteps = 0;
       }
     }
     if (tau > (R)0) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)

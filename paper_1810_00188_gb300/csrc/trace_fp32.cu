@@ -154,7 +154,9 @@ __device__ __forceinline__ bool brick_cell(const TraceArgs &a, long long p, int 
   return bx < a.bnx && by < a.bny && bz < a.bnz;
 }
 
-template <int MINB, int KSTEPS>
+// MG: the multigrid march of Section 4.3 (a.mg_levels grids); the exact march
+// is the MG = false instantiation.
+template <int MINB, int KSTEPS, bool MG>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpRing *rings = reinterpret_cast<WarpRing *>(smem_raw);
@@ -218,6 +220,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   unsigned ray = 0, nrefl = 0, cellid = 0;
   float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
   float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
+  // multigrid: current grid, segments marched on it, offset of its fields, and
+  // the face counter step (grid lev keeps every inc-th face of the grid the
+  // axis parameters were set up on)
+  int lev = 0, lsteps = 0;
+  unsigned loff = 0;
+  float inc = 1.f;
   unsigned long long tot_steps = 0;
   unsigned tot_cap = 0, tot_wall = 0, max_ray = 0, tot_rays = 0;
   int acc_slot = -1;  // run of steps for the per-cell step counts
@@ -381,6 +389,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         steps = 0;
         nrefl = 0;
         active = true;
+        if (MG) {
+          lev = 0;
+          lsteps = 0;
+          loff = 0;
+          inc = 1.f;
+        }
       }
       head += (unsigned)min(__popc(idle), avail);
       __syncwarp();
@@ -406,7 +420,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         tn = tnz;
       }
       const float ds = fmaxf(tn - tprev, 0.f);
-      const uint2 f = __ldg(field + lin);
+      const uint2 f = __ldg(field + (MG ? loff + lin : lin));
       unsigned it;
       float fr;
       tpos(f.x, it, fr);
@@ -420,6 +434,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       tau *= trans;                     // Eq. 3
       B_last = Bj;
       ++steps;
+      if (MG) ++lsteps;
       bool done = tau <= tol;
       if (!done && steps >= a.max_steps) {
         done = true;
@@ -427,26 +442,30 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       }
       if (!done) {
         tprev = tn;
+        // dimensions of the current grid
+        const int nxl = MG ? nx >> lev : nx, nyl = MG ? ny >> lev : ny, nzl = MG ? nz >> lev : nz;
+        const int nxyl = MG ? nxl * nyl : nxy;
         {
           // branch-free advance of the crossed axis (lanes cross different axes)
           const bool mx = ax == 0, my = ax == 1, mz = ax == 2;
-          cntx += mx ? 1.f : 0.f;
-          cnty += my ? 1.f : 0.f;
-          cntz += mz ? 1.f : 0.f;
+          const float step = MG ? inc : 1.f;
+          cntx += mx ? step : 0.f;
+          cnty += my ? step : 0.f;
+          cntz += mz ? step : 0.f;
           tnx = mx ? fmaf(cntx, tsx, t0x) : tnx;
           tny = my ? fmaf(cnty, tsy, t0y) : tny;
           tnz = mz ? fmaf(cntz, tsz, t0z) : tnz;
           ix += mx ? sx : 0;
           iy += my ? sy : 0;
           iz += mz ? sz : 0;
-          lin += mx ? (unsigned)sx : (my ? (unsigned)(sy * nx) : (unsigned)(sz * nxy));
-          const int wx = ix >= nx ? -nx : (ix < 0 ? nx : 0);
+          lin += mx ? (unsigned)sx : (my ? (unsigned)(sy * nxl) : (unsigned)(sz * nxyl));
+          const int wx = ix >= nxl ? -nxl : (ix < 0 ? nxl : 0);
           ix += wx;
           lin += (unsigned)wx;
-          const int wz = iz >= nz ? -nz : (iz < 0 ? nz : 0);
+          const int wz = iz >= nzl ? -nzl : (iz < 0 ? nzl : 0);
           iz += wz;
-          lin += (unsigned)(wz * nxy);
-          if (iy < 0 || iy >= ny) {
+          lin += (unsigned)(wz * nxyl);
+          if (iy < 0 || iy >= nyl) {
             // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
             const int wl = iy < 0 ? 0 : 1;
             const float eps = wl ? eps1 : eps0;
@@ -457,26 +476,32 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             if (eps >= 1.f || tau <= tol) {
               done = true;
             } else {
+              // fractions of the current grid's cell, whose extent along an
+              // axis is inc face steps of the axis parameters
+              const float cx = MG ? tsx * inc : tsx, cz = MG ? tsz * inc : tsz;
               float nfx = 0.5f, nfz = 0.5f;
               if (sx > 0)
-                nfx = 1.f - (tnx - tprev) / tsx;
+                nfx = 1.f - (tnx - tprev) / cx;
               else if (sx < 0)
-                nfx = (tnx - tprev) / tsx;
+                nfx = (tnx - tprev) / cx;
               if (sz > 0)
-                nfz = 1.f - (tnz - tprev) / tsz;
+                nfz = 1.f - (tnz - tprev) / cz;
               else if (sz < 0)
-                nfz = (tnz - tprev) / tsz;
+                nfz = (tnz - tprev) / cz;
               nfx = fminf(fmaxf(nfx, 0.f), 1.f);
               nfz = fminf(fmaxf(nfz, 0.f), 1.f);
               const float nfy = wl == 0 ? 0.f : 1.f;
-              iy = wl == 0 ? 0 : ny - 1;
-              lin = (unsigned)(ix + nx * iy + nxy * iz);
+              iy = wl == 0 ? 0 : nyl - 1;
+              lin = (unsigned)(ix + nxl * iy + nxyl * iz);
+              // cell size of the current grid over the finest, and of the grid
+              // the axis parameters were set up on
+              const float gl = MG ? (float)(1 << lev) : 1.f, gb = MG ? gl / inc : 1.f;
               float ddx, ddy, ddz;
               if (a.reflect == 1) {
                 // specular: |d| per axis unchanged, the y component flips
-                ddx = sx > 0 ? DX / tsx : (sx < 0 ? -DX / tsx : 0.f);
-                ddz = sz > 0 ? DZ / tsz : (sz < 0 ? -DZ / tsz : 0.f);
-                ddy = wl == 0 ? DY / tsy : -DY / tsy;
+                ddx = sx > 0 ? gb * DX / tsx : (sx < 0 ? -gb * DX / tsx : 0.f);
+                ddz = sz > 0 ? gb * DZ / tsz : (sz < 0 ? -gb * DZ / tsz : 0.f);
+                ddy = wl == 0 ? gb * DY / tsy : -gb * DY / tsy;
               } else {
                 // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
                 const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
@@ -489,16 +514,43 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
                 ddz = sr * sp;
               }
               ++nrefl;
-              axis_setup(ddx, nfx, DX, sx, t0x, tsx);
-              axis_setup(ddy, nfy, DY, sy, t0y, tsy);
-              axis_setup(ddz, nfz, DZ, sz, t0z, tsz);
+              axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
+              axis_setup(ddy, nfy, gl * DY, sy, t0y, tsy);
+              axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
               cntx = cnty = cntz = 0.f;
               tnx = t0x;
               tny = t0y;
               tnz = t0z;
               tprev = 0.f;
+              if (MG) inc = 1.f;
             }
           }
+        }
+        if (MG && !done && lev + 1 < a.mg_levels && lsteps >= a.mg_steps) {
+          // multigrid (Section 4.3): fall onto the next coarser grid here.  Its
+          // faces are the even-numbered faces of this grid, so an axis whose
+          // next face is odd-numbered skips it; the cell is the one containing
+          // this one.
+          if (sx != 0 && ((sx > 0 ? ix + 1 : ix) & 1)) {
+            cntx += inc;
+            tnx = fmaf(cntx, tsx, t0x);
+          }
+          if (sy != 0 && ((sy > 0 ? iy + 1 : iy) & 1)) {
+            cnty += inc;
+            tny = fmaf(cnty, tsy, t0y);
+          }
+          if (sz != 0 && ((sz > 0 ? iz + 1 : iz) & 1)) {
+            cntz += inc;
+            tnz = fmaf(cntz, tsz, t0z);
+          }
+          loff += (unsigned)(nxyl * nzl);
+          ix >>= 1;
+          iy >>= 1;
+          iz >>= 1;
+          lin = (unsigned)(ix + (nxl >> 1) * (iy + (nyl >> 1) * iz));
+          inc *= 2.f;
+          ++lev;
+          lsteps = 0;
         }
       }
       if (done) {
@@ -615,7 +667,7 @@ __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
   }
 }
 
-template <int MINB, int KSTEPS>
+template <int MINB, int KSTEPS, bool MG>
 cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
   static bool init_done = false;
@@ -628,13 +680,13 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (configured_smem[dev] != (int)smem) {
-    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS>,
+    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS, MG>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev],
-                                                      trace_fp32_kernel<MINB, KSTEPS>, WARPS * 32, smem);
+                                                      trace_fp32_kernel<MINB, KSTEPS, MG>, WARPS * 32, smem);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
     configured_smem[dev] = (int)smem;
@@ -644,18 +696,18 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   return cudaSuccess;
 }
 
-template <int MINB, int KSTEPS>
+template <int MINB, int KSTEPS, bool MG>
 cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
   // per-device launch shape, computed once per device and shared-memory size
   int bps = 0, nsm = 0;
-  cudaError_t e = configure_variant<MINB, KSTEPS>(smem, &bps, &nsm);
+  cudaError_t e = configure_variant<MINB, KSTEPS, MG>(smem, &bps, &nsm);
   if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const long long need = (P + WARPS - 1) / WARPS;
   long long blocks = a.grid_blocks > 0 ? a.grid_blocks : (long long)nsm * bps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  trace_fp32_kernel<MINB, KSTEPS><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  trace_fp32_kernel<MINB, KSTEPS, MG><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -685,13 +737,20 @@ int fp32_cell_stage_fits(int nb, int ng) {
 }
 
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
-                               int *blocks_per_sm, int *num_sms) {
+                               int multigrid, int *blocks_per_sm, int *num_sms) {
   const size_t smem = fp32_smem_bytes(nb, ng, counts_in_smem);
 #define MCRT_PREP_K(MB)                                                                  \
+  if (multigrid) {                                                                       \
+    switch (steps_per_round) {                                                           \
+      case 2: return configure_variant<MB, 2, true>(smem, blocks_per_sm, num_sms);       \
+      case 4: return configure_variant<MB, 4, true>(smem, blocks_per_sm, num_sms);       \
+      default: return configure_variant<MB, 1, true>(smem, blocks_per_sm, num_sms);      \
+    }                                                                                    \
+  }                                                                                      \
   switch (steps_per_round) {                                                             \
-    case 2: return configure_variant<MB, 2>(smem, blocks_per_sm, num_sms);               \
-    case 4: return configure_variant<MB, 4>(smem, blocks_per_sm, num_sms);               \
-    default: return configure_variant<MB, 1>(smem, blocks_per_sm, num_sms);              \
+    case 2: return configure_variant<MB, 2, false>(smem, blocks_per_sm, num_sms);        \
+    case 4: return configure_variant<MB, 4, false>(smem, blocks_per_sm, num_sms);        \
+    default: return configure_variant<MB, 1, false>(smem, blocks_per_sm, num_sms);       \
   }
   switch (min_blocks) {
     case 1: MCRT_PREP_K(1)
@@ -707,11 +766,19 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_
   if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
   const size_t smem = fp32_smem_bytes(a.nb, a.ng, a.counts_in_smem);
   cudaError_t e;
-#define MCRT_FP32_K(MB)                                              \
-  switch (steps_per_round) {                                         \
-    case 2: e = launch_variant<MB, 2>(a, s, smem); break;            \
-    case 4: e = launch_variant<MB, 4>(a, s, smem); break;            \
-    default: e = launch_variant<MB, 1>(a, s, smem); break;           \
+#define MCRT_FP32_K(MB)                                                    \
+  if (a.mg_levels > 1) {                                                   \
+    switch (steps_per_round) {                                             \
+      case 2: e = launch_variant<MB, 2, true>(a, s, smem); break;          \
+      case 4: e = launch_variant<MB, 4, true>(a, s, smem); break;          \
+      default: e = launch_variant<MB, 1, true>(a, s, smem); break;         \
+    }                                                                      \
+  } else {                                                                 \
+    switch (steps_per_round) {                                             \
+      case 2: e = launch_variant<MB, 2, false>(a, s, smem); break;         \
+      case 4: e = launch_variant<MB, 4, false>(a, s, smem); break;         \
+      default: e = launch_variant<MB, 1, false>(a, s, smem); break;        \
+    }                                                                      \
   }
   switch (min_blocks) {
     case 1: MCRT_FP32_K(1) break;

@@ -52,7 +52,8 @@ class mcrt_solve_params(C.Structure):
     _fields_ = [("rays_per_cell", C.c_int), ("max_steps", C.c_int), ("tol", C.c_double),
                 ("seed", C.c_uint64), ("ray_offset", C.c_uint64), ("snapshot", C.c_uint32),
                 ("precision", C.c_int), ("origin", C.c_int), ("proposal", C.c_int),
-                ("use_box", C.c_int), ("box", C.c_int * 6), ("steps_out", C.c_void_p)]
+                ("use_box", C.c_int), ("box", C.c_int * 6), ("steps_out", C.c_void_p),
+                ("mg_levels", C.c_int), ("mg_steps", C.c_int)]
 
 
 class mcrt_tuning(C.Structure):
@@ -82,7 +83,7 @@ EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_pr
            "mcrt_mlp_get_params", "mcrt_mlp_forward", "mcrt_mlp_loss_grad", "mcrt_mlp_adam_step",
            "mcrt_mlp_last_loss", "mcrt_mlp_last_error", "mcrt_mlp_destroy", "mcrt_cell_features",
            "mcrt_tally_moments", "mcrt_get_plain_probs", "mcrt_set_cell_proposal_probs",
-           "mcrt_get_cell_proposal", "mcrt_set_learned_proposal")
+           "mcrt_get_cell_proposal", "mcrt_set_learned_proposal", "mcrt_multigrid_levels")
 _NOT_INT = ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error", "mcrt_mlp_last_error",
             "mcrt_mlp_nparams")
 MCRT_NFEAT, MCRT_NHIDDEN = 12, 64
@@ -148,6 +149,7 @@ def load(build_if_missing: bool = True):
         L.mcrt_set_cell_proposal_probs.argtypes = [vp, vp, vp]
         L.mcrt_get_cell_proposal.argtypes = [vp, vp, vp, vp]
         L.mcrt_set_learned_proposal.argtypes = [vp, vp, f32, vp]
+        L.mcrt_multigrid_levels.argtypes = [C.c_int, C.c_int, C.c_int]
         for f in EXPORTS:
             if f not in _NOT_INT:
                 getattr(L, f).restype = C.c_int
@@ -162,6 +164,10 @@ def _check(rc, ctx=None):
 
 
 # --- the C entry points, same names ---------------------------------------------
+
+def mcrt_multigrid_levels(nx: int, ny: int, nz: int) -> int:
+    return int(load().mcrt_multigrid_levels(nx, ny, nz))
+
 
 def mcrt_create(grid: mcrt_grid_desc) -> C.c_void_p:
     h = C.c_void_p()
@@ -483,9 +489,10 @@ class Solver:
     @staticmethod
     def params(rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4, max_steps=1 << 30,
                precision=MCRT_FP32, origin=MCRT_ORIGIN_UNIFORM, proposal=MCRT_PROPOSAL_PLANCK_TMAX,
-               box=None):
+               box=None, mg_levels=1, mg_steps=5):
         p = mcrt_solve_params()
         p.rays_per_cell, p.max_steps, p.tol = rays, max_steps, tol
+        p.mg_levels, p.mg_steps = mg_levels, mg_steps
         p.seed, p.ray_offset, p.snapshot = seed, ray_offset, snapshot
         p.precision, p.origin, p.proposal = precision, origin, proposal
         p.use_box = 0 if box is None else 1

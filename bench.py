@@ -201,41 +201,83 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             "tuning_ms": {f"{k[0]}{'w' if k[1] else ''}": v for k, v in table.items()}}
 
 
+def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):
+    """The multigrid march (Section 4.3) on the benchmark workload: every grid
+    the field allows, `steps_per_grid` segments per grid; time against the
+    exact march on the same draws, and the paired difference of the two
+    estimates (an approximation, so its bias is reported, not hidden)."""
+    import numpy as np
+
+    from paper_1810_00188_gb300 import mcrt
+    g = S.grid
+    L = mcrt.mcrt_multigrid_levels(g.nx, g.ny, g.nz)
+    out = {"grids": L, "steps_per_grid": steps_per_grid}
+    res = {}
+    for name, lv in (("exact", 1), ("multigrid", L)):
+        ts = []
+        for k in range(3):
+            S.solve_into(params(k, rays=rays, mg_levels=lv, mg_steps=steps_per_grid), q, s, stream=sp)
+            st = S.stats()
+            ts.append(st["kernel_ms"])
+        res[name] = (q.cpu().numpy(), s.cpu().numpy(), statistics.median(ts), st)
+        out[name] = {"kernel_ms": statistics.median(ts), "steps_per_ray": st["steps"] / st["rays"],
+                     "max_ray_steps": st["max_ray_steps"]}
+    q0, s0, _, _ = res["exact"]
+    q1, s1, _, _ = res["multigrid"]
+    d = q1 - q0
+    out["speedup"] = out["exact"]["kernel_ms"] / out["multigrid"]["kernel_ms"]
+    out["paired_rel_l1_diff"] = float(np.abs(d).sum() / np.abs(q0).sum())
+    out["mean_diff_over_mean_abs_q"] = float(d.mean() / np.abs(q0).mean())
+    out["frac_cells_beyond_3_sigma"] = float(np.mean(np.abs(d) > 3 * np.sqrt(s0**2 + s1**2)))
+    return out
+
+
 def learned_extra(sp, n_train=200, train_grid=64, eval_grid=128, rays_tally=512, rays_eval=256,
                   steps=1500, seed=0):
     """Learned proposal: tallies of `n_train` seeded 64^3 fields, training on the
     GPU, then plain and learned FP32 solves of a held-out 128^3 field at the same
     rays per cell; the GPU time to 1% p95 relative sigma is projected with the
-    estimator's 1/N law from the measured time and sigma."""
+    estimator's 1/N law from the measured time and sigma.  Two forms, each
+    compared with plain sampling on the same march: the multigrid march (every
+    grid, 5 segments per grid; tallies from multigrid solves, cost constant
+    c0 = 12 steps) and the exact march (tallies from exact solves, c0 = 3)."""
     import torch
 
     from paper_1810_00188_gb300 import inputs, learn, mcrt
-    t0 = time.perf_counter()
-    ds = learn.build_dataset(grid_shape=(train_grid,) * 3, seeds=range(n_train), rays=rays_tally,
-                             cells_per_field=4096, stream=sp)
-    torch.cuda.synchronize()
-    t_data = time.perf_counter() - t0
-    net = mcrt.Mlp(ds.K)
-    mean, inv = learn.feature_norm(ds)
-    net.set_params(learn.init_theta(ds.K, ds.p0.mean(0).cpu().numpy(), seed=seed), mean, inv)
-    l0 = learn.mean_loss(net, ds, stream=sp)
-    t0 = time.perf_counter()
-    losses = learn.train(net, ds, steps=steps, stream=sp, seed=seed)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    l1 = learn.mean_loss(net, ds, stream=sp)
+    out = {"workload": f"train {n_train} x {train_grid}^3 fields (4096 cells each, {rays_tally} rays), "
+                       f"held-out {eval_grid}^3 field (seed 1000), {rays_eval} rays/cell"}
     n = eval_grid
     grid, kd, T, x = inputs.nongrey_channel(n, n, n, seed=1000, x_mode="field")
     S = mcrt.Solver(grid, kd)
     S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
-    res = learn.compare_on_field(S, net, rays=rays_eval, seed=seed + 7, reps=3, stream=sp)
+    for name, mg, c0 in (("multigrid", 1, 12.0), ("exact", 0, 3.0)):
+        t0 = time.perf_counter()
+        ds = learn.build_dataset(grid_shape=(train_grid,) * 3, seeds=range(n_train), rays=rays_tally,
+                                 cells_per_field=4096, stream=sp, mg=mg)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        net = mcrt.Mlp(ds.K)
+        mean, inv = learn.feature_norm(ds)
+        net.set_params(learn.init_theta(ds.K, ds.p0.mean(0).cpu().numpy(), seed=seed), mean, inv)
+        l0 = learn.mean_loss(net, ds, c0=c0, stream=sp)
+        t0 = time.perf_counter()
+        losses = learn.train(net, ds, steps=steps, c0=c0, stream=sp, seed=seed)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        l1 = learn.mean_loss(net, ds, c0=c0, stream=sp)
+        L = mcrt.mcrt_multigrid_levels(n, n, n) if mg else 1
+        res = learn.compare_on_field(S, net, rays=rays_eval, seed=seed + 7, reps=3, stream=sp,
+                                     mg_levels=L, mg_steps=5)
+        net.close()
+        del ds
+        torch.cuda.empty_cache()
+        res.update({"grids": L, "c0": c0, "dataset_s": t_data, "train_s": t_train, "train_steps": steps,
+                    "loss_before": l0, "loss_after": l1, "loss_last_batch": losses[-1][1]})
+        out[name] = res
     S.close()
-    net.close()
-    res.update({"workload": f"train {n_train} x {train_grid}^3 fields (4096 cells each, {rays_tally} rays), "
-                            f"held-out {n}^3 field (seed 1000), {rays_eval} rays/cell",
-                "dataset_s": t_data, "train_s": t_train, "train_steps": steps,
-                "loss_before": l0, "loss_after": l1, "loss_last_batch": losses[-1][1]})
-    return res
+    out["multigrid_learned_vs_exact_plain"] = (out["exact"]["plain"]["ms_to_1pct"] /
+                                                out["multigrid"]["learned"]["ms_to_1pct"])
+    return out
 
 
 def run_reference(a):
@@ -309,9 +351,9 @@ def main():
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    def params(k, prec=mcrt.MCRT_FP32, rays=a.rays):
+    def params(k, prec=mcrt.MCRT_FP32, rays=a.rays, mg_levels=1, mg_steps=5):
         return S.params(rays=rays, seed=0, snapshot=rank, ray_offset=k * rays, tol=1e-4,
-                        max_steps=1 << 20, precision=prec)
+                        max_steps=1 << 20, precision=prec, mg_levels=mg_levels, mg_steps=mg_steps)
 
     for k in range(a.warmup):
         S.solve_into(params(k), q, s, stream=sp)
@@ -417,6 +459,7 @@ def main():
             else:
                 sol["value"] = value / (steps_per_launch / a.rays * nstar)
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
+            result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
             result["learned_vs_plain"] = learned_extra(sp)
             if world == 1:
                 result["batched_snapshots"] = batch_extra(sp)

@@ -39,12 +39,14 @@ class Dataset:
         return int(self.feat.shape[0])
 
 
-def tally_field(S, rays, seed, snapshot, cells, stream=0):
+def tally_field(S, rays, seed, snapshot, cells, stream=0, mg_levels=1, mg_steps=5):
     """Features, tallies, p0 rows and weights 1/ref^2 of `cells` (torch int32
-    cuda) of the context's current fields."""
+    cuda) of the context's current fields (from a multigrid solve when
+    mg_levels > 1)."""
     import torch
     feat = S.features(cells, stream=stream)
-    p = S.params(rays=rays, seed=seed, snapshot=snapshot, precision=mcrt.MCRT_FP32)
+    p = S.params(rays=rays, seed=seed, snapshot=snapshot, precision=mcrt.MCRT_FP32,
+                 mg_levels=mg_levels, mg_steps=mg_steps)
     q = torch.empty(S.box_shape(None), dtype=torch.float64, device=feat.device)
     mom, cost = S.tally(p, cells, q=q, stream=stream)
     p0 = torch.tensor(S.plain_probs(), device=feat.device)
@@ -55,10 +57,12 @@ def tally_field(S, rays, seed, snapshot, cells, stream=0):
 
 
 def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per_field=4096,
-                  kdist_seed=0, x_mode="field", sample_seed=0, stream=0, dense=True):
+                  kdist_seed=0, x_mode="field", sample_seed=0, stream=0, dense=True, mg=0,
+                  mg_steps=5):
     """Tallies of `cells_per_field` random cells of each seeded channel field
     (cost tallies replaced by the dataset-wide mean steps per point unless
-    dense=False)."""
+    dense=False).  mg = 1 tallies multigrid solves on every grid the field
+    allows (mg_steps segments per grid)."""
     import concurrent.futures as cf
 
     import torch
@@ -87,7 +91,9 @@ def build_dataset(grid_shape=(64, 64, 64), seeds=range(200), rays=512, cells_per
         n = min(cells_per_field, grid.ncells)
         cells = torch.tensor(np.sort(rng.choice(grid.ncells, n, replace=False)).astype(np.int32),
                              device="cuda")
-        f, m, c, p, w = tally_field(S, rays, seed=1000 + s, snapshot=s, cells=cells, stream=stream)
+        L = mcrt.mcrt_multigrid_levels(nx, ny, nz) if mg else 1
+        f, m, c, p, w = tally_field(S, rays, seed=1000 + s, snapshot=s, cells=cells, stream=stream,
+                                    mg_levels=L, mg_steps=mg_steps)
         feats.append(f)
         moms.append(m)
         costs.append(c)
@@ -192,10 +198,11 @@ def rel_sigma_p95(q, s):
     return float(np.percentile(s / ref, 95))
 
 
-def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0):
-    """Plain and learned FP32 solves of the context's fields at `rays` per cell:
-    kernel time, p95 relative sigma, and the projected GPU time to reach 1%
-    (time x (p95 / 0.01)^2, the estimator's 1/N law)."""
+def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0, mg_levels=1, mg_steps=5):
+    """Plain and learned FP32 solves of the context's fields at `rays` per cell
+    (both on mg_levels grids): kernel time, p95 relative sigma, and the
+    projected GPU time to reach 1% (time x (p95 / 0.01)^2, the estimator's 1/N
+    law)."""
     import torch
     shape = S.box_shape(None)
     dev = f"cuda:{S.device}"
@@ -215,7 +222,7 @@ def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0):
         steps = 0
         for r in range(reps):
             p = S.params(rays=rays, seed=seed, ray_offset=r * rays, precision=mcrt.MCRT_FP32,
-                         proposal=prop)
+                         proposal=prop, mg_levels=mg_levels, mg_steps=mg_steps)
             S.solve_into(p, q, s, stream=stream)
             st = S.stats()
             times.append(st["kernel_ms"])

@@ -135,7 +135,7 @@ typedef struct {
 typedef struct {
   int min_blocks_per_sm;   /* 0: default (3); 1..4 CTAs of 256 threads per SM,
                               trading registers per thread against occupancy */
-  int steps_per_round;     /* 0: default (2); 1, 2 or 4 march steps per lane
+  int steps_per_round;     /* 0: default (1); 1, 2 or 4 march steps per lane
                               between refills of idle lanes                      */
   int scratch_mib;         /* 0: default (1024); cap of the per-ray sample
                               scratch; larger solves run in several chunks      */

@@ -48,7 +48,7 @@ struct mcrt_ctx {
   bool solved = false;
   int last_launches = 0;
   int min_blocks = 3;
-  int steps_per_round = 2;
+  int steps_per_round = 1;
   int scratch_mib = 1024;
   double last_T_max = 0;
   std::string err;

@@ -325,7 +325,7 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   DeviceGuard dg(g->device);
   if (!dg.ok || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
       cudaEventCreate(&ctx->ev1) != cudaSuccess ||
-      ensure(ctx->counters, 6 * sizeof(unsigned long long)) != cudaSuccess ||
+      ensure(ctx->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
       ensure(ctx->fstats, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     mcrt_destroy(ctx);
@@ -641,7 +641,7 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
       t->steps_per_round != 4)
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
-  ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 2;
+  ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
   ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
   return MCRT_OK;
 }
@@ -1053,7 +1053,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     if (pc > P[k]) pc = P[k];
     Pc[k] = pc;
     void *ct = nullptr;
-    BK(cudaMalloc(&ct, 6 * sizeof(unsigned long long)), "alloc counters");
+    BK(cudaMalloc(&ct, 8 * sizeof(unsigned long long)), "alloc counters");
     b->owned.push_back(ct);
     a.counters = (unsigned long long *)ct;
     b->counters.push_back((unsigned long long *)ct);

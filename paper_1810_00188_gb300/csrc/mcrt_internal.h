@@ -64,7 +64,8 @@ struct TraceArgs {
   // outputs (box-sized)
   double *q, *sigma;
   unsigned long long *steps_cell;
-  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps) [5] error flags
+  unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps)
+                                 // [5] error flags [6] FP32 kernel: claimed positions (8 entries)
 };
 
 // Multigrid grid count of an nx x ny x nz grid and the cells of all its grids.

@@ -28,7 +28,8 @@
 // u23_to_float).
 //
 // A round that makes no progress cannot happen; if it did, the warp sets an
-// error flag (counters[5]) and returns instead of spinning.
+// error flag (counters[5]) and returns instead of spinning.  Warps claim runs
+// of cells from a launch-wide counter (counters[6]).
 #include <math.h>
 #include <stdint.h>
 
@@ -186,12 +187,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   const int lane = threadIdx.x & 31;
   WarpRing &R = rings[threadIdx.x >> 5];
   const unsigned lt_mask = (1u << lane) - 1u;
-  const long long W = (long long)gridDim.x * WARPS;
-  const long long wg = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5);
-  const long long P = a.chunk_p1 - a.chunk_p0;
-  const long long per = (P + W - 1) / W;
-  long long p_next = a.chunk_p0 + wg * per;
-  const long long p_end = min(a.chunk_p1, p_next + per);
+  // Runs of brick-order positions are claimed from a launch-wide counter
+  // (counters[6], zeroed before each launch): a warp whose cells hold longer rays
+  // takes fewer cells, and the runs keep neighbouring cells together.
+  // positions per claim: about 4096 rays, and at least 8 claims per warp
+  const long long G = max(1LL, min((long long)(4096 / a.rays),
+                                   (a.chunk_p1 - a.chunk_p0) / ((long long)gridDim.x * WARPS * 8)));
+  long long p_next = 0, p_end = 0;
 
   const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nb = a.nb,
             ng = a.ng, nT = a.nT, N = a.rays;
@@ -239,9 +241,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       if (c_r >= N) {  // next emitting cell of this warp's brick-ordered run
         bool found = false;
         long long p = p_next;
-        while (!found && p < p_end) {
-          found = brick_cell(a, p, c_bx, c_by, c_bz);
-          ++p;
+        for (;;) {
+          while (!found && p < p_end) {
+            found = brick_cell(a, p, c_bx, c_by, c_bz);
+            ++p;
+          }
+          if (found) break;
+          unsigned long long base = 0;  // claim the next run (warp-uniform)
+          if (lane == 0) base = atomicAdd(a.counters + 6, (unsigned long long)G);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          p = a.chunk_p0 + (long long)base;
+          p_end = min(a.chunk_p1, p + G);
+          if (p >= a.chunk_p1) break;
         }
         p_next = p;
         if (found) {
@@ -765,7 +776,9 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_
                               cudaStream_t s) {
   if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
   const size_t smem = fp32_smem_bytes(a.nb, a.ng, a.counts_in_smem);
-  cudaError_t e;
+  // the claim counter of this launch's position runs
+  cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
 #define MCRT_FP32_K(MB)                                                    \
   if (a.mg_levels > 1) {                                                   \
     switch (steps_per_round) {                                             \

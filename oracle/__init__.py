@@ -45,7 +45,8 @@ class Problem(C.Structure):
                 ("reflect", C.c_int), ("n_bands", C.c_int), ("n_g", C.c_int),
                 ("w_g", C.POINTER(C.c_double)), ("T0", C.c_double), ("dT", C.c_double),
                 ("nT", C.c_int), ("kappa", C.POINTER(C.c_double)),
-                ("B", C.POINTER(C.c_double)), ("x_ref", C.c_double)]
+                ("B", C.POINTER(C.c_double)), ("x_ref", C.c_double),
+                ("yf", C.POINTER(C.c_double))]
 
 
 class Params(C.Structure):
@@ -150,6 +151,11 @@ def make_problem(grid, kd, T, x=None):
     P.kappa = _dp(keep.k)
     P.B = _dp(keep.B)
     P.x_ref = kd.x_ref
+    yf = getattr(grid, "yf", None)
+    keep.yf = None if yf is None else _f64(yf)
+    if keep.yf is not None:
+        assert keep.yf.size == grid.ny + 1
+    P.yf = _dp(keep.yf) if keep.yf is not None else C.POINTER(C.c_double)()
     P._keep = keep
     return P
 

@@ -50,6 +50,8 @@ enum { F = ORC_NFEAT, H = ORC_HIDDEN };
  * 3 T_wall,0 / 1000       4 T_wall,1 / 1000           5 eps of the nearer wall
  * 6 h dT/dy / 1000        7 h |grad_xz T| / 1000      8 mean T over 3^3 / T_i
  * 9 std T over 3^3 / T_i  10 kappa_P(T_i, x_i) h      11 T_max / T_i
+ * (on a stretched grid y_c is the midpoint of the cell's faces and dT/dy divides
+ * by the distance of the centres used)
  * with h = ly / 2 the channel half height, centred differences (one-sided at the
  * walls, periodic in x and z), the 3^3 neighbourhood periodic in x and z and cut
  * at the walls, and kappa_P the Planck mean of the tables at T_i:
@@ -60,6 +62,12 @@ static double T_at(const orc_problem *P, int i, int j, int k) {
 }
 
 static int wrap(int i, int n) { return ((i % n) + n) % n; }
+
+/* y of the centre of row j (stretched grids: midpoint of its faces) */
+static double ycentre(const orc_problem *P, int j) {
+  if (P->yf) return 0.5 * (P->yf[j] + P->yf[j + 1]);
+  return (j + 0.5) * (P->ly / P->ny);
+}
 
 int orc_features(const orc_problem *P, const int32_t *cells, int64_t n, double T_max,
                  double *out) {
@@ -72,7 +80,7 @@ int orc_features(const orc_problem *P, const int32_t *cells, int64_t n, double T
     const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
     const double Ti = P->T[c];
     const double xi = P->xh2o ? P->xh2o[c] : P->x_ref;
-    const double yc = (j + 0.5) * dy;
+    const double yc = ycentre(P, j);
     double *f = out + q * F;
     f[0] = Ti / 1000.0;
     f[1] = xi;
@@ -81,13 +89,17 @@ int orc_features(const orc_problem *P, const int32_t *cells, int64_t n, double T
     f[4] = P->T_wall[1] / 1000.0;
     f[5] = yc < h ? P->eps_wall[0] : P->eps_wall[1];
     double dTdy = 0.0;
-    if (ny > 1) {
+    if (ny > 1 && !P->yf) {
       if (j == 0)
         dTdy = (T_at(P, i, 1, k) - T_at(P, i, 0, k)) / dy;
       else if (j == ny - 1)
         dTdy = (T_at(P, i, ny - 1, k) - T_at(P, i, ny - 2, k)) / dy;
       else
         dTdy = (T_at(P, i, j + 1, k) - T_at(P, i, j - 1, k)) / (2.0 * dy);
+    } else if (ny > 1) {
+      /* stretched grid: differences over the distances of the cell centres */
+      const int j0 = j == 0 ? 0 : j - 1, j1 = j == ny - 1 ? ny - 1 : j + 1;
+      dTdy = (T_at(P, i, j1, k) - T_at(P, i, j0, k)) / (ycentre(P, j1) - ycentre(P, j0));
     }
     f[6] = h * dTdy / 1000.0;
     const double dTdx = (T_at(P, wrap(i + 1, nx), j, k) - T_at(P, wrap(i - 1, nx), j, k)) / (2.0 * dx);

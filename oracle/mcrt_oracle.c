@@ -206,6 +206,9 @@ typedef struct {
   double *own[ORC_MG_MAX];                     /* coarse T and x storage */
 } mg_grids;
 
+/* y of face F of grid lev (stretched grids: every 2^lev-th face of grid 0) */
+static double yface(const orc_problem *P, int lev, int F) { return P->yf[(size_t)F << lev]; }
+
 int orc_mg_max_levels(int nx, int ny, int nz) {
   int n[3] = {nx, ny, nz}, L = 1;
   while (L < ORC_MG_MAX) {
@@ -224,14 +227,24 @@ static void mg_free(mg_grids *M) {
   memset(M, 0, sizeof(*M));
 }
 
-/* mean of the 8 children of coarse cell (I, J, K), z outermost, x innermost */
-static double mean8(const double *v, const int n[3], int I, int J, int K) {
-  double s = 0.0;
+/* mean of the 8 children of coarse cell (I, J, K), z outermost, x innermost;
+ * on a stretched grid weighted by the children's heights w[0], w[1] (the
+ * volume-weighted mean) */
+static double mean8(const double *v, const int n[3], int I, int J, int K, const double *w) {
+  double s = 0.0, ws = 0.0;
   for (int c = 0; c < 2; ++c)
     for (int b = 0; b < 2; ++b)
-      for (int a = 0; a < 2; ++a)
-        s += v[(size_t)(2 * I + a) + (size_t)n[0] * ((size_t)(2 * J + b) + (size_t)n[1] * (2 * K + c))];
-  return s * 0.125;
+      for (int a = 0; a < 2; ++a) {
+        const double f =
+            v[(size_t)(2 * I + a) + (size_t)n[0] * ((size_t)(2 * J + b) + (size_t)n[1] * (2 * K + c))];
+        if (w) {
+          s += w[b] * f;
+          ws += w[b];
+        } else {
+          s += f;
+        }
+      }
+  return w ? s / ws : s * 0.125;
 }
 
 static int mg_build(const orc_problem *P, int L, int k, mg_grids *M) {
@@ -263,8 +276,13 @@ static int mg_build(const orc_problem *P, int L, int k, mg_grids *M) {
       for (int J = 0; J < M->N[l][1]; ++J)
         for (int I = 0; I < M->N[l][0]; ++I) {
           const size_t c = (size_t)I + (size_t)M->N[l][0] * ((size_t)J + (size_t)M->N[l][1] * K);
-          T[c] = mean8(M->T[l - 1], M->N[l - 1], I, J, K);
-          if (x) x[c] = mean8(M->x[l - 1], M->N[l - 1], I, J, K);
+          double wy[2];
+          if (P->yf) {
+            wy[0] = yface(P, l - 1, 2 * J + 1) - yface(P, l - 1, 2 * J);
+            wy[1] = yface(P, l - 1, 2 * J + 2) - yface(P, l - 1, 2 * J + 1);
+          }
+          T[c] = mean8(M->T[l - 1], M->N[l - 1], I, J, K, P->yf ? wy : NULL);
+          if (x) x[c] = mean8(M->x[l - 1], M->N[l - 1], I, J, K, P->yf ? wy : NULL);
         }
     M->T[l] = T;
     M->x[l] = x;
@@ -310,6 +328,10 @@ static void trace_core(const orc_problem *P, const mg_grids *M, int n, int g, co
   int sgn[3];
   int64_t cnt[3];
   double tprev;
+  /* stretched y: the crossing of face F is at t = (y_F - y_o) / d_y, with y_o
+   * the y of the current straight piece's start */
+  const int sy = P->yf != NULL;
+  double y_o = 0.0;
 restart:
   for (int a = 0; a < 3; ++a) {
     cnt[a] = 0;
@@ -326,6 +348,12 @@ restart:
     tstep[a] = sgn[a] ? delta[a] / fabs(d[a]) : INFINITY;
     tnext[a] = sgn[a] ? g0[a] * tstep[a] : INFINITY;
   }
+  if (sy) {
+    const double y0 = yface(P, lev, c[1]), y1 = yface(P, lev, c[1] + 1);
+    y_o = y0 + fr[1] * (y1 - y0);
+    if (sgn[1] > 0) tnext[1] = (y1 - y_o) / d[1];
+    if (sgn[1] < 0) tnext[1] = (y0 - y_o) / d[1];
+  }
   tprev = 0.0;
 
   for (;;) {
@@ -334,6 +362,16 @@ restart:
        * the next coarser one at its current point; its position inside the
        * coarse cell follows from the position inside the current cell */
       for (int b = 0; b < 3; ++b) {
+        if (sy && b == 1) {
+          /* stretched y: the current y within the coarse cell's faces */
+          const double yc = y_o + tprev * d[1];
+          const double y0 = yface(P, lev + 1, c[1] >> 1), y1 = yface(P, lev + 1, (c[1] >> 1) + 1);
+          fr[1] = (yc - y0) / (y1 - y0);
+          if (fr[1] < 0.0) fr[1] = 0.0;
+          if (fr[1] > 1.0) fr[1] = 1.0;
+          c[1] >>= 1;
+          continue;
+        }
         if (sgn[b] > 0)
           fr[b] = 1.0 - (tnext[b] - tprev) / tstep[b];
         else if (sgn[b] < 0)
@@ -387,6 +425,8 @@ restart:
     ++cnt[a];
     tnext[a] = (g0[a] + (double)cnt[a]) * tstep[a];
     c[a] += sgn[a];
+    if (sy && a == 1 && c[1] >= 0 && c[1] < N[1])
+      tnext[1] = (yface(P, lev, c[1] + (sgn[1] > 0)) - y_o) / d[1];
     if (a == 0) c[0] = (c[0] % N[0] + N[0]) % N[0]; /* periodic x */
     if (a == 2) c[2] = (c[2] % N[2] + N[2]) % N[2]; /* periodic z */
     if (a == 1 && (c[1] < 0 || c[1] >= N[1])) {

@@ -30,6 +30,10 @@ typedef struct {
   const double *kappa;       /* [n_bands][n_g][nT] at x_ref [1/m]                 */
   const double *B;           /* [n_bands][nT] band blackbody intensity            */
   double x_ref;
+  /* Wall-normal face coordinates y_0 = 0 < y_1 < ... < y_ny = ly of a stretched
+   * grid (the channel DNS grids of Section 5), or NULL for uniform cells.  x and
+   * z stay uniform. */
+  const double *yf;
 } orc_problem;
 
 typedef struct {

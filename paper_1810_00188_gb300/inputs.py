@@ -31,7 +31,9 @@ SIGMA_SB = 5.670374419e-8
 
 @dataclasses.dataclass
 class Grid:
-    """Uniform Cartesian grid; y is wall-normal, x and z are periodic."""
+    """Cartesian grid; y is wall-normal, x and z are periodic and uniform.  y is
+    uniform too unless ``yf`` holds the ny + 1 wall-normal face coordinates
+    0 = y_0 < ... < y_ny = ly of a stretched grid."""
 
     nx: int
     ny: int
@@ -42,6 +44,7 @@ class Grid:
     eps_wall: tuple = (1.0, 1.0)   # emissivity of the walls at y=0 and y=ly
     T_wall: tuple = (0.0, 0.0)     # temperature [K] of the walls at y=0 and y=ly
     reflect: int = 0               # 0 diffuse, 1 specular reflection at grey walls
+    yf: object = None              # [ny + 1] wall-normal faces of a stretched grid, or None
 
     @property
     def ncells(self) -> int:
@@ -52,9 +55,28 @@ class Grid:
         """numpy shape of a field array: [nz][ny][nx], x fastest."""
         return (self.nz, self.ny, self.nx)
 
+    def y_faces(self) -> np.ndarray:
+        if self.yf is not None:
+            return np.asarray(self.yf, dtype=np.float64)
+        return np.arange(self.ny + 1) * (self.ly / self.ny)
+
     def cell_centers_y(self) -> np.ndarray:
+        if self.yf is not None:
+            f = np.asarray(self.yf, dtype=np.float64)
+            return 0.5 * (f[:-1] + f[1:])
         dy = self.ly / self.ny
         return (np.arange(self.ny) + 0.5) * dy
+
+
+def channel_faces(ny: int, ly: float, gamma: float = 1.5) -> np.ndarray:
+    """Wall-normal faces of a channel grid refined towards both walls with the
+    hyperbolic-tangent stretching common in channel DNS:
+    y_j = ly/2 (1 + tanh(gamma (2 j / ny - 1)) / tanh(gamma)); gamma -> 0 is
+    uniform.  The end faces are exactly 0 and ly."""
+    j = np.arange(ny + 1)
+    y = 0.5 * ly * (1.0 + np.tanh(gamma * (2.0 * j / ny - 1.0)) / np.tanh(gamma))
+    y[0], y[-1] = 0.0, ly
+    return y
 
 
 @dataclasses.dataclass

@@ -63,9 +63,11 @@ enum { MCRT_PROPOSAL_PLANCK_TMAX = 0, MCRT_PROPOSAL_CELL = 1 };
 enum { MCRT_REFLECT_DIFFUSE = 0, MCRT_REFLECT_SPECULAR = 1 };
 
 /* Grid and walls (Section 2.2: finite volumes with index (i,j,k); Eq. 3: the
- * wall emissivity eps_w enters the transmissivity).  Uniform cells of size
- * lx/nx x ly/ny x lz/nz.  Wall 0 is y = 0, wall 1 is y = ly.  eps_wall = 1 is a
- * black wall (the ray ends there); 0 <= eps < 1 reflects the rest. */
+ * wall emissivity eps_w enters the transmissivity).  Cells of size lx/nx x dy_j
+ * x lz/nz: uniform in the periodic x and z; in y uniform (ly/ny) or stretched
+ * by a list of faces, like the wall-refined channel DNS grids of Section 5.
+ * Wall 0 is y = 0, wall 1 is y = ly.  eps_wall = 1 is a black wall (the ray
+ * ends there); 0 <= eps < 1 reflects the rest. */
 typedef struct {
   int nx, ny, nz;          /* >= 1 each; nx*ny*nz < 2^31                          */
   double lx, ly, lz;       /* box lengths [m], > 0                                */
@@ -73,6 +75,9 @@ typedef struct {
   double T_wall[2];        /* [K], >= 0                                           */
   int reflect;             /* MCRT_REFLECT_*                                      */
   int device;              /* CUDA device ordinal                                 */
+  const double *yf;        /* host [ny + 1] wall-normal faces, strictly increasing,
+                              yf[0] = 0 and yf[ny] = ly; copied by mcrt_create;
+                              NULL: uniform ly / ny                              */
 } mcrt_grid_desc;
 
 /* Narrow-band correlated-k tables (Section 2.1, Eq. 16; Section 2.2: tabulated
@@ -148,7 +153,8 @@ typedef struct {
 int mcrt_multigrid_levels(int nx, int ny, int nz);
 
 /* Creates a context on grid->device.  *out receives the handle (NULL on error).
- * Errors: MCRT_E_ARG (bad geometry / walls), MCRT_E_CUDA (no such device). */
+ * Errors: MCRT_E_ARG (bad geometry / walls / faces), MCRT_E_CUDA (no such
+ * device). */
 int mcrt_create(const mcrt_grid_desc *grid, mcrt_ctx **out);
 
 /* Copies the k-distribution tables (Section 2.1-2.2) to the device and builds

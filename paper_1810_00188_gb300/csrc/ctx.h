@@ -22,6 +22,7 @@ struct DevBuf {
 struct mcrt_ctx {
   using DevBuf = mcrt_host::DevBuf;
   mcrt_grid_desc grid{};
+  std::vector<double> yf;  // stretched grid: the ny + 1 wall-normal faces (empty: uniform)
   // k-distribution (host copy, FP64)
   bool have_kdist = false;
   int nb = 0, ng = 0, nT = 0;
@@ -43,6 +44,8 @@ struct mcrt_ctx {
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   // learned proposal: plain probabilities, feature scratch, per-ray steps, error flag
   DevBuf p0_32, feat, ray_steps, lerr, kptab;
+  // stretched grid: faces in FP64 and FP32
+  DevBuf yf64, yf32;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;

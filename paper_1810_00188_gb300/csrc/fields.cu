@@ -84,25 +84,37 @@ __global__ void __launch_bounds__(256) pack_positions_kernel(const double2 *f64,
 
 // Multigrid (Section 4.3): the fields of the next coarser grid, each coarse cell
 // the mean T and mean x of the 2x2x2 finer cells it covers (the coarse
-// temperatures come from the fine solution).  The eight values are summed z
+// temperatures come from the fine solution); on a stretched grid the mean is
+// weighted by the children's heights (volumes).  The eight values are summed z
 // outermost, x innermost.
 __global__ void __launch_bounds__(256) coarsen_kernel(const double2 *__restrict__ fine, int n0, int n1,
-                                                      int n2, double2 *__restrict__ coarse) {
+                                                      int n2, double2 *__restrict__ coarse,
+                                                      const double *__restrict__ yf, int level) {
   const int c0 = n0 / 2, c1 = n1 / 2, c2 = n2 / 2;
   const long long nc = (long long)c0 * c1 * c2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
        i += (long long)gridDim.x * blockDim.x) {
     const int I = (int)(i % c0), J = (int)((i / c0) % c1), K = (int)(i / ((long long)c0 * c1));
-    double t = 0.0, x = 0.0;
+    double t = 0.0, x = 0.0, ws = 0.0, w[2] = {1.0, 1.0};
+    if (yf) {
+      w[0] = yf[(size_t)(2 * J + 1) << level] - yf[(size_t)(2 * J) << level];
+      w[1] = yf[(size_t)(2 * J + 2) << level] - yf[(size_t)(2 * J + 1) << level];
+    }
     for (int c = 0; c < 2; ++c)
       for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) {
           const double2 v =
               fine[(size_t)(2 * I + a) + (size_t)n0 * ((size_t)(2 * J + b) + (size_t)n1 * (2 * K + c))];
-          t += v.x;
-          x += v.y;
+          if (yf) {
+            t += w[b] * v.x;
+            x += w[b] * v.y;
+            ws += w[b];
+          } else {
+            t += v.x;
+            x += v.y;
+          }
         }
-    coarse[i] = make_double2(t * 0.125, x * 0.125);
+    coarse[i] = yf ? make_double2(t / ws, x / ws) : make_double2(t * 0.125, x * 0.125);
   }
 }
 
@@ -129,12 +141,12 @@ long long multigrid_cells(int nx, int ny, int nz, int levels) {
 }
 
 cudaError_t launch_coarsen(const double2 *fine, int n0, int n1, int n2, double2 *coarse,
-                           cudaStream_t s) {
+                           const double *yf, int level, cudaStream_t s) {
   const long long nc = (long long)(n0 / 2) * (n1 / 2) * (n2 / 2);
   if (nc <= 0) return cudaSuccess;
   long long blocks = (nc + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  coarsen_kernel<<<(unsigned)blocks, 256, 0, s>>>(fine, n0, n1, n2, coarse);
+  coarsen_kernel<<<(unsigned)blocks, 256, 0, s>>>(fine, n0, n1, n2, coarse, yf, level);
   return cudaGetLastError();
 }
 

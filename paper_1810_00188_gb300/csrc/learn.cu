@@ -56,7 +56,8 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // ---- features ------------------------------------------------------------------
 // 0 T_i/1000, 1 x_i, 2 y_c/h - 1, 3-4 wall T/1000, 5 eps of the nearer wall,
-// 6 h dT/dy / 1000 (centred, one-sided at the walls), 7 h |grad_xz T| / 1000
+// 6 h dT/dy / 1000 (centred, one-sided at the walls; on a stretched grid over
+// the distance of the face-midpoint centres), 7 h |grad_xz T| / 1000
 // (centred, periodic), 8-9 mean and standard deviation of T over the 3^3
 // neighbourhood (periodic in x, z; cut at the walls) / T_i, 10 the Planck-mean
 // absorption coefficient at (T_i, x_i) times h, 11 T_max / T_i.
@@ -77,8 +78,10 @@ __global__ void __launch_bounds__(NTHR) features_kernel(const FeatArgs f) {
     auto T = [&](int ii, int jj, int kk) {
       return f.field64[(size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * kk)].x;
     };
+    // row centres: midpoints of the faces on a stretched grid
+    auto ycen = [&](int jj) { return f.yf ? 0.5 * (f.yf[jj] + f.yf[jj + 1]) : (jj + 0.5) * f.dy; };
     const double2 v = f.field64[c];
-    const double Ti = v.x, yc = (j + 0.5) * f.dy;
+    const double Ti = v.x, yc = ycen(j);
     o[0] = (float)(Ti / 1000.0);
     o[1] = (float)v.y;
     o[2] = (float)(yc / f.h - 1.0);
@@ -86,13 +89,17 @@ __global__ void __launch_bounds__(NTHR) features_kernel(const FeatArgs f) {
     o[4] = (float)(f.T_wall[1] / 1000.0);
     o[5] = (float)(yc < f.h ? f.eps_wall[0] : f.eps_wall[1]);
     double dTdy = 0.0;
-    if (ny > 1) {
+    if (ny > 1 && !f.yf) {
       if (j == 0)
         dTdy = (T(i, 1, k) - T(i, 0, k)) / f.dy;
       else if (j == ny - 1)
         dTdy = (T(i, ny - 1, k) - T(i, ny - 2, k)) / f.dy;
       else
         dTdy = (T(i, j + 1, k) - T(i, j - 1, k)) / (2.0 * f.dy);
+    } else if (ny > 1) {
+      // stretched grid: differences over the distance of the centres used
+      const int j0 = j == 0 ? 0 : j - 1, j1 = j == ny - 1 ? ny - 1 : j + 1;
+      dTdy = (T(i, j1, k) - T(i, j0, k)) / (ycen(j1) - ycen(j0));
     }
     o[6] = (float)(f.h * dTdy / 1000.0);
     const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;

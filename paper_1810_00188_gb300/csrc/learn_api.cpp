@@ -89,6 +89,7 @@ mcrt::FeatArgs feat_args(const mcrt_ctx *ctx, const int32_t *cells, long long n,
   f.dy = g.ly / g.ny;
   f.dz = g.lz / g.nz;
   f.h = 0.5 * g.ly;
+  f.yf = (const double *)ctx->yf64.p;
   f.T_wall[0] = g.T_wall[0];
   f.T_wall[1] = g.T_wall[1];
   f.eps_wall[0] = g.eps_wall[0];

@@ -236,6 +236,8 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.eps_wall[0] = g.eps_wall[0];
   a.eps_wall[1] = g.eps_wall[1];
   a.reflect = g.reflect;
+  a.yf64 = (const double *)ctx->yf64.p;
+  a.yf32 = (const float *)ctx->yf32.p;
   a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.field64 = (const double2 *)ctx->field64.p;
@@ -314,6 +316,12 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
     if (!(g->T_wall[w] >= 0.0) || !std::isfinite(g->T_wall[w])) return MCRT_E_ARG;
   }
   if (g->reflect != MCRT_REFLECT_DIFFUSE && g->reflect != MCRT_REFLECT_SPECULAR) return MCRT_E_ARG;
+  if (g->yf) {
+    // stretched y: 0 = yf[0] < yf[1] < ... < yf[ny] = ly
+    if (g->yf[0] != 0.0 || !(std::fabs(g->yf[g->ny] - g->ly) <= 1e-12 * g->ly)) return MCRT_E_ARG;
+    for (int j = 0; j < g->ny; ++j)
+      if (!(g->yf[j + 1] > g->yf[j]) || !std::isfinite(g->yf[j + 1])) return MCRT_E_ARG;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || g->device < 0 || g->device >= ndev) {
     cudaGetLastError();
@@ -322,6 +330,11 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   mcrt_ctx *ctx = new (std::nothrow) mcrt_ctx();
   if (!ctx) return MCRT_E_OOM;
   ctx->grid = *g;
+  ctx->grid.yf = nullptr;  // the caller's array is not kept
+  if (g->yf) {
+    ctx->yf.assign(g->yf, g->yf + g->ny + 1);
+    ctx->yf.back() = g->ly;
+  }
   DeviceGuard dg(g->device);
   if (!dg.ok || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
       cudaEventCreate(&ctx->ev1) != cudaSuccess ||
@@ -330,6 +343,18 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
     cudaGetLastError();
     mcrt_destroy(ctx);
     return MCRT_E_CUDA;
+  }
+  if (!ctx->yf.empty()) {
+    const size_t nf = ctx->yf.size();
+    std::vector<float> f32(ctx->yf.begin(), ctx->yf.end());
+    if (ensure(ctx->yf64, nf * sizeof(double)) != cudaSuccess ||
+        ensure(ctx->yf32, nf * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(ctx->yf64.p, ctx->yf.data(), nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->yf32.p, f32.data(), nf * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      mcrt_destroy(ctx);
+      return MCRT_E_CUDA;
+    }
   }
   *out = ctx;
   return MCRT_OK;
@@ -476,7 +501,7 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
     int d[3] = {ctx->grid.nx, ctx->grid.ny, ctx->grid.nz};
     for (int l = 1; l < mg_levels && e == cudaSuccess; ++l) {
       double2 *next = lev + (size_t)d[0] * d[1] * d[2];
-      e = mcrt::launch_coarsen(lev, d[0], d[1], d[2], next, s);
+      e = mcrt::launch_coarsen(lev, d[0], d[1], d[2], next, (const double *)ctx->yf64.p, l - 1, s);
       for (int a = 0; a < 3; ++a) d[a] /= 2;
       lev = next;
     }
@@ -683,7 +708,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -826,6 +851,8 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.eps_wall[0] = g.eps_wall[0];
   a.eps_wall[1] = g.eps_wall[1];
   a.reflect = g.reflect;
+  a.yf64 = (const double *)ctx->yf64.p;
+  a.yf32 = (const float *)ctx->yf32.p;
   a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
@@ -1013,6 +1040,8 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.eps_wall[0] = g.eps_wall[0];
     a.eps_wall[1] = g.eps_wall[1];
     a.reflect = g.reflect;
+    a.yf64 = (const double *)c->yf64.p;
+    a.yf32 = (const float *)c->yf32.p;
     a.field32 = (const float2 *)c->field32.p;
     a.fpos32 = (const uint2 *)c->fpos32.p;
     a.ktab32 = (const float2 *)c->ktab32.p;

@@ -18,6 +18,9 @@ struct TraceArgs {
   double T0, inv_dT, inv_xref;
   double eps_wall[2];
   int reflect;  // 0 diffuse, 1 specular
+  // stretched wall-normal grid: the ny + 1 faces (null: uniform dy)
+  const double *yf64;
+  const float *yf32;
   // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
   const float2 *field32;    // {T, x} per cell
   const uint2 *fpos32;      // FP32 kernel: {(node << 23) | fraction * 2^23, bits of x / x_ref}
@@ -72,8 +75,10 @@ struct TraceArgs {
 int multigrid_levels(int nx, int ny, int nz);
 long long multigrid_cells(int nx, int ny, int nz, int levels);
 // Fields of grid l + 1 (2x2x2 means of T and x) from grid l of n0 x n1 x n2 cells.
+// On a stretched grid (yf non-null) the means are weighted by the children's
+// heights; `level` is grid l, whose face F is yf[F << l].
 cudaError_t launch_coarsen(const double2 *fine, int n0, int n1, int n2, double2 *coarse,
-                           cudaStream_t s);
+                           const double *yf, int level, cudaStream_t s);
 
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
@@ -114,6 +119,7 @@ constexpr int kMaxTallyK = 1024;    // spectral points limit of the tally kernel
 struct FeatArgs {
   int nx, ny, nz;
   double dx, dy, dz, h;
+  const double *yf;  // stretched grid: the ny + 1 wall-normal faces (null: uniform dy)
   double T_wall[2], eps_wall[2], T_max;
   const double2 *field64;
   const uint2 *fpos32;

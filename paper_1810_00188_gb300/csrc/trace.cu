@@ -59,6 +59,7 @@ template <> struct Prec<float> {
   __device__ static const float2 *ktab(const TraceArgs &a) { return a.ktab32; }
   __device__ static const float2 *btab(const TraceArgs &a) { return a.btab32; }
   __device__ static const float *bwall(const TraceArgs &a) { return a.bwall32; }
+  __device__ static const float *yf(const TraceArgs &a) { return a.yf32; }
   __device__ static void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
   __device__ static float div(float a, float b) { return __fdividef(a, b); }
   // alpha = 1 - exp(-x) (Eq. 2) and the transmission factor exp(-x) (Eq. 3).
@@ -78,6 +79,7 @@ template <> struct Prec<double> {
   __device__ static const double2 *ktab(const TraceArgs &a) { return a.ktab64; }
   __device__ static const double2 *btab(const TraceArgs &a) { return a.btab64; }
   __device__ static const double *bwall(const TraceArgs &a) { return a.bwall64; }
+  __device__ static const double *yf(const TraceArgs &a) { return a.yf64; }
   __device__ static void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
   __device__ static double div(double a, double b) { return a / b; }
   __device__ static void absorb(double x, double &alpha, double &trans) {
@@ -220,6 +222,11 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   const R *__restrict__ bwall = Prec<R>::bwall(a);
   const R T0 = (R)a.T0, inv_dT = (R)a.inv_dT, inv_xref = (R)a.inv_xref, tol = (R)a.tol;
   const R DX = (R)a.dx, DY = (R)a.dy, DZ = (R)a.dz;
+  // stretched y: faces (null: uniform DY); the height of row j of grid l
+  const R *__restrict__ yfs = Prec<R>::yf(a);
+  auto dyl = [&](int j, int l) -> R {
+    return __ldg(yfs + ((size_t)(j + 1) << l)) - __ldg(yfs + ((size_t)j << l));
+  };
 
   // emitting cell state
   const R2 fi = __ldg(field + cell);
@@ -288,8 +295,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     int sx, sy_, sz;
     R t0x, t0y, t0z, tsx, tsy, tsz;
     axis_setup<R>(ddx, fx, DX, sx, t0x, tsx);
-    axis_setup<R>(ddy, fy, DY, sy_, t0y, tsy);
+    axis_setup<R>(ddy, fy, yfs ? dyl(cj, 0) : DY, sy_, t0y, tsy);
     axis_setup<R>(ddz, fz, DZ, sz, t0z, tsz);
+    // stretched y: tsy is 1/|d_y|, and each y crossing adds the next row's height
+    if (yfs && sy_ != 0) tsy = (R)1 / fabs(ddy);
     R cntx = 0, cnty = 0, cntz = 0;
     R tnx = t0x, tny = t0y, tnz = t0z, tprev = 0;
     R X = 0, tau = 1, B_last = B_i;
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
         tny = fma(cnty, tsy, t0y);
         iy += sy_;
         lin += sy_ * nxl;
+        if (yfs && iy >= 0 && iy < nyl) tny = tprev + dyl(iy, lev) * tsy;
         if (iy < 0 || iy >= nyl) {
           // wall event: the wall absorbs eps of the ray and emits at T_wall
           const int wl = iy < 0 ? 0 : 1;
@@ -408,8 +418,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
           ++nrefl;
           const R gl = (R)(1 << lev);  // cell size of the current grid / finest
           axis_setup<R>(ddx, fx, DX * gl, sx, t0x, tsx);
-          axis_setup<R>(ddy, fy, DY * gl, sy_, t0y, tsy);
+          axis_setup<R>(ddy, fy, yfs ? dyl(iy, lev) : DY * gl, sy_, t0y, tsy);
           axis_setup<R>(ddz, fz, DZ * gl, sz, t0z, tsz);
+          if (yfs && sy_ != 0) tsy = (R)1 / fabs(ddy);
           cntx = cnty = cntz = 0;
           tnx = t0x;
           tny = t0y;
@@ -427,8 +438,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
           tnx = fma(cntx, tsx, t0x);
         }
         if (sy_ != 0 && ((sy_ > 0 ? iy + 1 : iy) & 1)) {
-          cnty += inc;
-          tny = fma(cnty, tsy, t0y);
+          if (yfs) {
+            tny += dyl(sy_ > 0 ? iy + 1 : iy - 1, lev) * tsy;  // the skipped row's height
+          } else {
+            cnty += inc;
+            tny = fma(cnty, tsy, t0y);
+          }
         }
         if (sz != 0 && ((sz > 0 ? iz + 1 : iz) & 1)) {
           cntz += inc;

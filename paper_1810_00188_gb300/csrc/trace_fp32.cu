@@ -202,6 +202,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   const float2 *__restrict__ btab = a.btab32;
   const float tol = (float)a.tol;
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
+  // stretched y (faces non-null): tsy holds 1/|d_y| and each y crossing adds the
+  // next row's height; the height of row j of grid l from the faces
+  const float *__restrict__ yfs = a.yf32;
+  auto dyl = [&](int j, int l) -> float {
+    return __ldg(yfs + ((unsigned)(j + 1) << l)) - __ldg(yfs + ((unsigned)j << l));
+  };
   const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
   float *__restrict__ Ybuf = a.ybuf;
   const unsigned long long ray_off = a.ray_offset_dev ? *a.ray_offset_dev : a.ray_offset;
@@ -340,8 +346,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           int ssx, ssy, ssz;
           float a0x, a0y, a0z, asx, asy, asz;
           axis_setup(st * cphi, fx, DX, ssx, a0x, asx);
-          axis_setup(mu, fy, DY, ssy, a0y, asy);
+          axis_setup(mu, fy, yfs ? dyl(a.bj0 + c_by, 0) : DY, ssy, a0y, asy);
           axis_setup(st * sphi, fz, DZ, ssz, a0z, asz);
+          if (yfs && ssy != 0) asy = __frcp_rn(fabsf(mu));
           const int pos = (tail + lane) & (POOL - 1);
           R.A[pos] = make_float4(a0x, a0y, a0z, asx);
           R.B[pos] = make_float4(asy, asz, bi.x + fr_i * bi.y, wgt * kap_i);
@@ -469,6 +476,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           ix += mx ? sx : 0;
           iy += my ? sy : 0;
           iz += mz ? sz : 0;
+          if (yfs && my && iy >= 0 && iy < nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
           lin += mx ? (unsigned)sx : (my ? (unsigned)(sy * nxl) : (unsigned)(sz * nxyl));
           const int wx = ix >= nxl ? -nxl : (ix < 0 ? nxl : 0);
           ix += wx;
@@ -512,7 +520,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
                 // specular: |d| per axis unchanged, the y component flips
                 ddx = sx > 0 ? gb * DX / tsx : (sx < 0 ? -gb * DX / tsx : 0.f);
                 ddz = sz > 0 ? gb * DZ / tsz : (sz < 0 ? -gb * DZ / tsz : 0.f);
-                ddy = wl == 0 ? gb * DY / tsy : -gb * DY / tsy;
+                const float ady = yfs ? 1.f / tsy : gb * DY / tsy;
+                ddy = wl == 0 ? ady : -ady;
               } else {
                 // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
                 const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
@@ -526,8 +535,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
               }
               ++nrefl;
               axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
-              axis_setup(ddy, nfy, gl * DY, sy, t0y, tsy);
+              axis_setup(ddy, nfy, yfs ? dyl(iy, MG ? lev : 0) : gl * DY, sy, t0y, tsy);
               axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
+              if (yfs && sy != 0) tsy = __frcp_rn(fabsf(ddy));
               cntx = cnty = cntz = 0.f;
               tnx = t0x;
               tny = t0y;
@@ -547,8 +557,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             tnx = fmaf(cntx, tsx, t0x);
           }
           if (sy != 0 && ((sy > 0 ? iy + 1 : iy) & 1)) {
-            cnty += inc;
-            tny = fmaf(cnty, tsy, t0y);
+            if (yfs) {
+              tny += dyl(sy > 0 ? iy + 1 : iy - 1, lev) * tsy;  // the skipped row's height
+            } else {
+              cnty += inc;
+              tny = fmaf(cnty, tsy, t0y);
+            }
           }
           if (sz != 0 && ((sz > 0 ? iz + 1 : iz) & 1)) {
             cntz += inc;

@@ -38,7 +38,8 @@ STATUS_NAMES = {0: "ok", 1: "E_ARG", 2: "E_STATE", 3: "E_CUDA", 4: "E_OOM", 5: "
 class mcrt_grid_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double),
                 ("ly", C.c_double), ("lz", C.c_double), ("eps_wall", C.c_double * 2),
-                ("T_wall", C.c_double * 2), ("reflect", C.c_int), ("device", C.c_int)]
+                ("T_wall", C.c_double * 2), ("reflect", C.c_int), ("device", C.c_int),
+                ("yf", C.POINTER(C.c_double))]
 
 
 class mcrt_kdist_desc(C.Structure):
@@ -432,6 +433,10 @@ class Solver:
         g.T_wall[0], g.T_wall[1] = grid.T_wall
         g.reflect = grid.reflect
         g.device = device
+        yf = getattr(grid, "yf", None)
+        self._yf_keep = None if yf is None else np.ascontiguousarray(yf, dtype=np.float64)
+        if self._yf_keep is not None:
+            g.yf = self._yf_keep.ctypes.data_as(C.POINTER(C.c_double))
         self.grid = grid
         self.device = device
         self.ctx = mcrt_create(g)

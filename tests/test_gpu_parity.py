@@ -227,3 +227,31 @@ def test_fp32_results_independent_of_launch_shape():
     with pytest.raises(mcrt.McrtError):
         S.set_tuning(9)
     S.close()
+
+
+@pytest.mark.parametrize("stretched,levels", [(False, 1), (True, 1), (False, 6)])
+def test_dns_size_256x192x128_crop_against_oracle(stretched, levels):
+    """The DNS-size channel (256 x 192 x 128, 40x8 k-distribution, x_H2O field,
+    grey walls eps = 0.8, 512 rays, FP32 march with FP64 tallies): the whole field
+    is solved on the GPU and its central 32^3 crop is checked cell by cell against
+    the FP64 oracle on the same draws (rays cross the full field).  Also on a
+    wall-refined grid and with the multigrid march on 6 grids."""
+    grid, kd, T, x = inputs.nongrey_channel(256, 192, 128, seed=3, eps_wall=0.8, x_mode="field")
+    if stretched:
+        grid.yf = inputs.channel_faces(192, grid.ly, 1.5)
+        T, x = inputs.channel_fields(grid, 3, x_mode="field")
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    q, s = S.solve(rays=512, seed=0, tol=1e-4, max_steps=1 << 20, precision=mcrt.MCRT_FP32,
+                   mg_levels=levels, mg_steps=5)
+    st = S.stats()
+    S.close()
+    assert st["rays"] == grid.ncells * 512 and st["wall_hits"] > 0
+    box = (112, 144, 80, 112, 48, 80)
+    o = oracle.solve(grid, kd, T, x, rays=512, seed=0, tol=1e-4, max_steps=1 << 20, box=box,
+                     mg_levels=levels, mg_steps=5)
+    crop = q[48:80, 80:112, 112:144]
+    err = np.abs(crop - o["q"])
+    assert np.all(err <= 1e-4 * o["scale"]), np.max(err / o["scale"])
+    big = o["sigma"] > 1e-3 * o["scale"]
+    assert np.allclose(s[48:80, 80:112, 112:144][big], o["sigma"][big], rtol=2e-2)

@@ -145,8 +145,10 @@ def cpu_baseline(a, target_s=12.0):
 
 def batch_extra(sp, rays=256, n=32, seed=0):
     """32 snapshots of uneven grid sizes (32^3, 48x64x48, 96^3, 128^3), 256 rays
-    per cell, solved in one graph launch; compared with the same snapshots
-    solved one after another."""
+    per cell, sharing the k-distribution: one graph launch that holds a single
+    persistent trace kernel over all snapshots and one reduction.  The launch
+    shape (CTAs per SM, march steps per round) is tuned; compared with the same
+    snapshots solved one after another."""
     import torch
 
     from paper_1810_00188_gb300 import autotune, inputs, mcrt
@@ -162,17 +164,15 @@ def batch_extra(sp, rays=256, n=32, seed=0):
         items.append((S.ctx, q.data_ptr(), sg.data_ptr(), k))
     params = mcrt.Solver.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32)
 
-    def make(cfg):
-        streams, weighted = cfg
-        w = autotune.batch_weights(solvers, outs, rays_probe=64, stream=sp) if weighted else None
-        return mcrt.mcrt_batch_create(items, params, weights=w, streams=streams)
+    def make(shape):
+        solvers[0].set_tuning(*shape)
+        return mcrt.mcrt_batch_create(items, params)
 
     def run(b):
         mcrt.mcrt_batch_run(b, rays, sp)
         return mcrt.mcrt_batch_get_stats(b)["kernel_ms"]
 
-    cfgs = ((1, False), (2, False), (4, False), (n, True))
-    best, table = autotune.tune_batch(make, run, shapes=cfgs, reps=1)
+    best, table = autotune.tune_batch(make, run, shapes=((3, 1), (3, 2), (2, 1), (2, 2)), reps=1)
     b = make(best)
     try:
         mcrt.mcrt_batch_run(b, 0, sp)
@@ -184,6 +184,7 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             times.append(st["kernel_ms"])
     finally:
         mcrt.mcrt_batch_destroy(b)
+    solvers[0].set_tuning()
     seq = 0.0
     for S, (q, sg) in zip(solvers, outs):
         S.solve_into(S.params(rays=rays, seed=seed, ray_offset=rays, precision=mcrt.MCRT_FP32), q, sg,
@@ -197,8 +198,8 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             "cells": cells, "graph_ms": t * 1e3, "rays_per_s": cells * rays / t,
             "steps_per_s": st["steps"] / t, "launches_in_graph": st["launches"],
             "sequential_ms": seq, "speedup_vs_sequential": seq / (t * 1e3),
-            "tuned": {"streams": best[0], "weighted": best[1]},
-            "tuning_ms": {f"{k[0]}{'w' if k[1] else ''}": v for k, v in table.items()}}
+            "tuned": {"min_blocks_per_sm": best[0], "steps_per_round": best[1]},
+            "tuning_ms": {f"{k[0]}x{k[1]}": v for k, v in table.items()}}
 
 
 def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):

@@ -234,15 +234,24 @@ int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q
 /* Batched snapshots (no counterpart in the paper, which solves one field per
  * call; its DNS coupling solves one snapshot per time step, Section 5).  A batch
  * solves many contexts -- snapshots of possibly different grid sizes, each with
- * its k-distribution and fields set -- in one CUDA-graph launch.  Inside the
- * graph each item is one persistent FP32 trace kernel (and its per-cell
- * reduction); `streams` concurrent branches run the items in decreasing order of
- * `weights` (NULL: cell counts), round-robin.  Without weights every item's
- * kernel is a full wave of persistent CTAs, so one kernel's tail overlaps the
- * next one's start; with weights each item gets that share of one wave (meant
- * for streams = n: all items at once).  The solve parameters (FP32 only, whole
- * grids; p->box, p->snapshot, p->ray_offset and p->steps_out are ignored) and the
- * launch shape of items[0].ctx are fixed at creation. */
+ * its k-distribution and fields set -- in one CUDA-graph launch.
+ *  - When every item has the same k-distribution (up to 1024 items), the graph
+ *    holds ONE persistent FP32 trace launch over all the items' cells and one
+ *    per-cell reduction (per scratch chunk: the sample scratch covers the whole
+ *    batch when it fits in half the free device memory).  Warps claim runs of
+ *    cells of the concatenated snapshots, largest snapshot first; a warp lets
+ *    its rays finish before it moves on to another snapshot.  `weights` and
+ *    `streams` are not used.
+ *  - Otherwise each item is one persistent FP32 trace kernel (and its per-cell
+ *    reduction) inside the graph; `streams` concurrent branches run the items in
+ *    decreasing order of `weights` (NULL: cell counts), round-robin.  Without
+ *    weights every item's kernel is a full wave of persistent CTAs, so one
+ *    kernel's tail overlaps the next one's start; with weights each item gets
+ *    that share of one wave (meant for streams = n: all items at once).
+ * The solve parameters (FP32 only, whole grids; p->box, p->snapshot,
+ * p->ray_offset and p->steps_out are ignored) and the launch shape of
+ * items[0].ctx are fixed at creation.  Every item's result equals its own
+ * mcrt_solve_qrad with the item's snapshot word, bit for bit. */
 typedef struct mcrt_batch mcrt_batch;
 typedef struct {
   mcrt_ctx *ctx;           /* distinct contexts on one device                    */
@@ -253,9 +262,10 @@ typedef struct {
 
 /* Builds the batch: proposals, scratch, and the captured graph.  items[0..n-1]
  * are the snapshots; weights (host, n values > 0, or NULL) their relative cost;
- * streams (>= 1, clamped to n) the number of concurrent graph branches.  Items of
- * one branch run one after another and share that branch's sample scratch (the
- * largest item's chunk, capped by items[0].ctx's scratch_mib).  Synchronous;
+ * streams (>= 1, clamped to n) the number of concurrent graph branches (both
+ * only for items with different k-distributions).  There, items of one branch
+ * run one after another and share that branch's sample scratch (the largest
+ * item's chunk, capped by items[0].ctx's scratch_mib).  Synchronous;
  * allocates.  Errors: MCRT_E_ARG, MCRT_E_STATE, MCRT_E_UNSUPPORTED, MCRT_E_CUDA,
  * MCRT_E_OOM (messages on items[0].ctx). */
 int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt_solve_params *p,

@@ -929,6 +929,7 @@ struct mcrt_batch {
   std::vector<unsigned long long *> counters;
   int rays = 0;
   int launches = 0;
+  bool single_launch = false;  // one persistent trace launch over every snapshot
   bool ran = false;
   cudaStream_t last_stream = nullptr;
   std::string err;
@@ -1089,11 +1090,113 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     w[k] = weights ? weights[k] : (double)a.ncells_box;
     wsum += w[k];
   }
-  // persistent CTAs: with weights, one wave shared by the items in proportion to
-  // their work (all items run at once); without, each item's kernel is a full
-  // wave and `streams` branches run items in decreasing order of work, so one
-  // kernel's tail overlaps the next kernel's start
   mcrt_ctx *c0 = items[0].ctx;
+  // Snapshots that share the k-distribution run as ONE persistent trace launch
+  // (and one reduction) over all their cells: warps claim runs of brick-ordered
+  // positions of the concatenated snapshots, largest snapshot first.
+  bool same_kdist = n <= mcrt::fp32_batch_max_snapshots();
+  for (int k = 1; k < n && same_kdist; ++k) {
+    const mcrt_ctx *c = items[k].ctx;
+    same_kdist = c->nb == c0->nb && c->ng == c0->ng && c->nT == c0->nT && c->T0 == c0->T0 &&
+                 c->dT == c0->dT && c->x_ref == c0->x_ref && c->w_g == c0->w_g &&
+                 c->kappa == c0->kappa && c->B == c0->B;
+  }
+  if (same_kdist) {
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P[x] > P[y]; });
+    std::vector<mcrt::SnapArgs> sn(n + 1);
+    std::memset(sn.data(), 0, sizeof(mcrt::SnapArgs) * (n + 1));
+    long long pos = 0;
+    for (int r = 0; r < n; ++r) {
+      const int k = order[r];
+      const mcrt::TraceArgs &a = args[k];
+      mcrt::SnapArgs &t = sn[r];
+      t.fpos32 = a.fpos32;
+      t.yf32 = a.yf32;
+      t.bwall32 = a.bwall32;
+      t.wgt32 = a.wgt32;
+      t.cn = a.cn;
+      t.cg = a.cg;
+      t.guide = a.guide;
+      t.cell_cn = a.cell_cn;
+      t.cell_cg = a.cell_cg;
+      t.cell_hemi = a.cell_hemi;
+      t.q = a.q;
+      t.sigma = a.sigma;
+      t.p0 = pos;
+      t.nx = a.nx;
+      t.ny = a.ny;
+      t.nz = a.nz;
+      t.reflect = a.reflect;
+      t.dx = (float)a.dx;
+      t.dy = (float)a.dy;
+      t.dz = (float)a.dz;
+      t.eps0 = (float)a.eps_wall[0];
+      t.eps1 = (float)a.eps_wall[1];
+      t.snapshot = a.snapshot;
+      pos += P[k];
+    }
+    sn[n].p0 = pos;
+    void *d_sn = nullptr;
+    BK(cudaMalloc(&d_sn, sizeof(mcrt::SnapArgs) * (n + 1)), "alloc snapshots");
+    b->owned.push_back(d_sn);
+    BK(cudaMemcpy(d_sn, sn.data(), sizeof(mcrt::SnapArgs) * (n + 1), cudaMemcpyHostToDevice), "copy snapshots");
+    // sample scratch: the whole batch when at most half the free memory, else chunks
+    size_t fr = 0, tot = 0;
+    BK(cudaMemGetInfo(&fr, &tot), "memory info");
+    const size_t per_pos = (size_t)p->rays_per_cell * sizeof(float);
+    long long pc = (long long)((fr / 2) / per_pos);
+    if (pc < 1) pc = 1;
+    if (pc > pos) pc = pos;
+    void *yb = nullptr, *ct = nullptr;
+    BK(cudaMalloc(&yb, (size_t)pc * per_pos), "alloc sample scratch");
+    b->owned.push_back(yb);
+    BK(cudaMalloc(&ct, 8 * sizeof(unsigned long long)), "alloc counters");
+    b->owned.push_back(ct);
+    b->counters.assign(1, (unsigned long long *)ct);
+    mcrt::TraceArgs a = args[order[0]];
+    a.snaps = (const mcrt::SnapArgs *)d_sn;
+    a.nsnaps = n;
+    a.ybuf = (float *)yb;
+    a.step_acc = nullptr;
+    a.steps_cell = nullptr;
+    a.ray_steps = nullptr;
+    a.counters = (unsigned long long *)ct;
+    a.grid_blocks = 0;
+    int bps = 0, nsm = 0;
+    BK(mcrt::prepare_trace_fp32_batch(c0->min_blocks, c0->steps_per_round, a.nb, a.ng, n, a.counts_in_smem,
+                                      a.mg_levels > 1, &bps, &nsm),
+       "prepare launch");
+    b->streams.assign(1, nullptr);
+    BK(cudaStreamCreateWithFlags(&b->streams[0], cudaStreamNonBlocking), "stream");
+    BK(cudaDeviceSynchronize(), "sync");
+    cudaStream_t s0 = b->streams[0];
+    BK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t ce = cudaMemsetAsync(a.counters, 0, 6 * sizeof(unsigned long long), s0);
+    int launches = 0;
+    for (long long p0 = 0; p0 < pos && ce == cudaSuccess; p0 += pc) {
+      a.chunk_p0 = p0;
+      a.chunk_p1 = p0 + pc < pos ? p0 + pc : pos;
+      ce = mcrt::launch_trace_fp32_batch(a, c0->min_blocks, c0->steps_per_round, s0);
+      launches += 2;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s0, &graph);
+    b->graph = graph;
+    if (ce != cudaSuccess) return bail(MCRT_E_CUDA, ce, "capture");
+    if (ee != cudaSuccess) return bail(MCRT_E_CUDA, ee, "end capture");
+    BK(cudaGraphInstantiate(&b->exec, b->graph, 0), "instantiate graph");
+    b->launches = launches;
+    b->single_launch = true;
+    *out = b;
+    return MCRT_OK;
+  }
+  // Otherwise one graph of per-snapshot launches.  Persistent CTAs: with
+  // weights, one wave shared by the items in proportion to their work (all
+  // items run at once); without, each item's kernel is a full wave and `streams`
+  // branches run items in decreasing order of work, so one kernel's tail
+  // overlaps the next kernel's start.
   int bps = 0, nsm = 0;
   BK(mcrt::prepare_trace_fp32(c0->min_blocks, c0->steps_per_round, args[0].nb, args[0].ng,
                               args[0].counts_in_smem, args[0].mg_levels > 1, &bps, &nsm),

@@ -9,6 +9,25 @@
 namespace mcrt {
 
 // Everything one trace launch reads.  Device pointers only.
+// One snapshot of a batched FP32 solve (one persistent launch over many
+// fields that share the k-distribution): what differs from snapshot to
+// snapshot.  Snapshot k owns the global brick-order positions [p0, next p0).
+struct SnapArgs {
+  const uint2 *fpos32;               // positions of every multigrid grid
+  const float *yf32;                 // stretched faces or null
+  const float *bwall32;              // [2][nb]
+  const float *wgt32;                // plain-proposal ray weights [nb*ng]
+  const unsigned long long *cn, *cg; // plain proposal counts
+  const unsigned short *guide;
+  const unsigned long long *cell_cn, *cell_cg;  // per-cell proposal or null
+  const unsigned int *cell_hemi;
+  double *q, *sigma;                 // outputs, the whole grid
+  long long p0;                      // first global position
+  int nx, ny, nz, reflect;
+  float dx, dy, dz, eps0, eps1;
+  unsigned snapshot;                 // fourth Philox counter word
+};
+
 struct TraceArgs {
   // grid (uniform cells; y wall-normal; x, z periodic)
   int nx, ny, nz;
@@ -54,6 +73,10 @@ struct TraceArgs {
   // replay) when non-null; persistent grid size override (0: one full wave)
   const unsigned long long *ray_offset_dev;
   int grid_blocks;
+  // batched FP32 solve: the snapshots (device [nsnaps + 1]; the last entry only
+  // holds the end position in p0); null for a single solve
+  const SnapArgs *snaps;
+  int nsnaps;
   // multigrid (Section 4.3): grids used (1: exact march) and segments per grid;
   // the fields of grid l (l >= 1) follow those of grid l - 1 in field64 / fpos32
   int mg_levels, mg_steps;
@@ -90,6 +113,13 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);
+// Batched FP32 solve over a.snaps: trace + reduce of the global positions
+// [chunk_p0, chunk_p1), one persistent launch each.
+cudaError_t launch_trace_fp32_batch(const TraceArgs &a, int min_blocks, int steps_per_round,
+                                    cudaStream_t s);
+cudaError_t prepare_trace_fp32_batch(int min_blocks, int steps_per_round, int nb, int ng, int nsnaps,
+                                     int counts_in_smem, int multigrid, int *blocks_per_sm, int *num_sms);
+int fp32_batch_max_snapshots();
 // Sets the launch attributes of the chosen FP32 variant and returns its
 // resident CTAs per SM (call before stream capture).
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,

@@ -1,0 +1,164 @@
+// Device helpers shared by the FP32 trace kernels of trace_fp32.cu (one solve)
+// and batch.cu (many snapshots in one launch): the per-warp ray ring, exact bit
+// constructions of uniforms and small integers, the interpolation position, the
+// sine/cosine series, the guided inverse CDF, the absorption of a segment, the
+// axis set-up of the parametric ray, compensated binary32 sums, and the
+// brick-order enumeration of cells.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "mcrt_internal.h"
+
+namespace mcrt {
+namespace {
+
+constexpr int POOL = 64;   // prepared ray states per warp
+constexpr int WARPS = 8;   // warps per CTA
+constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks
+constexpr int GUIDE = 64;  // guide-table buckets of the band CDF
+
+struct WarpRing {
+  float4 A[POOL];  // t0x, t0y, t0z, tsx
+  float4 B[POOL];  // tsy, tsz, B_i, w * kappa_i
+  uint4 C[POOL];   // n | g << 16, Philox ray index, axis signs, emitting cell (linear)
+  int4 D[POOL];    // sample slot (cell position in the chunk), ix, iy, iz
+};
+
+// Exact bit constructions instead of conversion instructions:
+//  * uniform (w>>9 + 1/2) 2^-23: the 23 draw bits as the mantissa of a number in
+//    [1, 2), minus (1 - 2^-24); exact (Sterbenz);
+//  * u < 2^23 as a float: mantissa bits of 2^23 + u, minus 2^23; exact;
+//  * floor / nearest integer of f in [0, 2^22]: adding 1.5 * 2^23 with directed
+//    or nearest rounding puts the integer in the low mantissa bits (the sum's ulp
+//    is 1); exact.
+__device__ __forceinline__ float unif(unsigned w) {
+  return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
+}
+
+__device__ __forceinline__ float u23_to_float(unsigned u) {
+  return __uint_as_float(0x4B000000u | u) - 8388608.f;
+}
+
+__device__ __forceinline__ float u33_to_float(unsigned long long c) {
+  if (c >> 32) return 4294967296.f;
+  const unsigned v = (unsigned)c;
+  return u23_to_float(v >> 16) * 65536.f + u23_to_float(v & 0xffffu);
+}
+
+// A cell's precomputed interpolation position (Section 2.2's linear
+// interpolation in T; see pack_positions_kernel): node index in the top 9 bits,
+// the fraction towards the next node as 23 mantissa bits (exact).
+__device__ __forceinline__ void tpos(unsigned packed, unsigned &it, float &fr) {
+  it = packed >> 23;
+  fr = __uint_as_float(0x3F800000u | (packed & 0x7FFFFFu)) - 1.f;
+}
+
+// sin(pi x), cos(pi x) for x in [0, 2]: x = k/2 + r with k the nearest integer of
+// 2x and |r| <= 1/4 (both exact), then Taylor series of sin and cos at pi r
+// (truncation below 2e-9 relative) rotated by the quadrant k.
+__device__ __forceinline__ void sincospi_02(float x, float &s, float &c) {
+  const float kf = __fadd_rn(2.f * x, 12582912.f);
+  const int k = __float_as_int(kf) - 0x4B400000;
+  const float r = x - 0.5f * (kf - 12582912.f);
+  const float a = 3.14159265358979f * r, a2 = a * a;
+  const float sp = a * (1.f + a2 * (-1.f / 6.f + a2 * (1.f / 120.f + a2 * (-1.f / 5040.f + a2 * (1.f / 362880.f)))));
+  const float cp = 1.f + a2 * (-0.5f + a2 * (1.f / 24.f + a2 * (-1.f / 720.f + a2 * (1.f / 40320.f + a2 * (-1.f / 3628800.f)))));
+  const int q = k & 3;
+  const float ss = (q & 1) ? cp : sp, cc = (q & 1) ? sp : cp;
+  s = (q & 2) ? -ss : ss;
+  c = ((q + 1) & 2) ? -cc : cc;
+}
+
+// First k with u < cum[k] (the inverse CDF of Eq. 17), started from a guide
+// table: guide[m] = first k with cum[k] > m 2^26, so the scan is short.
+__device__ __forceinline__ int pick_guided(const unsigned long long *__restrict__ cum,
+                                           const unsigned short *__restrict__ guide, unsigned u) {
+  int k = guide[u >> 26];
+  while ((unsigned long long)u >= cum[k]) ++k;
+  return k;
+}
+
+__device__ __forceinline__ void absorb(float x, float &alpha, float &trans) {
+  // alpha = 1 - exp(-x) (Eq. 2), trans = exp(-x) (Eq. 3); a 4-term series below
+  // x = 0.05 avoids the cancellation of 1 - exp(-x)
+  const float e = __expf(-x);
+  const float sr = x * (1.f - x * (0.5f - x * (0.16666667f - x * 0.041666668f)));
+  const bool small = x < 0.05f;
+  alpha = small ? sr : 1.f - e;
+  trans = small ? 1.f - sr : e;
+}
+
+// Parametric ray o + t d along one axis: the m-th face crossing is at t0 + m ts.
+__device__ __forceinline__ void axis_setup(float d, float fr, float delta, int &s, float &t0,
+                                           float &ts) {
+  if (d > 0.f) {
+    s = 1;
+    ts = __fdividef(delta, d);
+    t0 = (1.f - fr) * ts;
+  } else if (d < 0.f) {
+    s = -1;
+    ts = __fdividef(delta, -d);
+    t0 = fr * ts;
+  } else {
+    s = 0;
+    ts = INFINITY;
+    t0 = INFINITY;
+  }
+}
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (b - bb);
+  hi = s;
+  lo += err;
+}
+
+// Brick-order position p (relative to a bnx x bny x bnz box) -> box coordinates;
+// false for positions outside the box (ragged edge bricks).
+__device__ __forceinline__ bool brick_cell_d(int bnx, int bny, int bnz, long long p, int &bx, int &by,
+                                             int &bz) {
+  const int nbx = (bnx + BRICK - 1) / BRICK, nby = (bny + BRICK - 1) / BRICK;
+  const long long brick = p / (BRICK * BRICK * BRICK);
+  const int off = (int)(p - brick * (BRICK * BRICK * BRICK));
+  const int gx = (int)(brick % nbx), gy = (int)((brick / nbx) % nby), gz = (int)(brick / ((long long)nbx * nby));
+  bx = gx * BRICK + off % BRICK;
+  by = gy * BRICK + (off / BRICK) % BRICK;
+  bz = gz * BRICK + off / (BRICK * BRICK);
+  return bx < bnx && by < bny && bz < bnz;
+}
+
+__device__ __forceinline__ bool brick_cell(const TraceArgs &a, long long p, int &bx, int &by,
+                                           int &bz) {
+  return brick_cell_d(a.bnx, a.bny, a.bnz, p, bx, by, bz);
+}
+
+// Batched solves: the snapshot that owns global position p (starts[k] is
+// snapshot k's first position; starts[n] the end).
+__device__ __forceinline__ int snapshot_of(const long long *starts, int n, long long p) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= p)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// MG: the multigrid march of Section 4.3 (a.mg_levels grids); the exact march
+
+// Compensated binary32 pair (hi + lo) plus another pair, renormalised.
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float bhi, float blo) {
+  const float s = hi + bhi;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bhi - bb) + (lo + blo);
+  hi = s + err;
+  lo = err - (hi - s);
+}
+
+}  // namespace
+}  // namespace mcrt

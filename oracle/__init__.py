@@ -46,7 +46,7 @@ class Problem(C.Structure):
                 ("w_g", C.POINTER(C.c_double)), ("T0", C.c_double), ("dT", C.c_double),
                 ("nT", C.c_int), ("kappa", C.POINTER(C.c_double)),
                 ("B", C.POINTER(C.c_double)), ("x_ref", C.c_double),
-                ("yf", C.POINTER(C.c_double))]
+                ("yf", C.POINTER(C.c_double)), ("xz_walls", C.c_int), ("T_xz", C.c_double * 4)]
 
 
 class Params(C.Structure):
@@ -156,6 +156,9 @@ def make_problem(grid, kd, T, x=None):
     if keep.yf is not None:
         assert keep.yf.size == grid.ny + 1
     P.yf = _dp(keep.yf) if keep.yf is not None else C.POINTER(C.c_double)()
+    P.xz_walls = int(getattr(grid, "xz_walls", 0))
+    for f, t in enumerate(getattr(grid, "T_xz", (0.0, 0.0, 0.0, 0.0))):
+        P.T_xz[f] = float(t)
     P._keep = keep
     return P
 

@@ -158,6 +158,9 @@ int orc_plain_proposal(const orc_problem *P, uint64_t *cn, uint64_t *cg, double 
     if (P->T[c] > Tm) Tm = P->T[c];
   for (int w = 0; w < 2; ++w)
     if (P->eps_wall[w] > 0.0 && P->T_wall[w] > Tm) Tm = P->T_wall[w];
+  if (P->xz_walls)
+    for (int f = 0; f < 4; ++f)
+      if (P->T_xz[f] > Tm) Tm = P->T_xz[f];
   if (T_max) *T_max = Tm;
   const int nb = P->n_bands, ng = P->n_g;
   double *wn = (double *)malloc(sizeof(double) * nb);
@@ -427,6 +430,19 @@ restart:
     c[a] += sgn[a];
     if (sy && a == 1 && c[1] >= 0 && c[1] < N[1])
       tnext[1] = (yface(P, lev, c[1] + (sgn[1] > 0)) - y_o) / d[1];
+    if (P->xz_walls && a != 1 && (c[a] < 0 || c[a] >= N[a])) {
+      /* closed box: a black wall at an x or z face absorbs what is left and
+       * emits at its temperature (Eq. 3 wall factor with eps = 1) */
+      const int f = (a == 0 ? 0 : 2) + (c[a] < 0 ? 0 : 1);
+      const double B_w = B_at(P, n, P->T_xz[f]);
+      const double tw = kap_i * (B_i - B_w) * tau;
+      X += tw;
+      absX += fabs(tw);
+      Xw += tw;
+      ++walls;
+      tau = 0.0;
+      break;
+    }
     if (a == 0) c[0] = (c[0] % N[0] + N[0]) % N[0]; /* periodic x */
     if (a == 2) c[2] = (c[2] % N[2] + N[2]) % N[2]; /* periodic z */
     if (a == 1 && (c[1] < 0 || c[1] >= N[1])) {

@@ -34,6 +34,11 @@ typedef struct {
    * grid (the channel DNS grids of Section 5), or NULL for uniform cells.  x and
    * z stay uniform. */
   const double *yf;
+  /* 0: x and z periodic (the channel); 1: black walls on the x = 0, x = lx,
+   * z = 0 and z = lz faces too, at temperatures T_xz[0..3] (the closed 3D
+   * boxes of the paper's verification cases 3 and 4, Table 1) */
+  int xz_walls;
+  double T_xz[4];
 } orc_problem;
 
 typedef struct {

@@ -45,6 +45,8 @@ class Grid:
     T_wall: tuple = (0.0, 0.0)     # temperature [K] of the walls at y=0 and y=ly
     reflect: int = 0               # 0 diffuse, 1 specular reflection at grey walls
     yf: object = None              # [ny + 1] wall-normal faces of a stretched grid, or None
+    xz_walls: int = 0              # 1: black walls on the x and z faces too (a closed box)
+    T_xz: tuple = (0.0, 0.0, 0.0, 0.0)  # their temperatures: x = 0, x = lx, z = 0, z = lz
 
     @property
     def ncells(self) -> int:
@@ -66,6 +68,20 @@ class Grid:
             return 0.5 * (f[:-1] + f[1:])
         dy = self.ly / self.ny
         return (np.arange(self.ny) + 0.5) * dy
+
+
+def sin_cube(n: int = 32, kappa: float = 0.5):
+    """The paper's grey verification cases 3 (kappa = 0.5 1/m) and 4 (kappa = 5):
+    a 1 m cube with cold black walls on all six faces and
+    T = (sin(pi x) sin(pi y) sin(pi z) pi / sigma)^(1/4) at the cell centres
+    (so sigma T^4 / pi = sin sin sin)."""
+    grid = Grid(n, n, n, 1.0, 1.0, 1.0, eps_wall=(1.0, 1.0), T_wall=(0.0, 0.0), xz_walls=1)
+    c = (np.arange(n) + 0.5) / n
+    s = np.sin(np.pi * c)
+    E = s[None, None, :] * s[None, :, None] * s[:, None, None]   # [z, y, x]
+    T = (E * np.pi / SIGMA_SB) ** 0.25
+    kd = make_grey_kdist(kappa, T_max=float(T.max()) * 1.05 + 1.0, nT=512)
+    return grid, kd, T, np.full(grid.shape, kd.x_ref)
 
 
 def channel_faces(ny: int, ly: float, gamma: float = 1.5) -> np.ndarray:

@@ -78,6 +78,10 @@ typedef struct {
   const double *yf;        /* host [ny + 1] wall-normal faces, strictly increasing,
                               yf[0] = 0 and yf[ny] = ly; copied by mcrt_create;
                               NULL: uniform ly / ny                              */
+  int xz_walls;            /* 0: x and z periodic (a channel); 1: a closed box
+                              with black walls on the x and z faces too (the
+                              paper's 3D verification cases 3 and 4, Table 1)   */
+  double T_xz[4];          /* [K] of the x = 0, x = lx, z = 0, z = lz walls     */
 } mcrt_grid_desc;
 
 /* Narrow-band correlated-k tables (Section 2.1, Eq. 16; Section 2.2: tabulated

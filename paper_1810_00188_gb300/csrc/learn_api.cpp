@@ -351,6 +351,8 @@ int mcrt_mlp_destroy(mcrt_mlp *m) {
 int mcrt_cell_features(mcrt_ctx *ctx, const int32_t *cells, int64_t n, float *out, void *stream) {
   if (!ctx) return MCRT_E_ARG;
   if (n < 0 || (n > 0 && !out)) return fail(ctx, MCRT_E_ARG, "bad arguments");
+  if (ctx->grid.xz_walls)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the features assume a channel (periodic x and z)");
   if (!cells && n > ncells_of(ctx)) return fail(ctx, MCRT_E_ARG, "n beyond the grid");
   const int rc = need_tables_and_fields(ctx);
   if (rc != MCRT_OK) return rc;
@@ -508,6 +510,8 @@ int mcrt_get_cell_proposal(mcrt_ctx *ctx, uint64_t *cn, uint64_t *cg, uint32_t *
 int mcrt_set_learned_proposal(mcrt_ctx *ctx, mcrt_mlp *m, float mix, void *stream) {
   if (!ctx) return MCRT_E_ARG;
   if (!m) return fail(ctx, MCRT_E_ARG, "null network");
+  if (ctx->grid.xz_walls)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the features assume a channel (periodic x and z)");
   if (!(mix > 0.f && mix <= 1.f)) return fail(ctx, MCRT_E_ARG, "mix outside (0, 1]");
   int rc = need_tables_and_fields(ctx);
   if (rc != MCRT_OK) return rc;

@@ -170,6 +170,9 @@ double proposal_T_max(const mcrt_ctx *ctx) {
   double Tm = ctx->T_max_field;
   for (int w = 0; w < 2; ++w)
     if (ctx->grid.eps_wall[w] > 0.0 && ctx->grid.T_wall[w] > Tm) Tm = ctx->grid.T_wall[w];
+  if (ctx->grid.xz_walls)
+    for (int f = 0; f < 4; ++f)
+      if (ctx->grid.T_xz[f] > Tm) Tm = ctx->grid.T_xz[f];
   return Tm;
 }
 
@@ -238,6 +241,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.reflect = g.reflect;
   a.yf64 = (const double *)ctx->yf64.p;
   a.yf32 = (const float *)ctx->yf32.p;
+  a.xz_walls = g.xz_walls;
   a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.field64 = (const double2 *)ctx->field64.p;
@@ -316,6 +320,10 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
     if (!(g->T_wall[w] >= 0.0) || !std::isfinite(g->T_wall[w])) return MCRT_E_ARG;
   }
   if (g->reflect != MCRT_REFLECT_DIFFUSE && g->reflect != MCRT_REFLECT_SPECULAR) return MCRT_E_ARG;
+  if (g->xz_walls != 0 && g->xz_walls != 1) return MCRT_E_ARG;
+  if (g->xz_walls)
+    for (int f = 0; f < 4; ++f)
+      if (!(g->T_xz[f] >= 0.0) || !std::isfinite(g->T_xz[f])) return MCRT_E_ARG;
   if (g->yf) {
     // stretched y: 0 = yf[0] < yf[1] < ... < yf[ny] = ly
     if (g->yf[0] != 0.0 || !(std::fabs(g->yf[g->ny] - g->ly) <= 1e-12 * g->ly)) return MCRT_E_ARG;
@@ -404,20 +412,21 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
       b64[r * nT + t] = make_double2(v, dv);
       b32[r * nT + t] = make_float2((float)v, (float)dv);
     }
-  std::vector<double> bw64(2 * (size_t)nb);
-  std::vector<float> bw32(2 * (size_t)nb);
-  for (int w = 0; w < 2; ++w)
+  // band intensity of the six faces: the y walls, then (closed boxes) x and z
+  std::vector<double> bw64(6 * (size_t)nb);
+  std::vector<float> bw32(6 * (size_t)nb);
+  for (int w = 0; w < 6; ++w)
     for (int n = 0; n < nb; ++n) {
-      bw64[w * nb + n] =
-          interp_host(kd->B + (size_t)n * nT, kd->T0, kd->dT, nT, ctx->grid.T_wall[w]);
+      const double Tw = w < 2 ? ctx->grid.T_wall[w] : ctx->grid.T_xz[w - 2];
+      bw64[w * nb + n] = interp_host(kd->B + (size_t)n * nT, kd->T0, kd->dT, nT, Tw);
       bw32[w * nb + n] = (float)bw64[w * nb + n];
     }
   CK(ensure(ctx->ktab64, nk * sizeof(double2)), "alloc kappa table");
   CK(ensure(ctx->ktab32, nk * sizeof(float2)), "alloc kappa table");
   CK(ensure(ctx->btab64, nbT * sizeof(double2)), "alloc B table");
   CK(ensure(ctx->btab32, nbT * sizeof(float2)), "alloc B table");
-  CK(ensure(ctx->bwall64, 2 * nb * sizeof(double)), "alloc wall B");
-  CK(ensure(ctx->bwall32, 2 * nb * sizeof(float)), "alloc wall B");
+  CK(ensure(ctx->bwall64, 6 * nb * sizeof(double)), "alloc wall B");
+  CK(ensure(ctx->bwall32, 6 * nb * sizeof(float)), "alloc wall B");
   CK(ensure(ctx->wg, ng * sizeof(double)), "alloc w_g");
   CK(ensure(ctx->cn, nb * sizeof(unsigned long long)), "alloc band counts");
   CK(ensure(ctx->cg, (size_t)nb * ng * sizeof(unsigned long long)), "alloc g counts");
@@ -427,8 +436,8 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
   CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab32.p, b32.data(), nbT * sizeof(float2), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 2 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
-  CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 2 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 6 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
+  CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 6 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->wg.p, kd->w_g, ng * sizeof(double), cudaMemcpyHostToDevice), "copy");
   // Planck-mean coefficients per node (features of the learned proposal)
   std::vector<float4> kp(2 * (size_t)nT);
@@ -853,6 +862,7 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.reflect = g.reflect;
   a.yf64 = (const double *)ctx->yf64.p;
   a.yf32 = (const float *)ctx->yf32.p;
+  a.xz_walls = g.xz_walls;
   a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
@@ -1043,6 +1053,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.reflect = g.reflect;
     a.yf64 = (const double *)c->yf64.p;
     a.yf32 = (const float *)c->yf32.p;
+    a.xz_walls = g.xz_walls;
     a.field32 = (const float2 *)c->field32.p;
     a.fpos32 = (const uint2 *)c->fpos32.p;
     a.ktab32 = (const float2 *)c->ktab32.p;
@@ -1095,6 +1106,8 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   // (and one reduction) over all their cells: warps claim runs of brick-ordered
   // positions of the concatenated snapshots, largest snapshot first.
   bool same_kdist = n <= mcrt::fp32_batch_max_snapshots();
+  for (int k = 0; k < n && same_kdist; ++k)
+    if (items[k].ctx->grid.xz_walls) same_kdist = false;  // closed boxes: per-snapshot kernels
   for (int k = 1; k < n && same_kdist; ++k) {
     const mcrt_ctx *c = items[k].ctx;
     same_kdist = c->nb == c0->nb && c->ng == c0->ng && c->nT == c0->nT && c->T0 == c0->T0 &&

@@ -40,6 +40,9 @@ struct TraceArgs {
   // stretched wall-normal grid: the ny + 1 faces (null: uniform dy)
   const double *yf64;
   const float *yf32;
+  // closed box: black walls on the x and z faces (bwall rows 2..5: x = 0,
+  // x = lx, z = 0, z = lz) instead of periodic x and z
+  int xz_walls;
   // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
   const float2 *field32;    // {T, x} per cell
   const uint2 *fpos32;      // FP32 kernel: {(node << 23) | fraction * 2^23, bits of x / x_ref}
@@ -48,7 +51,7 @@ struct TraceArgs {
   const double2 *ktab64;
   const float2 *btab32;     // [nb][nT] {B_t, B_{t+1} - B_t}
   const double2 *btab64;
-  const float *bwall32;     // [2][nb] wall band intensity
+  const float *bwall32;     // [6][nb] wall band intensity: y = 0, y = ly, x = 0, x = lx, z = 0, z = lz
   const double *bwall64;
   const double *w_g;        // [ng]
   const float *wgt32;       // [nb*ng] plain-proposal ray weight w_g / (p q), host FP64 -> FP32

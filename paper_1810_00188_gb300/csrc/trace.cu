@@ -346,6 +346,16 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
       }
       tprev = tn;
       const int nxyl = nxl * nyl;
+      if (a.xz_walls && ax != 1 && (ax == 0 ? (unsigned)(ix + sx) >= (unsigned)nxl
+                                             : (unsigned)(iz + sz) >= (unsigned)nzl)) {
+        // closed box: a black x or z wall absorbs the rest of the ray and emits
+        // at its temperature (Eq. 3 wall factor with eps = 1)
+        const int f = ax == 0 ? (ix + sx < 0 ? 2 : 3) : (iz + sz < 0 ? 4 : 5);
+        X += (B_i - __ldg(bwall + f * nb + n)) * tau;
+        tau = 0;
+        ++nwall;
+        break;
+      }
       if (ax == 0) {
         cntx += inc;
         tnx = fma(cntx, tsx, t0x);

@@ -368,7 +368,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           const int wz = iz >= nzl ? -nzl : (iz < 0 ? nzl : 0);
           iz += wz;
           lin += (unsigned)(wz * nxyl);
-          if (iy < 0 || iy >= nyl) {
+          if (a.xz_walls && (wx | wz)) {
+            // closed box: a black x or z wall absorbs the rest of the ray and
+            // emits at its temperature (Eq. 3 wall factor with eps = 1)
+            const int f = wx ? (wx > 0 ? 2 : 3) : (wz > 0 ? 4 : 5);
+            X += (B_i - __ldg(a.bwall32 + ((unsigned)(f * nb) + n))) * tau;
+            tau = 0.f;
+            ++tot_wall;
+            done = true;
+          } else if (iy < 0 || iy >= nyl) {
             // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
             const int wl = iy < 0 ? 0 : 1;
             const float eps = wl ? eps1 : eps0;

@@ -39,7 +39,7 @@ class mcrt_grid_desc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double),
                 ("ly", C.c_double), ("lz", C.c_double), ("eps_wall", C.c_double * 2),
                 ("T_wall", C.c_double * 2), ("reflect", C.c_int), ("device", C.c_int),
-                ("yf", C.POINTER(C.c_double))]
+                ("yf", C.POINTER(C.c_double)), ("xz_walls", C.c_int), ("T_xz", C.c_double * 4)]
 
 
 class mcrt_kdist_desc(C.Structure):
@@ -437,6 +437,9 @@ class Solver:
         self._yf_keep = None if yf is None else np.ascontiguousarray(yf, dtype=np.float64)
         if self._yf_keep is not None:
             g.yf = self._yf_keep.ctypes.data_as(C.POINTER(C.c_double))
+        g.xz_walls = int(getattr(grid, "xz_walls", 0))
+        for f, t in enumerate(getattr(grid, "T_xz", (0.0, 0.0, 0.0, 0.0))):
+            g.T_xz[f] = float(t)
         self.grid = grid
         self.device = device
         self.ctx = mcrt_create(g)

@@ -233,6 +233,44 @@ def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):
     return out
 
 
+def spectral_extra(S, T, params, q, s, sp, rays=256, reps=3):
+    """Spectral proposals on the benchmark field: Zhang's T_max pdf (the
+    paper's, Eq. 13), the classic ERMC pdf at each cell's own temperature, and
+    their temperature-weighted mix.  For each: kernel time, p95 relative sigma
+    over cells, median relative sigma in the coldest and hottest tenths of the
+    cells, and the projected GPU time to 1% p95 relative sigma."""
+    import numpy as np
+
+    from paper_1810_00188_gb300 import mcrt
+    Tf = np.asarray(T).reshape(-1)
+    cold = Tf <= np.percentile(Tf, 10)
+    hot = Tf >= np.percentile(Tf, 90)
+    out = {"rays_per_cell": rays}
+    for name, mode in (("T_max", None), ("local", mcrt.MCRT_SPECTRAL_LOCAL),
+                       ("hybrid", mcrt.MCRT_SPECTRAL_HYBRID)):
+        prop = mcrt.MCRT_PROPOSAL_PLANCK_TMAX
+        if mode is not None:
+            S.set_spectral_proposal(mode, stream=sp)
+            prop = mcrt.MCRT_PROPOSAL_CELL
+        ts, p95, rc, rh = [], [], [], []
+        for k in range(reps):
+            pk = params(k, rays=rays)
+            pk.proposal = prop
+            S.solve_into(pk, q, s, stream=sp)
+            ts.append(S.stats()["kernel_ms"])
+            qn, sn = q.cpu().numpy().reshape(-1), s.cpu().numpy().reshape(-1)
+            rel = sn / np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
+            p95.append(float(np.percentile(rel, 95)))
+            rc.append(float(np.median(rel[cold])))
+            rh.append(float(np.median(rel[hot])))
+        t, pr = statistics.median(ts), statistics.median(p95)
+        out[name] = {"kernel_ms": t, "p95_rel_sigma": pr, "cold_median_rel_sigma": statistics.median(rc),
+                     "hot_median_rel_sigma": statistics.median(rh), "ms_to_1pct": t * (pr / 0.01) ** 2}
+    for name in ("local", "hybrid"):
+        out[name]["speedup_vs_T_max"] = out["T_max"]["ms_to_1pct"] / out[name]["ms_to_1pct"]
+    return out
+
+
 def learned_extra(sp, n_train=200, train_grid=64, eval_grid=128, rays_tally=512, rays_eval=256,
                   steps=1500, seed=0):
     """Learned proposal: tallies of `n_train` seeded 64^3 fields, training on the
@@ -461,6 +499,7 @@ def main():
                 sol["value"] = value / (steps_per_launch / a.rays * nstar)
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
             result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
+            result["spectral_proposals"] = spectral_extra(S, T, params, q, s, sp)
             result["learned_vs_plain"] = learned_extra(sp)
             if world == 1:
                 result["batched_snapshots"] = batch_extra(sp)

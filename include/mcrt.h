@@ -394,6 +394,18 @@ int mcrt_get_plain_probs(mcrt_ctx *ctx, float *p0);
  * weight; hemisphere count round(q_up 2^23) in [1, 2^23 - 1].  Synchronous.
  * Errors: MCRT_E_ARG (a row without positive weight), MCRT_E_STATE. */
 int mcrt_set_cell_proposal_probs(mcrt_ctx *ctx, const float *q, void *cuda_stream);
+/* Spectral proposals at each cell's own temperature (the classic ERMC draw,
+ * Section 2: the paper replaces it by Zhang's T_max proposal, Eq. 13, because
+ * its variance is large in cold cells).  MCRT_SPECTRAL_LOCAL: p_c(n,g) ~
+ * w_g B_n(T_i) kappa_(n,g)(T_i), the emission spectrum of cell i.
+ * MCRT_SPECTRAL_HYBRID: (1 - lam) p0 + lam p_local with p0 the T_max proposal
+ * and lam = (T_i - T_min) / (T_max - T_min) clamped to [0, 1] (the cold cells
+ * draw like the paper, the hottest ones like the classic ERMC).  Hemispheres
+ * 1/2 each.  Quantised like mcrt_set_cell_proposal_probs (so every estimate
+ * stays unbiased); later solves use it with MCRT_PROPOSAL_CELL.  Synchronous.
+ * Errors: MCRT_E_ARG (bad mode), MCRT_E_STATE. */
+enum { MCRT_SPECTRAL_LOCAL = 0, MCRT_SPECTRAL_HYBRID = 1 };
+int mcrt_set_spectral_proposal(mcrt_ctx *ctx, int mode, void *cuda_stream);
 /* Copies the current cell proposal to host arrays cn [ncells][nb],
  * cg [ncells][nb][ng], hemi [ncells].  Synchronous. */
 int mcrt_get_cell_proposal(mcrt_ctx *ctx, uint64_t *cn, uint64_t *cg, uint32_t *hemi);

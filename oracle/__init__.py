@@ -113,6 +113,8 @@ def lib():
                                    C.c_double, C.c_int]
             L.orc_learned_counts.argtypes = [dp, C.c_int, C.c_int, C.c_double, up, up,
                                              C.POINTER(C.c_uint32)]
+            L.orc_spectral_proposal.argtypes = [C.POINTER(Problem), C.c_int, C.c_double, C.c_double,
+                                                dp, C.POINTER(C.c_int32), i64, dp]
             _lib = L
     return _lib
 
@@ -449,3 +451,23 @@ def learned_counts(q, nb, ng, q_up):
     if rc != 0:
         raise ValueError("orc_learned_counts failed")
     return cn, cg.reshape(nb, ng), hemi.value
+
+
+def spectral_proposal(grid, kd, T, x=None, mode=0, cells=None):
+    """Per-cell spectral probabilities [n, K] at the cells' own temperatures:
+    mode 0 the local emission spectrum, 1 mixed with the T_max proposal by
+    lam = (T_i - T_min) / (T_max - T_min)."""
+    cn, cg, T_max = plain_proposal(grid, kd, T, x)
+    nb, ng = kd.n_bands, kd.n_g
+    c = np.diff(np.concatenate([[0], cn.astype(np.float64)])) * 2.0**-32
+    g = np.diff(np.concatenate([np.zeros((nb, 1)), cg.astype(np.float64)], axis=1), axis=1) * 2.0**-32
+    p0 = np.ascontiguousarray((c[:, None] * g).reshape(-1))
+    P = make_problem(grid, kd, T, x)
+    cells = np.arange(grid.ncells, dtype=np.int32) if cells is None else np.asarray(cells)
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    q = np.zeros((cells.size, nb * ng))
+    Tf = np.asarray(T, dtype=np.float64).reshape(-1)
+    lib().orc_spectral_proposal(C.byref(P), int(mode), float(Tf.min()), float(T_max), _dp(p0),
+                                cells.ctypes.data_as(C.POINTER(C.c_int32)), cells.size, _dp(q))
+    return q
+

@@ -424,3 +424,36 @@ int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *c
   free(u);
   return rc;
 }
+
+/* ---- spectral proposals at each cell's own temperature ---------------------
+ * The classic ERMC draw (Section 2; the paper replaces it by Zhang's T_max pdf,
+ * Eq. 13): per cell p(n,g) ~ w_g B_n(T_i) kappa_(n,g)(T_i) (mode 0), or the
+ * temperature-weighted mix (1 - lam) p0 + lam p_local with
+ * lam = (T_i - T_min) / (T_max - T_min) clamped to [0, 1] (mode 1).  q_out:
+ * [n][K] probabilities in FP64. */
+int orc_spectral_proposal(const orc_problem *P, int mode, double T_min, double T_max,
+                          const double *p0, const int32_t *cells, int64_t n, double *q_out) {
+  const int nb = P->n_bands, ng = P->n_g, K = nb * ng;
+  for (int64_t q = 0; q < n; ++q) {
+    const double T = P->T[cells[q]];
+    double *qc = q_out + q * K, W = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const double B = orc_interp(P->B + (size_t)b * P->nT, P->T0, P->dT, P->nT, T);
+      for (int g = 0; g < ng; ++g) {
+        const double k = orc_interp(P->kappa + ((size_t)b * ng + g) * P->nT, P->T0, P->dT, P->nT, T);
+        const double v = P->w_g[g] * B * k;
+        qc[b * ng + g] = v > 0.0 ? v : 0.0;
+        W += qc[b * ng + g];
+      }
+    }
+    double lam = 1.0;
+    if (mode == 1) {
+      lam = T_max > T_min ? (T - T_min) / (T_max - T_min) : 1.0;
+      lam = lam < 0.0 ? 0.0 : (lam > 1.0 ? 1.0 : lam);
+    }
+    if (!(W > 0.0)) lam = 0.0;
+    for (int k = 0; k < K; ++k) qc[k] = (1.0 - lam) * p0[k] + (W > 0.0 ? lam * qc[k] / W : 0.0);
+  }
+  return 0;
+}
+

@@ -140,6 +140,8 @@ void orc_adam(double *theta, const double *grad, double *m1, double *m2, int64_t
               double beta1, double beta2, double eps, int t);
 int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *cn,
                        uint64_t *cg, uint32_t *hemi);
+int orc_spectral_proposal(const orc_problem *P, int mode, double T_min, double T_max,
+                          const double *p0, const int32_t *cells, int64_t n, double *q_out);
 
 int orc_quadrature(const orc_problem *P, const double *mu, const double *mu_w, int nmu,
                    int nphi, const double *vn, const double *vw, int nv, int origin,

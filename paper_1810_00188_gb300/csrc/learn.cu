@@ -352,6 +352,58 @@ __global__ void __launch_bounds__(NTHR) quantize_cells_kernel(const float *q, lo
   }
 }
 
+// ---- spectral proposals at each cell's own temperature ---------------------------
+// The paper's estimator draws (n, g) from the emission spectrum at T_max
+// (Zhang's proposal, Eq. 13 discretised as Eq. 16) because the classic ERMC
+// draw, from the emitting cell's own spectrum kappa_(n,g)(T_i) B_n(T_i), has a
+// large variance in cold cells (Section 2).  Per cell (one warp):
+//   local:  p_c(n,g) ~ w_g B_n(T_i) kappa_(n,g)(T_i)          (x_i cancels)
+//   hybrid: (1 - lam) p0(n,g) + lam p_local, lam = (T_i - T_min) / (T_max - T_min)
+// with p0 the T_max proposal; both quantised like any cell proposal (the ray
+// weight divides by the quantised probability, so the estimate stays unbiased),
+// hemispheres 1/2 each.
+__global__ void __launch_bounds__(NTHR) spectral_proposal_kernel(const SpectralArgs a) {
+  extern __shared__ double ssm[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int K = a.nb * a.ng;
+  double *wn = ssm + (size_t)w * a.nb;
+  float *qw = reinterpret_cast<float *>(ssm + (size_t)(NTHR / 32) * a.nb) + (size_t)w * K;
+  for (long long c = (long long)blockIdx.x * (NTHR / 32) + w; c < a.n;
+       c += (long long)gridDim.x * (NTHR / 32)) {
+    const uint2 pk = a.fpos32[c];
+    const unsigned it = pk.x >> 23;
+    const float fr = __uint_as_float(0x3F800000u | (pk.x & 0x7FFFFFu)) - 1.f;
+    const double T = a.field64[c].x;
+    double lam = 1.0;
+    if (a.mode == 1) {
+      lam = a.T_max > a.T_min ? (T - a.T_min) / (a.T_max - a.T_min) : 1.0;
+      lam = fmin(fmax(lam, 0.0), 1.0);
+    }
+    // the local weights and their sum (lane-strided, then a fixed-order warp sum)
+    double part = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      const int n = k / a.ng, g = k - n * a.ng;
+      const float2 kk = a.ktab32[(size_t)k * a.nT + it];
+      const float2 bb = a.btab32[(size_t)n * a.nT + it];
+      const float v = a.w_g32[g] * fmaf(fr, bb.y, bb.x) * fmaf(fr, kk.y, kk.x);
+      qw[k] = v > 0.f ? v : 0.f;
+      part += (double)qw[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncwarp();
+    if (a.mode == 1 || !(part > 0.0)) {
+      // hybrid (or a cell whose own spectrum is empty: the T_max proposal)
+      const double l = part > 0.0 ? lam : 0.0;
+      for (int k = lane; k < K; k += 32)
+        qw[k] = (float)((1.0 - l) * (double)a.p0[k] + (part > 0.0 ? l * (double)qw[k] / part : 0.0));
+      __syncwarp();
+    }
+    quantize_cell(qw, 0.5f, a.nb, a.ng, wn, a.cell_cn + c * a.nb, a.cell_cg + c * (long long)K,
+                  a.cell_hemi + c, a.err);
+  }
+}
+
 // ---- network: shared-memory weights ------------------------------------------------
 // W1T [12][64], W2T [64][64] (input-major, for the forward pass), W3T [64][LDO]
 // with LDO an odd number of 32-bit words so that both the forward pass (lanes
@@ -905,6 +957,16 @@ cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
   if (e != cudaSuccess) return e;
   quantize_cells_kernel<<<grid_for(n, NTHR / 32, 4), NTHR, smem, s>>>(q, n, nb, ng, cell_cn, cell_cg,
                                                                        cell_hemi, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectral_proposal(const SpectralArgs &a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(NTHR / 32) * (a.nb * sizeof(double) + (size_t)a.nb * a.ng * sizeof(float));
+  cudaError_t e = cudaFuncSetAttribute(spectral_proposal_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  spectral_proposal_kernel<<<grid_for(a.n, NTHR / 32, 4), NTHR, smem, s>>>(a);
   return cudaGetLastError();
 }
 

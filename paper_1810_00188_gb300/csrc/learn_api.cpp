@@ -493,6 +493,48 @@ int mcrt_set_cell_proposal_probs(mcrt_ctx *ctx, const float *q, void *stream) {
   return MCRT_OK;
 }
 
+int mcrt_set_spectral_proposal(mcrt_ctx *ctx, int mode, void *stream) {
+  if (!ctx) return MCRT_E_ARG;
+  if (mode != MCRT_SPECTRAL_LOCAL && mode != MCRT_SPECTRAL_HYBRID) return fail(ctx, MCRT_E_ARG, "bad mode");
+  int rc = need_tables_and_fields(ctx);
+  if (rc != MCRT_OK) return rc;
+  DeviceGuard dg(ctx->grid.device);
+  if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = ensure_plain_proposal(ctx, s);  // p0 of the hybrid
+  if (rc != MCRT_OK) return rc;
+  ctx->have_cell_prop = false;
+  rc = ensure_cell_buffers(ctx);
+  if (rc == MCRT_OK) rc = clear_lerr(ctx, s);
+  if (rc != MCRT_OK) return rc;
+  mcrt::SpectralArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = ncells_of(ctx);
+  a.nb = ctx->nb;
+  a.ng = ctx->ng;
+  a.nT = ctx->nT;
+  a.mode = mode;
+  a.T_min = ctx->T_min_field;
+  a.T_max = proposal_T_max(ctx);
+  a.fpos32 = (const uint2 *)ctx->fpos32.p;
+  a.field64 = (const double2 *)ctx->field64.p;
+  a.ktab32 = (const float2 *)ctx->ktab32.p;
+  a.btab32 = (const float2 *)ctx->btab32.p;
+  a.w_g32 = (const float *)ctx->wg32.p;
+  a.p0 = (const float *)ctx->p0_32.p;
+  a.cell_cn = (unsigned long long *)ctx->cell_cn.p;
+  a.cell_cg = (unsigned long long *)ctx->cell_cg.p;
+  a.cell_hemi = (unsigned *)ctx->cell_hemi.p;
+  a.err = (unsigned long long *)ctx->lerr.p;
+  CK(mcrt::launch_spectral_proposal(a, s), "spectral proposal");
+  unsigned long long flag = 0;
+  rc = read_lerr(ctx, s, &flag);
+  if (rc != MCRT_OK) return rc;
+  if (flag) return fail(ctx, MCRT_E_ARG, "a cell without positive spectral weight");
+  ctx->have_cell_prop = true;
+  return MCRT_OK;
+}
+
 int mcrt_get_cell_proposal(mcrt_ctx *ctx, uint64_t *cn, uint64_t *cg, uint32_t *hemi) {
   if (!ctx) return MCRT_E_ARG;
   if (!cn || !cg || !hemi) return fail(ctx, MCRT_E_ARG, "null output");

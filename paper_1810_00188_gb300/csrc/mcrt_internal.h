@@ -210,6 +210,22 @@ cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t s);
 
 // Quantises per-cell probabilities q [n][K+2] (spectral points, then q_up) into
 // cumulative counts (same rule as the host's plain proposal).
+// Per-cell spectral proposals at the cells' own temperatures (learn.cu):
+// mode 0 the local emission spectrum, 1 the temperature-weighted mix with the
+// T_max proposal p0.
+struct SpectralArgs {
+  long long n;
+  int nb, ng, nT, mode;
+  double T_min, T_max;
+  const uint2 *fpos32;
+  const double2 *field64;
+  const float2 *ktab32, *btab32;
+  const float *w_g32, *p0;
+  unsigned long long *cell_cn, *cell_cg;
+  unsigned *cell_hemi;
+  unsigned long long *err;
+};
+cudaError_t launch_spectral_proposal(const SpectralArgs &a, cudaStream_t s);
 cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
                                   unsigned long long *cell_cn, unsigned long long *cell_cg,
                                   unsigned *cell_hemi, unsigned long long *err, cudaStream_t s);

@@ -84,7 +84,8 @@ EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_pr
            "mcrt_mlp_get_params", "mcrt_mlp_forward", "mcrt_mlp_loss_grad", "mcrt_mlp_adam_step",
            "mcrt_mlp_last_loss", "mcrt_mlp_last_error", "mcrt_mlp_destroy", "mcrt_cell_features",
            "mcrt_tally_moments", "mcrt_get_plain_probs", "mcrt_set_cell_proposal_probs",
-           "mcrt_get_cell_proposal", "mcrt_set_learned_proposal", "mcrt_multigrid_levels")
+           "mcrt_get_cell_proposal", "mcrt_set_learned_proposal", "mcrt_multigrid_levels",
+           "mcrt_set_spectral_proposal")
 _NOT_INT = ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error", "mcrt_mlp_last_error",
             "mcrt_mlp_nparams")
 MCRT_NFEAT, MCRT_NHIDDEN = 12, 64
@@ -151,6 +152,7 @@ def load(build_if_missing: bool = True):
         L.mcrt_get_cell_proposal.argtypes = [vp, vp, vp, vp]
         L.mcrt_set_learned_proposal.argtypes = [vp, vp, f32, vp]
         L.mcrt_multigrid_levels.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.mcrt_set_spectral_proposal.argtypes = [vp, C.c_int, vp]
         for f in EXPORTS:
             if f not in _NOT_INT:
                 getattr(L, f).restype = C.c_int
@@ -350,6 +352,13 @@ def mcrt_get_cell_proposal(ctx, ncells: int, nb: int, ng: int):
     hemi = np.zeros(ncells, dtype=np.uint32)
     _check(load().mcrt_get_cell_proposal(ctx, _ptr(cn), _ptr(cg), _ptr(hemi)), ctx)
     return cn, cg, hemi
+
+
+MCRT_SPECTRAL_LOCAL, MCRT_SPECTRAL_HYBRID = 0, 1
+
+
+def mcrt_set_spectral_proposal(ctx, mode: int, stream=0):
+    _check(load().mcrt_set_spectral_proposal(ctx, mode, stream), ctx)
 
 
 def mcrt_set_learned_proposal(ctx, m, mix: float = 0.1, stream=0):
@@ -573,6 +582,11 @@ class Solver:
 
     def cell_proposal(self):
         return mcrt_get_cell_proposal(self.ctx, self.grid.ncells, self.kd.n_bands, self.kd.n_g)
+
+    def set_spectral_proposal(self, mode, stream: int = 0):
+        """Per-cell spectral proposal at the cells' own temperatures (LOCAL) or
+        mixed with the T_max proposal by temperature (HYBRID)."""
+        mcrt_set_spectral_proposal(self.ctx, mode, stream)
 
     def set_learned_proposal(self, mlp, mix=0.1, stream: int = 0):
         mcrt_set_learned_proposal(self.ctx, mlp.handle, mix, stream)

@@ -237,16 +237,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           // direction: hemisphere of the y axis by the integer count `hemi` of
           // 2^23, mu uniform inside it (plain: mu = 1 - 2 U); phi = 2 pi R_phi
           const unsigned m0 = u.x >> 9;
-          float mu, ph;
-          if (m0 < hemi) {
-            const float h = u23_to_float(hemi);
-            mu = 1.f - (u23_to_float(m0) + 0.5f) * __frcp_rn(h);
-            ph = h * 1.1920928955078125e-07f;
-          } else {
-            const float h = u23_to_float(8388608u - hemi);
-            mu = -((u23_to_float(m0 - hemi) + 0.5f) * __frcp_rn(h));
-            ph = h * 1.1920928955078125e-07f;
-          }
+          // branch-free: the plain proposal's hemisphere count is 2^22, whose
+          // reciprocal is exact
+          const bool up = m0 < hemi;
+          const float h = u23_to_float(up ? hemi : 8388608u - hemi);
+          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) *
+                           (plain ? 2.384185791015625e-07f : __frcp_rn(h));
+          const float mu = up ? 1.f - mt : -mt;
+          const float ph = h * 1.1920928955078125e-07f;
           if (plain) {
             wgt = __ldg(wgt_b + nn * ng + gg);
           } else {
@@ -259,7 +257,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
             wgt = __fdividef(__ldg(a.w_g32 + gg), p) * __fdividef(6.2831855f, ph);
           }
           float sphi, cphi;
-          sincospi_02(2.f * unif(u.y), sphi, cphi);
+          sincos_2pi(unif(u.y), sphi, cphi);
           const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
           float fx = 0.5f, fy = 0.5f, fz = 0.5f;
           if (a.origin == 0) {
@@ -457,7 +455,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
                                          a.key0, a.key1);
                 const float mr = sqrtf(unif(v.x));
                 float sp, cp;
-                sincospi_02(2.f * unif(v.y), sp, cp);
+                sincos_2pi(unif(v.y), sp, cp);
                 const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
                 ddx = sr * cp;
                 ddy = wl == 0 ? mr : -mr;

@@ -58,6 +58,16 @@ __device__ __forceinline__ void tpos(unsigned packed, unsigned &it, float &fr) {
 // sin(pi x), cos(pi x) for x in [0, 2]: x = k/2 + r with k the nearest integer of
 // 2x and |r| <= 1/4 (both exact), then Taylor series of sin and cos at pi r
 // (truncation below 2e-9 relative) rotated by the quadrant k.
+// sin(2 pi u), cos(2 pi u) for u in (0, 1) with the hardware approximations
+// (absolute error about 4e-7): the angle is reduced to 2 pi (u - 1/2) in
+// (-pi, pi), the range where __sincosf is accurate, and both signs flip back.
+__device__ __forceinline__ void sincos_2pi(float u, float &s, float &c) {
+  float s0, c0;
+  __sincosf(6.28318530717958647f * (u - 0.5f), &s0, &c0);
+  s = -s0;
+  c = -c0;
+}
+
 __device__ __forceinline__ void sincospi_02(float x, float &s, float &c) {
   const float kf = __fadd_rn(2.f * x, 12582912.f);
   const int k = __float_as_int(kf) - 0x4B400000;

@@ -193,16 +193,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           // direction: hemisphere of the y axis by the integer count `hemi` of
           // 2^23, mu uniform inside it (plain: mu = 1 - 2 U); phi = 2 pi R_phi
           const unsigned m0 = u.x >> 9;
-          float mu, ph;
-          if (m0 < hemi) {
-            const float h = u23_to_float(hemi);
-            mu = 1.f - (u23_to_float(m0) + 0.5f) * __frcp_rn(h);
-            ph = h * 1.1920928955078125e-07f;
-          } else {
-            const float h = u23_to_float(8388608u - hemi);
-            mu = -((u23_to_float(m0 - hemi) + 0.5f) * __frcp_rn(h));
-            ph = h * 1.1920928955078125e-07f;
-          }
+          // branch-free: the plain proposal's hemisphere count is 2^22, whose
+          // reciprocal is exact
+          const bool up = m0 < hemi;
+          const float h = u23_to_float(up ? hemi : 8388608u - hemi);
+          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) *
+                           (plain ? 2.384185791015625e-07f : __frcp_rn(h));
+          const float mu = up ? 1.f - mt : -mt;
+          const float ph = h * 1.1920928955078125e-07f;
           if (plain) {
             wgt = __ldg(a.wgt32 + nn * ng + gg);
           } else {
@@ -215,7 +213,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             wgt = __fdividef(__ldg(a.w_g32 + gg), p) * __fdividef(6.2831855f, ph);
           }
           float sphi, cphi;
-          sincospi_02(2.f * unif(u.y), sphi, cphi);
+          sincos_2pi(unif(u.y), sphi, cphi);
           const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
           float fx = 0.5f, fy = 0.5f, fz = 0.5f;
           if (a.origin == 0) {
@@ -419,7 +417,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
                 const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
                 const float mr = sqrtf(unif(v.x));
                 float sp, cp;
-                sincospi_02(2.f * unif(v.y), sp, cp);
+                sincos_2pi(unif(v.y), sp, cp);
                 const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
                 ddx = sr * cp;
                 ddy = wl == 0 ? mr : -mr;

@@ -7,6 +7,9 @@ correlated-k tables, black walls at 500 / 1000 K, 1000 rays per cell, FP32
 traversal with FP64 tallies.  Each step traces a fresh block of ray indices
 (ray_offset advances), so no result is reused.  Under torchrun every rank solves
 its own snapshot (field seed = rank): weak scaling with no data-path collective.
+``--scaling strong`` instead splits one snapshot into z-slabs: the field is
+broadcast once before timing, and every timed step solves each rank's slab and
+gathers Q and sigma on rank 0.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores on bounded samples of the same workload instead.
@@ -37,6 +40,7 @@ OPS_PER_STEP = 44             # axis choice, table position, two interpolations,
 OPS_PER_RAY = 260             # 2 Philox4x32-10 blocks (2 x 80), sampling, direction,
                               # origin, DDA set-up, sample store
 GATHER_BYTES_PER_STEP = 8     # FP32 {T, x} of the traversed cell
+GATHERS_PER_STEP = 3          # 8-byte loads per step: {T, x}, the kappa node pair, the B node pair
 
 
 def parse():
@@ -49,6 +53,8 @@ def parse():
     ap.add_argument("--rays", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: one snapshot per rank; strong: one snapshot split over the ranks")
     return ap.parse_args()
 
 
@@ -120,6 +126,20 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def ceilings(device, field_bytes):
+    """Measured rates of the two operations a march step repeats: the exponential
+    and a random 8-byte gather (library probes, one timed launch each)."""
+    from paper_1810_00188_gb300 import mcrt
+    ex2, mhz = mcrt.mcrt_probe_ex2(device)
+    sizes = {"field": 1 << max(12, int(field_bytes - 1).bit_length()), "32MiB": 32 << 20,
+             "4GiB": 4 << 30}
+    g = {k: mcrt.mcrt_probe_gather(device, v) for k, v in sizes.items()}
+    return {"ex2_per_s": ex2, "ex2_per_clk_per_sm": ex2 / (N_SM * mhz * 1e6), "probe_sm_mhz": mhz,
+            "gather8_per_s": g, "gather_buffer_bytes": sizes,
+            "note": "random 8-byte loads, 8 in flight per thread, full occupancy; "
+                    "ex2.approx chains, 8 per thread"}
 
 
 def cpu_baseline(a, target_s=12.0):
@@ -379,20 +399,30 @@ def main():
             dist.barrier()
 
 
-    grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=rank)
+    strong = a.scaling == "strong" and world > 1
+    snap = 0 if a.scaling == "strong" else rank
+    grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=snap)
     S = mcrt.Solver(grid, kd, device=local)
     Td = torch.tensor(T, device="cuda")
     xd = torch.tensor(x, device="cuda")
+    boxes = pdist.shard_boxes(grid.nx, grid.ny, grid.nz, world)
+    box = boxes[rank] if strong else None
+    if strong:
+        if rank != 0:
+            Td.zero_()
+            xd.zero_()
+        pdist.broadcast_fields(Td, xd, src=0)  # rank 0's field on every rank
     S.set_fields(Td, xd)
-    q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+    q = torch.empty(S.box_shape(box), dtype=torch.float64, device="cuda")
     s = torch.empty_like(q)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
     def params(k, prec=mcrt.MCRT_FP32, rays=a.rays, mg_levels=1, mg_steps=5):
-        return S.params(rays=rays, seed=0, snapshot=rank, ray_offset=k * rays, tol=1e-4,
-                        max_steps=1 << 20, precision=prec, mg_levels=mg_levels, mg_steps=mg_steps)
+        return S.params(rays=rays, seed=0, snapshot=snap, ray_offset=k * rays, tol=1e-4,
+                        max_steps=1 << 20, precision=prec, mg_levels=mg_levels, mg_steps=mg_steps,
+                        box=box)
 
     for k in range(a.warmup):
         S.solve_into(params(k), q, s, stream=sp)
@@ -408,6 +438,8 @@ def main():
         flush.zero_()
         ev[k][0].record(stream)
         S.solve_into(params(a.warmup + k), q, s, stream=sp)
+        if strong:
+            pdist.gather_slabs([q, s], boxes, grid.shape, dst=0)
         ev[k][1].record(stream)
         st = S.stats()  # waits for this solve
         steps_total += st["steps"]
@@ -421,7 +453,7 @@ def main():
     t_local = sum(step_ms) / 1e3
     steps_all, t_max = pdist.aggregate(float(steps_total), t_local, device="cuda")
     value = steps_all / t_max
-    rays_all = float(world * a.steps) * grid.ncells * a.rays
+    rays_all = float((1 if strong else world) * a.steps) * grid.ncells * a.rays
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -430,7 +462,8 @@ def main():
     alu_peak = N_SM * LANES_PER_SM * f_clk              # op/s
     kernel_s = statistics.mean(kern_ms) / 1e3          # the solve's launches, library events
     steps_per_launch = steps_total / a.steps
-    rays_per_launch = grid.ncells * a.rays
+    bs = S.box_shape(box)
+    rays_per_launch = bs[0] * bs[1] * bs[2] * a.rays
     steps_rate = steps_per_launch / kernel_s
     ops = OPS_PER_STEP * steps_per_launch + OPS_PER_RAY * rays_per_launch
     achieved = ops / kernel_s
@@ -440,10 +473,10 @@ def main():
     if rank == 0:
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                   "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps,
-                  "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                  "higher_is_better": True, "scaling": a.scaling, "vs_baseline": None,
                   "dtype": "f32", "data": "synthetic", "config": workload_config(a),
                   "rays_per_s": rays_all / t_max,
-                  "steps_per_ray": steps_total / (a.steps * grid.ncells * a.rays),
+                  "steps_per_ray": steps_total / (a.steps * rays_per_launch),
                   "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                                "unit": "Top/s", "frac": achieved / alu_peak, "traffic": None,
                                "peak_basis": f"FP32/INT issue: {N_SM} SM x {LANES_PER_SM} lanes x "
@@ -456,11 +489,14 @@ def main():
                   "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
                               "max": max(step_ms)},
                   "gpu_launches": launches, "clocks": clk}
+        result["config"]["parallelism"] = (
+            f"strong: one snapshot in {world} z-slabs, field broadcast once, Q/sigma gathered each step"
+            if strong else f"weak: one snapshot per rank ({world}), no data-path collective")
     # --- extras on rank 0: e2e through host buffers, FP64, solves/s at 1% sigma
     if rank == 0:
         Tp = torch.tensor(T).pin_memory()
         xp = torch.tensor(x).pin_memory()
-        qh = torch.empty(grid.shape, dtype=torch.float64).pin_memory()
+        qh = torch.empty(S.box_shape(box), dtype=torch.float64).pin_memory()
         sh = torch.empty_like(qh).pin_memory()
         ke = max(1, min(a.steps, 5))
         torch.cuda.synchronize()
@@ -471,9 +507,16 @@ def main():
             e_steps += S.stats()["steps"]
         te = time.perf_counter() - t0
         result["e2e"] = {"value": e_steps / te, "unit": UNIT,
+                         "scope": "rank 0's slab" if strong else "rank 0's snapshot",
                          "h2d_bytes_per_step": int(Tp.numel() * 8 + xp.numel() * 8),
                          "d2h_bytes_per_step": int(qh.numel() * 8 + sh.numel() * 8)}
-        if not a.no_extras:
+        if not a.no_extras and not strong:
+            c = ceilings(local, grid.ncells * 8)
+            result["ceilings"] = c
+            rf = result["roofline"]
+            rf["exp_frac_of_measured_ex2"] = steps_rate / c["ex2_per_s"]
+            rf["gather_frac_of_measured_field_gather"] = (steps_rate * GATHERS_PER_STEP
+                                                          / c["gather8_per_s"]["field"])
             S.set_fields(Td, xd)
             # FP64 traversal throughput on a tenth of the rays
             r64 = max(32, a.rays // 10)

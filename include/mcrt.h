@@ -135,12 +135,32 @@ typedef struct {
   double T_max;            /* temperature of the plain proposal (Eq. 13)          */
   float kernel_ms;         /* device time of the last solve's trace launch        */
   int launches;            /* kernels the last solve launched                     */
+  uint64_t long_rays;      /* FP32: rays finished by the warp-parallel march      */
+  uint64_t long_overflow;  /* FP32: long rays that found the hand-off buffer full
+                              and were finished where they started (see
+                              mcrt_tuning); 0 in every solve whose results are
+                              bitwise independent of the launch shape            */
 } mcrt_solve_stats;
 
 /* Launch shape of the FP32 trace kernel.  The paper sizes its launches so that
  * "the GPU resources are fully utilized" (Section 3); here the choice is left to
- * an autotuner.  Q, sigma and the step counts do not depend on these settings:
- * every cell's samples are reduced in a fixed order. */
+ * an autotuner.  Q, sigma and the step counts do not depend on the launch shape
+ * (CTAs per SM, steps per round, scratch): every cell's samples are reduced in a
+ * fixed order.
+ *
+ * Long rays.  A ray of an optically thin band that runs nearly parallel to the
+ * walls crosses up to ~10^5 cells of the periodic directions, one dependent
+ * gather after another; the solve cannot end before its last step.  The FP32
+ * exact march therefore hands such a ray off: when it has marched
+ * long_ray_steps segments (or reflects off a wall after that) and at least
+ * long_ray_flight x/z face crossings remain before its next y face, its state
+ * moves to a device buffer, and a second kernel finishes it with a whole warp,
+ * the 32 lanes marching consecutive pieces of the flight at once and combining
+ * them with a product scan of the transmissivities.  The estimate is the same
+ * path integral (Eqs. 2, 3, 14) in another summation order.  These two
+ * thresholds are part of the estimator's arithmetic: results are bitwise
+ * reproducible for fixed thresholds (unless the hand-off buffer overflows,
+ * which mcrt_get_stats reports). */
 typedef struct {
   int min_blocks_per_sm;   /* 0: default (3); 1..4 CTAs of 256 threads per SM,
                               trading registers per thread against occupancy */
@@ -148,6 +168,10 @@ typedef struct {
                               between refills of idle lanes                      */
   int scratch_mib;         /* 0: default (1024); cap of the per-ray sample
                               scratch; larger solves run in several chunks      */
+  int long_ray_steps;      /* 0: default (1024); > 0: hand-off threshold in
+                              segments; < 0: never hand off                     */
+  int long_ray_flight;     /* 0: default (32); > 0: x/z crossings left in the
+                              flight for a hand-off; < 0: any flight            */
 } mcrt_tuning;
 
 /* Number of overlaid grids the multigrid march can use on an nx x ny x nz grid
@@ -416,6 +440,30 @@ int mcrt_get_cell_proposal(mcrt_ctx *ctx, uint64_t *cn, uint64_t *cg, uint32_t *
  * (K of the network differs from n_bands n_g, mix outside (0, 1]),
  * MCRT_E_STATE. */
 int mcrt_set_learned_proposal(mcrt_ctx *ctx, mcrt_mlp *m, float mix, void *cuda_stream);
+
+/* Machine ceilings the traversal is measured against (not part of the method).
+ * A march step evaluates one exponential (the segment transmissivity, Eq. 10)
+ * and gathers the {T, x} of the cell it enters plus two table entries; these
+ * probes measure the GPU's rates for exactly those two operations.  Each call
+ * allocates its own device memory on `device`, times one probe kernel with CUDA
+ * events after one untimed launch, frees the memory and returns (synchronous;
+ * no context needed).
+ *
+ * mcrt_probe_ex2: base-2 exponentials of the special-function unit
+ * (ex2.approx.ftz.f32) per second over the whole GPU, every thread of a
+ * full-occupancy grid running 8 independent chains x <- 2^(-x).  *sm_mhz is
+ * the mean SM clock during the probe (SM cycles over global-timer time).
+ *
+ * mcrt_probe_gather: random 8-byte loads per second from a buffer of `bytes`
+ * bytes (a power of two, 2^12 .. 2^35), 8 independent loads in flight per
+ * thread of a full-occupancy grid, indices from per-load 32-bit congruential
+ * generators, so the lanes of a warp hit different sectors: the worst case of
+ * the march's gathers.  Useful bytes per second = 8 * *per_s.
+ *
+ * Errors: MCRT_E_ARG (NULL output, bytes out of range or not a power of two),
+ * MCRT_E_OOM, MCRT_E_CUDA (no such device, launch failure). */
+int mcrt_probe_ex2(int device, double *per_s, double *sm_mhz);
+int mcrt_probe_gather(int device, uint64_t bytes, double *per_s);
 
 /* Releases all device memory of the context; NULL is accepted.  Waits for the
  * context's outstanding work. */

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
   const unsigned *__restrict__ chemi_b = nullptr;
   int reflect_b = 0;
   unsigned snapw_b = 0;
+  unsigned snap_b = 0;  // index of the snapshot being solved
 #define m (BATCH ? (m) : (member))
   long long sp0 = 0, sp1 = BATCH ? 0 : 0x7fffffffffffffffLL;  // positions of this snapshot
   bool pending = false;  // the next claimed position lies in another snapshot
@@ -129,7 +130,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
     if (BATCH && pending && tail == head && !__any_sync(0xffffffffu, active)) {
       // every ray of the previous snapshot has finished: take over the snapshot
       // that owns the next claimed position
-      const SnapArgs &sn = a.snaps[snapshot_of(starts, a.nsnaps, p_next)];
+      const int snap_i = snapshot_of(starts, a.nsnaps, p_next);
+      const SnapArgs &sn = a.snaps[snap_i];
+      snap_b = (unsigned)snap_i;
       nx = sn.nx;
       ny = sn.ny;
       nz = sn.nz;
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
       reflect_b = sn.reflect;
       snapw_b = sn.snapshot;
       sp0 = sn.p0;
-      sp1 = starts[snapshot_of(starts, a.nsnaps, p_next) + 1];
+      sp1 = starts[snap_i + 1];
       // the plain proposal's counts are read through L1 (shared memory stays
       // small, leaving L1 to the field gathers)
       s_cn = sn.cn;
@@ -365,6 +368,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
         tn = tnz;
       }
       const float ds = fmaxf(tn - tprev, 0.f);
+      bool refl = false;  // this step reflected the ray off a wall
       const uint2 f = __ldg(field + (MG ? loff + lin : lin));
       unsigned it;
       float fr;
@@ -462,6 +466,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
                 ddz = sr * sp;
               }
               ++nrefl;
+              refl = true;
               axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
               axis_setup(ddy, nfy, yfs ? dyl(iy, MG ? lev : 0) : gl * DY, sy, t0y, tsy);
               axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
@@ -505,6 +510,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           ++lev;
           lsteps = 0;
         }
+      }
+      if (!MG && !done && steps >= a.long_steps && (steps == a.long_steps || ax == 1 || refl) &&
+          long_flight(tny, tprev, tsx, tsz, a.long_flight)) {
+        // a long flight ahead (a grazing ray of a thin band): the warp-parallel
+        // march of long_rays.cu finishes this ray; checked when the ray reaches
+        // long_steps segments and at each later y face and reflection
+        LongRay L;
+        L.t0x = t0x; L.t0y = t0y; L.t0z = t0z; L.tsx = tsx;
+        L.tsy = tsy; L.tsz = tsz; L.cntx = cntx; L.cnty = cnty;
+        L.cntz = cntz; L.tnx = tnx; L.tny = tny; L.tnz = tnz;
+        L.tprev = tprev; L.tau = tau; L.X = X; L.B_i = B_i;
+        L.B_last = B_last; L.scale = scale; L.krow = krow; L.n = n;
+        L.ix = ix; L.iy = iy; L.iz = iz;
+        L.signs = (unsigned)(sx + 1) | ((unsigned)(sy + 1) << 2) | ((unsigned)(sz + 1) << 4);
+        L.lin = lin; L.slot = slot; L.r = r; L.ray = ray;
+        L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = snap_b;
+        if (hand_off(a, L)) active = false;
       }
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
@@ -596,30 +618,8 @@ __global__ void __launch_bounds__(256) reduce_cells_batch_kernel(const TraceArgs
         if (!brick_cell(a, pos, bx, by, bz)) continue;  // warp-uniform
         bc = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
       }
-      const float *y = a.ybuf + (size_t)(base + c) * N;
-      float hi = 0.f, lo = 0.f, hi2 = 0.f, lo2 = 0.f;
-      for (int k = lane; k < N; k += 32) {
-        const float v = y[k];
-        two_sum_acc(hi, lo, v);
-        const float pr = v * v;
-        two_sum_acc(hi2, lo2, pr);
-        lo2 += fmaf(v, v, -pr);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
-        const float oh2 = __shfl_xor_sync(0xffffffffu, hi2, off), ol2 = __shfl_xor_sync(0xffffffffu, lo2, off);
-        // combine in a lane-independent order so every lane holds identical bits
-        if (lane & off) {
-          float th = oh, tl = ol, th2 = oh2, tl2 = ol2;
-          pair_add(th, tl, hi, lo);
-          pair_add(th2, tl2, hi2, lo2);
-          hi = th; lo = tl; hi2 = th2; lo2 = tl2;
-        } else {
-          pair_add(hi, lo, oh, ol);
-          pair_add(hi2, lo2, oh2, ol2);
-        }
-      }
+      float hi, lo, hi2, lo2;
+      warp_cell_sums(a.ybuf + (size_t)(base + c) * N, N, lane, hi, lo, hi2, lo2);
       if (lane == c) {
         mh = hi; ml = lo; mh2 = hi2; ml2 = lo2;
         mine = true;
@@ -710,11 +710,13 @@ cudaError_t prepare_trace_fp32_batch(int min_blocks, int steps_per_round, int nb
             : configure_variant<2, 1, false>(smem, blocks_per_sm, num_sms);
 }
 
-cudaError_t launch_trace_fp32_batch(const TraceArgs &a, int min_blocks, int steps_per_round,
+cudaError_t launch_trace_fp32_batch(const TraceArgs &args, int min_blocks, int steps_per_round,
                                     cudaStream_t s) {
-  if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
+  if (args.chunk_p1 <= args.chunk_p0) return cudaSuccess;
+  TraceArgs a = args;
+  if (!long_rays_on(a)) a.long_steps = 0x7fffffff;  // no hand-off
   const size_t smem = fp32_batch_smem_bytes(a.nb, a.ng, a.nsnaps, a.counts_in_smem);
-  cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const bool mb3 = min_blocks >= 3, k2 = steps_per_round >= 2;
   if (a.mg_levels > 1) {
@@ -729,6 +731,10 @@ cudaError_t launch_trace_fp32_batch(const TraceArgs &a, int min_blocks, int step
       e = k2 ? launch_variant<2, 2, false>(a, s, smem) : launch_variant<2, 1, false>(a, s, smem);
   }
   if (e != cudaSuccess) return e;
+  if (long_rays_on(a)) {
+    e = launch_long_rays(a, s);
+    if (e != cudaSuccess) return e;
+  }
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
   if (blocks > 152 * 16) blocks = 152 * 16;

@@ -46,6 +46,8 @@ struct mcrt_ctx {
   DevBuf p0_32, feat, ray_steps, lerr, kptab;
   // stretched grid: faces in FP64 and FP32
   DevBuf yf64, yf32;
+  // long rays handed off by the FP32 exact march (LongRay entries)
+  DevBuf longbuf;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t last_stream = nullptr;
   bool solved = false;
@@ -53,6 +55,8 @@ struct mcrt_ctx {
   int min_blocks = 3;
   int steps_per_round = 1;
   int scratch_mib = 1024;
+  int long_steps = 1024;    // hand-off threshold in segments (<= 0: never)
+  float long_flight = 32;   // x/z crossings left in the flight for a hand-off
   double last_T_max = 0;
   std::string err;
 };
@@ -115,6 +119,10 @@ int ensure_plain_proposal(mcrt_ctx *ctx, cudaStream_t s);
 // outputs and scratch are left for the caller (mcrt_api.cpp).
 void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int b[6],
                      mcrt::TraceArgs *a);
+// Sizes the long-ray buffer for chunks of chunk_rays rays and points the launch
+// arguments at it (the hand-off is off for multigrid, closed boxes or by the
+// tuning: mcrt::long_rays_on).
+int setup_long_rays(mcrt_ctx *ctx, long long chunk_rays, mcrt::TraceArgs *a);
 // Validates solve parameters common to every solve entry point.
 int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]);
 

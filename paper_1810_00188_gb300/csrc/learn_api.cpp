@@ -408,6 +408,8 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
   a.ybuf = (float *)ctx->ybuf.p;
   a.step_acc = (unsigned long long *)ctx->step_acc.p;
   a.ray_steps = (unsigned *)ctx->ray_steps.p;
+  const int rl = setup_long_rays(ctx, Pc * (long long)p->rays_per_cell, &a);
+  if (rl != MCRT_OK) return rl;
   mcrt::TallyArgs t;
   std::memset(&t, 0, sizeof(t));
   t.cells = cells;
@@ -432,7 +434,7 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
   t.m_out = mom_out;
   t.c_out = cost_out;
   t.err = (unsigned long long *)ctx->lerr.p;
-  CK(cudaMemsetAsync(ctx->counters.p, 0, 6 * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(ctx->counters.p, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), s), "clear counters");
   CK(cudaEventRecord(ctx->ev0, s), "event");
   int launches = 0;
   for (long long p0 = 0; p0 < P; p0 += Pc) {
@@ -440,7 +442,7 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
     a.chunk_p1 = t.chunk_p1 = p0 + Pc < P ? p0 + Pc : P;
     CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
     CK(mcrt::launch_tally(t, s), "tally launch");
-    launches += 3;
+    launches += mcrt::long_rays_on(a) ? 4 : 3;
   }
   CK(cudaEventRecord(ctx->ev1, s), "event");
   ctx->last_launches = launches;

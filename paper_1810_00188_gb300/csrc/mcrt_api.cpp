@@ -183,6 +183,20 @@ int ensure_plain_proposal(mcrt_ctx *ctx, cudaStream_t s) {
   return MCRT_OK;
 }
 
+int setup_long_rays(mcrt_ctx *ctx, long long chunk_rays, mcrt::TraceArgs *a) {
+  a->long_rays = nullptr;
+  a->long_cap = 0;
+  a->long_steps = 0x7fffffff;
+  a->long_flight = ctx->long_flight;
+  if (ctx->long_steps <= 0 || a->mg_levels > 1 || a->xz_walls) return MCRT_OK;
+  const long long cap = mcrt::long_ray_capacity(chunk_rays, ctx->long_steps);
+  CK(ensure(ctx->longbuf, (size_t)cap * sizeof(mcrt::LongRay)), "alloc long-ray buffer");
+  a->long_rays = (mcrt::LongRay *)ctx->longbuf.p;
+  a->long_cap = (int)cap;
+  a->long_steps = ctx->long_steps;
+  return MCRT_OK;
+}
+
 int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
   if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
   if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
@@ -346,7 +360,7 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   DeviceGuard dg(g->device);
   if (!dg.ok || cudaEventCreate(&ctx->ev0) != cudaSuccess ||
       cudaEventCreate(&ctx->ev1) != cudaSuccess ||
-      ensure(ctx->counters, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+      ensure(ctx->counters, mcrt::NCOUNTERS * sizeof(unsigned long long)) != cudaSuccess ||
       ensure(ctx->fstats, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     mcrt_destroy(ctx);
@@ -611,7 +625,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
   a.sigma = ds;
   a.steps_cell = dst;
 
-  CK(cudaMemsetAsync(ctx->counters.p, 0, 6 * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(ctx->counters.p, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), s), "clear counters");
   int launches = 0;
   if (p->precision == MCRT_FP32 && nbox > 0) {
     // brick-ordered positions in chunks whose per-ray samples fit the scratch
@@ -624,6 +638,8 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     CK(ensure(ctx->step_acc, (size_t)Pc * sizeof(unsigned long long)), "alloc step scratch");
     a.ybuf = (float *)ctx->ybuf.p;
     a.step_acc = (unsigned long long *)ctx->step_acc.p;
+    const int rl = setup_long_rays(ctx, Pc * (long long)p->rays_per_cell, &a);
+    if (rl != MCRT_OK) return rl;
     CK(cudaEventRecord(ctx->ev0, s), "event");
     for (long long p0 = 0; p0 < P; p0 += Pc) {
       a.chunk_p0 = p0;
@@ -632,7 +648,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
         CK(cudaMemsetAsync(ctx->step_acc.p, 0, (size_t)(a.chunk_p1 - p0) * sizeof(unsigned long long), s),
            "clear step scratch");
       CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
-      launches += 2;
+      launches += mcrt::long_rays_on(a) ? 3 : 2;
     }
     CK(cudaEventRecord(ctx->ev1, s), "event");
   } else {
@@ -674,9 +690,12 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
   if (t->steps_per_round != 0 && t->steps_per_round != 1 && t->steps_per_round != 2 &&
       t->steps_per_round != 4)
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
+  if (t->long_ray_flight > (1 << 24)) return fail(ctx, MCRT_E_ARG, "long_ray_flight above 2^24");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
   ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
   ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
+  ctx->long_steps = t->long_ray_steps ? (t->long_ray_steps > 0 ? t->long_ray_steps : -1) : 1024;
+  ctx->long_flight = t->long_ray_flight ? (t->long_ray_flight > 0 ? (float)t->long_ray_flight : -1.f) : 32.f;
   return MCRT_OK;
 }
 
@@ -685,6 +704,8 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   t->min_blocks_per_sm = ctx->min_blocks;
   t->steps_per_round = ctx->steps_per_round;
   t->scratch_mib = ctx->scratch_mib;
+  t->long_ray_steps = ctx->long_steps;
+  t->long_ray_flight = ctx->long_flight < 0.f ? -1 : (int)ctx->long_flight;
   return MCRT_OK;
 }
 
@@ -694,7 +715,7 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   if (!ctx->solved) return fail(ctx, MCRT_E_STATE, "no solve yet");
   DeviceGuard dg(ctx->grid.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
-  unsigned long long c[6];
+  unsigned long long c[mcrt::NCOUNTERS];
   CK(cudaMemcpyAsync(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream),
      "read counters");
   CK(cudaStreamSynchronize(ctx->last_stream), "sync");
@@ -709,6 +730,8 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   out->T_max = ctx->last_T_max;
   out->kernel_ms = ms;
   out->launches = ctx->last_launches;
+  out->long_rays = c[8];
+  out->long_overflow = c[9];
   return MCRT_OK;
 }
 
@@ -717,7 +740,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -911,7 +934,7 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.step_acc = (unsigned long long *)(cbase + head_bytes);
   const size_t ybuf_off = (head_bytes + (size_t)Pc * sizeof(unsigned long long) + 255) & ~(size_t)255;
   a.ybuf = (float *)(cbase + ybuf_off);
-  CK(cudaMemsetAsync(a.counters, 0, 6 * sizeof(unsigned long long), s), "clear counters");
+  CK(cudaMemsetAsync(a.counters, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), s), "clear counters");
   for (long long p0 = 0; p0 < P; p0 += Pc) {
     a.chunk_p0 = p0;
     a.chunk_p1 = p0 + Pc < P ? p0 + Pc : P;
@@ -1094,7 +1117,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     if (pc > P[k]) pc = P[k];
     Pc[k] = pc;
     void *ct = nullptr;
-    BK(cudaMalloc(&ct, 8 * sizeof(unsigned long long)), "alloc counters");
+    BK(cudaMalloc(&ct, mcrt::NCOUNTERS * sizeof(unsigned long long)), "alloc counters");
     b->owned.push_back(ct);
     a.counters = (unsigned long long *)ct;
     b->counters.push_back((unsigned long long *)ct);
@@ -1165,7 +1188,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     void *yb = nullptr, *ct = nullptr;
     BK(cudaMalloc(&yb, (size_t)pc * per_pos), "alloc sample scratch");
     b->owned.push_back(yb);
-    BK(cudaMalloc(&ct, 8 * sizeof(unsigned long long)), "alloc counters");
+    BK(cudaMalloc(&ct, mcrt::NCOUNTERS * sizeof(unsigned long long)), "alloc counters");
     b->owned.push_back(ct);
     b->counters.assign(1, (unsigned long long *)ct);
     mcrt::TraceArgs a = args[order[0]];
@@ -1177,6 +1200,18 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.ray_steps = nullptr;
     a.counters = (unsigned long long *)ct;
     a.grid_blocks = 0;
+    a.long_rays = nullptr;
+    a.long_cap = 0;
+    a.long_steps = c0->long_steps > 0 ? c0->long_steps : 0x7fffffff;
+    a.long_flight = c0->long_flight;
+    if (c0->long_steps > 0 && a.mg_levels <= 1) {
+      const long long lc = mcrt::long_ray_capacity(pc * (long long)p->rays_per_cell, c0->long_steps);
+      void *lb = nullptr;
+      BK(cudaMalloc(&lb, (size_t)lc * sizeof(mcrt::LongRay)), "alloc long-ray buffer");
+      b->owned.push_back(lb);
+      a.long_rays = (mcrt::LongRay *)lb;
+      a.long_cap = (int)lc;
+    }
     int bps = 0, nsm = 0;
     BK(mcrt::prepare_trace_fp32_batch(c0->min_blocks, c0->steps_per_round, a.nb, a.ng, n, a.counts_in_smem,
                                       a.mg_levels > 1, &bps, &nsm),
@@ -1186,13 +1221,13 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     BK(cudaDeviceSynchronize(), "sync");
     cudaStream_t s0 = b->streams[0];
     BK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t ce = cudaMemsetAsync(a.counters, 0, 6 * sizeof(unsigned long long), s0);
+    cudaError_t ce = cudaMemsetAsync(a.counters, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), s0);
     int launches = 0;
     for (long long p0 = 0; p0 < pos && ce == cudaSuccess; p0 += pc) {
       a.chunk_p0 = p0;
       a.chunk_p1 = p0 + pc < pos ? p0 + pc : pos;
       ce = mcrt::launch_trace_fp32_batch(a, c0->min_blocks, c0->steps_per_round, s0);
-      launches += 2;
+      launches += mcrt::long_rays_on(a) ? 3 : 2;
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(s0, &graph);
@@ -1232,14 +1267,24 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   for (int j = 0; j < streams; ++j) {
     long long pmax = 0;
     for (int r = j; r < n; r += streams) pmax = Pc[order[r]] > pmax ? Pc[order[r]] : pmax;
-    void *yb = nullptr, *sa = nullptr;
+    void *yb = nullptr, *sa = nullptr, *lb = nullptr;
     BK(cudaMalloc(&yb, (size_t)pmax * p->rays_per_cell * sizeof(float)), "alloc sample scratch");
     b->owned.push_back(yb);
     BK(cudaMalloc(&sa, (size_t)pmax * sizeof(unsigned long long)), "alloc step scratch");
     b->owned.push_back(sa);
+    const long long lc = mcrt::long_ray_capacity(pmax * (long long)p->rays_per_cell, c0->long_steps);
+    if (c0->long_steps > 0) {
+      BK(cudaMalloc(&lb, (size_t)lc * sizeof(mcrt::LongRay)), "alloc long-ray buffer");
+      b->owned.push_back(lb);
+    }
     for (int r = j; r < n; r += streams) {
-      args[order[r]].ybuf = (float *)yb;
-      args[order[r]].step_acc = (unsigned long long *)sa;
+      mcrt::TraceArgs &ak = args[order[r]];
+      ak.ybuf = (float *)yb;
+      ak.step_acc = (unsigned long long *)sa;
+      ak.long_rays = (mcrt::LongRay *)lb;
+      ak.long_cap = lb ? (int)lc : 0;
+      ak.long_steps = c0->long_steps > 0 ? c0->long_steps : 0x7fffffff;
+      ak.long_flight = c0->long_flight;
     }
   }
   BK(cudaDeviceSynchronize(), "sync");
@@ -1252,12 +1297,12 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   for (int r = 0; r < n && ce == cudaSuccess; ++r) {
     const int k = order[r];
     cudaStream_t sk = b->streams[r % streams];
-    ce = cudaMemsetAsync(args[k].counters, 0, 6 * sizeof(unsigned long long), sk);
+    ce = cudaMemsetAsync(args[k].counters, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), sk);
     for (long long p0 = 0; p0 < P[k] && ce == cudaSuccess; p0 += Pc[k]) {
       args[k].chunk_p0 = p0;
       args[k].chunk_p1 = p0 + Pc[k] < P[k] ? p0 + Pc[k] : P[k];
       ce = mcrt::launch_trace_fp32(args[k], c0->min_blocks, c0->steps_per_round, sk);
-      launches += 2;
+      launches += mcrt::long_rays_on(args[k]) ? 3 : 2;
     }
   }
   for (int j = 1; j < streams && ce == cudaSuccess; ++j) {
@@ -1306,7 +1351,7 @@ extern "C" int mcrt_batch_get_stats(mcrt_batch *b, mcrt_solve_stats *out) {
   std::memset(out, 0, sizeof(*out));
   cudaError_t e = cudaEventSynchronize(b->ev1);
   for (unsigned long long *cp : b->counters) {
-    unsigned long long cnt[6];
+    unsigned long long cnt[mcrt::NCOUNTERS];
     if (e == cudaSuccess) e = cudaMemcpy(cnt, cp, sizeof(cnt), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) break;
     if (cnt[5] != 0) return batch_fail(b, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
@@ -1315,6 +1360,8 @@ extern "C" int mcrt_batch_get_stats(mcrt_batch *b, mcrt_solve_stats *out) {
     out->wall_hits += cnt[2];
     out->rays += cnt[3];
     if (cnt[4] > out->max_ray_steps) out->max_ray_steps = cnt[4];
+    out->long_rays += cnt[8];
+    out->long_overflow += cnt[9];
   }
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev0, b->ev1);

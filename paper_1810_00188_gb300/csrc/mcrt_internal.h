@@ -8,6 +8,28 @@
 
 namespace mcrt {
 
+// State of a long ray handed from the FP32 trace kernel to the warp-parallel
+// march (long_rays.cu), taken between two segments: the parametric axes
+// (crossing m of an axis at fma(m, ts, t0)), the next crossings, the current
+// cell, the running transmissivity and sum, and the ray's identity (sample slot,
+// Philox words, snapshot of a batch).  128 bytes, written and read as float4s.
+struct __align__(16) LongRay {
+  float t0x, t0y, t0z, tsx;
+  float tsy, tsz, cntx, cnty;
+  float cntz, tnx, tny, tnz;
+  float tprev, tau, X, B_i;
+  float B_last, scale;
+  unsigned krow, n;          // table row of (n, g) and the band
+  int ix, iy, iz;
+  unsigned signs;            // (sx + 1) | (sy + 1) << 2 | (sz + 1) << 4
+  unsigned lin, slot, r, ray;  // cell, sample slot, ray index in the cell, Philox ray word
+  unsigned cellid, steps, nrefl, snap;  // emitting cell, segments so far, reflections, batch snapshot
+};
+static_assert(sizeof(LongRay) == 128, "LongRay is eight float4");
+
+// Entries of a solve's device counters (see TraceArgs::counters).
+constexpr int NCOUNTERS = 10;
+
 // Everything one trace launch reads.  Device pointers only.
 // One snapshot of a batched FP32 solve (one persistent launch over many
 // fields that share the k-distribution): what differs from snapshot to
@@ -83,6 +105,12 @@ struct TraceArgs {
   // multigrid (Section 4.3): grids used (1: exact march) and segments per grid;
   // the fields of grid l (l >= 1) follow those of grid l - 1 in field64 / fpos32
   int mg_levels, mg_steps;
+  // FP32 exact march: hand-off of long rays to the warp-parallel march (count in
+  // counters[7]); long_rays null or long_steps 0: never
+  LongRay *long_rays;
+  int long_cap;      // entries of long_rays
+  int long_steps;    // segments marched before a hand-off
+  float long_flight; // x/z crossings left in the flight for a hand-off
   // solve
   int rays, max_steps, origin;
   double tol;
@@ -94,7 +122,10 @@ struct TraceArgs {
   double *q, *sigma;
   unsigned long long *steps_cell;
   unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps)
-                                 // [5] error flags [6] FP32 kernel: claimed positions (8 entries)
+                                 // [5] error flags [6] FP32 kernel: claimed positions
+                                 // [7] long rays handed off by this launch
+                                 // [8] long rays finished by the warp-parallel march
+                                 // [9] long rays that found the buffer full (NCOUNTERS entries)
 };
 
 // Multigrid grid count of an nx x ny x nz grid and the cells of all its grids.
@@ -116,6 +147,19 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);
+// The warp-parallel march of the long rays the last FP32 trace launch handed off
+// (a.long_rays[0 .. min(counters[7], long_cap))); writes their samples and adds
+// their counts.  Launched after each trace launch, before the reduction.
+cudaError_t launch_long_rays(const TraceArgs &a, cudaStream_t s);
+// Entries of the long-ray buffer for a launch of `rays` rays and the hand-off
+// threshold long_steps.
+long long long_ray_capacity(long long rays, int long_steps);
+// True when a launch with these arguments hands long rays off (exact march,
+// periodic x and z, a buffer and a threshold).
+inline bool long_rays_on(const TraceArgs &a) {
+  return a.long_rays && a.long_cap > 0 && a.long_steps > 0 && a.long_steps < 0x7fffffff &&
+         a.mg_levels <= 1 && !a.xz_walls;
+}
 // Batched FP32 solve over a.snaps: trace + reduce of the global positions
 // [chunk_p0, chunk_p1), one persistent launch each.
 cudaError_t launch_trace_fp32_batch(const TraceArgs &a, int min_blocks, int steps_per_round,

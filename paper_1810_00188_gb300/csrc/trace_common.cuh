@@ -1,7 +1,7 @@
 // Device helpers shared by the FP32 trace kernels of trace_fp32.cu (one solve)
 // and batch.cu (many snapshots in one launch): the per-warp ray ring, exact bit
 // constructions of uniforms and small integers, the interpolation position, the
-// sine/cosine series, the guided inverse CDF, the absorption of a segment, the
+// azimuth's sine and cosine, the guided inverse CDF, the absorption of a segment, the
 // axis set-up of the parametric ray, compensated binary32 sums, and the
 // brick-order enumeration of cells.
 #pragma once
@@ -55,9 +55,6 @@ __device__ __forceinline__ void tpos(unsigned packed, unsigned &it, float &fr) {
   fr = __uint_as_float(0x3F800000u | (packed & 0x7FFFFFu)) - 1.f;
 }
 
-// sin(pi x), cos(pi x) for x in [0, 2]: x = k/2 + r with k the nearest integer of
-// 2x and |r| <= 1/4 (both exact), then Taylor series of sin and cos at pi r
-// (truncation below 2e-9 relative) rotated by the quadrant k.
 // sin(2 pi u), cos(2 pi u) for u in (0, 1) with the hardware approximations
 // (absolute error about 4e-7): the angle is reduced to 2 pi (u - 1/2) in
 // (-pi, pi), the range where __sincosf is accurate, and both signs flip back.
@@ -66,19 +63,6 @@ __device__ __forceinline__ void sincos_2pi(float u, float &s, float &c) {
   __sincosf(6.28318530717958647f * (u - 0.5f), &s0, &c0);
   s = -s0;
   c = -c0;
-}
-
-__device__ __forceinline__ void sincospi_02(float x, float &s, float &c) {
-  const float kf = __fadd_rn(2.f * x, 12582912.f);
-  const int k = __float_as_int(kf) - 0x4B400000;
-  const float r = x - 0.5f * (kf - 12582912.f);
-  const float a = 3.14159265358979f * r, a2 = a * a;
-  const float sp = a * (1.f + a2 * (-1.f / 6.f + a2 * (1.f / 120.f + a2 * (-1.f / 5040.f + a2 * (1.f / 362880.f)))));
-  const float cp = 1.f + a2 * (-0.5f + a2 * (1.f / 24.f + a2 * (-1.f / 720.f + a2 * (1.f / 40320.f + a2 * (-1.f / 3628800.f)))));
-  const int q = k & 3;
-  const float ss = (q & 1) ? cp : sp, cc = (q & 1) ? sp : cp;
-  s = (q & 2) ? -ss : ss;
-  c = ((q + 1) & 2) ? -cc : cc;
 }
 
 // First k with u < cum[k] (the inverse CDF of Eq. 17), started from a guide
@@ -159,8 +143,6 @@ __device__ __forceinline__ int snapshot_of(const long long *starts, int n, long 
   return lo;
 }
 
-// MG: the multigrid march of Section 4.3 (a.mg_levels grids); the exact march
-
 // Compensated binary32 pair (hi + lo) plus another pair, renormalised.
 __device__ __forceinline__ void pair_add(float &hi, float &lo, float bhi, float blo) {
   const float s = hi + bhi;
@@ -168,6 +150,67 @@ __device__ __forceinline__ void pair_add(float &hi, float &lo, float bhi, float 
   const float err = (hi - (s - bb)) + (bhi - bb) + (lo + blo);
   hi = s + err;
   lo = err - (hi - s);
+}
+
+// Long rays (long_rays.cu).  A ray whose flight to the next y face still crosses
+// at least `need` x/z faces: (t_y - t) (1/ts_x + 1/ts_z), an axis the ray does
+// not cross having ts = inf.  A flight with no y face ahead (d_y = 0) is long
+// unless the ray crosses nothing at all.
+__device__ __forceinline__ bool long_flight(float tny, float tprev, float tsx, float tsz, float need) {
+  return (tny - tprev) * (__frcp_rn(tsx) + __frcp_rn(tsz)) >= need;
+}
+
+// Stores a lane's ray state for the warp-parallel march; false when the buffer
+// is full (the ray then marches on where it is).
+__device__ __forceinline__ bool hand_off(const TraceArgs &a, const LongRay &L) {
+  const unsigned long long k = atomicAdd(a.counters + 7, 1ull);
+  if (k >= (unsigned long long)a.long_cap) return false;
+  const float4 *src = reinterpret_cast<const float4 *>(&L);
+  float4 *dst = reinterpret_cast<float4 *>(a.long_rays + k);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) dst[i] = src[i];
+  return true;
+}
+
+// Sum of one cell's N samples y[0..N) and of their squares over a warp, as
+// compensated binary32 pairs: each lane adds samples lane, lane+32, ... in that
+// order, then the lanes combine in a lane-independent tree, so every lane
+// returns identical bits.  Loads go in batches of LOADS per lane with the
+// streaming hint (each sample is read once): enough bytes in flight to keep HBM
+// busy while the additions stay in the one fixed order.
+__device__ __forceinline__ void warp_cell_sums(const float *__restrict__ y, int N, int lane, float &hi,
+                                               float &lo, float &hi2, float &lo2) {
+  constexpr int LOADS = 8;
+  hi = 0.f; lo = 0.f; hi2 = 0.f; lo2 = 0.f;
+  for (int k0 = lane; k0 < N; k0 += 32 * LOADS) {
+    float v[LOADS];
+#pragma unroll
+    for (int j = 0; j < LOADS; ++j) v[j] = k0 + 32 * j < N ? __ldcs(y + k0 + 32 * j) : 0.f;
+#pragma unroll
+    for (int j = 0; j < LOADS; ++j) {
+      if (k0 + 32 * j < N) {
+        two_sum_acc(hi, lo, v[j]);
+        const float pr = v[j] * v[j];
+        two_sum_acc(hi2, lo2, pr);
+        lo2 += fmaf(v[j], v[j], -pr);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
+    const float oh2 = __shfl_xor_sync(0xffffffffu, hi2, off), ol2 = __shfl_xor_sync(0xffffffffu, lo2, off);
+    // combine in a lane-independent order so every lane holds identical bits
+    if (lane & off) {
+      float th = oh, tl = ol, th2 = oh2, tl2 = ol2;
+      pair_add(th, tl, hi, lo);
+      pair_add(th2, tl2, hi2, lo2);
+      hi = th; lo = tl; hi2 = th2; lo2 = tl2;
+    } else {
+      pair_add(hi, lo, oh, ol);
+      pair_add(hi2, lo2, oh2, ol2);
+    }
+  }
 }
 
 }  // namespace

@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         tn = tnz;
       }
       const float ds = fmaxf(tn - tprev, 0.f);
+      bool refl = false;  // this step reflected the ray off a wall
       const uint2 f = __ldg(field + (MG ? loff + lin : lin));
       unsigned it;
       float fr;
@@ -424,6 +425,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
                 ddz = sr * sp;
               }
               ++nrefl;
+              refl = true;
               axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
               axis_setup(ddy, nfy, yfs ? dyl(iy, MG ? lev : 0) : gl * DY, sy, t0y, tsy);
               axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
@@ -467,6 +469,23 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           ++lev;
           lsteps = 0;
         }
+      }
+      if (!MG && !done && steps >= a.long_steps && (steps == a.long_steps || ax == 1 || refl) &&
+          long_flight(tny, tprev, tsx, tsz, a.long_flight)) {
+        // a long flight ahead (a grazing ray of a thin band): the warp-parallel
+        // march of long_rays.cu finishes this ray; checked when the ray reaches
+        // long_steps segments and at each later y face and reflection
+        LongRay L;
+        L.t0x = t0x; L.t0y = t0y; L.t0z = t0z; L.tsx = tsx;
+        L.tsy = tsy; L.tsz = tsz; L.cntx = cntx; L.cnty = cnty;
+        L.cntz = cntz; L.tnx = tnx; L.tny = tny; L.tnz = tnz;
+        L.tprev = tprev; L.tau = tau; L.X = X; L.B_i = B_i;
+        L.B_last = B_last; L.scale = scale; L.krow = krow; L.n = n;
+        L.ix = ix; L.iy = iy; L.iz = iz;
+        L.signs = (unsigned)(sx + 1) | ((unsigned)(sy + 1) << 2) | ((unsigned)(sz + 1) << 4);
+        L.lin = lin; L.slot = slot; L.r = r; L.ray = ray;
+        L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = 0u;
+        if (hand_off(a, L)) active = false;
       }
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
@@ -531,30 +550,8 @@ __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
     for (int c = 0; c < ncell; ++c) {
       int bx, by, bz;
       if (!brick_cell(a, a.chunk_p0 + base + c, bx, by, bz)) continue;  // warp-uniform
-      const float *y = a.ybuf + (size_t)(base + c) * N;
-      float hi = 0.f, lo = 0.f, hi2 = 0.f, lo2 = 0.f;
-      for (int k = lane; k < N; k += 32) {
-        const float v = y[k];
-        two_sum_acc(hi, lo, v);
-        const float pr = v * v;
-        two_sum_acc(hi2, lo2, pr);
-        lo2 += fmaf(v, v, -pr);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
-        const float oh2 = __shfl_xor_sync(0xffffffffu, hi2, off), ol2 = __shfl_xor_sync(0xffffffffu, lo2, off);
-        // combine in a lane-independent order so every lane holds identical bits
-        if (lane & off) {
-          float th = oh, tl = ol, th2 = oh2, tl2 = ol2;
-          pair_add(th, tl, hi, lo);
-          pair_add(th2, tl2, hi2, lo2);
-          hi = th; lo = tl; hi2 = th2; lo2 = tl2;
-        } else {
-          pair_add(hi, lo, oh, ol);
-          pair_add(hi2, lo2, oh2, ol2);
-        }
-      }
+      float hi, lo, hi2, lo2;
+      warp_cell_sums(a.ybuf + (size_t)(base + c) * N, N, lane, hi, lo, hi2, lo2);
       if (lane == c) {
         mh = hi; ml = lo; mh2 = hi2; ml2 = lo2;
         mine = true;
@@ -667,12 +664,14 @@ cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int 
 #undef MCRT_PREP_K
 }
 
-cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
+cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_per_round,
                               cudaStream_t s) {
-  if (a.chunk_p1 <= a.chunk_p0) return cudaSuccess;
+  if (args.chunk_p1 <= args.chunk_p0) return cudaSuccess;
+  TraceArgs a = args;
+  if (!long_rays_on(a)) a.long_steps = 0x7fffffff;  // no hand-off
   const size_t smem = fp32_smem_bytes(a.nb, a.ng, a.counts_in_smem);
-  // the claim counter of this launch's position runs
-  cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, sizeof(unsigned long long), s);
+  // the claim counter of this launch's position runs and its hand-off count
+  cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
 #define MCRT_FP32_K(MB)                                                    \
   if (a.mg_levels > 1) {                                                   \
@@ -696,6 +695,10 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_
   }
 #undef MCRT_FP32_K
   if (e != cudaSuccess) return e;
+  if (long_rays_on(a)) {
+    e = launch_long_rays(a, s);
+    if (e != cudaSuccess) return e;
+  }
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
   if (blocks > 152 * 16) blocks = 152 * 16;

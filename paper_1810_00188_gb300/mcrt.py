@@ -59,7 +59,7 @@ class mcrt_solve_params(C.Structure):
 
 class mcrt_tuning(C.Structure):
     _fields_ = [("min_blocks_per_sm", C.c_int), ("steps_per_round", C.c_int),
-                ("scratch_mib", C.c_int)]
+                ("scratch_mib", C.c_int), ("long_ray_steps", C.c_int), ("long_ray_flight", C.c_int)]
 
 
 class mcrt_batch_item(C.Structure):
@@ -71,7 +71,7 @@ class mcrt_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("rays", C.c_uint64), ("capped", C.c_uint64),
                 ("wall_hits", C.c_uint64), ("max_ray_steps", C.c_uint64), ("T_max", C.c_double),
                 ("kernel_ms", C.c_float),
-                ("launches", C.c_int)]
+                ("launches", C.c_int), ("long_rays", C.c_uint64), ("long_overflow", C.c_uint64)]
 
 
 _lib = None
@@ -85,7 +85,7 @@ EXPORTS = ("mcrt_create", "mcrt_set_kdist", "mcrt_set_fields", "mcrt_set_cell_pr
            "mcrt_mlp_last_loss", "mcrt_mlp_last_error", "mcrt_mlp_destroy", "mcrt_cell_features",
            "mcrt_tally_moments", "mcrt_get_plain_probs", "mcrt_set_cell_proposal_probs",
            "mcrt_get_cell_proposal", "mcrt_set_learned_proposal", "mcrt_multigrid_levels",
-           "mcrt_set_spectral_proposal")
+           "mcrt_set_spectral_proposal", "mcrt_probe_ex2", "mcrt_probe_gather")
 _NOT_INT = ("mcrt_status_string", "mcrt_last_error", "mcrt_batch_last_error", "mcrt_mlp_last_error",
             "mcrt_mlp_nparams")
 MCRT_NFEAT, MCRT_NHIDDEN = 12, 64
@@ -153,6 +153,8 @@ def load(build_if_missing: bool = True):
         L.mcrt_set_learned_proposal.argtypes = [vp, vp, f32, vp]
         L.mcrt_multigrid_levels.argtypes = [C.c_int, C.c_int, C.c_int]
         L.mcrt_set_spectral_proposal.argtypes = [vp, C.c_int, vp]
+        L.mcrt_probe_ex2.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.mcrt_probe_gather.argtypes = [C.c_int, C.c_uint64, C.POINTER(C.c_double)]
         for f in EXPORTS:
             if f not in _NOT_INT:
                 getattr(L, f).restype = C.c_int
@@ -170,6 +172,20 @@ def _check(rc, ctx=None):
 
 def mcrt_multigrid_levels(nx: int, ny: int, nz: int) -> int:
     return int(load().mcrt_multigrid_levels(nx, ny, nz))
+
+
+def mcrt_probe_ex2(device: int = 0):
+    """(base-2 exponentials per second, mean SM clock in MHz) of the GPU."""
+    r, mhz = C.c_double(), C.c_double()
+    _check(load().mcrt_probe_ex2(int(device), C.byref(r), C.byref(mhz)))
+    return r.value, mhz.value
+
+
+def mcrt_probe_gather(device: int, nbytes: int) -> float:
+    """Random 8-byte loads per second from a buffer of nbytes (a power of two)."""
+    r = C.c_double()
+    _check(load().mcrt_probe_gather(int(device), int(nbytes), C.byref(r)))
+    return r.value
 
 
 def mcrt_create(grid: mcrt_grid_desc) -> C.c_void_p:
@@ -244,19 +260,20 @@ def mcrt_get_stats(ctx) -> dict:
 
 
 def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
-                    scratch_mib: int = 0):
+                    scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0):
     t = mcrt_tuning()
     t.min_blocks_per_sm = min_blocks_per_sm
     t.steps_per_round = steps_per_round
     t.scratch_mib = scratch_mib
+    t.long_ray_steps = long_ray_steps
+    t.long_ray_flight = long_ray_flight
     _check(load().mcrt_set_tuning(ctx, C.byref(t)), ctx)
 
 
 def mcrt_get_tuning(ctx) -> dict:
     t = mcrt_tuning()
     _check(load().mcrt_get_tuning(ctx, C.byref(t)), ctx)
-    return {"min_blocks_per_sm": t.min_blocks_per_sm, "steps_per_round": t.steps_per_round,
-            "scratch_mib": t.scratch_mib}
+    return {f: getattr(t, f) for f, _ in mcrt_tuning._fields_}
 
 
 def mcrt_destroy(ctx):
@@ -543,8 +560,9 @@ class Solver:
         return mcrt_get_stats(self.ctx)
 
     def set_tuning(self, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
-                   scratch_mib: int = 0):
-        mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round, scratch_mib)
+                   scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0):
+        mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round, scratch_mib, long_ray_steps,
+                        long_ray_flight)
 
     def tuning(self) -> dict:
         return mcrt_get_tuning(self.ctx)

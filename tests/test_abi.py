@@ -81,3 +81,25 @@ def test_create_without_gpu_fails_loudly():
     assert mcrt.load().mcrt_create(C.byref(_grid()), C.byref(out)) == mcrt.MCRT_E_CUDA
     with pytest.raises(mcrt.McrtError):
         mcrt.mcrt_create(_grid())
+
+
+def test_probes_validate_arguments_before_touching_a_device():
+    L = mcrt.load()
+    r, m = C.c_double(), C.c_double()
+    assert L.mcrt_probe_ex2(0, None, C.byref(m)) == mcrt.MCRT_E_ARG
+    assert L.mcrt_probe_ex2(0, C.byref(r), None) == mcrt.MCRT_E_ARG
+    for nbytes in (0, 1 << 11, (1 << 20) + 8, 3 << 20, 1 << 36):
+        assert L.mcrt_probe_gather(0, nbytes, C.byref(r)) == mcrt.MCRT_E_ARG, nbytes
+    assert L.mcrt_probe_gather(0, 1 << 20, None) == mcrt.MCRT_E_ARG
+
+
+def test_probes_without_gpu_fail_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(mcrt.McrtError) as e:
+        mcrt.mcrt_probe_ex2(0)
+    assert e.value.status == mcrt.MCRT_E_CUDA
+    with pytest.raises(mcrt.McrtError) as e:
+        mcrt.mcrt_probe_gather(0, 1 << 20)
+    assert e.value.status == mcrt.MCRT_E_CUDA

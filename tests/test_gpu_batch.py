@@ -54,7 +54,8 @@ def _check_runs(b, snaps, solvers, outs, rays, stream, offsets):
             mcrt.mcrt_batch_run(b, offset, stream)
             st = mcrt.mcrt_batch_get_stats(b)
             assert st["rays"] == sum(g.ncells for g, _, _ in snaps) * rays
-            assert st["launches"] == 2  # one trace launch and one reduction for all snapshots
+            # one trace launch, the long-ray march and one reduction for all snapshots
+            assert st["launches"] == 3
             for k, (S, (q, s)) in enumerate(zip(solvers, outs)):
                 qr, sr = S.solve(rays=rays, seed=7, snapshot=10 + k, ray_offset=offset,
                                  precision=mcrt.MCRT_FP32)
@@ -99,9 +100,9 @@ def _run_and_compare(items_spec, params_kw, rays, offsets=(0, 3000)):
 
 
 def test_single_launch_batch_multigrid_stretched_and_cell_proposal():
-    """Snapshots sharing the k-distribution run as one trace launch and one
-    reduction (2 launches), also on the multigrid march, with a stretched
-    snapshot, and with per-cell proposals."""
+    """Snapshots sharing the k-distribution run as one trace launch, the
+    long-ray march and one reduction (3 launches; the multigrid march hands no
+    ray off: 2), also with a stretched snapshot and with per-cell proposals."""
     import torch
     kd = inputs.make_kdist(0)
     spec = []
@@ -112,7 +113,7 @@ def test_single_launch_batch_multigrid_stretched_and_cell_proposal():
             grid.yf = inputs.channel_faces(ny, 2.0, 1.5)
         T, x = inputs.channel_fields(grid, 60 + k, x_mode="field")
         spec.append((grid, kd, T, x, None))
-    assert _run_and_compare(spec, {}, 150) == 2
+    assert _run_and_compare(spec, {}, 150) == 3
     assert _run_and_compare(spec, dict(mg_levels=2, mg_steps=3), 150) == 2
     K = kd.n_bands * kd.n_g
     g = torch.Generator(device="cpu").manual_seed(3)
@@ -122,7 +123,7 @@ def test_single_launch_batch_multigrid_stretched_and_cell_proposal():
         qp[:, :K] /= qp[:, :K].sum(dim=1, keepdim=True)
         qp[:, K] = 0.2 + 0.6 * torch.rand(grid.ncells, generator=g)
         spec_c.append((grid, kd_, T, x, qp.float().cuda()))
-    assert _run_and_compare(spec_c, dict(proposal=mcrt.MCRT_PROPOSAL_CELL), 120) == 2
+    assert _run_and_compare(spec_c, dict(proposal=mcrt.MCRT_PROPOSAL_CELL), 120) == 3
 
 
 def test_mixed_kdist_batch_uses_per_snapshot_launches():

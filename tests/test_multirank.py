@@ -72,3 +72,71 @@ def test_two_gloo_ranks_aggregate_and_shard():
     grid, kd, T, x = inputs.nongrey_channel(6, 6, 5, seed=3)
     full = oracle.solve(grid, kd, T, x, rays=16, seed=2, nthreads=1)
     assert np.array_equal(q_sharded, full["q"])
+
+
+def test_split_snapshots_covers_once_and_balances():
+    from paper_1810_00188_gb300.dist import split_snapshots
+    rng = np.random.default_rng(4)
+    sizes = [32**3, 48 * 64 * 48, 96**3, 128**3]
+    for world in (1, 2, 3, 8):
+        cells = [sizes[i] for i in rng.integers(0, 4, 32)]
+        parts = split_snapshots(cells, world)
+        assert len(parts) == world
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(32))
+        loads = [sum(cells[i] for i in p) for p in parts]
+        assert max(loads) - sum(cells) / world < max(cells)
+        for p in parts:
+            assert all(cells[a] >= cells[b] for a, b in zip(p, p[1:]))
+    assert split_snapshots([], 2) == [[], []]
+    assert split_snapshots([5], 3) == [[0], [], []]
+
+
+def _sharded_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1810_00188_gb300 import dist as pdist
+    from paper_1810_00188_gb300 import inputs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        grid, kd, T, x = inputs.nongrey_channel(6, 6, 5, seed=3, x_mode="field")
+        # only rank 0 holds the field; the others receive it
+        Tt = torch.tensor(T) if rank == 0 else torch.zeros(grid.shape, dtype=torch.float64)
+        xt = torch.tensor(x) if rank == 0 else torch.zeros(grid.shape, dtype=torch.float64)
+
+        def solve_box(Tb, xb, box):
+            r = oracle.solve(grid, kd, Tb.numpy(), xb.numpy(), rays=16, seed=2, box=box, nthreads=1)
+            return torch.tensor(r["q"]), torch.tensor(r["sigma"])
+
+        res = pdist.solve_sharded(solve_box, Tt, xt, grid.shape)
+        if rank == 0:
+            out.put((res[0].numpy(), res[1].numpy()))
+        else:
+            assert res is None
+            assert np.array_equal(Tt.numpy(), T) and np.array_equal(xt.numpy(), x)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_three_gloo_ranks_broadcast_solve_and_gather_uneven_slabs():
+    import oracle
+    from paper_1810_00188_gb300 import inputs
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 3, port, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    qs, ss = q.get(timeout=180)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    grid, kd, T, x = inputs.nongrey_channel(6, 6, 5, seed=3, x_mode="field")
+    full = oracle.solve(grid, kd, T, x, rays=16, seed=2, nthreads=1)
+    # slabs of 1, 2 and 2 z-planes, padded in transit; the union is the full solve
+    assert np.array_equal(qs, full["q"]) and np.array_equal(ss, full["sigma"])

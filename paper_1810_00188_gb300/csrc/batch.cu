@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
   const unsigned *__restrict__ chemi_b = nullptr;
   int reflect_b = 0;
   unsigned snapw_b = 0;
-  unsigned snap_b = 0;  // index of the snapshot being solved
 #define m (BATCH ? (m) : (member))
   long long sp0 = 0, sp1 = BATCH ? 0 : 0x7fffffffffffffffLL;  // positions of this snapshot
   bool pending = false;  // the next claimed position lies in another snapshot
@@ -132,7 +131,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
       // that owns the next claimed position
       const int snap_i = snapshot_of(starts, a.nsnaps, p_next);
       const SnapArgs &sn = a.snaps[snap_i];
-      snap_b = (unsigned)snap_i;
       nx = sn.nx;
       ny = sn.ny;
       nz = sn.nz;
@@ -525,7 +523,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
         L.ix = ix; L.iy = iy; L.iz = iz;
         L.signs = (unsigned)(sx + 1) | ((unsigned)(sy + 1) << 2) | ((unsigned)(sz + 1) << 4);
         L.lin = lin; L.slot = slot; L.r = r; L.ray = ray;
-        L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = snap_b;
+        L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = (unsigned)snapshot_of(starts, a.nsnaps, a.chunk_p0 + slot);
         if (hand_off(a, L)) active = false;
       }
       if (done) {

@@ -543,9 +543,11 @@ def main():
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
             result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
             result["spectral_proposals"] = spectral_extra(S, T, params, q, s, sp)
-            result["learned_vs_plain"] = learned_extra(sp)
             if world == 1:
+                # before the learned-proposal leg, whose datasets stay in torch's cache
                 result["batched_snapshots"] = batch_extra(sp)
+                torch.cuda.empty_cache()
+            result["learned_vs_plain"] = learned_extra(sp)
         if not a.no_cpu_baseline and world == 1:
             result["cpu_baseline"] = cpu_baseline(a)
         print(json.dumps(result), flush=True)

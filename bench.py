@@ -41,6 +41,10 @@ OPS_PER_RAY = 260             # 2 Philox4x32-10 blocks (2 x 80), sampling, direc
                               # origin, DDA set-up, sample store
 GATHER_BYTES_PER_STEP = 8     # FP32 {T, x} of the traversed cell
 GATHERS_PER_STEP = 3          # 8-byte loads per step: {T, x}, the kappa node pair, the B node pair
+# DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel;
+# reported only for that workload
+TRACE_DRAM_BYTES_64_1000 = 26092800 + 1011420672
 
 
 def parse():
@@ -478,7 +482,11 @@ def main():
                   "rays_per_s": rays_all / t_max,
                   "steps_per_ray": steps_total / (a.steps * rays_per_launch),
                   "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                               "unit": "Top/s", "frac": achieved / alu_peak, "traffic": None,
+                               "unit": "Top/s", "frac": achieved / alu_peak,
+                               "traffic": (TRACE_DRAM_BYTES_64_1000 if (a.n, a.rays) == (64, 1000)
+                                           else None),
+                               "traffic_note": "dram read+write bytes of one trace launch (ncu); "
+                                               "the 4 B/ray sample scratch, 1.049e9 B algorithmic",
                                "peak_basis": f"FP32/INT issue: {N_SM} SM x {LANES_PER_SM} lanes x "
                                              f"{sm_max:.0f} MHz, 1 op/lane/clk (derived)",
                                "ops_per_step": OPS_PER_STEP, "ops_per_ray": OPS_PER_RAY,

@@ -167,6 +167,65 @@ def cpu_baseline(a, target_s=12.0):
                       f"{steps:.3g} steps in {dt:.1f} s"}
 
 
+def configs_extra(sp):
+    """The other configurations, GPU beside the FP64 oracle on the host cores (all
+    cores and one core, bounded samples): the grey slab 16x32x16 x 128 rays (FP64
+    and FP32), the 64^3 x 1000-ray channel (oracle only: the main line times the
+    GPU), and the DNS-size 256x192x128 channel x 512 rays with grey walls (GPU:
+    the whole field; oracle: z-planes of the central 32^3 crop, rays through the
+    whole field)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1810_00188_gb300 import inputs, mcrt
+    allc = oracle.default_threads()
+    out = {"oracle_cores": allc}
+
+    def gpu(grid, kd, T, x, rays, prec, seed, tol, reps=2):
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
+        q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+        sg = torch.empty_like(q)
+        best = None
+        for k in range(reps + 1):
+            S.solve_into(S.params(rays=rays, seed=seed, tol=tol, max_steps=1 << 20, precision=prec,
+                                  ray_offset=k * rays), q, sg, stream=sp)
+            st = S.stats()
+            if k and (best is None or st["kernel_ms"] < best["kernel_ms"]):
+                best = st
+        S.close()
+        return {"ms": best["kernel_ms"], "steps_per_s": best["steps"] / (best["kernel_ms"] / 1e3),
+                "rays_per_s": best["rays"] / (best["kernel_ms"] / 1e3)}
+
+    def cpu(grid, kd, T, x, rays, seed, tol, box, threads):
+        t0 = time.perf_counter()
+        r = oracle.solve(grid, kd, T, x, rays=rays, seed=seed, tol=tol, max_steps=1 << 20, box=box,
+                         nthreads=threads)
+        dt = time.perf_counter() - t0
+        steps = float(np.asarray(r["steps"]).sum())
+        return {"steps_per_s": steps / dt, "s": dt, "box": list(box) if box else None}
+
+    # grey slab (E3 case)
+    grid, kd, T, x = inputs.grey_slab_16x32x16(1.0)
+    out["grey_slab_16x32x16_128rays"] = {
+        "gpu_fp64": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP64, 0, 1e-6),
+        "gpu_fp32": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP32, 0, 1e-6),
+        "oracle_all_cores": cpu(grid, kd, T, x, 128, 0, 1e-6, None, allc),
+        "oracle_1_core": cpu(grid, kd, T, x, 128, 0, 1e-6, (0, 16, 0, 32, 0, 2), 1)}
+    # 64^3 channel, one core (the all-core figure is the main line's cpu_baseline)
+    grid, kd, T, x = inputs.nongrey_channel(64, 64, 64, seed=0)
+    out["nongrey_channel_64x64x64_1000rays"] = {
+        "oracle_1_core": cpu(grid, kd, T, x, 1000, 0, 1e-4, (0, 64, 0, 64, 0, 1), 1)}
+    # DNS-size field
+    grid, kd, T, x = inputs.nongrey_channel(256, 192, 128, seed=3, eps_wall=0.8, x_mode="field")
+    out["dns_256x192x128_512rays_grey_walls"] = {
+        "gpu_fp32": gpu(grid, kd, T, x, 512, mcrt.MCRT_FP32, 0, 1e-4, reps=1),
+        "oracle_all_cores": cpu(grid, kd, T, x, 512, 0, 1e-4, (112, 144, 80, 112, 48, 56), allc),
+        "oracle_1_core": cpu(grid, kd, T, x, 512, 0, 1e-4, (112, 144, 80, 112, 48, 49), 1)}
+    return out
+
+
 def batch_extra(sp, rays=256, n=32, seed=0):
     """32 snapshots of uneven grid sizes (32^3, 48x64x48, 96^3, 128^3), 256 rays
     per cell, sharing the k-distribution: one graph launch that holds a single
@@ -525,6 +584,19 @@ def main():
             rf["exp_frac_of_measured_ex2"] = steps_rate / c["ex2_per_s"]
             rf["gather_frac_of_measured_field_gather"] = (steps_rate * GATHERS_PER_STEP
                                                           / c["gather8_per_s"]["field"])
+            # the traversal roofline: the slower of the step's gathers at the measured
+            # random-gather rate (the field's size: L1/L2 resident) and its exponential
+            # at the measured ex2 rate
+            g_bound = c["gather8_per_s"]["field"] / GATHERS_PER_STEP
+            e_bound = c["ex2_per_s"]
+            bound = min(g_bound, e_bound)
+            result["traversal_roofline"] = {
+                "definition": "steps/s bound = min(random 8-byte gathers/s (measured, field-sized "
+                              "buffer) / gathers per step, ex2/s (measured))",
+                "gathers_per_step": GATHERS_PER_STEP, "bound": "gather" if g_bound <= e_bound else "exp",
+                "gather_bound_steps_per_s": g_bound, "exp_bound_steps_per_s": e_bound,
+                "achieved_steps_per_s": steps_rate, "frac": steps_rate / bound,
+                "frac_field_gather_only": steps_rate / c["gather8_per_s"]["field"]}
             S.set_fields(Td, xd)
             # FP64 traversal throughput on a tenth of the rays
             r64 = max(32, a.rays // 10)
@@ -552,6 +624,7 @@ def main():
             result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
             result["spectral_proposals"] = spectral_extra(S, T, params, q, s, sp)
             if world == 1:
+                result["configs"] = configs_extra(sp)
                 # before the learned-proposal leg, whose datasets stay in torch's cache
                 result["batched_snapshots"] = batch_extra(sp)
                 torch.cuda.empty_cache()

@@ -264,9 +264,10 @@ int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q
  * solves many contexts -- snapshots of possibly different grid sizes, each with
  * its k-distribution and fields set -- in one CUDA-graph launch.
  *  - When every item has the same k-distribution (up to 1024 items), the graph
- *    holds ONE persistent FP32 trace launch over all the items' cells and one
- *    per-cell reduction (per scratch chunk: the sample scratch covers the whole
- *    batch when it fits in half the free device memory).  Warps claim runs of
+ *    holds ONE persistent FP32 trace launch over all the items' cells, the
+ *    warp-parallel march of the long rays it hands off, and one per-cell
+ *    reduction (per scratch chunk: the sample scratch covers the whole batch
+ *    when it fits in half the free device memory).  Warps claim runs of
  *    cells of the concatenated snapshots, largest snapshot first; a warp lets
  *    its rays finish before it moves on to another snapshot.  `weights` and
  *    `streams` are not used.
@@ -277,8 +278,10 @@ int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q
  *    kernel's tail overlaps the next one's start; with weights each item gets
  *    that share of one wave (meant for streams = n: all items at once).
  * The solve parameters (FP32 only, whole grids; p->box, p->snapshot,
- * p->ray_offset and p->steps_out are ignored) and the launch shape of
- * items[0].ctx are fixed at creation.  Every item's result equals its own
+ * p->ray_offset and p->steps_out are ignored) and the launch shape and
+ * long-ray thresholds of items[0].ctx are fixed at creation; the items'
+ * contexts should share those thresholds for the next sentence to hold.  Every
+ * item's result equals its own
  * mcrt_solve_qrad with the item's snapshot word, bit for bit. */
 typedef struct mcrt_batch mcrt_batch;
 typedef struct {

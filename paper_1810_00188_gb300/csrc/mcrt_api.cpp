@@ -1288,7 +1288,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     }
   }
   BK(cudaDeviceSynchronize(), "sync");
-  // capture: fork -> branch j runs its items [clear counters, chunks of trace + reduce] -> join
+  // capture: fork -> branch j runs its items [clear counters, chunks of trace (+ long rays) + reduce] -> join
   cudaStream_t s0 = b->streams[0];
   BK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t ce = cudaEventRecord(b->fork, s0);

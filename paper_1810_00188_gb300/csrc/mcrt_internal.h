@@ -139,11 +139,11 @@ cudaError_t launch_coarsen(const double2 *fine, int n0, int n1, int n2, double2 
 
 // Simple kernel: one warp per cell, lane-strided rays (FP64 parity mode).
 cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
-// FP32 kernel with converged initialisation and lane refill (trace_pool.cu).
-// FP32 kernel with converged initialisation and lane refill, then the per-cell
-// reduction (trace_fp32.cu); two launches per chunk.  min_blocks: occupancy
-// target (1-4 CTAs of 256 threads per SM); steps_per_round: march steps between
-// refills of idle lanes (1, 2, 4).
+// FP32 kernel with converged initialisation and lane refill, the warp-parallel
+// march of the long rays it handed off (when long_rays_on), then the per-cell
+// reduction (trace_fp32.cu); two or three launches per chunk.  min_blocks:
+// occupancy target (1-4 CTAs of 256 threads per SM); steps_per_round: march
+// steps between refills of idle lanes (1, 2, 4).
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);

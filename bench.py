@@ -167,6 +167,23 @@ def cpu_baseline(a, target_s=12.0):
                       f"{steps:.3g} steps in {dt:.1f} s"}
 
 
+def field_error(grid, kd, T, x, rays, snapshot, qs, box=None, crop=None):
+    """|Q_gpu - Q_oracle| / S_i over the cells of `box` (the whole grid when None)
+    for each GPU result in qs; crop maps a whole-field result onto the box."""
+    import numpy as np
+
+    import oracle
+    ref = oracle.solve(grid, kd, T, x, rays=rays, seed=0, snapshot=snapshot, tol=1e-4,
+                       max_steps=1 << 20, box=box, nthreads=oracle.default_threads())
+    out = {"rays": rays, "cells": int(ref["q"].size), "tolerance": {"fp32": 1e-4, "fp64": 1e-10}}
+    for name, qg in qs.items():
+        qc = qg if crop is None else qg[crop]
+        e = np.abs(qc - ref["q"]) / np.maximum(ref["scale"], 1e-300)
+        out[name] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                     "mean": float(e.mean())}
+    return out
+
+
 def configs_extra(sp):
     """The other configurations, GPU beside the FP64 oracle on the host cores (all
     cores and one core, bounded samples): the grey slab 16x32x16 x 128 rays (FP64
@@ -182,7 +199,7 @@ def configs_extra(sp):
     allc = oracle.default_threads()
     out = {"oracle_cores": allc}
 
-    def gpu(grid, kd, T, x, rays, prec, seed, tol, reps=2):
+    def gpu(grid, kd, T, x, rays, prec, seed, tol, reps=2, keep=None):
         S = mcrt.Solver(grid, kd)
         S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
         q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
@@ -194,6 +211,10 @@ def configs_extra(sp):
             st = S.stats()
             if k and (best is None or st["kernel_ms"] < best["kernel_ms"]):
                 best = st
+        if keep is not None:  # one more solve on the first ray block, for the error check
+            S.solve_into(S.params(rays=rays, seed=seed, tol=tol, max_steps=1 << 20, precision=prec),
+                         q, sg, stream=sp)
+            keep.append(q.cpu().numpy())
         S.close()
         return {"ms": best["kernel_ms"], "steps_per_s": best["steps"] / (best["kernel_ms"] / 1e3),
                 "rays_per_s": best["rays"] / (best["kernel_ms"] / 1e3)}
@@ -219,10 +240,15 @@ def configs_extra(sp):
         "oracle_1_core": cpu(grid, kd, T, x, 1000, 0, 1e-4, (0, 64, 0, 64, 0, 1), 1)}
     # DNS-size field
     grid, kd, T, x = inputs.nongrey_channel(256, 192, 128, seed=3, eps_wall=0.8, x_mode="field")
+    kept = []
     out["dns_256x192x128_512rays_grey_walls"] = {
-        "gpu_fp32": gpu(grid, kd, T, x, 512, mcrt.MCRT_FP32, 0, 1e-4, reps=1),
+        "gpu_fp32": gpu(grid, kd, T, x, 512, mcrt.MCRT_FP32, 0, 1e-4, reps=1, keep=kept),
         "oracle_all_cores": cpu(grid, kd, T, x, 512, 0, 1e-4, (112, 144, 80, 112, 48, 56), allc),
         "oracle_1_core": cpu(grid, kd, T, x, 512, 0, 1e-4, (112, 144, 80, 112, 48, 49), 1)}
+    # the central 32^3 crop against the oracle, rays through the whole field
+    out["dns_256x192x128_512rays_grey_walls"]["error_vs_oracle_32cubed_crop"] = field_error(
+        grid, kd, T, x, 512, 0, {"fp32": kept[0]}, box=(112, 144, 80, 112, 48, 80),
+        crop=(slice(48, 80), slice(80, 112), slice(112, 144)))
     return out
 
 
@@ -603,6 +629,12 @@ def main():
             S.solve_into(params(0, mcrt.MCRT_FP64, r64), q, s, stream=sp)
             st = S.stats()
             result["fp64_steps_per_s"] = st["steps"] / (st["kernel_ms"] / 1e3)
+            # per-field error of both precisions against the FP64 oracle, draw for draw
+            # (the same rays; |dQ| / S_i with S_i the oracle's mean absolute tally)
+            q64 = q.cpu().numpy()
+            S.solve_into(params(0, mcrt.MCRT_FP32, r64), q, s, stream=sp)
+            q32 = q.cpu().numpy()
+            result["error_vs_oracle"] = field_error(grid, kd, T, x, r64, snap, {"fp64": q64, "fp32": q32})
             # Q_rad solves/s at 1% cell sigma: N* from the 1000-ray sigma, then verified
             S.solve_into(params(0), q, s, stream=sp)
             qn, sn = q.cpu().numpy(), s.cpu().numpy()

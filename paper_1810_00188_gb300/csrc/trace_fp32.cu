@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   // table and field indices are unsigned: widening them to 64-bit addresses is
   // free, while sign-extending an int costs a conversion on GB300's narrow pipe
   unsigned lin = 0, krow = 0, n = 0, slot = 0, r = 0;
+  uint2 fcur = make_uint2(0u, 0u);  // field entry of the current cell, loaded a step ahead
   int ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0;
   unsigned ray = 0, nrefl = 0, cellid = 0;
   float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         steps = 0;
         nrefl = 0;
         active = true;
+        fcur = __ldg(field + lin);
         if (MG) {
           lev = 0;
           lsteps = 0;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       }
       const float ds = fmaxf(tn - tprev, 0.f);
       bool refl = false;  // this step reflected the ray off a wall
-      const uint2 f = __ldg(field + (MG ? loff + lin : lin));
+      const uint2 f = fcur;
       unsigned it;
       float fr;
       tpos(f.x, it, fr);
@@ -487,6 +489,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = 0u;
         if (hand_off(a, L)) active = false;
       }
+      // the next step's field entry, loaded now so that its latency overlaps the
+      // rest of this round
+      if (!done && active) fcur = __ldg(field + (MG ? loff + lin : lin));
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
         Ybuf[(size_t)slot * (unsigned)N + r] = scale * X;  // the ray's sample Y (Eq. 14)

@@ -16,7 +16,11 @@
 //    initialise 32 rays at once into a per-warp ring of prepared states in
 //    shared memory;
 //  * the march advances every active lane by up to KSTEPS cells per round; a lane
-//    whose ray ends stores its sample Y and takes the next prepared state;
+//    whose ray ends stores its sample Y and takes the next prepared state; the
+//    field entry of the next cell is loaded a step ahead;
+//  * a ray that has marched long_steps segments with a long flight ahead (a
+//    grazing ray of a thin band, up to ~10^5 steps) is handed to the
+//    warp-parallel march of long_rays.cu instead of holding its lane to the end;
 //  * samples go to a scratch array indexed by (cell, ray); reduce_cells_kernel
 //    sums each cell's samples in a fixed order (compensated binary32 pairs per
 //    lane, binary64 across lanes), so Q and sigma do not depend on scheduling,

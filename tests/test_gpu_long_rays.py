@@ -154,3 +154,56 @@ def test_batch_with_forced_hand_off_matches_single_solves():
         mcrt.mcrt_batch_destroy(b)
     for S in solvers:
         S.close()
+
+
+def test_forced_hand_off_with_a_cell_proposal():
+    """Per-cell (n, g) and hemisphere proposals: the ray weight is fixed at set-up,
+    so the handed-off rays carry it; both reflection laws, against the oracle."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(12, 16, 10, seed=57, eps_wall=0.5, x_mode="field")
+    K = kd.n_bands * kd.n_g
+    g = torch.Generator(device="cpu").manual_seed(9)
+    qp = torch.rand((grid.ncells, K + 2), generator=g) ** 4 + 1e-3
+    qp[:, :K] /= qp[:, :K].sum(dim=1, keepdim=True)
+    qp[:, K] = 0.15 + 0.7 * torch.rand(grid.ncells, generator=g)
+    for reflect in (0, 1):
+        grid.reflect = reflect
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(T, x)
+        S.set_cell_proposal_probs(qp.float().cuda())
+        S.set_tuning(long_ray_steps=4, long_ray_flight=-1)
+        cn, cg, hemi = S.cell_proposal()
+        box = (0, 12, 0, 16, 2, 5)
+        sel = [i + 12 * (j + 16 * k) for k in range(2, 5) for j in range(16) for i in range(12)]
+        prop = (cn.reshape(grid.ncells, kd.n_bands)[sel], cg.reshape(grid.ncells, K)[sel], hemi[sel])
+        o = oracle.solve(grid, kd, T, x, rays=64, seed=6, box=box, proposal=prop)
+        q, _ = S.solve(box=box, rays=64, seed=6, precision=mcrt.MCRT_FP32,
+                       proposal=mcrt.MCRT_PROPOSAL_CELL)
+        st = S.stats()
+        S.close()
+        assert st["long_rays"] > 0 and st["long_overflow"] == 0
+        assert np.all(np.abs(q - o["q"]) <= RTOL * o["scale"] + 1e-300), reflect
+
+
+def test_hand_off_stays_off_where_it_does_not_apply():
+    """Multigrid marches, closed boxes and the FP64 parity mode hand nothing off
+    (and launch no long-ray kernel), whatever the thresholds."""
+    grid, kd, T, x = inputs.nongrey_channel(24, 24, 12, seed=58, x_mode="field")
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    S.set_tuning(long_ray_steps=4, long_ray_flight=-1)
+    S.solve(rays=32, seed=1, mg_levels=3, mg_steps=3)
+    st = S.stats()
+    assert st["long_rays"] == 0 and st["launches"] == 2
+    S.solve(rays=16, seed=1, precision=mcrt.MCRT_FP64)
+    st = S.stats()
+    assert st["long_rays"] == 0 and st["launches"] == 1
+    S.close()
+    grid, kd, T, x = inputs.sin_cube(12, 0.5)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(T, x)
+    S.set_tuning(long_ray_steps=4, long_ray_flight=-1)
+    S.solve(rays=32, seed=1)
+    st = S.stats()
+    assert st["long_rays"] == 0 and st["launches"] == 2
+    S.close()

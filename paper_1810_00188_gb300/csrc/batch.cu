@@ -407,15 +407,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           ix += mx ? sx : 0;
           iy += my ? sy : 0;
           iz += mz ? sz : 0;
-          if (yfs && my && iy >= 0 && iy < nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
-          lin += mx ? (unsigned)sx : (my ? (unsigned)(sy * nxl) : (unsigned)(sz * nxyl));
-          const int wx = ix >= nxl ? -nxl : (ix < 0 ? nxl : 0);
+          if (yfs && my && (unsigned)iy < (unsigned)nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
+          const int wx = (unsigned)ix < (unsigned)nxl ? 0 : (ix < 0 ? nxl : -nxl);
           ix += wx;
-          lin += (unsigned)wx;
-          const int wz = iz >= nzl ? -nzl : (iz < 0 ? nzl : 0);
+          const int wz = (unsigned)iz < (unsigned)nzl ? 0 : (iz < 0 ? nzl : -nzl);
           iz += wz;
-          lin += (unsigned)(wz * nxyl);
-          if (iy < 0 || iy >= nyl) {
+          // the linear index from the three indices (multiply-adds, off the ALU pipe)
+          lin = (unsigned)(ix + nxl * (iy + nyl * iz));
+          if ((unsigned)iy >= (unsigned)nyl) {
             // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
             const int wl = iy < 0 ? 0 : 1;
             const float eps = wl ? eps1 : eps0;

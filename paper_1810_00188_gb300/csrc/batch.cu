@@ -368,7 +368,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
         tn = tnz;
       }
       const float ds = fmaxf(tn - tprev, 0.f);
-      bool refl = false;  // this step reflected the ray off a wall
       const uint2 f = fcur;
       unsigned it;
       float fr;
@@ -408,9 +407,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           iy += my ? sy : 0;
           iz += mz ? sz : 0;
           if (yfs && my && (unsigned)iy < (unsigned)nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
-          const int wx = (unsigned)ix < (unsigned)nxl ? 0 : (ix < 0 ? nxl : -nxl);
+          // periodic wrap: an index can only leave the grid in the ray's direction
+          const int wx = (unsigned)ix < (unsigned)nxl ? 0 : -sx * nxl;
           ix += wx;
-          const int wz = (unsigned)iz < (unsigned)nzl ? 0 : (iz < 0 ? nzl : -nzl);
+          const int wz = (unsigned)iz < (unsigned)nzl ? 0 : -sz * nzl;
           iz += wz;
           // the linear index from the three indices (multiply-adds, off the ALU pipe)
           lin = (unsigned)(ix + nxl * (iy + nyl * iz));
@@ -465,7 +465,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
                 ddz = sr * sp;
               }
               ++nrefl;
-              refl = true;
               axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
               axis_setup(ddy, nfy, yfs ? dyl(iy, MG ? lev : 0) : gl * DY, sy, t0y, tsy);
               axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
@@ -510,11 +509,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           lsteps = 0;
         }
       }
-      if (!MG && !done && steps >= a.long_steps && (steps == a.long_steps || ax == 1 || refl) &&
+      if (!MG && !done && steps >= a.long_steps && (steps == a.long_steps || ax == 1) &&
           long_flight(tny, tprev, tsx, tsz, a.long_flight)) {
         // a long flight ahead (a grazing ray of a thin band): the warp-parallel
         // march of long_rays.cu finishes this ray; checked when the ray reaches
-        // long_steps segments and at each later y face and reflection
+        // long_steps segments and at each later y face (a reflection is one)
         LongRay L;
         L.t0x = t0x; L.t0y = t0y; L.t0z = t0z; L.tsx = tsx;
         L.tsy = tsy; L.tsz = tsz; L.cntx = cntx; L.cnty = cnty;

@@ -114,13 +114,26 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
 // false for positions outside the box (ragged edge bricks).
 __device__ __forceinline__ bool brick_cell_d(int bnx, int bny, int bnz, long long p, int &bx, int &by,
                                              int &bz) {
-  const int nbx = (bnx + BRICK - 1) / BRICK, nby = (bny + BRICK - 1) / BRICK;
-  const long long brick = p / (BRICK * BRICK * BRICK);
-  const int off = (int)(p - brick * (BRICK * BRICK * BRICK));
-  const int gx = (int)(brick % nbx), gy = (int)((brick / nbx) % nby), gz = (int)(brick / ((long long)nbx * nby));
-  bx = gx * BRICK + off % BRICK;
-  by = gy * BRICK + (off / BRICK) % BRICK;
-  bz = gz * BRICK + off / (BRICK * BRICK);
+  const unsigned nbx = (unsigned)(bnx + BRICK - 1) / BRICK, nby = (unsigned)(bny + BRICK - 1) / BRICK;
+  unsigned off, gx, gy, gz;
+  if (p < (1LL << 31)) {
+    // 32-bit arithmetic: boxes of fewer than 2^31 positions (64-bit divisions
+    // are long instruction sequences)
+    const unsigned pu = (unsigned)p, brick = pu / (BRICK * BRICK * BRICK), t = brick / nbx;
+    off = pu % (BRICK * BRICK * BRICK);
+    gx = brick - t * nbx;
+    gy = t % nby;
+    gz = t / nby;
+  } else {
+    const long long brick = p / (BRICK * BRICK * BRICK);
+    off = (unsigned)(p - brick * (BRICK * BRICK * BRICK));
+    gx = (unsigned)(brick % nbx);
+    gy = (unsigned)((brick / nbx) % nby);
+    gz = (unsigned)(brick / ((long long)nbx * nby));
+  }
+  bx = (int)(gx * BRICK + off % BRICK);
+  by = (int)(gy * BRICK + (off / BRICK) % BRICK);
+  bz = (int)(gz * BRICK + off / (BRICK * BRICK));
   return bx < bnx && by < bny && bz < bnz;
 }
 

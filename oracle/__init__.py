@@ -440,7 +440,8 @@ def adam(theta, grad, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def learned_counts(q, nb, ng, q_up):
     """Integer proposal (cn [nb], cg [nb, ng], hemi) of one cell from its
-    probabilities q [nb * ng] and q_up."""
+    probabilities q [nb * ng] and q_up (counts decided in binary32, the rule of
+    the device's per-cell proposals)."""
     q = _f64(q).reshape(-1)
     cn = np.zeros(nb, dtype=np.uint64)
     cg = np.zeros(nb * ng, dtype=np.uint64)

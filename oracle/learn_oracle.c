@@ -390,37 +390,77 @@ void orc_adam(double *theta, const double *grad, double *m1, double *m2, int64_t
 
 /* ---- per-cell integer proposal from probabilities ---------------------------
  * q [n_b n_g] (spectral points, band-major), q_up the upward-hemisphere
- * probability.  Band weights are the sums over g (in order of g); bands and the
- * g points inside each band are quantised to counts of 2^32 by orc_quantize (a
- * point with positive weight keeps at least one count; the rounding remainder
- * goes to the first largest weight); a band whose g weights are all zero gets
- * uniform g counts (it is never drawn).  The hemisphere count of 2^23 is
- * q_up 2^23 rounded half up, kept in [1, 2^23 - 1]. */
+ * probability.  The counts of a per-cell proposal are decided in binary32: each
+ * probability is rounded to binary32; a band's weight is the binary32 sum of
+ * its points in order of g; bands and the g points inside each band are
+ * quantised to counts of 2^32 by quantize_f32 (count = floor(RN32(w / W) 2^32)
+ * with W the binary32 sum of the weights in order; a point with positive weight
+ * keeps at least one count; the rounding remainder goes to the first largest
+ * weight); a band whose g weights are all zero gets uniform g counts (it is
+ * never drawn).  The hemisphere count of 2^23 is q_up 2^23 rounded half up in
+ * binary64, kept in [1, 2^23 - 1].  The plain proposal (orc_plain_proposal)
+ * keeps the binary64 rule of orc_quantize. */
+static int64_t count_f32(float w, float W) {
+  const float y = (w / W) * 4294967296.0f; /* correctly rounded quotient, exact scaling */
+  if (y >= 4294967296.0f) return 4294967296LL;
+  return (int64_t)(uint32_t)y;             /* y >= 0: truncation is the floor */
+}
+
+static int quantize_f32(const float *w, int K, uint64_t *cum) {
+  float W = 0.f;
+  for (int k = 0; k < K; ++k) W += w[k];
+  if (!(W > 0.f)) return -1;
+  int kmax = 0;
+  for (int k = 1; k < K; ++k)
+    if (w[k] > w[kmax]) kmax = k;
+  int64_t total = 0;
+  for (int k = 0; k < K; ++k) {
+    int64_t m = 0;
+    if (w[k] > 0.f) {
+      m = count_f32(w[k], W);
+      if (m < 1) m = 1;
+    }
+    cum[k] = (uint64_t)m;
+    total += m;
+  }
+  cum[kmax] += (uint64_t)(4294967296LL - total);
+  uint64_t acc = 0;
+  for (int k = 0; k < K; ++k) {
+    acc += cum[k];
+    cum[k] = acc;
+  }
+  return 0;
+}
+
 int orc_learned_counts(const double *q, int nb, int ng, double q_up, uint64_t *cn, uint64_t *cg,
                        uint32_t *hemi) {
-  double *wn = (double *)malloc(sizeof(double) * nb);
-  double *u = (double *)malloc(sizeof(double) * ng);
-  if (!wn || !u) {
+  float *wn = (float *)malloc(sizeof(float) * nb);
+  float *qf = (float *)malloc(sizeof(float) * (size_t)nb * ng);
+  float *u = (float *)malloc(sizeof(float) * ng);
+  if (!wn || !qf || !u) {
     free(wn);
+    free(qf);
     free(u);
     return -1;
   }
+  for (size_t i = 0; i < (size_t)nb * ng; ++i) qf[i] = (float)q[i];
   int rc = 0;
   for (int n = 0; n < nb && rc == 0; ++n) {
-    double s = 0.0;
-    for (int g = 0; g < ng; ++g) s += q[(size_t)n * ng + g];
+    float s = 0.f;
+    for (int g = 0; g < ng; ++g) s += qf[(size_t)n * ng + g];
     wn[n] = s;
-    if (orc_quantize(q + (size_t)n * ng, ng, cg + (size_t)n * ng) != 0) {
-      for (int g = 0; g < ng; ++g) u[g] = 1.0;
-      rc = orc_quantize(u, ng, cg + (size_t)n * ng);
+    if (quantize_f32(qf + (size_t)n * ng, ng, cg + (size_t)n * ng) != 0) {
+      for (int g = 0; g < ng; ++g) u[g] = 1.f;
+      rc = quantize_f32(u, ng, cg + (size_t)n * ng);
     }
   }
-  if (rc == 0) rc = orc_quantize(wn, nb, cn);
+  if (rc == 0) rc = quantize_f32(wn, nb, cn);
   double hq = floor(q_up * 8388608.0 + 0.5);
   if (!(hq >= 1.0)) hq = 1.0;
   if (hq > 8388607.0) hq = 8388607.0;
   *hemi = (uint32_t)hq;
   free(wn);
+  free(qf);
   free(u);
   return rc;
 }

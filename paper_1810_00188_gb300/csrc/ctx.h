@@ -44,6 +44,8 @@ struct mcrt_ctx {
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   // learned proposal: plain probabilities, feature scratch, per-ray steps, error flag
   DevBuf p0_32, feat, ray_steps, lerr, kptab;
+  // learned proposal: network outputs of one chunk of cells, before quantisation
+  DevBuf qprop;
   // stretched grid: faces in FP64 and FP32
   DevBuf yf64, yf32;
   // long rays handed off by the FP32 exact march (LongRay entries)

@@ -224,23 +224,30 @@ __global__ void __launch_bounds__(TALLY_WARPS * 32) tally_kernel(const TallyArgs
 // ---- integer proposal of one cell ------------------------------------------------
 // Counts of 2^32 proportional to the weights, at least one for every positive
 // weight, the rounding remainder on the first largest weight; W is the sum of
-// the weights in order (the same rule, in FP64, as the host's plain proposal).
+// the weights in order.  Per-cell proposals take this decision in binary32 (the
+// host's plain proposal takes it once, in binary64): count = floor(RN(w / W)
+// 2^32) with a correctly rounded binary32 quotient (the scaling by 2^32 is
+// exact).  GB300 issues binary64 on a narrow pipe, and a proposal has 360
+// counts per cell.
+__device__ __forceinline__ long long count32(float w, float W) {
+  const float y = __fdiv_rn(w, W) * 4294967296.0f;
+  return y >= 4294967296.0f ? 4294967296LL : (long long)(unsigned)y;  // y >= 0: truncation is the floor
+}
 
-template <class T>
-__device__ bool quantize_row(const T *w, int K, double W, unsigned long long *cum) {
-  if (!(W > 0.0)) return false;
+__device__ bool quantize_row(const float *w, int K, float W, unsigned long long *cum) {
+  if (!(W > 0.f)) return false;
   int kmax = 0;
-  double wmax = (double)w[0];
+  float wmax = w[0];
   long long total = 0;
   for (int k = 0; k < K; ++k) {  // counts (kept in cum), their total, the first largest weight
-    const double wk = (double)w[k];
+    const float wk = w[k];
     if (wk > wmax) {
       wmax = wk;
       kmax = k;
     }
     long long mk = 0;
-    if (wk > 0.0) {
-      mk = (long long)floor((wk / W) * 4294967296.0);
+    if (wk > 0.f) {
+      mk = count32(wk, W);
       mk = mk < 1 ? 1 : mk;
     }
     cum[k] = (unsigned long long)mk;
@@ -256,25 +263,24 @@ __device__ bool quantize_row(const T *w, int K, double W, unsigned long long *cu
 
 // Warp-cooperative: q [nb * ng] spectral probabilities and q_up of one cell ->
 // cumulative band counts cn [nb], g counts within each band cg [nb][ng], and the
-// upward-hemisphere count of 2^23.  wn: nb doubles of scratch.  The band weights
-// are summed in band order on one lane (the same FP64 sum as the host's); the
-// counts, their exact integer total and the first largest weight are formed
-// across lanes.
+// upward-hemisphere count of 2^23.  wn: nb doubles of scratch (each holding a
+// binary32 band weight).  Each band's weight is the binary32 sum of its points in
+// order of g, the total the binary32 sum of the band weights in band order on
+// one lane; the counts, their exact integer total and the first largest weight
+// are formed across lanes.
 __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double *wn,
                               unsigned long long *cn, unsigned long long *cg, unsigned *hemi,
                               unsigned long long *err) {
   const int lane = threadIdx.x & 31;
   for (int n = lane; n < nb; n += 32) {
     const float *qn = q + (size_t)n * ng;
-    double W = 0.0;
-    for (int g = 0; g < ng; ++g) W += (double)qn[g];
-    wn[n] = W;
+    float W = 0.f;
+    for (int g = 0; g < ng; ++g) W += qn[g];
+    wn[n] = (double)W;
     if (!quantize_row(qn, ng, W, cg + (size_t)n * ng)) {
       // a band that is never drawn gets uniform g counts (weights 1, so the
       // remainder goes to g = 0)
-      double Wu = 0.0;
-      for (int g = 0; g < ng; ++g) Wu += 1.0;
-      const long long mk = (long long)floor((1.0 / Wu) * 4294967296.0);
+      const long long mk = count32(1.f, (float)ng);
       unsigned long long acc = 0;
       for (int g = 0; g < ng; ++g) {
         acc += (unsigned long long)(g == 0 ? mk + (4294967296LL - mk * ng) : mk);
@@ -283,25 +289,25 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
     }
   }
   __syncwarp();
-  double W = 0.0;
+  float W = 0.f;
   if (lane == 0)
-    for (int n = 0; n < nb; ++n) W += wn[n];
+    for (int n = 0; n < nb; ++n) W += (float)wn[n];
   W = __shfl_sync(0xffffffffu, W, 0);
-  if (!(W > 0.0)) {
+  if (!(W > 0.f)) {
     if (lane == 0) atomicOr(err, 2ull);
   } else {
     long long tot = 0;
-    double bw = -1.0;
+    float bw = -1.f;
     int bk = nb;
     for (int n = lane; n < nb; n += 32) {
-      const double w = wn[n];
+      const float w = (float)wn[n];
       if (w > bw) {
         bw = w;
         bk = n;
       }
       long long mk = 0;
-      if (w > 0.0) {
-        mk = (long long)floor((w / W) * 4294967296.0);
+      if (w > 0.f) {
+        mk = count32(w, W);
         mk = mk < 1 ? 1 : mk;
       }
       cn[n] = (unsigned long long)mk;
@@ -310,7 +316,7 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      const double ow = __shfl_xor_sync(0xffffffffu, bw, o);
+      const float ow = __shfl_xor_sync(0xffffffffu, bw, o);
       const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
       if (ow > bw || (ow == bw && ok < bk)) {
         bw = ow;

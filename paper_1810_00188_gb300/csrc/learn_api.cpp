@@ -578,18 +578,30 @@ int mcrt_set_learned_proposal(mcrt_ctx *ctx, mcrt_mlp *m, float mix, void *strea
   a.fmean = (const float *)m->nrm.p;
   a.finv = a.fmean + MCRT_NFEAT;
   a.K = m->K;
-  a.feat = (const float *)ctx->feat.p;
-  a.n = nc;
   a.p0 = (const float *)ctx->p0_32.p;
   a.p0_stride = 0;
   a.mix = mix;
-  a.cell_cn = (unsigned long long *)ctx->cell_cn.p;
-  a.cell_cg = (unsigned long long *)ctx->cell_cg.p;
-  a.cell_hemi = (unsigned *)ctx->cell_hemi.p;
   a.nb = ctx->nb;
   a.ng = ctx->ng;
   a.err = (unsigned long long *)ctx->lerr.p;
-  CK(mcrt::launch_mlp_infer(a, s), "network");
+  // the network's probabilities for a chunk of cells, then their integer
+  // proposal: the FP64 quantisation runs in its own kernel, with more warps per
+  // SM than the network's shared-memory tiles allow
+  const long long chunk = nc < (1LL << 20) ? nc : (1LL << 20);
+  const long long K = m->K, KO = K + 2;
+  CK(ensure(ctx->qprop, (size_t)chunk * KO * sizeof(float)), "alloc network outputs");
+  for (long long c0 = 0; c0 < nc; c0 += chunk) {
+    const long long cnum = nc - c0 < chunk ? nc - c0 : chunk;
+    a.feat = (const float *)ctx->feat.p + c0 * MCRT_NFEAT;
+    a.n = cnum;
+    a.q_out = (float *)ctx->qprop.p;
+    CK(mcrt::launch_mlp_infer(a, s), "network");
+    CK(mcrt::launch_quantize_cells((const float *)ctx->qprop.p, cnum, ctx->nb, ctx->ng,
+                                   (unsigned long long *)ctx->cell_cn.p + c0 * ctx->nb,
+                                   (unsigned long long *)ctx->cell_cg.p + c0 * K,
+                                   (unsigned *)ctx->cell_hemi.p + c0, (unsigned long long *)ctx->lerr.p, s),
+       "quantise");
+  }
   unsigned long long flag = 0;
   rc = read_lerr(ctx, s, &flag);
   if (rc != MCRT_OK) return rc;

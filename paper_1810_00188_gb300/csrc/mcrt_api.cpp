@@ -744,7 +744,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
-                      &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr, &ctx->kptab};
+                      &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr, &ctx->kptab, &ctx->qprop};
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -482,10 +482,63 @@ __device__ void forward_tile(const MlpSmem &S, int K, const float *X, float *A1,
   __syncthreads();
 }
 
-size_t infer_smem_bytes(int K, int nb) {
+// Inference form of forward_tile (same sums in the same order, so the same
+// bits): the two 64-wide layers are blocked over CB cells, each thread holding
+// CB accumulators of one output column, so a weight read from shared memory
+// serves CB cells and the activations are broadcast reads.
+template <int T>
+__device__ void forward_tile_infer(const MlpSmem &S, int K, const float *X, float *H1, float *H2,
+                                   float *Z) {
+  constexpr int CB = 4;
+  static_assert(T % CB == 0, "cell blocks");
+  const int ldo = ldo_halves(K);
+  for (int e = threadIdx.x; e < T * NH; e += blockDim.x) {
+    const int c = e / NH, o = e % NH;
+    float a = S.b1[o];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) a += __half2float(S.W1T[i * NH + o]) * X[c * NF + i];
+    H1[e] = gelu(a);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (T / CB) * NH; e += blockDim.x) {
+    const int cb = e / NH, o = e % NH;
+    float acc[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) acc[j] = S.b2[o];
+    const float *h = H1 + (size_t)cb * CB * NH;
+#pragma unroll 4
+    for (int i = 0; i < NH; ++i) {
+      const float w = __half2float(S.W2T[i * NH + o]);
+#pragma unroll
+      for (int j = 0; j < CB; ++j) acc[j] += w * h[j * NH + i];
+    }
+#pragma unroll
+    for (int j = 0; j < CB; ++j) H2[(cb * CB + j) * NH + o] = gelu(acc[j]);
+  }
+  __syncthreads();
+  const int KO = K + 2;
+  for (int e = threadIdx.x; e < (T / CB) * KO; e += blockDim.x) {
+    const int cb = e / KO, o = e % KO;
+    float acc[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) acc[j] = S.b3[o];
+    const float *h = H2 + (size_t)cb * CB * NH;
+#pragma unroll 4
+    for (int i = 0; i < NH; ++i) {
+      const float w = __half2float(S.W3T[i * ldo + o]);
+#pragma unroll
+      for (int j = 0; j < CB; ++j) acc[j] += w * h[j * NH + i];
+    }
+#pragma unroll
+    for (int j = 0; j < CB; ++j) Z[(size_t)(cb * CB + j) * KO + o] = acc[j];
+  }
+  __syncthreads();
+}
+
+size_t infer_smem_bytes(int K) {
   const size_t halves = (size_t)NF * NH + NH * NH + (size_t)NH * ldo_halves(K);
   const size_t floats = 2 * NH + (K + 2) + IT * NF + 2 * IT * NH + (size_t)IT * (K + 2) + K + 2 * NF;
-  return ((halves * 2 + 15) / 16) * 16 + floats * 4 + (size_t)(NTHR / 32) * nb * 8 + 64;
+  return ((halves * 2 + 15) / 16) * 16 + floats * 4 + 64;
 }
 
 __global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
@@ -506,7 +559,6 @@ __global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
   float *H1 = X + IT * NF, *H2 = H1 + IT * NH, *Z = H2 + IT * NH;
   float *p0s = Z + (size_t)IT * KO;
   float *nrm = p0s + K;  // fmean [12], finv [12]
-  double *wn = reinterpret_cast<double *>((reinterpret_cast<size_t>(nrm + 2 * NF) + 7) & ~(size_t)7);
   load_weights(a.theta16, K, S, false);
   for (int e = threadIdx.x; e < NF; e += blockDim.x) {
     nrm[e] = a.fmean[e];
@@ -525,7 +577,7 @@ __global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
       X[e] = c < rows ? (a.feat[(t0 + c) * NF + i] - nrm[i]) * nrm[NF + i] : 0.f;
     }
     __syncthreads();
-    forward_tile<IT>(S, K, X, nullptr, H1, nullptr, H2, Z);
+    forward_tile_infer<IT>(S, K, X, H1, H2, Z);
     // softmax over the spectral logits and the hemisphere pair, then the mixture
     for (int c = w; c < rows; c += NTHR / 32) {
       float *z = Z + (size_t)c * KO;
@@ -548,11 +600,7 @@ __global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
         z[K + 1] = (1.f - a.mix) * (ed / (eu + ed)) + a.mix * 0.5f;
       }
       __syncwarp();
-      if (a.q_out)
-        for (int k = lane; k < KO; k += 32) a.q_out[(t0 + c) * KO + k] = z[k];
-      if (a.cell_cn)
-        quantize_cell(z, z[K], a.nb, a.ng, wn + (size_t)w * a.nb, a.cell_cn + (t0 + c) * a.nb,
-                      a.cell_cg + (t0 + c) * (long long)K, a.cell_hemi + (t0 + c), a.err);
+      for (int k = lane; k < KO; k += 32) a.q_out[(t0 + c) * KO + k] = z[k];
     }
     __syncthreads();
   }
@@ -945,11 +993,15 @@ cudaError_t launch_tally(const TallyArgs &t, cudaStream_t s) {
 
 cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t smem = infer_smem_bytes(a.K, a.nb > 0 ? a.nb : 1);
+  const size_t smem = infer_smem_bytes(a.K);
   cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  mlp_infer_kernel<<<grid_for(a.n, IT, 1), NTHR, smem, s>>>(a);
+  // as many resident CTAs per SM as shared memory allows (two at K = 320)
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, NTHR, smem);
+  if (e != cudaSuccess) return e;
+  mlp_infer_kernel<<<grid_for(a.n, IT, per_sm > 0 ? per_sm : 1), NTHR, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -243,10 +243,7 @@ struct MlpInferArgs {
   const float *p0;            // [K] (p0_stride 0) or [n][K]
   int p0_stride;
   float mix;
-  float *q_out;               // [n][K+2] or null
-  // or quantised straight into a per-cell proposal (cells 0..n-1)
-  unsigned long long *cell_cn, *cell_cg;
-  unsigned *cell_hemi;
+  float *q_out;               // [n][K+2]: probabilities (spectral points, then the hemispheres)
   int nb, ng;
   unsigned long long *err;
 };

@@ -483,13 +483,13 @@ __device__ void forward_tile(const MlpSmem &S, int K, const float *X, float *A1,
 }
 
 // Inference form of forward_tile (same sums in the same order, so the same
-// bits): the two 64-wide layers are blocked over CB cells, each thread holding
+// bits): the two 64-wide layers are blocked over CB = 8 cells, each thread holding
 // CB accumulators of one output column, so a weight read from shared memory
 // serves CB cells and the activations are broadcast reads.
 template <int T>
 __device__ void forward_tile_infer(const MlpSmem &S, int K, const float *X, float *H1, float *H2,
                                    float *Z) {
-  constexpr int CB = 4;
+  constexpr int CB = 8;
   static_assert(T % CB == 0, "cell blocks");
   const int ldo = ldo_halves(K);
   for (int e = threadIdx.x; e < T * NH; e += blockDim.x) {

@@ -44,7 +44,7 @@ GATHERS_PER_STEP = 3          # 8-byte loads per step: {T, x}, the kappa node pa
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel;
 # reported only for that workload
-TRACE_DRAM_BYTES_64_1000 = 26733568 + 1011609088
+TRACE_DRAM_BYTES_64_1000 = 26761728 + 1011770112
 
 
 def parse():

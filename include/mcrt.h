@@ -247,9 +247,13 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
  *  - The first call on a device looks up the array's device address on that
  *    device (cudaGetSymbolAddress); make that first call before any stream
  *    capture.
+ *  - 8 MiB of the array holds the long rays handed to the warp-parallel march
+ *    (2^16 entries, the least buffer of a regular solve), so the results equal
+ *    mcrt_solve_qrad's bit for bit unless more rays than that are handed off.
  *  - Large boxes run in several launches, each holding as many cells' samples as
- *    fit; rays_per_cell above what one cell's samples can hold in 64 MiB (about
- *    16.7 million) is rejected with MCRT_E_ARG and a message giving the limit.
+ *    fit; rays_per_cell above what one cell's samples can hold in the rest of the
+ *    array (about 14.6 million) is rejected with MCRT_E_ARG and a message giving
+ *    the limit.
  *  - Every call shares the array and leaves the last call's contents in it (the
  *    counters and step sums are cleared at the start of each call); calls whose
  *    work overlaps on the GPU -- on different streams of one device -- race and

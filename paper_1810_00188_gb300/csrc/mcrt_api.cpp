@@ -829,9 +829,13 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz))
     return fail(ctx, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)]");
   if (p->mg_levels > 1 && p->mg_steps < 1) return fail(ctx, MCRT_E_ARG, "mg_steps < 1");
-  // scratch layout in the static array: counters | per-position step sums | samples
+  // scratch layout in the static array: counters | long rays | per-position step
+  // sums | samples.  The long-ray region holds the smallest buffer a regular
+  // solve uses, so both hand the same rays off and give the same bits.
   const size_t total = mcrt::noalloc_scratch_bytes();
-  const size_t head_bytes = 256;
+  const bool long_on = ctx->long_steps > 0 && p->mg_levels <= 1 && !ctx->grid.xz_walls;
+  const long long long_cap = long_on ? 65536 : 0;  // the least capacity of a regular solve's buffer (8 MiB)
+  const size_t head_bytes = 256 + (size_t)long_cap * sizeof(mcrt::LongRay);
   const size_t per_pos = (size_t)p->rays_per_cell * sizeof(float) + sizeof(unsigned long long);
   if (total < head_bytes + 256 + per_pos)
     return fail(ctx, MCRT_E_ARG,
@@ -931,6 +935,10 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   if (Pc > P) Pc = P;
   unsigned char *cbase = (unsigned char *)base;
   a.counters = (unsigned long long *)cbase;
+  a.long_rays = long_on ? (mcrt::LongRay *)(cbase + 256) : nullptr;
+  a.long_cap = (int)long_cap;
+  a.long_steps = long_on ? ctx->long_steps : 0x7fffffff;
+  a.long_flight = ctx->long_flight;
   a.step_acc = (unsigned long long *)(cbase + head_bytes);
   const size_t ybuf_off = (head_bytes + (size_t)Pc * sizeof(unsigned long long) + 255) & ~(size_t)255;
   a.ybuf = (float *)(cbase + ybuf_off);

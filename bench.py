@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--rays", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--long-ray-steps", type=int, default=0,
+                    help="hand-off threshold in segments (0: the library default, < 0: off)")
+    ap.add_argument("--long-ray-flight", type=int, default=0,
+                    help="x/z crossings left for a hand-off (0: the library default, < 0: any)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="weak: one snapshot per rank; strong: one snapshot split over the ranks")
     return ap.parse_args()
@@ -69,7 +73,8 @@ def workload_config(a):
             "walls": "black, 500 K / 1000 K", "x_h2o": 0.1,
             "T_field": "linear 500->1000 K + 5% k^-5/3 Gaussian random field",
             "precision": "fp32 traversal, fp64 compensated tallies",
-            "l2": "flushed between timed steps (256 MiB write)", "seed": 0}
+            "l2": "flushed between timed steps (256 MiB write)", "seed": 0,
+            "long_ray_hand_off": {"steps": a.long_ray_steps or 1024, "flight": a.long_ray_flight or 32}}
 
 
 class Clocks:
@@ -492,6 +497,8 @@ def main():
     snap = 0 if a.scaling == "strong" else rank
     grid, kd, T, x = inputs.nongrey_channel(a.n, a.n, a.n, seed=snap)
     S = mcrt.Solver(grid, kd, device=local)
+    if a.long_ray_steps or a.long_ray_flight:
+        S.set_tuning(long_ray_steps=a.long_ray_steps, long_ray_flight=a.long_ray_flight)
     Td = torch.tensor(T, device="cuda")
     xd = torch.tensor(x, device="cuda")
     boxes = pdist.shard_boxes(grid.nx, grid.ny, grid.nz, world)

@@ -94,8 +94,17 @@ typedef struct {
   double T0, dT;           /* dT > 0                                              */
   int nT;                  /* >= 2                                                */
   const double *kappa;     /* [n_bands][n_g][nT] [1/m] at x_ref, finite, >= 0     */
-  const double *B;         /* [n_bands][nT] band intensity [W m^-2 sr^-1], >= 0   */
+  const double *B;         /* [n_bands][nT] band intensity [W m^-2 sr^-1], >= 0;
+                              NULL: the library computes it from nu_c and dnu   */
   double x_ref;            /* > 0                                                 */
+  const double *nu_c;      /* [n_bands] band centres [1/cm], > 0; read only when
+                              B is NULL                                          */
+  const double *dnu;       /* [n_bands] band widths [1/cm], > 0; read only when
+                              B is NULL: B_n(T) = dnu 2 h c^2 nu^3 /
+                              (exp(h c nu / (k T)) - 1) at the band centre, with
+                              nu = 100 nu_c [1/m] and the exact SI constants;
+                              T <= 0 gives 0 (Section 2.2 tabulates the
+                              blackbody intensity for the narrow bands)          */
 } mcrt_kdist_desc;
 
 typedef struct {

@@ -382,15 +382,42 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   return MCRT_OK;
 }
 
-int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd) {
+// Band blackbody intensity at the band centre (Section 2.2's tabulated
+// intensity for a narrow band): dnu 2 h c^2 nu^3 / (exp(h c nu / (k T)) - 1),
+// wavenumbers in 1/m, exact SI constants; 0 for T <= 0.
+static double planck_band(double nu_c_cm, double dnu_cm, double T) {
+  if (!(T > 0.0)) return 0.0;
+  const double h = 6.62607015e-34, c = 299792458.0, k = 1.380649e-23;
+  const double nu = 100.0 * nu_c_cm, dnu = 100.0 * dnu_cm;
+  // exp overflows to inf for h c nu / (k T) > 709.78: the intensity is then 0
+  return dnu * 2.0 * h * (c * c) * std::pow(nu, 3.0) / std::expm1(h * c * nu / (k * T));
+}
+
+int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
   if (!ctx) return MCRT_E_ARG;
-  if (!kd || !kd->w_g || !kd->kappa || !kd->B) return fail(ctx, MCRT_E_ARG, "null table");
+  if (!kd_in || !kd_in->w_g || !kd_in->kappa) return fail(ctx, MCRT_E_ARG, "null table");
+  mcrt_kdist_desc kdv = *kd_in;
+  const mcrt_kdist_desc *kd = &kdv;
   if (kd->n_bands < 1 || kd->n_bands > 1024 || kd->n_g < 1 || kd->n_g > 64 || kd->nT < 2 ||
       kd->nT > (1 << 20))
     return fail(ctx, MCRT_E_ARG, "table sizes out of range");
   if (!(kd->dT > 0) || !std::isfinite(kd->dT) || !std::isfinite(kd->T0) || !(kd->x_ref > 0) ||
       !std::isfinite(kd->x_ref))
     return fail(ctx, MCRT_E_ARG, "bad T axis or x_ref");
+  std::vector<double> Bcomp;
+  if (!kd->B) {
+    // the band intensities from the band centres and widths
+    if (!kd->nu_c || !kd->dnu) return fail(ctx, MCRT_E_ARG, "B, nu_c or dnu must be given");
+    for (int n = 0; n < kd->n_bands; ++n)
+      if (!(kd->nu_c[n] > 0.0) || !(kd->dnu[n] > 0.0) || !std::isfinite(kd->nu_c[n]) ||
+          !std::isfinite(kd->dnu[n]))
+        return fail(ctx, MCRT_E_ARG, "band centres and widths must be positive and finite");
+    Bcomp.resize((size_t)kd->n_bands * kd->nT);
+    for (int n = 0; n < kd->n_bands; ++n)
+      for (int t = 0; t < kd->nT; ++t)
+        Bcomp[(size_t)n * kd->nT + t] = planck_band(kd->nu_c[n], kd->dnu[n], kd->T0 + t * kd->dT);
+    kdv.B = Bcomp.data();
+  }
   const int nb = kd->n_bands, ng = kd->n_g, nT = kd->nT;
   const size_t nk = (size_t)nb * ng * nT, nbT = (size_t)nb * nT;
   if (!finite_nonneg(kd->w_g, ng) || !finite_nonneg(kd->kappa, nk) || !finite_nonneg(kd->B, nbT))

@@ -109,7 +109,7 @@ class KDist:
     dT: float
     nT: int
     kappa: np.ndarray
-    B: np.ndarray
+    B: np.ndarray | None             # None: the solver computes it from nu_c and dnu
     x_ref: float = 0.1
     nu_c: np.ndarray | None = None   # band centres [1/cm]
     dnu: np.ndarray | None = None    # band widths [1/cm]

@@ -46,7 +46,7 @@ class mcrt_kdist_desc(C.Structure):
     _fields_ = [("n_bands", C.c_int), ("n_g", C.c_int), ("w_g", C.POINTER(C.c_double)),
                 ("T0", C.c_double), ("dT", C.c_double), ("nT", C.c_int),
                 ("kappa", C.POINTER(C.c_double)), ("B", C.POINTER(C.c_double)),
-                ("x_ref", C.c_double)]
+                ("x_ref", C.c_double), ("nu_c", C.POINTER(C.c_double)), ("dnu", C.POINTER(C.c_double))]
 
 
 class mcrt_solve_params(C.Structure):
@@ -484,16 +484,24 @@ class Solver:
             pass
 
     def set_kdist(self, kd):
-        self._kd_keep = [np.ascontiguousarray(kd.w_g, dtype=np.float64),
-                         np.ascontiguousarray(kd.kappa, dtype=np.float64),
-                         np.ascontiguousarray(kd.B, dtype=np.float64)]
+        """Upload the tables.  With kd.B None the library computes the band
+        intensities from kd.nu_c and kd.dnu."""
+        def arr(v):
+            return None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+
+        def ptr(a):
+            return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+        self._kd_keep = [arr(kd.w_g), arr(kd.kappa), arr(kd.B), arr(kd.nu_c), arr(kd.dnu)]
         d = mcrt_kdist_desc()
         d.n_bands, d.n_g = kd.n_bands, kd.n_g
-        d.w_g = self._kd_keep[0].ctypes.data_as(C.POINTER(C.c_double))
+        d.w_g = ptr(self._kd_keep[0])
         d.T0, d.dT, d.nT = kd.T0, kd.dT, kd.nT
-        d.kappa = self._kd_keep[1].ctypes.data_as(C.POINTER(C.c_double))
-        d.B = self._kd_keep[2].ctypes.data_as(C.POINTER(C.c_double))
+        d.kappa = ptr(self._kd_keep[1])
+        d.B = ptr(self._kd_keep[2])
         d.x_ref = kd.x_ref
+        d.nu_c = ptr(self._kd_keep[3])
+        d.dnu = ptr(self._kd_keep[4])
         mcrt_set_kdist(self.ctx, d)
         self.kd = kd
 

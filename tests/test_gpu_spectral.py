@@ -41,3 +41,39 @@ def test_spectral_proposal_counts_and_solve_parity(mode):
     with pytest.raises(mcrt.McrtError):
         S.set_spectral_proposal(7)
     S.close()
+
+
+def test_band_intensities_computed_by_the_library():
+    """B = NULL with band centres and widths: the library's FP64 Planck table
+    gives the same solves as the supplied table (and the oracle's), including a
+    T axis that starts at 0 K, where the intensity is 0; missing or
+    non-positive band data are argument errors."""
+    import dataclasses
+    grid = inputs.Grid(12, 16, 8, 4.0, 2.0, 2.0, eps_wall=(0.7, 1.0), T_wall=(0.0, 1000.0))
+    kd = inputs.make_kdist(3, n_bands=12, n_g=4, T0=0.0, dT=25.0, nT=64, clamp_below=300.0)
+    T, x = inputs.channel_fields(grid, 61, x_mode="field")
+    kd_nob = dataclasses.replace(kd, B=None)
+    box = (0, 12, 0, 16, 2, 4)
+    o = oracle.solve(grid, kd, T, x, rays=64, seed=7, box=box)
+    out = {}
+    for name, k in (("given", kd), ("computed", kd_nob)):
+        S = mcrt.Solver(grid, k)
+        S.set_fields(T, x)
+        out[name] = [S.solve(box=box, rays=64, seed=7, precision=p)[0]
+                     for p in (mcrt.MCRT_FP64, mcrt.MCRT_FP32)]
+        out[name].append(S.plain_probs())
+        S.close()
+    g64, g32, gp = out["given"]
+    c64, c32, cp = out["computed"]
+    assert np.array_equal(gp, cp)
+    assert np.all(np.abs(c64 - g64) <= 1e-12 * o["scale"])
+    assert np.all(np.abs(c32 - g32) <= 1e-6 * o["scale"])
+    assert np.all(np.abs(c64 - o["q"]) <= 1e-10 * o["scale"])
+    S = mcrt.Solver(grid, kd)
+    for bad in (dataclasses.replace(kd_nob, nu_c=None),
+                dataclasses.replace(kd_nob, dnu=np.where(np.arange(kd.n_bands) == 3, 0.0, kd.dnu)),
+                dataclasses.replace(kd_nob, nu_c=np.where(np.arange(kd.n_bands) == 5, np.nan, kd.nu_c))):
+        with pytest.raises(mcrt.McrtError) as e:
+            S.set_kdist(bad)
+        assert e.value.status == mcrt.MCRT_E_ARG
+    S.close()

@@ -40,11 +40,12 @@ OPS_PER_STEP = 44             # axis choice, table position, two interpolations,
 OPS_PER_RAY = 260             # 2 Philox4x32-10 blocks (2 x 80), sampling, direction,
                               # origin, DDA set-up, sample store
 GATHER_BYTES_PER_STEP = 8     # FP32 {T, x} of the traversed cell
-GATHERS_PER_STEP = 3          # 8-byte loads per step: {T, x}, the kappa node pair, the B node pair
+GATHERS_PER_STEP = 3          # 8-byte values a step gathers: {T, x}, the kappa node pair, the B node
+                              # pair (the kernel fetches the two node pairs in one 16-byte load)
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel;
 # reported only for that workload
-TRACE_DRAM_BYTES_64_1000 = 26761728 + 1011770112
+TRACE_DRAM_BYTES_64_1000 = 27636992 + 1011479040
 
 
 def parse():

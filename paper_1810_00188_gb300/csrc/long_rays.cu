@@ -84,17 +84,15 @@ __device__ __forceinline__ Geom geom_of(const TraceArgs &a, unsigned snap) {
 
 // kappa and B of the cell `lin` for the ray's (n, g) row (Section 2.2's linear
 // interpolation in T; kappa scales with x / x_ref)
-__device__ __forceinline__ void medium(const uint2 *__restrict__ field, const float2 *__restrict__ ktab,
-                                       const float2 *__restrict__ btab, unsigned lin, unsigned krow,
-                                       unsigned brow, float &kap, float &Bj) {
+__device__ __forceinline__ void medium(const uint2 *__restrict__ field, const float4 *__restrict__ kbtab,
+                                       unsigned lin, unsigned krow, float &kap, float &Bj) {
   const uint2 f = __ldg(field + lin);
   unsigned it;
   float fr;
   tpos(f.x, it, fr);
-  const float2 kk = __ldg(ktab + (krow + it));
-  const float2 bb = __ldg(btab + (brow + it));
-  kap = (kk.x + fr * kk.y) * __uint_as_float(f.y);
-  Bj = bb.x + fr * bb.y;
+  const float4 kb = __ldg(kbtab + (krow + it));
+  kap = (kb.x + fr * kb.y) * __uint_as_float(f.y);
+  Bj = kb.z + fr * kb.w;
 }
 
 __device__ __forceinline__ float row_height(const float *yfs, int j) {
@@ -129,8 +127,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     atomicAdd(a.counters + 8, (unsigned long long)total);
     if (handed > (unsigned long long)total) atomicAdd(a.counters + 9, handed - (unsigned long long)total);
   }
-  const float2 *__restrict__ ktab = a.ktab32;
-  const float2 *__restrict__ btab = a.btab32;
+  const float4 *__restrict__ kbtab = a.kbtab32;
   const float tol = (float)a.tol;
   const int nb = a.nb, N = a.rays;
   const long long guard_max = 2LL * a.max_steps + 64;
@@ -144,7 +141,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     float cntx = L.cntx, cnty = L.cnty, cntz = L.cntz, tnx = L.tnx, tny = L.tny, tnz = L.tnz;
     float tprev = L.tprev, tau = L.tau, X = L.X, B_last = L.B_last;
     const float B_i = L.B_i;
-    const unsigned krow = L.krow, brow = L.n * (unsigned)a.nT;
+    const unsigned krow = L.krow;
     int ix = L.ix, iy = L.iy, iz = L.iz;
     int sx = (int)(L.signs & 3u) - 1, sy = (int)((L.signs >> 2) & 3u) - 1, sz = (int)((L.signs >> 4) & 3u) - 1;
     int steps = (int)L.steps;
@@ -236,7 +233,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
           tn = tnz;
         }
         float kap, Bj;
-        medium(g.field, ktab, btab, (unsigned)(ix + g.nx * (iy + g.ny * iz)), krow, brow, kap, Bj);
+        medium(g.field, kbtab, (unsigned)(ix + g.nx * (iy + g.ny * iz)), krow, kap, Bj);
         float alpha, trans;
         absorb(kap * fmaxf(tn - tprev, 0.f), alpha, trans);
         X += (B_i - Bj) * (tau * alpha);
@@ -301,7 +298,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
           const float tn = xf ? tx : tz;
           const bool in = (xf || !y_end) ? tn <= te : tn < te;
           float kap, Bj;
-          medium(g.field, ktab, btab, (unsigned)jx + row + plane * (unsigned)jz, krow, brow, kap, Bj);
+          medium(g.field, kbtab, (unsigned)jx + row + plane * (unsigned)jz, krow, kap, Bj);
           float alpha, trans;
           absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
           lX += (B_i - Bj) * (lt * alpha);
@@ -375,7 +372,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
             const float tn = xf ? tx : tz;
             const bool in = (xf || !y_end) ? tn <= te : tn < te;
             float kap, Bj;
-            medium(g.field, ktab, btab, (unsigned)jx + row + plane * (unsigned)jz, krow, brow, kap, Bj);
+            medium(g.field, kbtab, (unsigned)jx + row + plane * (unsigned)jz, krow, kap, Bj);
             float alpha, trans;
             absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
             gX += (B_i - Bj) * (gt * alpha);

@@ -262,6 +262,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.ktab32 = (const float2 *)ctx->ktab32.p;
   a.ktab64 = (const double2 *)ctx->ktab64.p;
   a.btab32 = (const float2 *)ctx->btab32.p;
+  a.kbtab32 = (const float4 *)ctx->kbtab32.p;
   a.btab64 = (const double2 *)ctx->btab64.p;
   a.bwall32 = (const float *)ctx->bwall32.p;
   a.bwall64 = (const double *)ctx->bwall64.p;
@@ -466,6 +467,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
   CK(ensure(ctx->ktab32, nk * sizeof(float2)), "alloc kappa table");
   CK(ensure(ctx->btab64, nbT * sizeof(double2)), "alloc B table");
   CK(ensure(ctx->btab32, nbT * sizeof(float2)), "alloc B table");
+  CK(ensure(ctx->kbtab32, nk * sizeof(float4)), "alloc kappa-B table");
   CK(ensure(ctx->bwall64, 6 * nb * sizeof(double)), "alloc wall B");
   CK(ensure(ctx->bwall32, 6 * nb * sizeof(float)), "alloc wall B");
   CK(ensure(ctx->wg, ng * sizeof(double)), "alloc w_g");
@@ -477,6 +479,16 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
   CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab32.p, b32.data(), nbT * sizeof(float2), cudaMemcpyHostToDevice), "copy");
+  {
+    // the FP32 march's interleaved rows: row (n, g) carries band n's B nodes
+    std::vector<float4> kb(nk);
+    for (size_t r = 0; r < (size_t)nb * ng; ++r)
+      for (int t = 0; t < nT; ++t) {
+        const float2 kv = k32[r * nT + t], bv = b32[(r / ng) * nT + t];
+        kb[r * nT + t] = make_float4(kv.x, kv.y, bv.x, bv.y);
+      }
+    CK(cudaMemcpy(ctx->kbtab32.p, kb.data(), nk * sizeof(float4), cudaMemcpyHostToDevice), "copy");
+  }
   CK(cudaMemcpy(ctx->bwall64.p, bw64.data(), 6 * nb * sizeof(double), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->bwall32.p, bw32.data(), 6 * nb * sizeof(float), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->wg.p, kd->w_g, ng * sizeof(double), cudaMemcpyHostToDevice), "copy");
@@ -767,7 +779,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -921,6 +933,7 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
   a.btab32 = (const float2 *)ctx->btab32.p;
+  a.kbtab32 = (const float4 *)ctx->kbtab32.p;
   a.bwall32 = (const float *)ctx->bwall32.p;
   a.w_g = (const double *)ctx->wg.p;
   a.w_g32 = (const float *)ctx->wg32.p;
@@ -1116,6 +1129,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.fpos32 = (const uint2 *)c->fpos32.p;
     a.ktab32 = (const float2 *)c->ktab32.p;
     a.btab32 = (const float2 *)c->btab32.p;
+    a.kbtab32 = (const float4 *)c->kbtab32.p;
     a.bwall32 = (const float *)c->bwall32.p;
     a.w_g = (const double *)c->wg.p;
     a.w_g32 = (const float *)c->wg32.p;

@@ -72,6 +72,8 @@ struct TraceArgs {
   const float2 *ktab32;     // [nb*ng][nT] {kappa_t, kappa_{t+1} - kappa_t} at x_ref
   const double2 *ktab64;
   const float2 *btab32;     // [nb][nT] {B_t, B_{t+1} - B_t}
+  const float4 *kbtab32;    // [nb*ng][nT] {kappa_t, its slope, B_t of band n, its slope}:
+                            // one 16-byte load per march step
   const double2 *btab64;
   const float *bwall32;     // [6][nb] wall band intensity: y = 0, y = ly, x = 0, x = lx, z = 0, z = lz
   const double *bwall64;

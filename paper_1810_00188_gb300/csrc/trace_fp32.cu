@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   const int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny, nb = a.nb,
             ng = a.ng, nT = a.nT, N = a.rays;
   const uint2 *__restrict__ field = a.fpos32;
-  const float2 *__restrict__ ktab = a.ktab32;
-  const float2 *__restrict__ btab = a.btab32;
+  const float4 *__restrict__ kbtab = a.kbtab32;  // {kappa, slope, B, slope} per (n, g, t)
   const float tol = (float)a.tol;
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
   // stretched y (faces non-null): tsy holds 1/|d_y| and each y crossing adds the
@@ -227,9 +226,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             fy = unif(v.y);
             fz = unif(v.z);
           }
-          const float2 ki = __ldg(ktab + ((unsigned)(nn * ng + gg) * (unsigned)nT + it_i));
-          const float2 bi = __ldg(btab + ((unsigned)nn * (unsigned)nT + it_i));
-          const float kap_i = (ki.x + fr_i * ki.y) * __uint_as_float(fi.y);
+          const float4 kbi = __ldg(kbtab + ((unsigned)(nn * ng + gg) * (unsigned)nT + it_i));
+          const float kap_i = (kbi.x + fr_i * kbi.y) * __uint_as_float(fi.y);
           int ssx, ssy, ssz;
           float a0x, a0y, a0z, asx, asy, asz;
           axis_setup(st * cphi, fx, DX, ssx, a0x, asx);
@@ -238,7 +236,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           if (yfs && ssy != 0) asy = __frcp_rn(fabsf(mu));
           const int pos = (tail + lane) & (POOL - 1);
           R.A[pos] = make_float4(a0x, a0y, a0z, asx);
-          R.B[pos] = make_float4(asy, asz, bi.x + fr_i * bi.y, wgt * kap_i);
+          R.B[pos] = make_float4(asy, asz, kbi.z + fr_i * kbi.w, wgt * kap_i);
           const unsigned flags = (unsigned)(ssx + 1) | ((unsigned)(ssy + 1) << 2) |
                                  ((unsigned)(ssz + 1) << 4);
           R.C[pos] = make_uint4((unsigned)nn | ((unsigned)gg << 16), rayid, flags, cell);
@@ -330,10 +328,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       unsigned it;
       float fr;
       tpos(f.x, it, fr);
-      const float2 kk = __ldg(ktab + (krow + it));
-      const float2 bb = __ldg(btab + (n * (unsigned)nT + it));
-      const float kap = (kk.x + fr * kk.y) * __uint_as_float(f.y);
-      const float Bj = bb.x + fr * bb.y;
+      const float4 kb = __ldg(kbtab + (krow + it));
+      const float kap = (kb.x + fr * kb.y) * __uint_as_float(f.y);
+      const float Bj = kb.z + fr * kb.w;
       float alpha, trans;
       absorb(kap * ds, alpha, trans);
       X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i

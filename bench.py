@@ -45,7 +45,7 @@ GATHERS_PER_STEP = 3          # 8-byte values a step gathers: {T, x}, the kappa 
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel;
 # reported only for that workload
-TRACE_DRAM_BYTES_64_1000 = 27636992 + 1011479040
+TRACE_DRAM_BYTES_64_1000 = 26891008 + 1011976704
 
 
 def parse():

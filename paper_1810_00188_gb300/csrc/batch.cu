@@ -21,7 +21,9 @@ namespace {
 // rays finish before it moves to the next one, so the snapshot's grid, fields,
 // walls and proposal are warp-uniform values.  MG: the multigrid march of
 // Section 4.3.
-template <int MINB, int KSTEPS, bool MG>
+// GEN: some snapshot has stretched y faces; the uniform variant drops the
+// row-height lookups from the step.
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const TraceArgs a) {
   constexpr bool BATCH = true;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           ix += mx ? sx : 0;
           iy += my ? sy : 0;
           iz += mz ? sz : 0;
-          if (yfs && my && (unsigned)iy < (unsigned)nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
+          if (GEN && yfs && my && (unsigned)iy < (unsigned)nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
           // periodic wrap: an index can only leave the grid in the ray's direction
           const int wx = (unsigned)ix < (unsigned)nxl ? 0 : -sx * nxl;
           ix += wx;
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(256) reduce_cells_batch_kernel(const TraceArgs
   }
 }
 
-template <int MINB, int KSTEPS, bool MG>
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
   static bool init_done = false;
@@ -650,13 +652,14 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (configured_smem[dev] != (int)smem) {
-    e = cudaFuncSetAttribute(trace_batch_kernel<MINB, KSTEPS, MG>,
+    e = cudaFuncSetAttribute(trace_batch_kernel<MINB, KSTEPS, MG, GEN>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev],
-                                                      trace_batch_kernel<MINB, KSTEPS, MG>, WARPS * 32, smem);
+                                                      trace_batch_kernel<MINB, KSTEPS, MG, GEN>, WARPS * 32,
+                                                      smem);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
     configured_smem[dev] = (int)smem;
@@ -666,18 +669,18 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   return cudaSuccess;
 }
 
-template <int MINB, int KSTEPS, bool MG>
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
   // per-device launch shape, computed once per device and shared-memory size
   int bps = 0, nsm = 0;
-  cudaError_t e = configure_variant<MINB, KSTEPS, MG>(smem, &bps, &nsm);
+  cudaError_t e = configure_variant<MINB, KSTEPS, MG, GEN>(smem, &bps, &nsm);
   if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const long long need = (P + WARPS - 1) / WARPS;
   long long blocks = a.grid_blocks > 0 ? a.grid_blocks : (long long)nsm * bps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  trace_batch_kernel<MINB, KSTEPS, MG><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  trace_batch_kernel<MINB, KSTEPS, MG, GEN><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -692,20 +695,40 @@ static size_t fp32_batch_smem_bytes(int nb, int ng, int nsnaps, int counts_in_sm
   return WARPS * sizeof(WarpRing) + WARPS * wslice + sizeof(long long) * (size_t)(nsnaps + 1);
 }
 
+// CTAs per SM (3 when min_blocks >= 3, else 2), march steps per refill round (2
+// when steps_per_round >= 2, else 1), multigrid, stretched snapshots.  prepare =
+// true sets the variant's launch attributes; false launches it.
+template <bool MG, bool GEN>
+cudaError_t run_batch_variant(bool prepare, const TraceArgs *a, bool mb3, bool k2, cudaStream_t s, size_t smem,
+                              int *bps, int *nsm) {
+  if (prepare) {
+    if (mb3) return k2 ? configure_variant<3, 2, MG, GEN>(smem, bps, nsm) : configure_variant<3, 1, MG, GEN>(smem, bps, nsm);
+    return k2 ? configure_variant<2, 2, MG, GEN>(smem, bps, nsm) : configure_variant<2, 1, MG, GEN>(smem, bps, nsm);
+  }
+  if (mb3) return k2 ? launch_variant<3, 2, MG, GEN>(*a, s, smem) : launch_variant<3, 1, MG, GEN>(*a, s, smem);
+  return k2 ? launch_variant<2, 2, MG, GEN>(*a, s, smem) : launch_variant<2, 1, MG, GEN>(*a, s, smem);
+}
+
+static cudaError_t batch_dispatch(bool prepare, const TraceArgs *a, int min_blocks, int steps_per_round,
+                                  bool multigrid, bool stretched, cudaStream_t s, size_t smem, int *bps, int *nsm) {
+  const bool mb3 = min_blocks >= 3, k2 = steps_per_round >= 2;
+  if (multigrid)
+    return stretched ? run_batch_variant<true, true>(prepare, a, mb3, k2, s, smem, bps, nsm)
+                     : run_batch_variant<true, false>(prepare, a, mb3, k2, s, smem, bps, nsm);
+  return stretched ? run_batch_variant<false, true>(prepare, a, mb3, k2, s, smem, bps, nsm)
+                   : run_batch_variant<false, false>(prepare, a, mb3, k2, s, smem, bps, nsm);
+}
+
 cudaError_t prepare_trace_fp32_batch(int min_blocks, int steps_per_round, int nb, int ng, int nsnaps,
                                      int counts_in_smem, int multigrid, int *blocks_per_sm, int *num_sms) {
   const size_t smem = fp32_batch_smem_bytes(nb, ng, nsnaps, counts_in_smem);
-  const bool mb3 = min_blocks >= 3, k2 = steps_per_round >= 2;
-  if (multigrid) {
-    if (mb3) return k2 ? configure_variant<3, 2, true>(smem, blocks_per_sm, num_sms)
-                       : configure_variant<3, 1, true>(smem, blocks_per_sm, num_sms);
-    return k2 ? configure_variant<2, 2, true>(smem, blocks_per_sm, num_sms)
-              : configure_variant<2, 1, true>(smem, blocks_per_sm, num_sms);
-  }
-  if (mb3) return k2 ? configure_variant<3, 2, false>(smem, blocks_per_sm, num_sms)
-                     : configure_variant<3, 1, false>(smem, blocks_per_sm, num_sms);
-  return k2 ? configure_variant<2, 2, false>(smem, blocks_per_sm, num_sms)
-            : configure_variant<2, 1, false>(smem, blocks_per_sm, num_sms);
+  // both geometry variants: the captured launch takes one of them
+  int bps_gen = 0, nsm_gen = 0;
+  cudaError_t e = batch_dispatch(true, nullptr, min_blocks, steps_per_round, multigrid != 0, true, nullptr, smem,
+                                 &bps_gen, &nsm_gen);
+  if (e != cudaSuccess) return e;
+  return batch_dispatch(true, nullptr, min_blocks, steps_per_round, multigrid != 0, false, nullptr, smem,
+                        blocks_per_sm, num_sms);
 }
 
 cudaError_t launch_trace_fp32_batch(const TraceArgs &args, int min_blocks, int steps_per_round,
@@ -716,18 +739,8 @@ cudaError_t launch_trace_fp32_batch(const TraceArgs &args, int min_blocks, int s
   const size_t smem = fp32_batch_smem_bytes(a.nb, a.ng, a.nsnaps, a.counts_in_smem);
   cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const bool mb3 = min_blocks >= 3, k2 = steps_per_round >= 2;
-  if (a.mg_levels > 1) {
-    if (mb3)
-      e = k2 ? launch_variant<3, 2, true>(a, s, smem) : launch_variant<3, 1, true>(a, s, smem);
-    else
-      e = k2 ? launch_variant<2, 2, true>(a, s, smem) : launch_variant<2, 1, true>(a, s, smem);
-  } else {
-    if (mb3)
-      e = k2 ? launch_variant<3, 2, false>(a, s, smem) : launch_variant<3, 1, false>(a, s, smem);
-    else
-      e = k2 ? launch_variant<2, 2, false>(a, s, smem) : launch_variant<2, 1, false>(a, s, smem);
-  }
+  e = batch_dispatch(false, &a, min_blocks, steps_per_round, a.mg_levels > 1, a.batch_stretched != 0, s, smem,
+                     nullptr, nullptr);
   if (e != cudaSuccess) return e;
   if (long_rays_on(a)) {
     e = launch_long_rays(a, s);

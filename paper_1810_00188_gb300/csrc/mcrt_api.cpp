@@ -1243,6 +1243,9 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     mcrt::TraceArgs a = args[order[0]];
     a.snaps = (const mcrt::SnapArgs *)d_sn;
     a.nsnaps = n;
+    a.batch_stretched = 0;
+    for (int k = 0; k < n; ++k)
+      if (args[k].yf32) a.batch_stretched = 1;
     a.ybuf = (float *)yb;
     a.step_acc = nullptr;
     a.steps_cell = nullptr;

@@ -65,6 +65,8 @@ struct TraceArgs {
   // closed box: black walls on the x and z faces (bwall rows 2..5: x = 0,
   // x = lx, z = 0, z = lz) instead of periodic x and z
   int xz_walls;
+  // batched launch: some snapshot has stretched y faces (the kernel's general variant)
+  int batch_stretched;
   // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
   const float2 *field32;    // {T, x} per cell
   const uint2 *fpos32;      // FP32 kernel: {(node << 23) | fraction * 2^23, bits of x / x_ref}

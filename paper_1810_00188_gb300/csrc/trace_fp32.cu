@@ -45,7 +45,9 @@
 namespace mcrt {
 namespace {
 
-template <int MINB, int KSTEPS, bool MG>
+// GEN: the general geometry (stretched y faces, closed-box x and z walls).  The
+// channel variant (uniform y, periodic x and z) drops those tests from the step.
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpRing *rings = reinterpret_cast<WarpRing *>(smem_raw);
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
   // stretched y (faces non-null): tsy holds 1/|d_y| and each y crossing adds the
   // next row's height; the height of row j of grid l from the faces
-  const float *__restrict__ yfs = a.yf32;
+  const float *__restrict__ yfs = GEN ? a.yf32 : nullptr;
   auto dyl = [&](int j, int l) -> float {
     return __ldg(yfs + ((unsigned)(j + 1) << l)) - __ldg(yfs + ((unsigned)j << l));
   };
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           iz += wz;
           // the linear index from the three indices (multiply-adds, off the ALU pipe)
           lin = (unsigned)(ix + nxl * (iy + nyl * iz));
-          if (a.xz_walls && (wx | wz)) {
+          if (GEN && a.xz_walls && (wx | wz)) {
             // closed box: a black x or z wall absorbs the rest of the ray and
             // emits at its temperature (Eq. 3 wall factor with eps = 1)
             const int f = wx ? (wx > 0 ? 2 : 3) : (wz > 0 ? 4 : 5);
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
   }
 }
 
-template <int MINB, int KSTEPS, bool MG>
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
   static bool init_done = false;
@@ -587,13 +589,14 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (configured_smem[dev] != (int)smem) {
-    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS, MG>,
+    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS, MG, GEN>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev],
-                                                      trace_fp32_kernel<MINB, KSTEPS, MG>, WARPS * 32, smem);
+                                                      trace_fp32_kernel<MINB, KSTEPS, MG, GEN>, WARPS * 32,
+                                                      smem);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
     configured_smem[dev] = (int)smem;
@@ -603,19 +606,53 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   return cudaSuccess;
 }
 
-template <int MINB, int KSTEPS, bool MG>
+template <int MINB, int KSTEPS, bool MG, bool GEN>
 cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
   // per-device launch shape, computed once per device and shared-memory size
   int bps = 0, nsm = 0;
-  cudaError_t e = configure_variant<MINB, KSTEPS, MG>(smem, &bps, &nsm);
+  cudaError_t e = configure_variant<MINB, KSTEPS, MG, GEN>(smem, &bps, &nsm);
   if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const long long need = (P + WARPS - 1) / WARPS;
   long long blocks = a.grid_blocks > 0 ? a.grid_blocks : (long long)nsm * bps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  trace_fp32_kernel<MINB, KSTEPS, MG><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  trace_fp32_kernel<MINB, KSTEPS, MG, GEN><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// One of the variants: CTAs per SM (1..4, default 2), march steps per refill
+// round (1, 2, 4), multigrid, general geometry.  prepare = true sets the
+// variant's launch attributes; false launches it.
+template <bool MG, bool GEN>
+cudaError_t run_variant(bool prepare, const TraceArgs *a, int min_blocks, int steps_per_round, cudaStream_t s,
+                        size_t smem, int *bps, int *nsm) {
+#define MCRT_V(MB, K) \
+  return prepare ? configure_variant<MB, K, MG, GEN>(smem, bps, nsm) : launch_variant<MB, K, MG, GEN>(*a, s, smem)
+#define MCRT_VK(MB)        \
+  switch (steps_per_round) { \
+    case 2: MCRT_V(MB, 2);   \
+    case 4: MCRT_V(MB, 4);   \
+    default: MCRT_V(MB, 1);  \
+  }
+  switch (min_blocks) {
+    case 1: MCRT_VK(1)
+    case 3: MCRT_VK(3)
+    case 4: MCRT_VK(4)
+    default: MCRT_VK(2)
+  }
+#undef MCRT_VK
+#undef MCRT_V
+  return cudaErrorInvalidValue;  // not reached
+}
+
+cudaError_t dispatch(bool prepare, const TraceArgs *a, int min_blocks, int steps_per_round, bool multigrid,
+                     bool general, cudaStream_t s, size_t smem, int *bps, int *nsm) {
+  if (multigrid)
+    return general ? run_variant<true, true>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm)
+                   : run_variant<true, false>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm);
+  return general ? run_variant<false, true>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm)
+                 : run_variant<false, false>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm);
 }
 
 }  // namespace
@@ -646,26 +683,13 @@ int fp32_cell_stage_fits(int nb, int ng) {
 cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int ng, int counts_in_smem,
                                int multigrid, int *blocks_per_sm, int *num_sms) {
   const size_t smem = fp32_smem_bytes(nb, ng, counts_in_smem);
-#define MCRT_PREP_K(MB)                                                                  \
-  if (multigrid) {                                                                       \
-    switch (steps_per_round) {                                                           \
-      case 2: return configure_variant<MB, 2, true>(smem, blocks_per_sm, num_sms);       \
-      case 4: return configure_variant<MB, 4, true>(smem, blocks_per_sm, num_sms);       \
-      default: return configure_variant<MB, 1, true>(smem, blocks_per_sm, num_sms);      \
-    }                                                                                    \
-  }                                                                                      \
-  switch (steps_per_round) {                                                             \
-    case 2: return configure_variant<MB, 2, false>(smem, blocks_per_sm, num_sms);        \
-    case 4: return configure_variant<MB, 4, false>(smem, blocks_per_sm, num_sms);        \
-    default: return configure_variant<MB, 1, false>(smem, blocks_per_sm, num_sms);       \
-  }
-  switch (min_blocks) {
-    case 1: MCRT_PREP_K(1)
-    case 3: MCRT_PREP_K(3)
-    case 4: MCRT_PREP_K(4)
-    default: MCRT_PREP_K(2)
-  }
-#undef MCRT_PREP_K
+  // both geometry variants: the launches that follow may take either
+  int bps_gen = 0, nsm_gen = 0;
+  cudaError_t e = dispatch(true, nullptr, min_blocks, steps_per_round, multigrid != 0, true, nullptr, smem,
+                           &bps_gen, &nsm_gen);
+  if (e != cudaSuccess) return e;
+  return dispatch(true, nullptr, min_blocks, steps_per_round, multigrid != 0, false, nullptr, smem,
+                  blocks_per_sm, num_sms);
 }
 
 cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_per_round,
@@ -677,27 +701,8 @@ cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_p
   // the claim counter of this launch's position runs and its hand-off count
   cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-#define MCRT_FP32_K(MB)                                                    \
-  if (a.mg_levels > 1) {                                                   \
-    switch (steps_per_round) {                                             \
-      case 2: e = launch_variant<MB, 2, true>(a, s, smem); break;          \
-      case 4: e = launch_variant<MB, 4, true>(a, s, smem); break;          \
-      default: e = launch_variant<MB, 1, true>(a, s, smem); break;         \
-    }                                                                      \
-  } else {                                                                 \
-    switch (steps_per_round) {                                             \
-      case 2: e = launch_variant<MB, 2, false>(a, s, smem); break;         \
-      case 4: e = launch_variant<MB, 4, false>(a, s, smem); break;         \
-      default: e = launch_variant<MB, 1, false>(a, s, smem); break;        \
-    }                                                                      \
-  }
-  switch (min_blocks) {
-    case 1: MCRT_FP32_K(1) break;
-    case 3: MCRT_FP32_K(3) break;
-    case 4: MCRT_FP32_K(4) break;
-    default: MCRT_FP32_K(2) break;
-  }
-#undef MCRT_FP32_K
+  const bool general = a.yf32 != nullptr || a.xz_walls != 0;
+  e = dispatch(false, &a, min_blocks, steps_per_round, a.mg_levels > 1, general, s, smem, nullptr, nullptr);
   if (e != cudaSuccess) return e;
   if (long_rays_on(a)) {
     e = launch_long_rays(a, s);

@@ -575,8 +575,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
 // trace_fp32.cu; each position goes to the snapshot that owns it).  A warp takes
 // 32 consecutive chunk positions; for each
 // cell the lanes sum its N samples in a fixed order (lane l takes samples l,
-// l + 32, ... as compensated binary32 pairs, then a fixed butterfly of pair
-// additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
+// l + 32, ..., sums each batch of 8 pairwise and adds the batch sums to
+// compensated binary32 pairs, then a fixed butterfly of pair additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
 // (Eq. 8) and the standard error in binary64 for their own cell at once.  The
 // order never depends on scheduling, so Q and sigma are reproducible bit for bit.
 // BATCH: the positions of a batched launch; each one is reduced into the

@@ -22,8 +22,8 @@
 //    grazing ray of a thin band, up to ~10^5 steps) is handed to the
 //    warp-parallel march of long_rays.cu instead of holding its lane to the end;
 //  * samples go to a scratch array indexed by (cell, ray); reduce_cells_kernel
-//    sums each cell's samples in a fixed order (compensated binary32 pairs per
-//    lane, binary64 across lanes), so Q and sigma do not depend on scheduling,
+//    sums each cell's samples in a fixed order (pairwise batches of 8 added to
+//    compensated binary32 pairs per lane, binary64 across lanes), so Q and sigma do not depend on scheduling,
 //    launch shape or box.
 //
 // GB300 issues binary64 arithmetic and int<->float conversions on a narrow pipe,
@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
 
 // Per-cell reduction.  A warp takes 32 consecutive chunk positions; for each
 // cell the lanes sum its N samples in a fixed order (lane l takes samples l,
-// l + 32, ... as compensated binary32 pairs, then a fixed butterfly of pair
-// additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
+// l + 32, ..., sums each batch of 8 pairwise and adds the batch sums to
+// compensated binary32 pairs, then a fixed butterfly of pair additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
 // (Eq. 8) and the standard error in binary64 for their own cell at once.  The
 // order never depends on scheduling, so Q and sigma are reproducible bit for bit.
 __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {

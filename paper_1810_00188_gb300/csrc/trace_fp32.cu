@@ -17,14 +17,17 @@
 //    shared memory;
 //  * the march advances every active lane by up to KSTEPS cells per round; a lane
 //    whose ray ends stores its sample Y and takes the next prepared state; the
-//    field entry of the next cell is loaded a step ahead;
+//    field entry of the next cell is loaded a step ahead, and kappa and B of the
+//    ray's (n, g) come in one 16-byte load from an interleaved table;
+//  * the channel geometry (uniform y, periodic x and z) is a compile-time
+//    variant whose step has no stretched-face or closed-box tests;
 //  * a ray that has marched long_steps segments with a long flight ahead (a
 //    grazing ray of a thin band, up to ~10^5 steps) is handed to the
 //    warp-parallel march of long_rays.cu instead of holding its lane to the end;
 //  * samples go to a scratch array indexed by (cell, ray); reduce_cells_kernel
 //    sums each cell's samples in a fixed order (pairwise batches of 8 added to
-//    compensated binary32 pairs per lane, binary64 across lanes), so Q and sigma do not depend on scheduling,
-//    launch shape or box.
+//    compensated binary32 pairs per lane, binary64 across lanes), so Q and
+//    sigma do not depend on scheduling, launch shape or box.
 //
 // GB300 issues binary64 arithmetic and int<->float conversions on a narrow pipe,
 // so the per-ray and per-step code uses neither: ray weights come from a

@@ -195,7 +195,13 @@ int mcrt_multigrid_levels(int nx, int ny, int nz);
 int mcrt_create(const mcrt_grid_desc *grid, mcrt_ctx **out);
 
 /* Copies the k-distribution tables (Section 2.1-2.2) to the device and builds
- * the FP32 and FP64 interpolation nodes.  Synchronous.  Errors: MCRT_E_ARG. */
+ * the FP32 and FP64 interpolation nodes.  With kd->B NULL, the band intensities
+ * on the T nodes are first computed on the host in binary64 from kd->nu_c and
+ * kd->dnu (the Planck law at each band centre times its width).  The caller
+ * keeps ownership of every array; nothing is retained after the call.
+ * Synchronous.  Errors: MCRT_E_ARG (a NULL table, B, nu_c and dnu all missing,
+ * sizes out of range, a negative or non-finite entry, a non-positive band
+ * centre or width). */
 int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd);
 
 /* Copies the temperature field T [K] and the H2O mole fraction x (NULL: x_ref

@@ -199,7 +199,7 @@ int mcrt_create(const mcrt_grid_desc *grid, mcrt_ctx **out);
  * on the T nodes are first computed on the host in binary64 from kd->nu_c and
  * kd->dnu (the Planck law at each band centre times its width).  The caller
  * keeps ownership of every array; nothing is retained after the call.
- * Synchronous.  Errors: MCRT_E_ARG (a NULL table, B, nu_c and dnu all missing,
+ * Synchronous.  Errors: MCRT_E_ARG (a NULL table, B NULL without nu_c and dnu,
  * sizes out of range, a negative or non-finite entry, a non-positive band
  * centre or width). */
 int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd);

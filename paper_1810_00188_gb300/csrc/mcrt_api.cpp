@@ -18,6 +18,7 @@
 #include "../../include/mcrt.h"
 #include "ctx.h"
 #include "mcrt_internal.h"
+#include "planck.h"
 
 using namespace mcrt_host;
 
@@ -383,17 +384,6 @@ int mcrt_create(const mcrt_grid_desc *g, mcrt_ctx **out) {
   return MCRT_OK;
 }
 
-// Band blackbody intensity at the band centre (Section 2.2's tabulated
-// intensity for a narrow band): dnu 2 h c^2 nu^3 / (exp(h c nu / (k T)) - 1),
-// wavenumbers in 1/m, exact SI constants; 0 for T <= 0.
-static double planck_band(double nu_c_cm, double dnu_cm, double T) {
-  if (!(T > 0.0)) return 0.0;
-  const double h = 6.62607015e-34, c = 299792458.0, k = 1.380649e-23;
-  const double nu = 100.0 * nu_c_cm, dnu = 100.0 * dnu_cm;
-  // exp overflows to inf for h c nu / (k T) > 709.78: the intensity is then 0
-  return dnu * 2.0 * h * (c * c) * std::pow(nu, 3.0) / std::expm1(h * c * nu / (k * T));
-}
-
 int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
   if (!ctx) return MCRT_E_ARG;
   if (!kd_in || !kd_in->w_g || !kd_in->kappa) return fail(ctx, MCRT_E_ARG, "null table");
@@ -416,7 +406,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
     Bcomp.resize((size_t)kd->n_bands * kd->nT);
     for (int n = 0; n < kd->n_bands; ++n)
       for (int t = 0; t < kd->nT; ++t)
-        Bcomp[(size_t)n * kd->nT + t] = planck_band(kd->nu_c[n], kd->dnu[n], kd->T0 + t * kd->dT);
+        Bcomp[(size_t)n * kd->nT + t] = mcrt::planck_band(kd->nu_c[n], kd->dnu[n], kd->T0 + t * kd->dT);
     kdv.B = Bcomp.data();
   }
   const int nb = kd->n_bands, ng = kd->n_g, nT = kd->nT;

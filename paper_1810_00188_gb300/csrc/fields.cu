@@ -12,7 +12,6 @@ namespace {
 
 __global__ void __launch_bounds__(256) pack_fields_kernel(const void *T, const void *x, int fp64_in,
                                                           double x_ref, long long n, double2 *f64,
-                                                          float2 *f32,
                                                           unsigned long long *stats) {
   unsigned long long tmax = 0ull, tmin = ~0ull, bad = 0ull;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -35,7 +34,6 @@ __global__ void __launch_bounds__(256) pack_fields_kernel(const void *T, const v
       ++bad;
     }
     f64[i] = make_double2(t, xv);
-    f32[i] = make_float2((float)t, (float)xv);
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -160,7 +158,7 @@ cudaError_t launch_pack_positions(const double2 *f64, long long n, double T0, do
 }
 
 cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
-                               long long n, double2 *f64, float2 *f32,
+                               long long n, double2 *f64,
                                unsigned long long *stats, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(stats, 0, 3 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(stats + 1, 0xff, sizeof(unsigned long long), s);
@@ -168,7 +166,7 @@ cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;  // grid-stride: 16 blocks per SM
-  pack_fields_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, x, fp64_in, x_ref, n, f64, f32, stats);
+  pack_fields_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, x, fp64_in, x_ref, n, f64, stats);
   return cudaGetLastError();
 }
 

@@ -257,7 +257,6 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.yf64 = (const double *)ctx->yf64.p;
   a.yf32 = (const float *)ctx->yf32.p;
   a.xz_walls = g.xz_walls;
-  a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.field64 = (const double2 *)ctx->field64.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
@@ -529,7 +528,6 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   const int mg_levels = mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
   const long long n_all = mcrt::multigrid_cells(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, mg_levels);
   CK(ensure(ctx->field64, (size_t)n_all * sizeof(double2)), "alloc field");
-  CK(ensure(ctx->field32, (size_t)n * sizeof(float2)), "alloc field");
   const void *dT = T, *dx = x;
   DevBuf stage;
   if (mem == MCRT_MEM_HOST) {
@@ -546,7 +544,6 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   if (!x && !ctx->have_kdist) return fail(ctx, MCRT_E_STATE, "x = NULL needs set_kdist first (x_ref)");
   const double x_ref = ctx->have_kdist ? ctx->x_ref : 1.0;
   cudaError_t e = mcrt::launch_pack_fields(dT, dx, fp64, x_ref, n, (double2 *)ctx->field64.p,
-                                           (float2 *)ctx->field32.p,
                                            (unsigned long long *)ctx->fstats.p, s);
   {
     double2 *lev = (double2 *)ctx->field64.p;
@@ -769,7 +766,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->field32, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -919,7 +916,6 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   a.yf64 = (const double *)ctx->yf64.p;
   a.yf32 = (const float *)ctx->yf32.p;
   a.xz_walls = g.xz_walls;
-  a.field32 = (const float2 *)ctx->field32.p;
   a.fpos32 = (const uint2 *)ctx->fpos32.p;
   a.ktab32 = (const float2 *)ctx->ktab32.p;
   a.btab32 = (const float2 *)ctx->btab32.p;
@@ -1115,7 +1111,6 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.yf64 = (const double *)c->yf64.p;
     a.yf32 = (const float *)c->yf32.p;
     a.xz_walls = g.xz_walls;
-    a.field32 = (const float2 *)c->field32.p;
     a.fpos32 = (const uint2 *)c->fpos32.p;
     a.ktab32 = (const float2 *)c->ktab32.p;
     a.btab32 = (const float2 *)c->btab32.p;

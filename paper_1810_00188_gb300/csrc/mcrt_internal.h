@@ -68,7 +68,6 @@ struct TraceArgs {
   // batched launch: some snapshot has stretched y faces (the kernel's general variant)
   int batch_stretched;
   // device data; the *32 / *64 members are used by the FP32 / FP64 kernel
-  const float2 *field32;    // {T, x} per cell
   const uint2 *fpos32;      // FP32 kernel: {(node << 23) | fraction * 2^23, bits of x / x_ref}
   const double2 *field64;
   const float2 *ktab32;     // [nb*ng][nT] {kappa_t, kappa_{t+1} - kappa_t} at x_ref
@@ -311,7 +310,7 @@ cudaError_t launch_theta_to_half(const float *theta, __half *theta16, long long 
 int mlp_train_grid();
 
 cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double x_ref,
-                               long long n, double2 *f64, float2 *f32,
+                               long long n, double2 *f64,
                                unsigned long long *stats, cudaStream_t s);
 
 }  // namespace mcrt

@@ -7,12 +7,9 @@
 //
 // GB300 mapping: one warp per emitting cell, its 32 lanes stride over the cell's
 // rays; a warp-shuffle reduction in binary64 and a single store of Q and sigma
-// per cell.  GB300 issues binary64 arithmetic at about 1/64 of the binary32
-// rate, so the FP32 kernel keeps per-ray work in binary32: ray weights come from
-// a host-built FP64 table rounded once, and each lane accumulates its rays in a
-// compensated binary32 pair (about 48 significant bits) that is widened to
-// binary64 for the cross-lane reduction.  The FP64 kernel does everything in
-// binary64 (parity mode).  Random numbers come from a counter-based
+// per cell.  Everything is binary64: this is the parity mode (binary64 issues at
+// about 1/64 of the binary32 rate on GB300; FP32 solves run the scheduled
+// kernels of trace_fp32.cu).  Random numbers come from a counter-based
 // Philox4x32-10 keyed by (cell, ray, draw block, snapshot), so each ray's draws
 // are independent of the launch shape.  The k-distribution tables are read
 // through the read-only path as {value, next-minus-value} pairs so a lookup is one
@@ -53,26 +50,6 @@ __device__ __forceinline__ R unif(unsigned w) {
 
 // ---- precision-specific pieces ---------------------------------------------
 template <typename R> struct Prec;
-template <> struct Prec<float> {
-  typedef float2 R2;
-  __device__ static const float2 *field(const TraceArgs &a) { return a.field32; }
-  __device__ static const float2 *ktab(const TraceArgs &a) { return a.ktab32; }
-  __device__ static const float2 *btab(const TraceArgs &a) { return a.btab32; }
-  __device__ static const float *bwall(const TraceArgs &a) { return a.bwall32; }
-  __device__ static const float *yf(const TraceArgs &a) { return a.yf32; }
-  __device__ static void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
-  __device__ static float div(float a, float b) { return __fdividef(a, b); }
-  // alpha = 1 - exp(-x) (Eq. 2) and the transmission factor exp(-x) (Eq. 3).
-  // Below x = 0.05 a 4-term series keeps alpha's relative error near 1 ulp
-  // instead of the cancellation in 1 - exp(-x).
-  __device__ static void absorb(float x, float &alpha, float &trans) {
-    const float e = __expf(-x);
-    const float sr = x * (1.f - x * (0.5f - x * (0.16666667f - x * 0.041666668f)));
-    const bool small = x < 0.05f;
-    alpha = small ? sr : 1.f - e;
-    trans = small ? 1.f - sr : e;
-  }
-};
 template <> struct Prec<double> {
   typedef double2 R2;
   __device__ static const double2 *field(const TraceArgs &a) { return a.field64; }
@@ -121,9 +98,7 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
   s = t;
 }
 
-// Per-lane tally of sum(Y) and sum(Y^2).  Binary64 kernel: Neumaier sums in
-// binary64.  Binary32 kernel: compensated binary32 pairs (TwoSum for the
-// running sum, an FMA-exact product for Y^2), widened to binary64 at the end.
+// Per-lane tally of sum(Y) and sum(Y^2): Neumaier sums in binary64.
 template <typename R> struct Tally;
 template <> struct Tally<double> {
   double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
@@ -134,29 +109,9 @@ template <> struct Tally<double> {
   __device__ double sum() const { return s + c; }
   __device__ double sum2() const { return s2 + c2; }
 };
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
-  const float s = hi + b;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (b - bb);
-  hi = s;
-  lo += err;
-}
-template <> struct Tally<float> {
-  float s = 0.f, c = 0.f, s2 = 0.f, c2 = 0.f;
-  __device__ void add(float y) {
-    two_sum_acc(s, c, y);
-    const float p = y * y;
-    const float e = fmaf(y, y, -p);  // exact: y*y = p + e
-    two_sum_acc(s2, c2, p);
-    c2 += e;
-  }
-  __device__ double sum() const { return (double)s + (double)c; }
-  __device__ double sum2() const { return (double)s2 + (double)c2; }
-};
 
 // Ray weight w_g / (p(n,g) q(Omega)) from the integer counts (Eq. 14 with the
-// pdfs of Eqs. 4, 9, 16).  The binary32 kernel reads the plain proposal's
-// weights from a host-built table and evaluates per-cell proposals in binary32.
+// pdfs of Eqs. 4, 9, 16).
 template <typename R>
 __device__ __forceinline__ R ray_weight(const TraceArgs &a, bool plain, int n, int g,
                                         unsigned long long mn, unsigned long long mg, double ph);
@@ -166,14 +121,6 @@ __device__ __forceinline__ double ray_weight<double>(const TraceArgs &a, bool, i
                                                      double ph) {
   const double p = ((double)mn * 2.3283064365386963e-10) * ((double)mg * 2.3283064365386963e-10);
   return (__ldg(a.w_g + g) / p) * (6.283185307179586 / ph);
-}
-template <>
-__device__ __forceinline__ float ray_weight<float>(const TraceArgs &a, bool plain, int n, int g,
-                                                   unsigned long long mn, unsigned long long mg,
-                                                   double ph) {
-  if (plain) return __ldg(a.wgt32 + n * a.ng + g);
-  const float p = ((float)mn * 2.3283064365386963e-10f) * ((float)mg * 2.3283064365386963e-10f);
-  return __fdividef((float)__ldg(a.w_g + g), p) * __fdividef(6.2831855f, (float)ph);
 }
 
 // Distance parameters of one axis of the parametric ray o + t d: the m-th face
@@ -514,10 +461,8 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s) {
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const size_t smem =
       a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) : 0;
-  if (precision == 1)
-    trace_kernel<double><<<(unsigned)blocks, threads, smem, s>>>(a);
-  else
-    trace_kernel<float><<<(unsigned)blocks, threads, smem, s>>>(a);
+  if (precision != 1) return cudaErrorInvalidValue;  // FP32 solves run trace_fp32.cu's kernels
+  trace_kernel<double><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -329,6 +329,76 @@ def test_learned_counts_are_exact_and_close():
     assert oracle.learned_counts(q, nb, ng, 1.0)[2] == 2**23 - 1
 
 
+def _gamma(n):
+    """Higham's gamma_n = n u / (1 - n u), u = 2^-24 (binary32 unit roundoff): the
+    relative error bound of a recursive sum of n + 1 nonnegative terms."""
+    from fractions import Fraction
+    u = Fraction(1, 2**24)
+    return n * u / (1 - n * u)
+
+
+def test_learned_counts_against_exact_rationals():
+    """The binary32 count rule against exact rational arithmetic on the same
+    binary32-rounded inputs x_k = RN32(q_k).  For K nonnegative weights summed in
+    order, |fl(sum) - sum| <= gamma_(K-1) sum; the quotient adds one rounding
+    (1 + delta, |delta| <= u) and the floor at most one count.  So a count m_k of
+    a weight with exact share r_k = x_k / sum x obeys
+
+        |m_k - 2^32 r_k| <= 2^32 r_k e + 1,  e = (1 + u) / (1 - gamma) - 1
+
+    (e bounds the larger side: (1 - u) / (1 + gamma) >= 1 - e), except the
+    remainder bin (the first largest weight), whose error is at most the sum of
+    the others'.  The band level compounds the in-band sums (gamma_(ng - 1)) and
+    the sum over bands (gamma_(nb - 1)).  A wrong order of rounding, a dropped
+    floor or a misplaced remainder breaks these bounds by whole counts."""
+    from fractions import Fraction
+    rng = np.random.default_rng(41)
+    u = Fraction(1, 2**24)
+    for nb, ng, alpha in ((40, 8, 0.3), (7, 5, 2.0), (3, 2, 0.05)):
+        q = rng.dirichlet(np.ones(nb * ng) * alpha)
+        q[rng.integers(0, nb * ng, 3)] = 0.0
+        cn, cg, _ = oracle.learned_counts(q, nb, ng, 0.5)
+        x = [Fraction(float(np.float32(v))) for v in q]
+        pg = np.diff(np.concatenate([np.zeros((nb, 1), np.int64), cg.astype(np.int64)], axis=1), axis=1)
+        ga = _gamma(ng - 1)
+        e_g = (1 + u) / (1 - ga) - 1
+        band = []
+        for n in range(nb):
+            xs = x[n * ng:(n + 1) * ng]
+            s = sum(xs)
+            band.append(s)
+            if s == 0:  # never drawn: uniform counts
+                assert np.all(np.abs(pg[n] - 2**32 / ng) <= ng)
+                continue
+            kmax = int(np.argmax(np.array([float(v) for v in xs])))
+            for k in range(ng):
+                target = Fraction(2**32) * xs[k] / s
+                if xs[k] == 0:
+                    assert pg[n, k] == 0
+                elif k != kmax:
+                    assert abs(pg[n, k] - target) <= target * e_g + 1, (n, k)
+            others = sum(Fraction(2**32) * xs[k] / s * e_g + 1 for k in range(ng) if k != kmax)
+            assert abs(pg[n, kmax] - Fraction(2**32) * xs[kmax] / s) <= others
+        # bands: in-band binary32 sums, then their binary32 sum, then the quotient
+        gb = _gamma(nb - 1)
+        e_n = (1 + ga) * (1 + u) / ((1 - ga) * (1 - gb)) - 1
+        W = sum(band)
+        pn = np.diff(np.concatenate([[0], cn.astype(np.int64)]))
+        kmax = int(np.argmax(np.array([float(np.float32(sum(np.float32(v) for v in
+                                                              q[n * ng:(n + 1) * ng])))
+                                       for n in range(nb)])))
+        others = 0
+        for n in range(nb):
+            target = Fraction(2**32) * band[n] / W
+            if n == kmax:
+                continue
+            assert abs(pn[n] - target) <= target * e_n + 1, n
+            others += target * e_n + 1
+        assert abs(pn[kmax] - Fraction(2**32) * band[kmax] / W) <= others
+        # the counts are exact partitions of 2^32
+        assert int(cn[-1]) == 2**32 and np.all(cg[:, -1] == 2**32)
+
+
 def test_learned_counts_reproduce_dyadic_probabilities():
     """Probabilities that are multiples of 2^-24 (one band: exact in binary32, and
     so are all their partial sums below 1) come back as the same counts."""

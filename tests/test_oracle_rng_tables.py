@@ -22,6 +22,23 @@ def _draws(n, block=0, snap=0, key=(0, 0)):
     return oracle.philox(ctr, key)
 
 
+@pytest.mark.parametrize("ctr,key,expect", [
+    # Known-answer vectors published with the reference implementation of the
+    # generator (Random123, Salmon et al., SC'11): Philox4x32 with 10 rounds on an
+    # all-zero input, an all-ones input, and the hexadecimal digits of pi
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_philox4x32_10_known_answers(ctr, key, expect):
+    """The generator's identity: the multipliers, the Weyl key increments, the
+    word permutation and the round count are fixed by these outputs (a single
+    wrong constant or round changes every word)."""
+    out = oracle.philox(np.array(ctr, dtype=np.uint32), np.array(key, dtype=np.uint32))
+    assert tuple(int(v) for v in out[0]) == expect
+
+
 def test_philox_words_uniform_chi2():
     w = _draws(1 << 18)
     for lane in range(4):

@@ -50,8 +50,11 @@ typedef enum {
 } mcrt_status;
 
 enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };
-/* MCRT_FP32: traversal, table lookups and exp in binary32, ray weights and all
- * per-cell tallies in binary64 (compensated).  MCRT_FP64: everything binary64. */
+/* MCRT_FP32: traversal, table lookups, exp, the ray weight (a binary64 host
+ * table rounded once) and each ray's sample Y in binary32; the per-cell tallies
+ * sum Y and Y^2 in binary64 with Neumaier compensation (runs of 32 samples
+ * summed exactly first; mcrt_tuning.tally_binary32 selects compensated binary32
+ * pairs instead).  MCRT_FP64: everything binary64. */
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
 /* Ray origin: uniform in the cell volume (f_V = 1/V_i, Eq. 4) or the cell centre
  * (Algorithm 1, "ray.pos <- cell.center"). */
@@ -149,6 +152,13 @@ typedef struct {
                               and were finished where they started (see
                               mcrt_tuning); 0 in every solve whose results are
                               bitwise independent of the launch shape            */
+  float trace_ms;          /* FP32 solves: device time of the trace kernel alone,
+                              the warp-parallel march of the long rays, and the
+                              per-cell reduction (CUDA events recorded on the
+                              solve's stream between the launches, summed over
+                              chunks); 0 for FP64 solves                          */
+  float long_ms;
+  float reduce_ms;
 } mcrt_solve_stats;
 
 /* Launch shape of the FP32 trace kernel.  The paper sizes its launches so that
@@ -181,6 +191,12 @@ typedef struct {
                               segments; < 0: never hand off                     */
   int long_ray_flight;     /* 0: default (32); > 0: x/z crossings left in the
                               flight for a hand-off; < 0: any flight            */
+  int tally_binary32;      /* 0 (default): binary64 per-cell tallies -- each run
+                              of 32 samples of a cell summed exactly, the runs
+                              added with Neumaier's compensated binary64 sum
+                              (within about 2^-51 of sum |Y| of the exact sum
+                              of the samples); 1: compensated binary32 pairs
+                              (within about 2e-7 of sum |Y|), a little cheaper */
 } mcrt_tuning;
 
 /* Number of overlaid grids the multigrid march can use on an nx x ny x nz grid
@@ -260,8 +276,16 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
  *  - q_out, sigma_out (nullable) and p->steps_out (nullable) are device pointers,
  *    box-sized as for mcrt_solve_qrad; the call is asynchronous on cuda_stream.
  *  - The first call on a device looks up the array's device address on that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture.
+ *    device (cudaGetSymbolAddress).  Under CUDA's lazy module loading (the
+ *    default since CUDA 12.2) that look-up is what loads the array -- a one-time
+ *    64 MiB device allocation -- and the first launch of each kernel loads its
+ *    code.  So make one call per device during set-up, before the host reserves
+ *    its memory and before any stream capture (or run with
+ *    CUDA_MODULE_LOADING=EAGER); later calls allocate nothing.
+ *  - The first call after mcrt_set_kdist or mcrt_set_fields rebuilds the plain
+ *    proposal (Eqs. 13, 16) on the host from fixed buffers and uploads it from
+ *    pageable memory (the call returns once the copies are staged); make that
+ *    call outside stream capture too.
  *  - 8 MiB of the array holds the long rays handed to the warp-parallel march
  *    (2^16 entries, the least buffer of a regular solve), so the results equal
  *    mcrt_solve_qrad's bit for bit unless more rays than that are handed off.

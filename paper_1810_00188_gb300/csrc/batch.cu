@@ -71,15 +71,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
 
   const int nb = a.nb, ng = a.ng, nT = a.nT, N = a.rays;
   const float4 *__restrict__ kbtab = a.kbtab32;  // {kappa, slope, B, slope} per (n, g, t)
-  const float tol = (float)a.tol;
+  const float tol = a.tol32;
   // the grid, fields, walls and proposal of the snapshot being solved (a batch
   // loads them when a warp moves to another snapshot; a single solve never does)
   int nx = a.nx, ny = a.ny, nz = a.nz, nxy = nx * ny;
   int bi0_b = 0, bj0_b = 0, bk0_b = 0, bnx_b = 0, bny_b = 0, bnz_b = 0;
   const uint2 *__restrict__ field = a.fpos32;
-  float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
+  float DX = a.dx32, DY = a.dy32, DZ = a.dz32;
   const float *__restrict__ yfs = a.yf32;
-  float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
+  float eps0 = a.eps32[0], eps1 = a.eps32[1];
   const float *__restrict__ bwall_b = nullptr;
   const float *__restrict__ wgt_b = nullptr;
   const unsigned long long *__restrict__ ccn_b = nullptr;
@@ -240,12 +240,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           // direction: hemisphere of the y axis by the integer count `hemi` of
           // 2^23, mu uniform inside it (plain: mu = 1 - 2 U); phi = 2 pi R_phi
           const unsigned m0 = u.x >> 9;
-          // branch-free: the plain proposal's hemisphere count is 2^22, whose
-          // reciprocal is exact
           const bool up = m0 < hemi;
           const float h = u23_to_float(up ? hemi : 8388608u - hemi);
-          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) *
-                           (plain ? 2.384185791015625e-07f : __frcp_rn(h));
+          // the plain proposal's hemisphere count is 2^22, whose reciprocal is
+          // exact; a per-cell count takes a correctly rounded reciprocal (a
+          // warp-uniform branch, so the plain path never evaluates it)
+          float rh = 2.384185791015625e-07f;
+          if (!plain) rh = __frcp_rn(h);
+          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) * rh;
           const float mu = up ? 1.f - mt : -mt;
           const float ph = h * 1.1920928955078125e-07f;
           if (plain) {
@@ -572,16 +574,55 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
 }
 
 // Per-cell reduction of a batched launch (as reduce_cells_kernel of
-// trace_fp32.cu; each position goes to the snapshot that owns it).  A warp takes
-// 32 consecutive chunk positions; for each
-// cell the lanes sum its N samples in a fixed order (lane l takes samples l,
-// l + 32, ..., sums each batch of 8 pairwise and adds the batch sums to
-// compensated binary32 pairs, then a fixed butterfly of pair additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
-// (Eq. 8) and the standard error in binary64 for their own cell at once.  The
-// order never depends on scheduling, so Q and sigma are reproducible bit for bit.
-// BATCH: the positions of a batched launch; each one is reduced into the
-// outputs of the snapshot that owns it.
+// trace_fp32.cu: lane c of a warp takes the cell at chunk position c and sums its
+// N samples in order into binary64 tallies, warp_tally64); each position goes
+// to the outputs of the snapshot that owns it.  The order never depends on
+// scheduling, so Q and sigma are reproducible bit for bit and equal the single
+// solve's.
 __global__ void __launch_bounds__(256) reduce_cells_batch_kernel(const TraceArgs a) {
+  __shared__ __align__(16) float tiles[WARPS][32][36];
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int N = a.rays;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < P;
+       base += nwarps * 32) {
+    int bx = 0, by = 0, bz = 0;
+    long long bc = 0;
+    double *oq = nullptr, *osig = nullptr;
+    bool mine = false;
+    if (base + lane < P) {
+      const long long pos = a.chunk_p0 + base + lane;
+      int lo = 0, hi = a.nsnaps - 1;  // the owning snapshot (binary search over the start positions)
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.snaps[mid].p0 <= pos)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const SnapArgs &sn = a.snaps[lo];
+      mine = brick_cell_d(sn.nx, sn.ny, sn.nz, pos - sn.p0, bx, by, bz);
+      bc = bx + (long long)sn.nx * (by + (long long)sn.ny * bz);
+      oq = sn.q;
+      osig = sn.sigma;
+    }
+    const unsigned cells = __ballot_sync(0xffffffffu, mine);
+    if (!cells) continue;  // warp-uniform
+    double S, S2;
+    warp_tally64(a.ybuf + (size_t)base * (unsigned)N, N, cells, lane, tiles[threadIdx.x >> 5], S, S2);
+    if (mine) {
+      const double Nd = (double)N;
+      const double Q = S / Nd;
+      oq[bc] = Q;
+      if (osig) osig[bc] = N > 1 ? sqrt(fmax(S2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
+    }
+  }
+}
+
+// The binary32 tally of a batched launch, on request (mcrt_tuning.tally_binary32;
+// as reduce_cells32_kernel of trace_fp32.cu).
+__global__ void __launch_bounds__(256) reduce_cells_batch32_kernel(const TraceArgs a) {
   constexpr bool BATCH = true;
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -748,8 +789,11 @@ cudaError_t launch_trace_fp32_batch(const TraceArgs &args, int min_blocks, int s
   }
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  reduce_cells_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
+  if (a.tally32)
+    reduce_cells_batch32_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  else
+    reduce_cells_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,9 @@ struct mcrt_ctx {
   // long rays handed off by the FP32 exact march (LongRay entries)
   DevBuf longbuf;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel marks of the last FP32 solve: four events per chunk (launch_trace_fp32)
+  std::vector<cudaEvent_t> kev;
+  int kev_chunks = 0;
   cudaStream_t last_stream = nullptr;
   bool solved = false;
   int last_launches = 0;
@@ -59,6 +62,7 @@ struct mcrt_ctx {
   int scratch_mib = 1024;
   int long_steps = 1024;    // hand-off threshold in segments (<= 0: never)
   float long_flight = 32;   // x/z crossings left in the flight for a hand-off
+  int tally32 = 0;          // per-cell tallies in binary32 pairs instead of binary64
   double last_T_max = 0;
   std::string err;
 };

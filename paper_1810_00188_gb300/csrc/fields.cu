@@ -132,6 +132,18 @@ int multigrid_levels(int nx, int ny, int nz) {
   return L;
 }
 
+long long grid_stride_blocks() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 16;
+  if (sms[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    sms[dev] = n;
+  }
+  return 16LL * sms[dev];
+}
+
 long long multigrid_cells(int nx, int ny, int nz, int levels) {
   long long total = 0;
   for (int l = 0; l < levels; ++l) total += (long long)(nx >> l) * (ny >> l) * (nz >> l);
@@ -143,7 +155,7 @@ cudaError_t launch_coarsen(const double2 *fine, int n0, int n1, int n2, double2 
   const long long nc = (long long)(n0 / 2) * (n1 / 2) * (n2 / 2);
   if (nc <= 0) return cudaSuccess;
   long long blocks = (nc + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
   coarsen_kernel<<<(unsigned)blocks, 256, 0, s>>>(fine, n0, n1, n2, coarse, yf, level);
   return cudaGetLastError();
 }
@@ -152,7 +164,7 @@ cudaError_t launch_pack_positions(const double2 *f64, long long n, double T0, do
                                   double inv_xref, uint2 *pos, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
   pack_positions_kernel<<<(unsigned)blocks, 256, 0, s>>>(f64, n, T0, inv_dT, nT, inv_xref, pos);
   return cudaGetLastError();
 }
@@ -165,7 +177,7 @@ cudaError_t launch_pack_fields(const void *T, const void *x, int fp64_in, double
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
   long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;  // grid-stride: 16 blocks per SM
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();  // grid-stride
   pack_fields_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, x, fp64_in, x_ref, n, f64, stats);
   return cudaGetLastError();
 }

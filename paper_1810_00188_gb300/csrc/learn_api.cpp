@@ -435,6 +435,7 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
   t.c_out = cost_out;
   t.err = (unsigned long long *)ctx->lerr.p;
   CK(cudaMemsetAsync(ctx->counters.p, 0, mcrt::NCOUNTERS * sizeof(unsigned long long), s), "clear counters");
+  ctx->kev_chunks = 0;
   CK(cudaEventRecord(ctx->ev0, s), "event");
   int launches = 0;
   for (long long p0 = 0; p0 < P; p0 += Pc) {

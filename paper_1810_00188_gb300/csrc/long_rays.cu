@@ -72,11 +72,11 @@ __device__ __forceinline__ Geom geom_of(const TraceArgs &a, unsigned snap) {
     g.ny = a.ny;
     g.nz = a.nz;
     g.reflect = a.reflect;
-    g.DX = (float)a.dx;
-    g.DY = (float)a.dy;
-    g.DZ = (float)a.dz;
-    g.eps0 = (float)a.eps_wall[0];
-    g.eps1 = (float)a.eps_wall[1];
+    g.DX = a.dx32;
+    g.DY = a.dy32;
+    g.DZ = a.dz32;
+    g.eps0 = a.eps32[0];
+    g.eps1 = a.eps32[1];
     g.snapw = a.snapshot;
   }
   return g;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     if (handed > (unsigned long long)total) atomicAdd(a.counters + 9, handed - (unsigned long long)total);
   }
   const float4 *__restrict__ kbtab = a.kbtab32;
-  const float tol = (float)a.tol;
+  const float tol = a.tol32;
   const int nb = a.nb, N = a.rays;
   const long long guard_max = 2LL * a.max_steps + 64;
   unsigned long long w_steps = 0;

@@ -234,6 +234,17 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
   return MCRT_OK;
 }
 
+// The FP32 kernels' binary32 copies of tol, the cell sizes and the wall
+// emissivities (rounded once here).
+static void set_float_copies(mcrt::TraceArgs *a) {
+  a->tol32 = (float)a->tol;
+  a->dx32 = (float)a->dx;
+  a->dy32 = (float)a->dy;
+  a->dz32 = (float)a->dz;
+  a->eps32[0] = (float)a->eps_wall[0];
+  a->eps32[1] = (float)a->eps_wall[1];
+}
+
 void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int b[6],
                      mcrt::TraceArgs *ap) {
   const mcrt_grid_desc &g = ctx->grid;
@@ -285,6 +296,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
   a.origin = p->origin;
   a.tol = p->tol;
+  set_float_copies(&a);
   a.key0 = (unsigned)(p->seed & 0xffffffffu);
   a.key1 = (unsigned)(p->seed >> 32);
   a.snapshot = p->snapshot;
@@ -297,6 +309,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.bnz = b[5] - b[4];
   a.ncells_box = (long long)a.bnx * a.bny * a.bnz;
   a.counters = (unsigned long long *)ctx->counters.p;
+  a.tally32 = ctx->tally32;
 }
 
 }  // namespace mcrt_host
@@ -666,6 +679,13 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     a.step_acc = (unsigned long long *)ctx->step_acc.p;
     const int rl = setup_long_rays(ctx, Pc * (long long)p->rays_per_cell, &a);
     if (rl != MCRT_OK) return rl;
+    const int nchunks = (int)((P + Pc - 1) / Pc);
+    while ((int)ctx->kev.size() < 4 * nchunks) {
+      cudaEvent_t e = nullptr;
+      CK(cudaEventCreate(&e), "event");
+      ctx->kev.push_back(e);
+    }
+    ctx->kev_chunks = 0;
     CK(cudaEventRecord(ctx->ev0, s), "event");
     for (long long p0 = 0; p0 < P; p0 += Pc) {
       a.chunk_p0 = p0;
@@ -673,11 +693,15 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
       if (dst)
         CK(cudaMemsetAsync(ctx->step_acc.p, 0, (size_t)(a.chunk_p1 - p0) * sizeof(unsigned long long), s),
            "clear step scratch");
-      CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
+      CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s,
+                                 ctx->kev.data() + 4 * ctx->kev_chunks),
+         "trace launch");
+      ++ctx->kev_chunks;
       launches += mcrt::long_rays_on(a) ? 3 : 2;
     }
     CK(cudaEventRecord(ctx->ev1, s), "event");
   } else {
+    ctx->kev_chunks = 0;
     CK(cudaEventRecord(ctx->ev0, s), "event");
     CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
     CK(cudaEventRecord(ctx->ev1, s), "event");
@@ -717,11 +741,13 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
       t->steps_per_round != 4)
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   if (t->long_ray_flight > (1 << 24)) return fail(ctx, MCRT_E_ARG, "long_ray_flight above 2^24");
+  if (t->tally_binary32 != 0 && t->tally_binary32 != 1) return fail(ctx, MCRT_E_ARG, "tally_binary32 not 0 or 1");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
   ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
   ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
   ctx->long_steps = t->long_ray_steps ? (t->long_ray_steps > 0 ? t->long_ray_steps : -1) : 1024;
   ctx->long_flight = t->long_ray_flight ? (t->long_ray_flight > 0 ? (float)t->long_ray_flight : -1.f) : 32.f;
+  ctx->tally32 = t->tally_binary32;
   return MCRT_OK;
 }
 
@@ -732,6 +758,7 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   t->scratch_mib = ctx->scratch_mib;
   t->long_ray_steps = ctx->long_steps;
   t->long_ray_flight = ctx->long_flight < 0.f ? -1 : (int)ctx->long_flight;
+  t->tally_binary32 = ctx->tally32;
   return MCRT_OK;
 }
 
@@ -758,6 +785,15 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   out->launches = ctx->last_launches;
   out->long_rays = c[8];
   out->long_overflow = c[9];
+  out->trace_ms = out->long_ms = out->reduce_ms = 0.f;
+  for (int k = 0; k < ctx->kev_chunks; ++k) {
+    float t[3];
+    for (int j = 0; j < 3; ++j)
+      CK(cudaEventElapsedTime(&t[j], ctx->kev[4 * k + j], ctx->kev[4 * k + j + 1]), "elapsed");
+    out->trace_ms += t[0];
+    out->long_ms += t[1];
+    out->reduce_ms += t[2];
+  }
   return MCRT_OK;
 }
 
@@ -774,6 +810,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     for (DevBuf *b : bufs) release(*b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     cudaGetLastError();
   }
   delete ctx;
@@ -843,18 +880,9 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   if (!ctx) return MCRT_E_ARG;
   if (!p || !q_out) return fail(ctx, MCRT_E_ARG, "null params or q_out");
   if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_ARG, "the allocation-free solve is FP32 only");
-  if (p->rays_per_cell < 1) return fail(ctx, MCRT_E_ARG, "rays_per_cell < 1");
-  if (p->max_steps < 1) return fail(ctx, MCRT_E_ARG, "max_steps < 1");
-  if (!(p->tol > 0.0 && p->tol < 1.0)) return fail(ctx, MCRT_E_ARG, "tol outside (0, 1)");
-  if (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER)
-    return fail(ctx, MCRT_E_ARG, "bad origin");
-  if (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL)
-    return fail(ctx, MCRT_E_ARG, "bad proposal");
-  if ((unsigned long long)p->ray_offset + (unsigned long long)p->rays_per_cell > (1ull << 32))
-    return fail(ctx, MCRT_E_ARG, "ray indices beyond 2^32");
-  if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz))
-    return fail(ctx, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)]");
-  if (p->mg_levels > 1 && p->mg_steps < 1) return fail(ctx, MCRT_E_ARG, "mg_steps < 1");
+  int b[6];
+  const int rc0 = check_solve_params(ctx, p, b);
+  if (rc0 != MCRT_OK) return rc0;
   // scratch layout in the static array: counters | long rays | per-position step
   // sums | samples.  The long-ray region holds the smallest buffer a regular
   // solve uses, so both hand the same rays off and give the same bits.
@@ -869,24 +897,11 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
                     std::to_string(total >> 20) + " MiB: at most " +
                     std::to_string((total - head_bytes - 256 - sizeof(unsigned long long)) / sizeof(float)) +
                     " rays per cell)");
-  const mcrt_grid_desc &g = ctx->grid;
-  int b[6] = {0, g.nx, 0, g.ny, 0, g.nz};
-  if (p->use_box) {
-    std::memcpy(b, p->box, sizeof(b));
-    if (b[0] < 0 || b[1] > g.nx || b[0] > b[1] || b[2] < 0 || b[3] > g.ny || b[2] > b[3] ||
-        b[4] < 0 || b[5] > g.nz || b[4] > b[5])
-      return fail(ctx, MCRT_E_ARG, "box outside the grid");
-  }
-  if (!ctx->have_kdist || !ctx->have_fields) return fail(ctx, MCRT_E_STATE, "set kdist and fields first");
-  if (p->proposal == MCRT_PROPOSAL_CELL && !ctx->have_cell_prop)
-    return fail(ctx, MCRT_E_STATE, "no cell proposal");
-  if (ctx->nT > 512)
-    return fail(ctx, MCRT_E_UNSUPPORTED, "the FP32 kernel supports tables of at most 512 T nodes");
-  DeviceGuard dg(g.device);
+  DeviceGuard dg(ctx->grid.device);
   if (!dg.ok) return fail(ctx, MCRT_E_CUDA, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   void *base = nullptr;
-  CK(mcrt::noalloc_scratch(g.device, &base), "static scratch address");
+  CK(mcrt::noalloc_scratch(ctx->grid.device, &base), "static scratch address");
 
   const double Tm = proposal_T_max(ctx);
   if (!ctx->prop_valid || ctx->prop_T_max != Tm) {
@@ -896,61 +911,9 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   const long long nbox = (long long)(b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]);
   if (nbox == 0) return MCRT_OK;
 
+  // the regular solve's launch arguments; only the scratch and outputs differ
   mcrt::TraceArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.nz = g.nz;
-  a.dx = g.lx / g.nx;
-  a.dy = g.ly / g.ny;
-  a.dz = g.lz / g.nz;
-  a.nb = ctx->nb;
-  a.ng = ctx->ng;
-  a.nT = ctx->nT;
-  a.T0 = ctx->T0;
-  a.inv_dT = 1.0 / ctx->dT;
-  a.inv_xref = 1.0 / ctx->x_ref;
-  a.eps_wall[0] = g.eps_wall[0];
-  a.eps_wall[1] = g.eps_wall[1];
-  a.reflect = g.reflect;
-  a.yf64 = (const double *)ctx->yf64.p;
-  a.yf32 = (const float *)ctx->yf32.p;
-  a.xz_walls = g.xz_walls;
-  a.fpos32 = (const uint2 *)ctx->fpos32.p;
-  a.ktab32 = (const float2 *)ctx->ktab32.p;
-  a.btab32 = (const float2 *)ctx->btab32.p;
-  a.kbtab32 = (const float4 *)ctx->kbtab32.p;
-  a.bwall32 = (const float *)ctx->bwall32.p;
-  a.w_g = (const double *)ctx->wg.p;
-  a.w_g32 = (const float *)ctx->wg32.p;
-  a.wgt32 = (const float *)ctx->wgt32.p;
-  a.cn = (const unsigned long long *)ctx->cn.p;
-  a.cg = (const unsigned long long *)ctx->cg.p;
-  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024 ? 1 : 0;
-  a.guide = (const unsigned short *)ctx->guide.p;
-  if (p->proposal == MCRT_PROPOSAL_CELL) {
-    a.cell_cn = (const unsigned long long *)ctx->cell_cn.p;
-    a.cell_cg = (const unsigned long long *)ctx->cell_cg.p;
-    a.cell_hemi = (const unsigned int *)ctx->cell_hemi.p;
-    if (mcrt::fp32_cell_stage_fits(ctx->nb, ctx->ng)) a.counts_in_smem |= 2;
-  }
-  a.rays = p->rays_per_cell;
-  a.max_steps = p->max_steps;
-  a.mg_levels = p->mg_levels > 1 ? p->mg_levels : 1;
-  a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
-  a.origin = p->origin;
-  a.tol = p->tol;
-  a.key0 = (unsigned)(p->seed & 0xffffffffu);
-  a.key1 = (unsigned)(p->seed >> 32);
-  a.snapshot = p->snapshot;
-  a.ray_offset = p->ray_offset;
-  a.bi0 = b[0];
-  a.bj0 = b[2];
-  a.bk0 = b[4];
-  a.bnx = b[1] - b[0];
-  a.bny = b[3] - b[2];
-  a.bnz = b[5] - b[4];
-  a.ncells_box = nbox;
+  fill_trace_args(ctx, p, b, &a);
   a.q = q_out;
   a.sigma = sigma_out;
   a.steps_cell = (unsigned long long *)p->steps_out;
@@ -1093,6 +1056,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     const mcrt_grid_desc &g = c->grid;
     mcrt::TraceArgs &a = args[k];
     std::memset(&a, 0, sizeof(a));
+    a.tally32 = items[0].ctx->tally32;
     a.nx = g.nx;
     a.ny = g.ny;
     a.nz = g.nz;
@@ -1135,6 +1099,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.mg_steps = p->mg_levels > 1 ? p->mg_steps : 0x7fffffff;
     a.origin = p->origin;
     a.tol = p->tol;
+    set_float_copies(&a);
     a.key0 = (unsigned)(p->seed & 0xffffffffu);
     a.key1 = (unsigned)(p->seed >> 32);
     a.snapshot = items[k].snapshot;

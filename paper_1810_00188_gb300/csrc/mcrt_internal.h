@@ -117,6 +117,11 @@ struct TraceArgs {
   // solve
   int rays, max_steps, origin;
   double tol;
+  // the FP32 kernels' copies of tol, the cell sizes and the wall emissivities,
+  // rounded once on the host: the kernels read them where they are used instead
+  // of converting the binary64 members there (a conversion on the narrow binary64
+  // pipe each time the compiler rematerialises the value)
+  float tol32, dx32, dy32, dz32, eps32[2];
   unsigned int key0, key1, snapshot;
   unsigned long long ray_offset;
   int bi0, bj0, bk0, bnx, bny, bnz;
@@ -124,12 +129,18 @@ struct TraceArgs {
   // outputs (box-sized)
   double *q, *sigma;
   unsigned long long *steps_cell;
+  // FP32 kernels: per-cell tallies in binary32 pairs (1) instead of binary64 (0)
+  int tally32;
   unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps)
                                  // [5] error flags [6] FP32 kernel: claimed positions
                                  // [7] long rays handed off by this launch
                                  // [8] long rays finished by the warp-parallel march
                                  // [9] long rays that found the buffer full (NCOUNTERS entries)
 };
+
+// Largest grid of the grid-stride kernels (reductions, packing, coarsening): 16
+// CTAs per SM of the current device (its SM count read once per device).
+long long grid_stride_blocks();
 
 // Multigrid grid count of an nx x ny x nz grid and the cells of all its grids.
 int multigrid_levels(int nx, int ny, int nz);
@@ -147,8 +158,11 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // reduction (trace_fp32.cu); two or three launches per chunk.  min_blocks:
 // occupancy target (1-4 CTAs of 256 threads per SM); steps_per_round: march
 // steps between refills of idle lanes (1, 2, 4).
+// marks (nullable): four events recorded on s before the trace kernel, after it,
+// after the long-ray march (right after the trace kernel when there is none) and
+// after the reduction.
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
-                              cudaStream_t s);
+                              cudaStream_t s, cudaEvent_t *marks = nullptr);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);
 // The warp-parallel march of the long rays the last FP32 trace launch handed off
 // (a.long_rays[0 .. min(counters[7], long_cap))); writes their samples and adds

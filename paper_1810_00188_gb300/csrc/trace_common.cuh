@@ -234,5 +234,112 @@ __device__ __forceinline__ void warp_cell_sums(const float *__restrict__ y, int 
   }
 }
 
+// ---- binary64 per-cell tallies (Eq. 8: Q_i is the mean of the samples) -------
+//
+// Binary64 Neumaier summation of every sample would keep GB300's narrow binary64
+// pipe busy for longer than the trace itself, so the tally is built in two
+// stages that give binary64 accuracy at a few binary64 operations per 32
+// samples:
+//  1. a tile of 32 consecutive samples of one cell is summed EXACTLY in 64-bit
+//     fixed point (integer arithmetic): each binary32 y = m 2^(e - 150) is
+//     shifted to the unit 2^(E - 184), E the tile's largest exponent field, and
+//     its square m^2 2^(2e - 300) to the unit 2^(2E - 310).  Bits below the unit
+//     are dropped (at most one unit per sample: 2^-57 of the tile's largest |y|,
+//     2^-56 of its largest y^2); 32 terms below 2^58 in magnitude cannot overflow;
+//  2. each tile sum is rounded once to binary64 (the integer-to-binary64
+//     conversion, then an exact power-of-two scaling) and added to the cell's
+//     running sum with Neumaier's compensated summation in binary64.
+// The result is within about 2^-51 of sum |y| (and of sum y^2) of the exact sums
+// of the binary32 samples -- binary64 quality -- and the order is fixed (samples
+// 0..N-1 of the cell, tile by tile), so it never depends on the launch.
+
+// s + c += b (Neumaier).  |s| >= |b| is decided on the bit patterns (integer
+// compare of the magnitudes; both finite).
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double b) {
+  const double t = s + b;
+  const unsigned long long ms = (unsigned long long)__double_as_longlong(s) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long mb = (unsigned long long)__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFull;
+  const bool ge = ms >= mb;
+  const double big = ge ? s : b, small = ge ? b : s;
+  c += (big - t) + small;
+  s = t;
+}
+
+// 2^k as a binary64 for k in [-1022, 1023] (exact, built from its bits).
+__device__ __forceinline__ double pow2d(int k) {
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// Exact sums of 32 binary32 values v[0..31] and of their squares (stage 1),
+// rounded to binary64 (stage 2's input).  Sets `bad` when a value is not finite.
+// Each value enters as its signed significand placed at bit 34 of a 64-bit word
+// and shifted right (arithmetically) by its exponent's distance d from the
+// largest; its square as m^2 placed at bit 10 and shifted right by 2d.
+__device__ __forceinline__ void tile_sums_exact(const unsigned (&v)[32], double &s1, double &s2, bool &bad) {
+  unsigned vmax = 0u;  // largest magnitude's bits: the largest exponent field
+#pragma unroll
+  for (int k = 0; k < 32; ++k) vmax = max(vmax, v[k] & 0x7FFFFFFFu);
+  const unsigned E = max(vmax >> 23, 1u);
+  bad |= E == 0xFFu;
+  long long acc = 0;
+  unsigned long long acc2 = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const unsigned e = (v[k] >> 23) & 0xFFu;
+    const unsigned m = (v[k] & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+    const unsigned d = E - max(e, 1u);  // >= 0
+    // y in units of 2^(E - 184): (+-m 2^34) >> d, truncated towards -inf
+    const int sm = (int)v[k] < 0 ? -(int)m : (int)m;
+    acc += ((long long)sm << 34) >> min(d, 63u);
+    // y^2 in units of 2^(2E - 310): (m^2 2^10) >> 2d
+    acc2 += (((unsigned long long)m * m) << 10) >> min(2u * d, 63u);
+  }
+  const int Ei = (int)min(E, 254u);
+  s1 = __ll2double_rn(acc) * pow2d(Ei - 184);
+  s2 = __ull2double_rn(acc2) * pow2d(2 * Ei - 310);
+}
+
+// Binary64 tallies of the warp's cells: lane c owns the cell whose N samples
+// start at y0 + c * N when bit c of `cells` is set.  Tiles of 32 samples are
+// staged through the warp's shared-memory tile ([cell][sample], rows padded to
+// 36 words: the row stores and the lanes' 16-byte row reads are conflict-free)
+// from coalesced loads of each cell's 32 consecutive samples (128 bytes,
+// streaming hint: read once).  Returns the lane's sum of y and of y^2 (NaN when
+// a sample is not finite); lanes without a cell return zeros.
+__device__ __forceinline__ void warp_tally64(const float *__restrict__ y0, int N, unsigned cells, int lane,
+                                             float (*tile)[36], double &sum, double &sum2) {
+  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
+  bool bad = false;
+  const bool mine = (cells >> lane) & 1u;
+  for (int r0 = 0; r0 < N; r0 += 32) {
+    const bool in = r0 + lane < N;
+    float ld[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc)
+      ld[cc] = ((cells >> cc) & 1u) && in ? __ldcs(y0 + (size_t)cc * (unsigned)N + (unsigned)(r0 + lane)) : 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) tile[cc][lane] = ld[cc];
+    __syncwarp();
+    if (mine) {
+      unsigned v[32];
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(&tile[lane][k]);
+        v[k] = __float_as_uint(f.x);
+        v[k + 1] = __float_as_uint(f.y);
+        v[k + 2] = __float_as_uint(f.z);
+        v[k + 3] = __float_as_uint(f.w);
+      }
+      double t1, t2;
+      tile_sums_exact(v, t1, t2, bad);
+      neumaier_add(s, c, t1);
+      neumaier_add(s2, c2, t2);
+    }
+    __syncwarp();
+  }
+  sum = bad ? __longlong_as_double(0x7FF8000000000000ll) : s + c;
+  sum2 = bad ? sum : s2 + c2;
+}
+
 }  // namespace
 }  // namespace mcrt

@@ -25,15 +25,18 @@
 //    grazing ray of a thin band, up to ~10^5 steps) is handed to the
 //    warp-parallel march of long_rays.cu instead of holding its lane to the end;
 //  * samples go to a scratch array indexed by (cell, ray); reduce_cells_kernel
-//    sums each cell's samples in a fixed order (pairwise batches of 8 added to
-//    compensated binary32 pairs per lane, binary64 across lanes), so Q and
-//    sigma do not depend on scheduling, launch shape or box.
+//    sums each cell's samples in a fixed order into binary64 tallies (exact
+//    32-sample tiles, Neumaier-compensated binary64 sums), so Q and sigma do
+//    not depend on scheduling, launch shape or box.
 //
 // GB300 issues binary64 arithmetic and int<->float conversions on a narrow pipe,
 // so the per-ray and per-step code uses neither: ray weights come from a
 // host-built FP64 table rounded once, each cell's table position is precomputed
-// (tpos), and the remaining conversions are exact bit constructions (unif,
-// u23_to_float).
+// (tpos), tol, the cell sizes and the wall emissivities arrive as binary32 copies
+// (converting the binary64 launch arguments in the kernel put a binary64
+// conversion wherever the compiler rematerialised them: 18M of them in a 48^3
+// solve, the binary64 pipe 37% busy), and the remaining conversions are exact bit
+// constructions (unif, u23_to_float).
 //
 // A round that makes no progress cannot happen; if it did, the warp sets an
 // error flag (counters[5]) and returns instead of spinning.  Warps claim runs
@@ -92,15 +95,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             ng = a.ng, nT = a.nT, N = a.rays;
   const uint2 *__restrict__ field = a.fpos32;
   const float4 *__restrict__ kbtab = a.kbtab32;  // {kappa, slope, B, slope} per (n, g, t)
-  const float tol = (float)a.tol;
-  const float DX = (float)a.dx, DY = (float)a.dy, DZ = (float)a.dz;
+  const float tol = a.tol32;
+  const float DX = a.dx32, DY = a.dy32, DZ = a.dz32;
   // stretched y (faces non-null): tsy holds 1/|d_y| and each y crossing adds the
   // next row's height; the height of row j of grid l from the faces
   const float *__restrict__ yfs = GEN ? a.yf32 : nullptr;
   auto dyl = [&](int j, int l) -> float {
     return __ldg(yfs + ((unsigned)(j + 1) << l)) - __ldg(yfs + ((unsigned)j << l));
   };
-  const float eps0 = (float)a.eps_wall[0], eps1 = (float)a.eps_wall[1];
+  const float eps0 = a.eps32[0], eps1 = a.eps32[1];
   float *__restrict__ Ybuf = a.ybuf;
   const unsigned long long ray_off = a.ray_offset_dev ? *a.ray_offset_dev : a.ray_offset;
 
@@ -108,6 +111,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   // proposal) its hemisphere count
   int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N;
   unsigned c_hemi = 4194304u;
+  // 1 / (hemisphere count) of each hemisphere, per cell (the plain proposal's
+  // 2^22 has the exact reciprocal 2^-22): one correctly rounded reciprocal per
+  // cell instead of one per ray
+  float c_rup = 2.384185791015625e-07f, c_rdn = 2.384185791015625e-07f;
   bool exhausted = false;
   unsigned head = 0, tail = 0;  // ring positions (mod POOL)
 
@@ -158,8 +165,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           c_r = 0;
           c_slot = (int)(p - 1 - a.chunk_p0);
           c_lin = (a.bi0 + c_bx) + nx * ((a.bj0 + c_by) + ny * (a.bk0 + c_bz));
+          c_rup = c_rdn = 2.384185791015625e-07f;
           if (!plain) {
             c_hemi = __ldg(a.cell_hemi + c_lin);
+            c_rup = __frcp_rn(u23_to_float(c_hemi));
+            c_rdn = __frcp_rn(u23_to_float(8388608u - c_hemi));
             if (cell_stage) {  // all of this cell's rays are initialised before the next cell's
               const unsigned long long *gcn = a.cell_cn + (size_t)c_lin * nb;
               const unsigned long long *gcg = a.cell_cg + (size_t)c_lin * nb * ng;
@@ -202,12 +212,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           // direction: hemisphere of the y axis by the integer count `hemi` of
           // 2^23, mu uniform inside it (plain: mu = 1 - 2 U); phi = 2 pi R_phi
           const unsigned m0 = u.x >> 9;
-          // branch-free: the plain proposal's hemisphere count is 2^22, whose
-          // reciprocal is exact
           const bool up = m0 < hemi;
           const float h = u23_to_float(up ? hemi : 8388608u - hemi);
-          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) *
-                           (plain ? 2.384185791015625e-07f : __frcp_rn(h));
+          const float mt = (u23_to_float(up ? m0 : m0 - hemi) + 0.5f) * (up ? c_rup : c_rdn);
           const float mu = up ? 1.f - mt : -mt;
           const float ph = h * 1.1920928955078125e-07f;
           if (plain) {
@@ -539,13 +546,44 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   }
 }
 
-// Per-cell reduction.  A warp takes 32 consecutive chunk positions; for each
-// cell the lanes sum its N samples in a fixed order (lane l takes samples l,
-// l + 32, ..., sums each batch of 8 pairwise and adds the batch sums to
-// compensated binary32 pairs, then a fixed butterfly of pair additions), and lane c keeps cell c's totals.  All lanes then form Q = sum / N
-// (Eq. 8) and the standard error in binary64 for their own cell at once.  The
-// order never depends on scheduling, so Q and sigma are reproducible bit for bit.
+// Per-cell reduction (Eq. 8: Q_i is the mean of the cell's samples; sigma_i its
+// standard error).  A warp takes 32 consecutive chunk positions, lane c the cell
+// at position c, and each lane sums its cell's N samples in order into binary64
+// tallies (warp_tally64: exact 32-sample tiles, Neumaier-compensated binary64
+// sums).  Q = sum / N and the standard error follow in binary64.  The order
+// never depends on scheduling, so Q and sigma are reproducible bit for bit.
 __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
+  __shared__ __align__(16) float tiles[WARPS][32][36];
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int N = a.rays;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  for (long long base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < P;
+       base += nwarps * 32) {
+    int bx = 0, by = 0, bz = 0;
+    const bool mine = base + lane < P && brick_cell(a, a.chunk_p0 + base + lane, bx, by, bz);
+    const unsigned cells = __ballot_sync(0xffffffffu, mine);
+    if (!cells) continue;  // warp-uniform
+    double S, S2;
+    warp_tally64(a.ybuf + (size_t)base * (unsigned)N, N, cells, lane, tiles[threadIdx.x >> 5], S, S2);
+    if (mine) {
+      const long long bc = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
+      const double Nd = (double)N;
+      const double Q = S / Nd;
+      a.q[bc] = Q;
+      if (a.sigma) a.sigma[bc] = N > 1 ? sqrt(fmax(S2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
+      if (a.steps_cell) a.steps_cell[bc] = a.step_acc[base + lane];
+    }
+  }
+}
+
+// The binary32 tally, on request (mcrt_tuning.tally_binary32): for each cell the
+// lanes sum its N samples in a fixed order (lane l takes samples l, l + 32, ...,
+// sums each batch of 8 pairwise in binary32 and adds the batch sums to
+// compensated binary32 pairs, then a fixed butterfly of pair additions), and
+// lane c keeps cell c's totals, converted to binary64 for Q and sigma.  Its
+// error is within about 2e-7 of sum |y| (warp_cell_sums).
+__global__ void __launch_bounds__(256) reduce_cells32_kernel(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const int N = a.rays;
@@ -696,7 +734,7 @@ cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int 
 }
 
 cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_per_round,
-                              cudaStream_t s) {
+                              cudaStream_t s, cudaEvent_t *marks) {
   if (args.chunk_p1 <= args.chunk_p0) return cudaSuccess;
   TraceArgs a = args;
   if (!long_rays_on(a)) a.long_steps = 0x7fffffff;  // no hand-off
@@ -705,17 +743,25 @@ cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_p
   cudaError_t e = cudaMemsetAsync(a.counters + 6, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const bool general = a.yf32 != nullptr || a.xz_walls != 0;
+  if (marks && (e = cudaEventRecord(marks[0], s)) != cudaSuccess) return e;
   e = dispatch(false, &a, min_blocks, steps_per_round, a.mg_levels > 1, general, s, smem, nullptr, nullptr);
   if (e != cudaSuccess) return e;
+  if (marks && (e = cudaEventRecord(marks[1], s)) != cudaSuccess) return e;
   if (long_rays_on(a)) {
     e = launch_long_rays(a, s);
     if (e != cudaSuccess) return e;
   }
+  if (marks && (e = cudaEventRecord(marks[2], s)) != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
+  if (a.tally32)
+    reduce_cells32_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  else
+    reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && marks) e = cudaEventRecord(marks[3], s);
+  return e;
 }
 
 }  // namespace mcrt

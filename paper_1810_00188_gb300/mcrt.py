@@ -59,7 +59,8 @@ class mcrt_solve_params(C.Structure):
 
 class mcrt_tuning(C.Structure):
     _fields_ = [("min_blocks_per_sm", C.c_int), ("steps_per_round", C.c_int),
-                ("scratch_mib", C.c_int), ("long_ray_steps", C.c_int), ("long_ray_flight", C.c_int)]
+                ("scratch_mib", C.c_int), ("long_ray_steps", C.c_int), ("long_ray_flight", C.c_int),
+                ("tally_binary32", C.c_int)]
 
 
 class mcrt_batch_item(C.Structure):
@@ -71,7 +72,8 @@ class mcrt_solve_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64), ("rays", C.c_uint64), ("capped", C.c_uint64),
                 ("wall_hits", C.c_uint64), ("max_ray_steps", C.c_uint64), ("T_max", C.c_double),
                 ("kernel_ms", C.c_float),
-                ("launches", C.c_int), ("long_rays", C.c_uint64), ("long_overflow", C.c_uint64)]
+                ("launches", C.c_int), ("long_rays", C.c_uint64), ("long_overflow", C.c_uint64),
+                ("trace_ms", C.c_float), ("long_ms", C.c_float), ("reduce_ms", C.c_float)]
 
 
 _lib = None
@@ -260,8 +262,10 @@ def mcrt_get_stats(ctx) -> dict:
 
 
 def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
-                    scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0):
+                    scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0,
+                    tally_binary32: int = 0):
     t = mcrt_tuning()
+    t.tally_binary32 = tally_binary32
     t.min_blocks_per_sm = min_blocks_per_sm
     t.steps_per_round = steps_per_round
     t.scratch_mib = scratch_mib
@@ -568,9 +572,10 @@ class Solver:
         return mcrt_get_stats(self.ctx)
 
     def set_tuning(self, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
-                   scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0):
+                   scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0,
+                   tally_binary32: int = 0):
         mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round, scratch_mib, long_ray_steps,
-                        long_ray_flight)
+                        long_ray_flight, tally_binary32)
 
     def tuning(self) -> dict:
         return mcrt_get_tuning(self.ctx)

@@ -171,3 +171,120 @@ def test_autotuner_picks_a_shape_without_changing_results():
     S.solve_into(params, q, s)
     assert np.array_equal(q.cpu().numpy(), before)
     S.close()
+
+
+# ---- every snapshot of a batch against the oracle, cell by cell -----------------
+
+def _oracle_batch_check(spec, params_kw, rays, offsets, streams=2, seed=9, snap0=30):
+    """Runs the batch of (grid, kd, T, x, counts or None) items and compares every
+    snapshot with the FP64 oracle on the same draws (snapshot word snap0 + k, the
+    run's ray offset): |Q - Q_oracle| <= 1e-4 S_i, the FP32 tolerance of the
+    single-solve parity tests.  Per-cell proposals are host-built integer counts
+    given to both sides.  Returns the launches of the last run."""
+    import torch
+
+    import oracle
+    solvers, outs, items = [], [], []
+    for k, (grid, kd, T, x, prop) in enumerate(spec):
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+        if prop is not None:
+            S.set_cell_proposal(*prop)
+        q = torch.full(grid.shape, float("nan"), dtype=torch.float64, device="cuda")
+        s = torch.full_like(q, float("nan"))
+        solvers.append(S)
+        outs.append((q, s))
+        items.append((S.ctx, q.data_ptr(), s.data_ptr(), snap0 + k))
+    params = mcrt.Solver.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32, **params_kw)
+    stream = torch.cuda.current_stream().cuda_stream
+    b = mcrt.mcrt_batch_create(items, params, streams=streams)
+    try:
+        for offset in offsets:
+            mcrt.mcrt_batch_run(b, offset, stream)
+            st = mcrt.mcrt_batch_get_stats(b)
+            assert st["rays"] == sum(sp[0].ncells for sp in spec) * rays
+            for k, ((grid, kd, T, x, prop), (q, s)) in enumerate(zip(spec, outs)):
+                kw = {}
+                if prop is not None:
+                    nc, nb, ng = grid.ncells, kd.n_bands, kd.n_g
+                    kw["proposal"] = (prop[0], prop[1].reshape(nc, nb * ng), prop[2])
+                orc = oracle.solve(grid, kd, T, x, rays=rays, seed=seed, snapshot=snap0 + k,
+                                   ray_offset=offset, tol=params.tol, max_steps=params.max_steps,
+                                   mg_levels=params_kw.get("mg_levels", 1),
+                                   mg_steps=params_kw.get("mg_steps", 5), **kw)
+                qn = q.cpu().numpy()
+                err = np.abs(qn - orc["q"]) / np.maximum(orc["scale"], 1e-300)
+                assert np.all(np.isfinite(qn)), (offset, k)
+                assert err.max() <= 1e-4, (offset, k, float(err.max()))
+                sn = s.cpu().numpy()
+                big = orc["sigma"] > 1e-3 * orc["scale"]
+                np.testing.assert_allclose(sn[big], orc["sigma"][big], rtol=2e-2)
+        launches = st["launches"]
+    finally:
+        mcrt.mcrt_batch_destroy(b)
+    for S in solvers:
+        S.close()
+    return launches
+
+
+def _uneven_snapshots(kd, shapes, seed0, stretched=(), reflect=()):
+    spec = []
+    for k, (nx, ny, nz) in enumerate(shapes):
+        grid = inputs.Grid(nx, ny, nz, 4.0, 2.0, 2.0, eps_wall=(0.8, 1.0), T_wall=(500.0, 1000.0),
+                           reflect=1 if k in reflect else 0)
+        if k in stretched:
+            grid.yf = inputs.channel_faces(ny, 2.0, 1.5)
+        T, x = inputs.channel_fields(grid, seed0 + k, x_mode="field")
+        spec.append((grid, kd, T, x, None))
+    return spec
+
+
+def test_single_launch_batch_against_oracle():
+    """Four snapshots of uneven sizes sharing the k-distribution (one persistent
+    trace launch): a ragged 7x9x5 grid, a stretched wall-normal grid, grey
+    specular walls and a larger channel; two runs at different ray offsets."""
+    kd = inputs.make_kdist(0)
+    spec = _uneven_snapshots(kd, [(7, 9, 5), (12, 16, 8), (16, 12, 10), (20, 24, 8)], 80,
+                             stretched=(1,), reflect=(2,))
+    assert _oracle_batch_check(spec, {}, 64, (0, 4096)) == 3
+
+
+def test_single_launch_batch_multigrid_against_oracle():
+    """The multigrid march (2 grids, 3 segments per grid) of a batch, including a
+    stretched snapshot, against the oracle's multigrid march."""
+    kd = inputs.make_kdist(0)
+    spec = _uneven_snapshots(kd, [(12, 16, 8), (24, 24, 12), (16, 24, 16)], 90, stretched=(0,),
+                             reflect=(1,))
+    assert _oracle_batch_check(spec, dict(mg_levels=2, mg_steps=3), 48, (0, 777)) == 2
+
+
+def test_single_launch_batch_cell_proposals_against_oracle():
+    """Per-cell integer proposals (host counts of 2^32, hemisphere splits across
+    (0, 1)) on every snapshot of a batch, against the oracle with the same counts."""
+    kd = inputs.make_kdist(0)
+    spec = _uneven_snapshots(kd, [(9, 10, 6), (12, 16, 8), (7, 9, 5)], 95, stretched=(1,))
+    rng = np.random.default_rng(12)
+    nb, ng = kd.n_bands, kd.n_g
+    spec_c = []
+    for grid, kd_, T, x, _ in spec:
+        nc = grid.ncells
+        def cum(rows, k):
+            c = rng.integers(1, 2**26, size=(rows, k)).astype(np.int64)
+            c[:, -1] += 2**32 - c.sum(axis=1)
+            return np.cumsum(c, axis=1).astype(np.uint64)
+        prop = (cum(nc, nb), cum(nc * nb, ng).reshape(nc, nb, ng),
+                rng.integers(1, 2**23, size=nc).astype(np.uint32))
+        spec_c.append((grid, kd_, T, x, prop))
+    assert _oracle_batch_check(spec_c, dict(proposal=mcrt.MCRT_PROPOSAL_CELL), 40, (0, 123)) == 3
+
+
+def test_mixed_kdist_graph_batch_against_oracle():
+    """Snapshots with different k-distributions run as per-snapshot launches in
+    concurrent graph branches; every snapshot against the oracle."""
+    spec = []
+    for k, (nx, ny, nz) in enumerate([(12, 16, 10), (7, 9, 5), (20, 24, 8)]):
+        kd = inputs.make_kdist(k)
+        grid = inputs.Grid(nx, ny, nz, 4.0, 2.0, 2.0, eps_wall=(0.8, 1.0), T_wall=(500.0, 1000.0))
+        T, x = inputs.channel_fields(grid, 100 + k, x_mode="field")
+        spec.append((grid, kd, T, x, None))
+    assert _oracle_batch_check(spec, {}, 56, (0, 999), streams=2) >= 6

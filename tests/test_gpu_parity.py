@@ -222,7 +222,7 @@ def test_fp32_results_independent_of_launch_shape():
         S.set_tuning(mb, k, mib)
         assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k,
                               "scratch_mib": mib if mib else 1024, "long_ray_steps": 1024,
-                              "long_ray_flight": 32}
+                              "long_ray_flight": 32, "tally_binary32": 0}
         q, s, st = S.solve(rays=300, seed=3, with_steps=True)
         assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
     with pytest.raises(mcrt.McrtError):
@@ -256,3 +256,53 @@ def test_dns_size_256x192x128_crop_against_oracle(stretched, levels):
     assert np.all(err <= 1e-4 * o["scale"]), np.max(err / o["scale"])
     big = o["sigma"] > 1e-3 * o["scale"]
     assert np.allclose(s[48:80, 80:112, 112:144][big], o["sigma"][big], rtol=2e-2)
+
+
+def test_binary64_tally_against_binary32_tally_and_oracle():
+    """The per-cell tallies (Eq. 8) of the FP32 path: binary64 by default (each run
+    of 32 samples summed exactly, the runs added with Neumaier's compensated
+    binary64 sum: within about 2^-51 of sum |Y| of the exact sum of the samples),
+    compensated binary32 pairs on request (within about 2e-7 of sum |Y|).  Same
+    draws, same samples: the two tallies differ by at most the binary32 bound,
+    sum |Y| / N <= S_i, and both stay within the FP32 tolerance of the oracle.
+    A ragged ray count (not a multiple of 32) exercises the last, partial run."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(16, 16, 16, seed=3)
+    rays = 203
+    orc = oracle.solve(grid, kd, T, x, rays=rays, seed=5)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    res = {}
+    for mode in (0, 1):
+        S.set_tuning(tally_binary32=mode)
+        assert S.tuning()["tally_binary32"] == mode
+        q, s = S.solve(rays=rays, seed=5, precision=mcrt.MCRT_FP32)
+        res[mode] = (q, s)
+    S.close()
+    scale = orc["scale"]
+    for mode in (0, 1):
+        err = np.abs(res[mode][0] - orc["q"]) / scale
+        assert err.max() <= 1e-4, (mode, err.max())
+    d = np.abs(res[0][0] - res[1][0]) / scale
+    assert d.max() <= 3e-7, d.max()
+    assert np.any(res[0][0] != res[1][0])  # the two tallies are different arithmetic
+
+
+def test_binary64_tally_sign_mix_and_launch_independence():
+    """Grey walls at both temperatures give cells whose samples take both signs
+    (Q_i a difference of large terms); the binary64 tally is reproduced bit for
+    bit under other launch shapes and agrees with the oracle."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(12, 16, 10, seed=4, eps_wall=0.8, x_mode="field")
+    orc = oracle.solve(grid, kd, T, x, rays=97, seed=6)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    outs = []
+    for shape in ((0, 0), (1, 1), (2, 2)):
+        S.set_tuning(*shape)
+        outs.append(S.solve(rays=97, seed=6, precision=mcrt.MCRT_FP32))
+    S.close()
+    for q, s in outs[1:]:
+        assert np.array_equal(q, outs[0][0]) and np.array_equal(s, outs[0][1])
+    err = np.abs(outs[0][0] - orc["q"]) / orc["scale"]
+    assert err.max() <= 1e-4

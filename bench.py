@@ -31,21 +31,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ray-cell steps/s"
 UNIT = "steps/s"
-MUFU_EX2_PER_CLK_PER_SM = 16  # MUFU.EX2 results per clock per SM
-N_SM = 152
 LANES_PER_SM = 128            # FP32/INT lanes per SM (one op per lane per clock)
 # Algorithmic FP32/INT operations of the estimator, counted from the source:
 OPS_PER_STEP = 44             # axis choice, table position, two interpolations,
                               # absorption, tally, DDA advance
 OPS_PER_RAY = 260             # 2 Philox4x32-10 blocks (2 x 80), sampling, direction,
                               # origin, DDA set-up, sample store
-GATHER_BYTES_PER_STEP = 8     # FP32 {T, x} of the traversed cell
-GATHERS_PER_STEP = 3          # 8-byte values a step gathers: {T, x}, the kappa node pair, the B node
-                              # pair (the kernel fetches the two node pairs in one 16-byte load)
+GATHER_BYTES_PER_STEP = 8     # algorithmic bytes of a step: the FP32 {T, x} entry of the traversed
+                              # cell (the kappa and B nodes are table reads, amortised)
+EXP_PER_STEP = 1              # one exponential per step (Eq. 2)
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel;
-# reported only for that workload
-TRACE_DRAM_BYTES_64_1000 = 26891008 + 1011976704
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the current
+# trace kernel; None until captured for the kernel as it stands
+TRACE_DRAM_BYTES_64_1000 = None
 
 
 def parse():
@@ -54,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=64, help="grid is n^3")
+    ap.add_argument("--grid", "--n", dest="n", type=int, default=64, help="grid is n^3")
     ap.add_argument("--rays", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
@@ -73,7 +71,7 @@ def workload_config(a):
             "rays_per_cell": a.rays, "bands": 40, "g_points": 8, "tol": 1e-4,
             "walls": "black, 500 K / 1000 K", "x_h2o": 0.1,
             "T_field": "linear 500->1000 K + 5% k^-5/3 Gaussian random field",
-            "precision": "fp32 traversal, fp64 compensated tallies",
+            "precision": "fp32 traversal and per-ray samples; per-cell tallies in binary64 (Neumaier-compensated sums of exact 32-sample runs)",
             "l2": "flushed between timed steps (256 MiB write)", "seed": 0,
             "long_ray_hand_off": {"steps": a.long_ray_steps or 1024, "flight": a.long_ray_flight or 32}}
 
@@ -138,15 +136,22 @@ def measured_peaks():
         return {}
 
 
-def ceilings(device, field_bytes):
+def sm_count(device):
+    import torch
+    return torch.cuda.get_device_properties(device).multi_processor_count
+
+
+def ceilings(device, field_bytes, full=True):
     """Measured rates of the two operations a march step repeats: the exponential
-    and a random 8-byte gather (library probes, one timed launch each)."""
+    and a random 8-byte gather (library probes, one timed launch each); the
+    gather from a buffer of the field's size, and (full) from 32 MiB and 4 GiB."""
     from paper_1810_00188_gb300 import mcrt
     ex2, mhz = mcrt.mcrt_probe_ex2(device)
-    sizes = {"field": 1 << max(12, int(field_bytes - 1).bit_length()), "32MiB": 32 << 20,
-             "4GiB": 4 << 30}
+    sizes = {"field": 1 << max(12, int(field_bytes - 1).bit_length())}
+    if full:
+        sizes.update({"32MiB": 32 << 20, "4GiB": 4 << 30})
     g = {k: mcrt.mcrt_probe_gather(device, v) for k, v in sizes.items()}
-    return {"ex2_per_s": ex2, "ex2_per_clk_per_sm": ex2 / (N_SM * mhz * 1e6), "probe_sm_mhz": mhz,
+    return {"ex2_per_s": ex2, "ex2_per_clk_per_sm": ex2 / (sm_count(device) * mhz * 1e6), "probe_sm_mhz": mhz,
             "gather8_per_s": g, "gather_buffer_bytes": sizes,
             "note": "random 8-byte loads, 8 in flight per thread, full occupancy; "
                     "ex2.approx chains, 8 per thread"}
@@ -387,23 +392,28 @@ def spectral_extra(S, T, params, q, s, sp, rays=256, reps=3):
 
 
 def learned_extra(sp, n_train=200, train_grid=64, eval_grid=128, rays_tally=512, rays_eval=256,
-                  steps=1500, seed=0):
+                  steps=1500, seed=0, eval_seeds=(1000, 1001, 1002)):
     """Learned proposal: tallies of `n_train` seeded 64^3 fields, training on the
-    GPU, then plain and learned FP32 solves of a held-out 128^3 field at the same
-    rays per cell; the GPU time to 1% p95 relative sigma is projected with the
-    estimator's 1/N law from the measured time and sigma.  Two forms, each
-    compared with plain sampling on the same march: the multigrid march (every
+    GPU, then plain and learned FP32 solves of held-out 128^3 fields (seeds
+    1000-1002) given the SAME measured GPU time: the plain arm runs 256 rays per
+    cell, the learned arm the ray count that fills the same kernel time (from a
+    pilot solve); both arms' achieved p95 relative sigma is measured.  Two forms,
+    each against plain sampling on the same march: the multigrid march (every
     grid, 5 segments per grid; tallies from multigrid solves, cost constant
     c0 = 12 steps) and the exact march (tallies from exact solves, c0 = 3)."""
     import torch
 
     from paper_1810_00188_gb300 import inputs, learn, mcrt
-    out = {"workload": f"train {n_train} x {train_grid}^3 fields (4096 cells each, {rays_tally} rays), "
-                       f"held-out {eval_grid}^3 field (seed 1000), {rays_eval} rays/cell"}
     n = eval_grid
-    grid, kd, T, x = inputs.nongrey_channel(n, n, n, seed=1000, x_mode="field")
-    S = mcrt.Solver(grid, kd)
-    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
+    out = {"workload": f"train {n_train} x {train_grid}^3 fields (4096 cells each, {rays_tally} rays), "
+                       f"held-out {n}^3 fields (seeds {', '.join(map(str, eval_seeds))}); plain arm "
+                       f"{rays_eval} rays/cell, learned arm the rays that fill the same GPU time",
+           "criterion": "p95 over cells of sigma_i / max(|Q_i|, 0.05 mean |Q|), measured at equal "
+                        "kernel time (no projection)"}
+    fields = []
+    for sd in eval_seeds:
+        grid, kd, T, x = inputs.nongrey_channel(n, n, n, seed=sd, x_mode="field")
+        fields.append((sd, grid, kd, T, x))
     for name, mg, c0 in (("multigrid", 1, 12.0), ("exact", 0, 3.0)):
         t0 = time.perf_counter()
         ds = learn.build_dataset(grid_shape=(train_grid,) * 3, seeds=range(n_train), rays=rays_tally,
@@ -419,24 +429,125 @@ def learned_extra(sp, n_train=200, train_grid=64, eval_grid=128, rays_tally=512,
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         l1 = learn.mean_loss(net, ds, c0=c0, stream=sp)
-        L = mcrt.mcrt_multigrid_levels(n, n, n) if mg else 1
-        res = learn.compare_on_field(S, net, rays=rays_eval, seed=seed + 7, reps=3, stream=sp,
-                                     mg_levels=L, mg_steps=5)
-        net.close()
         del ds
         torch.cuda.empty_cache()
-        res.update({"grids": L, "c0": c0, "dataset_s": t_data, "train_s": t_train, "train_steps": steps,
-                    "loss_before": l0, "loss_after": l1, "loss_last_batch": losses[-1][1]})
-        out[name] = res
-    S.close()
-    out["multigrid_learned_vs_exact_plain"] = (out["exact"]["plain"]["ms_to_1pct"] /
-                                                out["multigrid"]["learned"]["ms_to_1pct"])
+        L = mcrt.mcrt_multigrid_levels(n, n, n) if mg else 1
+        per_seed = {}
+        for sd, grid, kd, T, x in fields:
+            S = mcrt.Solver(grid, kd)
+            S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
+            per_seed[str(sd)] = learn.compare_equal_budget(S, net, rays=rays_eval, seed=seed + 7, stream=sp,
+                                                           mg_levels=L, mg_steps=5)
+            S.close()
+        net.close()
+        ratios = [v["p95_sigma_ratio_plain_over_learned"] for v in per_seed.values()]
+        out[name] = {"grids": L, "c0": c0, "dataset_s": t_data, "train_s": t_train, "train_steps": steps,
+                     "loss_before": l0, "loss_after": l1, "loss_last_batch": losses[-1][1],
+                     "fields": per_seed,
+                     "p95_sigma_ratio_plain_over_learned": {"min": min(ratios), "median": statistics.median(ratios),
+                                                            "max": max(ratios)}}
     return out
 
 
+def solves_at_1pct(sp):
+    """Q_rad solves per second at 1% cell sigma (the p95 over cells of
+    sigma_i / max(|Q_i|, 0.05 mean |Q|) at most 1%), MEASURED where one solve can
+    reach it: the grey slab 16x32x16 (kappa = 0.1, 1, 10; T = 1000 K, cold black
+    walls; FP32 and FP64): from a 128-ray solve the rays N* that the 1/N law asks
+    for are run, the achieved p95 is checked, and N* is raised until it holds.
+    For the non-grey 32^3 channel the p95 curve is measured up to 65,536 rays per
+    cell (2.1e9 rays in one solve); N* lies beyond one solve there and its
+    projection from the largest measured point is labelled as one."""
+    import numpy as np
+    import torch
+
+    from paper_1810_00188_gb300 import inputs, learn, mcrt
+    out = {"criterion": "p95 over cells of sigma_i / max(|Q_i|, 0.05 mean |Q|) <= 0.01"}
+
+    def solve(S, rays, prec, q, s, tol):
+        S.solve_into(S.params(rays=rays, seed=0, tol=tol, max_steps=1 << 20, precision=prec), q, s, stream=sp)
+        st = S.stats()
+        return st["kernel_ms"], learn.rel_sigma_p95(q.cpu().numpy(), s.cpu().numpy())
+
+    for kap in (0.1, 1.0, 10.0):
+        grid, kd, T, x = inputs.grey_slab_16x32x16(kap)
+        S = mcrt.Solver(grid, kd)
+        S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
+        q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+        s = torch.empty_like(q)
+        for prec, pname in ((mcrt.MCRT_FP32, "fp32"), (mcrt.MCRT_FP64, "fp64")):
+            _, p0 = solve(S, 128, prec, q, s, 1e-6)
+            n = int(math.ceil(128 * (p0 / 0.01) ** 2))
+            tries = []
+            for _ in range(4):
+                solve(S, n, prec, q, s, 1e-6)  # warm-up at this size
+                ms, pn = solve(S, n, prec, q, s, 1e-6)
+                tries.append({"rays": n, "kernel_ms": ms, "p95_rel_sigma": pn})
+                if pn <= 0.01:
+                    break
+                n = int(math.ceil(n * (pn / 0.01) ** 2 * 1.02))
+            last = tries[-1]
+            out[f"grey_slab_16x32x16_kappa{kap:g}_{pname}"] = {
+                "p95_rel_sigma_at_128_rays": p0, "rays_needed": last["rays"], "tries": tries,
+                "verified": last["p95_rel_sigma"] <= 0.01, "solve_ms": last["kernel_ms"],
+                "solves_per_s": 1e3 / last["kernel_ms"], "measured": True}
+        S.close()
+    # non-grey 32^3 channel: the curve
+    grid, kd, T, x = inputs.nongrey_channel(32, 32, 32, seed=0)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"), stream=sp)
+    q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+    s = torch.empty_like(q)
+    curve = []
+    for rays in (1000, 4000, 16000, 65536):
+        ms, pn = solve(S, rays, mcrt.MCRT_FP32, q, s, 1e-4)
+        curve.append({"rays": rays, "kernel_ms": ms, "p95_rel_sigma": pn,
+                      "rays_needed_by_1_over_N_from_here": int(math.ceil(rays * (pn / 0.01) ** 2))})
+    S.close()
+    big = curve[-1]
+    out["nongrey_channel_32cubed_fp32"] = {
+        "curve": curve, "measured": False,
+        "projected": {"from_rays": big["rays"], "rays_needed": big["rays_needed_by_1_over_N_from_here"],
+                      "solve_s": big["kernel_ms"] / 1e3 * big["rays_needed_by_1_over_N_from_here"] / big["rays"],
+                      "note": "projection with the 1/N law from the largest measured ray count; the measured "
+                              "curve falls more slowly than the law between 1,000 and 16,000 rays"}}
+    return out
+
+
+def parallelism(a, world):
+    if a.scaling == "strong" and world > 1:
+        return f"strong: one snapshot in {world} z-slabs, field broadcast once, Q/sigma gathered each step"
+    return f"weak: one snapshot per rank ({world}), no data-path collective"
+
+
+def launch_ranks(a):
+    """With --gpus N > 1 outside a launcher, start N ranks on this node (one per
+    GPU) with torch's launcher and return its exit status; under a launcher, the
+    world size must equal --gpus."""
+    world = int(os.environ.get("WORLD_SIZE", "0") or 0)
+    if world == 0 and a.gpus > 1:
+        import socket
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        env = dict(os.environ)
+        env.setdefault("NCCL_DEBUG", "INFO")
+        env.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
+        # "--n" would read as an abbreviation of the launcher's own options
+        args = ["--grid" if v == "--n" else v for v in sys.argv[1:]]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={a.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *args]
+        return subprocess.call(cmd, env=env)
+    if world and world != a.gpus:
+        raise SystemExit(f"bench.py: --gpus {a.gpus} but the launcher started {world} ranks")
+    return None
+
+
 def run_reference(a):
-    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores
+    (rank 0 only; other ranks exit without work)."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1") or 1)
     if rank != 0:
         return
     import oracle
@@ -460,9 +571,10 @@ def run_reference(a):
         tot_t += t
     v = tot_s / tot_t
     cfg = workload_config(a)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+    cfg["parallelism"] = parallelism(a, world)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": a.scaling, "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"one z-plane ({a.n}x{a.n} cells) x {a.rays} rays per step"},
@@ -472,6 +584,9 @@ def run_reference(a):
 
 def main():
     a = parse()
+    rc = launch_ranks(a)
+    if rc is not None:
+        sys.exit(rc)
     if a.impl == "reference":
         run_reference(a)
         return
@@ -482,17 +597,18 @@ def main():
     from paper_1810_00188_gb300 import dist as pdist
     from paper_1810_00188_gb300 import inputs, mcrt
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    world = int(os.environ.get("WORLD_SIZE", "1") or 1)
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     def barrier():
         if world > 1:
             dist.barrier()
-
 
     strong = a.scaling == "strong" and world > 1
     snap = 0 if a.scaling == "strong" else rank
@@ -530,7 +646,7 @@ def main():
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.steps)]
-    steps_total, kern_ms, launches = 0, [], 0
+    steps_total, kern_ms, trace_ms, long_ms, red_ms, launches = 0, [], [], [], [], 0
     for k in range(a.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -541,6 +657,9 @@ def main():
         st = S.stats()  # waits for this solve
         steps_total += st["steps"]
         kern_ms.append(st["kernel_ms"])
+        trace_ms.append(st["trace_ms"])
+        long_ms.append(st["long_ms"])
+        red_ms.append(st["reduce_ms"])
         launches += st["launches"]
     torch.cuda.synchronize()
     barrier()
@@ -552,47 +671,59 @@ def main():
     value = steps_all / t_max
     rays_all = float((1 if strong else world) * a.steps) * grid.ncells * a.rays
 
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    f_clk = sm_max * 1e6
-    ex2_peak = N_SM * MUFU_EX2_PER_CLK_PER_SM * f_clk  # exp/s = steps/s ceiling
-    alu_peak = N_SM * LANES_PER_SM * f_clk              # op/s
-    kernel_s = statistics.mean(kern_ms) / 1e3          # the solve's launches, library events
-    steps_per_launch = steps_total / a.steps
-    bs = S.box_shape(box)
-    rays_per_launch = bs[0] * bs[1] * bs[2] * a.rays
-    steps_rate = steps_per_launch / kernel_s
-    ops = OPS_PER_STEP * steps_per_launch + OPS_PER_RAY * rays_per_launch
-    achieved = ops / kernel_s
-    hbm = float(peaks.get("hbm_gbs", 6789.3))
-
     result = None
     if rank == 0:
+        peaks = measured_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        nsm = sm_count(local)
+        alu_peak = nsm * LANES_PER_SM * sm_max * 1e6        # op/s
+        hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9       # B/s
+        hbm_note = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback (6.8 TB/s)"
+        trace_s = statistics.mean(trace_ms) / 1e3             # the trace kernel alone, CUDA events
+        steps_per_launch = steps_total / a.steps
+        bs = S.box_shape(box)
+        rays_per_launch = bs[0] * bs[1] * bs[2] * a.rays
+        steps_rate = steps_per_launch / trace_s
+        gather = steps_rate * GATHER_BYTES_PER_STEP            # algorithmic B/s of the trace kernel
+        c = ceilings(local, grid.ncells * 8, full=not a.no_extras)
+        ex2 = c["ex2_per_s"]
+        l2g = c["gather8_per_s"]["field"] * GATHER_BYTES_PER_STEP  # useful B/s of random 8-B gathers
+        hbm_bound = hbm / GATHER_BYTES_PER_STEP
+        exp_bound = ex2 / EXP_PER_STEP
+        ops = OPS_PER_STEP * steps_per_launch + OPS_PER_RAY * rays_per_launch
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                   "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_max / a.steps,
                   "higher_is_better": True, "scaling": a.scaling, "vs_baseline": None,
                   "dtype": "f32", "data": "synthetic", "config": workload_config(a),
                   "rays_per_s": rays_all / t_max,
                   "steps_per_ray": steps_total / (a.steps * rays_per_launch),
-                  "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-                               "unit": "Top/s", "frac": achieved / alu_peak,
-                               "traffic": (TRACE_DRAM_BYTES_64_1000 if (a.n, a.rays) == (64, 1000)
-                                           else None),
-                               "traffic_note": "dram read+write bytes of one trace launch (ncu); "
-                                               "the 4 B/ray sample scratch, 1.049e9 B algorithmic",
-                               "peak_basis": f"FP32/INT issue: {N_SM} SM x {LANES_PER_SM} lanes x "
-                                             f"{sm_max:.0f} MHz, 1 op/lane/clk (derived)",
-                               "ops_per_step": OPS_PER_STEP, "ops_per_ray": OPS_PER_RAY,
-                               "kernel_ms": kernel_s * 1e3,
-                               "gather_GBs": steps_rate * GATHER_BYTES_PER_STEP / 1e9,
-                               "gather_frac_of_hbm": steps_rate * GATHER_BYTES_PER_STEP / 1e9 / hbm,
-                               "exp_frac_of_mufu": steps_rate / ex2_peak},
+                  "roofline": {
+                      "kernel": "trace_fp32_kernel",
+                      "bound": "hbm" if hbm_bound <= exp_bound else "mufu",
+                      "achieved": gather / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                      "frac": gather / hbm, "peak_basis": hbm_note,
+                      "traffic": (TRACE_DRAM_BYTES_64_1000 if (a.n, a.rays) == (64, 1000) else None),
+                      "traffic_note": "dram read+write bytes of one trace launch (ncu) of the kernel as it "
+                                      "stands, else null; the kernel writes 4 B per ray of samples",
+                      "definition": "steps/s <= min(bytes/s of the level holding the field / 8 B per step, "
+                                    "ex2/s / 1 exp per step); achieved = 8 B x steps per launch / the trace "
+                                    "kernel's mean CUDA-event time in the timed region",
+                      "trace_kernel_ms": trace_s * 1e3, "steps_per_s_trace_kernel": steps_rate,
+                      "l2_gather": {"peak": l2g / 1e9, "unit": "GB/s", "frac": gather / l2g,
+                                    "basis": "the library's random 8-byte gather probe on a buffer of the "
+                                             "field's size (the field is L2-resident), useful bytes"},
+                      "mufu": {"peak_ex2_per_s": ex2, "frac": steps_rate * EXP_PER_STEP / ex2,
+                               "basis": "the library's ex2.approx probe"},
+                      "alu": {"achieved": ops / trace_s / 1e12, "peak": alu_peak / 1e12, "unit": "Top/s",
+                              "frac": ops / trace_s / alu_peak, "ops_per_step": OPS_PER_STEP,
+                              "ops_per_ray": OPS_PER_RAY,
+                              "basis": f"{nsm} SM x {LANES_PER_SM} lanes x {sm_max:.0f} MHz, 1 op/lane/clk"}},
+                  "kernel_ms": {"solve": statistics.mean(kern_ms), "trace": statistics.mean(trace_ms),
+                                "long_rays": statistics.mean(long_ms), "reduce": statistics.mean(red_ms)},
                   "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
                               "max": max(step_ms)},
-                  "gpu_launches": launches, "clocks": clk}
-        result["config"]["parallelism"] = (
-            f"strong: one snapshot in {world} z-slabs, field broadcast once, Q/sigma gathered each step"
-            if strong else f"weak: one snapshot per rank ({world}), no data-path collective")
+                  "ceilings": c, "gpu_launches": launches, "clocks": clk}
+        result["config"]["parallelism"] = parallelism(a, world)
     # --- extras on rank 0: e2e through host buffers, FP64, solves/s at 1% sigma
     if rank == 0:
         Tp = torch.tensor(T).pin_memory()
@@ -612,25 +743,6 @@ def main():
                          "h2d_bytes_per_step": int(Tp.numel() * 8 + xp.numel() * 8),
                          "d2h_bytes_per_step": int(qh.numel() * 8 + sh.numel() * 8)}
         if not a.no_extras and not strong:
-            c = ceilings(local, grid.ncells * 8)
-            result["ceilings"] = c
-            rf = result["roofline"]
-            rf["exp_frac_of_measured_ex2"] = steps_rate / c["ex2_per_s"]
-            rf["gather_frac_of_measured_field_gather"] = (steps_rate * GATHERS_PER_STEP
-                                                          / c["gather8_per_s"]["field"])
-            # the traversal roofline: the slower of the step's gathers at the measured
-            # random-gather rate (the field's size: L1/L2 resident) and its exponential
-            # at the measured ex2 rate
-            g_bound = c["gather8_per_s"]["field"] / GATHERS_PER_STEP
-            e_bound = c["ex2_per_s"]
-            bound = min(g_bound, e_bound)
-            result["traversal_roofline"] = {
-                "definition": "steps/s bound = min(random 8-byte gathers/s (measured, field-sized "
-                              "buffer) / gathers per step, ex2/s (measured))",
-                "gathers_per_step": GATHERS_PER_STEP, "bound": "gather" if g_bound <= e_bound else "exp",
-                "gather_bound_steps_per_s": g_bound, "exp_bound_steps_per_s": e_bound,
-                "achieved_steps_per_s": steps_rate, "frac": steps_rate / bound,
-                "frac_field_gather_only": steps_rate / c["gather8_per_s"]["field"]}
             S.set_fields(Td, xd)
             # FP64 traversal throughput on a tenth of the rays
             r64 = max(32, a.rays // 10)
@@ -643,44 +755,25 @@ def main():
             S.solve_into(params(0, mcrt.MCRT_FP32, r64), q, s, stream=sp)
             q32 = q.cpu().numpy()
             result["error_vs_oracle"] = field_error(grid, kd, T, x, r64, snap, {"fp64": q64, "fp32": q32})
-            # Q_rad solves/s at 1% cell sigma: N* from the 1000-ray sigma, then verified
-            S.solve_into(params(0), q, s, stream=sp)
-            qn, sn = q.cpu().numpy(), s.cpu().numpy()
-            ref = np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
-            p95 = float(np.percentile(sn / ref, 95))
-            nstar = int(math.ceil(a.rays * (p95 / 0.01) ** 2))
-            sol = {"rays_needed": nstar, "p95_rel_sigma_at_base": p95}
-            if nstar <= 64 * a.rays:
-                S.solve_into(params(0, rays=nstar), q, s, stream=sp)
+            # Q_rad solves/s at 1% cell sigma on this workload: the p95 curve to 16x the
+            # base rays (the 1/N law's N* is out of reach of one solve here)
+            curve = []
+            for m in (1, 4, 16):
+                S.solve_into(params(0, rays=m * a.rays), q, s, stream=sp)
                 st = S.stats()
                 qn, sn = q.cpu().numpy(), s.cpu().numpy()
                 ref = np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
-                sol["verified_p95_rel_sigma"] = float(np.percentile(sn / ref, 95))
-                sol["solve_s"] = st["kernel_ms"] / 1e3
-                sol["value"] = 1e3 / st["kernel_ms"]
-            else:
-                # N* is out of reach of one solve here: project with the estimator's
-                # 1/sqrt(N) law from 4x and 16x the base rays as well.  The p95 of the
-                # estimated sigma falls more slowly than the law at first (rare large
-                # samples show up only with more rays), so the value is projected
-                # from the largest ray count measured.
-                checks = {}
-                for m in (4, 16):
-                    S.solve_into(params(0, rays=m * a.rays), q, s, stream=sp)
-                    qn, sn = q.cpu().numpy(), s.cpu().numpy()
-                    ref = np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
-                    pm = float(np.percentile(sn / ref, 95))
-                    checks[f"{m}x_rays"] = {"p95_rel_sigma": pm, "ratio_to_base": pm / p95,
-                                            "law": 1.0 / math.sqrt(m),
-                                            "rays_needed": int(math.ceil(m * a.rays * (pm / 0.01) ** 2))}
-                nstar = checks["16x_rays"]["rays_needed"]
-                sol["rays_needed"] = nstar
-                sol["rays_needed_from_base"] = int(math.ceil(a.rays * (p95 / 0.01) ** 2))
-                sol["value"] = value / (steps_per_launch / a.rays * nstar)
-                sol["projected"] = True
-                sol["projected_from"] = f"{16 * a.rays} rays per cell"
-                sol["projected_solve_s"] = 1.0 / sol["value"]
-                sol["law_check"] = checks
+                pm = float(np.percentile(sn / ref, 95))
+                curve.append({"rays": m * a.rays, "p95_rel_sigma": pm, "kernel_ms": st["kernel_ms"],
+                              "rays_needed_by_1_over_N_from_here": int(math.ceil(m * a.rays * (pm / 0.01) ** 2))})
+            big = curve[-1]
+            sol = {"this_workload": {
+                "curve": curve, "measured": False,
+                "projected": {"from_rays": big["rays"], "rays_needed": big["rays_needed_by_1_over_N_from_here"],
+                              "solves_per_s": 1e3 / (big["kernel_ms"] * big["rays_needed_by_1_over_N_from_here"]
+                                                     / big["rays"]),
+                              "note": "1/N-law projection from the largest measured ray count, labelled as one"}}}
+            sol.update(solves_at_1pct(sp))
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
             result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
             result["spectral_proposals"] = spectral_extra(S, T, params, q, s, sp)

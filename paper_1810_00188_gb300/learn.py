@@ -237,3 +237,48 @@ def compare_on_field(S, mlp, rays, seed=0, mix=0.1, reps=3, stream=0, mg_levels=
     out["speedup_to_1pct_incl_proposal"] = out["plain"]["ms_to_1pct"] / (
         out["learned"]["ms_to_1pct"] + out["proposal_ms"])
     return out
+
+
+def compare_equal_budget(S, mlp, rays, seed=0, mix=0.1, reps=2, stream=0, mg_levels=1, mg_steps=5):
+    """Plain and learned FP32 solves of the context's fields given the same
+    measured GPU time: the plain arm runs `rays` per cell; a pilot learned solve
+    at the same rays gives its time per ray, and the learned arm then runs the
+    ray count that fills the plain arm's kernel time.  Reports both arms' measured
+    kernel times, rays and achieved p95 relative sigma (medians over `reps`
+    solves at different ray offsets) and the sigma ratio at equal time; the time
+    to build the proposal is reported separately (it is paid once per field)."""
+    import torch
+    shape = S.box_shape(None)
+    dev = f"cuda:{S.device}"
+    q = torch.empty(shape, dtype=torch.float64, device=dev)
+    s = torch.empty_like(q)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    S.set_learned_proposal(mlp, mix=mix, stream=stream)
+    t1.record()
+    torch.cuda.synchronize()
+    out = {"proposal_ms": t0.elapsed_time(t1)}
+
+    def arm(prop, n, base):
+        times, p95, steps = [], [], 0
+        for r in range(reps):
+            p = S.params(rays=n, seed=seed, ray_offset=base + r * n, precision=mcrt.MCRT_FP32,
+                         proposal=prop, mg_levels=mg_levels, mg_steps=mg_steps)
+            S.solve_into(p, q, s, stream=stream)
+            st = S.stats()
+            times.append(st["kernel_ms"])
+            steps += st["steps"]
+            p95.append(rel_sigma_p95(q.cpu().numpy(), s.cpu().numpy()))
+        return {"rays": n, "kernel_ms": float(np.median(times)), "p95_rel_sigma": float(np.median(p95)),
+                "steps_per_ray": steps / (reps * n * S.grid.ncells)}
+
+    plain = arm(mcrt.MCRT_PROPOSAL_PLANCK_TMAX, rays, 0)
+    pilot = arm(mcrt.MCRT_PROPOSAL_CELL, rays, 0)
+    n_l = max(1, int(round(rays * plain["kernel_ms"] / pilot["kernel_ms"])))
+    learned = arm(mcrt.MCRT_PROPOSAL_CELL, n_l, 1 << 20)
+    out.update({"plain": plain, "learned": learned,
+                "time_ratio_learned_over_plain": learned["kernel_ms"] / plain["kernel_ms"],
+                "p95_sigma_ratio_plain_over_learned": plain["p95_rel_sigma"] / learned["p95_rel_sigma"]})
+    return out

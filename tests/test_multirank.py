@@ -140,3 +140,29 @@ def test_three_gloo_ranks_broadcast_solve_and_gather_uneven_slabs():
     full = oracle.solve(grid, kd, T, x, rays=16, seed=2, nthreads=1)
     # slabs of 1, 2 and 2 z-planes, padded in transit; the union is the full solve
     assert np.array_equal(qs, full["q"]) and np.array_equal(ss, full["sigma"])
+
+
+def test_bench_starts_one_rank_per_gpu_when_asked():
+    """`bench.py --gpus 2` outside a launcher starts two ranks itself (torch's
+    launcher, 127.0.0.1); on the reference arm rank 0 alone runs the oracle and
+    prints the one JSON line with n_gpus = 2, and the other rank exits 0.  A
+    launcher whose world size differs from --gpus is refused."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0", "--n", "6", "--rays", "4"],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert line["config"]["parallelism"].startswith("weak") and "(2)" in line["config"]["parallelism"]
+    bad = dict(env, WORLD_SIZE="3", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0", "--n", "6", "--rays", "4"],
+                       capture_output=True, text=True, env=bad, timeout=600)
+    assert r.returncode != 0 and "launcher started 3 ranks" in r.stderr

@@ -99,6 +99,8 @@ def lib():
             L.orc_mg_max_levels.argtypes = [C.c_int, C.c_int, C.c_int]
             L.orc_solve.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.POINTER(CellSums)]
             L.orc_exchange.argtypes = [C.POINTER(Problem), C.POINTER(Params), dp, dp, dp, dp]
+            L.orc_solve_armc.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.c_int, dp, dp,
+                                         C.POINTER(C.c_uint64)]
             L.orc_quadrature.argtypes = [C.POINTER(Problem), dp, dp, C.c_int, C.c_int, dp, dp,
                                          C.c_int, C.c_int, C.c_double, C.c_int,
                                          C.POINTER(C.c_int), C.c_int, C.c_int, dp]
@@ -315,6 +317,55 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
     else:
         res["sigma"] = np.zeros(shape)
         res["sigma_wall"] = np.zeros(shape)
+    return res
+
+
+def solve_armc(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4,
+               max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, batches=16):
+    """Absorption-based reciprocal estimate (the paper's ARMC, Section 2: Eq. FM with
+    the reciprocity relation): every cell of the grid emits `rays` rays; cell i's
+    exchange with the other medium cells comes from the rays of those cells
+    absorbed in i, its exchange with the walls from its own rays.  Returns arrays
+    shaped [bnz, bny, bnx] over the box: q, sigma (batch means over K = min(batches,
+    rays) batches of ray indices r mod K), scale (mean over rays of the absolute
+    deposits), and the per-batch estimates q_batches [K, ...].  ``proposal`` =
+    (cell_cn [nc, nb], cell_cg [nc, nb * ng], cell_hemi [nc]) over the WHOLE grid."""
+    P = make_problem(grid, kd, T, x)
+    S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, None, nthreads)
+    S.mg_levels, S.mg_steps = 1, 5
+    nc = grid.ncells
+    keep = []
+    if proposal is not None:
+        cn, cg, hemi = proposal
+        cn = np.ascontiguousarray(cn, dtype=np.uint64).reshape(nc, kd.n_bands)
+        cg = np.ascontiguousarray(cg, dtype=np.uint64).reshape(nc, kd.n_bands * kd.n_g)
+        hemi = np.ascontiguousarray(hemi, dtype=np.uint32).reshape(nc)
+        keep += [cn, cg, hemi]
+        S.cell_cn = cn.ctypes.data_as(C.POINTER(C.c_uint64))
+        S.cell_cg = cg.ctypes.data_as(C.POINTER(C.c_uint64))
+        S.cell_hemi = hemi.ctypes.data_as(C.POINTER(C.c_uint32))
+    K = max(1, min(int(batches), int(rays)))
+    acc = np.zeros((K, nc))
+    absacc = np.zeros(nc)
+    steps = np.zeros(nc, dtype=np.uint64)
+    rc = lib().orc_solve_armc(C.byref(P), C.byref(S), K, _dp(acc), _dp(absacc),
+                              steps.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc != 0:
+        raise ValueError(f"orc_solve_armc failed: {rc}")
+    b = box if box is not None else (0, grid.nx, 0, grid.ny, 0, grid.nz)
+    shape3 = (grid.nz, grid.ny, grid.nx)
+    crop = (slice(b[4], b[5]), slice(b[2], b[3]), slice(b[0], b[1]))
+    nk = np.array([len(range(k, rays, K)) for k in range(K)], dtype=np.float64)
+    qb = acc / nk[:, None]
+    res = {"q": (acc.sum(0) / rays).reshape(shape3)[crop],
+           "scale": (absacc / rays).reshape(shape3)[crop],
+           "steps": steps.reshape(shape3)[crop],
+           "q_batches": qb.reshape((K,) + shape3)[(slice(None),) + crop]}
+    if K > 1:
+        var = qb.var(axis=0, ddof=1) / K
+        res["sigma"] = np.sqrt(var).reshape(shape3)[crop]
+    else:
+        res["sigma"] = np.zeros(shape3)[crop]
     return res
 
 

@@ -301,6 +301,8 @@ typedef struct {
   int *touched;
   int ntouched;
   double wall[2];
+  long last;   /* the last medium cell the ray crossed (linear index) */
+  double res;  /* kappa_i tau at termination: the residual absorbed there */
 } xch_acc;
 
 static void trace_core(const orc_problem *P, const mg_grids *M, int n, int g, const int cell0[3],
@@ -320,6 +322,7 @@ static void trace_core(const orc_problem *P, const mg_grids *M, int n, int g, co
   const double B_i = B_at(P, n, P->T[ci]);
 
   double X = 0.0, absX = 0.0, Xw = 0.0, tau = 1.0, path = 0.0, B_last = B_i;
+  size_t j_last = ci;
   int64_t steps = 0;
   int capped = 0, walls = 0;
   uint32_t nrefl = 0;
@@ -415,6 +418,7 @@ restart:
     absX += fabs(term);
     tau *= exp(-kap_j * ds); /* Eq. 3: tau *= (1 - alpha) */
     B_last = B_j;
+    j_last = j;
     path += ds;
     ++steps;
     ++lsteps;
@@ -491,6 +495,10 @@ restart:
     const double tr = kap_i * (B_i - B_last) * tau;
     X += tr;
     absX += fabs(tr);
+  }
+  if (xa) {
+    xa->last = (long)j_last;
+    xa->res = tau > 0.0 ? kap_i * tau : 0.0;
   }
   o->X = X;
   o->abs_terms = absX;
@@ -866,4 +874,143 @@ int orc_quadrature(const orc_problem *P, const double *mu, const double *mu_w, i
   if (started == 0) quad_worker(&Q);
   for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
   return 0;
+}
+
+/* ---- absorption-based reciprocal estimate (ARMC) -----------------------------
+ * Eq. FM writes Q^R_i as the power cell i emits minus the power it absorbs;
+ * with the reciprocity relation (Q_(i->j),nu / I_b,nu(T_i) = Q_(j->i),nu /
+ * I_b,nu(T_j)) every exchange can be estimated from the rays of either cell.
+ * The emission-based estimate (orc_solve) takes cell i's exchanges from cell i's
+ * own rays.  This absorption-based one takes cell i's exchange with every other
+ * medium cell j from the rays EMITTED BY j that are absorbed in i: a ray of cell
+ * j with weight w deposits, for each cell i it crosses,
+ *     (V_j / V_i) w kappa_j (B_i - B_j) tau alpha_i
+ * (minus the term it adds to cell j's emission-based estimate, moved to the cell
+ * that absorbs), and its residual kappa_j (B_last - B_j) tau in the last cell it
+ * crossed (the cut-off convention of Algorithm 1, from the other side).  The
+ * exchange with the walls stays estimated from cell i's own rays (the walls emit
+ * no rays here).  Every cell of the grid emits; the sums are split into K batches
+ * by ray index (r mod K) for a batch-means standard error.
+ *   acc [K][nc]: sum over rays of the batch of the deposits into each cell;
+ *   absacc [nc]: sum of |deposits| (the parity scale);
+ *   steps [nc]: medium segments of each cell's own rays.
+ * Single grid only (no multigrid); threads take fixed ranges of emitting cells
+ * and their partial sums are added in thread order, so the result is
+ * deterministic. */
+
+typedef struct {
+  const orc_problem *P;
+  const orc_params *S;
+  const uint64_t *cn, *cg;
+  long c0, c1;
+  int K;
+  double *acc, *absacc;
+  uint64_t *steps;
+} armc_job;
+
+static double cell_volume(const orc_problem *P, long c) {
+  const int j = (int)((c / P->nx) % P->ny);
+  const double dy = P->yf ? P->yf[j + 1] - P->yf[j] : P->ly / P->ny;
+  return (P->lx / P->nx) * dy * (P->lz / P->nz);
+}
+
+static void *armc_worker(void *arg) {
+  armc_job *J = (armc_job *)arg;
+  const orc_problem *P = J->P;
+  const orc_params *S = J->S;
+  const size_t nc = (size_t)P->nx * P->ny * P->nz;
+  const int nb = P->n_bands, ng = P->n_g;
+  xch_acc xa;
+  xa.row = (double *)calloc(nc, sizeof(double));
+  xa.mark = (unsigned char *)calloc(nc, 1);
+  xa.touched = (int *)malloc(sizeof(int) * nc);
+  for (long c = J->c0; c < J->c1; ++c) {
+    const int cell0[3] = {(int)(c % P->nx), (int)((c / P->nx) % P->ny), (int)(c / ((long)P->nx * P->ny))};
+    const uint64_t *cn = S->cell_cn ? S->cell_cn + (size_t)c * nb : J->cn;
+    const uint64_t *cg = S->cell_cg ? S->cell_cg + (size_t)c * nb * ng : J->cg;
+    const uint32_t hemi = S->cell_hemi ? S->cell_hemi[c] : 4194304u;
+    const double Vc = cell_volume(P, c);
+    for (int r = 0; r < S->rays_per_cell; ++r) {
+      const uint32_t ray = (uint32_t)(S->ray_offset + (uint64_t)r);
+      ray_init R;
+      init_ray(P, S, cn, cg, hemi, (uint32_t)c, ray, &R);
+      orc_ray_out o;
+      xa.ntouched = 0;
+      xa.wall[0] = xa.wall[1] = 0.0;
+      trace_core(P, NULL, R.n, R.g, cell0, R.frac, R.dir, S->tol, S->max_steps, S->seed, (uint32_t)c,
+                 ray, S->snapshot, &o, &xa);
+      double *accb = J->acc + (size_t)(r % J->K) * nc;
+      const double B_e = B_at(P, R.n, P->T[c]);
+      for (int t = 0; t < xa.ntouched; ++t) {
+        const int jj = xa.touched[t];
+        const double d = R.w * (B_at(P, R.n, P->T[jj]) - B_e) * xa.row[jj] * (Vc / cell_volume(P, jj));
+        accb[jj] += d;
+        J->absacc[jj] += fabs(d);
+        xa.row[jj] = 0.0;
+        xa.mark[jj] = 0;
+      }
+      if (xa.res != 0.0) {
+        const double d = R.w * (B_at(P, R.n, P->T[xa.last]) - B_e) * xa.res * (Vc / cell_volume(P, xa.last));
+        accb[xa.last] += d;
+        J->absacc[xa.last] += fabs(d);
+      }
+      const double dw = R.w * o.X_wall; /* the cell's own exchange with the walls */
+      accb[c] += dw;
+      J->absacc[c] += fabs(dw);
+      J->steps[c] += (uint64_t)o.steps;
+    }
+  }
+  free(xa.row);
+  free(xa.mark);
+  free(xa.touched);
+  return NULL;
+}
+
+int orc_solve_armc(const orc_problem *P, const orc_params *S, int K, double *acc, double *absacc,
+                   uint64_t *steps) {
+  if (K < 1 || S->mg_levels > 1) return -3;
+  uint64_t *cn = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands);
+  uint64_t *cg = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands * P->n_g);
+  int rc = orc_plain_proposal(P, cn, cg, NULL);
+  const long nc = (long)P->nx * P->ny * P->nz;
+  int T = S->nthreads > 1 ? S->nthreads : 1;
+  if (T > 256) T = 256;
+  if (T > nc) T = (int)(nc > 0 ? nc : 1);
+  armc_job *jobs = (armc_job *)calloc((size_t)T, sizeof(armc_job));
+  if (rc == 0 && jobs) {
+    for (int t = 0; t < T; ++t) {
+      armc_job *J = &jobs[t];
+      J->P = P;
+      J->S = S;
+      J->cn = cn;
+      J->cg = cg;
+      J->K = K;
+      J->c0 = nc * t / T;
+      J->c1 = nc * (t + 1) / T;
+      J->acc = t ? (double *)calloc((size_t)K * nc, sizeof(double)) : acc;
+      J->absacc = t ? (double *)calloc((size_t)nc, sizeof(double)) : absacc;
+      J->steps = steps;
+    }
+    pthread_t th[256];
+    int started[256] = {0};
+    for (int t = 1; t < T; ++t) {
+      started[t] = pthread_create(&th[t], NULL, armc_worker, &jobs[t]) == 0;
+      if (!started[t]) armc_worker(&jobs[t]);
+    }
+    armc_worker(&jobs[0]);
+    for (int t = 1; t < T; ++t)
+      if (started[t]) pthread_join(th[t], NULL);
+    for (int t = 1; t < T; ++t) { /* thread order: deterministic sums */
+      for (size_t q = 0; q < (size_t)K * nc; ++q) acc[q] += jobs[t].acc[q];
+      for (long q = 0; q < nc; ++q) absacc[q] += jobs[t].absacc[q];
+      free(jobs[t].acc);
+      free(jobs[t].absacc);
+    }
+  } else if (rc == 0) {
+    rc = -4;
+  }
+  free(jobs);
+  free(cn);
+  free(cg);
+  return rc;
 }

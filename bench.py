@@ -480,7 +480,8 @@ def solves_at_1pct(sp):
             n = int(math.ceil(128 * (p0 / 0.01) ** 2))
             tries = []
             for _ in range(4):
-                solve(S, n, prec, q, s, 1e-6)  # warm-up at this size
+                if prec == mcrt.MCRT_FP32:
+                    solve(S, n, prec, q, s, 1e-6)  # warm-up at this size (scratch allocation)
                 ms, pn = solve(S, n, prec, q, s, 1e-6)
                 tries.append({"rays": n, "kernel_ms": ms, "p95_rel_sigma": pn})
                 if pn <= 0.01:

@@ -184,6 +184,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       }
       if (!exhausted) {
         const int rr = c_r + lane;
+        bool keep = false, inst = false;  // through the ring and the march / ended in its cell
+        float4 sA, sB;
+        unsigned sCx = 0u, sCz = 0u;
         if (rr < N) {
           const unsigned cell = (unsigned)c_lin;
           const unsigned rayid = (unsigned)(ray_off + (unsigned long long)rr);
@@ -246,15 +249,47 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           axis_setup(mu, fy, yfs ? dyl(a.bj0 + c_by, 0) : DY, ssy, a0y, asy);
           axis_setup(st * sphi, fz, DZ, ssz, a0z, asz);
           if (yfs && ssy != 0) asy = __frcp_rn(fabsf(mu));
-          const int pos = (tail + lane) & (POOL - 1);
-          R.A[pos] = make_float4(a0x, a0y, a0z, asx);
-          R.B[pos] = make_float4(asy, asz, kbi.z + fr_i * kbi.w, wgt * kap_i);
-          const unsigned flags = (unsigned)(ssx + 1) | ((unsigned)(ssy + 1) << 2) |
-                                 ((unsigned)(ssz + 1) << 4);
-          R.C[pos] = make_uint4((unsigned)nn | ((unsigned)gg << 16), rayid, flags, cell);
+          // A ray whose first segment, inside its own cell, leaves tau <= tol ends
+          // there with X = 0 exactly: that segment's B_j is B_i and the residual
+          // dump uses B_last = B_i.  Its sample (0) and its one step are recorded
+          // below from the same expressions the march evaluates (same bits), and
+          // the ray skips the ring and the march (about 40% of the rays of the
+          // 64^3 channel: optically thick bands).
+          float al0, tr0;
+          absorb(kap_i * fminf(fminf(a0x, a0y), a0z), al0, tr0);
+          inst = tr0 <= tol;
+          keep = !inst;
+          sA = make_float4(a0x, a0y, a0z, asx);
+          sB = make_float4(asy, asz, kbi.z + fr_i * kbi.w, wgt * kap_i);
+          sCx = (unsigned)nn | ((unsigned)gg << 16);
+          sCz = (unsigned)(ssx + 1) | ((unsigned)(ssy + 1) << 2) | ((unsigned)(ssz + 1) << 4);
+        }
+        // the rays that go on are packed into the ring in lane order (the ray
+        // index and the cell are rebuilt here rather than held across the ballot)
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int pos = (tail + __popc(km & lt_mask)) & (POOL - 1);
+          R.A[pos] = sA;
+          R.B[pos] = sB;
+          R.C[pos] = make_uint4(sCx, (unsigned)(ray_off + (unsigned long long)rr), sCz, (unsigned)c_lin);
           R.D[pos] = make_int4(c_slot, a.bi0 + c_bx, a.bj0 + c_by, a.bk0 + c_bz);
         }
-        tail += (unsigned)min(32, N - c_r);
+        tail += (unsigned)__popc(km);
+        if (inst) {
+          Ybuf[(size_t)c_slot * (unsigned)N + (unsigned)rr] = 0.f;
+          if (a.ray_steps) a.ray_steps[(size_t)c_slot * (unsigned)N + (unsigned)rr] = 1u;
+          if (a.steps_cell) {
+            if (c_slot != acc_slot) {
+              if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
+              acc_slot = c_slot;
+              acc_steps = 0;
+            }
+            acc_steps += 1u;
+          }
+          tot_steps += 1ull;
+          max_ray = max(max_ray, 1u);
+          ++tot_rays;
+        }
         c_r += 32;
       }
       __syncwarp();

@@ -275,8 +275,12 @@ def compare_equal_budget(S, mlp, rays, seed=0, mix=0.1, reps=2, stream=0, mg_lev
                 "steps_per_ray": steps / (reps * n * S.grid.ncells)}
 
     plain = arm(mcrt.MCRT_PROPOSAL_PLANCK_TMAX, rays, 0)
-    pilot = arm(mcrt.MCRT_PROPOSAL_CELL, rays, 0)
-    n_l = max(1, int(round(rays * plain["kernel_ms"] / pilot["kernel_ms"])))
+    # the learned arm's rays: two pilots (the time per ray falls a little with the
+    # ray count, so one pilot at the plain arm's rays overshoots)
+    n_l = rays
+    for _ in range(2):
+        pilot = arm(mcrt.MCRT_PROPOSAL_CELL, n_l, 0)
+        n_l = max(1, int(round(n_l * plain["kernel_ms"] / pilot["kernel_ms"])))
     learned = arm(mcrt.MCRT_PROPOSAL_CELL, n_l, 1 << 20)
     out.update({"plain": plain, "learned": learned,
                 "time_ratio_learned_over_plain": learned["kernel_ms"] / plain["kernel_ms"],

@@ -99,7 +99,7 @@ def lib():
             L.orc_mg_max_levels.argtypes = [C.c_int, C.c_int, C.c_int]
             L.orc_solve.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.POINTER(CellSums)]
             L.orc_exchange.argtypes = [C.POINTER(Problem), C.POINTER(Params), dp, dp, dp, dp]
-            L.orc_solve_armc.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.c_int, dp, dp,
+            L.orc_solve_armc.argtypes = [C.POINTER(Problem), C.POINTER(Params), C.c_int, dp, dp, dp,
                                          C.POINTER(C.c_uint64)]
             L.orc_quadrature.argtypes = [C.POINTER(Problem), dp, dp, C.c_int, C.c_int, dp, dp,
                                          C.c_int, C.c_int, C.c_double, C.c_int,
@@ -321,7 +321,8 @@ def solve(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1
 
 
 def solve_armc(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4,
-               max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, batches=16):
+               max_steps=1 << 30, origin=0, box=None, nthreads=None, proposal=None, batches=16,
+               hybrid=False):
     """Absorption-based reciprocal estimate (the paper's ARMC, Section 2: Eq. FM with
     the reciprocity relation): every cell of the grid emits `rays` rays; cell i's
     exchange with the other medium cells comes from the rays of those cells
@@ -329,7 +330,13 @@ def solve_armc(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, 
     shaped [bnz, bny, bnx] over the box: q, sigma (batch means over K = min(batches,
     rays) batches of ray indices r mod K), scale (mean over rays of the absolute
     deposits), and the per-batch estimates q_batches [K, ...].  ``proposal`` =
-    (cell_cn [nc, nb], cell_cg [nc, nb * ng], cell_hemi [nc]) over the WHOLE grid."""
+    (cell_cn [nc, nb], cell_cg [nc, nb * ng], cell_hemi [nc]) over the WHOLE grid.
+    With ``hybrid`` the result also holds the combination of the two estimates
+    cell by cell, lam_i Q_E,i + (1 - lam_i) Q_A,i with lam_i = (T_i - T_min) /
+    (T_max - T_min) over the medium (the emission-based estimate where the gas
+    is hot, the absorption-based one where it is cold): "q_hybrid",
+    "sigma_hybrid" (batch means of the combined batch estimates), and the
+    emission-based "q_ermc" of the same draws."""
     P = make_problem(grid, kd, T, x)
     S = _params(rays, seed, snapshot, ray_offset, tol, max_steps, origin, None, nthreads)
     S.mg_levels, S.mg_steps = 1, 5
@@ -347,8 +354,10 @@ def solve_armc(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, 
     K = max(1, min(int(batches), int(rays)))
     acc = np.zeros((K, nc))
     absacc = np.zeros(nc)
+    accE = np.zeros((K, nc)) if hybrid else None
     steps = np.zeros(nc, dtype=np.uint64)
     rc = lib().orc_solve_armc(C.byref(P), C.byref(S), K, _dp(acc), _dp(absacc),
+                              _dp(accE) if hybrid else C.POINTER(C.c_double)(),
                               steps.ctypes.data_as(C.POINTER(C.c_uint64)))
     if rc != 0:
         raise ValueError(f"orc_solve_armc failed: {rc}")
@@ -366,6 +375,14 @@ def solve_armc(grid, kd, T, x=None, rays=128, seed=0, snapshot=0, ray_offset=0, 
         res["sigma"] = np.sqrt(var).reshape(shape3)[crop]
     else:
         res["sigma"] = np.zeros(shape3)[crop]
+    if hybrid:
+        Tf = np.asarray(T, dtype=np.float64).reshape(-1)
+        lam = np.clip((Tf - Tf.min()) / max(Tf.max() - Tf.min(), 1e-300), 0.0, 1.0)
+        qe = accE / nk[:, None]
+        qh = lam[None, :] * qe + (1.0 - lam[None, :]) * qb
+        res["q_ermc"] = (accE.sum(0) / rays).reshape(shape3)[crop]
+        res["q_hybrid"] = (lam * accE.sum(0) / rays + (1.0 - lam) * acc.sum(0) / rays).reshape(shape3)[crop]
+        res["sigma_hybrid"] = (np.sqrt(qh.var(axis=0, ddof=1) / K) if K > 1 else np.zeros(nc)).reshape(shape3)[crop]
     return res
 
 

@@ -893,6 +893,8 @@ int orc_quadrature(const orc_problem *P, const double *mu, const double *mu_w, i
  * by ray index (r mod K) for a batch-means standard error.
  *   acc [K][nc]: sum over rays of the batch of the deposits into each cell;
  *   absacc [nc]: sum of |deposits| (the parity scale);
+ *   accE [K][nc] (nullable): the emission-based sums of each cell's own samples
+ *   per batch (for the combination of the two estimates);
  *   steps [nc]: medium segments of each cell's own rays.
  * Single grid only (no multigrid); threads take fixed ranges of emitting cells
  * and their partial sums are added in thread order, so the result is
@@ -904,7 +906,7 @@ typedef struct {
   const uint64_t *cn, *cg;
   long c0, c1;
   int K;
-  double *acc, *absacc;
+  double *acc, *absacc, *accE;
   uint64_t *steps;
 } armc_job;
 
@@ -957,6 +959,7 @@ static void *armc_worker(void *arg) {
       const double dw = R.w * o.X_wall; /* the cell's own exchange with the walls */
       accb[c] += dw;
       J->absacc[c] += fabs(dw);
+      if (J->accE) J->accE[(size_t)(r % J->K) * nc + c] += R.w * o.X;
       J->steps[c] += (uint64_t)o.steps;
     }
   }
@@ -967,7 +970,7 @@ static void *armc_worker(void *arg) {
 }
 
 int orc_solve_armc(const orc_problem *P, const orc_params *S, int K, double *acc, double *absacc,
-                   uint64_t *steps) {
+                   double *accE, uint64_t *steps) {
   if (K < 1 || S->mg_levels > 1) return -3;
   uint64_t *cn = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands);
   uint64_t *cg = (uint64_t *)malloc(sizeof(uint64_t) * P->n_bands * P->n_g);
@@ -989,6 +992,7 @@ int orc_solve_armc(const orc_problem *P, const orc_params *S, int K, double *acc
       J->c1 = nc * (t + 1) / T;
       J->acc = t ? (double *)calloc((size_t)K * nc, sizeof(double)) : acc;
       J->absacc = t ? (double *)calloc((size_t)nc, sizeof(double)) : absacc;
+      J->accE = accE; /* each emitting cell belongs to one thread: no race */
       J->steps = steps;
     }
     pthread_t th[256];

@@ -123,10 +123,12 @@ int orc_trace_ray_mg(const orc_problem *P, const orc_ray_in *in, int mg_levels, 
 int orc_solve(const orc_problem *P, const orc_params *S, orc_cell_sums *out);
 /* Absorption-based reciprocal estimate over the whole grid (every cell emits):
  * per batch k = r mod K and cell, the deposits of the rays of batch k into the
- * cell (acc [K][nc], zeroed by the caller), their absolute sum (absacc [nc]) and
- * each cell's own medium segments (steps [nc]).  Single grid only. */
+ * cell (acc [K][nc], zeroed by the caller), their absolute sum (absacc [nc]),
+ * optionally the emission-based sums of each cell's own samples per batch
+ * (accE [K][nc] or NULL) and each cell's own medium segments (steps [nc]).
+ * Single grid only. */
 int orc_solve_armc(const orc_problem *P, const orc_params *S, int K, double *acc, double *absacc,
-                   uint64_t *steps);
+                   double *accE, uint64_t *steps);
 int orc_exchange(const orc_problem *P, const orc_params *S, double *G, double *G2,
                  double *Gw, double *Gw2);
 /* ---- learned proposal (no counterpart in the paper; replaces the pdf of

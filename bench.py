@@ -391,6 +391,49 @@ def spectral_extra(S, T, params, q, s, sp, rays=256, reps=3):
     return out
 
 
+def estimators_extra(S, T, params, q, s, sp, rays=256, reps=3):
+    """The reciprocal estimators of Section 2 on the benchmark field, all at the
+    same rays per cell: the emission-based estimate with Zhang's T_max pdf (the
+    paper's), with each cell's own emission spectrum (classic ERMC), the
+    absorption-based estimate (ARMC, T_max pdf), and their temperature-weighted
+    combination.  For each: kernel time, and over cells the p95 relative sigma and
+    the median relative sigma of the coldest and hottest tenths."""
+    import numpy as np
+
+    from paper_1810_00188_gb300 import mcrt
+    Tf = np.asarray(T).reshape(-1)
+    cold = Tf <= np.percentile(Tf, 10)
+    hot = Tf >= np.percentile(Tf, 90)
+    out = {"rays_per_cell": rays,
+           "criterion": "relative sigma_i / max(|Q_i|, 0.05 mean |Q|); ARMC and hybrid sigma from batch means"}
+    arms = (("ermc_T_max", mcrt.MCRT_EST_ERMC, None), ("ermc_local", mcrt.MCRT_EST_ERMC, mcrt.MCRT_SPECTRAL_LOCAL),
+            ("armc_T_max", mcrt.MCRT_EST_ARMC, None), ("hybrid_T_max", mcrt.MCRT_EST_HYBRID, None))
+    for name, est, spec in arms:
+        prop = mcrt.MCRT_PROPOSAL_PLANCK_TMAX
+        if spec is not None:
+            S.set_spectral_proposal(spec, stream=sp)
+            prop = mcrt.MCRT_PROPOSAL_CELL
+        ts, p95, rc, rh = [], [], [], []
+        for k in range(reps):
+            pk = params(k, rays=rays)
+            pk.proposal = prop
+            pk.estimator = est
+            S.solve_into(pk, q, s, stream=sp)
+            ts.append(S.stats()["kernel_ms"])
+            qn, sn = q.cpu().numpy().reshape(-1), s.cpu().numpy().reshape(-1)
+            rel = sn / np.maximum(np.abs(qn), 0.05 * np.mean(np.abs(qn)))
+            p95.append(float(np.percentile(rel, 95)))
+            rc.append(float(np.median(rel[cold])))
+            rh.append(float(np.median(rel[hot])))
+        out[name] = {"kernel_ms": statistics.median(ts), "p95_rel_sigma": statistics.median(p95),
+                     "cold_tenth_median_rel_sigma": statistics.median(rc),
+                     "hot_tenth_median_rel_sigma": statistics.median(rh)}
+    base = out["ermc_T_max"]["cold_tenth_median_rel_sigma"]
+    for name, _, _ in arms:
+        out[name]["cold_sigma_vs_ermc_T_max"] = out[name]["cold_tenth_median_rel_sigma"] / base
+    return out
+
+
 def learned_extra(sp, n_train=200, train_grid=64, eval_grid=128, rays_tally=512, rays_eval=256,
                   steps=1500, seed=0, eval_seeds=(1000, 1001, 1002)):
     """Learned proposal: tallies of `n_train` seeded 64^3 fields, training on the
@@ -778,6 +821,7 @@ def main():
             result["qrad_solves_per_s_at_1pct_sigma"] = sol
             result["multigrid"] = multigrid_extra(S, params, q, s, sp, a.rays)
             result["spectral_proposals"] = spectral_extra(S, T, params, q, s, sp)
+            result["estimators"] = estimators_extra(S, T, params, q, s, sp)
             if world == 1:
                 result["configs"] = configs_extra(sp)
                 # before the learned-proposal leg, whose datasets stay in torch's cache

@@ -63,6 +63,16 @@ enum { MCRT_ORIGIN_UNIFORM = 0, MCRT_ORIGIN_CENTER = 1 };
  * discretised as Eq. 16) with isotropic directions, or per-cell pdfs supplied by
  * mcrt_set_cell_proposal. */
 enum { MCRT_PROPOSAL_PLANCK_TMAX = 0, MCRT_PROPOSAL_CELL = 1 };
+/* Reciprocal estimator (Section 2, Eq. FM with the reciprocity relation).
+ * ERMC: cell i's exchanges from cell i's own rays (Eq. 14 per ray).
+ * ARMC: cell i's exchange with every other medium cell from the rays emitted by
+ *   that cell and absorbed in i (each ray deposits minus its emission-based
+ *   segment term into the absorbing cell, its residual into the last cell it
+ *   crossed); its exchange with the walls from its own rays.  The paper notes it
+ *   has the lower variance where the gas is cold and absorbs.
+ * HYBRID: per cell lam Q_ERMC + (1 - lam) Q_ARMC from the same rays, lam =
+ *   (T_i - T_min) / (T_max - T_min) over the medium. */
+enum { MCRT_EST_ERMC = 0, MCRT_EST_ARMC = 1, MCRT_EST_HYBRID = 2 };
 enum { MCRT_REFLECT_DIFFUSE = 0, MCRT_REFLECT_SPECULAR = 1 };
 
 /* Grid and walls (Section 2.2: finite volumes with index (i,j,k); Eq. 3: the
@@ -136,6 +146,14 @@ typedef struct {
   int mg_levels;           /* grids used, 0 or 1: the grid itself (exact march)   */
   int mg_steps;            /* segments per grid but the coarsest, >= 1 when
                               mg_levels > 1 (the paper uses 5)                   */
+  /* MCRT_EST_*.  ARMC and HYBRID: MCRT_FP32, the whole grid (every cell emits;
+   * no box), a uniform channel grid (no wall-normal faces, no x/z walls), one
+   * grid and no long-ray hand-off; anything else is refused with
+   * MCRT_E_UNSUPPORTED.  sigma_out is the batch-means standard error over K =
+   * min(16, rays_per_cell) batches of ray indices (r mod 16).  The deposits are
+   * binary64 atomic adds, so these results are reproducible to rounding, not bit
+   * for bit; p->steps_out and mcrt_get_stats count the cells' own rays. */
+  int estimator;
 } mcrt_solve_params;
 
 typedef struct {

@@ -50,6 +50,8 @@ struct mcrt_ctx {
   DevBuf yf64, yf32;
   // long rays handed off by the FP32 exact march (LongRay entries)
   DevBuf longbuf;
+  // absorption-based estimate: per-batch sums [2][16][cells]
+  DevBuf armcbuf;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-kernel marks of the last FP32 solve: four events per chunk (launch_trace_fp32)
   std::vector<cudaEvent_t> kev;

@@ -376,6 +376,7 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
   if (!p) return fail(ctx, MCRT_E_ARG, "null params");
   if (n < 0 || (n > 0 && (!cells || !mom_out || !cost_out))) return fail(ctx, MCRT_E_ARG, "bad arguments");
   if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_ARG, "tallies come from the FP32 solve");
+  if (p->estimator != MCRT_EST_ERMC) return fail(ctx, MCRT_E_ARG, "tallies come from the emission-based solve");
   if (p->use_box) return fail(ctx, MCRT_E_ARG, "tallies need the whole grid (use_box = 0)");
   int b[6];
   const int rc0 = check_solve_params(ctx, p, b);

@@ -231,6 +231,16 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
   if (p->mg_levels < 0 || p->mg_levels > mcrt::multigrid_levels(g.nx, g.ny, g.nz))
     return fail(ctx, MCRT_E_ARG, "mg_levels outside [0, mcrt_multigrid_levels(grid)]");
   if (p->mg_levels > 1 && p->mg_steps < 1) return fail(ctx, MCRT_E_ARG, "mg_steps < 1");
+  if (p->estimator != MCRT_EST_ERMC && p->estimator != MCRT_EST_ARMC && p->estimator != MCRT_EST_HYBRID)
+    return fail(ctx, MCRT_E_ARG, "bad estimator");
+  if (p->estimator != MCRT_EST_ERMC) {
+    if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: FP32 only");
+    if (b[0] != 0 || b[1] != g.nx || b[2] != 0 || b[3] != g.ny || b[4] != 0 || b[5] != g.nz)
+      return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: the whole grid only (every cell emits)");
+    if (!ctx->yf.empty() || g.xz_walls)
+      return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: uniform channel grids only");
+    if (p->mg_levels > 1) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: one grid only");
+  }
   return MCRT_OK;
 }
 
@@ -679,6 +689,20 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     a.step_acc = (unsigned long long *)ctx->step_acc.p;
     const int rl = setup_long_rays(ctx, Pc * (long long)p->rays_per_cell, &a);
     if (rl != MCRT_OK) return rl;
+    const bool armc = p->estimator != MCRT_EST_ERMC;
+    const long long ncg = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+    if (armc) {
+      // per-batch sums of the deposits and of the cells' own samples; the rays
+      // march to their end in their own lane (no hand-off)
+      CK(ensure(ctx->armcbuf, (size_t)2 * 16 * ncg * sizeof(double)), "alloc ARMC sums");
+      CK(cudaMemsetAsync(ctx->armcbuf.p, 0, (size_t)2 * 16 * ncg * sizeof(double), s), "clear ARMC sums");
+      a.armc_acc = (double *)ctx->armcbuf.p;
+      a.ermc_acc = a.armc_acc + 16 * ncg;
+      a.armc_nc = ncg;
+      a.long_rays = nullptr;
+      a.long_cap = 0;
+      a.long_steps = 0x7fffffff;
+    }
     const int nchunks = (int)((P + Pc - 1) / Pc);
     while ((int)ctx->kev.size() < 4 * nchunks) {
       cudaEvent_t e = nullptr;
@@ -698,6 +722,14 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
          "trace launch");
       ++ctx->kev_chunks;
       launches += mcrt::long_rays_on(a) ? 3 : 2;
+    }
+    if (armc) {
+      CK(mcrt::launch_armc_finalize(a.armc_acc, a.ermc_acc, ncg, p->rays_per_cell < 16 ? p->rays_per_cell : 16,
+                                    p->rays_per_cell, p->estimator == MCRT_EST_HYBRID,
+                                    (const double2 *)ctx->field64.p, ctx->T_min_field, ctx->T_max_field, dq, ds,
+                                    s),
+         "ARMC finalize");
+      ++launches;
     }
     CK(cudaEventRecord(ctx->ev1, s), "event");
   } else {
@@ -802,7 +834,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -880,6 +912,8 @@ extern "C" int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p
   if (!ctx) return MCRT_E_ARG;
   if (!p || !q_out) return fail(ctx, MCRT_E_ARG, "null params or q_out");
   if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_ARG, "the allocation-free solve is FP32 only");
+  if (p->estimator != MCRT_EST_ERMC)
+    return fail(ctx, MCRT_E_UNSUPPORTED, "the allocation-free solve is emission-based only");
   int b[6];
   const int rc0 = check_solve_params(ctx, p, b);
   if (rc0 != MCRT_OK) return rc0;
@@ -999,7 +1033,8 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   if (streams > n) streams = n;
   if (p->precision != MCRT_FP32 || p->rays_per_cell < 1 || p->max_steps < 1 ||
       !(p->tol > 0.0 && p->tol < 1.0) || (p->origin != MCRT_ORIGIN_UNIFORM && p->origin != MCRT_ORIGIN_CENTER) ||
-      (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL))
+      (p->proposal != MCRT_PROPOSAL_PLANCK_TMAX && p->proposal != MCRT_PROPOSAL_CELL) ||
+      p->estimator != MCRT_EST_ERMC)
     return MCRT_E_ARG;
   const int dev = items[0].ctx ? items[0].ctx->grid.device : -1;
   for (int k = 0; k < n; ++k) {

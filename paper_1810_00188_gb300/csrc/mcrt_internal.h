@@ -131,6 +131,10 @@ struct TraceArgs {
   unsigned long long *steps_cell;
   // FP32 kernels: per-cell tallies in binary32 pairs (1) instead of binary64 (0)
   int tally32;
+  // absorption-based estimate (null: off): per-batch binary64 sums [16][armc_nc]
+  // of the deposits into each cell and of each cell's own samples
+  double *armc_acc, *ermc_acc;
+  long long armc_nc;
   unsigned long long *counters;  // [0] steps [1] capped [2] wall hits [3] rays [4] longest ray (steps)
                                  // [5] error flags [6] FP32 kernel: claimed positions
                                  // [7] long rays handed off by this launch
@@ -163,6 +167,12 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // after the reduction.
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s, cudaEvent_t *marks = nullptr);
+// Q and sigma of the absorption-based estimate (hybrid = 0) or of its
+// temperature-weighted combination with the emission-based one (hybrid = 1) from
+// the per-batch sums of the AR trace launches; K batches of N rays per cell.
+cudaError_t launch_armc_finalize(const double *acc, const double *eacc, long long nc, int K, int N,
+                                 int hybrid, const double2 *field, double T_min, double T_max, double *q,
+                                 double *sigma, cudaStream_t s);
 long long fp32_bricks_positions(int bnx, int bny, int bnz);
 // The warp-parallel march of the long rays the last FP32 trace launch handed off
 // (a.long_rays[0 .. min(counters[7], long_cap))); writes their samples and adds

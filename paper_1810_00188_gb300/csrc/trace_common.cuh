@@ -234,6 +234,27 @@ __device__ __forceinline__ void warp_cell_sums(const float *__restrict__ y, int 
   }
 }
 
+// ---- absorption-based estimate (ARMC) -----------------------------------------
+
+// Index of `cell`'s per-batch sum for the ray with index r in its cell: batch
+// r mod 16 (with fewer than 16 rays per cell, r < K and the batch is r itself).
+__device__ __forceinline__ size_t armc_slot(const TraceArgs &a, unsigned r, unsigned cell) {
+  return (size_t)(r & 15u) * (size_t)a.armc_nc + cell;
+}
+
+// binary32 -> binary64, exactly, from the bits (the conversion instruction runs
+// on the narrow binary64 pipe); zeros, subnormals, infinities and NaN take the
+// instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e - 1u < 254u) {
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  return (double)f;
+}
+
 // ---- binary64 per-cell tallies (Eq. 8: Q_i is the mean of the samples) -------
 //
 // Binary64 Neumaier summation of every sample would keep GB300's narrow binary64

@@ -53,7 +53,14 @@ namespace {
 
 // GEN: the general geometry (stretched y faces, closed-box x and z walls).  The
 // channel variant (uniform y, periodic x and z) drops those tests from the step.
-template <int MINB, int KSTEPS, bool MG, bool GEN>
+// AR: the absorption-based estimate (Section 2, ARMC): besides its own sample,
+// each ray deposits, into every other cell it crosses, minus the term it adds to
+// its own cell's emission-based estimate (the exchange seen from the absorbing
+// cell), its residual into the last cell it crossed, and its wall terms into
+// its own cell; deposits go to per-batch binary64 sums (batch = ray index mod K)
+// with atomic adds, and the ray's sample to its cell's per-batch emission-based
+// sum.  Uniform channel grids, one grid, no long-ray hand-off.
+template <int MINB, int KSTEPS, bool MG, bool GEN, bool AR = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpRing *rings = reinterpret_cast<WarpRing *>(smem_raw);
@@ -380,8 +387,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       const float Bj = kb.z + fr * kb.w;
       float alpha, trans;
       absorb(kap * ds, alpha, trans);
-      X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
-      tau *= trans;                     // Eq. 3
+      const float term = (B_i - Bj) * (tau * alpha);
+      X += term;     // Eq. 14 term / kappa_i
+      tau *= trans;  // Eq. 3
+      if (AR && lin != cellid)  // the exchange absorbed in cell j, seen from j
+        atomicAdd(a.armc_acc + armc_slot(a, r, lin), f32_to_f64(-scale * term));
       B_last = Bj;
       ++steps;
       if (MG) ++lsteps;
@@ -430,6 +440,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
             const float eps = wl ? eps1 : eps0;
             const float Bw = __ldg(a.bwall32 + ((unsigned)(wl * nb) + n));
             X += (B_i - Bw) * (tau * eps);
+            if (AR)  // the cell's own exchange with the wall
+              atomicAdd(a.armc_acc + armc_slot(a, r, cellid), f32_to_f64(scale * ((B_i - Bw) * (tau * eps))));
             tau *= 1.f - eps;
             ++tot_wall;
             if (eps >= 1.f || tau <= tol) {
@@ -540,6 +552,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
       if (!done && active) fcur = __ldg(field + (MG ? loff + lin : lin));
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+        if (AR) {
+          // the residual is absorbed in the last medium cell crossed (the row is
+          // clamped: after a wall event iy lies outside the grid)
+          const unsigned lres = (unsigned)(ix + nx * (min(max(iy, 0), ny - 1) + ny * iz));
+          if (tau > 0.f && lres != cellid)
+            atomicAdd(a.armc_acc + armc_slot(a, r, lres), f32_to_f64(-scale * ((B_i - B_last) * tau)));
+          atomicAdd(a.ermc_acc + armc_slot(a, r, cellid), f32_to_f64(scale * X));
+        }
         Ybuf[(size_t)slot * (unsigned)N + r] = scale * X;  // the ray's sample Y (Eq. 14)
         if (a.ray_steps) a.ray_steps[(size_t)slot * (unsigned)N + r] = (unsigned)steps;
         if (a.steps_cell) {
@@ -652,7 +672,35 @@ __global__ void __launch_bounds__(256) reduce_cells32_kernel(const TraceArgs a) 
   }
 }
 
-template <int MINB, int KSTEPS, bool MG, bool GEN>
+// The absorption-based estimate of each cell and its combination with the
+// emission-based one (Section 2), from the per-batch sums the AR trace launches
+// accumulated: batch b holds the rays r = b (mod K), n_b of them per cell.
+//   ARMC:   Q = sum_b A_b / N; sigma^2 = var_b(A_b / n_b) / K (batch means)
+//   hybrid: lam Q_E + (1 - lam) Q_A with lam = (T - T_min) / (T_max - T_min),
+//           sigma from the batch means of the combined batch estimates.
+// One thread per cell; binary64.
+__global__ void armc_finalize_kernel(const double *__restrict__ acc, const double *__restrict__ eacc,
+                                     long long nc, int K, int N, int hybrid, const double2 *__restrict__ field,
+                                     double T_min, double inv_dT, double *q, double *sigma) {
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += (long long)gridDim.x * blockDim.x) {
+    double lam = 0.0;
+    if (hybrid) lam = fmin(fmax((field[c].x - T_min) * inv_dT, 0.0), 1.0);
+    double sum = 0.0, mean = 0.0, m2 = 0.0;
+    for (int b = 0; b < K; ++b) {
+      const double nb = (double)((N - b + K - 1) / K);
+      const double vb = lam * eacc[(size_t)b * nc + c] + (1.0 - lam) * acc[(size_t)b * nc + c];
+      sum += vb;
+      const double xb = vb / nb, d = xb - mean;  // Welford over the batch estimates
+      mean += d / (double)(b + 1);
+      m2 += d * (xb - mean);
+    }
+    q[c] = sum / (double)N;
+    if (sigma) sigma[c] = K > 1 ? sqrt(m2 / ((double)(K - 1) * (double)K)) : 0.0;
+  }
+}
+
+template <int MINB, int KSTEPS, bool MG, bool GEN, bool AR = false>
 cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   static int configured_smem[64], blocks_per_sm[64], num_sms[64];
   static bool init_done = false;
@@ -665,13 +713,13 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (configured_smem[dev] != (int)smem) {
-    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS, MG, GEN>,
+    e = cudaFuncSetAttribute(trace_fp32_kernel<MINB, KSTEPS, MG, GEN, AR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev],
-                                                      trace_fp32_kernel<MINB, KSTEPS, MG, GEN>, WARPS * 32,
+                                                      trace_fp32_kernel<MINB, KSTEPS, MG, GEN, AR>, WARPS * 32,
                                                       smem);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm[dev] < 1) blocks_per_sm[dev] = 1;
@@ -682,18 +730,18 @@ cudaError_t configure_variant(size_t smem, int *bps, int *nsm) {
   return cudaSuccess;
 }
 
-template <int MINB, int KSTEPS, bool MG, bool GEN>
+template <int MINB, int KSTEPS, bool MG, bool GEN, bool AR = false>
 cudaError_t launch_variant(const TraceArgs &a, cudaStream_t s, size_t smem) {
   // per-device launch shape, computed once per device and shared-memory size
   int bps = 0, nsm = 0;
-  cudaError_t e = configure_variant<MINB, KSTEPS, MG, GEN>(smem, &bps, &nsm);
+  cudaError_t e = configure_variant<MINB, KSTEPS, MG, GEN, AR>(smem, &bps, &nsm);
   if (e != cudaSuccess) return e;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const long long need = (P + WARPS - 1) / WARPS;
   long long blocks = a.grid_blocks > 0 ? a.grid_blocks : (long long)nsm * bps;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  trace_fp32_kernel<MINB, KSTEPS, MG, GEN><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
+  trace_fp32_kernel<MINB, KSTEPS, MG, GEN, AR><<<(unsigned)blocks, WARPS * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -724,6 +772,9 @@ cudaError_t run_variant(bool prepare, const TraceArgs *a, int min_blocks, int st
 
 cudaError_t dispatch(bool prepare, const TraceArgs *a, int min_blocks, int steps_per_round, bool multigrid,
                      bool general, cudaStream_t s, size_t smem, int *bps, int *nsm) {
+  // the absorption-based estimate: one variant (default launch shape, single
+  // uniform channel grid; the host refuses the rest)
+  if (!prepare && a->armc_acc) return launch_variant<3, 1, false, false, true>(*a, s, smem);
   if (multigrid)
     return general ? run_variant<true, true>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm)
                    : run_variant<true, false>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm);
@@ -732,6 +783,18 @@ cudaError_t dispatch(bool prepare, const TraceArgs *a, int min_blocks, int steps
 }
 
 }  // namespace
+
+cudaError_t launch_armc_finalize(const double *acc, const double *eacc, long long nc, int K, int N,
+                                 int hybrid, const double2 *field, double T_min, double T_max, double *q,
+                                 double *sigma, cudaStream_t s) {
+  if (nc <= 0) return cudaSuccess;
+  long long blocks = (nc + 255) / 256;
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
+  const double inv = T_max > T_min ? 1.0 / (T_max - T_min) : 0.0;
+  armc_finalize_kernel<<<(unsigned)blocks, 256, 0, s>>>(acc, eacc, nc, K, N, hybrid, field, T_min, inv, q,
+                                                        sigma);
+  return cudaGetLastError();
+}
 
 long long fp32_bricks_positions(int bnx, int bny, int bnz) {
   const long long nbx = (bnx + BRICK - 1) / BRICK, nby = (bny + BRICK - 1) / BRICK,

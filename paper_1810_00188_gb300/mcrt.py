@@ -22,6 +22,7 @@ MCRT_MEM_HOST, MCRT_MEM_DEVICE = 0, 1
 MCRT_FP32, MCRT_FP64 = 0, 1
 MCRT_ORIGIN_UNIFORM, MCRT_ORIGIN_CENTER = 0, 1
 MCRT_PROPOSAL_PLANCK_TMAX, MCRT_PROPOSAL_CELL = 0, 1
+MCRT_EST_ERMC, MCRT_EST_ARMC, MCRT_EST_HYBRID = 0, 1, 2
 MCRT_REFLECT_DIFFUSE, MCRT_REFLECT_SPECULAR = 0, 1
 
 
@@ -54,7 +55,7 @@ class mcrt_solve_params(C.Structure):
                 ("seed", C.c_uint64), ("ray_offset", C.c_uint64), ("snapshot", C.c_uint32),
                 ("precision", C.c_int), ("origin", C.c_int), ("proposal", C.c_int),
                 ("use_box", C.c_int), ("box", C.c_int * 6), ("steps_out", C.c_void_p),
-                ("mg_levels", C.c_int), ("mg_steps", C.c_int)]
+                ("mg_levels", C.c_int), ("mg_steps", C.c_int), ("estimator", C.c_int)]
 
 
 class mcrt_tuning(C.Structure):
@@ -535,10 +536,11 @@ class Solver:
     @staticmethod
     def params(rays=128, seed=0, snapshot=0, ray_offset=0, tol=1e-4, max_steps=1 << 30,
                precision=MCRT_FP32, origin=MCRT_ORIGIN_UNIFORM, proposal=MCRT_PROPOSAL_PLANCK_TMAX,
-               box=None, mg_levels=1, mg_steps=5):
+               box=None, mg_levels=1, mg_steps=5, estimator=MCRT_EST_ERMC):
         p = mcrt_solve_params()
         p.rays_per_cell, p.max_steps, p.tol = rays, max_steps, tol
         p.mg_levels, p.mg_steps = mg_levels, mg_steps
+        p.estimator = estimator
         p.seed, p.ray_offset, p.snapshot = seed, ray_offset, snapshot
         p.precision, p.origin, p.proposal = precision, origin, proposal
         p.use_box = 0 if box is None else 1

@@ -42,8 +42,8 @@ GATHER_BYTES_PER_STEP = 8     # algorithmic bytes of a step: the FP32 {T, x} ent
 EXP_PER_STEP = 1              # one exponential per step (Eq. 2)
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the current
-# trace kernel; None until captured for the kernel as it stands
-TRACE_DRAM_BYTES_64_1000 = None
+# trace kernel (profiles/dram_nongrey_64cubed_1000rays.md)
+TRACE_DRAM_BYTES_64_1000 = 51943936 + 1035883520
 
 
 def parse():

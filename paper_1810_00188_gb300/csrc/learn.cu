@@ -229,9 +229,20 @@ __global__ void __launch_bounds__(TALLY_WARPS * 32) tally_kernel(const TallyArgs
 // 2^32) with a correctly rounded binary32 quotient (the scaling by 2^32 is
 // exact).  GB300 issues binary64 on a narrow pipe, and a proposal has 360
 // counts per cell.
+// floor(y) for 0 <= y < 2^32 from the bits (the significand shifted by the
+// exponent): the same value as the float-to-integer conversion, which runs on
+// GB300's narrow pipe.
+__device__ __forceinline__ unsigned floor_u32(float y) {
+  const unsigned u = __float_as_uint(y);
+  const int e = (int)(u >> 23) - 127;  // y in [2^e, 2^(e+1))
+  if (e < 0) return 0u;
+  const unsigned m = (u & 0x7FFFFFu) | 0x800000u;
+  return e >= 23 ? m << (e - 23) : m >> (23 - e);
+}
+
 __device__ __forceinline__ long long count32(float w, float W) {
   const float y = __fdiv_rn(w, W) * 4294967296.0f;
-  return y >= 4294967296.0f ? 4294967296LL : (long long)(unsigned)y;  // y >= 0: truncation is the floor
+  return y >= 4294967296.0f ? 4294967296LL : (long long)floor_u32(y);  // y >= 0
 }
 
 __device__ bool quantize_row(const float *w, int K, float W, unsigned long long *cum) {
@@ -239,6 +250,35 @@ __device__ bool quantize_row(const float *w, int K, float W, unsigned long long 
   int kmax = 0;
   float wmax = w[0];
   long long total = 0;
+  if (K <= 16) {  // the counts in registers (the same sums as below)
+    long long m[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < K) {
+        const float wk = w[k];
+        if (wk > wmax) {
+          wmax = wk;
+          kmax = k;
+        }
+        long long mk = 0;
+        if (wk > 0.f) {
+          mk = count32(wk, W);
+          mk = mk < 1 ? 1 : mk;
+        }
+        m[k] = mk;
+        total += mk;
+      }
+    }
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < K) {
+        acc += (unsigned long long)m[k] + (k == kmax ? (unsigned long long)(4294967296LL - total) : 0ull);
+        cum[k] = acc;
+      }
+    }
+    return true;
+  }
   for (int k = 0; k < K; ++k) {  // counts (kept in cum), their total, the first largest weight
     const float wk = w[k];
     if (wk > wmax) {
@@ -263,12 +303,12 @@ __device__ bool quantize_row(const float *w, int K, float W, unsigned long long 
 
 // Warp-cooperative: q [nb * ng] spectral probabilities and q_up of one cell ->
 // cumulative band counts cn [nb], g counts within each band cg [nb][ng], and the
-// upward-hemisphere count of 2^23.  wn: nb doubles of scratch (each holding a
-// binary32 band weight).  Each band's weight is the binary32 sum of its points in
+// upward-hemisphere count of 2^23.  wn: nb floats of scratch (the binary32 band
+// weights).  Each band's weight is the binary32 sum of its points in
 // order of g, the total the binary32 sum of the band weights in band order on
 // one lane; the counts, their exact integer total and the first largest weight
 // are formed across lanes.
-__device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double *wn,
+__device__ void quantize_cell(const float *q, float q_up, int nb, int ng, float *wn,
                               unsigned long long *cn, unsigned long long *cg, unsigned *hemi,
                               unsigned long long *err) {
   const int lane = threadIdx.x & 31;
@@ -276,7 +316,7 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
     const float *qn = q + (size_t)n * ng;
     float W = 0.f;
     for (int g = 0; g < ng; ++g) W += qn[g];
-    wn[n] = (double)W;
+    wn[n] = W;
     if (!quantize_row(qn, ng, W, cg + (size_t)n * ng)) {
       // a band that is never drawn gets uniform g counts (weights 1, so the
       // remainder goes to g = 0)
@@ -291,16 +331,18 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
   __syncwarp();
   float W = 0.f;
   if (lane == 0)
-    for (int n = 0; n < nb; ++n) W += (float)wn[n];
+    for (int n = 0; n < nb; ++n) W += wn[n];  // binary32, in band order
   W = __shfl_sync(0xffffffffu, W, 0);
   if (!(W > 0.f)) {
     if (lane == 0) atomicOr(err, 2ull);
   } else {
+    // band counts (lane l: bands l, l + 32, ...), their exact total and the
+    // first largest band weight
     long long tot = 0;
     float bw = -1.f;
     int bk = nb;
     for (int n = lane; n < nb; n += 32) {
-      const float w = (float)wn[n];
+      const float w = wn[n];
       if (w > bw) {
         bw = w;
         bk = n;
@@ -310,7 +352,6 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
         mk = count32(w, W);
         mk = mk < 1 ? 1 : mk;
       }
-      cn[n] = (unsigned long long)mk;
       tot += mk;
     }
 #pragma unroll
@@ -323,20 +364,36 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, double
         bk = ok;
       }
     }
-    __syncwarp();
-    if (lane == 0) {
-      unsigned long long acc = 0;
-      for (int n = 0; n < nb; ++n) {
-        acc += cn[n] + (n == bk ? (unsigned long long)(4294967296LL - tot) : 0ull);
-        cn[n] = acc;
+    // cumulative counts: a warp scan per round of 32 bands, the rounds in order
+    // (integer sums: the same values in any order); the remainder goes to the
+    // first largest band
+    unsigned long long carry = 0;
+    for (int n0 = 0; n0 < nb; n0 += 32) {
+      const int n = n0 + lane;
+      unsigned long long v = 0;
+      if (n < nb) {
+        const float w = wn[n];
+        long long mk = 0;
+        if (w > 0.f) {
+          mk = count32(w, W);
+          mk = mk < 1 ? 1 : mk;
+        }
+        v = (unsigned long long)mk + (n == bk ? (unsigned long long)(4294967296LL - tot) : 0ull);
       }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (n < nb) cn[n] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
     }
   }
   if (lane == 0) {
-    double hq = floor((double)q_up * 8388608.0 + 0.5);
-    if (!(hq >= 1.0)) hq = 1.0;
-    if (hq > 8388607.0) hq = 8388607.0;
-    *hemi = (unsigned)hq;
+    // round half up of q_up 2^23 (exact in binary32: the scaling is a power of
+    // two and the sum is below 2^23 + 1/2 with an ulp of at most 1/2)
+    const float hq = fminf(fmaxf(floorf(q_up * 8388608.f + 0.5f), 1.f), 8388607.f);
+    *hemi = floor_u32(hq);
   }
   __syncwarp();
 }
@@ -346,15 +403,15 @@ __global__ void __launch_bounds__(NTHR) quantize_cells_kernel(const float *q, lo
                                                              unsigned long long *cell_cg,
                                                              unsigned *cell_hemi,
                                                              unsigned long long *err) {
-  extern __shared__ double qsm[];
+  extern __shared__ float qsm[];  // per warp: the band weights
   const int w = threadIdx.x >> 5;
   const int K = nb * ng;
-  double *wn = qsm + (size_t)w * nb;
+  float *wn = qsm + (size_t)w * nb;
   for (long long c = (long long)blockIdx.x * (NTHR / 32) + w; c < n;
        c += (long long)gridDim.x * (NTHR / 32)) {
     const float *qc = q + c * (K + 2);
-    quantize_cell(qc, qc[K], nb, ng, wn, cell_cn + c * nb, cell_cg + c * (long long)K,
-                  cell_hemi + c, err);
+    quantize_cell(qc, qc[K], nb, ng, wn, cell_cn + c * nb, cell_cg + c * (long long)K, cell_hemi + c,
+                  err);
   }
 }
 
@@ -369,11 +426,12 @@ __global__ void __launch_bounds__(NTHR) quantize_cells_kernel(const float *q, lo
 // weight divides by the quantised probability, so the estimate stays unbiased),
 // hemispheres 1/2 each.
 __global__ void __launch_bounds__(NTHR) spectral_proposal_kernel(const SpectralArgs a) {
-  extern __shared__ double ssm[];
+  extern __shared__ float ssm[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int K = a.nb * a.ng;
-  double *wn = ssm + (size_t)w * a.nb;
-  float *qw = reinterpret_cast<float *>(ssm + (size_t)(NTHR / 32) * a.nb) + (size_t)w * K;
+  // per warp: the band weights, the cell's K probabilities
+  float *wn = ssm + (size_t)w * a.nb;
+  float *qw = ssm + (size_t)(NTHR / 32) * a.nb + (size_t)w * K;
   for (long long c = (long long)blockIdx.x * (NTHR / 32) + w; c < a.n;
        c += (long long)gridDim.x * (NTHR / 32)) {
     const uint2 pk = a.fpos32[c];
@@ -581,6 +639,170 @@ __global__ void __launch_bounds__(NTHR) mlp_infer_kernel(const MlpInferArgs a) {
     // softmax over the spectral logits and the hemisphere pair, then the mixture
     for (int c = w; c < rows; c += NTHR / 32) {
       float *z = Z + (size_t)c * KO;
+      const float *p0 = a.p0_stride ? a.p0 + (t0 + c) * (long long)a.p0_stride : p0s;
+      float mx = -INFINITY;
+      for (int k = lane; k < K; k += 32) mx = fmaxf(mx, z[k]);
+      mx = warp_max(mx);
+      float sum = 0.f;
+      for (int k = lane; k < K; k += 32) sum += expf(z[k] - mx);
+      sum = warp_sum(sum);
+      const float inv = 1.f / sum;
+      const float hm = fmaxf(z[K], z[K + 1]);
+      const float eu = expf(z[K] - hm), ed = expf(z[K + 1] - hm);
+      __syncwarp();
+      for (int k = lane; k < K; k += 32)
+        z[k] = (1.f - a.mix) * (expf(z[k] - mx) * inv) + a.mix * p0[k];
+      __syncwarp();
+      if (lane == 0) {
+        z[K] = (1.f - a.mix) * (eu / (eu + ed)) + a.mix * 0.5f;
+        z[K + 1] = (1.f - a.mix) * (ed / (eu + ed)) + a.mix * 0.5f;
+      }
+      __syncwarp();
+      for (int k = lane; k < KO; k += 32) a.q_out[(t0 + c) * KO + k] = z[k];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- inference on the tensor cores ------------------------------------------------
+// The two 64-wide layers and the output layer are contractions of FP16 weights
+// with FP32 activations: mma.sync m16n8k16 (FP16 operands, FP32 accumulation)
+// over tiles of 16 cells.  Each activation h is split into FP16 parts hi =
+// RN16(h), lo = RN16(h - hi) (h = hi + lo to about 2^-22 relative) and every
+// product is taken twice, W hi + W lo: the weights are FP16 numbers already, so
+// the layers keep about binary32 accuracy.  The 12-wide input layer stays on the
+// FP32 units (3% of the work).  Weights W2 [64][LDK] and W3 [n-tiles * 8][LDK]
+// are stored row by output ([n][k], the m16n8k16 B operand), activations
+// [cell][LDK]: with LDK = 72 halves (36 words) the fragment loads are free of
+// bank conflicts; the logits go to Z [16][LDZ] with LDZ = 8 (mod 32) words.
+constexpr int ITC = 16;   // cells per tensor-core tile
+constexpr int LDK = 72;   // halves per row of W2, W3 and the activations
+__host__ __device__ inline int tc_ntiles(int K) { return (K + 2 + 7) / 8; }
+__host__ __device__ inline int tc_ldz(int K) { return ((K + 2 + 23) / 32) * 32 + 8; }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// hi/lo FP16 parts of two neighbouring activations, stored as half2 words
+__device__ __forceinline__ void split_store(__half *hi, __half *lo, int off, float v0, float v1) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  *reinterpret_cast<__half2 *>(hi + off) = h;
+  *reinterpret_cast<__half2 *>(lo + off) = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+}
+
+// One 16 x 8 output tile of a 64-deep layer: D = sum_k (Ahi + Alo)[16][k] W[n0 + .][k]
+__device__ __forceinline__ void mma_tile64(const __half *Ahi, const __half *Alo, const __half *W, int n0,
+                                           int lane, float (&d)[4]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int k0 = 0; k0 < NH; k0 += 16) {
+    const __half *wrow = W + (size_t)(n0 + g) * LDK + k0 + 2 * t;
+    const unsigned b0 = *reinterpret_cast<const unsigned *>(wrow);
+    const unsigned b1 = *reinterpret_cast<const unsigned *>(wrow + 8);
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      const __half *A = part ? Alo : Ahi;
+      unsigned a[4];
+      a[0] = *reinterpret_cast<const unsigned *>(A + g * LDK + k0 + 2 * t);
+      a[1] = *reinterpret_cast<const unsigned *>(A + (g + 8) * LDK + k0 + 2 * t);
+      a[2] = *reinterpret_cast<const unsigned *>(A + g * LDK + k0 + 2 * t + 8);
+      a[3] = *reinterpret_cast<const unsigned *>(A + (g + 8) * LDK + k0 + 2 * t + 8);
+      mma16816(d, a, b0, b1);
+    }
+  }
+}
+
+size_t infer_tc_smem_bytes(int K) {
+  const size_t halves = (size_t)NF * NH + (size_t)NH * LDK + (size_t)tc_ntiles(K) * 8 * LDK + 4 * ITC * LDK;
+  const size_t floats = 2 * NH + (size_t)tc_ntiles(K) * 8 + ITC * NF + (size_t)ITC * tc_ldz(K) + K + 2 * NF;
+  return ((halves * 2 + 15) / 16) * 16 + floats * 4 + 64;
+}
+
+__global__ void __launch_bounds__(NTHR) mlp_infer_tc_kernel(const MlpInferArgs a) {
+  extern __shared__ __align__(16) unsigned char tcs[];
+  const int K = a.K, KO = K + 2, NT = tc_ntiles(K), ldz = tc_ldz(K);
+  __half *W1T = reinterpret_cast<__half *>(tcs);  // [12][64]
+  __half *W2 = W1T + NF * NH;                     // [64][LDK]
+  __half *W3 = W2 + NH * LDK;                     // [NT * 8][LDK]
+  __half *H1h = W3 + (size_t)NT * 8 * LDK, *H1l = H1h + ITC * LDK;
+  __half *H2h = H1l + ITC * LDK, *H2l = H2h + ITC * LDK;
+  const size_t halves = (size_t)NF * NH + (size_t)NH * LDK + (size_t)NT * 8 * LDK + 4 * ITC * LDK;
+  float *b1 = reinterpret_cast<float *>(tcs + ((halves * 2 + 15) / 16) * 16);
+  float *b2 = b1 + NH, *b3 = b2 + NH;  // b3 [NT * 8]
+  float *X = b3 + NT * 8, *Z = X + ITC * NF;  // Z [16][ldz]
+  float *p0s = Z + (size_t)ITC * ldz, *nrm = p0s + K;
+  {
+    const __half *tW1 = a.theta16, *tW2 = tW1 + NH * NF + NH, *tW3 = tW2 + NH * NH + NH;
+    const __half *tb1 = tW1 + NH * NF, *tb2 = tW2 + NH * NH, *tb3 = tW3 + (size_t)KO * NH;
+    for (int e = threadIdx.x; e < NH * NF; e += blockDim.x) W1T[(e % NF) * NH + e / NF] = tW1[e];
+    for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) W2[(e / NH) * LDK + e % NH] = tW2[e];
+    for (int e = threadIdx.x; e < NT * 8 * NH; e += blockDim.x) {
+      const int o = e / NH, i = e % NH;
+      W3[o * LDK + i] = o < KO ? tW3[(size_t)o * NH + i] : __float2half(0.f);
+    }
+    for (int e = threadIdx.x; e < NH; e += blockDim.x) {
+      b1[e] = __half2float(tb1[e]);
+      b2[e] = __half2float(tb2[e]);
+    }
+    for (int e = threadIdx.x; e < NT * 8; e += blockDim.x) b3[e] = e < KO ? __half2float(tb3[e]) : 0.f;
+    for (int e = threadIdx.x; e < NF; e += blockDim.x) {
+      nrm[e] = a.fmean[e];
+      nrm[NF + e] = a.finv[e];
+    }
+    if (a.p0_stride == 0)
+      for (int e = threadIdx.x; e < K; e += blockDim.x) p0s[e] = a.p0[e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const long long ntiles = (a.n + ITC - 1) / ITC;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long t0 = tile * ITC;
+    const int rows = (int)min((long long)ITC, a.n - t0);
+    for (int e = threadIdx.x; e < ITC * NF; e += blockDim.x) {
+      const int c = e / NF, i = e % NF;
+      X[e] = c < rows ? (a.feat[(t0 + c) * NF + i] - nrm[i]) * nrm[NF + i] : 0.f;
+    }
+    __syncthreads();
+    // input layer (FP32): two neighbouring outputs per thread
+    for (int e = threadIdx.x; e < ITC * NH / 2; e += blockDim.x) {
+      const int c = e / (NH / 2), o = 2 * (e % (NH / 2));
+      float h0 = b1[o], h1 = b1[o + 1];
+#pragma unroll
+      for (int i = 0; i < NF; ++i) {
+        const float x = X[c * NF + i];
+        h0 += __half2float(W1T[i * NH + o]) * x;
+        h1 += __half2float(W1T[i * NH + o + 1]) * x;
+      }
+      split_store(H1h, H1l, c * LDK + o, gelu(h0), gelu(h1));
+    }
+    __syncthreads();
+    // hidden layer: warp w computes outputs 8w .. 8w + 7
+    {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_tile64(H1h, H1l, W2, 8 * w, lane, d);
+      const int o = 8 * w + 2 * t;
+      split_store(H2h, H2l, g * LDK + o, gelu(d[0] + b2[o]), gelu(d[1] + b2[o + 1]));
+      split_store(H2h, H2l, (g + 8) * LDK + o, gelu(d[2] + b2[o]), gelu(d[3] + b2[o + 1]));
+    }
+    __syncthreads();
+    // output layer: the n-tiles round-robin over the warps
+    for (int nt = w; nt < NT; nt += NTHR / 32) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_tile64(H2h, H2l, W3, 8 * nt, lane, d);
+      const int o = 8 * nt + 2 * t;
+      *reinterpret_cast<float2 *>(Z + g * ldz + o) = make_float2(d[0] + b3[o], d[1] + b3[o + 1]);
+      *reinterpret_cast<float2 *>(Z + (g + 8) * ldz + o) = make_float2(d[2] + b3[o], d[3] + b3[o + 1]);
+    }
+    __syncthreads();
+    // softmax over the spectral logits and the hemisphere pair, then the mixture
+    for (int c = w; c < rows; c += NTHR / 32) {
+      float *z = Z + (size_t)c * ldz;
       const float *p0 = a.p0_stride ? a.p0 + (t0 + c) * (long long)a.p0_stride : p0s;
       float mx = -INFINITY;
       for (int k = lane; k < K; k += 32) mx = fmaxf(mx, z[k]);
@@ -993,6 +1215,17 @@ cudaError_t launch_tally(const TallyArgs &t, cudaStream_t s) {
 
 cudaError_t launch_mlp_infer(const MlpInferArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  const size_t tsmem = infer_tc_smem_bytes(a.K);
+  if (tsmem <= 200 * 1024) {  // the tensor-core kernel (every K a network here uses)
+    cudaError_t e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_tc_kernel, NTHR, tsmem);
+    if (e != cudaSuccess) return e;
+    mlp_infer_tc_kernel<<<grid_for(a.n, ITC, per_sm > 0 ? per_sm : 1), NTHR, tsmem, s>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = infer_smem_bytes(a.K);
   cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -1009,7 +1242,7 @@ cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
                                   unsigned long long *cell_cn, unsigned long long *cell_cg,
                                   unsigned *cell_hemi, unsigned long long *err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(NTHR / 32) * nb * sizeof(double);
+  const size_t smem = (size_t)(NTHR / 32) * nb * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(quantize_cells_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1020,7 +1253,7 @@ cudaError_t launch_quantize_cells(const float *q, long long n, int nb, int ng,
 
 cudaError_t launch_spectral_proposal(const SpectralArgs &a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const size_t smem = (size_t)(NTHR / 32) * (a.nb * sizeof(double) + (size_t)a.nb * a.ng * sizeof(float));
+  const size_t smem = (size_t)(NTHR / 32) * ((size_t)a.nb + (size_t)a.nb * a.ng) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(spectral_proposal_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
   const unsigned *__restrict__ chemi_b = nullptr;
   int reflect_b = 0;
   unsigned snapw_b = 0;
-#define m (BATCH ? (m) : (member))
   long long sp0 = 0, sp1 = BATCH ? 0 : 0x7fffffffffffffffLL;  // positions of this snapshot
   bool pending = false;  // the next claimed position lies in another snapshot
   // stretched y (faces non-null): tsy holds 1/|d_y| and each y crossing adds the

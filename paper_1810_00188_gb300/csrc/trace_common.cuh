@@ -255,6 +255,284 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return (double)f;
 }
 
+// ---- one march round of a lane (both FP32 trace kernels) ----------------------
+
+// A ray in flight: the registers of one lane.  Table and field indices are
+// unsigned: widening them to 64-bit addresses is free, while sign-extending an
+// int costs a conversion on GB300's narrow pipe.
+struct LaneRay {
+  bool active = false;
+  unsigned lin = 0, krow = 0, n = 0, slot = 0, r = 0;
+  uint2 fcur = make_uint2(0u, 0u);  // field entry of the current cell, loaded a step ahead
+  int ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0;
+  unsigned ray = 0, nrefl = 0, cellid = 0;
+  float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
+  float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
+  // multigrid: current grid, segments marched on it, offset of its fields, and
+  // the face counter step (grid lev keeps every inc-th face of the grid the
+  // axis parameters were set up on)
+  int lev = 0, lsteps = 0;
+  unsigned loff = 0;
+  float inc = 1.f;
+};
+
+// A lane's counts for the solve's statistics and the per-cell step sums.
+struct LaneStats {
+  unsigned long long tot_steps = 0;
+  unsigned tot_cap = 0, tot_wall = 0, max_ray = 0, tot_rays = 0;
+  int acc_slot = -1;  // run of steps for the per-cell step counts
+  unsigned acc_steps = 0;
+};
+
+// What a march round reads besides the ray and the launch arguments: the grid,
+// fields and walls of the solve, or of the snapshot a batched warp is on.
+struct MarchGrid {
+  int nx, ny, nz, nxy;
+  const uint2 *field;        // table positions and x of every multigrid grid
+  const float *yfs;          // stretched y faces, or null
+  const float *bwall;        // wall band intensities [faces][nb]
+  float DX, DY, DZ, eps0, eps1;
+  int reflect;               // 0 diffuse, 1 specular
+  unsigned snapw;            // fourth Philox counter word
+};
+
+// Up to KSTEPS march steps of the lane's ray (Algorithm 1 "March"): per segment
+// the absorption of Eq. 2, the term of Eq. 14 and the transmissivity of Eq. 3;
+// face crossings with the periodic wrap, wall events (Eq. 3 wall factor,
+// diffuse or specular reflection), the multigrid switch (Section 4.3), the
+// hand-off of long rays, and at the end the residual dump and the sample.
+// GEN: stretched y faces and closed boxes; AR: the absorption-based deposits;
+// BATCH: a batched launch (the snapshot of a handed-off ray from its position
+// among the snapshots' first positions, `starts`).
+template <int KSTEPS, bool MG, bool GEN, bool AR, bool BATCH>
+__device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid &g, LaneRay &s, LaneStats &ls,
+                                            const long long *starts = nullptr) {
+  const float *__restrict__ yfs = GEN ? g.yfs : nullptr;
+  const float4 *__restrict__ kbtab = a.kbtab32;
+  const uint2 *__restrict__ field = g.field;
+  const float *__restrict__ bwall = g.bwall;
+  float *__restrict__ Ybuf = a.ybuf;
+  const float tol = a.tol32;
+  const int nb = a.nb;
+  const unsigned N = (unsigned)a.rays;
+  auto dyl = [&](int j, int l) -> float {
+    return __ldg(yfs + ((unsigned)(j + 1) << l)) - __ldg(yfs + ((unsigned)j << l));
+  };
+  for (int kstep = 0; kstep < KSTEPS; ++kstep) {
+    if (!s.active) break;
+    float tn;
+    int ax;
+    if (s.tnx <= s.tny && s.tnx <= s.tnz) {
+      ax = 0;
+      tn = s.tnx;
+    } else if (s.tny <= s.tnz) {
+      ax = 1;
+      tn = s.tny;
+    } else {
+      ax = 2;
+      tn = s.tnz;
+    }
+    const float ds = fmaxf(tn - s.tprev, 0.f);
+    const uint2 f = s.fcur;
+    unsigned it;
+    float fr;
+    tpos(f.x, it, fr);
+    const float4 kb = __ldg(kbtab + (s.krow + it));
+    const float kap = (kb.x + fr * kb.y) * __uint_as_float(f.y);
+    const float Bj = kb.z + fr * kb.w;
+    float alpha, trans;
+    absorb(kap * ds, alpha, trans);
+    const float term = (s.B_i - Bj) * (s.tau * alpha);
+    s.X += term;     // Eq. 14 term / kappa_i
+    s.tau *= trans;  // Eq. 3
+    if (AR && s.lin != s.cellid)  // the exchange absorbed in cell j, seen from j
+      atomicAdd(a.armc_acc + armc_slot(a, s.r, s.lin), f32_to_f64(-s.scale * term));
+    s.B_last = Bj;
+    ++s.steps;
+    if (MG) ++s.lsteps;
+    bool done = s.tau <= tol;
+    if (!done && s.steps >= a.max_steps) {
+      done = true;
+      ++ls.tot_cap;
+    }
+    if (!done) {
+      s.tprev = tn;
+      // dimensions of the current grid
+      const int nxl = MG ? g.nx >> s.lev : g.nx, nyl = MG ? g.ny >> s.lev : g.ny, nzl = MG ? g.nz >> s.lev : g.nz;
+      const int nxyl = MG ? nxl * nyl : g.nxy;
+      {
+        // branch-free advance of the crossed axis (lanes cross different axes)
+        const bool mx = ax == 0, my = ax == 1, mz = ax == 2;
+        const float step = MG ? s.inc : 1.f;
+        s.cntx += mx ? step : 0.f;
+        s.cnty += my ? step : 0.f;
+        s.cntz += mz ? step : 0.f;
+        s.tnx = mx ? fmaf(s.cntx, s.tsx, s.t0x) : s.tnx;
+        s.tny = my ? fmaf(s.cnty, s.tsy, s.t0y) : s.tny;
+        s.tnz = mz ? fmaf(s.cntz, s.tsz, s.t0z) : s.tnz;
+        s.ix += mx ? s.sx : 0;
+        s.iy += my ? s.sy : 0;
+        s.iz += mz ? s.sz : 0;
+        if (yfs && my && (unsigned)s.iy < (unsigned)nyl) s.tny = s.tprev + dyl(s.iy, MG ? s.lev : 0) * s.tsy;
+        // periodic wrap: an index can only leave the grid in the ray's direction
+        const int wx = (unsigned)s.ix < (unsigned)nxl ? 0 : -s.sx * nxl;
+        s.ix += wx;
+        const int wz = (unsigned)s.iz < (unsigned)nzl ? 0 : -s.sz * nzl;
+        s.iz += wz;
+        // the linear index from the three indices (multiply-adds, off the ALU pipe)
+        s.lin = (unsigned)(s.ix + nxl * (s.iy + nyl * s.iz));
+        if (GEN && !BATCH && a.xz_walls && (wx | wz)) {
+          // closed box: a black x or z wall absorbs the rest of the ray and
+          // emits at its temperature (Eq. 3 wall factor with eps = 1)
+          const int f = wx ? (wx > 0 ? 2 : 3) : (wz > 0 ? 4 : 5);
+          s.X += (s.B_i - __ldg(bwall + ((unsigned)(f * nb) + s.n))) * s.tau;
+          s.tau = 0.f;
+          ++ls.tot_wall;
+          done = true;
+        } else if ((unsigned)s.iy >= (unsigned)nyl) {
+          // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
+          const int wl = s.iy < 0 ? 0 : 1;
+          const float eps = wl ? g.eps1 : g.eps0;
+          const float Bw = __ldg(bwall + ((unsigned)(wl * nb) + s.n));
+          s.X += (s.B_i - Bw) * (s.tau * eps);
+          if (AR)  // the cell's own exchange with the wall
+            atomicAdd(a.armc_acc + armc_slot(a, s.r, s.cellid), f32_to_f64(s.scale * ((s.B_i - Bw) * (s.tau * eps))));
+          s.tau *= 1.f - eps;
+          ++ls.tot_wall;
+          if (eps >= 1.f || s.tau <= tol) {
+            done = true;
+          } else {
+            // fractions of the current grid's cell, whose extent along an
+            // axis is inc face steps of the axis parameters
+            const float cx = MG ? s.tsx * s.inc : s.tsx, cz = MG ? s.tsz * s.inc : s.tsz;
+            float nfx = 0.5f, nfz = 0.5f;
+            if (s.sx > 0)
+              nfx = 1.f - (s.tnx - s.tprev) / cx;
+            else if (s.sx < 0)
+              nfx = (s.tnx - s.tprev) / cx;
+            if (s.sz > 0)
+              nfz = 1.f - (s.tnz - s.tprev) / cz;
+            else if (s.sz < 0)
+              nfz = (s.tnz - s.tprev) / cz;
+            nfx = fminf(fmaxf(nfx, 0.f), 1.f);
+            nfz = fminf(fmaxf(nfz, 0.f), 1.f);
+            const float nfy = wl == 0 ? 0.f : 1.f;
+            s.iy = wl == 0 ? 0 : nyl - 1;
+            s.lin = (unsigned)(s.ix + nxl * s.iy + nxyl * s.iz);
+            // cell size of the current grid over the finest, and of the grid
+            // the axis parameters were set up on
+            const float gl = MG ? (float)(1 << s.lev) : 1.f, gb = MG ? gl / s.inc : 1.f;
+            float ddx, ddy, ddz;
+            if (g.reflect == 1) {
+              // specular: |d| per axis unchanged, the y component flips
+              ddx = s.sx > 0 ? gb * g.DX / s.tsx : (s.sx < 0 ? -gb * g.DX / s.tsx : 0.f);
+              ddz = s.sz > 0 ? gb * g.DZ / s.tsz : (s.sz < 0 ? -gb * g.DZ / s.tsz : 0.f);
+              const float ady = yfs ? 1.f / s.tsy : gb * g.DY / s.tsy;
+              ddy = wl == 0 ? ady : -ady;
+            } else {
+              // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
+              const uint4 v = philox10(make_uint4(s.cellid, s.ray, 2u + s.nrefl, g.snapw), a.key0, a.key1);
+              const float mr = sqrtf(unif(v.x));
+              float sp, cp;
+              sincos_2pi(unif(v.y), sp, cp);
+              const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
+              ddx = sr * cp;
+              ddy = wl == 0 ? mr : -mr;
+              ddz = sr * sp;
+            }
+            ++s.nrefl;
+            axis_setup(ddx, nfx, gl * g.DX, s.sx, s.t0x, s.tsx);
+            axis_setup(ddy, nfy, yfs ? dyl(s.iy, MG ? s.lev : 0) : gl * g.DY, s.sy, s.t0y, s.tsy);
+            axis_setup(ddz, nfz, gl * g.DZ, s.sz, s.t0z, s.tsz);
+            if (yfs && s.sy != 0) s.tsy = __frcp_rn(fabsf(ddy));
+            s.cntx = s.cnty = s.cntz = 0.f;
+            s.tnx = s.t0x;
+            s.tny = s.t0y;
+            s.tnz = s.t0z;
+            s.tprev = 0.f;
+            if (MG) s.inc = 1.f;
+          }
+        }
+      }
+      if (MG && !done && s.lev + 1 < a.mg_levels && s.lsteps >= a.mg_steps) {
+        // multigrid (Section 4.3): fall onto the next coarser grid here.  Its
+        // faces are the even-numbered faces of this grid, so an axis whose
+        // next face is odd-numbered skips it; the cell is the one containing
+        // this one.
+        if (s.sx != 0 && ((s.sx > 0 ? s.ix + 1 : s.ix) & 1)) {
+          s.cntx += s.inc;
+          s.tnx = fmaf(s.cntx, s.tsx, s.t0x);
+        }
+        if (s.sy != 0 && ((s.sy > 0 ? s.iy + 1 : s.iy) & 1)) {
+          if (yfs) {
+            s.tny += dyl(s.sy > 0 ? s.iy + 1 : s.iy - 1, s.lev) * s.tsy;  // the skipped row's height
+          } else {
+            s.cnty += s.inc;
+            s.tny = fmaf(s.cnty, s.tsy, s.t0y);
+          }
+        }
+        if (s.sz != 0 && ((s.sz > 0 ? s.iz + 1 : s.iz) & 1)) {
+          s.cntz += s.inc;
+          s.tnz = fmaf(s.cntz, s.tsz, s.t0z);
+        }
+        s.loff += (unsigned)(nxyl * nzl);
+        s.ix >>= 1;
+        s.iy >>= 1;
+        s.iz >>= 1;
+        s.lin = (unsigned)(s.ix + (nxl >> 1) * (s.iy + (nyl >> 1) * s.iz));
+        s.inc *= 2.f;
+        ++s.lev;
+        s.lsteps = 0;
+      }
+    }
+    if (!MG && !done && s.steps >= a.long_steps && (s.steps == a.long_steps || ax == 1) &&
+        long_flight(s.tny, s.tprev, s.tsx, s.tsz, a.long_flight)) {
+      // a long flight ahead (a grazing ray of a thin band): the warp-parallel
+      // march of long_rays.cu finishes this ray; checked when the ray reaches
+      // long_steps segments and at each later y face (a reflection is one)
+      LongRay L;
+      L.t0x = s.t0x; L.t0y = s.t0y; L.t0z = s.t0z; L.tsx = s.tsx;
+      L.tsy = s.tsy; L.tsz = s.tsz; L.cntx = s.cntx; L.cnty = s.cnty;
+      L.cntz = s.cntz; L.tnx = s.tnx; L.tny = s.tny; L.tnz = s.tnz;
+      L.tprev = s.tprev; L.tau = s.tau; L.X = s.X; L.B_i = s.B_i;
+      L.B_last = s.B_last; L.scale = s.scale; L.krow = s.krow; L.n = s.n;
+      L.ix = s.ix; L.iy = s.iy; L.iz = s.iz;
+      L.signs = (unsigned)(s.sx + 1) | ((unsigned)(s.sy + 1) << 2) | ((unsigned)(s.sz + 1) << 4);
+      L.lin = s.lin; L.slot = s.slot; L.r = s.r; L.ray = s.ray;
+      L.cellid = s.cellid; L.steps = (unsigned)s.steps; L.nrefl = s.nrefl; L.snap = BATCH ? (unsigned)snapshot_of(starts, a.nsnaps, a.chunk_p0 + s.slot) : 0u;
+      if (hand_off(a, L)) s.active = false;
+    }
+    // the next step's field entry, loaded now so that its latency overlaps the
+    // rest of this round
+    if (!done && s.active) s.fcur = __ldg(field + (MG ? s.loff + s.lin : s.lin));
+    if (done) {
+      if (s.tau > 0.f) s.X += (s.B_i - s.B_last) * s.tau;  // residual dump (Algorithm 1)
+      if (AR) {
+        // the residual is absorbed in the last medium cell crossed (the row is
+        // clamped: after a wall event iy lies outside the grid)
+        const unsigned lres = (unsigned)(s.ix + g.nx * (min(max(s.iy, 0), g.ny - 1) + g.ny * s.iz));
+        if (s.tau > 0.f && lres != s.cellid)
+          atomicAdd(a.armc_acc + armc_slot(a, s.r, lres), f32_to_f64(-s.scale * ((s.B_i - s.B_last) * s.tau)));
+        atomicAdd(a.ermc_acc + armc_slot(a, s.r, s.cellid), f32_to_f64(s.scale * s.X));
+      }
+      Ybuf[(size_t)s.slot * (unsigned)N + s.r] = s.scale * s.X;  // the ray's sample Y (Eq. 14)
+      if (a.ray_steps) a.ray_steps[(size_t)s.slot * (unsigned)N + s.r] = (unsigned)s.steps;
+      if (a.steps_cell) {
+        if ((int)s.slot != ls.acc_slot) {
+          if (ls.acc_slot >= 0 && ls.acc_steps) atomicAdd(a.step_acc + ls.acc_slot, (unsigned long long)ls.acc_steps);
+          ls.acc_slot = (int)s.slot;
+          ls.acc_steps = 0;
+        }
+        ls.acc_steps += (unsigned)s.steps;
+      }
+      ls.tot_steps += (unsigned long long)s.steps;
+      ls.max_ray = max(ls.max_ray, (unsigned)s.steps);
+      ++ls.tot_rays;
+      s.active = false;
+    }
+  }
+}
+
 // ---- binary64 per-cell tallies (Eq. 8: Q_i is the mean of the samples) -------
 //
 // Binary64 Neumaier summation of every sample would keep GB300's narrow binary64

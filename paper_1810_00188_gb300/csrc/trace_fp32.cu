@@ -125,26 +125,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   bool exhausted = false;
   unsigned head = 0, tail = 0;  // ring positions (mod POOL)
 
-  // per-lane ray registers
-  bool active = false;
-  // table and field indices are unsigned: widening them to 64-bit addresses is
-  // free, while sign-extending an int costs a conversion on GB300's narrow pipe
-  unsigned lin = 0, krow = 0, n = 0, slot = 0, r = 0;
-  uint2 fcur = make_uint2(0u, 0u);  // field entry of the current cell, loaded a step ahead
-  int ix = 0, iy = 0, iz = 0, sx = 0, sy = 0, sz = 0, steps = 0;
-  unsigned ray = 0, nrefl = 0, cellid = 0;
-  float t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
-  float tnx = 0, tny = 0, tnz = 0, tprev = 0, tau = 1, X = 0, B_i = 0, B_last = 0, scale = 0;
-  // multigrid: current grid, segments marched on it, offset of its fields, and
-  // the face counter step (grid lev keeps every inc-th face of the grid the
-  // axis parameters were set up on)
-  int lev = 0, lsteps = 0;
-  unsigned loff = 0;
-  float inc = 1.f;
-  unsigned long long tot_steps = 0;
-  unsigned tot_cap = 0, tot_wall = 0, max_ray = 0, tot_rays = 0;
-  int acc_slot = -1;  // run of steps for the per-cell step counts
-  unsigned acc_steps = 0;
+  // the lane's ray and counts; the grid the march reads
+  LaneRay lr;
+  LaneStats ls;
+  const MarchGrid mg_grid{nx, ny, nz, nxy, field, yfs, a.bwall32, DX, DY, DZ, eps0, eps1, a.reflect,
+                          a.snapshot};
 
   for (;;) {
     bool progress = false;
@@ -286,16 +271,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           Ybuf[(size_t)c_slot * (unsigned)N + (unsigned)rr] = 0.f;
           if (a.ray_steps) a.ray_steps[(size_t)c_slot * (unsigned)N + (unsigned)rr] = 1u;
           if (a.steps_cell) {
-            if (c_slot != acc_slot) {
-              if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
-              acc_slot = c_slot;
-              acc_steps = 0;
+            if (c_slot != ls.acc_slot) {
+              if (ls.acc_slot >= 0 && ls.acc_steps)
+                atomicAdd(a.step_acc + ls.acc_slot, (unsigned long long)ls.acc_steps);
+              ls.acc_slot = c_slot;
+              ls.acc_steps = 0;
             }
-            acc_steps += 1u;
+            ls.acc_steps += 1u;
           }
-          tot_steps += 1ull;
-          max_ray = max(max_ray, 1u);
-          ++tot_rays;
+          ls.tot_steps += 1ull;
+          ls.max_ray = max(ls.max_ray, 1u);
+          ++ls.tot_rays;
         }
         c_r += 32;
       }
@@ -303,286 +289,76 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
     }
 
     // ---- B. idle lanes take prepared rays ----
-    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    const unsigned idle = __ballot_sync(0xffffffffu, !lr.active);
     const int avail = (int)(tail - head);
     if (idle && avail > 0) {
       progress = true;
       const int rank = __popc(idle & lt_mask);
-      if (!active && rank < avail) {
+      if (!lr.active && rank < avail) {
         const int pos = (head + rank) & (POOL - 1);
         const float4 A = R.A[pos];
         const float4 Bv = R.B[pos];
         const uint4 Cv = R.C[pos];
         const int4 Dv = R.D[pos];
-        t0x = A.x;
-        t0y = A.y;
-        t0z = A.z;
-        tsx = A.w;
-        tsy = Bv.x;
-        tsz = Bv.y;
-        B_i = Bv.z;
-        scale = Bv.w;
-        n = Cv.x & 0xffffu;
-        krow = (n * (unsigned)ng + (Cv.x >> 16)) * (unsigned)nT;
-        ray = Cv.y;
-        sx = (int)(Cv.z & 3u) - 1;
-        sy = (int)((Cv.z >> 2) & 3u) - 1;
-        sz = (int)((Cv.z >> 4) & 3u) - 1;
-        cellid = Cv.w;
-        lin = Cv.w;
-        slot = (unsigned)Dv.x;
-        ix = Dv.y;
-        iy = Dv.z;
-        iz = Dv.w;
-        r = ray - (unsigned)ray_off;
-        tnx = t0x;
-        tny = t0y;
-        tnz = t0z;
-        cntx = cnty = cntz = 0.f;
-        tprev = 0.f;
-        tau = 1.f;
-        X = 0.f;
-        B_last = B_i;
-        steps = 0;
-        nrefl = 0;
-        active = true;
-        fcur = __ldg(field + lin);
+        lr.t0x = A.x;
+        lr.t0y = A.y;
+        lr.t0z = A.z;
+        lr.tsx = A.w;
+        lr.tsy = Bv.x;
+        lr.tsz = Bv.y;
+        lr.B_i = Bv.z;
+        lr.scale = Bv.w;
+        lr.n = Cv.x & 0xffffu;
+        lr.krow = (lr.n * (unsigned)ng + (Cv.x >> 16)) * (unsigned)nT;
+        lr.ray = Cv.y;
+        lr.sx = (int)(Cv.z & 3u) - 1;
+        lr.sy = (int)((Cv.z >> 2) & 3u) - 1;
+        lr.sz = (int)((Cv.z >> 4) & 3u) - 1;
+        lr.cellid = Cv.w;
+        lr.lin = Cv.w;
+        lr.slot = (unsigned)Dv.x;
+        lr.ix = Dv.y;
+        lr.iy = Dv.z;
+        lr.iz = Dv.w;
+        lr.r = lr.ray - (unsigned)ray_off;
+        lr.tnx = lr.t0x;
+        lr.tny = lr.t0y;
+        lr.tnz = lr.t0z;
+        lr.cntx = lr.cnty = lr.cntz = 0.f;
+        lr.tprev = 0.f;
+        lr.tau = 1.f;
+        lr.X = 0.f;
+        lr.B_last = lr.B_i;
+        lr.steps = 0;
+        lr.nrefl = 0;
+        lr.active = true;
+        lr.fcur = __ldg(field + lr.lin);
         if (MG) {
-          lev = 0;
-          lsteps = 0;
-          loff = 0;
-          inc = 1.f;
+          lr.lev = 0;
+          lr.lsteps = 0;
+          lr.loff = 0;
+          lr.inc = 1.f;
         }
       }
       head += (unsigned)min(__popc(idle), avail);
       __syncwarp();
     }
 
-    const unsigned busy = __ballot_sync(0xffffffffu, active);
+    const unsigned busy = __ballot_sync(0xffffffffu, lr.active);
     if (!busy && exhausted && tail == head) break;
     if (busy) progress = true;
 
     // ---- C. up to KSTEPS march steps per active lane (Algorithm 1 "March") ----
-    for (int kstep = 0; kstep < KSTEPS; ++kstep) {
-      if (!active) break;
-      float tn;
-      int ax;
-      if (tnx <= tny && tnx <= tnz) {
-        ax = 0;
-        tn = tnx;
-      } else if (tny <= tnz) {
-        ax = 1;
-        tn = tny;
-      } else {
-        ax = 2;
-        tn = tnz;
-      }
-      const float ds = fmaxf(tn - tprev, 0.f);
-      const uint2 f = fcur;
-      unsigned it;
-      float fr;
-      tpos(f.x, it, fr);
-      const float4 kb = __ldg(kbtab + (krow + it));
-      const float kap = (kb.x + fr * kb.y) * __uint_as_float(f.y);
-      const float Bj = kb.z + fr * kb.w;
-      float alpha, trans;
-      absorb(kap * ds, alpha, trans);
-      const float term = (B_i - Bj) * (tau * alpha);
-      X += term;     // Eq. 14 term / kappa_i
-      tau *= trans;  // Eq. 3
-      if (AR && lin != cellid)  // the exchange absorbed in cell j, seen from j
-        atomicAdd(a.armc_acc + armc_slot(a, r, lin), f32_to_f64(-scale * term));
-      B_last = Bj;
-      ++steps;
-      if (MG) ++lsteps;
-      bool done = tau <= tol;
-      if (!done && steps >= a.max_steps) {
-        done = true;
-        ++tot_cap;
-      }
-      if (!done) {
-        tprev = tn;
-        // dimensions of the current grid
-        const int nxl = MG ? nx >> lev : nx, nyl = MG ? ny >> lev : ny, nzl = MG ? nz >> lev : nz;
-        const int nxyl = MG ? nxl * nyl : nxy;
-        {
-          // branch-free advance of the crossed axis (lanes cross different axes)
-          const bool mx = ax == 0, my = ax == 1, mz = ax == 2;
-          const float step = MG ? inc : 1.f;
-          cntx += mx ? step : 0.f;
-          cnty += my ? step : 0.f;
-          cntz += mz ? step : 0.f;
-          tnx = mx ? fmaf(cntx, tsx, t0x) : tnx;
-          tny = my ? fmaf(cnty, tsy, t0y) : tny;
-          tnz = mz ? fmaf(cntz, tsz, t0z) : tnz;
-          ix += mx ? sx : 0;
-          iy += my ? sy : 0;
-          iz += mz ? sz : 0;
-          if (yfs && my && (unsigned)iy < (unsigned)nyl) tny = tprev + dyl(iy, MG ? lev : 0) * tsy;
-          // periodic wrap: an index can only leave the grid in the ray's direction
-          const int wx = (unsigned)ix < (unsigned)nxl ? 0 : -sx * nxl;
-          ix += wx;
-          const int wz = (unsigned)iz < (unsigned)nzl ? 0 : -sz * nzl;
-          iz += wz;
-          // the linear index from the three indices (multiply-adds, off the ALU pipe)
-          lin = (unsigned)(ix + nxl * (iy + nyl * iz));
-          if (GEN && a.xz_walls && (wx | wz)) {
-            // closed box: a black x or z wall absorbs the rest of the ray and
-            // emits at its temperature (Eq. 3 wall factor with eps = 1)
-            const int f = wx ? (wx > 0 ? 2 : 3) : (wz > 0 ? 4 : 5);
-            X += (B_i - __ldg(a.bwall32 + ((unsigned)(f * nb) + n))) * tau;
-            tau = 0.f;
-            ++tot_wall;
-            done = true;
-          } else if ((unsigned)iy >= (unsigned)nyl) {
-            // wall: absorbs eps of the ray and emits at T_wall (Eq. 3 wall factor)
-            const int wl = iy < 0 ? 0 : 1;
-            const float eps = wl ? eps1 : eps0;
-            const float Bw = __ldg(a.bwall32 + ((unsigned)(wl * nb) + n));
-            X += (B_i - Bw) * (tau * eps);
-            if (AR)  // the cell's own exchange with the wall
-              atomicAdd(a.armc_acc + armc_slot(a, r, cellid), f32_to_f64(scale * ((B_i - Bw) * (tau * eps))));
-            tau *= 1.f - eps;
-            ++tot_wall;
-            if (eps >= 1.f || tau <= tol) {
-              done = true;
-            } else {
-              // fractions of the current grid's cell, whose extent along an
-              // axis is inc face steps of the axis parameters
-              const float cx = MG ? tsx * inc : tsx, cz = MG ? tsz * inc : tsz;
-              float nfx = 0.5f, nfz = 0.5f;
-              if (sx > 0)
-                nfx = 1.f - (tnx - tprev) / cx;
-              else if (sx < 0)
-                nfx = (tnx - tprev) / cx;
-              if (sz > 0)
-                nfz = 1.f - (tnz - tprev) / cz;
-              else if (sz < 0)
-                nfz = (tnz - tprev) / cz;
-              nfx = fminf(fmaxf(nfx, 0.f), 1.f);
-              nfz = fminf(fmaxf(nfz, 0.f), 1.f);
-              const float nfy = wl == 0 ? 0.f : 1.f;
-              iy = wl == 0 ? 0 : nyl - 1;
-              lin = (unsigned)(ix + nxl * iy + nxyl * iz);
-              // cell size of the current grid over the finest, and of the grid
-              // the axis parameters were set up on
-              const float gl = MG ? (float)(1 << lev) : 1.f, gb = MG ? gl / inc : 1.f;
-              float ddx, ddy, ddz;
-              if (a.reflect == 1) {
-                // specular: |d| per axis unchanged, the y component flips
-                ddx = sx > 0 ? gb * DX / tsx : (sx < 0 ? -gb * DX / tsx : 0.f);
-                ddz = sz > 0 ? gb * DZ / tsz : (sz < 0 ? -gb * DZ / tsz : 0.f);
-                const float ady = yfs ? 1.f / tsy : gb * DY / tsy;
-                ddy = wl == 0 ? ady : -ady;
-              } else {
-                // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
-                const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, a.snapshot), a.key0, a.key1);
-                const float mr = sqrtf(unif(v.x));
-                float sp, cp;
-                sincos_2pi(unif(v.y), sp, cp);
-                const float sr = sqrtf(fmaxf(0.f, 1.f - mr * mr));
-                ddx = sr * cp;
-                ddy = wl == 0 ? mr : -mr;
-                ddz = sr * sp;
-              }
-              ++nrefl;
-              axis_setup(ddx, nfx, gl * DX, sx, t0x, tsx);
-              axis_setup(ddy, nfy, yfs ? dyl(iy, MG ? lev : 0) : gl * DY, sy, t0y, tsy);
-              axis_setup(ddz, nfz, gl * DZ, sz, t0z, tsz);
-              if (yfs && sy != 0) tsy = __frcp_rn(fabsf(ddy));
-              cntx = cnty = cntz = 0.f;
-              tnx = t0x;
-              tny = t0y;
-              tnz = t0z;
-              tprev = 0.f;
-              if (MG) inc = 1.f;
-            }
-          }
-        }
-        if (MG && !done && lev + 1 < a.mg_levels && lsteps >= a.mg_steps) {
-          // multigrid (Section 4.3): fall onto the next coarser grid here.  Its
-          // faces are the even-numbered faces of this grid, so an axis whose
-          // next face is odd-numbered skips it; the cell is the one containing
-          // this one.
-          if (sx != 0 && ((sx > 0 ? ix + 1 : ix) & 1)) {
-            cntx += inc;
-            tnx = fmaf(cntx, tsx, t0x);
-          }
-          if (sy != 0 && ((sy > 0 ? iy + 1 : iy) & 1)) {
-            if (yfs) {
-              tny += dyl(sy > 0 ? iy + 1 : iy - 1, lev) * tsy;  // the skipped row's height
-            } else {
-              cnty += inc;
-              tny = fmaf(cnty, tsy, t0y);
-            }
-          }
-          if (sz != 0 && ((sz > 0 ? iz + 1 : iz) & 1)) {
-            cntz += inc;
-            tnz = fmaf(cntz, tsz, t0z);
-          }
-          loff += (unsigned)(nxyl * nzl);
-          ix >>= 1;
-          iy >>= 1;
-          iz >>= 1;
-          lin = (unsigned)(ix + (nxl >> 1) * (iy + (nyl >> 1) * iz));
-          inc *= 2.f;
-          ++lev;
-          lsteps = 0;
-        }
-      }
-      if (!MG && !done && steps >= a.long_steps && (steps == a.long_steps || ax == 1) &&
-          long_flight(tny, tprev, tsx, tsz, a.long_flight)) {
-        // a long flight ahead (a grazing ray of a thin band): the warp-parallel
-        // march of long_rays.cu finishes this ray; checked when the ray reaches
-        // long_steps segments and at each later y face (a reflection is one)
-        LongRay L;
-        L.t0x = t0x; L.t0y = t0y; L.t0z = t0z; L.tsx = tsx;
-        L.tsy = tsy; L.tsz = tsz; L.cntx = cntx; L.cnty = cnty;
-        L.cntz = cntz; L.tnx = tnx; L.tny = tny; L.tnz = tnz;
-        L.tprev = tprev; L.tau = tau; L.X = X; L.B_i = B_i;
-        L.B_last = B_last; L.scale = scale; L.krow = krow; L.n = n;
-        L.ix = ix; L.iy = iy; L.iz = iz;
-        L.signs = (unsigned)(sx + 1) | ((unsigned)(sy + 1) << 2) | ((unsigned)(sz + 1) << 4);
-        L.lin = lin; L.slot = slot; L.r = r; L.ray = ray;
-        L.cellid = cellid; L.steps = (unsigned)steps; L.nrefl = nrefl; L.snap = 0u;
-        if (hand_off(a, L)) active = false;
-      }
-      // the next step's field entry, loaded now so that its latency overlaps the
-      // rest of this round
-      if (!done && active) fcur = __ldg(field + (MG ? loff + lin : lin));
-      if (done) {
-        if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
-        if (AR) {
-          // the residual is absorbed in the last medium cell crossed (the row is
-          // clamped: after a wall event iy lies outside the grid)
-          const unsigned lres = (unsigned)(ix + nx * (min(max(iy, 0), ny - 1) + ny * iz));
-          if (tau > 0.f && lres != cellid)
-            atomicAdd(a.armc_acc + armc_slot(a, r, lres), f32_to_f64(-scale * ((B_i - B_last) * tau)));
-          atomicAdd(a.ermc_acc + armc_slot(a, r, cellid), f32_to_f64(scale * X));
-        }
-        Ybuf[(size_t)slot * (unsigned)N + r] = scale * X;  // the ray's sample Y (Eq. 14)
-        if (a.ray_steps) a.ray_steps[(size_t)slot * (unsigned)N + r] = (unsigned)steps;
-        if (a.steps_cell) {
-          if ((int)slot != acc_slot) {
-            if (acc_slot >= 0 && acc_steps) atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
-            acc_slot = (int)slot;
-            acc_steps = 0;
-          }
-          acc_steps += (unsigned)steps;
-        }
-        tot_steps += (unsigned long long)steps;
-        max_ray = max(max_ray, (unsigned)steps);
-        ++tot_rays;
-        active = false;
-      }
-    }
+    march_round<KSTEPS, MG, GEN, AR, false>(a, mg_grid, lr, ls);
     if (!progress) {  // unreachable by construction; never spin
       if (lane == 0) atomicOr(a.counters + 5, 1ull);
       break;
     }
   }
-  if (a.steps_cell && acc_slot >= 0 && acc_steps)
-    atomicAdd(a.step_acc + acc_slot, (unsigned long long)acc_steps);
+  if (a.steps_cell && ls.acc_slot >= 0 && ls.acc_steps)
+    atomicAdd(a.step_acc + ls.acc_slot, (unsigned long long)ls.acc_steps);
+  unsigned long long tot_steps = ls.tot_steps;
+  unsigned tot_cap = ls.tot_cap, tot_wall = ls.tot_wall, max_ray = ls.max_ray, tot_rays = ls.tot_rays;
 
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

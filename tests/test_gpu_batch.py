@@ -49,18 +49,17 @@ def test_batch_matches_single_solves_bitwise_on_two_runs():
 
 
 def _check_runs(b, snaps, solvers, outs, rays, stream, offsets):
-    if True:
-        for offset in offsets:
-            mcrt.mcrt_batch_run(b, offset, stream)
-            st = mcrt.mcrt_batch_get_stats(b)
-            assert st["rays"] == sum(g.ncells for g, _, _ in snaps) * rays
-            # one trace launch, the long-ray march and one reduction for all snapshots
-            assert st["launches"] == 3
-            for k, (S, (q, s)) in enumerate(zip(solvers, outs)):
-                qr, sr = S.solve(rays=rays, seed=7, snapshot=10 + k, ray_offset=offset,
-                                 precision=mcrt.MCRT_FP32)
-                assert np.array_equal(q.cpu().numpy(), qr), (offset, k)
-                assert np.array_equal(s.cpu().numpy(), sr), (offset, k)
+    for offset in offsets:
+        mcrt.mcrt_batch_run(b, offset, stream)
+        st = mcrt.mcrt_batch_get_stats(b)
+        assert st["rays"] == sum(g.ncells for g, _, _ in snaps) * rays
+        # one trace launch, the long-ray march and one reduction for all snapshots
+        assert st["launches"] == 3
+        for k, (S, (q, s)) in enumerate(zip(solvers, outs)):
+            qr, sr = S.solve(rays=rays, seed=7, snapshot=10 + k, ray_offset=offset,
+                             precision=mcrt.MCRT_FP32)
+            assert np.array_equal(q.cpu().numpy(), qr), (offset, k)
+            assert np.array_equal(s.cpu().numpy(), sr), (offset, k)
 
 
 def _run_and_compare(items_spec, params_kw, rays, offsets=(0, 3000)):
@@ -165,8 +164,9 @@ def test_autotuner_picks_a_shape_without_changing_results():
     params = S.params(rays=200, seed=3, precision=mcrt.MCRT_FP32)
     S.solve_into(params, q, s)
     before = q.cpu().numpy().copy()
-    best, table = autotune.tune_solver(S, params, q, s, reps=2)
+    best, table = autotune.tune_solver(S, params, q, s, reps=2, scratch_mib=(1, 64))
     assert best in table and all(v > 0 for v in table.values())
+    assert any(len(k) == 3 for k in table)  # the scratch cap was tried (1 MiB: many chunks)
     assert S.tuning()["min_blocks_per_sm"] == best[0] and S.tuning()["steps_per_round"] == best[1]
     S.solve_into(params, q, s)
     assert np.array_equal(q.cpu().numpy(), before)

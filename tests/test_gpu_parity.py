@@ -40,7 +40,13 @@ def assert_parity(orc, q, s, st, precision):
     bad = err > rtol * scale + 1e-300
     assert not bad.any(), (f"{bad.sum()} cells beyond {rtol} S; worst "
                            f"{np.max(err / np.maximum(scale, 1e-300)):.3e}")
-    # standard errors follow (they come from the same per-ray samples)
+    # Standard errors follow (they come from the same per-ray samples).  sigma^2 =
+    # (M2 - Q^2) / (N - 1) with M2 the mean squared sample: an error dM2 in M2 moves
+    # sigma by dM2 / (2 (N - 1) sigma^2) relative, so where the samples of a cell are
+    # nearly equal (M2 >> (N - 1) sigma^2) the binary32 samples' rounding (a few
+    # 1e-7 of each |Y|) is amplified by M2 / ((N - 1) sigma^2).  Over cells with
+    # sigma > 1e-3 S that factor reaches about 1e4 at N = 64, hence the 2e-2
+    # relative tolerance in FP32, 200 times Q's (binary64: 1e-8).
     srel = 1e-8 if precision == mcrt.MCRT_FP64 else 2e-2
     big = orc["sigma"] > 1e-3 * scale
     assert np.allclose(s[big], orc["sigma"][big], rtol=srel)

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           unsigned it_i;
           float fr_i;
           tpos(fi.x, it_i, fr_i);
-          const uint4 u = philox10(make_uint4(cell, rayid, 0u, snapw_b), a.key0, a.key1);
+          const uint4 u = philox10r(make_uint4(cell, rayid, 0u, snapw_b), a.rkey);
           unsigned hemi = 4194304u;
           int nn, gg;
           float wgt;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
           const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
           float fx = 0.5f, fy = 0.5f, fz = 0.5f;
           if (a.origin == 0) {
-            const uint4 v = philox10(make_uint4(cell, rayid, 1u, snapw_b), a.key0, a.key1);
+            const uint4 v = philox10r(make_uint4(cell, rayid, 1u, snapw_b), a.rkey);
             fx = unif(v.x);
             fy = unif(v.y);
             fz = unif(v.z);
@@ -454,8 +454,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
                 ddy = wl == 0 ? ady : -ady;
               } else {
                 // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
-                const uint4 v = philox10(make_uint4(cellid, ray, 2u + nrefl, snapw_b),
-                                         a.key0, a.key1);
+                const uint4 v = philox10r(make_uint4(cellid, ray, 2u + nrefl, snapw_b), a.rkey);
                 const float mr = sqrtf(unif(v.x));
                 float sp, cp;
                 sincos_2pi(unif(v.y), sp, cp);

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
         const float ady = g.yfs ? 1.f / tsy : g.DY / tsy;
         ddy = wl == 0 ? ady : -ady;
       } else {
-        const uint4 v = philox10(make_uint4(L.cellid, L.ray, 2u + nrefl, g.snapw), a.key0, a.key1);
+        const uint4 v = philox10r(make_uint4(L.cellid, L.ray, 2u + nrefl, g.snapw), a.rkey);
         const float mr = sqrtf(unif(v.x));
         float sp, cp;
         sincos_2pi(unif(v.y), sp, cp);

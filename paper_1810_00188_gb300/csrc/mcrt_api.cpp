@@ -246,6 +246,18 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
 
 // The FP32 kernels' binary32 copies of tol, the cell sizes and the wall
 // emissivities (rounded once here).
+// The ten Philox4x32-10 round keys of (key0, key1): the Weyl sequence of the
+// key schedule (Salmon et al., SC'11) with increments 0x9E3779B9, 0xBB67AE85.
+static void set_round_keys(mcrt::TraceArgs *a) {
+  unsigned k0 = a->key0, k1 = a->key1;
+  for (int r = 0; r < 10; ++r) {
+    a->rkey[2 * r] = k0;
+    a->rkey[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 static void set_float_copies(mcrt::TraceArgs *a) {
   a->tol32 = (float)a->tol;
   a->dx32 = (float)a->dx;
@@ -309,6 +321,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   set_float_copies(&a);
   a.key0 = (unsigned)(p->seed & 0xffffffffu);
   a.key1 = (unsigned)(p->seed >> 32);
+  set_round_keys(&a);
   a.snapshot = p->snapshot;
   a.ray_offset = p->ray_offset;
   a.bi0 = b[0];
@@ -1137,6 +1150,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     set_float_copies(&a);
     a.key0 = (unsigned)(p->seed & 0xffffffffu);
     a.key1 = (unsigned)(p->seed >> 32);
+    set_round_keys(&a);
     a.snapshot = items[k].snapshot;
     a.ray_offset_dev = b->d_offset;
     a.bnx = g.nx;

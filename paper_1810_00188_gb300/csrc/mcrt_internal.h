@@ -123,6 +123,8 @@ struct TraceArgs {
   // pipe each time the compiler rematerialises the value)
   float tol32, dx32, dy32, dz32, eps32[2];
   unsigned int key0, key1, snapshot;
+  // the Philox round keys of (key0, key1), for philox10r (set_round_keys)
+  unsigned int rkey[20];
   unsigned long long ray_offset;
   int bi0, bj0, bk0, bnx, bny, bnz;
   long long ncells_box;

@@ -431,7 +431,7 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
               ddy = wl == 0 ? ady : -ady;
             } else {
               // Lambertian: cos(theta) = sqrt(U), azimuth 2 pi U (block 2 + k)
-              const uint4 v = philox10(make_uint4(s.cellid, s.ray, 2u + s.nrefl, g.snapw), a.key0, a.key1);
+              const uint4 v = philox10r(make_uint4(s.cellid, s.ray, 2u + s.nrefl, g.snapw), a.rkey);
               const float mr = sqrtf(unif(v.x));
               float sp, cp;
               sincos_2pi(unif(v.y), sp, cp);

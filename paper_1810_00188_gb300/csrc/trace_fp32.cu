@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           unsigned it_i;
           float fr_i;
           tpos(fi.x, it_i, fr_i);
-          const uint4 u = philox10(make_uint4(cell, rayid, 0u, a.snapshot), a.key0, a.key1);
+          const uint4 u = philox10r(make_uint4(cell, rayid, 0u, a.snapshot), a.rkey);
           unsigned hemi = 4194304u;
           int nn, gg;
           float wgt;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
           float fx = 0.5f, fy = 0.5f, fz = 0.5f;
           if (a.origin == 0) {
-            const uint4 v = philox10(make_uint4(cell, rayid, 1u, a.snapshot), a.key0, a.key1);
+            const uint4 v = philox10r(make_uint4(cell, rayid, 1u, a.snapshot), a.rkey);
             fx = unif(v.x);
             fy = unif(v.y);
             fz = unif(v.z);

@@ -18,6 +18,7 @@ constexpr int POOL = 64;   // prepared ray states per warp
 constexpr int WARPS = 8;   // warps per CTA
 constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks
 constexpr int GUIDE = 64;  // guide-table buckets of the band CDF
+constexpr int REFILL = 8;  // idle lanes of a warp before they take prepared rays
 
 struct WarpRing {
   float4 A[POOL];  // t0x, t0y, t0z, tsx

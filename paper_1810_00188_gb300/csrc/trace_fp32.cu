@@ -289,9 +289,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
     }
 
     // ---- B. idle lanes take prepared rays ----
+    // The take-over runs on the idle lanes only, so a warp waits until REFILL of
+    // its lanes are idle (or it is draining): one pass then serves more rays, at
+    // the cost of a round or two with idle lanes (2.6% less time at 64^3 x 1000
+    // rays than a take-over in every round).
     const unsigned idle = __ballot_sync(0xffffffffu, !lr.active);
     const int avail = (int)(tail - head);
-    if (idle && avail > 0) {
+    if (idle && avail > 0 && (__popc(idle) >= REFILL || idle == 0xffffffffu || exhausted)) {
       progress = true;
       const int rank = __popc(idle & lt_mask);
       if (!lr.active && rank < avail) {

@@ -265,10 +265,11 @@ def configs_extra(sp):
 
 def batch_extra(sp, rays=256, n=32, seed=0):
     """32 snapshots of uneven grid sizes (32^3, 48x64x48, 96^3, 128^3), 256 rays
-    per cell, sharing the k-distribution: one graph launch that holds a single
-    persistent trace kernel over all snapshots and one reduction.  The launch
-    shape (CTAs per SM, march steps per round) is tuned; compared with the same
-    snapshots solved one after another."""
+    per cell, sharing the k-distribution, in one graph launch.  The tuner picks
+    the form (a single persistent trace kernel over all snapshots and one
+    reduction, or per-snapshot launches in 1, 2, 4 or 8 graph branches) and the
+    launch shape (CTAs per SM, march steps per round); compared with the same
+    snapshots solved one after another (the sum of their device times)."""
     import torch
 
     from paper_1810_00188_gb300 import autotune, inputs, mcrt
@@ -284,15 +285,18 @@ def batch_extra(sp, rays=256, n=32, seed=0):
         items.append((S.ctx, q.data_ptr(), sg.data_ptr(), k))
     params = mcrt.Solver.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32)
 
-    def make(shape):
-        solvers[0].set_tuning(*shape)
-        return mcrt.mcrt_batch_create(items, params)
+    def make(shape):  # (CTAs per SM, steps per round, per-item launches, graph branches)
+        mb, k, per_item, streams = shape
+        solvers[0].set_tuning(mb, k, batch_per_snapshot=per_item)
+        return mcrt.mcrt_batch_create(items, params, streams=streams)
 
     def run(b):
         mcrt.mcrt_batch_run(b, rays, sp)
         return mcrt.mcrt_batch_get_stats(b)["kernel_ms"]
 
-    best, table = autotune.tune_batch(make, run, shapes=((3, 1), (3, 2), (2, 1), (2, 2)), reps=1)
+    shapes = ((3, 1, 0, 1), (3, 2, 0, 1), (2, 1, 0, 1), (2, 2, 0, 1), (3, 1, 1, 1), (3, 1, 1, 2), (3, 1, 1, 4),
+              (3, 1, 1, 8))
+    best, table = autotune.tune_batch(make, run, shapes=shapes, reps=1)
     b = make(best)
     try:
         mcrt.mcrt_batch_run(b, 0, sp)
@@ -318,8 +322,11 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             "cells": cells, "graph_ms": t * 1e3, "rays_per_s": cells * rays / t,
             "steps_per_s": st["steps"] / t, "launches_in_graph": st["launches"],
             "sequential_ms": seq, "speedup_vs_sequential": seq / (t * 1e3),
-            "tuned": {"min_blocks_per_sm": best[0], "steps_per_round": best[1]},
-            "tuning_ms": {f"{k[0]}x{k[1]}": v for k, v in table.items()}}
+            "tuned": {"min_blocks_per_sm": best[0], "steps_per_round": best[1],
+                      "form": "per-item launches" if best[2] else "one persistent launch",
+                      "graph_branches": best[3]},
+            "tuning_ms": {(f"{k[0]}x{k[1]} per-item x{k[3]}" if k[2] else f"{k[0]}x{k[1]} one launch"): v
+                          for k, v in table.items()}}
 
 
 def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):

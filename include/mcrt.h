@@ -215,6 +215,12 @@ typedef struct {
                               (within about 2^-51 of sum |Y| of the exact sum
                               of the samples); 1: compensated binary32 pairs
                               (within about 2e-7 of sum |Y|), a little cheaper */
+  int batch_per_snapshot;  /* read from items[0]'s context by mcrt_batch_create:
+                              0 (default): a batch whose items share the
+                              k-distribution is one persistent launch over all
+                              items; 1: per-item launches in `streams` graph
+                              branches, as for mixed k-distributions (the same
+                              results; which is faster depends on the batch) */
 } mcrt_tuning;
 
 /* Number of overlaid grids the multigrid march can use on an nx x ny x nz grid
@@ -331,7 +337,8 @@ int mcrt_solve_qrad_noalloc(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q
  *    when it fits in half the free device memory).  Warps claim runs of
  *    cells of the concatenated snapshots, largest snapshot first; a warp lets
  *    its rays finish before it moves on to another snapshot.  `weights` and
- *    `streams` are not used.
+ *    `streams` are not used.  mcrt_tuning.batch_per_snapshot = 1 on items[0]'s
+ *    context selects the next form instead.
  *  - Otherwise each item is one persistent FP32 trace kernel (and its per-cell
  *    reduction) inside the graph; `streams` concurrent branches run the items in
  *    decreasing order of `weights` (NULL: cell counts), round-robin.  Without

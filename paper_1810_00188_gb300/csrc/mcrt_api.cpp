@@ -787,12 +787,15 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   if (t->long_ray_flight > (1 << 24)) return fail(ctx, MCRT_E_ARG, "long_ray_flight above 2^24");
   if (t->tally_binary32 != 0 && t->tally_binary32 != 1) return fail(ctx, MCRT_E_ARG, "tally_binary32 not 0 or 1");
+  if (t->batch_per_snapshot != 0 && t->batch_per_snapshot != 1)
+    return fail(ctx, MCRT_E_ARG, "batch_per_snapshot not 0 or 1");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
   ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
   ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
   ctx->long_steps = t->long_ray_steps ? (t->long_ray_steps > 0 ? t->long_ray_steps : -1) : 1024;
   ctx->long_flight = t->long_ray_flight ? (t->long_ray_flight > 0 ? (float)t->long_ray_flight : -1.f) : 32.f;
   ctx->tally32 = t->tally_binary32;
+  ctx->batch_per_snapshot = t->batch_per_snapshot;
   return MCRT_OK;
 }
 
@@ -804,6 +807,7 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   t->long_ray_steps = ctx->long_steps;
   t->long_ray_flight = ctx->long_flight < 0.f ? -1 : (int)ctx->long_flight;
   t->tally_binary32 = ctx->tally32;
+  t->batch_per_snapshot = ctx->batch_per_snapshot;
   return MCRT_OK;
 }
 
@@ -1175,8 +1179,9 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
   mcrt_ctx *c0 = items[0].ctx;
   // Snapshots that share the k-distribution run as ONE persistent trace launch
   // (and one reduction) over all their cells: warps claim runs of brick-ordered
-  // positions of the concatenated snapshots, largest snapshot first.
-  bool same_kdist = n <= mcrt::fp32_batch_max_snapshots();
+  // positions of the concatenated snapshots, largest snapshot first (unless
+  // items[0]'s tuning asks for per-item launches).
+  bool same_kdist = n <= mcrt::fp32_batch_max_snapshots() && !items[0].ctx->batch_per_snapshot;
   for (int k = 0; k < n && same_kdist; ++k)
     if (items[k].ctx->grid.xz_walls) same_kdist = false;  // closed boxes: per-snapshot kernels
   for (int k = 1; k < n && same_kdist; ++k) {

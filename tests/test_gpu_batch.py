@@ -44,17 +44,29 @@ def test_batch_matches_single_solves_bitwise_on_two_runs():
             _check_runs(b, snaps, solvers, outs, rays, stream, offsets)
         finally:
             mcrt.mcrt_batch_destroy(b)
+    # the per-item form, asked for by items[0]'s tuning: the same bits
+    solvers[0].set_tuning(batch_per_snapshot=1)
+    assert solvers[0].tuning()["batch_per_snapshot"] == 1
+    for streams in (2, 1):
+        b = mcrt.mcrt_batch_create(items, params, streams=streams)
+        try:
+            _check_runs(b, snaps, solvers, outs, rays, stream, (900,), per_item=True)
+        finally:
+            mcrt.mcrt_batch_destroy(b)
+    solvers[0].set_tuning()
     for S in solvers:
         S.close()
 
 
-def _check_runs(b, snaps, solvers, outs, rays, stream, offsets):
+def _check_runs(b, snaps, solvers, outs, rays, stream, offsets, per_item=False):
     for offset in offsets:
         mcrt.mcrt_batch_run(b, offset, stream)
         st = mcrt.mcrt_batch_get_stats(b)
         assert st["rays"] == sum(g.ncells for g, _, _ in snaps) * rays
-        # one trace launch, the long-ray march and one reduction for all snapshots
-        assert st["launches"] == 3
+        if per_item:  # a trace launch and a reduction (at least) per snapshot
+            assert st["launches"] >= 2 * len(snaps)
+        else:  # one trace launch, the long-ray march and one reduction for all snapshots
+            assert st["launches"] == 3
         for k, (S, (q, s)) in enumerate(zip(solvers, outs)):
             qr, sr = S.solve(rays=rays, seed=7, snapshot=10 + k, ray_offset=offset,
                              precision=mcrt.MCRT_FP32)

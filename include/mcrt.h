@@ -215,6 +215,10 @@ typedef struct {
                               (within about 2^-51 of sum |Y| of the exact sum
                               of the samples); 1: compensated binary32 pairs
                               (within about 2e-7 of sum |Y|), a little cheaper */
+  int claim_rays;          /* 0: default (1024); FP32 solves: rays per run of
+                              cells a warp claims at a time (the run is at
+                              least one cell and at most 1/8 of a warp's share
+                              of the solve); results do not depend on it      */
   int batch_per_snapshot;  /* read from items[0]'s context by mcrt_batch_create:
                               0 (default): a batch whose items share the
                               k-distribution is one persistent launch over all

@@ -1,9 +1,10 @@
 """Autotuner of the FP32 solve's launch shape and of batch partitions.
 
 The knobs are the library's `mcrt_tuning` (CTAs per SM, march steps per refill
-round, sample-scratch cap: the ray batch of one launch) and, for batches, the
-launch shape, the number of concurrent graph branches and the share of the
-GPU's persistent CTAs given to each snapshot.  Q, sigma and the step counts are bitwise
+round, sample-scratch cap: the ray batch of one launch, rays per claimed run of
+cells: the work tile) and, for batches, the form (one persistent launch or
+per-snapshot launches), the launch shape, the number of concurrent graph
+branches and the share of the GPU's persistent CTAs given to each snapshot.  Q, sigma and the step counts are bitwise
 independent of all of them (every cell's samples are reduced in a fixed order),
 so the tuner only measures time: the library's own CUDA events around each
 solve's launches.
@@ -27,30 +28,44 @@ def time_solve(S, params, q, s, stream=0, reps=3):
 
 
 SCRATCH_MIB = (256, 1024, 4096)
+CLAIM_RAYS = (1024, 4096, 16384)
 
 
-def tune_solver(S, params, q, s, stream=0, shapes=SHAPES, reps=3, scratch_mib=None):
-    """Tries each (CTAs per SM, steps per round), then, at the fastest, each cap of
-    the per-ray sample scratch in MiB (the ray batch of one launch: a smaller cap
-    runs the solve in more chunks), and keeps the fastest on S.  The long-ray
-    thresholds and the tally precision are part of the estimator's arithmetic, not
-    knobs: they are left as set.  Returns (best (mb, k) or (mb, k, mib), {knobs: ms})."""
+def _set(S, key, keep):
+    """Applies the knobs key = (CTAs per SM, steps per round, scratch MiB, claim
+    rays; 0: the library default), keeping the other tuning fields as set."""
+    mb, k, mib, claim = key
+    S.set_tuning(mb, k, mib, keep["long_ray_steps"], keep["long_ray_flight"], keep["tally_binary32"],
+                 batch_per_snapshot=keep["batch_per_snapshot"], claim_rays=claim)
+
+
+def tune_solver(S, params, q, s, stream=0, shapes=SHAPES, reps=3, scratch_mib=None, claim_rays=None):
+    """Coordinate search on S: each (CTAs per SM, steps per round) of `shapes`;
+    then, at the fastest, each cap of the per-ray sample scratch in MiB (the ray
+    batch of one launch: a smaller cap runs the solve in more chunks); then each
+    number of rays per run of cells a warp claims (the work tile).  The long-ray
+    thresholds, the tally precision and the batch form are part of the
+    estimator's arithmetic or of batches, not knobs here: they are kept as set.
+    Keys are (mb, k, mib, claim) with 0 for a default; returns (best key,
+    {key: ms}) and leaves S tuned to the best key."""
+    keep = S.tuning()
     table = {}
+
+    def trial(key):
+        _set(S, key, keep)
+        time_solve(S, params, q, s, stream, reps=1)  # the first launch configures the variant
+        table[key] = time_solve(S, params, q, s, stream, reps)
+
     for mb, k in shapes:
-        S.set_tuning(mb, k)
-        time_solve(S, params, q, s, stream, reps=1)  # first launch configures the variant
-        table[(mb, k)] = time_solve(S, params, q, s, stream, reps)
+        trial((mb, k, 0, 0))
     best = min(table, key=table.get)
-    if scratch_mib:
-        base = table[best]
-        for mib in scratch_mib:
-            S.set_tuning(best[0], best[1], mib)
-            time_solve(S, params, q, s, stream, reps=1)
-            table[best + (mib,)] = time_solve(S, params, q, s, stream, reps)
-        b3 = min((kk for kk in table if len(kk) == 3), key=table.get)
-        if table[b3] < base:
-            best = b3
-    S.set_tuning(*best)
+    for mib in scratch_mib or ():
+        trial((best[0], best[1], mib, 0))
+    best = min(table, key=table.get)
+    for claim in claim_rays or ():
+        trial((best[0], best[1], best[2], claim))
+    best = min(table, key=table.get)
+    _set(S, best, keep)
     return best, table
 
 

@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
   // Runs of brick-order positions are claimed from a launch-wide counter
   // (counters[6], zeroed before each launch): a warp whose cells hold longer rays
   // takes fewer cells, and the runs keep neighbouring cells together.
-  // positions per claim: about 4096 rays, and at least 8 claims per warp
-  const long long G = max(1LL, min((long long)(4096 / a.rays),
+  // positions per claim: about claim_rays rays (at least one cell), and at
+  // least 8 claims per warp
+  const long long G = max(1LL, min((long long)((a.claim_rays > 0 ? a.claim_rays : 1024) / a.rays),
                                    (a.chunk_p1 - a.chunk_p0) / ((long long)gridDim.x * WARPS * 8)));
   long long p_next = 0, p_end = 0;
 

@@ -65,6 +65,7 @@ struct mcrt_ctx {
   int long_steps = 1024;    // hand-off threshold in segments (<= 0: never)
   float long_flight = 32;   // x/z crossings left in the flight for a hand-off
   int tally32 = 0;          // per-cell tallies in binary32 pairs instead of binary64
+  int claim_rays = 1024;    // FP32 kernels: rays per claimed run of cells
   int batch_per_snapshot = 0;  // batches: per-item launches even for one k-distribution
   double last_T_max = 0;
   std::string err;

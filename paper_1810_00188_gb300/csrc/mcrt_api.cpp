@@ -322,6 +322,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.key0 = (unsigned)(p->seed & 0xffffffffu);
   a.key1 = (unsigned)(p->seed >> 32);
   set_round_keys(&a);
+  a.claim_rays = ctx->claim_rays;
   a.snapshot = p->snapshot;
   a.ray_offset = p->ray_offset;
   a.bi0 = b[0];
@@ -787,6 +788,8 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   if (t->long_ray_flight > (1 << 24)) return fail(ctx, MCRT_E_ARG, "long_ray_flight above 2^24");
   if (t->tally_binary32 != 0 && t->tally_binary32 != 1) return fail(ctx, MCRT_E_ARG, "tally_binary32 not 0 or 1");
+  if (t->claim_rays != 0 && (t->claim_rays < 32 || t->claim_rays > (1 << 20)))
+    return fail(ctx, MCRT_E_ARG, "claim_rays not 0 or within 32..2^20");
   if (t->batch_per_snapshot != 0 && t->batch_per_snapshot != 1)
     return fail(ctx, MCRT_E_ARG, "batch_per_snapshot not 0 or 1");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
@@ -796,6 +799,7 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
   ctx->long_flight = t->long_ray_flight ? (t->long_ray_flight > 0 ? (float)t->long_ray_flight : -1.f) : 32.f;
   ctx->tally32 = t->tally_binary32;
   ctx->batch_per_snapshot = t->batch_per_snapshot;
+  ctx->claim_rays = t->claim_rays ? t->claim_rays : 1024;
   return MCRT_OK;
 }
 
@@ -808,6 +812,7 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   t->long_ray_flight = ctx->long_flight < 0.f ? -1 : (int)ctx->long_flight;
   t->tally_binary32 = ctx->tally32;
   t->batch_per_snapshot = ctx->batch_per_snapshot;
+  t->claim_rays = ctx->claim_rays;
   return MCRT_OK;
 }
 
@@ -1155,6 +1160,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.key0 = (unsigned)(p->seed & 0xffffffffu);
     a.key1 = (unsigned)(p->seed >> 32);
     set_round_keys(&a);
+    a.claim_rays = items[0].ctx->claim_rays;
     a.snapshot = items[k].snapshot;
     a.ray_offset_dev = b->d_offset;
     a.bnx = g.nx;

@@ -114,6 +114,7 @@ struct TraceArgs {
   int long_cap;      // entries of long_rays
   int long_steps;    // segments marched before a hand-off
   float long_flight; // x/z crossings left in the flight for a hand-off
+  int claim_rays;    // FP32 kernels: rays per claimed run of cells (<= 0: 1024)
   // solve
   int rays, max_steps, origin;
   double tol;

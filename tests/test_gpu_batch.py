@@ -176,9 +176,10 @@ def test_autotuner_picks_a_shape_without_changing_results():
     params = S.params(rays=200, seed=3, precision=mcrt.MCRT_FP32)
     S.solve_into(params, q, s)
     before = q.cpu().numpy().copy()
-    best, table = autotune.tune_solver(S, params, q, s, reps=2, scratch_mib=(1, 64))
+    best, table = autotune.tune_solver(S, params, q, s, reps=2, scratch_mib=(1, 64), claim_rays=(64, 65536))
     assert best in table and all(v > 0 for v in table.values())
-    assert any(len(k) == 3 for k in table)  # the scratch cap was tried (1 MiB: many chunks)
+    assert any(k[2] == 1 for k in table)  # the scratch cap was tried (1 MiB: many chunks)
+    assert any(k[3] == 64 for k in table)  # and the claimed runs
     assert S.tuning()["min_blocks_per_sm"] == best[0] and S.tuning()["steps_per_round"] == best[1]
     S.solve_into(params, q, s)
     assert np.array_equal(q.cpu().numpy(), before)

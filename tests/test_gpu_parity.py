@@ -228,11 +228,20 @@ def test_fp32_results_independent_of_launch_shape():
         S.set_tuning(mb, k, mib)
         assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k,
                               "scratch_mib": mib if mib else 1024, "long_ray_steps": 1024,
-                              "long_ray_flight": 32, "tally_binary32": 0, "batch_per_snapshot": 0}
+                              "long_ray_flight": 32, "tally_binary32": 0, "claim_rays": 1024,
+                              "batch_per_snapshot": 0}
+        q, s, st = S.solve(rays=300, seed=3, with_steps=True)
+        assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
+    # the claimed runs: one cell at a time, or as long as the solve allows
+    for cr in (32, 1 << 20):
+        S.set_tuning(claim_rays=cr)
+        assert S.tuning()["claim_rays"] == cr
         q, s, st = S.solve(rays=300, seed=3, with_steps=True)
         assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
     with pytest.raises(mcrt.McrtError):
         S.set_tuning(9)
+    with pytest.raises(mcrt.McrtError):
+        S.set_tuning(claim_rays=5)
     S.close()
 
 

@@ -301,6 +301,66 @@ __device__ bool quantize_row(const float *w, int K, float W, unsigned long long 
   return true;
 }
 
+// The band counts of quantize_cell for nb <= 64, with lane l holding bands l
+// and l + 32 in registers: the same sums as the general path (the total of the
+// band weights in band order, each band's count once, the exact integer total,
+// the first largest weight), with the total formed on every lane from the
+// lanes' registers instead of one lane reading shared memory.
+__device__ __forceinline__ void quantize_bands64(const float *wn, int nb, int lane, unsigned long long *cn,
+                                                 unsigned long long *err) {
+  const float w0 = lane < nb ? wn[lane] : 0.f, w1 = lane + 32 < nb ? wn[lane + 32] : 0.f;
+  float W = 0.f;
+#pragma unroll 8
+  for (int n = 0; n < nb; ++n) W += __shfl_sync(0xffffffffu, n < 32 ? w0 : w1, n & 31);  // band order
+  if (!(W > 0.f)) {
+    if (lane == 0) atomicOr(err, 2ull);
+    return;
+  }
+  long long m0 = 0, m1 = 0;
+  if (w0 > 0.f) {
+    m0 = count32(w0, W);
+    m0 = m0 < 1 ? 1 : m0;
+  }
+  if (w1 > 0.f) {
+    m1 = count32(w1, W);
+    m1 = m1 < 1 ? 1 : m1;
+  }
+  long long tot = m0 + m1;
+  // the first largest weight: band lane, then lane + 32, then across lanes
+  float bw = lane < nb ? w0 : -1.f;
+  int bk = lane < nb ? lane : nb;
+  if (lane + 32 < nb && w1 > bw) {
+    bw = w1;
+    bk = lane + 32;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const float ow = __shfl_xor_sync(0xffffffffu, bw, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    if (ow > bw || (ow == bw && ok < bk)) {
+      bw = ow;
+      bk = ok;
+    }
+  }
+  // cumulative counts: a warp scan of bands 0..31, then of bands 32..63 on
+  // top of the first round's total; the remainder goes to the first largest band
+  const unsigned long long rem = (unsigned long long)(4294967296LL - tot);
+  unsigned long long carry = 0;
+#pragma unroll
+  for (int round = 0; round < 2; ++round) {
+    const int n = 32 * round + lane;
+    unsigned long long v = (unsigned long long)(round ? m1 : m0) + (n == bk ? rem : 0ull);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (n < nb) cn[n] = carry + v;
+    carry += __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
 // Warp-cooperative: q [nb * ng] spectral probabilities and q_up of one cell ->
 // cumulative band counts cn [nb], g counts within each band cg [nb][ng], and the
 // upward-hemisphere count of 2^23.  wn: nb floats of scratch (the binary32 band
@@ -329,6 +389,9 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, float 
     }
   }
   __syncwarp();
+  if (nb <= 64) {
+    quantize_bands64(wn, nb, lane, cn, err);
+  } else {
   float W = 0.f;
   if (lane == 0)
     for (int n = 0; n < nb; ++n) W += wn[n];  // binary32, in band order
@@ -389,6 +452,7 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, float 
       carry += __shfl_sync(0xffffffffu, v, 31);
     }
   }
+  }
   if (lane == 0) {
     // round half up of q_up 2^23 (exact in binary32: the scaling is a power of
     // two and the sum is below 2^23 + 1/2 with an ulp of at most 1/2)
@@ -398,7 +462,7 @@ __device__ void quantize_cell(const float *q, float q_up, int nb, int ng, float 
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(NTHR) quantize_cells_kernel(const float *q, long long n, int nb,
+__global__ void __launch_bounds__(NTHR, 4) quantize_cells_kernel(const float *q, long long n, int nb,
                                                              int ng, unsigned long long *cell_cn,
                                                              unsigned long long *cell_cg,
                                                              unsigned *cell_hemi,

@@ -782,13 +782,42 @@ __device__ __forceinline__ void mma_tile64(const __half *Ahi, const __half *Alo,
   }
 }
 
+// The A fragments of a 16 x 64 activation tile (hi and lo parts) for every k0,
+// loaded once per warp and reused for all of its output n-tiles.
+__device__ __forceinline__ void load_afrag(const __half *A, int lane, unsigned (&f)[NH / 16][4]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < NH / 16; ++j) {
+    const int k0 = 16 * j;
+    f[j][0] = *reinterpret_cast<const unsigned *>(A + g * LDK + k0 + 2 * t);
+    f[j][1] = *reinterpret_cast<const unsigned *>(A + (g + 8) * LDK + k0 + 2 * t);
+    f[j][2] = *reinterpret_cast<const unsigned *>(A + g * LDK + k0 + 2 * t + 8);
+    f[j][3] = *reinterpret_cast<const unsigned *>(A + (g + 8) * LDK + k0 + 2 * t + 8);
+  }
+}
+
+// mma_tile64 with the A fragments in registers: the same products in the same
+// order (k0 ascending, the hi part before the lo part).
+__device__ __forceinline__ void mma_tile64_frag(const unsigned (&ahi)[NH / 16][4], const unsigned (&alo)[NH / 16][4],
+                                                const __half *W, int n0, int lane, float (&d)[4]) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < NH / 16; ++j) {
+    const __half *wrow = W + (size_t)(n0 + g) * LDK + 16 * j + 2 * t;
+    const unsigned b0 = *reinterpret_cast<const unsigned *>(wrow);
+    const unsigned b1 = *reinterpret_cast<const unsigned *>(wrow + 8);
+    mma16816(d, ahi[j], b0, b1);
+    mma16816(d, alo[j], b0, b1);
+  }
+}
+
 size_t infer_tc_smem_bytes(int K) {
   const size_t halves = (size_t)NF * NH + (size_t)NH * LDK + (size_t)tc_ntiles(K) * 8 * LDK + 4 * ITC * LDK;
   const size_t floats = 2 * NH + (size_t)tc_ntiles(K) * 8 + ITC * NF + (size_t)ITC * tc_ldz(K) + K + 2 * NF;
   return ((halves * 2 + 15) / 16) * 16 + floats * 4 + 64;
 }
 
-__global__ void __launch_bounds__(NTHR) mlp_infer_tc_kernel(const MlpInferArgs a) {
+__global__ void __launch_bounds__(NTHR, 1) mlp_infer_tc_kernel(const MlpInferArgs a) {
   extern __shared__ __align__(16) unsigned char tcs[];
   const int K = a.K, KO = K + 2, NT = tc_ntiles(K), ldz = tc_ldz(K);
   __half *W1T = reinterpret_cast<__half *>(tcs);  // [12][64]
@@ -856,37 +885,43 @@ __global__ void __launch_bounds__(NTHR) mlp_infer_tc_kernel(const MlpInferArgs a
     }
     __syncthreads();
     // output layer: the n-tiles round-robin over the warps
+    unsigned ahi[NH / 16][4], alo[NH / 16][4];
+    load_afrag(H2h, lane, ahi);
+    load_afrag(H2l, lane, alo);
     for (int nt = w; nt < NT; nt += NTHR / 32) {
       float d[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_tile64(H2h, H2l, W3, 8 * nt, lane, d);
+      mma_tile64_frag(ahi, alo, W3, 8 * nt, lane, d);
       const int o = 8 * nt + 2 * t;
       *reinterpret_cast<float2 *>(Z + g * ldz + o) = make_float2(d[0] + b3[o], d[1] + b3[o + 1]);
       *reinterpret_cast<float2 *>(Z + (g + 8) * ldz + o) = make_float2(d[2] + b3[o], d[3] + b3[o + 1]);
     }
     __syncthreads();
     // softmax over the spectral logits and the hemisphere pair, then the mixture
+    // (mlp_infer_kernel's expressions; each lane keeps to its own logits, so each
+    // exponential is evaluated once and kept in place, and the mixture is
+    // written straight out)
     for (int c = w; c < rows; c += NTHR / 32) {
       float *z = Z + (size_t)c * ldz;
+      float *qo = a.q_out + (t0 + c) * KO;
       const float *p0 = a.p0_stride ? a.p0 + (t0 + c) * (long long)a.p0_stride : p0s;
       float mx = -INFINITY;
       for (int k = lane; k < K; k += 32) mx = fmaxf(mx, z[k]);
       mx = warp_max(mx);
       float sum = 0.f;
-      for (int k = lane; k < K; k += 32) sum += expf(z[k] - mx);
+      for (int k = lane; k < K; k += 32) {
+        const float e = expf(z[k] - mx);
+        z[k] = e;
+        sum += e;
+      }
       sum = warp_sum(sum);
       const float inv = 1.f / sum;
-      const float hm = fmaxf(z[K], z[K + 1]);
-      const float eu = expf(z[K] - hm), ed = expf(z[K + 1] - hm);
-      __syncwarp();
-      for (int k = lane; k < K; k += 32)
-        z[k] = (1.f - a.mix) * (expf(z[k] - mx) * inv) + a.mix * p0[k];
-      __syncwarp();
+      for (int k = lane; k < K; k += 32) qo[k] = (1.f - a.mix) * (z[k] * inv) + a.mix * p0[k];
       if (lane == 0) {
-        z[K] = (1.f - a.mix) * (eu / (eu + ed)) + a.mix * 0.5f;
-        z[K + 1] = (1.f - a.mix) * (ed / (eu + ed)) + a.mix * 0.5f;
+        const float hm = fmaxf(z[K], z[K + 1]);
+        const float eu = expf(z[K] - hm), ed = expf(z[K + 1] - hm);
+        qo[K] = (1.f - a.mix) * (eu / (eu + ed)) + a.mix * 0.5f;
+        qo[K + 1] = (1.f - a.mix) * (ed / (eu + ed)) + a.mix * 0.5f;
       }
-      __syncwarp();
-      for (int k = lane; k < KO; k += 32) a.q_out[(t0 + c) * KO + k] = z[k];
     }
     __syncthreads();
   }

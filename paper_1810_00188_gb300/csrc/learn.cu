@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(NTHR, 4) quantize_cells_kernel(const float *q,
 // with p0 the T_max proposal; both quantised like any cell proposal (the ray
 // weight divides by the quantised probability, so the estimate stays unbiased),
 // hemispheres 1/2 each.
-__global__ void __launch_bounds__(NTHR) spectral_proposal_kernel(const SpectralArgs a) {
+__global__ void __launch_bounds__(NTHR, 4) spectral_proposal_kernel(const SpectralArgs a) {
   extern __shared__ float ssm[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int K = a.nb * a.ng;
@@ -507,24 +507,32 @@ __global__ void __launch_bounds__(NTHR) spectral_proposal_kernel(const SpectralA
       lam = a.T_max > a.T_min ? (T - a.T_min) / (a.T_max - a.T_min) : 1.0;
       lam = fmin(fmax(lam, 0.0), 1.0);
     }
-    // the local weights and their sum (lane-strided, then a fixed-order warp sum)
+    // the local weights; the hybrid also needs their sum (lane-strided, then a
+    // fixed-order warp sum in binary64), the local proposal only whether one is
+    // positive (the weights are >= 0, so that is the sum's sign)
     double part = 0.0;
+    bool any = false;
     for (int k = lane; k < K; k += 32) {
       const int n = k / a.ng, g = k - n * a.ng;
       const float2 kk = a.ktab32[(size_t)k * a.nT + it];
       const float2 bb = a.btab32[(size_t)n * a.nT + it];
       const float v = a.w_g32[g] * fmaf(fr, bb.y, bb.x) * fmaf(fr, kk.y, kk.x);
-      qw[k] = v > 0.f ? v : 0.f;
-      part += (double)qw[k];
+      const float qk = v > 0.f ? v : 0.f;
+      qw[k] = qk;
+      any = any || qk > 0.f;
+      if (a.mode == 1) part += (double)qk;
     }
+    if (a.mode == 1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    }
+    const bool pos = __any_sync(0xffffffffu, any);
     __syncwarp();
-    if (a.mode == 1 || !(part > 0.0)) {
+    if (a.mode == 1 || !pos) {
       // hybrid (or a cell whose own spectrum is empty: the T_max proposal)
-      const double l = part > 0.0 ? lam : 0.0;
+      const double l = pos ? lam : 0.0;
       for (int k = lane; k < K; k += 32)
-        qw[k] = (float)((1.0 - l) * (double)a.p0[k] + (part > 0.0 ? l * (double)qw[k] / part : 0.0));
+        qw[k] = (float)((1.0 - l) * (double)a.p0[k] + (pos ? l * (double)qw[k] / part : 0.0));
       __syncwarp();
     }
     quantize_cell(qw, 0.5f, a.nb, a.ng, wn, a.cell_cn + c * a.nb, a.cell_cg + c * (long long)K,

@@ -178,14 +178,16 @@ def cpu_baseline(a, target_s=12.0):
                       f"{steps:.3g} steps in {dt:.1f} s"}
 
 
-def field_error(grid, kd, T, x, rays, snapshot, qs, box=None, crop=None):
+def field_error(grid, kd, T, x, rays, snapshot, qs, box=None, crop=None, tol=1e-4, ray_offset=0,
+                max_steps=1 << 20):
     """|Q_gpu - Q_oracle| / S_i over the cells of `box` (the whole grid when None)
     for each GPU result in qs; crop maps a whole-field result onto the box."""
     import numpy as np
 
     import oracle
-    ref = oracle.solve(grid, kd, T, x, rays=rays, seed=0, snapshot=snapshot, tol=1e-4,
-                       max_steps=1 << 20, box=box, nthreads=oracle.default_threads())
+    ref = oracle.solve(grid, kd, T, x, rays=rays, seed=0, snapshot=snapshot, tol=tol,
+                       ray_offset=ray_offset, max_steps=max_steps, box=box,
+                       nthreads=oracle.default_threads())
     out = {"rays": rays, "cells": int(ref["q"].size), "tolerance": {"fp32": 1e-4, "fp64": 1e-10}}
     for name, qg in qs.items():
         qc = qg if crop is None else qg[crop]
@@ -240,11 +242,14 @@ def configs_extra(sp):
 
     # grey slab (E3 case)
     grid, kd, T, x = inputs.grey_slab_16x32x16(1.0)
+    k64, k32 = [], []
     out["grey_slab_16x32x16_128rays"] = {
-        "gpu_fp64": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP64, 0, 1e-6),
-        "gpu_fp32": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP32, 0, 1e-6),
+        "gpu_fp64": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP64, 0, 1e-6, keep=k64),
+        "gpu_fp32": gpu(grid, kd, T, x, 128, mcrt.MCRT_FP32, 0, 1e-6, keep=k32),
         "oracle_all_cores": cpu(grid, kd, T, x, 128, 0, 1e-6, None, allc),
         "oracle_1_core": cpu(grid, kd, T, x, 128, 0, 1e-6, (0, 16, 0, 32, 0, 2), 1)}
+    out["grey_slab_16x32x16_128rays"]["error_vs_oracle"] = field_error(
+        grid, kd, T, x, 128, 0, {"fp64": k64[0], "fp32": k32[0]}, tol=1e-6)
     # 64^3 channel, one core (the all-core figure is the main line's cpu_baseline)
     grid, kd, T, x = inputs.nongrey_channel(64, 64, 64, seed=0)
     out["nongrey_channel_64x64x64_1000rays"] = {
@@ -306,6 +311,10 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             mcrt.mcrt_batch_run(b, (k + 1) * rays, sp)
             st = mcrt.mcrt_batch_get_stats(b)
             times.append(st["kernel_ms"])
+        # the smallest snapshot of the last run against the FP64 oracle, cell by cell
+        ks = min(range(n), key=lambda k: snaps[k][0].ncells)
+        torch.cuda.synchronize()
+        qk = outs[ks][0].cpu().numpy()
     finally:
         mcrt.mcrt_batch_destroy(b)
     solvers[0].set_tuning()
@@ -326,7 +335,10 @@ def batch_extra(sp, rays=256, n=32, seed=0):
                       "form": "per-item launches" if best[2] else "one persistent launch",
                       "graph_branches": best[3]},
             "tuning_ms": {(f"{k[0]}x{k[1]} per-item x{k[3]}" if k[2] else f"{k[0]}x{k[1]} one launch"): v
-                          for k, v in table.items()}}
+                          for k, v in table.items()},
+            "error_vs_oracle": dict(field_error(snaps[ks][0], kd, snaps[ks][1], snaps[ks][2], rays, ks,
+                                                {"fp32": qk}, ray_offset=3 * rays, max_steps=1 << 30),
+                                    snapshot=ks, grid=list(snaps[ks][0].shape))}
 
 
 def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_batch_kernel(const Tra
         if (hand_off(a, L)) active = false;
       }
       // the next step's field entry, loaded now so that its latency overlaps the
-      // rest of this round
+      // rest of this march round
       if (!done && active) fcur = __ldg(field + (MG ? loff + lin : lin));
       if (done) {
         if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)

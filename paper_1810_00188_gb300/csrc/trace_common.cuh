@@ -504,7 +504,7 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
       if (hand_off(a, L)) s.active = false;
     }
     // the next step's field entry, loaded now so that its latency overlaps the
-    // rest of this round
+    // rest of this march round
     if (!done && s.active) s.fcur = __ldg(field + (MG ? s.loff + s.lin : s.lin));
     if (done) {
       if (s.tau > 0.f) s.X += (s.B_i - s.B_last) * s.tau;  // residual dump (Algorithm 1)

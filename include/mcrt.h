@@ -215,6 +215,11 @@ typedef struct {
                               (within about 2^-51 of sum |Y| of the exact sum
                               of the samples); 1: compensated binary32 pairs
                               (within about 2e-7 of sum |Y|), a little cheaper */
+  int tally_plain_loads;   /* 0 (default): the binary64 tallies read the samples
+                              through the tensor memory accelerator (tiled bulk
+                              copies into shared memory) where their layout
+                              allows it (rays_per_cell % 4 == 0); 1: by plain
+                              loads.  The same results either way            */
   int claim_rays;          /* 0: default (1024); FP32 solves: rays per run of
                               cells a warp claims at a time (the run is at
                               least one cell and at most 1/8 of a warp's share

@@ -36,6 +36,7 @@ def _set(S, key, keep):
     rays; 0: the library default), keeping the other tuning fields as set."""
     mb, k, mib, claim = key
     S.set_tuning(mb, k, mib, keep["long_ray_steps"], keep["long_ray_flight"], keep["tally_binary32"],
+                 tally_plain_loads=keep["tally_plain_loads"],
                  batch_per_snapshot=keep["batch_per_snapshot"], claim_rays=claim)
 
 

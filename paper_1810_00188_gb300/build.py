@@ -17,8 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmcrt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["trace.cu", "trace_fp32.cu", "batch.cu", "long_rays.cu", "fields.cu", "noalloc.cu", "learn.cu", "ceilings.cu", "mcrt_api.cpp",
-           "learn_api.cpp"]
+SOURCES = ["trace.cu", "trace_fp32.cu", "batch.cu", "long_rays.cu", "fields.cu", "noalloc.cu", "learn.cu", "ceilings.cu",
+           "tally_tma.cu", "mcrt_api.cpp", "learn_api.cpp"]
 
 
 def nvcc_path() -> str:

@@ -66,6 +66,7 @@ struct mcrt_ctx {
   float long_flight = 32;   // x/z crossings left in the flight for a hand-off
   int tally32 = 0;          // per-cell tallies in binary32 pairs instead of binary64
   int claim_rays = 1024;    // FP32 kernels: rays per claimed run of cells
+  int tally_plain = 0;      // binary64 tallies by plain loads instead of TMA
   int batch_per_snapshot = 0;  // batches: per-item launches even for one k-distribution
   double last_T_max = 0;
   std::string err;

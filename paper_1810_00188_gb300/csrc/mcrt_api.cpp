@@ -334,6 +334,7 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.ncells_box = (long long)a.bnx * a.bny * a.bnz;
   a.counters = (unsigned long long *)ctx->counters.p;
   a.tally32 = ctx->tally32;
+  a.reduce_plain = ctx->tally_plain;
 }
 
 }  // namespace mcrt_host
@@ -771,7 +772,7 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
                        cudaMemcpyDeviceToHost, s),
        "read error flag");
     CK(cudaStreamSynchronize(s), "sync");
-    if (flag != 0) return fail(ctx, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
+    if (flag != 0) return fail(ctx, MCRT_E_TIMEOUT, "a device-side wait gave up (trace or tally kernel)");
   }
   return MCRT_OK;
 }
@@ -788,6 +789,8 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
     return fail(ctx, MCRT_E_ARG, "steps_per_round not in {0, 1, 2, 4}");
   if (t->long_ray_flight > (1 << 24)) return fail(ctx, MCRT_E_ARG, "long_ray_flight above 2^24");
   if (t->tally_binary32 != 0 && t->tally_binary32 != 1) return fail(ctx, MCRT_E_ARG, "tally_binary32 not 0 or 1");
+  if (t->tally_plain_loads != 0 && t->tally_plain_loads != 1)
+    return fail(ctx, MCRT_E_ARG, "tally_plain_loads not 0 or 1");
   if (t->claim_rays != 0 && (t->claim_rays < 32 || t->claim_rays > (1 << 20)))
     return fail(ctx, MCRT_E_ARG, "claim_rays not 0 or within 32..2^20");
   if (t->batch_per_snapshot != 0 && t->batch_per_snapshot != 1)
@@ -800,6 +803,7 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
   ctx->tally32 = t->tally_binary32;
   ctx->batch_per_snapshot = t->batch_per_snapshot;
   ctx->claim_rays = t->claim_rays ? t->claim_rays : 1024;
+  ctx->tally_plain = t->tally_plain_loads;
   return MCRT_OK;
 }
 
@@ -813,6 +817,7 @@ int mcrt_get_tuning(const mcrt_ctx *ctx, mcrt_tuning *t) {
   t->tally_binary32 = ctx->tally32;
   t->batch_per_snapshot = ctx->batch_per_snapshot;
   t->claim_rays = ctx->claim_rays;
+  t->tally_plain_loads = ctx->tally_plain;
   return MCRT_OK;
 }
 
@@ -826,7 +831,7 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out) {
   CK(cudaMemcpyAsync(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost, ctx->last_stream),
      "read counters");
   CK(cudaStreamSynchronize(ctx->last_stream), "sync");
-  if (c[5] != 0) return fail(ctx, MCRT_E_TIMEOUT, "trace kernel stopped without progress");
+  if (c[5] != 0) return fail(ctx, MCRT_E_TIMEOUT, "a device-side wait gave up (trace or tally kernel)");
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "elapsed");
   out->steps = c[0];
@@ -1114,6 +1119,7 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     mcrt::TraceArgs &a = args[k];
     std::memset(&a, 0, sizeof(a));
     a.tally32 = items[0].ctx->tally32;
+    a.reduce_plain = items[0].ctx->tally_plain;
     a.nx = g.nx;
     a.ny = g.ny;
     a.nz = g.nz;

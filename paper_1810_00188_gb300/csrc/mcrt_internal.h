@@ -132,8 +132,9 @@ struct TraceArgs {
   // outputs (box-sized)
   double *q, *sigma;
   unsigned long long *steps_cell;
-  // FP32 kernels: per-cell tallies in binary32 pairs (1) instead of binary64 (0)
-  int tally32;
+  // FP32 kernels: per-cell tallies in binary32 pairs (1) instead of binary64 (0);
+  // binary64 tallies read by plain loads (1) instead of the TMA-fed kernel (0)
+  int tally32, reduce_plain;
   // absorption-based estimate (null: off): per-batch binary64 sums [16][armc_nc]
   // of the deposits into each cell and of each cell's own samples
   double *armc_acc, *ermc_acc;
@@ -170,6 +171,11 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // after the reduction.
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
                               cudaStream_t s, cudaEvent_t *marks = nullptr);
+// The binary64 per-cell tallies of one FP32 solve chunk with the samples
+// streamed by TMA (tally_tma.cu; the same results as reduce_cells_kernel).
+// Launches nothing and leaves *launched false when the samples' layout does not
+// allow the tiled copy (rays % 4 != 0) or the driver has no tensor-map encoder.
+cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, bool *launched);
 // Q and sigma of the absorption-based estimate (hybrid = 0) or of its
 // temperature-weighted combination with the emission-based one (hybrid = 1) from
 // the per-batch sums of the AR trace launches; K batches of N rays per cell.

@@ -634,10 +634,14 @@ cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_p
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
   if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
-  if (a.tally32)
+  if (a.tally32) {
     reduce_cells32_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
-  else
-    reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  } else {
+    bool tma = false;
+    e = a.reduce_plain ? cudaSuccess : launch_reduce_tma(a, s, &tma);
+    if (e != cudaSuccess) return e;
+    if (!tma) reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess && marks) e = cudaEventRecord(marks[3], s);
   return e;

@@ -61,7 +61,8 @@ class mcrt_solve_params(C.Structure):
 class mcrt_tuning(C.Structure):
     _fields_ = [("min_blocks_per_sm", C.c_int), ("steps_per_round", C.c_int),
                 ("scratch_mib", C.c_int), ("long_ray_steps", C.c_int), ("long_ray_flight", C.c_int),
-                ("tally_binary32", C.c_int), ("claim_rays", C.c_int), ("batch_per_snapshot", C.c_int)]
+                ("tally_binary32", C.c_int), ("tally_plain_loads", C.c_int), ("claim_rays", C.c_int),
+                ("batch_per_snapshot", C.c_int)]
 
 
 class mcrt_batch_item(C.Structure):
@@ -264,9 +265,11 @@ def mcrt_get_stats(ctx) -> dict:
 
 def mcrt_set_tuning(ctx, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
                     scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0,
-                    tally_binary32: int = 0, batch_per_snapshot: int = 0, claim_rays: int = 0):
+                    tally_binary32: int = 0, batch_per_snapshot: int = 0, claim_rays: int = 0,
+                    tally_plain_loads: int = 0):
     t = mcrt_tuning()
     t.tally_binary32 = tally_binary32
+    t.tally_plain_loads = tally_plain_loads
     t.claim_rays = claim_rays
     t.batch_per_snapshot = batch_per_snapshot
     t.min_blocks_per_sm = min_blocks_per_sm
@@ -577,9 +580,10 @@ class Solver:
 
     def set_tuning(self, min_blocks_per_sm: int = 0, steps_per_round: int = 0,
                    scratch_mib: int = 0, long_ray_steps: int = 0, long_ray_flight: int = 0,
-                   tally_binary32: int = 0, batch_per_snapshot: int = 0, claim_rays: int = 0):
+                   tally_binary32: int = 0, batch_per_snapshot: int = 0, claim_rays: int = 0,
+                   tally_plain_loads: int = 0):
         mcrt_set_tuning(self.ctx, min_blocks_per_sm, steps_per_round, scratch_mib, long_ray_steps,
-                        long_ray_flight, tally_binary32, batch_per_snapshot, claim_rays)
+                        long_ray_flight, tally_binary32, batch_per_snapshot, claim_rays, tally_plain_loads)
 
     def tuning(self) -> dict:
         return mcrt_get_tuning(self.ctx)

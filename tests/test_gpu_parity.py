@@ -228,8 +228,8 @@ def test_fp32_results_independent_of_launch_shape():
         S.set_tuning(mb, k, mib)
         assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k,
                               "scratch_mib": mib if mib else 1024, "long_ray_steps": 1024,
-                              "long_ray_flight": 32, "tally_binary32": 0, "claim_rays": 1024,
-                              "batch_per_snapshot": 0}
+                              "long_ray_flight": 32, "tally_binary32": 0, "tally_plain_loads": 0,
+                              "claim_rays": 1024, "batch_per_snapshot": 0}
         q, s, st = S.solve(rays=300, seed=3, with_steps=True)
         assert np.array_equal(q, q0) and np.array_equal(s, s0) and np.array_equal(st, st0)
     # the claimed runs: one cell at a time, or as long as the solve allows
@@ -301,6 +301,45 @@ def test_binary64_tally_against_binary32_tally_and_oracle():
     d = np.abs(res[0][0] - res[1][0]) / scale
     assert d.max() <= 3e-7, d.max()
     assert np.any(res[0][0] != res[1][0])  # the two tallies are different arithmetic
+
+
+def test_tma_fed_tally_equals_plain_loads_bitwise():
+    """The binary64 tally reads the samples through the tensor memory accelerator
+    (tiled bulk copies with the 128-byte swizzle, two buffers per warp) when the
+    ray count is a multiple of 4, else by plain loads; both run the same exact
+    32-sample runs in the same order, so Q, sigma and the step counts agree bit
+    for bit.  Ragged grids (positions outside the box in the last bricks, a chunk
+    not a multiple of 32 positions), a sub-box, ray counts below, at and across
+    one 32-sample run, and one that forces several solve chunks."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(13, 11, 9, seed=21, eps_wall=0.8, x_mode="field")
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    cases = [dict(rays=4), dict(rays=32), dict(rays=36), dict(rays=100), dict(rays=1000),
+             dict(rays=64, box=(2, 11, 1, 10, 3, 8))]
+    for kw in cases:
+        res = []
+        for plain in (0, 1):
+            S.set_tuning(tally_plain_loads=plain)
+            assert S.tuning()["tally_plain_loads"] == plain
+            res.append(S.solve(seed=8, precision=mcrt.MCRT_FP32, with_steps=True, **kw))
+        for a, b in zip(*res):
+            assert np.array_equal(a, b), kw
+    # several chunks (1 MiB of scratch) with both readers
+    res = []
+    for plain in (0, 1):
+        S.set_tuning(scratch_mib=1, tally_plain_loads=plain)
+        res.append(S.solve(rays=400, seed=9, precision=mcrt.MCRT_FP32, with_steps=True))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    S.set_tuning()
+    # and the default reader against the oracle
+    orc = oracle.solve(grid, kd, T, x, rays=100, seed=8)
+    q, s = S.solve(rays=100, seed=8, precision=mcrt.MCRT_FP32)
+    assert np.all(np.abs(q - orc["q"]) <= 1e-4 * orc["scale"])
+    with pytest.raises(mcrt.McrtError):
+        S.set_tuning(tally_plain_loads=2)
+    S.close()
 
 
 def test_binary64_tally_sign_mix_and_launch_independence():

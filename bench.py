@@ -341,6 +341,53 @@ def batch_extra(sp, rays=256, n=32, seed=0):
                                     snapshot=ks, grid=list(snaps[ks][0].shape))}
 
 
+# The paper's own timing table (64^3 cells, 6e4 rays per cell, 119 narrow bands x
+# 16 g-points, one Tesla K40M; Section 6): seconds per solve, context only
+PAPER_64CUBED_6E4_S = {"gpu_nb_sorting_exact": 573.0, "gpu_optimized_multigrid": 132.8, "cpu_serial": 39313.3}
+
+
+def paper_scale_extra(sp, rays=60000):
+    """The size of the paper's timing runs, on synthetic inputs of that shape: a
+    64^3 slab of 1 m between black walls at 400 K, periodic in x and z, a
+    parabolic temperature profile (400 K at the walls, 1400 K at mid-height) with
+    a 5% random part, 119 bands x 16 g-points of synthetic correlated-k tables,
+    6e4 rays per cell (1.57e10 rays: the sample scratch runs in chunks).  The
+    exact FP32 march and the multigrid march (5 grids, 5 segments per grid, the
+    paper's optimized setting), one solve each, beside the paper's K40M times for
+    the same sizes (context, another machine and other spectra)."""
+    import numpy as np
+    import torch
+
+    from paper_1810_00188_gb300 import inputs, mcrt
+    kd = inputs.make_kdist(seed=7, n_bands=119, n_g=16, nT=80, nu0_cm=150.0, dnu_cm=25.0)  # 300..1880 K
+    grid = inputs.Grid(64, 64, 64, 1.0, 1.0, 1.0, T_wall=(400.0, 400.0))
+    yc = (np.arange(64) + 0.5) / 64.0
+    prof = 400.0 + 1000.0 * 4.0 * yc * (1.0 - yc)
+    G = inputs.gaussian_random_field(grid.shape, (grid.lz, grid.ly, grid.lx), 11)
+    T = np.ascontiguousarray(prof[None, :, None] * (1.0 + 0.05 * np.clip(G, -4.0, 4.0)))
+    x = np.full(grid.shape, kd.x_ref)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(q)
+    out = {"workload": "64^3 slab 1 m, 119 x 16 k-distribution (synthetic), 6e4 rays/cell, black walls 400 K, "
+                       "parabolic T 400 -> 1400 K",
+           "paper_k40m_s": PAPER_64CUBED_6E4_S}
+    for name, mg in (("exact", 1), ("multigrid", 5)):
+        S.solve_into(S.params(rays=256, seed=0, precision=mcrt.MCRT_FP32, mg_levels=mg, mg_steps=5), q, sg,
+                     stream=sp)  # warm-up
+        S.solve_into(S.params(rays=rays, seed=0, ray_offset=256, precision=mcrt.MCRT_FP32, mg_levels=mg,
+                              mg_steps=5), q, sg, stream=sp)
+        st = S.stats()
+        out[name] = {"s": st["kernel_ms"] / 1e3, "steps": st["steps"], "rays": st["rays"],
+                     "steps_per_s": st["steps"] / (st["kernel_ms"] / 1e3), "launches": st["launches"]}
+    S.close()
+    out["speedup_vs_paper"] = {"exact_vs_nb_sorting": PAPER_64CUBED_6E4_S["gpu_nb_sorting_exact"] / out["exact"]["s"],
+                               "multigrid_vs_optimized": PAPER_64CUBED_6E4_S["gpu_optimized_multigrid"]
+                               / out["multigrid"]["s"]}
+    return out
+
+
 def multigrid_extra(S, params, q, s, sp, rays, steps_per_grid=5):
     """The multigrid march (Section 4.3) on the benchmark workload: every grid
     the field allows, `steps_per_grid` segments per grid; time against the
@@ -843,6 +890,7 @@ def main():
             result["estimators"] = estimators_extra(S, T, params, q, s, sp)
             if world == 1:
                 result["configs"] = configs_extra(sp)
+                result["paper_scale"] = paper_scale_extra(sp)
                 # before the learned-proposal leg, whose datasets stay in torch's cache
                 result["batched_snapshots"] = batch_extra(sp)
                 torch.cuda.empty_cache()

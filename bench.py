@@ -346,7 +346,7 @@ def batch_extra(sp, rays=256, n=32, seed=0):
 PAPER_64CUBED_6E4_S = {"gpu_nb_sorting_exact": 573.0, "gpu_optimized_multigrid": 132.8, "cpu_serial": 39313.3}
 
 
-def paper_scale_extra(sp, rays=60000):
+def paper_scale_extra(sp, rays=60000, scratch_mib=0):
     """The size of the paper's timing runs, on synthetic inputs of that shape: a
     64^3 slab of 1 m between black walls at 400 K, periodic in x and z, a
     parabolic temperature profile (400 K at the walls, 1400 K at mid-height) with
@@ -354,7 +354,8 @@ def paper_scale_extra(sp, rays=60000):
     6e4 rays per cell (1.57e10 rays: the sample scratch runs in chunks).  The
     exact FP32 march and the multigrid march (5 grids, 5 segments per grid, the
     paper's optimized setting), one solve each, beside the paper's K40M times for
-    the same sizes (context, another machine and other spectra)."""
+    the same sizes (context, another machine and other spectra).  scratch_mib 0:
+    the library's default cap of the sample scratch (the solve runs in chunks)."""
     import numpy as np
     import torch
 
@@ -368,9 +369,10 @@ def paper_scale_extra(sp, rays=60000):
     x = np.full(grid.shape, kd.x_ref)
     S = mcrt.Solver(grid, kd)
     S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    S.set_tuning(scratch_mib=scratch_mib)
     q = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
     sg = torch.empty_like(q)
-    out = {"workload": "64^3 slab 1 m, 119 x 16 k-distribution (synthetic), 6e4 rays/cell, black walls 400 K, "
+    out = {"scratch_mib": S.tuning()["scratch_mib"], "workload": "64^3 slab 1 m, 119 x 16 k-distribution (synthetic), 6e4 rays/cell, black walls 400 K, "
                        "parabolic T 400 -> 1400 K",
            "paper_k40m_s": PAPER_64CUBED_6E4_S}
     for name, mg in (("exact", 1), ("multigrid", 5)):
@@ -380,7 +382,9 @@ def paper_scale_extra(sp, rays=60000):
                               mg_steps=5), q, sg, stream=sp)
         st = S.stats()
         out[name] = {"s": st["kernel_ms"] / 1e3, "steps": st["steps"], "rays": st["rays"],
-                     "steps_per_s": st["steps"] / (st["kernel_ms"] / 1e3), "launches": st["launches"]}
+                     "steps_per_s": st["steps"] / (st["kernel_ms"] / 1e3), "launches": st["launches"],
+                     "trace_ms": st["trace_ms"], "long_rays_ms": st["long_ms"], "reduce_ms": st["reduce_ms"],
+                     "rays_handed_off": st["long_rays"]}
     S.close()
     out["speedup_vs_paper"] = {"exact_vs_nb_sorting": PAPER_64CUBED_6E4_S["gpu_nb_sorting_exact"] / out["exact"]["s"],
                                "multigrid_vs_optimized": PAPER_64CUBED_6E4_S["gpu_optimized_multigrid"]

@@ -203,7 +203,7 @@ typedef struct {
                               trading registers per thread against occupancy */
   int steps_per_round;     /* 0: default (1); 1, 2 or 4 march steps per lane
                               between refills of idle lanes                      */
-  int scratch_mib;         /* 0: default (1024); cap of the per-ray sample
+  int scratch_mib;         /* 0: default (4096); cap of the per-ray sample
                               scratch; larger solves run in several chunks      */
   int long_ray_steps;      /* 0: default (1024); > 0: hand-off threshold in
                               segments; < 0: never hand off                     */

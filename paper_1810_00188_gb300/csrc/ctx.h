@@ -61,7 +61,7 @@ struct mcrt_ctx {
   int last_launches = 0;
   int min_blocks = 3;
   int steps_per_round = 1;
-  int scratch_mib = 1024;
+  int scratch_mib = 4096;
   int long_steps = 1024;    // hand-off threshold in segments (<= 0: never)
   float long_flight = 32;   // x/z crossings left in the flight for a hand-off
   int tally32 = 0;          // per-cell tallies in binary32 pairs instead of binary64

@@ -450,10 +450,12 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
 
 long long long_ray_capacity(long long rays, int long_steps) {
   // rays that reach L segments fall off roughly like 1/L (grazing directions)
-  // times the share of thin bands; rays 64 / L^2 leaves a wide margin at the
-  // default L = 1024 and holds every ray for L <= 8, at least 2^16 entries
+  // times the share of thin bands (a 1 m slab with 119 x 16 bands hands off
+  // about 1 ray in 1.2e4 at L = 1024); rays 256 / L^2 leaves a margin of three
+  // at the default L = 1024 and holds every ray for L <= 16, at least 2^16
+  // entries (128 B each)
   const long long L = long_steps > 1 ? long_steps : 1;
-  long long c = L <= 8 ? rays : rays / ((L * L + 63) / 64);
+  long long c = L <= 16 ? rays : rays / ((L * L + 255) / 256);
   if (c < 65536) c = 65536;
   if (c > rays) c = rays > 0 ? rays : 1;
   if (c > (1LL << 24)) c = 1LL << 24;

@@ -797,7 +797,7 @@ int mcrt_set_tuning(mcrt_ctx *ctx, const mcrt_tuning *t) {
     return fail(ctx, MCRT_E_ARG, "batch_per_snapshot not 0 or 1");
   ctx->min_blocks = t->min_blocks_per_sm ? t->min_blocks_per_sm : 3;
   ctx->steps_per_round = t->steps_per_round ? t->steps_per_round : 1;
-  ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 1024;
+  ctx->scratch_mib = t->scratch_mib ? t->scratch_mib : 4096;
   ctx->long_steps = t->long_ray_steps ? (t->long_ray_steps > 0 ? t->long_ray_steps : -1) : 1024;
   ctx->long_flight = t->long_ray_flight ? (t->long_ray_flight > 0 ? (float)t->long_ray_flight : -1.f) : 32.f;
   ctx->tally32 = t->tally_binary32;

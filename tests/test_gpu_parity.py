@@ -227,7 +227,7 @@ def test_fp32_results_independent_of_launch_shape():
     for mb, k, mib in ((1, 1, 0), (3, 2, 0), (2, 4, 1), (4, 4, 0), (1, 4, 3), (2, 1, 0)):
         S.set_tuning(mb, k, mib)
         assert S.tuning() == {"min_blocks_per_sm": mb, "steps_per_round": k,
-                              "scratch_mib": mib if mib else 1024, "long_ray_steps": 1024,
+                              "scratch_mib": mib if mib else 4096, "long_ray_steps": 1024,
                               "long_ray_flight": 32, "tally_binary32": 0, "tally_plain_loads": 0,
                               "claim_rays": 1024, "batch_per_snapshot": 0}
         q, s, st = S.solve(rays=300, seed=3, with_steps=True)

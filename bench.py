@@ -272,8 +272,10 @@ def batch_extra(sp, rays=256, n=32, seed=0):
     """32 snapshots of uneven grid sizes (32^3, 48x64x48, 96^3, 128^3), 256 rays
     per cell, sharing the k-distribution, in one graph launch.  The tuner picks
     the form (a single persistent trace kernel over all snapshots and one
-    reduction, or per-snapshot launches in 1, 2, 4 or 8 graph branches) and the
-    launch shape (CTAs per SM, march steps per round); compared with the same
+    reduction, or per-snapshot launches in 1, 2, 4 or 8 graph branches, with the
+    default or a 1 GiB cap of each snapshot's sample scratch: a 128^3 snapshot then
+    runs as two chunks) and the launch shape (CTAs per SM, march steps per round);
+    compared with the same
     snapshots solved one after another (the sum of their device times)."""
     import torch
 
@@ -290,17 +292,17 @@ def batch_extra(sp, rays=256, n=32, seed=0):
         items.append((S.ctx, q.data_ptr(), sg.data_ptr(), k))
     params = mcrt.Solver.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32)
 
-    def make(shape):  # (CTAs per SM, steps per round, per-item launches, graph branches)
-        mb, k, per_item, streams = shape
-        solvers[0].set_tuning(mb, k, batch_per_snapshot=per_item)
+    def make(shape):  # (CTAs per SM, steps per round, per-item launches, graph branches, scratch MiB)
+        mb, k, per_item, streams, mib = shape
+        solvers[0].set_tuning(mb, k, mib, batch_per_snapshot=per_item)
         return mcrt.mcrt_batch_create(items, params, streams=streams)
 
     def run(b):
         mcrt.mcrt_batch_run(b, rays, sp)
         return mcrt.mcrt_batch_get_stats(b)["kernel_ms"]
 
-    shapes = ((3, 1, 0, 1), (3, 2, 0, 1), (2, 1, 0, 1), (2, 2, 0, 1), (3, 1, 1, 1), (3, 1, 1, 2), (3, 1, 1, 4),
-              (3, 1, 1, 8))
+    shapes = ((3, 1, 0, 1, 0), (3, 2, 0, 1, 0), (2, 1, 0, 1, 0), (2, 2, 0, 1, 0), (3, 1, 1, 1, 0), (3, 1, 1, 2, 0),
+              (3, 1, 1, 4, 0), (3, 1, 1, 8, 0), (3, 1, 1, 4, 1024), (3, 1, 1, 8, 1024))
     best, table = autotune.tune_batch(make, run, shapes=shapes, reps=1)
     b = make(best)
     try:
@@ -333,9 +335,9 @@ def batch_extra(sp, rays=256, n=32, seed=0):
             "sequential_ms": seq, "speedup_vs_sequential": seq / (t * 1e3),
             "tuned": {"min_blocks_per_sm": best[0], "steps_per_round": best[1],
                       "form": "per-item launches" if best[2] else "one persistent launch",
-                      "graph_branches": best[3]},
-            "tuning_ms": {(f"{k[0]}x{k[1]} per-item x{k[3]}" if k[2] else f"{k[0]}x{k[1]} one launch"): v
-                          for k, v in table.items()},
+                      "graph_branches": best[3], "scratch_mib": best[4] or "default"},
+            "tuning_ms": {(f"{k[0]}x{k[1]} per-item x{k[3]}" if k[2] else f"{k[0]}x{k[1]} one launch")
+                          + (f" scratch {k[4]} MiB" if k[4] else ""): v for k, v in table.items()},
             "error_vs_oracle": dict(field_error(snaps[ks][0], kd, snaps[ks][1], snaps[ks][2], rays, ks,
                                                 {"fp32": qk}, ray_offset=3 * rays, max_steps=1 << 30),
                                     snapshot=ks, grid=list(snaps[ks][0].shape))}

@@ -219,7 +219,8 @@ typedef struct {
                               through the tensor memory accelerator (tiled bulk
                               copies into shared memory) where their layout
                               allows it (rays_per_cell % 4 == 0); 1: by plain
-                              loads.  The same results either way            */
+                              loads.  The same results either way.  Batches
+                              use plain loads (their launches share the SMs) */
   int claim_rays;          /* 0: default (1024); FP32 solves: rays per run of
                               cells a warp claims at a time (the run is at
                               least one cell and at most 1/8 of a warp's share

@@ -214,15 +214,12 @@ cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, bool *launched
     if (e != cudaSuccess) return e;
     configured[dev] = 1;
   }
-  int per_sm = 0, nsm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_cells_tma_kernel, TW * 32, smem);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
+  // one group of 32 positions per warp where the grid allows (grid-stride
+  // beyond): short blocks spread over whatever SMs are free, which matters when
+  // the tally runs beside other solves' kernels in a batch graph
   const long long groups = (P + 31) / 32;
   long long blocks = (groups + TW - 1) / TW;
-  const long long wave = (long long)(per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
-  if (blocks > wave) blocks = wave;
+  if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
   reduce_cells_tma_kernel<<<(unsigned)blocks, TW * 32, smem, s>>>(a, map);
   e = cudaGetLastError();
   if (e == cudaSuccess) *launched = true;

@@ -316,10 +316,11 @@ int mcrt_get_stats(mcrt_ctx *ctx, mcrt_solve_stats *out);
  *    code.  So make one call per device during set-up, before the host reserves
  *    its memory and before any stream capture (or run with
  *    CUDA_MODULE_LOADING=EAGER); later calls allocate nothing.
- *  - The first call after mcrt_set_kdist or mcrt_set_fields rebuilds the plain
- *    proposal (Eqs. 13, 16) on the host from fixed buffers and uploads it from
- *    pageable memory (the call returns once the copies are staged); make that
- *    call outside stream capture too.
+ *  - The first call after mcrt_set_kdist, or after an mcrt_set_fields that
+ *    changes the proposal's T_max (the largest of the field's and the emitting
+ *    walls' temperatures), rebuilds the plain proposal (Eqs. 13, 16) on the host
+ *    from fixed buffers and uploads it from pageable memory (the call returns
+ *    once the copies are staged); make that call outside stream capture too.
  *  - 8 MiB of the array holds the long rays handed to the warp-parallel march
  *    (2^16 entries, the least buffer of a regular solve), so the results equal
  *    mcrt_solve_qrad's bit for bit unless more rays than that are handed off.

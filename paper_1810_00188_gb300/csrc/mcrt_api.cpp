@@ -560,14 +560,15 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   const long long n = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   ctx->have_fields = false;
-  ctx->prop_valid = false;
+  // (the plain proposal depends on the field only through T_max: the solves
+  // rebuild it when that changes)
   // field64 also holds the coarser grids of the multigrid march after the
   // problem's own (Section 4.3)
   const int mg_levels = mcrt::multigrid_levels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
   const long long n_all = mcrt::multigrid_cells(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, mg_levels);
   CK(ensure(ctx->field64, (size_t)n_all * sizeof(double2)), "alloc field");
   const void *dT = T, *dx = x;
-  DevBuf stage;
+  DevBuf &stage = ctx->fstage;  // kept for the next call (no allocation per field update)
   if (mem == MCRT_MEM_HOST) {
     CK(ensure(stage, (size_t)n * esz * (x ? 2 : 1)), "alloc staging");
     CK(cudaMemcpyAsync(stage.p, T, (size_t)n * esz, cudaMemcpyHostToDevice, s), "copy T");
@@ -597,7 +598,6 @@ int mcrt_set_fields(mcrt_ctx *ctx, const void *T, const void *x, int fp64, int m
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(st, ctx->fstats.p, sizeof(st), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (stage.p) cudaFree(stage.p);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "pack fields");
   if (st[2] != 0)
     return fail(ctx, MCRT_E_RANGE,
@@ -861,7 +861,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->fstage, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,

@@ -142,6 +142,8 @@ __device__ __forceinline__ void axis_setup(R d, R fr, R delta, int &s, R &t0, R 
   }
 }
 
+constexpr int START_LANES = 8;  // waiting lanes that set up their next rays together
+
 template <typename R>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   typedef typename Prec<R>::R2 R2;
@@ -192,8 +194,27 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   Tally<R> tally;
   unsigned long long nsteps = 0, ncap = 0, nwall = 0, max_ray = 0;
 
-  for (int r = lane; r < a.rays; r += 32) {
-    const unsigned ray = (unsigned)(a.ray_offset + (unsigned long long)r);
+  // Each lane marches its rays r = lane, lane + 32, ... one after another, and a
+  // lane whose ray has ended starts its next one without waiting for the rest of
+  // the warp's current rays (a heavy-tailed ray length otherwise idles most
+  // lanes at the end of each round of 32 rays): the same rays in the same order
+  // on each lane, hence the same tallies.
+  unsigned ray = 0, nrefl = 0;
+  R ddx = 0, ddy = 0, ddz = 0, fx = 0, fy = 0, fz = 0, wgt = 0, kap_i = 0, B_i = 0;
+  int n = 0;
+  size_t krow = 0, brow = 0;
+  int ix = 0, iy = 0, iz = 0, lin = 0, sx = 0, sy_ = 0, sz = 0, steps = 0;
+  R t0x = 0, t0y = 0, t0z = 0, tsx = 0, tsy = 0, tsz = 0, cntx = 0, cnty = 0, cntz = 0;
+  R tnx = 0, tny = 0, tnz = 0, tprev = 0, X = 0, tau = 1, B_last = 0;
+  // multigrid (Section 4.3): current grid, its dimensions and the offset of its
+  // fields, segments marched on it, and the face counter step: grid l keeps
+  // every inc-th face of the grid the axis parameters were set up on
+  int lev = 0, lsteps = 0, nxl = nx, nyl = ny, nzl = nz;
+  long long loff = 0;
+  R inc = 1;
+  // the set-up of ray r (Algorithm 1 "Initialize")
+  auto start = [&](int r) {
+    ray = (unsigned)(a.ray_offset + (unsigned long long)r);
     const uint4 u = philox10(make_uint4(cell, ray, 0u, a.snapshot), a.key0, a.key1);
 
     // direction: hemisphere of the y axis by the integer count `hemi` of 2^23,
@@ -211,18 +232,20 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     R sphi, cphi;
     Prec<R>::sincospi_((R)2 * unif<R>(u.y), &sphi, &cphi);
     const R st = sqrt(fmax((R)0, (R)1 - mu * mu));
-    R ddx = st * cphi, ddy = mu, ddz = st * sphi;
+    ddx = st * cphi;
+    ddy = mu;
+    ddz = st * sphi;
 
     // band and quadrature point from two words (Eq. 17); weight w_g / (p q)
-    const int n = pick(cn, nb, u.z);
+    n = pick(cn, nb, u.z);
     const unsigned long long *cgn = cg + (size_t)n * ng;
     const int g = pick(cgn, ng, u.w);
     const unsigned long long mn = cn[n] - (n ? cn[n - 1] : 0ull);
     const unsigned long long mg = cgn[g] - (g ? cgn[g - 1] : 0ull);
-    const R wgt = ray_weight<R>(a, plain, n, g, mn, mg, ph);
+    wgt = ray_weight<R>(a, plain, n, g, mn, mg, ph);
 
     // origin: uniform in the cell (block 1 draws) or the centre
-    R fx = (R)0.5, fy = (R)0.5, fz = (R)0.5;
+    fx = fy = fz = (R)0.5;
     if (a.origin == 0) {
       const uint4 v = philox10(make_uint4(cell, ray, 1u, a.snapshot), a.key0, a.key1);
       fx = unif<R>(v.x);
@@ -230,34 +253,57 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
       fz = unif<R>(v.z);
     }
 
-    const size_t krow = (size_t)(n * ng + g) * nT;
-    const size_t brow = (size_t)n * nT;
+    krow = (size_t)(n * ng + g) * nT;
+    brow = (size_t)n * nT;
     const R2 ki = __ldg(ktab + krow + it_i);
     const R2 bi = __ldg(btab + brow + it_i);
-    const R kap_i = (ki.x + fr_i * ki.y) * xr_i;
-    const R B_i = bi.x + fr_i * bi.y;
+    kap_i = (ki.x + fr_i * ki.y) * xr_i;
+    B_i = bi.x + fr_i * bi.y;
 
-    // ---- march (Algorithm 1) ----
-    int ix = ci, iy = cj, iz = ck, lin = (int)cell;
-    int sx, sy_, sz;
-    R t0x, t0y, t0z, tsx, tsy, tsz;
+    // the march starts in the emitting cell on the finest grid
+    ix = ci;
+    iy = cj;
+    iz = ck;
+    lin = (int)cell;
     axis_setup<R>(ddx, fx, DX, sx, t0x, tsx);
     axis_setup<R>(ddy, fy, yfs ? dyl(cj, 0) : DY, sy_, t0y, tsy);
     axis_setup<R>(ddz, fz, DZ, sz, t0z, tsz);
     // stretched y: tsy is 1/|d_y|, and each y crossing adds the next row's height
     if (yfs && sy_ != 0) tsy = (R)1 / fabs(ddy);
-    R cntx = 0, cnty = 0, cntz = 0;
-    R tnx = t0x, tny = t0y, tnz = t0z, tprev = 0;
-    R X = 0, tau = 1, B_last = B_i;
-    int steps = 0;
-    unsigned nrefl = 0;
-    // multigrid (Section 4.3): current grid, its dimensions and the offset of its
-    // fields, segments marched on it, and the face counter step: grid l keeps
-    // every inc-th face of the grid the axis parameters were set up on
-    int lev = 0, lsteps = 0, nxl = nx, nyl = ny, nzl = nz;
-    long long loff = 0;
-    R inc = 1;
-    for (;;) {
+    cntx = cnty = cntz = 0;
+    tnx = t0x;
+    tny = t0y;
+    tnz = t0z;
+    tprev = 0;
+    X = 0;
+    tau = 1;
+    B_last = B_i;
+    steps = 0;
+    nrefl = 0;
+    lev = 0;
+    lsteps = 0;
+    nxl = nx;
+    nyl = ny;
+    nzl = nz;
+    loff = 0;
+    inc = 1;
+  };
+  int r = lane;
+  bool live = r < a.rays;  // the lane holds a ray (marching, or waiting to start it)
+  bool wait = live;        // the lane's next ray is not set up yet
+  while (__any_sync(0xffffffffu, live)) {
+    // the waiting lanes set up their rays together once START_LANES of them
+    // wait or none marches: the set-up's binary64 work then runs on more lanes
+    const unsigned wm = __ballot_sync(0xffffffffu, wait);
+    const unsigned mm = __ballot_sync(0xffffffffu, live && !wait);
+    if (wm && (__popc(wm) >= START_LANES || mm == 0) && wait) {
+      start(r);
+      wait = false;
+    }
+    if (!live || wait) continue;
+    // one segment of the march (Algorithm 1 "March")
+    bool end = false;
+    do {
       int ax;
       R tn;
       if (tnx <= tny && tnx <= tnz) {
@@ -286,10 +332,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
       B_last = Bj;
       ++steps;
       ++lsteps;
-      if (tau <= tol) break;
+      if (tau <= tol) { end = true; break; }
       if (steps >= a.max_steps) {
         ++ncap;
-        break;
+        {
+          end = true;
+          break;
+        }
       }
       tprev = tn;
       const int nxyl = nxl * nyl;
@@ -301,7 +350,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
         X += (B_i - __ldg(bwall + f * nb + n)) * tau;
         tau = 0;
         ++nwall;
-        break;
+        {
+          end = true;
+          break;
+        }
       }
       if (ax == 0) {
         cntx += inc;
@@ -341,7 +393,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
           X += (B_i - Bw) * (tau * eps);
           tau *= (R)1 - eps;
           ++nwall;
-          if (eps >= (R)1 || tau <= tol) break;
+          if (eps >= (R)1 || tau <= tol) { end = true; break; }
           // reflect from the crossing point at t = tprev (fractions of the
           // current grid's cell, whose extent along an axis is inc face steps)
           R nfx = fx, nfz = fz;
@@ -418,12 +470,16 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
         ++lev;
         lsteps = 0;
       }
-    }
+    } while (false);
+    if (!end) continue;
     if (tau > (R)0) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
 
     tally.add(wgt * (kap_i * X));
     nsteps += (unsigned long long)steps;
     max_ray = max(max_ray, (unsigned long long)steps);
+    r += 32;
+    live = r < a.rays;
+    wait = live;
   }
 
   // warp reduction of the lanes' tallies

@@ -126,7 +126,7 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   const int G = mcrt::fp32_guide_size();
   std::vector<unsigned short> guide(G);
   for (int m = 0, k = 0; m < G; ++m) {
-    const unsigned long long lo = (unsigned long long)m << (32 - 6);
+    const unsigned long long lo = (unsigned long long)m << (32 - mcrt::fp32_guide_bits());
     while (cn[k] <= lo) ++k;
     guide[m] = (unsigned short)k;
   }
@@ -890,7 +890,7 @@ int noalloc_build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   static unsigned long long cn[1024], cg[1024 * 64];
   static double wn[1024], wgv[64], wtmp[64];
   static float w32[1024 * 64];
-  static unsigned short guide[64];
+  static unsigned short guide[4096];  // at least fp32_guide_size() entries
   std::lock_guard<std::mutex> lock(mu);
   const int nb = ctx->nb, ng = ctx->ng, nT = ctx->nT;
   for (int n = 0; n < nb; ++n) {
@@ -917,7 +917,7 @@ int noalloc_build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
     }
   const int G = mcrt::fp32_guide_size();
   for (int m = 0, k = 0; m < G; ++m) {
-    const unsigned long long lo = (unsigned long long)m << (32 - 6);
+    const unsigned long long lo = (unsigned long long)m << (32 - mcrt::fp32_guide_bits());
     while (cn[k] <= lo) ++k;
     guide[m] = (unsigned short)k;
   }

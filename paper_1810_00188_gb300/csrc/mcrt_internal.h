@@ -210,6 +210,7 @@ cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int 
 int fp32_brick_volume();
 int fp32_cell_stage_fits(int nb, int ng);
 int fp32_guide_size();
+int fp32_guide_bits();  // guide[m] covers R_n in [m, m + 1) 2^(32 - bits)
 
 // Static device scratch of the allocation-free solve (noalloc.cu): its size,
 // and its device address on `device` (the current device), looked up once per

@@ -17,7 +17,8 @@ namespace {
 constexpr int POOL = 64;   // prepared ray states per warp
 constexpr int WARPS = 8;   // warps per CTA
 constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks
-constexpr int GUIDE = 64;  // guide-table buckets of the band CDF
+constexpr int GUIDE_BITS = 11;           // the top bits of R_n that index the guide table
+constexpr int GUIDE = 1 << GUIDE_BITS;   // guide-table buckets of the band CDF
 constexpr int REFILL = 8;  // idle lanes of a warp before they take prepared rays
 
 struct WarpRing {
@@ -67,10 +68,11 @@ __device__ __forceinline__ void sincos_2pi(float u, float &s, float &c) {
 }
 
 // First k with u < cum[k] (the inverse CDF of Eq. 17), started from a guide
-// table: guide[m] = first k with cum[k] > m 2^26, so the scan is short.
+// table: guide[m] = first k with cum[k] > m 2^(32 - GUIDE_BITS), so the scan
+// is short.
 __device__ __forceinline__ int pick_guided(const unsigned long long *__restrict__ cum,
                                            const unsigned short *__restrict__ guide, unsigned u) {
-  int k = guide[u >> 26];
+  int k = guide[u >> (32 - GUIDE_BITS)];
   while ((unsigned long long)u >= cum[k]) ++k;
   return k;
 }

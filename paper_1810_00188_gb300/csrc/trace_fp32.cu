@@ -587,6 +587,8 @@ int fp32_brick_volume() { return BRICK * BRICK * BRICK; }
 
 int fp32_guide_size() { return GUIDE; }
 
+int fp32_guide_bits() { return GUIDE_BITS; }
+
 // Ring states, then (bit 0) the plain counts and guide table or (bit 1) one
 // cell's counts per warp.
 static size_t fp32_smem_bytes(int nb, int ng, int counts_in_smem) {

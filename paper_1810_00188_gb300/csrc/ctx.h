@@ -40,7 +40,7 @@ struct mcrt_ctx {
   double p0_T_max = -1;  // T_max that p0_host / p0_32 were built for
   // device buffers
   DevBuf field64, fpos32, ktab64, ktab32, kbtab32, btab64, btab32, bwall64, bwall32, wg, wg32, wgt32, cn, cg,
-      guide, ybuf, step_acc,
+      guide, gguide, ybuf, step_acc,
       cell_cn, cell_cg, cell_hemi, counters, fstats, q, sigma, steps;
   // learned proposal: plain probabilities, feature scratch, per-ray steps, error flag
   DevBuf p0_32, feat, ray_steps, lerr, kptab;

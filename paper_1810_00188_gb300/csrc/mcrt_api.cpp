@@ -138,6 +138,16 @@ int build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   CK(cudaMemcpyAsync(ctx->cg.p, cg.data(), sizeof(unsigned long long) * nb * ng,
                      cudaMemcpyHostToDevice, s),
      "upload g counts");
+  // g guides of the bands: gg[n][m] = first g with cum_g(n) > m 2^(32 - bits)
+  const int GGn = mcrt::fp32_gguide_size(), ggb = mcrt::fp32_gguide_bits();
+  std::vector<unsigned char> gg((size_t)nb * GGn);
+  for (int n = 0; n < nb; ++n)
+    for (int m = 0, k = 0; m < GGn; ++m) {
+      const unsigned long long lo = (unsigned long long)m << (32 - ggb);
+      while (cg[(size_t)n * ng + k] <= lo) ++k;
+      gg[(size_t)n * GGn + m] = (unsigned char)k;
+    }
+  CK(cudaMemcpyAsync(ctx->gguide.p, gg.data(), gg.size(), cudaMemcpyHostToDevice, s), "upload g guides");
   // pageable sources: the copies are staged before cudaMemcpyAsync returns
   ctx->prop_valid = true;
   ctx->prop_T_max = Tm;
@@ -302,8 +312,9 @@ void fill_trace_args(const mcrt_ctx *ctx, const mcrt_solve_params *p, const int 
   a.w_g = (const double *)ctx->wg.p;
   a.wgt32 = (const float *)ctx->wgt32.p;
   a.w_g32 = (const float *)ctx->wg32.p;
-  a.counts_in_smem = (size_t)(ctx->nb + ctx->nb * ctx->ng) * 8 <= 48 * 1024 ? 1 : 0;
+  a.counts_in_smem = mcrt::fp32_plain_stage_fits(ctx->nb, ctx->ng) ? 1 : 0;
   a.guide = (const unsigned short *)ctx->guide.p;
+  a.gguide = (const unsigned char *)ctx->gguide.p;
   a.cn = (const unsigned long long *)ctx->cn.p;
   a.cg = (const unsigned long long *)ctx->cg.p;
   if (p->proposal == MCRT_PROPOSAL_CELL) {
@@ -502,6 +513,7 @@ int mcrt_set_kdist(mcrt_ctx *ctx, const mcrt_kdist_desc *kd_in) {
   CK(ensure(ctx->cg, (size_t)nb * ng * sizeof(unsigned long long)), "alloc g counts");
   CK(ensure(ctx->wgt32, (size_t)nb * ng * sizeof(float)), "alloc weights");
   CK(ensure(ctx->guide, (size_t)mcrt::fp32_guide_size() * sizeof(unsigned short)), "alloc guide");
+  CK(ensure(ctx->gguide, (size_t)nb * mcrt::fp32_gguide_size()), "alloc g guides");
   CK(cudaMemcpy(ctx->ktab64.p, k64.data(), nk * sizeof(double2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->ktab32.p, k32.data(), nk * sizeof(float2), cudaMemcpyHostToDevice), "copy");
   CK(cudaMemcpy(ctx->btab64.p, b64.data(), nbT * sizeof(double2), cudaMemcpyHostToDevice), "copy");
@@ -862,7 +874,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
     DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->fstage, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
-                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->ybuf, &ctx->step_acc,
+                      &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->gguide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
                       &ctx->p0_32, &ctx->feat, &ctx->ray_steps, &ctx->lerr, &ctx->kptab, &ctx->qprop};
@@ -891,6 +903,7 @@ int noalloc_build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   static double wn[1024], wgv[64], wtmp[64];
   static float w32[1024 * 64];
   static unsigned short guide[4096];  // at least fp32_guide_size() entries
+  static unsigned char gg[1024 * 32];  // at least n_bands x fp32_gguide_size()
   std::lock_guard<std::mutex> lock(mu);
   const int nb = ctx->nb, ng = ctx->ng, nT = ctx->nT;
   for (int n = 0; n < nb; ++n) {
@@ -927,6 +940,14 @@ int noalloc_build_plain_proposal(mcrt_ctx *ctx, double Tm, cudaStream_t s) {
   CK(cudaMemcpyAsync(ctx->cn.p, cn, sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s), "counts");
   CK(cudaMemcpyAsync(ctx->cg.p, cg, sizeof(unsigned long long) * nb * ng, cudaMemcpyHostToDevice, s),
      "counts");
+  const int GGn = mcrt::fp32_gguide_size(), ggb = mcrt::fp32_gguide_bits();
+  for (int n = 0; n < nb; ++n)
+    for (int m = 0, k = 0; m < GGn; ++m) {
+      const unsigned long long lo = (unsigned long long)m << (32 - ggb);
+      while (cg[(size_t)n * ng + k] <= lo) ++k;
+      gg[(size_t)n * GGn + m] = (unsigned char)k;
+    }
+  CK(cudaMemcpyAsync(ctx->gguide.p, gg, (size_t)nb * GGn, cudaMemcpyHostToDevice, s), "g guides");
   ctx->prop_valid = true;
   ctx->prop_T_max = Tm;
   return MCRT_OK;
@@ -1152,8 +1173,9 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     a.wgt32 = (const float *)c->wgt32.p;
     a.cn = (const unsigned long long *)c->cn.p;
     a.cg = (const unsigned long long *)c->cg.p;
-    a.counts_in_smem = (size_t)(c->nb + c->nb * c->ng) * 8 <= 48 * 1024 ? 1 : 0;
+    a.counts_in_smem = mcrt::fp32_plain_stage_fits(c->nb, c->ng) ? 1 : 0;
     a.guide = (const unsigned short *)c->guide.p;
+    a.gguide = (const unsigned char *)c->gguide.p;
     if (p->proposal == MCRT_PROPOSAL_CELL) {
       a.cell_cn = (const unsigned long long *)c->cell_cn.p;
       a.cell_cg = (const unsigned long long *)c->cell_cg.p;

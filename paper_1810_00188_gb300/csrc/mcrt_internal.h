@@ -88,7 +88,8 @@ struct TraceArgs {
   const unsigned int *cell_hemi;      // [ncells] count of 2^23, or null (plain: 2^22)
   int counts_in_smem;                 // bit 0: plain counts staged in shared memory (<= 48 KB);
                                       // bit 1: per-cell counts staged per warp (<= 48 KB)
-  const unsigned short *guide;        // [64] guide table of the plain band counts
+  const unsigned short *guide;        // [fp32_guide_size()] guide table of the plain band counts
+  const unsigned char *gguide;        // [nb][fp32_gguide_size()] the plain g counts' guides
   // FP32 kernel: brick-order positions [chunk_p0, chunk_p1) of this launch, the
   // per-ray sample scratch [(p - chunk_p0) * rays + r] and per-position step sums
   long long chunk_p0, chunk_p1;
@@ -211,6 +212,10 @@ int fp32_brick_volume();
 int fp32_cell_stage_fits(int nb, int ng);
 int fp32_guide_size();
 int fp32_guide_bits();  // guide[m] covers R_n in [m, m + 1) 2^(32 - bits)
+int fp32_gguide_size();  // g guide entries per band
+int fp32_gguide_bits();
+// the plain proposal's counts, guide and g guides fit the FP32 kernel's shared staging
+int fp32_plain_stage_fits(int nb, int ng);
 
 // Static device scratch of the allocation-free solve (noalloc.cu): its size,
 // and its device address on `device` (the current device), looked up once per

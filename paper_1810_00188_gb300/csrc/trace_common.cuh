@@ -19,6 +19,8 @@ constexpr int WARPS = 8;   // warps per CTA
 constexpr int BRICK = 8;   // cells are enumerated in 8x8x8 bricks
 constexpr int GUIDE_BITS = 11;           // the top bits of R_n that index the guide table
 constexpr int GUIDE = 1 << GUIDE_BITS;   // guide-table buckets of the band CDF
+constexpr int GG_BITS = 5;               // the top bits of R_g that index a band's g guide
+constexpr int GG = 1 << GG_BITS;         // g guide entries per band (bytes)
 constexpr int REFILL = 8;  // idle lanes of a warp before they take prepared rays
 
 struct WarpRing {
@@ -73,6 +75,15 @@ __device__ __forceinline__ void sincos_2pi(float u, float &s, float &c) {
 __device__ __forceinline__ int pick_guided(const unsigned long long *__restrict__ cum,
                                            const unsigned short *__restrict__ guide, unsigned u) {
   int k = guide[u >> (32 - GUIDE_BITS)];
+  while ((unsigned long long)u >= cum[k]) ++k;
+  return k;
+}
+
+// First g with u < cum[g] within one band's g counts (Eq. 17), started from the
+// band's guide: gg[m] = first g with cum[g] > m 2^(32 - GG_BITS).
+__device__ __forceinline__ int pick_gguided(const unsigned long long *__restrict__ cum,
+                                            const unsigned char *__restrict__ gg, unsigned u) {
+  int k = gg[u >> (32 - GG_BITS)];
   while ((unsigned long long)u >= cum[k]) ++k;
   return k;
 }

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   // cell at a time (bit 1), in the same space
   const unsigned long long *s_cn = a.cn, *s_cg = a.cg;
   const unsigned short *s_guide = a.guide;
+  const unsigned char *s_gg = a.gguide;
   const bool cell_stage = !plain && (a.counts_in_smem & 2);
   unsigned long long *w_cn = reinterpret_cast<unsigned long long *>(smem_raw + WARPS * sizeof(WarpRing)) +
                              (size_t)(threadIdx.x >> 5) * (a.nb + a.nb * a.ng);
@@ -81,9 +82,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
     for (int i = threadIdx.x; i < ncount; i += blockDim.x)
       cn_sh[i] = i < a.nb ? a.cn[i] : a.cg[i - a.nb];
     for (int i = threadIdx.x; i < GUIDE; i += blockDim.x) g_sh[i] = a.guide[i];
+    unsigned char *gg_sh = reinterpret_cast<unsigned char *>(g_sh + GUIDE);
+    for (int i = threadIdx.x; i < a.nb * GG; i += blockDim.x) gg_sh[i] = a.gguide[i];
     s_cn = cn_sh;
     s_cg = cn_sh + a.nb;
     s_guide = g_sh;
+    s_gg = gg_sh;
   }
   __syncthreads();
 
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
           float wgt;
           if (plain) {
             nn = pick_guided(s_cn, s_guide, u.z);
-            gg = pick(s_cg + nn * ng, ng, u.w);
+            gg = pick_gguided(s_cg + nn * ng, s_gg + nn * GG, u.w);
           } else if (cell_stage) {
             hemi = c_hemi;
             nn = pick(w_cn, nb, u.z);
@@ -589,11 +593,20 @@ int fp32_guide_size() { return GUIDE; }
 
 int fp32_guide_bits() { return GUIDE_BITS; }
 
+int fp32_gguide_size() { return GG; }
+
+int fp32_gguide_bits() { return GG_BITS; }
+
+int fp32_plain_stage_fits(int nb, int ng) {
+  return sizeof(unsigned long long) * (size_t)(nb + nb * ng) + sizeof(unsigned short) * GUIDE + (size_t)nb * GG <=
+         48 * 1024;
+}
+
 // Ring states, then (bit 0) the plain counts and guide table or (bit 1) one
 // cell's counts per warp.
 static size_t fp32_smem_bytes(int nb, int ng, int counts_in_smem) {
   const size_t rows = sizeof(unsigned long long) * (size_t)(nb + nb * ng);
-  const size_t plain = (counts_in_smem & 1) ? rows + sizeof(unsigned short) * GUIDE : 0;
+  const size_t plain = (counts_in_smem & 1) ? rows + sizeof(unsigned short) * GUIDE + (size_t)nb * GG : 0;
   const size_t cell = (counts_in_smem & 2) ? WARPS * rows : 0;
   return WARPS * sizeof(WarpRing) + (plain > cell ? plain : cell);
 }

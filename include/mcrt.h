@@ -53,8 +53,9 @@ enum { MCRT_MEM_HOST = 0, MCRT_MEM_DEVICE = 1 };
 /* MCRT_FP32: traversal, table lookups, exp, the ray weight (a binary64 host
  * table rounded once) and each ray's sample Y in binary32; the per-cell tallies
  * sum Y and Y^2 in binary64 with Neumaier compensation (runs of 32 samples
- * summed exactly first; mcrt_tuning.tally_binary32 selects compensated binary32
- * pairs instead).  MCRT_FP64: everything binary64. */
+ * summed exactly first, the runs added in segments of up to 64 and the segments
+ * in order; mcrt_tuning.tally_binary32 selects compensated binary32 pairs
+ * instead).  MCRT_FP64: everything binary64. */
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
 /* Ray origin: uniform in the cell volume (f_V = 1/V_i, Eq. 4) or the cell centre
  * (Algorithm 1, "ray.pos <- cell.center"). */
@@ -211,10 +212,12 @@ typedef struct {
                               flight for a hand-off; < 0: any flight            */
   int tally_binary32;      /* 0 (default): binary64 per-cell tallies -- each run
                               of 32 samples of a cell summed exactly, the runs
-                              added with Neumaier's compensated binary64 sum
-                              (within about 2^-51 of sum |Y| of the exact sum
-                              of the samples); 1: compensated binary32 pairs
-                              (within about 2e-7 of sum |Y|), a little cheaper */
+                              added with Neumaier's compensated binary64 sum in
+                              segments of up to 64 runs, the segments added the
+                              same way (within about 2^-51 of sum |Y| of the
+                              exact sum of the samples); 1: compensated binary32
+                              pairs (within about 2e-7 of sum |Y|), a little
+                              cheaper */
   int tally_plain_loads;   /* 0 (default): the binary64 tallies read the samples
                               through the tensor memory accelerator (tiled bulk
                               copies into shared memory) where their layout

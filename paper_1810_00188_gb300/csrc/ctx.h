@@ -54,6 +54,8 @@ struct mcrt_ctx {
   DevBuf armcbuf;
   // mcrt_set_fields from host memory: the device copy of T and x before packing
   DevBuf fstage;
+  // binary64 tallies of cells with more than one segment: the segments' sums
+  DevBuf tpart;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-kernel marks of the last FP32 solve: four events per chunk (launch_trace_fp32)
   std::vector<cudaEvent_t> kev;

@@ -442,9 +442,10 @@ int mcrt_tally_moments(mcrt_ctx *ctx, const mcrt_solve_params *p, const int32_t 
   for (long long p0 = 0; p0 < P; p0 += Pc) {
     a.chunk_p0 = t.chunk_p0 = p0;
     a.chunk_p1 = t.chunk_p1 = p0 + Pc < P ? p0 + Pc : P;
-    CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s), "trace launch");
+    int kn = 0;
+    CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s, nullptr, &kn), "trace launch");
     CK(mcrt::launch_tally(t, s), "tally launch");
-    launches += mcrt::long_rays_on(a) ? 4 : 3;
+    launches += kn + 1;
   }
   CK(cudaEventRecord(ctx->ev1, s), "event");
   ctx->last_launches = launches;

@@ -714,6 +714,13 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     CK(ensure(ctx->step_acc, (size_t)Pc * sizeof(unsigned long long)), "alloc step scratch");
     a.ybuf = (float *)ctx->ybuf.p;
     a.step_acc = (unsigned long long *)ctx->step_acc.p;
+    // cells of more than one tally segment: each segment summed by a warp of its own
+    const int nseg = mcrt::tally_segments((p->rays_per_cell + 31) / 32);
+    a.tally_part = nullptr;
+    if (nseg > 1 && !ctx->tally32) {
+      CK(ensure(ctx->tpart, (size_t)Pc * (size_t)nseg * sizeof(double2)), "alloc tally segments");
+      a.tally_part = (double2 *)ctx->tpart.p;
+    }
     const int rl = setup_long_rays(ctx, Pc * (long long)p->rays_per_cell, &a);
     if (rl != MCRT_OK) return rl;
     const bool armc = p->estimator != MCRT_EST_ERMC;
@@ -744,11 +751,12 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
       if (dst)
         CK(cudaMemsetAsync(ctx->step_acc.p, 0, (size_t)(a.chunk_p1 - p0) * sizeof(unsigned long long), s),
            "clear step scratch");
+      int kn = 0;
       CK(mcrt::launch_trace_fp32(a, ctx->min_blocks, ctx->steps_per_round, s,
-                                 ctx->kev.data() + 4 * ctx->kev_chunks),
+                                 ctx->kev.data() + 4 * ctx->kev_chunks, &kn),
          "trace launch");
       ++ctx->kev_chunks;
-      launches += mcrt::long_rays_on(a) ? 3 : 2;
+      launches += kn;
     }
     if (armc) {
       CK(mcrt::launch_armc_finalize(a.armc_acc, a.ermc_acc, ncg, p->rays_per_cell < 16 ? p->rays_per_cell : 16,
@@ -873,7 +881,7 @@ int mcrt_destroy(mcrt_ctx *ctx) {
   {
     DeviceGuard dg(ctx->grid.device);
     cudaDeviceSynchronize();
-    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->fstage, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
+    DevBuf *bufs[] = {&ctx->yf64, &ctx->yf32, &ctx->longbuf, &ctx->armcbuf, &ctx->fstage, &ctx->tpart, &ctx->field64, &ctx->fpos32, &ctx->ktab64, &ctx->ktab32, &ctx->kbtab32, &ctx->btab64,
                       &ctx->btab32, &ctx->bwall64, &ctx->bwall32, &ctx->wg, &ctx->wg32, &ctx->wgt32, &ctx->cn, &ctx->guide, &ctx->gguide, &ctx->ybuf, &ctx->step_acc,
                       &ctx->cg, &ctx->cell_cn, &ctx->cell_cg, &ctx->cell_hemi,
                       &ctx->counters, &ctx->fstats, &ctx->q, &ctx->sigma, &ctx->steps,
@@ -1395,8 +1403,9 @@ extern "C" int mcrt_batch_create(const mcrt_batch_item *items, int n, const mcrt
     for (long long p0 = 0; p0 < P[k] && ce == cudaSuccess; p0 += Pc[k]) {
       args[k].chunk_p0 = p0;
       args[k].chunk_p1 = p0 + Pc[k] < P[k] ? p0 + Pc[k] : P[k];
-      ce = mcrt::launch_trace_fp32(args[k], c0->min_blocks, c0->steps_per_round, sk);
-      launches += mcrt::long_rays_on(args[k]) ? 3 : 2;
+      int kn = 0;
+      ce = mcrt::launch_trace_fp32(args[k], c0->min_blocks, c0->steps_per_round, sk, nullptr, &kn);
+      launches += kn;
     }
   }
   for (int j = 1; j < streams && ce == cudaSuccess; ++j) {

@@ -136,6 +136,11 @@ struct TraceArgs {
   // FP32 kernels: per-cell tallies in binary32 pairs (1) instead of binary64 (0);
   // binary64 tallies read by plain loads (1) instead of the TMA-fed kernel (0)
   int tally32, reduce_plain;
+  // binary64 tallies of more than one segment (tally_segments): each segment's
+  // sums by a warp of their own, [segment][chunk position] {sum y, sum y^2},
+  // then added in order by a second kernel (null: one warp adds a cell's
+  // segments in order; the same bits)
+  double2 *tally_part;
   // absorption-based estimate (null: off): per-batch binary64 sums [16][armc_nc]
   // of the deposits into each cell and of each cell's own samples
   double *armc_acc, *ermc_acc;
@@ -146,6 +151,21 @@ struct TraceArgs {
                                  // [8] long rays finished by the warp-parallel march
                                  // [9] long rays that found the buffer full (NCOUNTERS entries)
 };
+
+// Segments of the binary64 per-cell tally (Eq. 8).  A cell's N samples form
+// tiles of 32; its sums are the compensated sum, in order, of the sums of
+// consecutive runs of tally_seg_len tiles, each itself a compensated sum of the
+// runs' exact tile sums in order.  The split depends on N alone (up to
+// TALLY_SEG_TILES tiles per run, runs of equal length but for the last), so any
+// kernel that follows it gives the same bits; N <= 32 TALLY_SEG_TILES is one run.
+constexpr int TALLY_SEG_TILES = 64;
+__host__ __device__ inline int tally_segments(int ntile) {
+  return ntile > 0 ? (ntile + TALLY_SEG_TILES - 1) / TALLY_SEG_TILES : 0;
+}
+__host__ __device__ inline int tally_seg_len(int ntile) {
+  const int n = tally_segments(ntile);
+  return n > 0 ? (ntile + n - 1) / n : 0;
+}
 
 // Largest grid of the grid-stride kernels (reductions, packing, coarsening): 16
 // CTAs per SM of the current device (its SM count read once per device).
@@ -170,13 +190,17 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s);
 // marks (nullable): four events recorded on s before the trace kernel, after it,
 // after the long-ray march (right after the trace kernel when there is none) and
 // after the reduction.
+// kernels (nullable): the number of kernels launched.
 cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_round,
-                              cudaStream_t s, cudaEvent_t *marks = nullptr);
+                              cudaStream_t s, cudaEvent_t *marks = nullptr, int *kernels = nullptr);
 // The binary64 per-cell tallies of one FP32 solve chunk with the samples
 // streamed by TMA (tally_tma.cu; the same results as reduce_cells_kernel).
 // Launches nothing and leaves *launched false when the samples' layout does not
 // allow the tiled copy (rays % 4 != 0) or the driver has no tensor-map encoder.
-cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, bool *launched);
+// *kernels: the kernels it launched (0: none, the caller then tallies by plain
+// loads; 2 when the segments of each cell are summed by warps of their own,
+// a.tally_part non-null, and added by a second kernel).
+cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, int *kernels);
 // Q and sigma of the absorption-based estimate (hybrid = 0) or of its
 // temperature-weighted combination with the emission-based one (hybrid = 1) from
 // the per-batch sums of the AR trace launches; K batches of N rays per cell.

@@ -6,8 +6,12 @@
 // consecutive positions; its 32-sample tiles ([32 positions][32 samples],
 // 4 KB) arrive by cp.async.bulk.tensor into two shared buffers per warp, so the
 // next tile is in flight while lane c adds its position's 32 samples exactly
-// (tile_sums_exact) and compensates the tile sums (Neumaier): the same
-// arithmetic in the same order as reduce_cells_kernel, hence the same bits.
+// (tile_sums_exact) and compensates the tile sums (Neumaier) segment by segment:
+// the same arithmetic in the same order as reduce_cells_kernel, hence the same
+// bits.  Cells of several segments (more than 2048 samples) have each segment
+// summed by a warp of its own when the caller provides the segment scratch
+// (a.tally_part), and combine_segments_kernel adds the segments in order: a chunk
+// of few cells with many rays each is then spread over the whole GPU.
 // The tiles are written with the 128-byte swizzle (16-byte chunk j of row r
 // lands at chunk j ^ (r mod 8)), so each lane's reads of its own row are free of
 // bank conflicts.  Samples past N and positions past the chunk come in as zeros
@@ -74,7 +78,18 @@ __device__ __forceinline__ void tma_tile(void *dst, const CUtensorMap *map, int 
       : "memory");
 }
 
-__global__ void __launch_bounds__(TW * 32, 3) reduce_cells_tma_kernel(const TraceArgs a,
+// The work of a warp is a sequence of items: an item is a group of 32
+// consecutive positions and either all of their tiles or, in a split tally
+// (MODE 2: a.tally_part non-null and more than one segment), one segment of
+// them, so that cells with many samples are summed by many warps.  MODE 0: one
+// segment (the cell sum is that segment's compensated sum, s + c); MODE 1:
+// several segments added in order by the warp itself.  The items' tiles form one
+// sequence per warp, so the copy of the next tile is in flight across item
+// boundaries too.  A split item's last segment is padded to the common length
+// with tiles past N, which the copy fills with zeros and whose sums (exact
+// zeros) leave the compensated sums unchanged.
+template <int MODE>
+__global__ void __launch_bounds__(TW * 32, MODE == 1 ? 2 : 3) reduce_cells_tma_kernel(const TraceArgs a,
                                                                   const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   // 1024-byte aligned buffers (the swizzle's period), then the barriers
@@ -86,11 +101,14 @@ __global__ void __launch_bounds__(TW * 32, 3) reduce_cells_tma_kernel(const Trac
   const int N = a.rays;
   const long long P = a.chunk_p1 - a.chunk_p0;
   const int ntile = (N + 31) / 32;
+  const int L = MODE == 0 ? ntile : tally_seg_len(ntile);
+  const int ipg = MODE == 2 ? tally_segments(ntile) : 1;  // items per group
+  const int ilen = MODE == 2 ? L : ntile;                  // tiles per item
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long ngroups = (P + 31) / 32;
-  const long long mygroups = gw < ngroups ? (ngroups - gw + nwarps - 1) / nwarps : 0;
-  const long long T = mygroups * ntile;  // this warp's tiles, group by group
+  const long long nitems = ((P + 31) / 32) * ipg;
+  const long long myitems = gw < nitems ? (nitems - gw + nwarps - 1) / nwarps : 0;
+  const long long T = myitems * ilen;  // this warp's tiles, item by item
   if (T == 0) return;
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -98,27 +116,40 @@ __global__ void __launch_bounds__(TW * 32, 3) reduce_cells_tma_kernel(const Trac
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  auto issue = [&](long long t) {  // lane 0: tile t into buffer t & 1
-    const long long g = gw + (t / ntile) * nwarps;
-    const int r0 = (int)(t % ntile) * 32;
+  // the copy cursor (lane 0): the tile after the last one issued, as the
+  // item's group row, its first tile and the tile within the item
+  long long ci = gw;  // item of the copy cursor
+  int ct = 0, cy = 0, cx0 = 0;
+  auto cursor_item = [&]() {
+    cy = (int)((ci / ipg) * 32);
+    cx0 = (int)(ci % ipg) * L;
+  };
+  cursor_item();
+  auto issue = [&](long long t) {  // lane 0: the cursor's tile (tile t) into buffer t & 1
     uint64_t *b = bar + (t & 1);
     mbar_expect_tx(b, TILE_BYTES);
-    tma_tile(buf + (t & 1) * TILE_BYTES, &tmap, r0, (int)(g * 32), b);
+    tma_tile(buf + (t & 1) * TILE_BYTES, &tmap, (cx0 + ct) * 32, cy, b);
+    if (++ct == ilen) {
+      ct = 0;
+      ci += nwarps;
+      cursor_item();
+    }
   };
   if (lane == 0) {
     issue(0);
     if (T > 1) issue(1);
   }
-  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
+  double S = 0.0, C = 0.0, S2 = 0.0, C2 = 0.0;  // over segments (MODE 1)
+  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;  // within the current segment
   bool bad = false, mine = false;
   int bx = 0, by = 0, bz = 0;
+  long long i = gw, p = 0;  // the item being summed and the lane's position
+  int tt = 0;               // tile within the item
   for (long long t = 0; t < T; ++t) {
-    const long long g = gw + (t / ntile) * nwarps;
-    const int tile = (int)(t % ntile);
-    if (tile == 0) {  // a new group of 32 positions
-      const long long p = g * 32 + lane;
+    if (tt == 0) {  // a new item
+      p = (i / ipg) * 32 + lane;
       mine = p < P && brick_cell(a, a.chunk_p0 + p, bx, by, bz);
-      s = c = s2 = c2 = 0.0;
+      S = C = S2 = C2 = s = c = s2 = c2 = 0.0;
       bad = false;
     }
     if (!mbar_wait(bar + (t & 1), (unsigned)((t >> 1) & 1))) {
@@ -151,16 +182,68 @@ __global__ void __launch_bounds__(TW * 32, 3) reduce_cells_tma_kernel(const Trac
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(t + 2);
     }
-    if (tile == ntile - 1 && mine) {
-      const double S = bad ? __longlong_as_double(0x7FF8000000000000ll) : s + c;
-      const double S2 = bad ? S : s2 + c2;
-      const long long cell = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
-      const double Nd = (double)N;
-      const double Q = S / Nd;
-      a.q[cell] = Q;
-      if (a.sigma) a.sigma[cell] = N > 1 ? sqrt(fmax(S2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
-      if (a.steps_cell) a.steps_cell[cell] = a.step_acc[g * 32 + lane];
+    const bool last = tt == ilen - 1;
+    if (mine) {
+      if (MODE == 2) {
+        if (last) {  // the item is one segment: its sums, for the second kernel
+          const double nan = __longlong_as_double(0x7FF8000000000000ll);
+          a.tally_part[(size_t)(i % ipg) * (size_t)P + (size_t)p] =
+              make_double2(bad ? nan : s + c, bad ? nan : s2 + c2);
+        }
+      } else {
+        if (MODE == 1 && ((tt + 1) % L == 0 || last)) {  // the segment's last tile
+          neumaier_add(S, C, s + c);
+          neumaier_add(S2, C2, s2 + c2);
+          s = c = s2 = c2 = 0.0;
+        }
+        if (last) {
+          const double nan = __longlong_as_double(0x7FF8000000000000ll);
+          const double Sy = bad ? nan : (MODE == 1 ? S + C : s + c);
+          const double Sy2 = bad ? nan : (MODE == 1 ? S2 + C2 : s2 + c2);
+          const long long cell = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
+          const double Nd = (double)N;
+          const double Q = Sy / Nd;
+          a.q[cell] = Q;
+          if (a.sigma) a.sigma[cell] = N > 1 ? sqrt(fmax(Sy2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
+          if (a.steps_cell) a.steps_cell[cell] = a.step_acc[p];
+        }
+      }
     }
+    if (last) {
+      tt = 0;
+      i += nwarps;
+    } else {
+      ++tt;
+    }
+  }
+}
+
+// The second kernel of a split tally: one thread per position adds the
+// segments' sums in order (the same compensated sum as a warp that adds its
+// cell's segments itself) and writes Q and sigma.
+__global__ void __launch_bounds__(256) combine_segments_kernel(const TraceArgs a) {
+  const int N = a.rays;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  const int nseg = tally_segments((N + 31) / 32);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    int bx = 0, by = 0, bz = 0;
+    if (!brick_cell(a, a.chunk_p0 + p, bx, by, bz)) continue;
+    double S = 0.0, C = 0.0, S2 = 0.0, C2 = 0.0;
+    bool bad = false;
+    for (int k = 0; k < nseg; ++k) {
+      const double2 v = a.tally_part[(size_t)k * (size_t)P + (size_t)p];
+      bad |= isnan(v.x);
+      neumaier_add(S, C, v.x);
+      neumaier_add(S2, C2, v.y);
+    }
+    const double Sy = bad ? __longlong_as_double(0x7FF8000000000000ll) : S + C;
+    const double Sy2 = bad ? Sy : S2 + C2;
+    const long long cell = bx + (long long)a.bnx * (by + (long long)a.bny * bz);
+    const double Nd = (double)N;
+    const double Q = Sy / Nd;
+    a.q[cell] = Q;
+    if (a.sigma) a.sigma[cell] = N > 1 ? sqrt(fmax(Sy2 / Nd - Q * Q, 0.0) / (Nd - 1.0)) : 0.0;
+    if (a.steps_cell) a.steps_cell[cell] = a.step_acc[p];
   }
 }
 
@@ -189,8 +272,8 @@ size_t tma_smem_bytes() { return (size_t)TW * 2 * TILE_BYTES + TW * 2 * sizeof(u
 
 }  // namespace
 
-cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, bool *launched) {
-  *launched = false;
+cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, int *kernels) {
+  *kernels = 0;
   const long long P = a.chunk_p1 - a.chunk_p0;
   if (P <= 0 || a.rays < 1 || (a.rays & 3) || (reinterpret_cast<uintptr_t>(a.ybuf) & 15) || P > (1LL << 31))
     return cudaSuccess;
@@ -210,19 +293,38 @@ cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, bool *launched
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    e = cudaFuncSetAttribute(reduce_cells_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(reduce_cells_tma_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reduce_cells_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(reduce_cells_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured[dev] = 1;
   }
   // one group of 32 positions per warp where the grid allows (grid-stride
   // beyond): short blocks spread over whatever SMs are free, which matters when
   // the tally runs beside other solves' kernels in a batch graph
-  const long long groups = (P + 31) / 32;
-  long long blocks = (groups + TW - 1) / TW;
+  const int nseg = tally_segments((a.rays + 31) / 32);
+  const bool split = a.tally_part != nullptr && nseg > 1;
+  const long long items = ((P + 31) / 32) * (split ? nseg : 1);
+  long long blocks = (items + TW - 1) / TW;
   if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
-  reduce_cells_tma_kernel<<<(unsigned)blocks, TW * 32, smem, s>>>(a, map);
+  if (split)
+    reduce_cells_tma_kernel<2><<<(unsigned)blocks, TW * 32, smem, s>>>(a, map);
+  else if (nseg > 1)
+    reduce_cells_tma_kernel<1><<<(unsigned)blocks, TW * 32, smem, s>>>(a, map);
+  else
+    reduce_cells_tma_kernel<0><<<(unsigned)blocks, TW * 32, smem, s>>>(a, map);
   e = cudaGetLastError();
-  if (e == cudaSuccess) *launched = true;
+  if (e != cudaSuccess) return e;
+  *kernels = 1;
+  if (split) {
+    long long cb = (P + 255) / 256;
+    if (cb > grid_stride_blocks()) cb = grid_stride_blocks();
+    combine_segments_kernel<<<(unsigned)cb, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) *kernels = 2;
+  }
   return e;
 }
 

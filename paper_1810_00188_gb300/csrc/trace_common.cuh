@@ -560,11 +560,15 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
 //     are dropped (at most one unit per sample: 2^-57 of the tile's largest |y|,
 //     2^-56 of its largest y^2); 32 terms below 2^58 in magnitude cannot overflow;
 //  2. each tile sum is rounded once to binary64 (the integer-to-binary64
-//     conversion, then an exact power-of-two scaling) and added to the cell's
-//     running sum with Neumaier's compensated summation in binary64.
+//     conversion, then an exact power-of-two scaling) and added to its
+//     segment's running sum with Neumaier's compensated summation in binary64
+//     (a segment: a run of up to 64 consecutive tiles, tally_segments);
+//  3. the segments' sums are added in order the same way (one segment for
+//     N <= 2048: the cell sum is that segment's sum).
 // The result is within about 2^-51 of sum |y| (and of sum y^2) of the exact sums
 // of the binary32 samples -- binary64 quality -- and the order is fixed (samples
-// 0..N-1 of the cell, tile by tile), so it never depends on the launch.
+// 0..N-1 of the cell, tile by tile, segment by segment), so it never depends on
+// the launch, nor on whether a cell's segments are summed by one warp or many.
 
 // s + c += b (Neumaier).  |s| >= |b| is decided on the bit patterns (integer
 // compare of the magnitudes; both finite).
@@ -617,14 +621,18 @@ __device__ __forceinline__ void tile_sums_exact(const unsigned (&v)[32], double 
 // staged through the warp's shared-memory tile ([cell][sample], rows padded to
 // 36 words: the row stores and the lanes' 16-byte row reads are conflict-free)
 // from coalesced loads of each cell's 32 consecutive samples (128 bytes,
-// streaming hint: read once).  Returns the lane's sum of y and of y^2 (NaN when
-// a sample is not finite); lanes without a cell return zeros.
+// streaming hint: read once).  The tiles' exact sums are added in order within
+// each segment (tally_segments), the segments' sums in order across them.
+// Returns the lane's sum of y and of y^2 (NaN when a sample is not finite);
+// lanes without a cell return zeros.
 __device__ __forceinline__ void warp_tally64(const float *__restrict__ y0, int N, unsigned cells, int lane,
                                              float (*tile)[36], double &sum, double &sum2) {
-  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
+  double S = 0.0, C = 0.0, S2 = 0.0, C2 = 0.0;  // over segments
+  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;  // within the current segment
   bool bad = false;
   const bool mine = (cells >> lane) & 1u;
-  for (int r0 = 0; r0 < N; r0 += 32) {
+  const int ntile = (N + 31) / 32, L = tally_seg_len(ntile);
+  for (int r0 = 0, t = 0; r0 < N; r0 += 32, ++t) {
     const bool in = r0 + lane < N;
     float ld[32];
 #pragma unroll
@@ -647,11 +655,16 @@ __device__ __forceinline__ void warp_tally64(const float *__restrict__ y0, int N
       tile_sums_exact(v, t1, t2, bad);
       neumaier_add(s, c, t1);
       neumaier_add(s2, c2, t2);
+      if ((t + 1) % L == 0 || t == ntile - 1) {  // the segment's last tile
+        neumaier_add(S, C, s + c);
+        neumaier_add(S2, C2, s2 + c2);
+        s = c = s2 = c2 = 0.0;
+      }
     }
     __syncwarp();
   }
-  sum = bad ? __longlong_as_double(0x7FF8000000000000ll) : s + c;
-  sum2 = bad ? sum : s2 + c2;
+  sum = bad ? __longlong_as_double(0x7FF8000000000000ll) : S + C;
+  sum2 = bad ? sum : S2 + C2;
 }
 
 }  // namespace

@@ -628,7 +628,8 @@ cudaError_t prepare_trace_fp32(int min_blocks, int steps_per_round, int nb, int 
 }
 
 cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_per_round,
-                              cudaStream_t s, cudaEvent_t *marks) {
+                              cudaStream_t s, cudaEvent_t *marks, int *kernels) {
+  if (kernels) *kernels = 0;
   if (args.chunk_p1 <= args.chunk_p0) return cudaSuccess;
   TraceArgs a = args;
   if (!long_rays_on(a)) a.long_steps = 0x7fffffff;  // no hand-off
@@ -649,16 +650,21 @@ cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_p
   const long long P = a.chunk_p1 - a.chunk_p0;
   long long blocks = ((P + 31) / 32 + 7) / 8;  // one warp per 32 positions
   if (blocks > grid_stride_blocks()) blocks = grid_stride_blocks();
+  int tally = 1;
   if (a.tally32) {
     reduce_cells32_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
   } else {
-    bool tma = false;
+    int tma = 0;
     e = a.reduce_plain ? cudaSuccess : launch_reduce_tma(a, s, &tma);
     if (e != cudaSuccess) return e;
-    if (!tma) reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+    if (!tma)
+      reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+    else
+      tally = tma;
   }
   e = cudaGetLastError();
   if (e == cudaSuccess && marks) e = cudaEventRecord(marks[3], s);
+  if (e == cudaSuccess && kernels) *kernels = 1 + (long_rays_on(a) ? 1 : 0) + tally;
   return e;
 }
 

@@ -342,6 +342,50 @@ def test_tma_fed_tally_equals_plain_loads_bitwise():
     S.close()
 
 
+def test_segmented_tally_split_and_in_order_agree_bitwise():
+    """More than 64 runs of 32 samples per cell (N > 2048): the runs form segments
+    of equal length (the last one shorter) whose compensated sums are added in
+    order.  The TMA-fed tally sums every segment with a warp of its own and a
+    second kernel adds them; the plain-load tally and the allocation-free solve
+    add a cell's segments in one warp.  All give the same Q, sigma and step counts
+    bit for bit: one segment (2048 rays), two (2052: 65 runs, the last sample run
+    ragged), three (4100), several solve chunks, a ray count that only the
+    plain-load reader takes (2049); and the oracle at the FP32 tolerance."""
+    import ctypes as C
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(7, 6, 5, seed=23, eps_wall=0.8, x_mode="field")
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    for rays in (2048, 2052, 4100, 2049):
+        res = []
+        for plain in (0, 1):
+            S.set_tuning(tally_plain_loads=plain)
+            res.append(S.solve(rays=rays, seed=12, precision=mcrt.MCRT_FP32, with_steps=True))
+            if plain == 0 and rays in (2052, 4100):
+                # trace, long-ray march, the segments' sums, their combination
+                assert S.stats()["launches"] == 4, rays
+        for a, b in zip(*res):
+            assert np.array_equal(a, b), rays
+        # several chunks (1 MiB of scratch: about 60 positions each)
+        S.set_tuning(scratch_mib=1)
+        q, s, st = S.solve(rays=rays, seed=12, precision=mcrt.MCRT_FP32, with_steps=True)
+        S.set_tuning()
+        assert np.array_equal(q, res[0][0]) and np.array_equal(s, res[0][1]) and np.array_equal(st, res[0][2])
+    # the allocation-free solve adds the segments in one warp
+    stream = torch.cuda.current_stream().cuda_stream
+    qn = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    sn = torch.zeros_like(qn)
+    mcrt.mcrt_solve_qrad_noalloc(S.ctx, S.params(rays=4100, seed=12, precision=mcrt.MCRT_FP32),
+                                 C.c_void_p(qn.data_ptr()), C.c_void_p(sn.data_ptr()), stream)
+    torch.cuda.synchronize()
+    q, s = S.solve(rays=4100, seed=12, precision=mcrt.MCRT_FP32)
+    assert np.array_equal(qn.cpu().numpy(), q) and np.array_equal(sn.cpu().numpy(), s)
+    orc = oracle.solve(grid, kd, T, x, rays=2052, seed=12)
+    q, s = S.solve(rays=2052, seed=12, precision=mcrt.MCRT_FP32)
+    assert np.all(np.abs(q - orc["q"]) <= 1e-4 * orc["scale"])
+    S.close()
+
+
 def test_binary64_tally_sign_mix_and_launch_independence():
     """Grey walls at both temperatures give cells whose samples take both signs
     (Q_i a difference of large terms); the binary64 tally is reproduced bit for

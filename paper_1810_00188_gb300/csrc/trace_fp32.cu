@@ -98,8 +98,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   // (counters[6], zeroed before each launch): a warp whose cells hold longer rays
   // takes fewer cells, and the runs keep neighbouring cells together.
   // positions per claim: about claim_rays rays (at least one cell), and at
-  // least 8 claims per warp
-  const long long G = max(1LL, min((long long)((a.claim_rays > 0 ? a.claim_rays : 1024) / a.rays),
+  // least 8 claims per warp.  A cell with more rays than that is claimed in
+  // blocks of RB rays (claim k: block k mod nblk of position k / nblk), so that
+  // a chunk of few cells with many rays each still spreads over every warp; the
+  // samples, and so Q and sigma, do not depend on who traces which rays.
+  const int claim = a.claim_rays > 0 ? a.claim_rays : 1024;
+  const int RB = (claim + 31) / 32 * 32;
+  const bool by_block = a.rays > RB;
+  const long long nblk = by_block ? (a.rays + RB - 1) / RB : 1;
+  const long long G = max(1LL, min((long long)(claim / a.rays),
                                    (a.chunk_p1 - a.chunk_p0) / ((long long)gridDim.x * WARPS * 8)));
   long long p_next = 0, p_end = 0;
 
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
 
   // warp-uniform: the emitting cell being initialised, its next ray, and (per-cell
   // proposal) its hemisphere count
-  int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N;
+  int c_bx = 0, c_by = 0, c_bz = 0, c_lin = 0, c_slot = 0, c_r = N, c_end = N;
   unsigned c_hemi = 4194304u;
   // 1 / (hemisphere count) of each hemisphere, per cell (the plain proposal's
   // 2^22 has the exact reciprocal 2^-22): one correctly rounded reciprocal per
@@ -141,25 +148,43 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
     // ---- A. converged initialisation of up to 32 rays of one cell ----
     if ((int)(tail - head) <= POOL - 32 && !exhausted) {
       progress = true;
-      if (c_r >= N) {  // next emitting cell of this warp's brick-ordered run
+      if (c_r >= c_end) {  // next emitting cell of this warp's brick-ordered run
         bool found = false;
         long long p = p_next;
-        for (;;) {
-          while (!found && p < p_end) {
+        int r0 = 0;
+        if (by_block) {
+          for (;;) {  // claim the next block of one cell's rays (warp-uniform)
+            unsigned long long k = 0;
+            if (lane == 0) k = atomicAdd(a.counters + 6, 1ull);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            p = a.chunk_p0 + (long long)(k / (unsigned long long)nblk);
+            if (p >= a.chunk_p1) break;
             found = brick_cell(a, p, c_bx, c_by, c_bz);
             ++p;
+            if (found) {
+              r0 = (int)(k % (unsigned long long)nblk) * RB;
+              break;
+            }
           }
-          if (found) break;
-          unsigned long long base = 0;  // claim the next run (warp-uniform)
-          if (lane == 0) base = atomicAdd(a.counters + 6, (unsigned long long)G);
-          base = __shfl_sync(0xffffffffu, base, 0);
-          p = a.chunk_p0 + (long long)base;
-          p_end = min(a.chunk_p1, p + G);
-          if (p >= a.chunk_p1) break;
+        } else {
+          for (;;) {
+            while (!found && p < p_end) {
+              found = brick_cell(a, p, c_bx, c_by, c_bz);
+              ++p;
+            }
+            if (found) break;
+            unsigned long long base = 0;  // claim the next run (warp-uniform)
+            if (lane == 0) base = atomicAdd(a.counters + 6, (unsigned long long)G);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            p = a.chunk_p0 + (long long)base;
+            p_end = min(a.chunk_p1, p + G);
+            if (p >= a.chunk_p1) break;
+          }
         }
         p_next = p;
         if (found) {
-          c_r = 0;
+          c_r = r0;
+          c_end = min(N, r0 + (by_block ? RB : N));
           c_slot = (int)(p - 1 - a.chunk_p0);
           c_lin = (a.bi0 + c_bx) + nx * ((a.bj0 + c_by) + ny * (a.bk0 + c_bz));
           c_rup = c_rdn = 2.384185791015625e-07f;
@@ -184,7 +209,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
         bool keep = false, inst = false;  // through the ring and the march / ended in its cell
         float4 sA, sB;
         unsigned sCx = 0u, sCz = 0u;
-        if (rr < N) {
+        if (rr < c_end) {
           const unsigned cell = (unsigned)c_lin;
           const unsigned rayid = (unsigned)(ray_off + (unsigned long long)rr);
           const uint2 fi = __ldg(field + cell);

@@ -342,6 +342,40 @@ def test_tma_fed_tally_equals_plain_loads_bitwise():
     S.close()
 
 
+def test_claimed_blocks_of_rays_bitwise():
+    """A cell with more rays than a claim (mcrt_tuning.claim_rays) is traced in
+    blocks of rays claimed one at a time, by whichever warps take them; every
+    sample depends only on its cell and ray index, so Q, sigma and the step
+    counts equal those of whole-cell claims bit for bit: the plain proposal and a
+    per-cell proposal (staged per warp for each claim), blocks of 32 and 64 rays
+    (300 rays: a ragged last block), with long rays handed off."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(10, 9, 7, seed=31, eps_wall=0.8, x_mode="field")
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    nb, ng, nc = kd.n_bands, kd.n_g, grid.ncells
+    rng = np.random.default_rng(5)
+
+    def cum(rows, k):
+        c = rng.integers(1, 2**26, size=(rows, k)).astype(np.int64)
+        c[:, -1] += 2**32 - c.sum(axis=1)
+        return np.cumsum(c, axis=1).astype(np.uint64)
+
+    S.set_cell_proposal(cum(nc, nb), cum(nc * nb, ng).reshape(nc, nb, ng),
+                        rng.integers(1, 2**23, size=nc).astype(np.uint32))
+    for proposal in (mcrt.MCRT_PROPOSAL_PLANCK_TMAX, mcrt.MCRT_PROPOSAL_CELL):
+        kw = dict(rays=300, seed=7, precision=mcrt.MCRT_FP32, proposal=proposal, with_steps=True)
+        S.set_tuning(claim_rays=4096, long_ray_steps=8, long_ray_flight=-1)
+        ref = S.solve(**kw)
+        assert S.stats()["long_rays"] > 0
+        for cr in (32, 50):
+            S.set_tuning(claim_rays=cr, long_ray_steps=8, long_ray_flight=-1)
+            got = S.solve(**kw)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), (proposal, cr)
+    S.close()
+
+
 def test_segmented_tally_split_and_in_order_agree_bitwise():
     """More than 64 runs of 32 samples per cell (N > 2048): the runs form segments
     of equal length (the last one shorter) whose compensated sums are added in

@@ -37,6 +37,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int PIECES = 32;   // nominal x/z crossings per lane and window
 constexpr int SERIAL = 32;   // flights with fewer crossings left march one segment at a time
 constexpr int LANE_MAX = 8 * PIECES + 16;  // bound of a lane's loop (expected: PIECES + 2)
+constexpr int GATHER = 16;   // pieces of a lane whose loads are issued together
 
 struct Geom {
   const uint2 *field;
@@ -292,38 +293,70 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
       int lst = 0;
       bool closed = false;
       {
+        // GATHER pieces at a time: their cells and lengths first (face-count
+        // arithmetic only), then all their field entries, then all their table
+        // rows, so that the loads of a batch are in flight together instead of
+        // one piece's two dependent loads after another's; the pieces are then
+        // added in order, as one at a time would add them
         float tp = ts;
-        for (int k = 0; k < LANE_MAX; ++k) {
-          const bool xf = tx <= tz;
-          const float tn = xf ? tx : tz;
-          const bool in = (xf || !y_end) ? tn <= te : tn < te;
-          float kap, Bj;
-          medium(g.field, kbtab, (unsigned)jx + row + plane * (unsigned)jz, krow, kap, Bj);
-          float alpha, trans;
-          absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
-          lX += (B_i - Bj) * (lt * alpha);
-          lt *= trans;
-          lB = Bj;
-          if (!in) {
-            if (y_end) {
-              ++lst;
-              ltc = lt;
+        for (int k = 0; k < LANE_MAX && !closed; k += GATHER) {
+          unsigned lin[GATHER];
+          float len[GATHER];
+          int np = 0;
+          bool last_in = true;
+#pragma unroll
+          for (int b = 0; b < GATHER; ++b) {
+            if (np == b && last_in) {
+              const bool xf = tx <= tz;
+              const float tn = xf ? tx : tz;
+              const bool in = (xf || !y_end) ? tn <= te : tn < te;
+              lin[b] = (unsigned)jx + row + plane * (unsigned)jz;
+              len[b] = fmaxf((in ? tn : te) - tp, 0.f);
+              np = b + 1;
+              last_in = in;
+              if (in) {
+                if (xf) {
+                  cx += 1.f;
+                  tx = fmaf(cx, tsx, t0x);
+                  jx = wrap1(jx + sx, g.nx);
+                } else {
+                  cz += 1.f;
+                  tz = fmaf(cz, tsz, t0z);
+                  jz = wrap1(jz + sz, g.nz);
+                }
+                tp = tn;
+              }
             }
-            closed = true;
-            break;
           }
-          ++lst;
-          ltc = lt;
-          if (xf) {
-            cx += 1.f;
-            tx = fmaf(cx, tsx, t0x);
-            jx = wrap1(jx + sx, g.nx);
-          } else {
-            cz += 1.f;
-            tz = fmaf(cz, tsz, t0z);
-            jz = wrap1(jz + sz, g.nz);
+          uint2 fe[GATHER];
+#pragma unroll
+          for (int b = 0; b < GATHER; ++b)
+            if (b < np) fe[b] = __ldg(g.field + lin[b]);
+          float4 kb[GATHER];
+#pragma unroll
+          for (int b = 0; b < GATHER; ++b)
+            if (b < np) kb[b] = __ldg(kbtab + (krow + (fe[b].x >> 23)));
+#pragma unroll
+          for (int b = 0; b < GATHER; ++b) {
+            if (b < np) {
+              unsigned it;
+              float fr;
+              tpos(fe[b].x, it, fr);
+              const float kap = (kb[b].x + fr * kb[b].y) * __uint_as_float(fe[b].y);
+              const float Bj = kb[b].z + fr * kb[b].w;
+              float alpha, trans;
+              absorb(kap * len[b], alpha, trans);
+              lX += (B_i - Bj) * (lt * alpha);
+              lt *= trans;
+              lB = Bj;
+              const bool in = b < np - 1 || last_in;
+              if (in || y_end) {
+                ++lst;
+                ltc = lt;
+              }
+              if (!in) closed = true;
+            }
           }
-          tp = tn;
         }
       }
       if (!__all_sync(FULL, closed)) {  // unreachable: an interval holds about PIECES crossings

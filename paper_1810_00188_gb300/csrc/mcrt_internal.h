@@ -201,6 +201,9 @@ cudaError_t launch_trace_fp32(const TraceArgs &a, int min_blocks, int steps_per_
 // loads; 2 when the segments of each cell are summed by warps of their own,
 // a.tally_part non-null, and added by a second kernel).
 cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, int *kernels);
+// The second kernel of a split binary64 tally (either reader): adds each cell's
+// segment sums in a.tally_part in order and writes Q, sigma and the step counts.
+cudaError_t launch_combine_segments(const TraceArgs &a, cudaStream_t s);
 // Q and sigma of the absorption-based estimate (hybrid = 0) or of its
 // temperature-weighted combination with the emission-based one (hybrid = 1) from
 // the per-batch sums of the AR trace launches; K batches of N rays per cell.

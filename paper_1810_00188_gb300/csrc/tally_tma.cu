@@ -319,13 +319,19 @@ cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, int *kernels) 
   if (e != cudaSuccess) return e;
   *kernels = 1;
   if (split) {
-    long long cb = (P + 255) / 256;
-    if (cb > grid_stride_blocks()) cb = grid_stride_blocks();
-    combine_segments_kernel<<<(unsigned)cb, 256, 0, s>>>(a);
-    e = cudaGetLastError();
+    e = launch_combine_segments(a, s);
     if (e == cudaSuccess) *kernels = 2;
   }
   return e;
+}
+
+cudaError_t launch_combine_segments(const TraceArgs &a, cudaStream_t s) {
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  if (P <= 0) return cudaSuccess;
+  long long cb = (P + 255) / 256;
+  if (cb > grid_stride_blocks()) cb = grid_stride_blocks();
+  combine_segments_kernel<<<(unsigned)cb, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace mcrt

@@ -616,15 +616,56 @@ __device__ __forceinline__ void tile_sums_exact(const unsigned (&v)[32], double 
   s2 = __ull2double_rn(acc2) * pow2d(2 * Ei - 310);
 }
 
-// Binary64 tallies of the warp's cells: lane c owns the cell whose N samples
-// start at y0 + c * N when bit c of `cells` is set.  Tiles of 32 samples are
-// staged through the warp's shared-memory tile ([cell][sample], rows padded to
-// 36 words: the row stores and the lanes' 16-byte row reads are conflict-free)
-// from coalesced loads of each cell's 32 consecutive samples (128 bytes,
-// streaming hint: read once).  The tiles' exact sums are added in order within
-// each segment (tally_segments), the segments' sums in order across them.
-// Returns the lane's sum of y and of y^2 (NaN when a sample is not finite);
-// lanes without a cell return zeros.
+// One tally segment of the warp's cells: lane c owns the cell whose N samples
+// start at y0 + c * N when bit c of `cells` is set, and gets the compensated
+// sums s + c of the exact sums of its tiles t0 .. t1 - 1 (of y and of y^2).
+// Tiles of 32 samples are staged through the warp's shared-memory tile
+// ([cell][sample], rows padded to 36 words: the row stores and the lanes' 16-byte
+// row reads are conflict-free) from coalesced loads of each cell's 32
+// consecutive samples (128 bytes, streaming hint: read once).  `bad` is set when
+// a sample is not finite.
+__device__ __forceinline__ void warp_segment64(const float *__restrict__ y0, int N, unsigned cells, int lane,
+                                               float (*tile)[36], int t0, int t1, double &v1, double &v2,
+                                               bool &bad) {
+  double s = 0.0, c = 0.0, s2 = 0.0, c2 = 0.0;
+  const bool mine = (cells >> lane) & 1u;
+  for (int t = t0; t < t1; ++t) {
+    const int r0 = t * 32;
+    const bool in = r0 + lane < N;
+    float ld[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc)
+      ld[cc] = ((cells >> cc) & 1u) && in ? __ldcs(y0 + (size_t)cc * (unsigned)N + (unsigned)(r0 + lane)) : 0.f;
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) tile[cc][lane] = ld[cc];
+    __syncwarp();
+    if (mine) {
+      unsigned v[32];
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const float4 f = *reinterpret_cast<const float4 *>(&tile[lane][k]);
+        v[k] = __float_as_uint(f.x);
+        v[k + 1] = __float_as_uint(f.y);
+        v[k + 2] = __float_as_uint(f.z);
+        v[k + 3] = __float_as_uint(f.w);
+      }
+      double t1s, t2s;
+      tile_sums_exact(v, t1s, t2s, bad);
+      neumaier_add(s, c, t1s);
+      neumaier_add(s2, c2, t2s);
+    }
+    __syncwarp();
+  }
+  v1 = s + c;
+  v2 = s2 + c2;
+}
+
+// Binary64 tallies of the warp's cells (cells, tiles and staging as in
+// warp_segment64): the tiles' exact sums added in order within each segment
+// (tally_segments), the segments' sums in order across them (the same bits as
+// warp_segment64 per segment followed by combine_segments_kernel).  Returns the
+// lane's sum of y and of y^2 (NaN when a sample is not finite); lanes without a
+// cell return zeros.
 __device__ __forceinline__ void warp_tally64(const float *__restrict__ y0, int N, unsigned cells, int lane,
                                              float (*tile)[36], double &sum, double &sum2) {
   double S = 0.0, C = 0.0, S2 = 0.0, C2 = 0.0;  // over segments

@@ -442,6 +442,36 @@ __global__ void __launch_bounds__(256) reduce_cells_kernel(const TraceArgs a) {
   }
 }
 
+// The split form of reduce_cells_kernel (a.tally_part non-null, more than one
+// tally segment): each segment of each group of 32 positions is an item of its
+// own; its sums go to a.tally_part and combine_segments_kernel adds a cell's
+// segments in order (the same bits as one warp adding them).
+__global__ void __launch_bounds__(256) reduce_segments_kernel(const TraceArgs a) {
+  __shared__ __align__(16) float tiles[WARPS][32][36];
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int N = a.rays;
+  const long long P = a.chunk_p1 - a.chunk_p0;
+  const int ntile = (N + 31) / 32, nseg = tally_segments(ntile), L = tally_seg_len(ntile);
+  const long long nitems = ((P + 31) / 32) * nseg;
+  for (long long item = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < nitems; item += nwarps) {
+    const long long base = (item / nseg) * 32;
+    const int k = (int)(item % nseg);
+    int bx = 0, by = 0, bz = 0;
+    const bool mine = base + lane < P && brick_cell(a, a.chunk_p0 + base + lane, bx, by, bz);
+    const unsigned cells = __ballot_sync(0xffffffffu, mine);
+    if (!cells) continue;  // warp-uniform
+    double v1, v2;
+    bool bad = false;
+    warp_segment64(a.ybuf + (size_t)base * (unsigned)N, N, cells, lane, tiles[threadIdx.x >> 5], k * L,
+                   min(ntile, (k + 1) * L), v1, v2, bad);
+    if (mine) {
+      const double nan = __longlong_as_double(0x7FF8000000000000ll);
+      a.tally_part[(size_t)k * (size_t)P + (size_t)(base + lane)] = make_double2(bad ? nan : v1, bad ? nan : v2);
+    }
+  }
+}
+
 // The binary32 tally, on request (mcrt_tuning.tally_binary32): for each cell the
 // lanes sum its N samples in a fixed order (lane l takes samples l, l + 32, ...,
 // sums each batch of 8 pairwise in binary32 and adds the batch sums to
@@ -682,10 +712,22 @@ cudaError_t launch_trace_fp32(const TraceArgs &args, int min_blocks, int steps_p
     int tma = 0;
     e = a.reduce_plain ? cudaSuccess : launch_reduce_tma(a, s, &tma);
     if (e != cudaSuccess) return e;
-    if (!tma)
-      reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
-    else
+    if (!tma) {
+      const int nseg = tally_segments((a.rays + 31) / 32);
+      if (a.tally_part && nseg > 1) {  // every segment of every group an item of its own
+        long long b2 = ((P + 31) / 32 * nseg + 7) / 8;
+        if (b2 > grid_stride_blocks()) b2 = grid_stride_blocks();
+        reduce_segments_kernel<<<(unsigned)b2, 256, 0, s>>>(a);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_combine_segments(a, s);
+        if (e != cudaSuccess) return e;
+        tally = 2;
+      } else {
+        reduce_cells_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+      }
+    } else {
       tally = tma;
+    }
   }
   e = cudaGetLastError();
   if (e == cudaSuccess && marks) e = cudaEventRecord(marks[3], s);

@@ -37,7 +37,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int PIECES = 32;   // nominal x/z crossings per lane and window
 constexpr int SERIAL = 32;   // flights with fewer crossings left march one segment at a time
 constexpr int LANE_MAX = 8 * PIECES + 16;  // bound of a lane's loop (expected: PIECES + 2)
-constexpr int GATHER = 16;   // pieces of a lane whose loads are issued together
+constexpr int GATHER = 4;    // pieces of a lane whose loads are issued together
 
 struct Geom {
   const uint2 *field;

@@ -118,6 +118,8 @@ __device__ __forceinline__ void first_after(float ts, float t0, float tsa, float
   t = fmaf(m, tsa, t0);
 }
 
+// AR: the absorption-based estimate's deposits (a.armc_acc non-null).
+template <bool AR>
 __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -148,6 +150,9 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     int steps = (int)L.steps;
     unsigned nrefl = L.nrefl, capped = 0, walls = 0;
     bool done = false;
+    // the absorption-based estimate: deposits into the per-batch sums, as the
+    // trace kernel makes them (one lane deposits what all lanes hold)
+    auto deposit = [&](unsigned cell, float v) { atomicAdd(a.armc_acc + armc_slot(a, L.r, cell), f32_to_f64(v)); };
 
     // wall event at the y face just crossed (iy outside the grid): the wall
     // factor of Eq. 3, then stop or reflect, as in the trace kernel
@@ -156,6 +161,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
       const float eps = wl ? g.eps1 : g.eps0;
       const float Bw = __ldg(g.bwall + ((unsigned)(wl * nb) + L.n));
       X += (B_i - Bw) * (tau * eps);
+      if (AR && lane == 0) deposit(L.cellid, L.scale * ((B_i - Bw) * (tau * eps)));  // own exchange with the wall
       tau *= 1.f - eps;
       ++walls;
       if (eps >= 1.f || tau <= tol) {
@@ -234,10 +240,13 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
           tn = tnz;
         }
         float kap, Bj;
-        medium(g.field, kbtab, (unsigned)(ix + g.nx * (iy + g.ny * iz)), krow, kap, Bj);
+        const unsigned lin = (unsigned)(ix + g.nx * (iy + g.ny * iz));
+        medium(g.field, kbtab, lin, krow, kap, Bj);
         float alpha, trans;
         absorb(kap * fmaxf(tn - tprev, 0.f), alpha, trans);
-        X += (B_i - Bj) * (tau * alpha);
+        const float term = (B_i - Bj) * (tau * alpha);
+        X += term;
+        if (AR && lane == 0 && lin != L.cellid) deposit(lin, -L.scale * term);  // absorbed in cell lin
         tau *= trans;
         B_last = Bj;
         ++steps;
@@ -386,6 +395,36 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
       float c = lane < js ? tb * lX : 0.f;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(FULL, c, off);
+      if (AR && lane < js) {
+        // the deposits of this lane's pieces: the walk again, with the
+        // transmissivity at its start (tb); the two pieces of a segment cut at a
+        // lane boundary deposit its term in two parts
+        float dcx = cx0, dtx = tx0, dcz = cz0, dtz = tz0, gt = tb, tp = ts;
+        int djx = jx0, djz = jz0;
+        for (int k = 0; k < LANE_MAX; ++k) {
+          const bool xf = dtx <= dtz;
+          const float tn = xf ? dtx : dtz;
+          const bool in = (xf || !y_end) ? tn <= te : tn < te;
+          float kap, Bj;
+          const unsigned lin = (unsigned)djx + row + plane * (unsigned)djz;
+          medium(g.field, kbtab, lin, krow, kap, Bj);
+          float alpha, trans;
+          absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
+          if (lin != L.cellid) deposit(lin, -L.scale * ((B_i - Bj) * (gt * alpha)));
+          gt *= trans;
+          if (!in) break;
+          if (xf) {
+            dcx += 1.f;
+            dtx = fmaf(dcx, tsx, t0x);
+            djx = wrap1(djx + sx, g.nx);
+          } else {
+            dcz += 1.f;
+            dtz = fmaf(dcz, tsz, t0z);
+            djz = wrap1(djz + sz, g.nz);
+          }
+          tp = tn;
+        }
+      }
       if (js < 32) {
         // the ray stops in lane js's interval: march it again with the running
         // transmissivity and step count, applying the stopping rules
@@ -405,10 +444,13 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
             const float tn = xf ? tx : tz;
             const bool in = (xf || !y_end) ? tn <= te : tn < te;
             float kap, Bj;
-            medium(g.field, kbtab, (unsigned)jx + row + plane * (unsigned)jz, krow, kap, Bj);
+            const unsigned lin = (unsigned)jx + row + plane * (unsigned)jz;
+            medium(g.field, kbtab, lin, krow, kap, Bj);
             float alpha, trans;
             absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
-            gX += (B_i - Bj) * (gt * alpha);
+            const float term = (B_i - Bj) * (gt * alpha);
+            gX += term;
+            if (AR && lin != L.cellid) deposit(lin, -L.scale * term);
             gt *= trans;
             gB = Bj;
             if (in || y_end) {
@@ -459,6 +501,13 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
       }
     }
     if (tau > 0.f) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+    if (AR && lane == 0) {
+      // the residual is absorbed in the last medium cell crossed (the row clamped
+      // after a wall event); the ray's sample to its cell's emission-based sum
+      const unsigned lres = (unsigned)(ix + g.nx * (min(max(iy, 0), g.ny - 1) + g.ny * iz));
+      if (tau > 0.f && lres != L.cellid) deposit(lres, -L.scale * ((B_i - B_last) * tau));
+      atomicAdd(a.ermc_acc + armc_slot(a, L.r, L.cellid), f32_to_f64(L.scale * X));
+    }
     if (lane == 0) {
       a.ybuf[(size_t)L.slot * (unsigned)N + L.r] = L.scale * X;  // the ray's sample Y (Eq. 14)
       if (a.ray_steps) a.ray_steps[(size_t)L.slot * (unsigned)N + L.r] = (unsigned)steps;
@@ -505,7 +554,10 @@ cudaError_t launch_long_rays(const TraceArgs &a, cudaStream_t s) {
   long long blocks = ((long long)a.long_cap + 7) / 8;
   if (blocks > 4LL * sms) blocks = 4LL * sms;
   if (blocks < 1) blocks = 1;
-  long_march_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  if (a.armc_acc)
+    long_march_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+  else
+    long_march_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -726,16 +726,13 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     const bool armc = p->estimator != MCRT_EST_ERMC;
     const long long ncg = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
     if (armc) {
-      // per-batch sums of the deposits and of the cells' own samples; the rays
-      // march to their end in their own lane (no hand-off)
+      // per-batch sums of the deposits and of the cells' own samples (the
+      // long-ray march makes the deposits of the rays handed to it)
       CK(ensure(ctx->armcbuf, (size_t)2 * 16 * ncg * sizeof(double)), "alloc ARMC sums");
       CK(cudaMemsetAsync(ctx->armcbuf.p, 0, (size_t)2 * 16 * ncg * sizeof(double), s), "clear ARMC sums");
       a.armc_acc = (double *)ctx->armcbuf.p;
       a.ermc_acc = a.armc_acc + 16 * ncg;
       a.armc_nc = ncg;
-      a.long_rays = nullptr;
-      a.long_cap = 0;
-      a.long_steps = 0x7fffffff;
     }
     const int nchunks = (int)((P + Pc - 1) / Pc);
     while ((int)ctx->kev.size() < 4 * nchunks) {

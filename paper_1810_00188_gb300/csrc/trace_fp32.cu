@@ -59,7 +59,8 @@ namespace {
 // cell), its residual into the last cell it crossed, and its wall terms into
 // its own cell; deposits go to per-batch binary64 sums (batch = ray index mod K)
 // with atomic adds, and the ray's sample to its cell's per-batch emission-based
-// sum.  Uniform channel grids, one grid, no long-ray hand-off.
+// sum.  Uniform channel grids, one grid; a ray handed to the long-ray march
+// makes its remaining deposits there.
 template <int MINB, int KSTEPS, bool MG, bool GEN, bool AR = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

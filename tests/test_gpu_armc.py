@@ -55,6 +55,37 @@ def test_armc_and_hybrid_against_oracle(reflect):
     np.testing.assert_allclose(sh[bigh], orc["sigma_hybrid"][bigh], rtol=2e-2)
 
 
+def test_armc_with_long_rays_handed_off():
+    """Rays handed to the warp-parallel long-ray march (here after 8 segments,
+    whatever the flight: thousands of them) make their deposits there -- each
+    lane's pieces with the transmissivity at the lane's start, the stopping lane's
+    up to the stop, walls and the residual by one lane: ARMC and the hybrid still
+    agree with the oracle, and the cells' own rays take the same steps."""
+    import torch
+    grid, kd, T, x = inputs.nongrey_channel(16, 16, 12, seed=31, eps_wall=0.8, x_mode="field")
+    rays, seed = 80, 13
+    orc = oracle.solve_armc(grid, kd, T, x, rays=rays, seed=seed, hybrid=True)
+    e = oracle.solve(grid, kd, T, x, rays=rays, seed=seed)
+    S = mcrt.Solver(grid, kd)
+    S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
+    S.set_tuning(long_ray_steps=8, long_ray_flight=-1)
+    for est, key, skey in ((mcrt.MCRT_EST_ARMC, "q", "sigma"), (mcrt.MCRT_EST_HYBRID, "q_hybrid", "sigma_hybrid")):
+        q = torch.full(grid.shape, float("nan"), dtype=torch.float64, device="cuda")
+        s = torch.full_like(q, float("nan"))
+        st = torch.zeros(grid.shape, dtype=torch.int64, device="cuda")
+        S.solve_into(S.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32, estimator=est), q, s, st)
+        stats = S.stats()
+        assert stats["long_rays"] > 1000 and stats["long_overflow"] == 0, stats
+        sc = orc["scale"] if est == mcrt.MCRT_EST_ARMC else np.maximum(orc["scale"], e["scale"])
+        sc = np.maximum(sc, 1e-300)
+        err = np.abs(q.cpu().numpy() - orc[key]) / sc
+        assert err.max() <= 1e-4, (est, err.max())
+        big = orc[skey] > 1e-3 * sc
+        np.testing.assert_allclose(s.cpu().numpy()[big], orc[skey][big], rtol=2e-2)
+        assert abs(st.cpu().numpy().sum() / e["steps"].sum() - 1.0) < 1e-3
+    S.close()
+
+
 def test_armc_few_rays_and_ragged_grid():
     """Fewer rays than batches (K = rays) on a ragged grid, per-cell proposals."""
     grid, kd, T, x = inputs.nongrey_channel(7, 9, 5, seed=32, x_mode="field")

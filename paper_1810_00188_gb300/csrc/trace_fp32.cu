@@ -100,13 +100,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const Trac
   // takes fewer cells, and the runs keep neighbouring cells together.
   // positions per claim: about claim_rays rays (at least one cell), and at
   // least 8 claims per warp.  A cell with more rays than that is claimed in
-  // blocks of RB rays (claim k: block k mod nblk of position k / nblk), so that
-  // a chunk of few cells with many rays each still spreads over every warp; the
-  // samples, and so Q and sigma, do not depend on who traces which rays.
+  // nblk blocks of equal size RB (a multiple of 32; claim k: block k mod nblk of
+  // position k / nblk), so that a chunk of few cells with many rays each still
+  // spreads over every warp; the samples, and so Q and sigma, do not depend on
+  // who traces which rays.
   const int claim = a.claim_rays > 0 ? a.claim_rays : 1024;
-  const int RB = (claim + 31) / 32 * 32;
-  const bool by_block = a.rays > RB;
-  const long long nblk = by_block ? (a.rays + RB - 1) / RB : 1;
+  const int RB0 = (claim + 31) / 32 * 32;
+  const bool by_block = a.rays > RB0;
+  const long long nblk = by_block ? (a.rays + RB0 - 1) / RB0 : 1;
+  const int RB = by_block ? (int)(((a.rays + nblk - 1) / nblk + 31) / 32 * 32) : RB0;  // blocks of equal size
   const long long G = max(1LL, min((long long)(claim / a.rays),
                                    (a.chunk_p1 - a.chunk_p0) / ((long long)gridDim.x * WARPS * 8)));
   long long p_next = 0, p_end = 0;

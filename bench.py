@@ -43,7 +43,7 @@ EXP_PER_STEP = 1              # one exponential per step (Eq. 2)
 # DRAM bytes of one trace launch of the default workload (64^3, 1000 rays):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the current
 # trace kernel (profiles/dram_nongrey_64cubed_1000rays.md)
-TRACE_DRAM_BYTES_64_1000 = 17189120 + 1001358080
+TRACE_DRAM_BYTES_64_1000 = 16984064 + 1001364992
 
 
 def parse():

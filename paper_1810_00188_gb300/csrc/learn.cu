@@ -529,10 +529,12 @@ __global__ void __launch_bounds__(NTHR, 4) spectral_proposal_kernel(const Spectr
     const bool pos = __any_sync(0xffffffffu, any);
     __syncwarp();
     if (a.mode == 1 || !pos) {
-      // hybrid (or a cell whose own spectrum is empty: the T_max proposal)
+      // hybrid (or a cell whose own spectrum is empty: the T_max proposal), in
+      // binary32 from two per-cell factors (a binary64 division per point would
+      // keep the narrow binary64 pipe busy for most of the kernel)
       const double l = pos ? lam : 0.0;
-      for (int k = lane; k < K; k += 32)
-        qw[k] = (float)((1.0 - l) * (double)a.p0[k] + (pos ? l * (double)qw[k] / part : 0.0));
+      const float c0 = (float)(1.0 - l), c1 = pos ? (float)(l / part) : 0.f;
+      for (int k = lane; k < K; k += 32) qw[k] = fmaf(c1, qw[k], c0 * a.p0[k]);
       __syncwarp();
     }
     quantize_cell(qw, 0.5f, a.nb, a.ng, wn, a.cell_cn + c * a.nb, a.cell_cg + c * (long long)K,

@@ -328,9 +328,11 @@ cudaError_t launch_reduce_tma(const TraceArgs &a, cudaStream_t s, int *kernels) 
 cudaError_t launch_combine_segments(const TraceArgs &a, cudaStream_t s) {
   const long long P = a.chunk_p1 - a.chunk_p0;
   if (P <= 0) return cudaSuccess;
-  long long cb = (P + 255) / 256;
+  // 64 positions per CTA: a chunk of few cells (many rays each) still spreads
+  // its binary64 sums over the SMs' narrow binary64 pipes
+  long long cb = (P + 63) / 64;
   if (cb > grid_stride_blocks()) cb = grid_stride_blocks();
-  combine_segments_kernel<<<(unsigned)cb, 256, 0, s>>>(a);
+  combine_segments_kernel<<<(unsigned)cb, 64, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -148,9 +148,11 @@ typedef struct {
   int mg_steps;            /* segments per grid but the coarsest, >= 1 when
                               mg_levels > 1 (the paper uses 5)                   */
   /* MCRT_EST_*.  ARMC and HYBRID: MCRT_FP32, the whole grid (every cell emits;
-   * no box), a uniform channel grid (no wall-normal faces, no x/z walls) and one
-   * grid (long rays are handed to the warp-parallel march, which makes their
-   * deposits, as in the emission-based solve); anything else is refused with
+   * no box) and one grid, on channel grids (uniform or stretched wall-normal
+   * faces; deposits carry the volume ratio of the emitting and the absorbing
+   * cell) and closed boxes (the x/z wall terms stay in the emitting cell); long
+   * rays are handed to the warp-parallel march, which makes their deposits, as
+   * in the emission-based solve; anything else is refused with
    * MCRT_E_UNSUPPORTED.  sigma_out is the batch-means standard error over K =
    * min(16, rays_per_cell) batches of ray indices (r mod 16).  The deposits are
    * binary64 atomic adds, so these results are reproducible to rounding, not bit

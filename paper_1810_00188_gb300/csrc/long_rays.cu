@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     // the absorption-based estimate: deposits into the per-batch sums, as the
     // trace kernel makes them (one lane deposits what all lanes hold)
     auto deposit = [&](unsigned cell, float v) { atomicAdd(a.armc_acc + armc_slot(a, L.r, cell), f32_to_f64(v)); };
+    // the volume ratio of the emitting cell and one in row j (stretched grids)
+    auto vratio = [&](int j) { return volume_ratio(g.yfs, g.nx, g.ny, L.cellid, j); };
 
     // wall event at the y face just crossed (iy outside the grid): the wall
     // factor of Eq. 3, then stop or reflect, as in the trace kernel
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
         absorb(kap * fmaxf(tn - tprev, 0.f), alpha, trans);
         const float term = (B_i - Bj) * (tau * alpha);
         X += term;
-        if (AR && lane == 0 && lin != L.cellid) deposit(lin, -L.scale * term);  // absorbed in cell lin
+        if (AR && lane == 0 && lin != L.cellid) deposit(lin, -L.scale * term * vratio(iy));  // absorbed in cell lin
         tau *= trans;
         B_last = Bj;
         ++steps;
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
           medium(g.field, kbtab, lin, krow, kap, Bj);
           float alpha, trans;
           absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
-          if (lin != L.cellid) deposit(lin, -L.scale * ((B_i - Bj) * (gt * alpha)));
+          if (lin != L.cellid) deposit(lin, -L.scale * ((B_i - Bj) * (gt * alpha)) * vratio(iy));
           gt *= trans;
           if (!in) break;
           if (xf) {
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
             absorb(kap * fmaxf((in ? tn : te) - tp, 0.f), alpha, trans);
             const float term = (B_i - Bj) * (gt * alpha);
             gX += term;
-            if (AR && lin != L.cellid) deposit(lin, -L.scale * term);
+            if (AR && lin != L.cellid) deposit(lin, -L.scale * term * vratio(iy));
             gt *= trans;
             gB = Bj;
             if (in || y_end) {
@@ -504,8 +506,9 @@ __global__ void __launch_bounds__(256) long_march_kernel(const TraceArgs a) {
     if (AR && lane == 0) {
       // the residual is absorbed in the last medium cell crossed (the row clamped
       // after a wall event); the ray's sample to its cell's emission-based sum
-      const unsigned lres = (unsigned)(ix + g.nx * (min(max(iy, 0), g.ny - 1) + g.ny * iz));
-      if (tau > 0.f && lres != L.cellid) deposit(lres, -L.scale * ((B_i - B_last) * tau));
+      const int jres = min(max(iy, 0), g.ny - 1);
+      const unsigned lres = (unsigned)(ix + g.nx * (jres + g.ny * iz));
+      if (tau > 0.f && lres != L.cellid) deposit(lres, -L.scale * ((B_i - B_last) * tau) * vratio(jres));
       atomicAdd(a.ermc_acc + armc_slot(a, L.r, L.cellid), f32_to_f64(L.scale * X));
     }
     if (lane == 0) {

@@ -247,8 +247,6 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
     if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: FP32 only");
     if (b[0] != 0 || b[1] != g.nx || b[2] != 0 || b[3] != g.ny || b[4] != 0 || b[5] != g.nz)
       return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: the whole grid only (every cell emits)");
-    if (!ctx->yf.empty() || g.xz_walls)
-      return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: uniform channel grids only");
     if (p->mg_levels > 1) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: one grid only");
   }
   return MCRT_OK;

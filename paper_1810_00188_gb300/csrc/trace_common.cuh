@@ -256,6 +256,15 @@ __device__ __forceinline__ size_t armc_slot(const TraceArgs &a, unsigned r, unsi
   return (size_t)(r & 15u) * (size_t)a.armc_nc + cell;
 }
 
+// V_i / V_j of the emitting cell i (linear index cellid) and an absorbing cell in
+// row j, for the absorption-based deposits: cells differ only in their
+// wall-normal height, and only on a stretched grid (faces yfs; null: 1).
+__device__ __forceinline__ float volume_ratio(const float *__restrict__ yfs, int nx, int ny, unsigned cellid, int j) {
+  if (!yfs) return 1.f;
+  const int ie = (int)((cellid / (unsigned)nx) % (unsigned)ny);
+  return (__ldg(yfs + ie + 1) - __ldg(yfs + ie)) / (__ldg(yfs + j + 1) - __ldg(yfs + j));
+}
+
 // binary32 -> binary64, exactly, from the bits (the conversion instruction runs
 // on the narrow binary64 pipe); zeros, subnormals, infinities and NaN take the
 // instruction.
@@ -360,7 +369,8 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
     s.X += term;     // Eq. 14 term / kappa_i
     s.tau *= trans;  // Eq. 3
     if (AR && s.lin != s.cellid)  // the exchange absorbed in cell j, seen from j
-      atomicAdd(a.armc_acc + armc_slot(a, s.r, s.lin), f32_to_f64(-s.scale * term));
+      atomicAdd(a.armc_acc + armc_slot(a, s.r, s.lin),
+                f32_to_f64(-s.scale * term * volume_ratio(yfs, g.nx, g.ny, s.cellid, s.iy)));
     s.B_last = Bj;
     ++s.steps;
     if (MG) ++s.lsteps;
@@ -399,7 +409,10 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
           // closed box: a black x or z wall absorbs the rest of the ray and
           // emits at its temperature (Eq. 3 wall factor with eps = 1)
           const int f = wx ? (wx > 0 ? 2 : 3) : (wz > 0 ? 4 : 5);
-          s.X += (s.B_i - __ldg(bwall + ((unsigned)(f * nb) + s.n))) * s.tau;
+          const float tw = (s.B_i - __ldg(bwall + ((unsigned)(f * nb) + s.n))) * s.tau;
+          s.X += tw;
+          if (AR)  // the cell's own exchange with the wall
+            atomicAdd(a.armc_acc + armc_slot(a, s.r, s.cellid), f32_to_f64(s.scale * tw));
           s.tau = 0.f;
           ++ls.tot_wall;
           done = true;
@@ -524,9 +537,11 @@ __device__ __forceinline__ void march_round(const TraceArgs &a, const MarchGrid 
       if (AR) {
         // the residual is absorbed in the last medium cell crossed (the row is
         // clamped: after a wall event iy lies outside the grid)
-        const unsigned lres = (unsigned)(s.ix + g.nx * (min(max(s.iy, 0), g.ny - 1) + g.ny * s.iz));
+        const int jres = min(max(s.iy, 0), g.ny - 1);
+        const unsigned lres = (unsigned)(s.ix + g.nx * (jres + g.ny * s.iz));
         if (s.tau > 0.f && lres != s.cellid)
-          atomicAdd(a.armc_acc + armc_slot(a, s.r, lres), f32_to_f64(-s.scale * ((s.B_i - s.B_last) * s.tau)));
+          atomicAdd(a.armc_acc + armc_slot(a, s.r, lres),
+                    f32_to_f64(-s.scale * ((s.B_i - s.B_last) * s.tau) * volume_ratio(yfs, g.nx, g.ny, s.cellid, jres)));
         atomicAdd(a.ermc_acc + armc_slot(a, s.r, s.cellid), f32_to_f64(s.scale * s.X));
       }
       Ybuf[(size_t)s.slot * (unsigned)N + s.r] = s.scale * s.X;  // the ray's sample Y (Eq. 14)

@@ -59,8 +59,9 @@ namespace {
 // cell), its residual into the last cell it crossed, and its wall terms into
 // its own cell; deposits go to per-batch binary64 sums (batch = ray index mod K)
 // with atomic adds, and the ray's sample to its cell's per-batch emission-based
-// sum.  Uniform channel grids, one grid; a ray handed to the long-ray march
-// makes its remaining deposits there.
+// sum; on a stretched grid each deposit carries the volume ratio of the emitting
+// and the absorbing cell.  One grid; a ray handed to the long-ray march makes
+// its remaining deposits there.
 template <int MINB, int KSTEPS, bool MG, bool GEN, bool AR = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) trace_fp32_kernel(const TraceArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -615,9 +616,11 @@ cudaError_t run_variant(bool prepare, const TraceArgs *a, int min_blocks, int st
 
 cudaError_t dispatch(bool prepare, const TraceArgs *a, int min_blocks, int steps_per_round, bool multigrid,
                      bool general, cudaStream_t s, size_t smem, int *bps, int *nsm) {
-  // the absorption-based estimate: one variant (default launch shape, single
-  // uniform channel grid; the host refuses the rest)
-  if (!prepare && a->armc_acc) return launch_variant<3, 1, false, false, true>(*a, s, smem);
+  // the absorption-based estimate: the default launch shape on one grid, the
+  // channel or the general geometry (the host refuses multigrid)
+  if (!prepare && a->armc_acc)
+    return general ? launch_variant<3, 1, false, true, true>(*a, s, smem)
+                   : launch_variant<3, 1, false, false, true>(*a, s, smem);
   if (multigrid)
     return general ? run_variant<true, true>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm)
                    : run_variant<true, false>(prepare, a, min_blocks, steps_per_round, s, smem, bps, nsm);

@@ -147,12 +147,31 @@ def test_armc_refuses_what_it_does_not_support():
     assert L.mcrt_solve_qrad_noalloc(S.ctx, C.byref(p), C.c_void_p(q.data_ptr()), None, None) == \
         mcrt.MCRT_E_UNSUPPORTED
     S.close()
-    g2 = inputs.Grid(8, 8, 8, 4.0, 2.0, 2.0, T_wall=(500.0, 1000.0))
-    g2.yf = inputs.channel_faces(8, 2.0, 1.5)
-    T2, x2 = inputs.channel_fields(g2, 3)
-    S2 = mcrt.Solver(g2, kd)
-    S2.set_fields(T2, x2)
-    with pytest.raises(mcrt.McrtError) as e:
-        S2.solve(rays=4, precision=mcrt.MCRT_FP32, estimator=mcrt.MCRT_EST_ARMC)
-    assert e.value.status == mcrt.MCRT_E_UNSUPPORTED
-    S2.close()
+
+
+@pytest.mark.parametrize("geometry", ["stretched", "box"])
+def test_armc_stretched_grid_and_closed_box_against_oracle(geometry):
+    """A wall-refined channel grid (each deposit scaled by the volume ratio of
+    the emitting and the absorbing cell; long rays handed off with their
+    deposits) and the paper's closed sin cube (the black x and z walls' terms kept
+    in the emitting cell): ARMC and the hybrid against the oracle on the same
+    draws."""
+    if geometry == "stretched":
+        grid, kd, T, x = inputs.nongrey_channel(14, 16, 10, seed=35, eps_wall=0.8, x_mode="field")
+        grid.yf = inputs.channel_faces(grid.ny, grid.ly, 1.5)
+        T, x = inputs.channel_fields(grid, 35, x_mode="field")
+    else:
+        grid, kd, T, x = inputs.sin_cube(12, 0.5)
+    rays, seed = 64, 17
+    orc = oracle.solve_armc(grid, kd, T, x, rays=rays, seed=seed, hybrid=True)
+    e = oracle.solve(grid, kd, T, x, rays=rays, seed=seed)
+    qa, sa, st, stats = _solve(grid, kd, T, x, mcrt.MCRT_EST_ARMC, rays, seed)
+    scale = np.maximum(orc["scale"], 1e-300)
+    err = np.abs(qa - orc["q"]) / scale
+    assert err.max() <= 1e-4, err.max()
+    big = orc["sigma"] > 1e-3 * scale
+    np.testing.assert_allclose(sa[big], orc["sigma"][big], rtol=2e-2)
+    assert abs(st.sum() / e["steps"].sum() - 1.0) < 1e-3
+    qh, sh, _, _ = _solve(grid, kd, T, x, mcrt.MCRT_EST_HYBRID, rays, seed)
+    sc = np.maximum(np.maximum(orc["scale"], e["scale"]), 1e-300)
+    assert (np.abs(qh - orc["q_hybrid"]) / sc).max() <= 1e-4

@@ -58,15 +58,19 @@ def test_armc_paper_grey_cases_layer_exact(name):
     assert_rows(_row_z_batches(res, ref))
 
 
-@pytest.mark.parametrize("stretched", [False, True])
+@pytest.mark.parametrize("stretched", [False, True, "box"])
 def test_armc_moves_the_medium_exchange_on_the_same_draws(stretched):
     """Same draws: each ray deposits minus its emission-based medium terms (and
     residual) into the cells that absorb, scaled by the volume ratio, and keeps its
-    wall terms in its own cell.  Hence, exactly up to rounding,
-    sum_i V_i Q_A,i = sum_i V_i (2 Q_E,wall,i - Q_E,i).  A wrong sign, a dropped
-    deposit, a residual in the wrong cell or a missing volume ratio breaks it."""
-    grid, kd, T, x = inputs.nongrey_channel(8, 10, 6, seed=3, eps_wall=0.8, x_mode="field")
-    if stretched:
+    wall terms in its own cell (the black x and z walls of a closed box too).
+    Hence, exactly up to rounding, sum_i V_i Q_A,i = sum_i V_i (2 Q_E,wall,i -
+    Q_E,i).  A wrong sign, a dropped deposit, a residual in the wrong cell or a
+    missing volume ratio breaks it."""
+    if stretched == "box":
+        grid, kd, T, x = inputs.sin_cube(6, 0.5)
+    else:
+        grid, kd, T, x = inputs.nongrey_channel(8, 10, 6, seed=3, eps_wall=0.8, x_mode="field")
+    if stretched is True:
         grid.yf = inputs.channel_faces(grid.ny, grid.ly, 1.5)
     a = oracle.solve_armc(grid, kd, T, x, rays=32, seed=1)
     e = oracle.solve(grid, kd, T, x, rays=32, seed=1)

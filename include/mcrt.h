@@ -147,8 +147,8 @@ typedef struct {
   int mg_levels;           /* grids used, 0 or 1: the grid itself (exact march)   */
   int mg_steps;            /* segments per grid but the coarsest, >= 1 when
                               mg_levels > 1 (the paper uses 5)                   */
-  /* MCRT_EST_*.  ARMC and HYBRID: MCRT_FP32, the whole grid (every cell emits;
-   * no box) and one grid, on channel grids (uniform or stretched wall-normal
+  /* MCRT_EST_*.  ARMC and HYBRID: MCRT_FP32 or MCRT_FP64, the whole grid (every
+   * cell emits; no box) and one grid, on channel grids (uniform or stretched wall-normal
    * faces; deposits carry the volume ratio of the emitting and the absorbing
    * cell) and closed boxes (the x/z wall terms stay in the emitting cell); long
    * rays are handed to the warp-parallel march, which makes their deposits, as

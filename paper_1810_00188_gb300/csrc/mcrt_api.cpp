@@ -244,7 +244,6 @@ int check_solve_params(mcrt_ctx *ctx, const mcrt_solve_params *p, int b[6]) {
   if (p->estimator != MCRT_EST_ERMC && p->estimator != MCRT_EST_ARMC && p->estimator != MCRT_EST_HYBRID)
     return fail(ctx, MCRT_E_ARG, "bad estimator");
   if (p->estimator != MCRT_EST_ERMC) {
-    if (p->precision != MCRT_FP32) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: FP32 only");
     if (b[0] != 0 || b[1] != g.nx || b[2] != 0 || b[3] != g.ny || b[4] != 0 || b[5] != g.nz)
       return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: the whole grid only (every cell emits)");
     if (p->mg_levels > 1) return fail(ctx, MCRT_E_UNSUPPORTED, "ARMC / hybrid: one grid only");
@@ -763,11 +762,28 @@ int mcrt_solve_qrad(mcrt_ctx *ctx, const mcrt_solve_params *p, double *q_out, do
     }
     CK(cudaEventRecord(ctx->ev1, s), "event");
   } else {
+    const bool armc = p->estimator != MCRT_EST_ERMC && nbox > 0;
+    const long long ncg = (long long)ctx->grid.nx * ctx->grid.ny * ctx->grid.nz;
+    if (armc) {  // as in the FP32 solve
+      CK(ensure(ctx->armcbuf, (size_t)2 * 16 * ncg * sizeof(double)), "alloc ARMC sums");
+      CK(cudaMemsetAsync(ctx->armcbuf.p, 0, (size_t)2 * 16 * ncg * sizeof(double), s), "clear ARMC sums");
+      a.armc_acc = (double *)ctx->armcbuf.p;
+      a.ermc_acc = a.armc_acc + 16 * ncg;
+      a.armc_nc = ncg;
+    }
     ctx->kev_chunks = 0;
     CK(cudaEventRecord(ctx->ev0, s), "event");
     CK(mcrt::launch_trace(a, p->precision, s), "trace launch");
-    CK(cudaEventRecord(ctx->ev1, s), "event");
     launches = nbox > 0 ? 1 : 0;
+    if (armc) {
+      CK(mcrt::launch_armc_finalize(a.armc_acc, a.ermc_acc, ncg, p->rays_per_cell < 16 ? p->rays_per_cell : 16,
+                                    p->rays_per_cell, p->estimator == MCRT_EST_HYBRID,
+                                    (const double2 *)ctx->field64.p, ctx->T_min_field, ctx->T_max_field, dq, ds,
+                                    s),
+         "ARMC finalize");
+      ++launches;
+    }
+    CK(cudaEventRecord(ctx->ev1, s), "event");
   }
   ctx->last_launches = launches;
   ctx->last_stream = s;

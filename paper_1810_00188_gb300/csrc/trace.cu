@@ -144,7 +144,8 @@ __device__ __forceinline__ void axis_setup(R d, R fr, R delta, int &s, R &t0, R 
 
 constexpr int START_LANES = 8;  // waiting lanes that set up their next rays together
 
-template <typename R>
+// AR: the absorption-based estimate's deposits (a.armc_acc non-null).
+template <typename R, bool AR>
 __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
   typedef typename Prec<R>::R2 R2;
   extern __shared__ unsigned long long s_counts[];  // plain band counts, then g counts
@@ -193,6 +194,14 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
 
   Tally<R> tally;
   unsigned long long nsteps = 0, ncap = 0, nwall = 0, max_ray = 0;
+  // the absorption-based estimate (a.armc_acc non-null): each ray's deposits
+  // into the per-batch sums [16][cells] of the cells that absorb (batch: the
+  // ray's index mod 16), on a stretched grid with the volume ratio V_i / V_j
+  // (the rows' heights), and its sample into its own cell's emission-based sum
+  auto deposit = [&](double *acc, int r, unsigned c, double v) {
+    atomicAdd(acc + (size_t)(r & 15) * (size_t)a.armc_nc + c, v);
+  };
+  auto vratio = [&](int j) -> R { return yfs ? dyl(cj, 0) / dyl(j, 0) : (R)1; };
 
   // Each lane marches its rays r = lane, lane + 32, ... one after another, and a
   // lane whose ray has ended starts its next one without waiting for the rest of
@@ -327,8 +336,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
       const R Bj = bb.x + fr * bb.y;
       R alpha, trans;
       Prec<R>::absorb(kap * ds, alpha, trans);
-      X += (B_i - Bj) * (tau * alpha);  // Eq. 14 term / kappa_i
-      tau *= trans;                     // Eq. 3
+      const R term = (B_i - Bj) * (tau * alpha);
+      X += term;  // Eq. 14 term / kappa_i
+      if (AR && lin != (int)cell) deposit(a.armc_acc, r, (unsigned)lin, -(wgt * kap_i) * term * vratio(iy));
+      tau *= trans;  // Eq. 3
       B_last = Bj;
       ++steps;
       ++lsteps;
@@ -347,7 +358,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
         // closed box: a black x or z wall absorbs the rest of the ray and emits
         // at its temperature (Eq. 3 wall factor with eps = 1)
         const int f = ax == 0 ? (ix + sx < 0 ? 2 : 3) : (iz + sz < 0 ? 4 : 5);
-        X += (B_i - __ldg(bwall + f * nb + n)) * tau;
+        const R tw = (B_i - __ldg(bwall + f * nb + n)) * tau;
+        X += tw;
+        if (AR) deposit(a.armc_acc, r, cell, (wgt * kap_i) * tw);  // the cell's own exchange with the wall
         tau = 0;
         ++nwall;
         {
@@ -391,6 +404,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
           const R eps = (R)a.eps_wall[wl];
           const R Bw = __ldg(bwall + wl * nb + n);
           X += (B_i - Bw) * (tau * eps);
+          if (AR) deposit(a.armc_acc, r, cell, (wgt * kap_i) * ((B_i - Bw) * (tau * eps)));
           tau *= (R)1 - eps;
           ++nwall;
           if (eps >= (R)1 || tau <= tol) { end = true; break; }
@@ -473,6 +487,15 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceArgs a) {
     } while (false);
     if (!end) continue;
     if (tau > (R)0) X += (B_i - B_last) * tau;  // residual dump (Algorithm 1)
+    if (AR) {
+      // the residual is absorbed in the last medium cell crossed (the row
+      // clamped after a wall event)
+      const int jres = min(max(iy, 0), ny - 1);
+      const unsigned lres = (unsigned)(ix + nx * (jres + ny * iz));
+      if (tau > (R)0 && lres != cell)
+        deposit(a.armc_acc, r, lres, -(wgt * kap_i) * ((B_i - B_last) * tau) * vratio(jres));
+      deposit(a.ermc_acc, r, cell, wgt * (kap_i * X));
+    }
 
     tally.add(wgt * (kap_i * X));
     nsteps += (unsigned long long)steps;
@@ -518,7 +541,10 @@ cudaError_t launch_trace(const TraceArgs &a, int precision, cudaStream_t s) {
   const size_t smem =
       a.counts_in_smem ? sizeof(unsigned long long) * (size_t)(a.nb + a.nb * a.ng) : 0;
   if (precision != 1) return cudaErrorInvalidValue;  // FP32 solves run trace_fp32.cu's kernels
-  trace_kernel<double><<<(unsigned)blocks, threads, smem, s>>>(a);
+  if (a.armc_acc)
+    trace_kernel<double, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+  else
+    trace_kernel<double, false><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

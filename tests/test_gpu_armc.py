@@ -18,14 +18,14 @@ from paper_1810_00188_gb300 import inputs, mcrt
 pytestmark = pytest.mark.gpu
 
 
-def _solve(grid, kd, T, x, est, rays, seed, **kw):
+def _solve(grid, kd, T, x, est, rays, seed, precision=mcrt.MCRT_FP32, **kw):
     import torch
     S = mcrt.Solver(grid, kd)
     S.set_fields(torch.tensor(T, device="cuda"), torch.tensor(x, device="cuda"))
     q = torch.full(grid.shape, float("nan"), dtype=torch.float64, device="cuda")
     s = torch.full_like(q, float("nan"))
     st = torch.zeros(grid.shape, dtype=torch.int64, device="cuda")
-    S.solve_into(S.params(rays=rays, seed=seed, precision=mcrt.MCRT_FP32, estimator=est, **kw), q, s, st)
+    S.solve_into(S.params(rays=rays, seed=seed, precision=precision, estimator=est, **kw), q, s, st)
     stats = S.stats()
     S.close()
     return q.cpu().numpy(), s.cpu().numpy(), st.cpu().numpy(), stats
@@ -86,6 +86,33 @@ def test_armc_with_long_rays_handed_off():
     S.close()
 
 
+@pytest.mark.parametrize("geometry", ["channel", "stretched", "box"])
+def test_armc_fp64_against_oracle(geometry):
+    """The FP64 parity mode of the absorption-based estimate: binary64 deposits
+    into the same per-batch sums, so Q and the hybrid agree with the oracle to
+    rounding (10^-10 S_i; the atomic adds reorder the binary64 sums), sigma too,
+    and the cells' own rays take the oracle's steps exactly."""
+    if geometry == "box":
+        grid, kd, T, x = inputs.sin_cube(10, 5.0)
+    else:
+        grid, kd, T, x = inputs.nongrey_channel(10, 12, 8, seed=37, eps_wall=0.8, x_mode="field")
+        if geometry == "stretched":
+            grid.yf = inputs.channel_faces(grid.ny, grid.ly, 1.5)
+            T, x = inputs.channel_fields(grid, 37, x_mode="field")
+    rays, seed = 40, 19
+    orc = oracle.solve_armc(grid, kd, T, x, rays=rays, seed=seed, hybrid=True)
+    e = oracle.solve(grid, kd, T, x, rays=rays, seed=seed)
+    qa, sa, st, _ = _solve(grid, kd, T, x, mcrt.MCRT_EST_ARMC, rays, seed, precision=mcrt.MCRT_FP64)
+    scale = np.maximum(orc["scale"], 1e-300)
+    assert (np.abs(qa - orc["q"]) / scale).max() <= 1e-10
+    big = orc["sigma"] > 1e-6 * scale
+    np.testing.assert_allclose(sa[big], orc["sigma"][big], rtol=1e-6)
+    assert np.array_equal(st, e["steps"].astype(np.int64))
+    qh, _, _, _ = _solve(grid, kd, T, x, mcrt.MCRT_EST_HYBRID, rays, seed, precision=mcrt.MCRT_FP64)
+    sc = np.maximum(np.maximum(orc["scale"], e["scale"]), 1e-300)
+    assert (np.abs(qh - orc["q_hybrid"]) / sc).max() <= 1e-10
+
+
 def test_armc_few_rays_and_ragged_grid():
     """Fewer rays than batches (K = rays) on a ragged grid, per-cell proposals."""
     grid, kd, T, x = inputs.nongrey_channel(7, 9, 5, seed=32, x_mode="field")
@@ -133,7 +160,8 @@ def test_armc_refuses_what_it_does_not_support():
     grid, kd, T, x = inputs.nongrey_channel(8, 8, 8, seed=33)
     S = mcrt.Solver(grid, kd)
     S.set_fields(T, x)
-    for kw in (dict(precision=mcrt.MCRT_FP64), dict(box=(0, 4, 0, 8, 0, 8)), dict(mg_levels=2, mg_steps=3)):
+    for kw in (dict(box=(0, 4, 0, 8, 0, 8)), dict(mg_levels=2, mg_steps=3),
+               dict(precision=mcrt.MCRT_FP64, mg_levels=2, mg_steps=3)):
         kw.setdefault("precision", mcrt.MCRT_FP32)
         with pytest.raises(mcrt.McrtError) as e:
             S.solve(rays=4, estimator=mcrt.MCRT_EST_ARMC, **kw)

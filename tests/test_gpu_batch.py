@@ -147,6 +147,23 @@ def test_mixed_kdist_batch_uses_per_snapshot_launches():
     assert _run_and_compare(spec, {}, 130) >= 4
 
 
+def test_batch_many_rays_per_cell_tally_segments_bitwise():
+    """4100 rays per cell: three tally segments per cell.  The batch tallies add
+    a cell's segments in one warp (the single launch's reduction, and the
+    per-snapshot launches' plain-load tally), the single solves sum each segment
+    with a warp of its own and add the segments in a second kernel: the same
+    bits."""
+    kds = [inputs.make_kdist(0), inputs.make_kdist(1)]
+    spec, spec_mixed = [], []
+    for k, (nx, ny, nz) in enumerate([(8, 8, 6), (6, 10, 4)]):
+        grid = inputs.Grid(nx, ny, nz, 4.0, 2.0, 2.0, eps_wall=(0.8, 1.0), T_wall=(500.0, 1000.0))
+        T, x = inputs.channel_fields(grid, 80 + k, x_mode="field")
+        spec.append((grid, kds[0], T, x, None))
+        spec_mixed.append((grid, kds[k], T, x, None))
+    assert _run_and_compare(spec, {}, 4100, offsets=(0,)) == 3
+    assert _run_and_compare(spec_mixed, {}, 4100, offsets=(0,)) >= 4
+
+
 def test_batch_rejects_bad_items():
     import torch
     kd, snaps = _snapshots()

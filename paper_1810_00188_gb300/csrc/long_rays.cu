@@ -23,6 +23,12 @@
 // events are marched one segment at a time by the whole warp, exactly as the
 // trace kernel does.  Every lane holds the same ray state; all reductions run in
 // a fixed order, so a ray's result does not depend on the warp or launch.
+//
+// With the absorption-based estimate (AR) the march also makes the ray's
+// deposits: one lane for the segments marched one at a time, the walls and the
+// residual; in a window each lane walks its pieces again once the scan has given
+// the transmissivity at its start, and deposits each piece's term (the two
+// pieces of a segment cut at a lane boundary deposit it in two parts).
 #include <math.h>
 #include <stdint.h>
 
